@@ -1,0 +1,397 @@
+"""Benchmark: filtered backprojection of one 2048^2 slice (2048 bins, 1800 angles) on GB300.
+
+One step = the hot path over one synthetic slice: Shepp-Logan row filter (bp_filter)
+followed by the direct pixel-driven R* (bp_backproject_direct), both through the C ABI.
+Metric: backprojection pixel-angle updates per second (N^2 * n_theta per step), in G/s.
+
+Prints ONE JSON line on rank 0.  `--impl reference` times the FP64 CPU oracle instead.
+Multi-GPU (torchrun): each rank backprojects its own independent slice (no data-path
+collective); the barrier and max-over-ranks timing are the only cross-rank traffic.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+FLOPS_PER_UPDATE = 7          # coordinate FMA (2) + fraction (1) + lerp sub and FMA (3) + accumulate (1)
+FP32_LANES_PER_SM = 128       # FP32 FMA lanes per SM
+L2_FLUSH_BYTES = 256 << 20    # > 129 MB L2
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def _kernel_hash() -> str:
+    h = hashlib.sha256()
+    for fn in ("direct.cu", "common.cuh"):
+        with open(os.path.join(ROOT, "paper_1608_03589_gb300", "csrc", fn), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic_record():
+    """DRAM bytes per launch of the direct kernel from the committed ncu summary, if the
+    kernel source is unchanged since that capture; else None."""
+    path = os.path.join(ROOT, "profiles", "bp_direct_kernel_traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+        if rec.get("kernel_hash") == _kernel_hash():
+            return rec
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines: list[str] = []
+        self._t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self._t:
+            self._t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _gpu_id_for_smi(local_idx: int) -> str:
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        ids = [v.strip() for v in vis.split(",") if v.strip()]
+        if local_idx < len(ids):
+            return ids[local_idx]
+    return str(local_idx)
+
+
+def _dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ----------------------------------------------------------------------------------------------- oracle arm
+def run_reference(args, world, rank):
+    """FP64 CPU oracle on the host cores: each step backprojects a bounded pixel sample and
+    filters a bounded row sample of the same workload; throughput is extrapolated per update."""
+    if rank != 0:
+        return
+    import oracle
+    from paper_1608_03589_gb300 import synth
+
+    wl = synth.LARGE
+    g = wl.sinogram()
+    q = oracle.filter_rows(g[:8], wl.det_spacing, oracle.SHEPP_LOGAN)  # warm the library
+    q_full = g  # timing only: the per-pixel cost does not depend on the values
+    n_pix, n_rows = 2048, 60
+    rng = np.random.default_rng(0)
+    times, upd = [], 0
+    for s in range(args.warmup + args.steps):
+        pix = rng.choice(wl.N * wl.N, n_pix, replace=False)
+        rows = rng.choice(wl.n_theta, n_rows, replace=False)
+        t0 = time.perf_counter()
+        oracle.filter_rows(g[rows], wl.det_spacing, oracle.SHEPP_LOGAN)
+        t1 = time.perf_counter()
+        oracle.bp_linear_points(q_full, wl.N, wl.theta, wl.det_spacing, pix)
+        t2 = time.perf_counter()
+        if s >= args.warmup:
+            # this step's share of a full slice: n_pix / N^2 of the R* work and the same share of the filter
+            t_filter_share = (t1 - t0) * (wl.n_theta / n_rows) * (n_pix / (wl.N * wl.N))
+            times.append((t2 - t1) + t_filter_share)
+            upd += n_pix * wl.n_theta
+    total = sum(times)
+    value = upd / total / 1e9
+    cores = oracle.num_threads()
+    sample = (f"per step: oracle R* at {n_pix} random pixels x {wl.n_theta} angles plus the oracle filter on "
+              f"{n_rows} rows scaled to the same share of the slice; FP64, OpenMP")
+    line = {
+        "metric": "backprojection G pixel·angle updates/s at 2048²×1800; % of roofline",
+        "impl": "reference", "value": value, "unit": "Gupdates/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl.name, "N": wl.N, "n_det": wl.n_det, "n_theta": wl.n_theta,
+                   "filter": "shepp-logan", "step": "filter + direct R* (sampled)"},
+        "cpu_baseline": {"value": value, "unit": "Gupdates/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "Gupdates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(budget_s: float = 12.0):
+    """The oracle as it stands on this host's cores, on a bounded pixel sample of the workload."""
+    import oracle
+    from paper_1608_03589_gb300 import synth
+
+    wl = synth.LARGE
+    g = wl.sinogram()
+    rng = np.random.default_rng(1)
+    n_pix = 256
+    pix = rng.choice(wl.N * wl.N, n_pix, replace=False)
+    t0 = time.perf_counter()
+    oracle.bp_linear_points(g, wl.N, wl.theta, wl.det_spacing, pix)
+    dt_probe = time.perf_counter() - t0
+    n_pix = int(min(wl.N * wl.N, max(256, n_pix * budget_s * 0.8 / max(dt_probe, 1e-3))))
+    pix = rng.choice(wl.N * wl.N, n_pix, replace=False)
+    n_rows = 120
+    t0 = time.perf_counter()
+    oracle.filter_rows(g[:n_rows], wl.det_spacing, oracle.SHEPP_LOGAN)
+    t1 = time.perf_counter()
+    oracle.bp_linear_points(g, wl.N, wl.theta, wl.det_spacing, pix)
+    t2 = time.perf_counter()
+    t_slice = (t1 - t0) * (wl.n_theta / n_rows) + (t2 - t1) * (wl.N * wl.N / n_pix)
+    return {"value": wl.updates / t_slice / 1e9, "unit": "Gupdates/s", "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": f"FP64 oracle R* at {n_pix} random pixels x {wl.n_theta} angles and the oracle Shepp-Logan "
+                      f"filter on {n_rows} rows, extrapolated to one 2048^2 slice ({t2 - t0:.1f} s of CPU work)"}
+
+
+# ----------------------------------------------------------------------------------------------- GPU arm
+def run_gpu(args, world, rank, local):
+    import torch
+
+    import __graft_entry__
+    from paper_1608_03589_gb300 import bp, synth
+
+    if rank == 0 or world == 1:
+        __graft_entry__.build()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+        dist = dist_mod
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        if rank != 0:
+            __graft_entry__.build()
+        dist.barrier()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+
+    wl = synth.LARGE
+    g_host = wl.sinogram(slice_id=rank).astype(np.float32)
+    plan = bp.Plan(wl.N, wl.n_det, wl.theta, wl.det_spacing)
+    g = torch.from_numpy(g_host).to(dev)
+    q = torch.empty_like(g)
+    img = torch.empty((wl.N, wl.N), dtype=torch.float32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        plan.filter(g, "shepp-logan", out=q)
+        plan.backproject(q, out=img)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+        flush.zero_()
+    torch.cuda.synchronize()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    sampler = ClockSampler(_gpu_id_for_smi(local))
+    sampler.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush.zero_()  # L2 flush outside the timed interval
+        e0, e1, e2 = ev[i]
+        e0.record(stream)
+        plan.filter(g, "shepp-logan", out=q)
+        e1.record(stream)
+        plan.backproject(q, out=img)
+        e2.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    step_ms = [a.elapsed_time(c) for a, b, c in ev]
+    bp_ms = [b.elapsed_time(c) for a, b, c in ev]
+    filt_ms = [a.elapsed_time(b) for a, b, c in ev]
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+
+    # end to end through the host-buffer C-ABI call: pinned host sinogram in, host image out
+    g_pin = torch.from_numpy(g_host).pin_memory()
+    img_pin = torch.empty((wl.N, wl.N), dtype=torch.float32).pin_memory()
+    plan.fbp_host(g_pin, "shepp-logan", out=img_pin)
+    n_e2e = max(3, min(args.steps, 20))
+    if dist:
+        dist.barrier()
+    e2e_t = 0.0
+    for _ in range(n_e2e):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        plan.fbp_host(g_pin, "shepp-logan", out=img_pin)
+        e2e_t += time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_t], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_t = float(t.item())
+
+    # other operators of the path on the same slice (reported, not part of the step)
+    extra = {}
+    def timed(fn, reps=10):
+        fn()
+        torch.cuda.synchronize()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        tot = 0.0
+        for _ in range(reps):
+            flush.zero_()
+            s.record(stream)
+            fn()
+            e.record(stream)
+            torch.cuda.synchronize()
+            tot += s.elapsed_time(e)
+        return tot / reps
+    try:
+        ms = timed(lambda: plan.backproject_fourier(q, out=img))
+        extra["fourier_backprojection"] = {"ms": ms, "equiv_Gupdates_s": wl.updates / ms / 1e6}
+    except bp.BPError as exc:
+        extra["fourier_backprojection"] = {"unavailable": str(exc)[:120]}
+    try:
+        ms = timed(lambda: plan.radon(img, out=q))
+        extra["radon_direct"] = {"ms": ms, "Gupdates_s": wl.updates / ms / 1e6}
+    except bp.BPError as exc:
+        extra["radon_direct"] = {"unavailable": str(exc)[:120]}
+    try:
+        q16 = q.to(torch.bfloat16)
+        ms = timed(lambda: plan.backproject(q16, out=img))
+        extra["direct_bf16_storage"] = {"ms": ms, "Gupdates_s": wl.updates / ms / 1e6}
+    except bp.BPError as exc:
+        extra["direct_bf16_storage"] = {"unavailable": str(exc)[:120]}
+
+    if rank != 0:
+        if dist:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    props = torch.cuda.get_device_properties(dev)
+    peaks = _peaks()
+    sm_max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_tflops = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12
+    bp_avg_s = statistics.mean(bp_ms) / 1e3
+    achieved = wl.updates * FLOPS_PER_UPDATE / bp_avg_s / 1e12
+    traffic = _traffic_record()
+    updates_all = wl.updates * world * args.steps
+    line = {
+        "metric": "backprojection G pixel·angle updates/s at 2048²×1800; % of roofline",
+        "value": updates_all / (total_ms / 1e3) / 1e9,
+        "unit": "Gupdates/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": wl.name, "N": wl.N, "n_det": wl.n_det, "n_theta": wl.n_theta,
+                   "phantom": "50 seeded random ellipses + 1% Gaussian noise", "filter": "shepp-logan",
+                   "step": "bp_filter + bp_backproject_direct", "l2": "flushed (256 MiB write) between steps",
+                   "parallelism": f"independent slice per GPU x{world}"},
+        "roofline": {"bound": "alu", "kernel": "bp_direct_kernel", "achieved": achieved,
+                     "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
+                     "flops_per_update": FLOPS_PER_UPDATE,
+                     "peak_basis": f"{props.multi_processor_count} SM x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
+                                   f"{sm_max_mhz:.0f} MHz (max SM clock)",
+                     "traffic": (traffic["dram_bytes_per_launch"] if traffic else None),
+                     "algorithmic_bytes": wl.n_theta * wl.n_det * 4 + wl.N * wl.N * 4,
+                     "kernel_ms": bp_avg_s * 1e3, "filter_ms": statistics.mean(filt_ms)},
+        "e2e": {"value": wl.updates * world * n_e2e / e2e_t / 1e9, "unit": "Gupdates/s",
+                "h2d_bytes_per_step": g_host.nbytes, "d2h_bytes_per_step": wl.N * wl.N * 4,
+                "call": "bp_fbp_host (pinned host in/out)"},
+        "gpu_launches": 2 * args.steps,
+        "clocks": clocks,
+        "paths": extra,
+    }
+    if not args.no_cpu_baseline:
+        try:
+            line["cpu_baseline"] = cpu_baseline()
+        except Exception as exc:  # pragma: no cover
+            line["cpu_baseline"] = {"unavailable": str(exc)[:120]}
+    print(json.dumps(line), flush=True)
+    plan.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    world, rank, local = _dist_init()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_gpu(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

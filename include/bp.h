@@ -1,0 +1,170 @@
+/*
+ * bp.h -- C ABI of the GB300 (sm_103a) 2D parallel-beam backprojection library.
+ *
+ * Operators of Koshev, Helou & Miqueles, "Fast Backprojection Techniques for High
+ * Resolution Tomography" (arXiv:1608.03589):
+ *   - R*  backprojection, Section 1 eq "B", discretised as Section 2 eq "bp_app";
+ *   - the Backprojection-Slice-Theorem (Fourier) form of R*, Section 3 eq "bst",
+ *     Section 5.3 Steps 1-4;
+ *   - the FBP filter F of Section 3 Remark 1(ii) eq "fbp" and the Tikhonov filter of
+ *     Section 6;
+ *   - R, the Radon transform of Section 1 eq "P_theta", realised as the exact
+ *     (scaled) transpose of each discrete R*, so that the discrete form of the adjoint
+ *     identity (Section 1 eq "adjoint") holds.
+ *
+ * Geometry (Table "tab:symbols", Section 5), shared by every entry point:
+ *   image      img[b][iy][ix], N x N float32, row-major, y along rows; pixel centres
+ *              x_i = -1 + (i + 1/2) * dx, dx = 2/N, covering [-1, 1]^2.
+ *   sinogram   sino[b][k][j], n_theta x n_det, row-major (one projection per row);
+ *              detector centres t_j = (j - (n_det - 1)/2) * det_spacing.
+ *   angles     theta[k] in radians, any order, any value (taken mod pi for weights).
+ *   weights    w_k = half the sum of the two angular gaps around theta_k (mod pi);
+ *              w_k = pi / n_theta for theta_k = k pi / n_theta (eq "bp_app").
+ *   R*  (direct)   img[p] = sum_k w_k * lerp(sino[k], u_pk),
+ *                  u_pk = (x_p . xi_k)/det_spacing + (n_det - 1)/2, zero off-detector.
+ *   R   (direct)   sino[k][j] = (dx^2 / det_spacing) * sum_p hat(u_pk - j) * img[p].
+ *
+ * Conventions for every call:
+ *   - Device pointers are caller-owned CUDA device memory on the plan's device,
+ *     contiguous, 16-byte aligned; `batch` slices are packed back to back.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  All calls are
+ *     asynchronous on it unless stated otherwise; the returned status covers argument
+ *     validation and launch errors only.
+ *   - No call aborts the process.  On error the call returns a non-zero bp_status and
+ *     bp_last_error() returns a message (thread-local, valid until the next call on the
+ *     same thread).  A plan is not thread-safe: one plan per concurrently used stream.
+ *   - The calling thread must have the plan's device current.
+ */
+#ifndef BP_H
+#define BP_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bp_plan bp_plan; /* opaque */
+
+typedef enum {
+    BP_OK = 0,
+    BP_ERR_INVALID_ARG = 1,  /* null pointer, bad size, bad enum, misaligned pointer */
+    BP_ERR_CUDA = 2,         /* a CUDA runtime call or kernel launch failed */
+    BP_ERR_OOM = 3,          /* device or host allocation failed (nothing leaked) */
+    BP_ERR_UNSUPPORTED = 4,  /* valid request outside this build's limits */
+    BP_ERR_TIMEOUT = 5       /* a bounded device-side wait gave up (batched path) */
+} bp_status;
+
+typedef enum { BP_F32 = 0, BP_BF16 = 1, BP_F16 = 2 } bp_dtype;
+
+typedef enum {
+    BP_RAMLAK = 0,       /* |nu| band-limited to |nu| <= 1/(2 dt) (eq "fbp") */
+    BP_SHEPP_LOGAN = 1,  /* |nu| sinc(nu dt) */
+    BP_TIKHONOV = 2      /* |nu| / (1 + param |nu|), Section 6 (nu in cycles per unit t) */
+} bp_filter_kind;
+
+/* Limits of this build (BP_ERR_UNSUPPORTED beyond them). */
+#define BP_MAX_N 16384
+#define BP_MAX_NDET 16384
+#define BP_MAX_NTHETA 65536
+
+/*
+ * bp_plan_create -- geometry, angle tables and device workspaces for one geometry.
+ *   N            image side (pixels), 1..BP_MAX_N.
+ *   n_det        detector bins per projection, 1..BP_MAX_NDET.
+ *   n_theta      number of projections, 1..BP_MAX_NTHETA.
+ *   theta        host array of n_theta angles (radians, finite); copied, caller keeps it.
+ *   det_spacing  detector bin width in image units (> 0, finite); 2/n_det covers [-1, 1].
+ * Builds in FP64 on the host: the quadrature weights w_k, the per-angle coordinate
+ * tables (Section 2, eq "bp_app") and uploads them to the current device.  Fourier-path
+ * and filter workspaces are allocated on their first use (make that first call before
+ * any CUDA-graph capture).  Returns NULL on error (see bp_last_error()).
+ */
+bp_plan *bp_plan_create(int N, int n_det, int n_theta, const double *theta, double det_spacing);
+
+/* Release every device and host resource of the plan (NULL is a no-op).  Synchronises
+ * the plan's device before freeing. */
+void bp_destroy(bp_plan *plan);
+
+/*
+ * bp_filter -- FBP row filter, Section 3 Remark 1(ii) eq "fbp" (and Section 6 for
+ * BP_TIKHONOV): sino_out[b][k][j] = dt * sum_{i=0}^{n_det-1} h(j - i) * sino_in[b][k][i],
+ * a linear (zero-extended, non-circular) convolution with the band-limited spatial
+ * kernel h of the chosen frequency response, computed by FFT in float32.
+ *   sino_in   device, batch x n_theta x n_det elements of `dtype`.
+ *   sino_out  device, batch x n_theta x n_det float32; may equal sino_in only for BP_F32.
+ *   param     lambda for BP_TIKHONOV (>= 0), ignored otherwise.
+ */
+bp_status bp_filter(bp_plan *plan, const void *sino_in, bp_dtype dtype, float *sino_out,
+                    bp_filter_kind kind, float param, int batch, void *stream);
+
+/*
+ * bp_backproject_direct -- pixel-driven R* with linear interpolation, Section 2 eq
+ * "bp_app".  float32 interpolation and accumulation; BF16/F16 sinograms are widened
+ * to float32 on load.
+ *   sino        device, batch x n_theta x n_det elements of `dtype`.
+ *   img         device, batch x N x N float32 (output).
+ *   accumulate  0: img = R* sino;  1: img += R* sino.
+ */
+bp_status bp_backproject_direct(bp_plan *plan, const void *sino, bp_dtype dtype, float *img,
+                                int batch, int accumulate, void *stream);
+
+/*
+ * bp_backproject_fourier -- the Backprojection Slice Theorem form of R* (Section 3, eq
+ * "bst"; Section 5.3 Steps 2.2-4), realised as a type-1 non-uniform FFT: each projection
+ * is zero-padded to P = 2^ceil(log2(2 n_det)) and transformed (Step 2.2); its samples
+ * on the polar ray are spread onto a 2N x 2N Cartesian frequency grid with a
+ * Kaiser-Bessel kernel of width 6 (Step 3; the polar Jacobian |sigma| cancels the
+ * BST's 1/sigma, Section 6 eq "reg_fbp"); a 2D inverse FFT (Step 4) and
+ * deapodisation give the image.  It computes R* of the band-limited (trigonometric)
+ * interpolant of each projection (Nyquist bin dropped), up to the gridding error.
+ *   sino, dtype, img, batch as for bp_backproject_direct (img is overwritten).
+ * First call allocates the plan's Fourier workspace (about 8 (2N)^2 bytes + 8 n_theta P/2).
+ */
+bp_status bp_backproject_fourier(bp_plan *plan, const void *sino, bp_dtype dtype, float *img,
+                                 int batch, void *stream);
+
+/*
+ * bp_radon -- R, the forward Radon transform (Section 1 eq "P_theta"), as the scaled
+ * exact transpose of a discrete R*:  R = (dx^2/dt) diag(1/w_k) A^T  where A is the
+ * matrix of R*.  With fourier_adjoint = 0, A is the direct (linear-interpolation) R*;
+ * with fourier_adjoint = 1, A is the Fourier-path R* (band-limited interpolation).
+ *   img   device, batch x N x N float32.
+ *   sino  device, batch x n_theta x n_det float32 (output, overwritten).
+ */
+bp_status bp_radon(bp_plan *plan, const float *img, float *sino, int batch, int fourier_adjoint,
+                   void *stream);
+
+/*
+ * bp_fbp_host -- filtered backprojection from HOST memory to HOST memory:
+ * copy sino (host, batch x n_theta x n_det float32) to the device, bp_filter(kind, param),
+ * bp_backproject_direct, copy the image back into img (host, batch x N x N float32),
+ * and synchronise the stream before returning.  Pinned host memory gives asynchronous
+ * copies; pageable memory also works.  Device staging buffers are owned by the plan
+ * and allocated on the first call (sized for `batch`; a larger batch reallocates).
+ */
+bp_status bp_fbp_host(bp_plan *plan, const float *sino, float *img, bp_filter_kind kind,
+                      float param, int batch, void *stream);
+
+/*
+ * bp_backproject_batched -- R* (direct) of n independent slices with possibly different
+ * geometries in ONE persistent kernel launch: CTAs pull (slice, tile) work items from a
+ * device counter.  plans[i] gives slice i's geometry (all on the same device);
+ * sinos[i] / imgs[i] are device pointers, dtypes[i] the sinogram element type.
+ * The descriptor upload uses the first plan's stream-ordered workspace, so the call is
+ * graph-capturable after one warm-up call with the same n.
+ */
+bp_status bp_backproject_batched(bp_plan *const *plans, const void *const *sinos,
+                                 const bp_dtype *dtypes, float *const *imgs, int n, void *stream);
+
+/* Last error message of the calling thread ("" if none). */
+const char *bp_last_error(void);
+
+/* Library version string, e.g. "bp 0.1 sm_103a". */
+const char *bp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BP_H */

@@ -1,0 +1,130 @@
+// Shared declarations of the sm_103a backprojection library (internal, not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "bp.h"
+
+namespace bp {
+
+// ------------------------------------------------------------------------------ errors
+void set_error(const std::string &msg);
+bp_status fail(bp_status st, const std::string &msg);
+bp_status cuda_fail(cudaError_t e, const char *what);
+
+#define BP_CUDA_TRY(expr)                                         \
+    do {                                                          \
+        cudaError_t _e = (expr);                                  \
+        if (_e != cudaSuccess) return ::bp::cuda_fail(_e, #expr); \
+    } while (0)
+
+// ------------------------------------------------------------------------------ geometry
+// Direct kernels work on square pixel tiles; the per-angle table below gives the
+// detector coordinate u (in bins) of pixel (0,0) and its change per tile, in 32.32
+// fixed point (exact integer tile stepping), plus the per-pixel steps in float.
+constexpr int kTile = 64;         // pixel tile side of the direct R* / R kernels
+constexpr int kStage = 16;        // angles per shared-memory stage
+constexpr int kThreads = 256;     // threads per CTA of the direct kernels
+
+struct AngleParam {
+    long long U00;  // u(pixel 0,0) * 2^32
+    long long CT;   // u step per tile along x (kTile pixels) * 2^32
+    long long ST;   // u step per tile along y * 2^32
+    float c;        // u step per pixel along x = cos(theta) dx/dt
+    float s;        // u step per pixel along y = sin(theta) dx/dt
+    float w;        // quadrature weight w_k
+    float pad;
+};
+static_assert(sizeof(AngleParam) == 40, "AngleParam layout");
+
+// Fourier-path workspace (allocated on first use).
+struct FourierWork {
+    int M = 0;            // oversampled grid side (2N)
+    int P = 0;            // per-projection FFT length
+    int band = 0;         // number of grid rows/cols that can hold nonzeros
+    float2 *spec = nullptr;   // [n_theta][P/2] scaled projection half-spectra
+    float2 *grid = nullptr;   // [M][M] gridded spectrum (or [band][M])
+    float2 *mid = nullptr;    // [band][N] after the first 1D IFFT pass
+    float *deapod = nullptr;  // [N] separable deapodisation 1/phi_hat
+    float *kb = nullptr;      // kernel lookup table
+    float2 *twM = nullptr;    // M-point twiddles
+    float kb_beta = 0.f;
+    int kb_width = 6;
+    int kb_tab_n = 0;
+    size_t bytes = 0;
+};
+
+}  // namespace bp
+
+struct bp_plan {
+    int N = 0, n_det = 0, n_theta = 0;
+    double dt = 0.0, dx = 0.0;
+    int device = 0;
+    std::vector<double> theta, w;
+    // direct kernels
+    bp::AngleParam *d_ang = nullptr;
+    int W = 0;   // shared-memory window (entries) per (tile, angle)
+    int C = 0;   // window centre offset
+    // filter
+    int P = 0;                 // FFT length for the filter (power of two >= 2 n_det)
+    float2 *d_twP = nullptr;   // P/2 twiddles exp(-2 pi i r / P)
+    float *d_H[3] = {nullptr, nullptr, nullptr};   // bit-reversed scaled responses per kind
+    float H_param[3] = {0.f, 0.f, 0.f};
+    // Fourier path
+    bp::FourierWork four;
+    // host-buffer entry point staging
+    float *d_stage = nullptr;
+    size_t stage_batch = 0;
+    // batched descriptors
+    void *d_desc = nullptr;
+    size_t desc_cap = 0;
+    int *d_counter = nullptr;
+    int *d_status = nullptr;
+};
+
+namespace bp {
+bp_status check_plan(const bp_plan *p);
+bool aligned16(const void *ptr);
+int ilog2(int v);
+
+// launchers implemented in the kernel translation units
+bp_status launch_direct(bp_plan *p, const void *sino, bp_dtype dt, float *img, int batch, int accumulate,
+                        cudaStream_t st);
+bp_status launch_filter(bp_plan *p, const void *in, bp_dtype dt, float *out, int kind, float param, int batch,
+                        cudaStream_t st);
+bp_status launch_radon_direct(bp_plan *p, const float *img, float *sino, int batch, cudaStream_t st);
+bp_status launch_fourier(bp_plan *p, const void *sino, bp_dtype dt, float *img, int batch, cudaStream_t st);
+bp_status launch_radon_fourier(bp_plan *p, const float *img, float *sino, int batch, cudaStream_t st);
+bp_status ensure_filter(bp_plan *p, int kind, float param);
+bp_status ensure_fourier(bp_plan *p);
+void free_fourier(bp_plan *p);
+bp_status launch_batched(bp_plan *const *plans, const void *const *sinos, const bp_dtype *dtypes,
+                         float *const *imgs, int n, cudaStream_t st);
+
+// host FP64 FFT (plan tables only): in-place radix-2, sign -1 forward
+void host_fft(std::vector<double> &re, std::vector<double> &im, bool inverse);
+
+// element loads, widened to float
+template <typename T> __device__ __forceinline__ float load_f(const T *p);
+template <> __device__ __forceinline__ float load_f<float>(const float *p) { return __ldg(p); }
+template <> __device__ __forceinline__ float load_f<__nv_bfloat16>(const __nv_bfloat16 *p) {
+    return __bfloat162float(__ldg(p));
+}
+template <> __device__ __forceinline__ float load_f<__half>(const __half *p) { return __half2float(__ldg(p)); }
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ float2 lds64(unsigned addr) {
+    float2 v;
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(addr));
+    return v;
+}
+
+}  // namespace bp

@@ -1,0 +1,146 @@
+// FBP row filter (Section 3, Remark 1 (ii), eq "fbp"; Section 6 for the Tikhonov filter).
+//
+// q_j = dt * sum_{i<n_det} h(j - i) g_i  (linear convolution with the band-limited spatial
+// kernel h of the filter's frequency response) computed as a circular convolution of
+// length P >= 2 n_det - 1:  q = IFFT( FFT(g zero-padded) * H ),  H = (dt/P) DFT_P(h_circ),
+// h_circ[r] = h(r) for r < n_det, h_circ[P - r] = h(-r).  H is real and even, so two real
+// rows travel together as one complex row (a + i b): the real and imaginary parts of the
+// result are the two filtered rows.  One CTA per row pair, the whole P-point transform in
+// shared memory; the forward DIF leaves the spectrum bit-reversed, H is stored
+// bit-reversed, and the inverse DIT restores natural order.
+#include <algorithm>
+#include <cmath>
+
+#include "common.cuh"
+#include "fft.cuh"
+
+namespace bp {
+
+namespace {
+
+template <typename Tin>
+__global__ void __launch_bounds__(512)
+filter_kernel(const Tin *__restrict__ in, float *__restrict__ out, const float *__restrict__ Hbr,
+              const float2 *__restrict__ tw, long long rows, int n_det, int logP) {
+    extern __shared__ __align__(16) float2 z[];
+    const int P = 1 << logP;
+    const long long r0 = 2 * (long long)blockIdx.x, r1 = r0 + 1;
+    const bool has1 = r1 < rows;
+    const Tin *a = in + r0 * n_det;
+    const Tin *b = in + r1 * n_det;
+    for (int j = threadIdx.x; j < P; j += blockDim.x) {
+        float va = 0.f, vb = 0.f;
+        if (j < n_det) {
+            va = load_f(a + j);
+            if (has1) vb = load_f(b + j);
+        }
+        z[j] = make_float2(va, vb);
+    }
+    __syncthreads();
+    fft_dif_fwd(z, logP, tw, 1);
+    for (int j = threadIdx.x; j < P; j += blockDim.x) {
+        const float h = __ldg(Hbr + j);
+        const float2 v = z[j];
+        z[j] = make_float2(v.x * h, v.y * h);
+    }
+    __syncthreads();
+    fft_dit_inv(z, logP, tw, 1);
+    float *oa = out + r0 * n_det;
+    float *ob = out + r1 * n_det;
+    for (int j = threadIdx.x; j < n_det; j += blockDim.x) {
+        const float2 v = z[j];
+        oa[j] = v.x;
+        if (has1) ob[j] = v.y;
+    }
+}
+
+// Spatial taps h(n), |n| < n_det, of the three filters (host, FP64).
+void filter_taps(int kind, double dt, double lam, int n_det, std::vector<double> &h /* index n + n_det - 1 */) {
+    h.assign(2 * n_det - 1, 0.0);
+    if (kind == BP_RAMLAK) {
+        for (int n = -(n_det - 1); n <= n_det - 1; ++n) {
+            double v = 0.0;
+            if (n == 0) v = 1.0 / (4.0 * dt * dt);
+            else if (n & 1) v = -1.0 / (M_PI * M_PI * (double)n * (double)n * dt * dt);
+            h[n + n_det - 1] = v;
+        }
+    } else if (kind == BP_SHEPP_LOGAN) {
+        for (int n = -(n_det - 1); n <= n_det - 1; ++n)
+            h[n + n_det - 1] = -2.0 / (M_PI * M_PI * dt * dt * (4.0 * (double)n * (double)n - 1.0));
+    } else {
+        // h(n) = 2 int_0^{W} nu/(1 + lam nu) cos(2 pi nu n dt) d nu, W = 1/(2 dt), by composite
+        // Simpson on 2^16 panels.  With nu_i = i W / M the cosine is cos(pi i n / M), so all taps
+        // are one DCT-I of the weighted samples, evaluated with a 2M-point FFT.
+        const int M = 1 << 16;
+        const double Wn = 0.5 / dt, hs = Wn / M;
+        std::vector<double> re(2 * M, 0.0), im(2 * M, 0.0), a(M + 1);
+        for (int i = 0; i <= M; ++i) {
+            const double nu = i * hs;
+            const double c = (i == 0 || i == M) ? 1.0 : ((i & 1) ? 4.0 : 2.0);
+            a[i] = c * nu / (1.0 + lam * nu);
+        }
+        for (int i = 0; i <= M; ++i) re[i] = a[i];
+        for (int i = 1; i < M; ++i) re[2 * M - i] = a[i];
+        host_fft(re, im, false);
+        for (int n = -(n_det - 1); n <= n_det - 1; ++n) {
+            const int an = n < 0 ? -n : n;
+            const double sgn = (an & 1) ? -1.0 : 1.0;
+            const double s = 0.5 * (re[an] + a[0] + sgn * a[M]);
+            h[n + n_det - 1] = 2.0 * s * hs / 3.0;
+        }
+    }
+}
+
+}  // namespace
+
+bp_status ensure_filter(bp_plan *p, int kind, float param) {
+    if (p->d_H[kind] && (kind != BP_TIKHONOV || p->H_param[kind] == param)) return BP_OK;
+    const int P = p->P, n = p->n_det, logP = ilog2(P);
+    std::vector<double> h;
+    filter_taps(kind, p->dt, (double)param, n, h);
+    std::vector<double> re(P, 0.0), im(P, 0.0);
+    for (int r = 0; r < n; ++r) re[r] = h[r + n - 1];
+    for (int r = 1; r < n; ++r) re[P - r] = h[-r + n - 1];
+    host_fft(re, im, false);
+    std::vector<float> Hbr(P);
+    const double scale = p->dt / P;
+    for (int i = 0; i < P; ++i) {
+        unsigned v = (unsigned)i, r = 0;
+        for (int b = 0; b < logP; ++b) { r = (r << 1) | (v & 1u); v >>= 1; }
+        Hbr[i] = (float)(re[r] * scale);
+    }
+    if (!p->d_H[kind]) BP_CUDA_TRY(cudaMalloc(&p->d_H[kind], sizeof(float) * P));
+    BP_CUDA_TRY(cudaMemcpy(p->d_H[kind], Hbr.data(), sizeof(float) * P, cudaMemcpyHostToDevice));
+    p->H_param[kind] = param;
+    return BP_OK;
+}
+
+bp_status launch_filter(bp_plan *p, const void *in, bp_dtype dt, float *out, int kind, float param, int batch,
+                        cudaStream_t st) {
+    if ((size_t)p->P * sizeof(float2) > 200u * 1024u)
+        return fail(BP_ERR_UNSUPPORTED, "filter: n_det too large for the shared-memory FFT (n_det <= 8192)");
+    bp_status s = ensure_filter(p, kind, param);
+    if (s != BP_OK) return s;
+    const long long rows = (long long)batch * p->n_theta;
+    const int logP = ilog2(p->P);
+    const int threads = std::min(512, std::max(32, p->P / 2));
+    const size_t smem = sizeof(float2) * p->P;
+    const unsigned blocks = (unsigned)((rows + 1) / 2);
+#define BP_FILTER_LAUNCH(T)                                                                               \
+    do {                                                                                                  \
+        BP_CUDA_TRY(cudaFuncSetAttribute(filter_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
+                                         (int)smem));                                                     \
+        filter_kernel<T><<<blocks, threads, smem, st>>>((const T *)in, out, p->d_H[kind], p->d_twP, rows, \
+                                                        p->n_det, logP);                                  \
+    } while (0)
+    switch (dt) {
+        case BP_F32: BP_FILTER_LAUNCH(float); break;
+        case BP_BF16: BP_FILTER_LAUNCH(__nv_bfloat16); break;
+        case BP_F16: BP_FILTER_LAUNCH(__half); break;
+    }
+#undef BP_FILTER_LAUNCH
+    BP_CUDA_TRY(cudaGetLastError());
+    return BP_OK;
+}
+
+}  // namespace bp

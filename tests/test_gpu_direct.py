@@ -1,0 +1,182 @@
+"""GPU parity of the direct path (filter, R*, R) against the FP64 oracle, through the C ABI."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from gpu_util import (TOL_DIRECT, bp, dev, random_theta, rounded, sample_pixels, synth, to_dev)
+
+pytestmark = pytest.mark.gpu
+
+
+# ----------------------------------------------------------------------------------- R* (direct)
+def test_direct_small_workload():
+    wl = synth.SMALL
+    q = oracle.filter_rows(wl.sinogram(), wl.det_spacing, oracle.RAMLAK)
+    qd = to_dev(q)
+    plan = bp.Plan(wl.N, wl.n_det, wl.theta, wl.det_spacing)
+    img = plan.backproject(qd)
+    ref = oracle.bp_linear(rounded(qd), wl.N, wl.theta, wl.det_spacing)
+    assert oracle.rel_l2(img.cpu().numpy(), ref) <= TOL_DIRECT
+
+
+@pytest.mark.parametrize("N,n_det,n_theta,dt_scale,seed", [
+    (1, 1, 1, 1.0, 0), (2, 3, 2, 1.0, 1), (37, 41, 7, 1.0, 2), (65, 64, 33, 1.3, 3),
+    (130, 90, 50, 0.7, 4), (64, 100, 17, 0.5, 5), (200, 257, 181, 1.0, 6), (129, 129, 16, 1.0, 7)])
+def test_direct_ragged(N, n_det, n_theta, dt_scale, seed):
+    rng = np.random.default_rng(seed)
+    theta = random_theta(rng, n_theta) if seed % 2 else synth.uniform_theta(n_theta)
+    dt = dt_scale * 2.0 / n_det
+    g = rng.normal(size=(n_theta, n_det))
+    gd = to_dev(g)
+    plan = bp.Plan(N, n_det, theta, dt)
+    img = plan.backproject(gd)
+    ref = oracle.bp_linear(rounded(gd), N, theta, dt)
+    assert oracle.rel_l2(img.cpu().numpy(), ref) <= TOL_DIRECT
+
+
+def test_direct_unsupported_geometry_is_an_error():
+    with pytest.raises(bp.BPError, match="window"):
+        bp.Plan(64, 1000, synth.uniform_theta(8), 0.0005)
+
+
+def test_direct_accumulate_and_batch():
+    rng = np.random.default_rng(9)
+    N, n_det, n_theta = 96, 80, 45
+    theta = synth.uniform_theta(n_theta)
+    plan = bp.Plan(N, n_det, theta)
+    g = to_dev(rng.normal(size=(3, n_theta, n_det)))
+    out = plan.backproject(g)
+    for i in range(3):
+        single = plan.backproject(g[i].contiguous())
+        assert torch.equal(single, out[i])
+    base = to_dev(rng.normal(size=(3, N, N)))
+    acc = base.clone()
+    plan.backproject(g, out=acc, accumulate=True)
+    assert torch.allclose(acc, base + out, rtol=0, atol=1e-5)
+
+
+@pytest.mark.parametrize("dtype", [torch.bfloat16, torch.float16])
+def test_direct_low_precision_storage(dtype):
+    # 16-bit sinogram storage, float32 interpolation and accumulation: parity against the
+    # oracle on the same rounded values; the error of the rounding itself is only reported.
+    wl = synth.SMALL
+    q = oracle.filter_rows(wl.sinogram(), wl.det_spacing, oracle.SHEPP_LOGAN)
+    plan = bp.Plan(wl.N, wl.n_det, wl.theta, wl.det_spacing)
+    q16 = to_dev(q, dtype)
+    img = plan.backproject(q16)
+    ref = oracle.bp_linear(rounded(q16), wl.N, wl.theta, wl.det_spacing)
+    assert oracle.rel_l2(img.cpu().numpy(), ref) <= TOL_DIRECT
+    full = oracle.bp_linear(q, wl.N, wl.theta, wl.det_spacing)
+    print(f"{dtype}: storage-rounding error vs FP64 input {oracle.rel_l2(img.cpu().numpy(), full):.2e}")
+
+
+def test_direct_full_size_sampled():
+    # 2048^2 image, 2048 bins, 1800 angles, Shepp-Logan-filtered noisy 50-ellipse sinogram:
+    # the full launch, checked on sampled pixels that the oracle evaluates one by one.
+    wl = synth.LARGE
+    plan = bp.Plan(wl.N, wl.n_det, wl.theta, wl.det_spacing)
+    q = plan.filter(to_dev(wl.sinogram()), "shepp-logan")
+    img = plan.backproject(q)
+    pix = sample_pixels(wl.N, 400, seed=1)
+    ref = oracle.bp_linear_points(rounded(q), wl.N, wl.theta, wl.det_spacing, pix)
+    got = img.reshape(-1)[torch.from_numpy(pix).to(dev())].cpu().numpy()
+    assert oracle.rel_l2(got, ref) <= TOL_DIRECT
+
+
+# ----------------------------------------------------------------------------------- filter
+@pytest.mark.parametrize("kind,param", [("ramlak", 0.0), ("shepp-logan", 0.0), ("tikhonov", 0.02)])
+@pytest.mark.parametrize("n_det,rows", [(256, 180), (41, 7), (1, 3), (2048, 64)])
+def test_filter_parity(kind, param, n_det, rows):
+    okind = {"ramlak": oracle.RAMLAK, "shepp-logan": oracle.SHEPP_LOGAN, "tikhonov": oracle.TIKHONOV}[kind]
+    e = synth.random_ellipses(10, seed=n_det)
+    th = synth.uniform_theta(rows)
+    g = synth.add_gaussian_noise(synth.ellipse_sinogram(e, th, n_det), 0.01, seed=3)
+    gd = to_dev(g)
+    plan = bp.Plan(16, n_det, th)
+    q = plan.filter(gd, kind, param)
+    ref = oracle.filter_rows(rounded(gd), 2.0 / n_det, okind, param)
+    assert oracle.rel_l2(q.cpu().numpy(), ref) <= TOL_DIRECT
+
+
+def test_filter_in_place_and_low_precision():
+    wl = synth.SMALL
+    g = wl.sinogram()
+    plan = bp.Plan(wl.N, wl.n_det, wl.theta)
+    gd = to_dev(g)
+    ref = plan.filter(gd, "ramlak")
+    inplace = gd.clone()
+    plan.filter(inplace, "ramlak", out=inplace)
+    assert torch.equal(inplace, ref)
+    g16 = to_dev(g, torch.bfloat16)
+    q16 = plan.filter(g16, "ramlak")
+    ref16 = oracle.filter_rows(rounded(g16), wl.det_spacing, oracle.RAMLAK)
+    assert oracle.rel_l2(q16.cpu().numpy(), ref16) <= TOL_DIRECT
+
+
+# ----------------------------------------------------------------------------------- R (direct transpose)
+def test_radon_small_workload():
+    wl = synth.SMALL
+    e = synth.random_ellipses(wl.n_ellipses, wl.seed)
+    f = to_dev(synth.ellipse_image(e, wl.N, supersample=2))
+    plan = bp.Plan(wl.N, wl.n_det, wl.theta, wl.det_spacing)
+    g = plan.radon(f)
+    ref = oracle.radon(rounded(f), wl.n_det, wl.theta, wl.det_spacing)
+    assert oracle.rel_l2(g.cpu().numpy(), ref) <= TOL_DIRECT
+
+
+@pytest.mark.parametrize("N,n_det,n_theta,dt_scale,seed", [
+    (1, 1, 1, 1.0, 0), (37, 41, 7, 1.0, 2), (65, 64, 33, 1.3, 3), (130, 90, 50, 0.7, 4), (64, 100, 17, 0.5, 5)])
+def test_radon_ragged(N, n_det, n_theta, dt_scale, seed):
+    rng = np.random.default_rng(seed)
+    theta = random_theta(rng, n_theta)
+    dt = dt_scale * 2.0 / n_det
+    fd = to_dev(rng.normal(size=(2, N, N)))
+    plan = bp.Plan(N, n_det, theta, dt)
+    g = plan.radon(fd)
+    for i in range(2):
+        ref = oracle.radon(rounded(fd[i]), n_det, theta, dt)
+        assert oracle.rel_l2(g[i].cpu().numpy(), ref) <= TOL_DIRECT
+
+
+def test_radon_full_size_sampled_angles():
+    wl = synth.LARGE
+    e = synth.random_ellipses(wl.n_ellipses, wl.seed)
+    f = to_dev(synth.ellipse_image(e, wl.N))
+    plan = bp.Plan(wl.N, wl.n_det, wl.theta, wl.det_spacing)
+    g = plan.radon(f)
+    ks = np.array([0, 1, 449, 450, 451, 899, 900, 1234, 1799])
+    ref = oracle.radon(rounded(f), wl.n_det, wl.theta[ks], wl.det_spacing)
+    assert oracle.rel_l2(g[ks].cpu().numpy(), ref) <= TOL_DIRECT
+
+
+def test_adjoint_identity_on_device():
+    # Section 1, eq "adjoint", discrete and weighted: sum_k w_k dt <R f, g>_k = dx^2 <f, R* g>.
+    rng = np.random.default_rng(17)
+    N, n_det, n_theta = 300, 311, 97
+    theta = random_theta(rng, n_theta)
+    dt = 1.1 * 2.0 / n_det
+    plan = bp.Plan(N, n_det, theta, dt)
+    f = to_dev(rng.normal(size=(N, N)))
+    g = to_dev(rng.normal(size=(n_theta, n_det)))
+    Rf = rounded(plan.radon(f))
+    Bg = rounded(plan.backproject(g))
+    w = oracle.weights(theta)
+    lhs = float(np.sum(w[:, None] * dt * Rf * rounded(g)))
+    rhs = float((2.0 / N) ** 2 * np.sum(rounded(f) * Bg))
+    scale = float(np.linalg.norm(w[:, None] * dt * Rf) * np.linalg.norm(rounded(g)))
+    assert abs(lhs - rhs) <= TOL_DIRECT * scale
+
+
+# ----------------------------------------------------------------------------------- host entry point
+def test_fbp_host_matches_device_calls():
+    wl = synth.SMALL
+    g = torch.from_numpy(wl.sinogram().astype(np.float32))
+    plan = bp.Plan(wl.N, wl.n_det, wl.theta, wl.det_spacing)
+    out = plan.fbp_host(g.pin_memory(), "shepp-logan")
+    dev_img = plan.backproject(plan.filter(g.to(dev()), "shepp-logan"))
+    assert torch.equal(out, dev_img.cpu())
+    out2 = plan.fbp_host(torch.stack([g, 2 * g]), "shepp-logan")
+    assert torch.allclose(out2[1], 2 * out2[0], rtol=1e-6, atol=1e-6)
