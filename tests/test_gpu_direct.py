@@ -95,7 +95,7 @@ def test_filter_parity(kind, param, n_det, rows):
     th = synth.uniform_theta(rows)
     g = synth.add_gaussian_noise(synth.ellipse_sinogram(e, th, n_det), 0.01, seed=3)
     gd = to_dev(g)
-    plan = bp.Plan(16, n_det, th)
+    plan = bp.Plan(n_det, n_det, th)
     q = plan.filter(gd, kind, param)
     ref = oracle.filter_rows(rounded(gd), 2.0 / n_det, okind, param)
     assert oracle.rel_l2(q.cpu().numpy(), ref) <= TOL_DIRECT
