@@ -43,20 +43,20 @@ struct AngleParam {
 };
 static_assert(sizeof(AngleParam) == 40, "AngleParam layout");
 
-// Fourier-path workspace (allocated on first use).
+// Fourier-path workspace and gridding geometry (allocated on first use).
 struct FourierWork {
-    int M = 0;            // oversampled grid side (2N)
-    int P = 0;            // per-projection FFT length
-    int band = 0;         // number of grid rows/cols that can hold nonzeros
-    float2 *spec = nullptr;   // [n_theta][P/2] scaled projection half-spectra
-    float2 *grid = nullptr;   // [M][M] gridded spectrum (or [band][M])
-    float2 *mid = nullptr;    // [band][N] after the first 1D IFFT pass
-    float *deapod = nullptr;  // [N] separable deapodisation 1/phi_hat
-    float *kb = nullptr;      // kernel lookup table
-    float2 *twM = nullptr;    // M-point twiddles
-    float kb_beta = 0.f;
-    int kb_width = 6;
-    int kb_tab_n = 0;
+    int M = 0, logM = 0;        // oversampled grid side (power of two >= 2N)
+    float beta = 0.f;           // Kaiser-Bessel shape for W = 6 and oversampling M/N
+    float2 *spec = nullptr;     // [n_theta][P/2] sample values c_{k,m}
+    float2 *grid = nullptr;     // [M][M] gridded spectrum, G[l_x][l_y]
+    float2 *mid = nullptr;      // [N][M] after the first inverse-FFT pass
+    float *deapod = nullptr;    // [N] 1 / phi_hat(i - floor(N/2))
+    float *wk = nullptr;        // [n_theta] quadrature weights (float)
+    float2 *twM = nullptr;      // M/2 twiddles exp(-2 pi i r / M)
+    long long *ray = nullptr;   // [n_theta][2] rho cos, rho sin in 32.32 fixed point
+    void *segs = nullptr;       // gridding ray segments
+    void *items = nullptr;      // gridding work items (owners first, then extras)
+    int n_segs = 0, n_owner = 0, n_extra = 0;
     size_t bytes = 0;
 };
 

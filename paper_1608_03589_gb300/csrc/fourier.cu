@@ -1,13 +1,401 @@
-// Fourier (Backprojection Slice Theorem) path -- placeholder until the gridding kernels land.
+// Fourier form of R*: the Backprojection Slice Theorem (Section 3, eq "bst") evaluated as a
+// type-1 non-uniform FFT (Section 5.3, Steps 2.2-4, with Step 3 realised as gridding).
+//
+// With G_k[m] the P-point DFT of projection k (zero-padded, Step 2.2) and the Nyquist bin
+// dropped, the backprojection of the band-limited interpolant of every projection is
+//     b(x) = Re sum_k sum_{m=0}^{P/2-1} c_{k,m} exp(2 pi i kappa_m xi_k . x),
+//     c_{k,m} = (w_k / P) (m ? 2 : 1) G_k[m] exp(i pi m (n_det-1) / P),  kappa_m = m / (P dt).
+// The BST's 1/sigma is cancelled by the polar area element |sigma| (Section 6, eq
+// "reg_fbp"), so the samples carry plain quadrature weights.  In grid units of an
+// M x M oversampled frequency grid (M = 2^ceil(log2(2N))), sample (k, m) sits at
+//     z = m rho xi_k,   rho = M dx / (P dt),
+// and the image is  b(i) = Re sum_s c'_s exp(2 pi i z_s . i' / M),  i' = i - floor(N/2),
+// c'_s = c_s exp(2 pi i delta (z_x + z_y) / M), delta = floor(N/2) - (N-1)/2.
+// Gridding spreads every c'_s onto the grid with a separable Kaiser-Bessel kernel of
+// width W = 6 (Beatty et al.'s beta for the actual oversampling M/N), two pruned 1D
+// inverse FFT passes produce the N x N output, and dividing by the kernel's Fourier
+// transform (deapodisation) removes the kernel.
+//
+// Kernels: (1) fourier_spectra: one CTA per projection pair, P-point FFT in shared memory,
+// the two half spectra scaled into c_{k,m};  (2) grid_spread: one CTA per work item of a
+// 32 x 32 grid tile (host-built list of ray segments that touch the tile, split so no
+// item exceeds a fixed sample count), warp groups of 6 lanes spread one sample each into
+// the shared-memory tile; the tile's first item stores it, later items add with global
+// reductions (second launch);  (3) ifft_pass_y / ifft_pass_x: M-point inverse FFTs of R
+// rows per CTA with output pruning to N points, transposed intermediate, fused
+// deapodisation and real part.
+#include <algorithm>
+#include <cmath>
+
 #include "common.cuh"
+#include "fft.cuh"
 
 namespace bp {
 
-bp_status ensure_fourier(bp_plan *) { return fail(BP_ERR_UNSUPPORTED, "Fourier path not built yet"); }
-void free_fourier(bp_plan *) {}
-bp_status launch_fourier(bp_plan *, const void *, bp_dtype, float *, int, cudaStream_t) {
-    return fail(BP_ERR_UNSUPPORTED, "Fourier path not built yet");
+namespace {
+
+constexpr int kW = 6;          // kernel width (grid cells)
+constexpr int kTS = 32;        // grid tile side
+constexpr int kMaxItem = 4096; // samples per gridding work item
+constexpr int kGridThreads = 256;
+
+struct GridSeg {
+    int k, m_lo, m_hi, pad;
+};
+struct GridItem {
+    int x0, y0, seg_begin, seg_end;
+};
+
+__device__ __forceinline__ float kb_weight(float t, float beta) {
+    // I0(beta sqrt(1 - (2t/W)^2)) for |t| <= W/2
+    const float a = t * (2.0f / kW);
+    const float r = fmaxf(0.f, 1.f - a * a);
+    return cyl_bessel_i0f(beta * sqrtf(r));
 }
+
+// ---------------------------------------------------------------------------------- (1) spectra
+template <typename Tin>
+__global__ void __launch_bounds__(512)
+fourier_spectra_kernel(const Tin *__restrict__ sino, float2 *__restrict__ spec, const float *__restrict__ wk,
+                       const float2 *__restrict__ tw, int n_theta, int n_det, int logP) {
+    extern __shared__ __align__(16) float2 z[];
+    const int P = 1 << logP, H = P >> 1;
+    const int k0 = 2 * blockIdx.x, k1 = k0 + 1;
+    const bool has1 = k1 < n_theta;
+    const Tin *a = sino + (long long)k0 * n_det;
+    const Tin *b = sino + (long long)k1 * n_det;
+    for (int j = threadIdx.x; j < P; j += blockDim.x) {
+        float va = 0.f, vb = 0.f;
+        if (j < n_det) {
+            va = load_f(a + j);
+            if (has1) vb = load_f(b + j);
+        }
+        z[bitrev(j, logP)] = make_float2(va, vb);
+    }
+    __syncthreads();
+    fft_dit_fwd(z, logP, tw, 1);
+    // A[m] = (Z[m] + conj Z[P-m]) / 2,  B[m] = (Z[m] - conj Z[P-m]) / (2i)
+    const float wa = __ldg(wk + k0) / (float)P;
+    const float wb = has1 ? __ldg(wk + k1) / (float)P : 0.f;
+    const long long twoP = 2LL * P;
+    for (int m = threadIdx.x; m < H; m += blockDim.x) {
+        const float2 zm = z[m];
+        const float2 zc = z[(P - m) & (P - 1)];
+        const float2 A = make_float2(0.5f * (zm.x + zc.x), 0.5f * (zm.y - zc.y));
+        const float2 B = make_float2(0.5f * (zm.y + zc.y), -0.5f * (zm.x - zc.x));
+        // detector-centre phase exp(i pi m (n_det-1)/P), argument reduced exactly mod 2P
+        const long long r = ((long long)m * (n_det - 1)) % twoP;
+        float sn, cs;
+        sincospif((float)r / (float)P, &sn, &cs);
+        const float2 ph = make_float2(cs, sn);
+        const float f = (m == 0) ? 1.f : 2.f;
+        const float2 ca = cmul(A, ph), cb = cmul(B, ph);
+        spec[(long long)k0 * H + m] = make_float2(f * wa * ca.x, f * wa * ca.y);
+        if (has1) spec[(long long)k1 * H + m] = make_float2(f * wb * cb.x, f * wb * cb.y);
+    }
+}
+
+// ---------------------------------------------------------------------------------- (2) gridding
+// G[l_x][l_y] (l mod M).  One CTA per work item; groups of 6 lanes spread one sample each.
+__global__ void __launch_bounds__(kGridThreads)
+grid_spread_kernel(const float2 *__restrict__ spec, const long long *__restrict__ ray, const GridSeg *__restrict__ segs,
+                   const GridItem *__restrict__ items, float2 *__restrict__ grid, int M, int H, float beta,
+                   float delta2_over_M, int accumulate) {
+    __shared__ float2 acc[kTS][kTS + 1];
+    const GridItem it = items[blockIdx.x];
+    for (int i = threadIdx.x; i < kTS * kTS; i += kGridThreads) acc[i / kTS][i % kTS] = make_float2(0.f, 0.f);
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int grp = lane / 6, tx = lane - 6 * grp;   // grp 5 = idle lanes 30, 31
+    const unsigned gmask = 0x3fu << (6 * min(grp, 4));
+    const int Mmask = M - 1;
+    for (int j = it.seg_begin + warp; j < it.seg_end; j += kGridThreads / 32) {
+        const GridSeg sg = segs[j];
+        const long long ax = ray[2 * sg.k], ay = ray[2 * sg.k + 1];
+        for (int mb = sg.m_lo; mb <= sg.m_hi; mb += 5) {
+            const int m = mb + grp;
+            const bool act = (grp < 5) && (m <= sg.m_hi);
+            // all 6 lanes of a group agree on act; idle lanes still join the shuffles of their group
+            long long zx = (long long)m * ax, zy = (long long)m * ay;
+            const int fx = (int)(zx >> 32), fy = (int)(zy >> 32);
+            const float rx = (float)(unsigned)(zx & 0xffffffffLL) * 2.3283064365386963e-10f;
+            const float ry = (float)(unsigned)(zy & 0xffffffffLL) * 2.3283064365386963e-10f;
+            const float wx = kb_weight((float)(tx - 2) - rx, beta);
+            const float wyown = kb_weight((float)(tx - 2) - ry, beta);
+            float2 v = make_float2(0.f, 0.f);
+            if (act) {
+                v = __ldg(spec + (long long)sg.k * H + m);
+                float sn, cs;
+                sincospif(((float)(fx + fy) + (rx + ry)) * delta2_over_M, &sn, &cs);
+                v = cmul(v, make_float2(cs, sn));
+            }
+            const int cx = (fx - 2 + tx) & Mmask;
+            const int lx = cx - it.x0;
+            const bool inx = act && lx >= 0 && lx < kTS;
+#pragma unroll
+            for (int ty = 0; ty < kW; ++ty) {
+                const float wy = __shfl_sync(0xffffffffu, wyown, 6 * min(grp, 4) + ty);
+                const int cy = (fy - 2 + ty) & Mmask;
+                const int ly = cy - it.y0;
+                if (inx && ly >= 0 && ly < kTS) {
+                    const float w = wx * wy;
+                    atomicAdd(&acc[lx][ly].x, w * v.x);
+                    atomicAdd(&acc[lx][ly].y, w * v.y);
+                }
+            }
+            (void)gmask;
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kTS * kTS; i += kGridThreads) {
+        const int lx = i / kTS, ly = i % kTS;
+        float2 *dst = grid + (long long)(it.x0 + lx) * M + (it.y0 + ly);
+        const float2 v = acc[lx][ly];
+        if (accumulate) {
+            if (v.x != 0.f) atomicAdd(&dst->x, v.x);
+            if (v.y != 0.f) atomicAdd(&dst->y, v.y);
+        } else {
+            *dst = v;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------- (3) inverse FFT passes
+// Pass along y: rows l_x of G (contiguous in l_y), keep i_y in [0, N), write inter[i_y][l_x] * dy[i_y].
+__global__ void __launch_bounds__(512)
+ifft_pass_y_kernel(const float2 *__restrict__ grid, float2 *__restrict__ inter, const float *__restrict__ deap,
+                   const float2 *__restrict__ tw, int M, int logM, int N, int R) {
+    extern __shared__ __align__(16) float2 z[];
+    const int lx0 = blockIdx.x * R;
+    for (int i = threadIdx.x; i < R * M; i += blockDim.x) z[i] = grid[(long long)lx0 * M + i];
+    __syncthreads();
+    for (int r = 0; r < R; ++r) fft_dif_inv(z + r * M, logM, tw, 1);
+    const int h = N / 2;
+    for (int i = threadIdx.x; i < N * R; i += blockDim.x) {
+        const int iy = i / R, r = i - iy * R;
+        const int pos = bitrev((iy - h) & (M - 1), logM);
+        const float d = __ldg(deap + iy);
+        const float2 v = z[r * M + pos];
+        inter[(long long)iy * M + lx0 + r] = make_float2(v.x * d, v.y * d);
+    }
+}
+
+// Pass along x: rows i_y of inter (contiguous in l_x), keep i_x in [0, N), img = Re * dx[i_x].
+__global__ void __launch_bounds__(512)
+ifft_pass_x_kernel(const float2 *__restrict__ inter, float *__restrict__ img, const float *__restrict__ deap,
+                   const float2 *__restrict__ tw, int M, int logM, int N, int R) {
+    extern __shared__ __align__(16) float2 z[];
+    const int iy0 = blockIdx.x * R;
+    const int rows = min(R, N - iy0);
+    for (int i = threadIdx.x; i < rows * M; i += blockDim.x) z[i] = inter[(long long)iy0 * M + i];
+    __syncthreads();
+    for (int r = 0; r < rows; ++r) fft_dif_inv(z + r * M, logM, tw, 1);
+    const int h = N / 2;
+    for (int i = threadIdx.x; i < rows * N; i += blockDim.x) {
+        const int r = i / N, ix = i - r * N;
+        const int pos = bitrev((ix - h) & (M - 1), logM);
+        img[(long long)(iy0 + r) * N + ix] = z[r * M + pos].x * __ldg(deap + ix);
+    }
+}
+
+double kb_hat(double f, double beta) {
+    // Fourier transform of I0(beta sqrt(1 - (2t/W)^2)) on |t| <= W/2 at frequency f (cycles per cell)
+    const double x = M_PI * kW * f;
+    const double a2 = beta * beta - x * x;
+    if (a2 > 0) {
+        const double a = std::sqrt(a2);
+        return a < 1e-8 ? kW : kW * std::sinh(a) / a;
+    }
+    const double a = std::sqrt(-a2);
+    return a < 1e-8 ? kW : kW * std::sin(a) / a;
+}
+
+}  // namespace
+
+void free_fourier(bp_plan *p) {
+    FourierWork &f = p->four;
+    cudaFree(f.spec);
+    cudaFree(f.grid);
+    cudaFree(f.mid);
+    cudaFree(f.deapod);
+    cudaFree(f.wk);
+    cudaFree(f.twM);
+    cudaFree(f.ray);
+    cudaFree(f.segs);
+    cudaFree(f.items);
+    f = FourierWork();
+}
+
+// Host (FP64) geometry of the gridding step: per-angle ray steps in 32.32 fixed point,
+// the ray segments that touch every 32 x 32 grid tile, and balanced work items.
+bp_status ensure_fourier(bp_plan *p) {
+    FourierWork &f = p->four;
+    if (f.grid) return BP_OK;
+    const int N = p->N, n_theta = p->n_theta, P = p->P, H = P / 2;
+    int M = 1;
+    while (M < 2 * N) M <<= 1;
+    M = std::max(M, kTS);
+    if ((size_t)M * sizeof(float2) > 128u * 1024u)
+        return fail(BP_ERR_UNSUPPORTED, "Fourier path: N too large for the shared-memory FFT (N <= 8192)");
+    if ((size_t)P * sizeof(float2) > 200u * 1024u)
+        return fail(BP_ERR_UNSUPPORTED, "Fourier path: n_det too large for the shared-memory FFT (n_det <= 8192)");
+    const double sigma = (double)M / N;
+    double b2 = (kW / sigma) * (kW / sigma) * (sigma - 0.5) * (sigma - 0.5) - 0.8;
+    const double beta = M_PI * std::sqrt(std::max(b2, 1.0));
+    const double rho = (double)M * p->dx / ((double)P * p->dt);
+
+    // ray steps and the sample walk that builds the tile segments
+    std::vector<long long> ray(2 * (size_t)n_theta);
+    const int tiles1 = M / kTS;
+    std::vector<int> last(tiles1 * tiles1, -1);
+    std::vector<GridSeg> segs;
+    std::vector<int> seg_tile;
+    segs.reserve((size_t)n_theta * 4 * (H / kTS + 2));
+    for (int k = 0; k < n_theta; ++k) {
+        const long long ax = (long long)std::llround(std::ldexp(rho * std::cos(p->theta[k]), 32));
+        const long long ay = (long long)std::llround(std::ldexp(rho * std::sin(p->theta[k]), 32));
+        ray[2 * k] = ax;
+        ray[2 * k + 1] = ay;
+        for (int m = 0; m < H; ++m) {
+            const int fx = (int)(((long long)m * ax) >> 32), fy = (int)(((long long)m * ay) >> 32);
+            const int tx0 = ((fx - 2) & (M - 1)) / kTS, tx1 = ((fx + 3) & (M - 1)) / kTS;
+            const int ty0 = ((fy - 2) & (M - 1)) / kTS, ty1 = ((fy + 3) & (M - 1)) / kTS;
+            const int txs[2] = {tx0, tx1}, tys[2] = {ty0, ty1};
+            for (int a = 0; a < (tx0 == tx1 ? 1 : 2); ++a)
+                for (int b = 0; b < (ty0 == ty1 ? 1 : 2); ++b) {
+                    const int t = txs[a] * tiles1 + tys[b];
+                    const int li = last[t];
+                    if (li >= 0 && segs[li].k == k && segs[li].m_hi == m - 1) {
+                        segs[li].m_hi = m;
+                    } else {
+                        last[t] = (int)segs.size();
+                        segs.push_back(GridSeg{k, m, m, 0});
+                        seg_tile.push_back(t);
+                    }
+                }
+        }
+    }
+    // group segments by tile (counting sort), split each tile's list into items
+    const int ntiles = tiles1 * tiles1;
+    std::vector<int> cnt(ntiles + 1, 0);
+    for (int t : seg_tile) cnt[t + 1]++;
+    for (int t = 0; t < ntiles; ++t) cnt[t + 1] += cnt[t];
+    std::vector<GridSeg> sorted(segs.size());
+    {
+        std::vector<int> pos(cnt.begin(), cnt.end() - 1);
+        for (size_t i = 0; i < segs.size(); ++i) sorted[pos[seg_tile[i]]++] = segs[i];
+    }
+    std::vector<GridItem> owners, extras;
+    owners.reserve(ntiles);
+    for (int t = 0; t < ntiles; ++t) {
+        const int x0 = (t / tiles1) * kTS, y0 = (t % tiles1) * kTS;
+        int b = cnt[t], e = cnt[t + 1];
+        bool first = true;
+        do {
+            int s = b, load = 0;
+            while (s < e && (load == 0 || load + (sorted[s].m_hi - sorted[s].m_lo + 1) <= kMaxItem)) {
+                load += sorted[s].m_hi - sorted[s].m_lo + 1;
+                ++s;
+            }
+            (first ? owners : extras).push_back(GridItem{x0, y0, b, s});
+            first = false;
+            b = s;
+        } while (b < e);
+    }
+    // deapodisation 1 / phi_hat(i - floor(N/2)) (separable), weights, twiddles
+    std::vector<float> deap(N), wk(n_theta);
+    for (int i = 0; i < N; ++i) deap[i] = (float)(1.0 / kb_hat((double)(i - N / 2) / M, beta));
+    for (int k = 0; k < n_theta; ++k) wk[k] = (float)p->w[k];
+    std::vector<float2> tw(M / 2);
+    for (int i = 0; i < M / 2; ++i) {
+        const double a = -2.0 * M_PI * (double)i / (double)M;
+        tw[i] = make_float2((float)std::cos(a), (float)std::sin(a));
+    }
+    std::vector<GridItem> all(owners);
+    all.insert(all.end(), extras.begin(), extras.end());
+
+    f.M = M;
+    f.logM = ilog2(M);
+    f.beta = (float)beta;
+    f.n_segs = (int)sorted.size();
+    f.n_owner = (int)owners.size();
+    f.n_extra = (int)extras.size();
+    cudaError_t e = cudaSuccess;
+    auto alloc = [&](void **ptr, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMalloc(ptr, std::max<size_t>(bytes, 16));
+        if (e == cudaSuccess) f.bytes += bytes;
+    };
+    alloc((void **)&f.spec, sizeof(float2) * (size_t)n_theta * H);
+    alloc((void **)&f.grid, sizeof(float2) * (size_t)M * M);
+    alloc((void **)&f.mid, sizeof(float2) * (size_t)N * M);
+    alloc((void **)&f.deapod, sizeof(float) * N);
+    alloc((void **)&f.wk, sizeof(float) * n_theta);
+    alloc((void **)&f.twM, sizeof(float2) * tw.size());
+    alloc((void **)&f.ray, sizeof(long long) * ray.size());
+    alloc(&f.segs, sizeof(GridSeg) * sorted.size());
+    alloc(&f.items, sizeof(GridItem) * all.size());
+    if (e == cudaSuccess) e = cudaMemcpy(f.deapod, deap.data(), sizeof(float) * N, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(f.wk, wk.data(), sizeof(float) * n_theta, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(f.twM, tw.data(), sizeof(float2) * tw.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(f.ray, ray.data(), sizeof(long long) * ray.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !sorted.empty())
+        e = cudaMemcpy(f.segs, sorted.data(), sizeof(GridSeg) * sorted.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(f.items, all.data(), sizeof(GridItem) * all.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        free_fourier(p);
+        return cuda_fail(e, "Fourier workspace");
+    }
+    return BP_OK;
+}
+
+template <typename Tin>
+static bp_status spectra_t(bp_plan *p, const Tin *sino, cudaStream_t st) {
+    const int logP = ilog2(p->P);
+    const size_t smem = sizeof(float2) * p->P;
+    BP_CUDA_TRY(cudaFuncSetAttribute(fourier_spectra_kernel<Tin>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+    const int threads = std::min(512, std::max(32, p->P / 2));
+    fourier_spectra_kernel<Tin><<<(p->n_theta + 1) / 2, threads, smem, st>>>(sino, p->four.spec, p->four.wk,
+                                                                              p->d_twP, p->n_theta, p->n_det, logP);
+    return BP_OK;
+}
+
+static int rows_per_cta(int M) { return std::max(1, std::min(4, (int)(131072 / (sizeof(float2) * M)))); }
+
+bp_status launch_fourier(bp_plan *p, const void *sino, bp_dtype dt, float *img, int batch, cudaStream_t st) {
+    bp_status s = ensure_fourier(p);
+    if (s != BP_OK) return s;
+    FourierWork &f = p->four;
+    const int N = p->N, M = f.M, H = p->P / 2;
+    const size_t esz = dt == BP_F32 ? 4 : 2;
+    const int R = rows_per_cta(M);
+    const size_t smemR = sizeof(float2) * (size_t)R * M;
+    BP_CUDA_TRY(cudaFuncSetAttribute(ifft_pass_y_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smemR));
+    BP_CUDA_TRY(cudaFuncSetAttribute(ifft_pass_x_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smemR));
+    const int fft_threads = std::min(512, std::max(32, M / 2));
+    const float delta2 = (N % 2 == 0) ? 1.0f / (float)M : 0.0f;  // 2 delta / M
+    for (int b = 0; b < batch; ++b) {
+        const char *sb = (const char *)sino + esz * (size_t)b * p->n_theta * p->n_det;
+        switch (dt) {
+            case BP_F32: s = spectra_t(p, (const float *)sb, st); break;
+            case BP_BF16: s = spectra_t(p, (const __nv_bfloat16 *)sb, st); break;
+            case BP_F16: s = spectra_t(p, (const __half *)sb, st); break;
+        }
+        if (s != BP_OK) return s;
+        const GridItem *items = (const GridItem *)f.items;
+        grid_spread_kernel<<<f.n_owner, kGridThreads, 0, st>>>(f.spec, f.ray, (const GridSeg *)f.segs, items, f.grid,
+                                                               M, H, f.beta, delta2, 0);
+        if (f.n_extra > 0)
+            grid_spread_kernel<<<f.n_extra, kGridThreads, 0, st>>>(f.spec, f.ray, (const GridSeg *)f.segs,
+                                                                   items + f.n_owner, f.grid, M, H, f.beta, delta2, 1);
+        ifft_pass_y_kernel<<<M / R, fft_threads, smemR, st>>>(f.grid, f.mid, f.deapod, f.twM, M, f.logM, N, R);
+        ifft_pass_x_kernel<<<(N + R - 1) / R, fft_threads, smemR, st>>>(f.mid, img + (size_t)b * N * N, f.deapod,
+                                                                       f.twM, M, f.logM, N, R);
+        BP_CUDA_TRY(cudaGetLastError());
+    }
+    return BP_OK;
+}
+
 bp_status launch_radon_fourier(bp_plan *, const float *, float *, int, cudaStream_t) {
     return fail(BP_ERR_UNSUPPORTED, "Fourier adjoint not built yet");
 }
