@@ -63,7 +63,9 @@ def test_fourier_batch_and_low_precision():
     g = to_dev(rng.normal(size=(2, n_theta, n_det)))
     out = plan.backproject_fourier(g)
     for i in range(2):
-        assert torch.equal(plan.backproject_fourier(g[i].contiguous()), out[i])
+        # gridding accumulates with shared-memory atomics: equal up to summation order
+        single = plan.backproject_fourier(g[i].contiguous())
+        assert oracle.rel_l2(single.cpu().numpy(), out[i].cpu().numpy()) <= 1e-6
     g16 = g.to(torch.bfloat16)
     img16 = plan.backproject_fourier(g16)
     ref = oracle.bp_trig_dirichlet(rounded(g16[0]), N, theta, 2.0 / n_det)
