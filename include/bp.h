@@ -157,6 +157,30 @@ bp_status bp_fbp_host(bp_plan *plan, const float *sino, float *img, bp_filter_ki
 bp_status bp_backproject_batched(bp_plan *const *plans, const void *const *sinos,
                                  const bp_dtype *dtypes, float *const *imgs, int n, void *stream);
 
+/*
+ * bp_fbp_static -- the same filtered backprojection as bp_filter followed by
+ * bp_backproject_direct (device pointers, BP_RAMLAK or BP_SHEPP_LOGAN), for callers that
+ * cannot allocate device memory when they need it: code that runs while a CUDA graph is
+ * being captured, code inside a framework that owns every device allocation, or loops
+ * where allocation is not allowed.  The paper has no counterpart; it exists only for
+ * such callers.
+ *   Allocation: none.  Its scratch (the filter response and one filtered slice) lives in
+ *   a static device array of BP_STATIC_SCRATCH_BYTES that every GPU which loads the
+ *   library holds until the process exits.  P + n_theta * n_det (in floats, P the
+ *   filter FFT length) must fit in it, else BP_ERR_UNSUPPORTED; batch slices are done one
+ *   after another through the same scratch.
+ *   Set-up: the first call on each device looks up the array's device address
+ *   (cudaGetSymbolAddress) with that device current; make that first call before any
+ *   stream capture.  The plan itself is created beforehand with bp_plan_create.
+ *   Sharing: every call on a device uses the same array and leaves its last contents
+ *   there; calls whose work overlaps on the GPU (different streams, or different host
+ *   threads without ordering) race on it and must be serialised by the caller.
+ *   sino, dtype, img, batch, stream as for bp_backproject_direct.
+ */
+#define BP_STATIC_SCRATCH_BYTES (16u << 20)
+bp_status bp_fbp_static(bp_plan *plan, const void *sino, bp_dtype dtype, float *img, bp_filter_kind kind,
+                        int batch, void *stream);
+
 /* Last error message of the calling thread ("" if none). */
 const char *bp_last_error(void);
 

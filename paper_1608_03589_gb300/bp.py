@@ -25,7 +25,7 @@ _DTYPES = {torch.float32: BP_F32, torch.bfloat16: BP_BF16, torch.float16: BP_F16
 
 # Every symbol the header declares (checked by the ABI test).
 SYMBOLS = ("bp_plan_create", "bp_destroy", "bp_filter", "bp_backproject_direct", "bp_backproject_fourier",
-           "bp_radon", "bp_fbp_host", "bp_backproject_batched", "bp_last_error", "bp_version")
+           "bp_radon", "bp_fbp_host", "bp_backproject_batched", "bp_fbp_static", "bp_last_error", "bp_version")
 
 
 class BPError(RuntimeError):
@@ -54,10 +54,11 @@ def lib() -> ctypes.CDLL:
             L.bp_backproject_fourier.argtypes = [vp, vp, i, vp, i, vp]
             L.bp_radon.argtypes = [vp, vp, vp, i, i, vp]
             L.bp_fbp_host.argtypes = [vp, vp, vp, i, f, i, vp]
+            L.bp_fbp_static.argtypes = [vp, vp, i, vp, i, i, vp]
             L.bp_backproject_batched.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(i),
                                                  ctypes.POINTER(vp), i, vp]
             for name in ("bp_filter", "bp_backproject_direct", "bp_backproject_fourier", "bp_radon",
-                         "bp_fbp_host", "bp_backproject_batched"):
+                         "bp_fbp_host", "bp_backproject_batched", "bp_fbp_static"):
                 getattr(L, name).restype = i
             L.bp_last_error.argtypes = []
             L.bp_last_error.restype = ctypes.c_char_p

@@ -102,6 +102,8 @@ bp_status launch_radon_direct(bp_plan *p, const float *img, float *sino, int bat
 bp_status launch_fourier(bp_plan *p, const void *sino, bp_dtype dt, float *img, int batch, cudaStream_t st);
 bp_status launch_radon_fourier(bp_plan *p, const float *img, float *sino, int batch, cudaStream_t st);
 bp_status ensure_filter(bp_plan *p, int kind, float param);
+bp_status launch_filter_response(bp_plan *p, const void *in, bp_dtype dt, float *out, const float *Hbr, int batch,
+                                 cudaStream_t st);
 bp_status ensure_fourier(bp_plan *p);
 void free_fourier(bp_plan *p);
 bp_status launch_batched(bp_plan *const *plans, const void *const *sinos, const bp_dtype *dtypes,

@@ -143,4 +143,31 @@ bp_status launch_filter(bp_plan *p, const void *in, bp_dtype dt, float *out, int
     return BP_OK;
 }
 
+// Row filter with a caller-supplied bit-reversed response (P floats, already scaled by dt/P).
+bp_status launch_filter_response(bp_plan *p, const void *in, bp_dtype dt, float *out, const float *Hbr, int batch,
+                                 cudaStream_t st) {
+    if ((size_t)p->P * sizeof(float2) > 200u * 1024u)
+        return fail(BP_ERR_UNSUPPORTED, "filter: n_det too large for the shared-memory FFT (n_det <= 8192)");
+    const long long rows = (long long)batch * p->n_theta;
+    const int logP = ilog2(p->P);
+    const int threads = std::min(512, std::max(32, p->P / 2));
+    const size_t smem = sizeof(float2) * p->P;
+    const unsigned blocks = (unsigned)((rows + 1) / 2);
+#define BP_FILTER_LAUNCH_H(T)                                                                             \
+    do {                                                                                                  \
+        BP_CUDA_TRY(cudaFuncSetAttribute(filter_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
+                                         (int)smem));                                                     \
+        filter_kernel<T><<<blocks, threads, smem, st>>>((const T *)in, out, Hbr, p->d_twP, rows, p->n_det, \
+                                                        logP);                                            \
+    } while (0)
+    switch (dt) {
+        case BP_F32: BP_FILTER_LAUNCH_H(float); break;
+        case BP_BF16: BP_FILTER_LAUNCH_H(__nv_bfloat16); break;
+        case BP_F16: BP_FILTER_LAUNCH_H(__half); break;
+    }
+#undef BP_FILTER_LAUNCH_H
+    BP_CUDA_TRY(cudaGetLastError());
+    return BP_OK;
+}
+
 }  // namespace bp

@@ -1,0 +1,108 @@
+// bp_fbp_static: filtered backprojection that allocates no device memory.
+//
+// Some callers cannot call cudaMalloc at the point where they need a reconstruction:
+// code running while a CUDA graph is being captured, code embedded in a host framework
+// that owns every device allocation (a fixed memory pool or budget), or real-time loops
+// in which allocating is not allowed.  For them this entry point keeps its scratch -- the
+// filter's frequency response and the filtered sinogram of one slice -- in one file-scope
+// static device array of fixed size, which every GPU that loads the library holds until
+// the process exits.  The caller still passes its own input and output buffers.
+#include <mutex>
+
+#include "common.cuh"
+#include "fft.cuh"
+
+namespace bp {
+
+namespace {
+
+constexpr size_t kStaticFloats = BP_STATIC_SCRATCH_BYTES / sizeof(float);
+constexpr int kMaxDevices = 128;
+
+// The scratch itself.  In host code the symbol is only a host-side stand-in, never a
+// device address: host code must use the address that cudaGetSymbolAddress returns.
+static __device__ __align__(256) float g_static_scratch[kStaticFloats];
+
+std::mutex g_setup_mutex;
+float *g_scratch_addr[kMaxDevices] = {};
+
+// Once per device, with that device current: look up the device address of the array.
+bp_status scratch_address(int device, float **out) {
+    if (device < 0 || device >= kMaxDevices) return fail(BP_ERR_UNSUPPORTED, "bp_fbp_static: device index too large");
+    std::lock_guard<std::mutex> lock(g_setup_mutex);
+    if (!g_scratch_addr[device]) {
+        void *ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_static_scratch)");
+        g_scratch_addr[device] = static_cast<float *>(ptr);
+    }
+    *out = g_scratch_addr[device];
+    return BP_OK;
+}
+
+// Bit-reversed filter response (dt/P) DFT_P(h_circ), h_circ[r] = h(|r|) for |r| < n_det,
+// evaluated in double precision on the device (the host path uses an FP64 FFT).
+__global__ void static_response_kernel(float *__restrict__ Hbr, int P, int logP, int n_det, double dt, int kind) {
+    const int half = P / 2;
+    for (int m = blockIdx.x * blockDim.x + threadIdx.x; m <= half; m += gridDim.x * blockDim.x) {
+        const double pi2dt2 = M_PI * M_PI * dt * dt;
+        double acc = (kind == BP_RAMLAK) ? 1.0 / (4.0 * dt * dt) : 2.0 / pi2dt2;
+        for (int r = 1; r < n_det; ++r) {
+            double h;
+            if (kind == BP_RAMLAK) {
+                if (!(r & 1)) continue;
+                h = -1.0 / (pi2dt2 * (double)r * (double)r);
+            } else {
+                h = -2.0 / (pi2dt2 * (4.0 * (double)r * (double)r - 1.0));
+            }
+            const long long a = (2LL * m * r) % (2LL * P);  // cos(2 pi m r / P) = cospi(a / P)
+            acc += 2.0 * h * cospi((double)a / (double)P);
+        }
+        const float v = (float)(acc * dt / (double)P);
+        Hbr[bitrev(m, logP)] = v;
+        if (m > 0 && m < half) Hbr[bitrev(P - m, logP)] = v;
+    }
+}
+
+}  // namespace
+
+}  // namespace bp
+
+using namespace bp;
+
+extern "C" bp_status bp_fbp_static(bp_plan *p, const void *sino, bp_dtype dtype, float *img, bp_filter_kind kind,
+                                   int batch, void *stream) {
+    set_error("");
+    bp_status st = check_plan(p);
+    if (st != BP_OK) return st;
+    if (!sino || !img) return fail(BP_ERR_INVALID_ARG, "data pointer is NULL");
+    if (!aligned16(sino) || !aligned16(img)) return fail(BP_ERR_INVALID_ARG, "data pointers must be 16-byte aligned");
+    if (batch < 1 || batch > 65535) return fail(BP_ERR_INVALID_ARG, "batch out of range [1, 65535]");
+    if (dtype != BP_F32 && dtype != BP_BF16 && dtype != BP_F16) return fail(BP_ERR_INVALID_ARG, "invalid dtype");
+    if (kind != BP_RAMLAK && kind != BP_SHEPP_LOGAN)
+        return fail(BP_ERR_UNSUPPORTED, "bp_fbp_static supports BP_RAMLAK and BP_SHEPP_LOGAN only");
+    const size_t h_floats = ((size_t)p->P + 63) & ~(size_t)63;
+    const size_t slice = (size_t)p->n_theta * p->n_det;
+    if (h_floats + slice > kStaticFloats)
+        return fail(BP_ERR_UNSUPPORTED, "bp_fbp_static: P + n_theta * n_det exceeds the static scratch of "
+                                        "BP_STATIC_SCRATCH_BYTES / 4 floats");
+    float *scratch = nullptr;
+    st = scratch_address(p->device, &scratch);
+    if (st != BP_OK) return st;
+    float *Hbr = scratch;
+    float *q = scratch + h_floats;
+    cudaStream_t s = (cudaStream_t)stream;
+    // Every value the kernels read from the scratch is written earlier in this call, so
+    // nothing needs clearing.
+    static_response_kernel<<<(p->P / 2 + 256) / 256, 256, 0, s>>>(Hbr, p->P, ilog2(p->P), p->n_det, p->dt, (int)kind);
+    BP_CUDA_TRY(cudaGetLastError());
+    const size_t esz = dtype == BP_F32 ? 4 : 2;
+    for (int b = 0; b < batch; ++b) {
+        const char *sb = (const char *)sino + esz * slice * b;
+        st = launch_filter_response(p, sb, dtype, q, Hbr, 1, s);
+        if (st != BP_OK) return st;
+        st = launch_direct(p, q, BP_F32, img + (size_t)b * p->N * p->N, 1, 0, s);
+        if (st != BP_OK) return st;
+    }
+    return BP_OK;
+}
