@@ -181,6 +181,14 @@ bp_status bp_backproject_batched(bp_plan *const *plans, const void *const *sinos
 bp_status bp_fbp_static(bp_plan *plan, const void *sino, bp_dtype dtype, float *img, bp_filter_kind kind,
                         int batch, void *stream);
 
+/*
+ * bp_check -- synchronise `stream` and report device-side failures of earlier calls on
+ * this plan: BP_ERR_TIMEOUT if a kernel's bounded wait on an asynchronous copy gave up
+ * (the output of that call is invalid; the flag is cleared), else BP_OK.  Kernels never
+ * trap or hang; they record the failure in a plan-owned status word instead.
+ */
+bp_status bp_check(bp_plan *plan, void *stream);
+
 /* Last error message of the calling thread ("" if none). */
 const char *bp_last_error(void);
 

@@ -25,7 +25,7 @@ _DTYPES = {torch.float32: BP_F32, torch.bfloat16: BP_BF16, torch.float16: BP_F16
 
 # Every symbol the header declares (checked by the ABI test).
 SYMBOLS = ("bp_plan_create", "bp_destroy", "bp_filter", "bp_backproject_direct", "bp_backproject_fourier",
-           "bp_radon", "bp_fbp_host", "bp_backproject_batched", "bp_fbp_static", "bp_last_error", "bp_version")
+           "bp_radon", "bp_fbp_host", "bp_backproject_batched", "bp_fbp_static", "bp_check", "bp_last_error", "bp_version")
 
 
 class BPError(RuntimeError):
@@ -55,10 +55,11 @@ def lib() -> ctypes.CDLL:
             L.bp_radon.argtypes = [vp, vp, vp, i, i, vp]
             L.bp_fbp_host.argtypes = [vp, vp, vp, i, f, i, vp]
             L.bp_fbp_static.argtypes = [vp, vp, i, vp, i, i, vp]
+            L.bp_check.argtypes = [vp, vp]
             L.bp_backproject_batched.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(i),
                                                  ctypes.POINTER(vp), i, vp]
             for name in ("bp_filter", "bp_backproject_direct", "bp_backproject_fourier", "bp_radon",
-                         "bp_fbp_host", "bp_backproject_batched", "bp_fbp_static"):
+                         "bp_fbp_host", "bp_backproject_batched", "bp_fbp_static", "bp_check"):
                 getattr(L, name).restype = i
             L.bp_last_error.argtypes = []
             L.bp_last_error.restype = ctypes.c_char_p
@@ -201,6 +202,11 @@ class Plan:
             _check(lib().bp_fbp_host(self.handle, sino.data_ptr(), out.data_ptr(), k, float(param), b,
                                      torch.cuda.current_stream(self.device).cuda_stream), "bp_fbp_host")
         return out
+
+    def check(self) -> None:
+        """Synchronise the current stream; raise if a device-side bounded wait gave up (bp_check)."""
+        with torch.cuda.device(self.device):
+            _check(lib().bp_check(self.handle, torch.cuda.current_stream(self.device).cuda_stream), "bp_check")
 
     def close(self) -> None:
         if getattr(self, "_h", None) is not None:

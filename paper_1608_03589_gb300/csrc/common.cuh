@@ -86,6 +86,8 @@ struct bp_plan {
     size_t desc_cap = 0;
     int *d_counter = nullptr;
     int *d_status = nullptr;
+    // device-side error word: set to non-zero by a kernel whose bounded wait gave up
+    int *d_err = nullptr;
 };
 
 namespace bp {

@@ -115,6 +115,7 @@ static void plan_free_device(bp_plan *p) {
     cudaFree(p->d_desc);
     cudaFree(p->d_counter);
     cudaFree(p->d_status);
+    cudaFree(p->d_err);
 }
 
 extern "C" bp_plan *bp_plan_create(int N, int n_det, int n_theta, const double *theta, double det_spacing) {
@@ -170,7 +171,9 @@ extern "C" bp_plan *bp_plan_create(int N, int n_det, int n_theta, const double *
     }
     p->P = 1 << ilog2(2 * n_det);
 
-    cudaError_t e = cudaMalloc(&p->d_ang, sizeof(AngleParam) * n_theta);
+    cudaError_t e = cudaMalloc(&p->d_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(p->d_err, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_ang, sizeof(AngleParam) * n_theta);
     if (e == cudaSuccess) e = cudaMemcpy(p->d_ang, ap.data(), sizeof(AngleParam) * n_theta, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) {
         // filter twiddles exp(-2 pi i r / P), r < P/2, from FP64
@@ -298,4 +301,19 @@ extern "C" bp_status bp_backproject_batched(bp_plan *const *plans, const void *c
         if (plans[i]->device != plans[0]->device) return fail(BP_ERR_INVALID_ARG, "plans on different devices");
     }
     return launch_batched(plans, sinos, dtypes, imgs, n, (cudaStream_t)stream);
+}
+
+extern "C" bp_status bp_check(bp_plan *p, void *stream) {
+    set_error("");
+    bp_status st = check_plan(p);
+    if (st != BP_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    int h = 0;
+    BP_CUDA_TRY(cudaMemcpyAsync(&h, p->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    BP_CUDA_TRY(cudaStreamSynchronize(s));
+    if (h) {
+        BP_CUDA_TRY(cudaMemset(p->d_err, 0, sizeof(int)));
+        return fail(BP_ERR_TIMEOUT, "a device-side bounded wait gave up (results of the affected call are invalid)");
+    }
+    return BP_OK;
 }

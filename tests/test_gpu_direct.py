@@ -37,6 +37,15 @@ def test_direct_ragged(N, n_det, n_theta, dt_scale, seed):
     assert oracle.rel_l2(img.cpu().numpy(), ref) <= TOL_DIRECT
 
 
+def test_direct_status_word_clean_after_calls():
+    # bp_check synchronises and reports device-side wait failures; none after normal calls.
+    wl = synth.SMALL
+    plan = bp.Plan(wl.N, wl.n_det, wl.theta, wl.det_spacing)
+    for dtype in (torch.float32, torch.bfloat16):
+        plan.backproject(to_dev(np.ones((wl.n_theta, wl.n_det)), dtype))
+    plan.check()
+
+
 def test_direct_unsupported_geometry_is_an_error():
     with pytest.raises(bp.BPError, match="window"):
         bp.Plan(64, 1000, synth.uniform_theta(8), 0.0005)
