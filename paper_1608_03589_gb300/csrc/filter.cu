@@ -6,8 +6,7 @@
 // h_circ[r] = h(r) for r < n_det, h_circ[P - r] = h(-r).  H is real and even, so two real
 // rows travel together as one complex row (a + i b): the real and imaginary parts of the
 // result are the two filtered rows.  One CTA per row pair, the whole P-point transform in
-// shared memory; the forward DIF leaves the spectrum bit-reversed, H is stored
-// bit-reversed, and the inverse DIT restores natural order.
+// shared memory (register-blocked Stockham passes, natural order throughout).
 #include <algorithm>
 #include <cmath>
 
@@ -19,8 +18,8 @@ namespace bp {
 namespace {
 
 template <typename Tin>
-__global__ void __launch_bounds__(512)
-filter_kernel(const Tin *__restrict__ in, float *__restrict__ out, const float *__restrict__ Hbr,
+__global__ void __launch_bounds__(1024)
+filter_kernel(const Tin *__restrict__ in, float *__restrict__ out, const float *__restrict__ H,
               const float2 *__restrict__ tw, long long rows, int n_det, int logP) {
     extern __shared__ __align__(16) float2 z[];
     const int P = 1 << logP;
@@ -37,14 +36,14 @@ filter_kernel(const Tin *__restrict__ in, float *__restrict__ out, const float *
         z[j] = make_float2(va, vb);
     }
     __syncthreads();
-    fft_dif_fwd(z, logP, tw, 1);
+    stockham_fft(z, logP, tw, 1, false);
     for (int j = threadIdx.x; j < P; j += blockDim.x) {
-        const float h = __ldg(Hbr + j);
+        const float h = __ldg(H + j);
         const float2 v = z[j];
         z[j] = make_float2(v.x * h, v.y * h);
     }
     __syncthreads();
-    fft_dit_inv(z, logP, tw, 1);
+    stockham_fft(z, logP, tw, 1, true);
     float *oa = out + r0 * n_det;
     float *ob = out + r1 * n_det;
     for (int j = threadIdx.x; j < n_det; j += blockDim.x) {
@@ -102,15 +101,12 @@ bp_status ensure_filter(bp_plan *p, int kind, float param) {
     for (int r = 0; r < n; ++r) re[r] = h[r + n - 1];
     for (int r = 1; r < n; ++r) re[P - r] = h[-r + n - 1];
     host_fft(re, im, false);
-    std::vector<float> Hbr(P);
+    std::vector<float> H(P);
     const double scale = p->dt / P;
-    for (int i = 0; i < P; ++i) {
-        unsigned v = (unsigned)i, r = 0;
-        for (int b = 0; b < logP; ++b) { r = (r << 1) | (v & 1u); v >>= 1; }
-        Hbr[i] = (float)(re[r] * scale);
-    }
+    for (int i = 0; i < P; ++i) H[i] = (float)(re[i] * scale);
+    (void)logP;
     if (!p->d_H[kind]) BP_CUDA_TRY(cudaMalloc(&p->d_H[kind], sizeof(float) * P));
-    BP_CUDA_TRY(cudaMemcpy(p->d_H[kind], Hbr.data(), sizeof(float) * P, cudaMemcpyHostToDevice));
+    BP_CUDA_TRY(cudaMemcpy(p->d_H[kind], H.data(), sizeof(float) * P, cudaMemcpyHostToDevice));
     p->H_param[kind] = param;
     return BP_OK;
 }
@@ -123,7 +119,7 @@ bp_status launch_filter(bp_plan *p, const void *in, bp_dtype dt, float *out, int
     if (s != BP_OK) return s;
     const long long rows = (long long)batch * p->n_theta;
     const int logP = ilog2(p->P);
-    const int threads = std::min(512, std::max(32, p->P / 2));
+    const int threads = fft_threads(p->P);
     const size_t smem = sizeof(float2) * p->P;
     const unsigned blocks = (unsigned)((rows + 1) / 2);
 #define BP_FILTER_LAUNCH(T)                                                                               \
@@ -143,21 +139,21 @@ bp_status launch_filter(bp_plan *p, const void *in, bp_dtype dt, float *out, int
     return BP_OK;
 }
 
-// Row filter with a caller-supplied bit-reversed response (P floats, already scaled by dt/P).
-bp_status launch_filter_response(bp_plan *p, const void *in, bp_dtype dt, float *out, const float *Hbr, int batch,
+// Row filter with a caller-supplied response (P floats, natural order, already scaled by dt/P).
+bp_status launch_filter_response(bp_plan *p, const void *in, bp_dtype dt, float *out, const float *H, int batch,
                                  cudaStream_t st) {
     if ((size_t)p->P * sizeof(float2) > 200u * 1024u)
         return fail(BP_ERR_UNSUPPORTED, "filter: n_det too large for the shared-memory FFT (n_det <= 8192)");
     const long long rows = (long long)batch * p->n_theta;
     const int logP = ilog2(p->P);
-    const int threads = std::min(512, std::max(32, p->P / 2));
+    const int threads = fft_threads(p->P);
     const size_t smem = sizeof(float2) * p->P;
     const unsigned blocks = (unsigned)((rows + 1) / 2);
 #define BP_FILTER_LAUNCH_H(T)                                                                             \
     do {                                                                                                  \
         BP_CUDA_TRY(cudaFuncSetAttribute(filter_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
                                          (int)smem));                                                     \
-        filter_kernel<T><<<blocks, threads, smem, st>>>((const T *)in, out, Hbr, p->d_twP, rows, p->n_det, \
+        filter_kernel<T><<<blocks, threads, smem, st>>>((const T *)in, out, H, p->d_twP, rows, p->n_det,   \
                                                         logP);                                            \
     } while (0)
     switch (dt) {

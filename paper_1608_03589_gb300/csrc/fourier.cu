@@ -55,7 +55,7 @@ __device__ __forceinline__ float kb_weight(float t, float beta) {
 
 // ---------------------------------------------------------------------------------- (1) spectra
 template <typename Tin>
-__global__ void __launch_bounds__(512)
+__global__ void __launch_bounds__(1024)
 fourier_spectra_kernel(const Tin *__restrict__ sino, float2 *__restrict__ spec, const float *__restrict__ wk,
                        const float2 *__restrict__ tw, int n_theta, int n_det, int logP) {
     extern __shared__ __align__(16) float2 z[];
@@ -70,10 +70,10 @@ fourier_spectra_kernel(const Tin *__restrict__ sino, float2 *__restrict__ spec, 
             va = load_f(a + j);
             if (has1) vb = load_f(b + j);
         }
-        z[bitrev(j, logP)] = make_float2(va, vb);
+        z[j] = make_float2(va, vb);
     }
     __syncthreads();
-    fft_dit_fwd(z, logP, tw, 1);
+    stockham_fft(z, logP, tw, 1, false);
     // A[m] = (Z[m] + conj Z[P-m]) / 2,  B[m] = (Z[m] - conj Z[P-m]) / (2i)
     const float wa = __ldg(wk + k0) / (float)P;
     const float wb = has1 ? __ldg(wk + k1) / (float)P : 0.f;
@@ -162,18 +162,18 @@ grid_spread_kernel(const float2 *__restrict__ spec, const long long *__restrict_
 
 // ---------------------------------------------------------------------------------- (3) inverse FFT passes
 // Pass along y: rows l_x of G (contiguous in l_y), keep i_y in [0, N), write inter[i_y][l_x] * dy[i_y].
-__global__ void __launch_bounds__(512)
+__global__ void __launch_bounds__(1024)
 ifft_pass_y_kernel(const float2 *__restrict__ grid, float2 *__restrict__ inter, const float *__restrict__ deap,
                    const float2 *__restrict__ tw, int M, int logM, int N, int R) {
     extern __shared__ __align__(16) float2 z[];
     const int lx0 = blockIdx.x * R;
     for (int i = threadIdx.x; i < R * M; i += blockDim.x) z[i] = grid[(long long)lx0 * M + i];
     __syncthreads();
-    for (int r = 0; r < R; ++r) fft_dif_inv(z + r * M, logM, tw, 1);
+    for (int r = 0; r < R; ++r) stockham_fft(z + r * M, logM, tw, 1, true);
     const int h = N / 2;
     for (int i = threadIdx.x; i < N * R; i += blockDim.x) {
         const int iy = i / R, r = i - iy * R;
-        const int pos = bitrev((iy - h) & (M - 1), logM);
+        const int pos = (iy - h) & (M - 1);
         const float d = __ldg(deap + iy);
         const float2 v = z[r * M + pos];
         inter[(long long)iy * M + lx0 + r] = make_float2(v.x * d, v.y * d);
@@ -181,7 +181,7 @@ ifft_pass_y_kernel(const float2 *__restrict__ grid, float2 *__restrict__ inter, 
 }
 
 // Pass along x: rows i_y of inter (contiguous in l_x), keep i_x in [0, N), img = Re * dx[i_x].
-__global__ void __launch_bounds__(512)
+__global__ void __launch_bounds__(1024)
 ifft_pass_x_kernel(const float2 *__restrict__ inter, float *__restrict__ img, const float *__restrict__ deap,
                    const float2 *__restrict__ tw, int M, int logM, int N, int R) {
     extern __shared__ __align__(16) float2 z[];
@@ -189,11 +189,11 @@ ifft_pass_x_kernel(const float2 *__restrict__ inter, float *__restrict__ img, co
     const int rows = min(R, N - iy0);
     for (int i = threadIdx.x; i < rows * M; i += blockDim.x) z[i] = inter[(long long)iy0 * M + i];
     __syncthreads();
-    for (int r = 0; r < rows; ++r) fft_dif_inv(z + r * M, logM, tw, 1);
+    for (int r = 0; r < rows; ++r) stockham_fft(z + r * M, logM, tw, 1, true);
     const int h = N / 2;
     for (int i = threadIdx.x; i < rows * N; i += blockDim.x) {
         const int r = i / N, ix = i - r * N;
-        const int pos = bitrev((ix - h) & (M - 1), logM);
+        const int pos = (ix - h) & (M - 1);
         img[(long long)(iy0 + r) * N + ix] = z[r * M + pos].x * __ldg(deap + ix);
     }
 }
@@ -354,7 +354,7 @@ static bp_status spectra_t(bp_plan *p, const Tin *sino, cudaStream_t st) {
     const size_t smem = sizeof(float2) * p->P;
     BP_CUDA_TRY(cudaFuncSetAttribute(fourier_spectra_kernel<Tin>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem));
-    const int threads = std::min(512, std::max(32, p->P / 2));
+    const int threads = fft_threads(p->P);
     fourier_spectra_kernel<Tin><<<(p->n_theta + 1) / 2, threads, smem, st>>>(sino, p->four.spec, p->four.wk,
                                                                               p->d_twP, p->n_theta, p->n_det, logP);
     return BP_OK;
@@ -372,7 +372,7 @@ bp_status launch_fourier(bp_plan *p, const void *sino, bp_dtype dt, float *img, 
     const size_t smemR = sizeof(float2) * (size_t)R * M;
     BP_CUDA_TRY(cudaFuncSetAttribute(ifft_pass_y_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smemR));
     BP_CUDA_TRY(cudaFuncSetAttribute(ifft_pass_x_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smemR));
-    const int fft_threads = std::min(512, std::max(32, M / 2));
+    const int nthr = fft_threads(M);
     const float delta2 = (N % 2 == 0) ? 1.0f / (float)M : 0.0f;  // 2 delta / M
     for (int b = 0; b < batch; ++b) {
         const char *sb = (const char *)sino + esz * (size_t)b * p->n_theta * p->n_det;
@@ -388,8 +388,8 @@ bp_status launch_fourier(bp_plan *p, const void *sino, bp_dtype dt, float *img, 
         if (f.n_extra > 0)
             grid_spread_kernel<<<f.n_extra, kGridThreads, 0, st>>>(f.spec, f.ray, (const GridSeg *)f.segs,
                                                                    items + f.n_owner, f.grid, M, H, f.beta, delta2, 1);
-        ifft_pass_y_kernel<<<M / R, fft_threads, smemR, st>>>(f.grid, f.mid, f.deapod, f.twM, M, f.logM, N, R);
-        ifft_pass_x_kernel<<<(N + R - 1) / R, fft_threads, smemR, st>>>(f.mid, img + (size_t)b * N * N, f.deapod,
+        ifft_pass_y_kernel<<<M / R, nthr, smemR, st>>>(f.grid, f.mid, f.deapod, f.twM, M, f.logM, N, R);
+        ifft_pass_x_kernel<<<(N + R - 1) / R, nthr, smemR, st>>>(f.mid, img + (size_t)b * N * N, f.deapod,
                                                                        f.twM, M, f.logM, N, R);
         BP_CUDA_TRY(cudaGetLastError());
     }

@@ -40,9 +40,9 @@ bp_status scratch_address(int device, float **out) {
     return BP_OK;
 }
 
-// Bit-reversed filter response (dt/P) DFT_P(h_circ), h_circ[r] = h(|r|) for |r| < n_det,
+// Filter response (dt/P) DFT_P(h_circ), h_circ[r] = h(|r|) for |r| < n_det, natural order,
 // evaluated in double precision on the device (the host path uses an FP64 FFT).
-__global__ void static_response_kernel(float *__restrict__ Hbr, int P, int logP, int n_det, double dt, int kind) {
+__global__ void static_response_kernel(float *__restrict__ H, int P, int n_det, double dt, int kind) {
     const int half = P / 2;
     for (int m = blockIdx.x * blockDim.x + threadIdx.x; m <= half; m += gridDim.x * blockDim.x) {
         const double pi2dt2 = M_PI * M_PI * dt * dt;
@@ -59,8 +59,8 @@ __global__ void static_response_kernel(float *__restrict__ Hbr, int P, int logP,
             acc += 2.0 * h * cospi((double)a / (double)P);
         }
         const float v = (float)(acc * dt / (double)P);
-        Hbr[bitrev(m, logP)] = v;
-        if (m > 0 && m < half) Hbr[bitrev(P - m, logP)] = v;
+        H[m] = v;
+        if (m > 0 && m < half) H[P - m] = v;
     }
 }
 
@@ -89,17 +89,17 @@ extern "C" bp_status bp_fbp_static(bp_plan *p, const void *sino, bp_dtype dtype,
     float *scratch = nullptr;
     st = scratch_address(p->device, &scratch);
     if (st != BP_OK) return st;
-    float *Hbr = scratch;
+    float *H = scratch;
     float *q = scratch + h_floats;
     cudaStream_t s = (cudaStream_t)stream;
     // Every value the kernels read from the scratch is written earlier in this call, so
     // nothing needs clearing.
-    static_response_kernel<<<(p->P / 2 + 256) / 256, 256, 0, s>>>(Hbr, p->P, ilog2(p->P), p->n_det, p->dt, (int)kind);
+    static_response_kernel<<<(p->P / 2 + 256) / 256, 256, 0, s>>>(H, p->P, p->n_det, p->dt, (int)kind);
     BP_CUDA_TRY(cudaGetLastError());
     const size_t esz = dtype == BP_F32 ? 4 : 2;
     for (int b = 0; b < batch; ++b) {
         const char *sb = (const char *)sino + esz * slice * b;
-        st = launch_filter_response(p, sb, dtype, q, Hbr, 1, s);
+        st = launch_filter_response(p, sb, dtype, q, H, 1, s);
         if (st != BP_OK) return st;
         st = launch_direct(p, q, BP_F32, img + (size_t)b * p->N * p->N, 1, 0, s);
         if (st != BP_OK) return st;
