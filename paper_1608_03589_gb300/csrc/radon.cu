@@ -7,12 +7,17 @@
 // the band's 64 x 64 pixel tiles (the next tile is prefetched into registers while the
 // current one is processed) and keeps the full detector rows of its angles in shared
 // memory, so each sinogram bin is written to global memory once per band.  Within a tile
-// each warp owns a private window of bins per angle.  Lanes of a warp take pixels that
-// are S_k pixels apart along the angle's dominant axis, with S_k |dominant step| > 1 bin,
-// so the 32 lanes of one instruction always hit 32 different bins: the deposits are plain
-// shared-memory read-modify-writes, no atomics.  After each tile the warp windows are
-// summed into the detector rows (each bin owned by one thread).  The window origin J0 and
-// the tile-local coordinate come from the same 32.32 fixed-point tile stepping as R*.
+// each warp owns a private window per angle of interval sums (A_m, B_m) = (sum f,
+// sum f (q - m)) over the pixels whose tile-local coordinate q rounds to m; the two bins
+// around interval m then receive A/2 - B and A/2 + B (exactly (1 - fr) f and fr f summed),
+// with no cancellation because |q - m| <= 1/2.  Lanes of a warp take pixels S pixels apart
+// along the dominant axis of the block's angles, with S |dominant step| > 1 bin, so the 32
+// lanes of one instruction always hit 32 different intervals: each deposit is one plain
+// float2 shared-memory read-modify-write, no atomics; a pixel value is read once and
+// deposited for all angles of the block (independent windows, so their latencies
+// overlap).  After each tile the warp windows are folded into the detector rows (each bin
+// owned by one thread).  The window origin J0 and the tile-local coordinate come from the
+// same 32.32 fixed-point tile stepping as R*.
 #include <algorithm>
 
 #include "common.cuh"
@@ -32,11 +37,12 @@ radon_direct_kernel(const float *__restrict__ img, float *__restrict__ sino, con
                     int N, int n_det, int n_theta, int W, int C, int kAng, int tiles_per_band, float scale,
                     int use_atomic, long long img_stride, long long sino_stride) {
     extern __shared__ __align__(16) float rsm[];
-    float *rows = rsm;                                   // [kAng][n_det] detector rows of this CTA
-    float *tile = rows + kAng * n_det;                   // [64][65] current pixel tile
-    float *win = tile + kTile * (kTile + 1);             // [warps][kAng][W] private bin windows
-    __shared__ float4 sp[kAngMax];                       // q0, c, s, dominant step
-    __shared__ int sJ0[kAngMax], sS[kAngMax], sX[kAngMax];
+    float *rows = rsm;                                                   // [kAng][n_det] detector rows
+    float2 *win = reinterpret_cast<float2 *>(rows + ((kAng * n_det + 3) & ~3));  // [warps][kAng][W] (A, B)
+    float *tile = reinterpret_cast<float *>(win + kRWarps * kAng * W);  // [64][65] pixel tile
+    __shared__ float4 sp[kAngMax];  // q0, c, s, -
+    __shared__ int sJ0[kAngMax];
+    __shared__ int sMode[2];        // common (x-dominant, S) of the block's angles, or S = 0 if mixed
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int k0 = blockIdx.x * kAng;
@@ -48,8 +54,23 @@ radon_direct_kernel(const float *__restrict__ img, float *__restrict__ sino, con
     sino += (long long)blockIdx.z * sino_stride;
 
     for (int i = tid; i < kAng * n_det; i += kRThreads) rows[i] = 0.f;
-    float *mywin = win + warp * kAng * W;
-    for (int i = lane; i < kAng * W; i += 32) mywin[i] = 0.f;
+    float2 *mywin = win + warp * kAng * W;
+    for (int i = lane; i < kAng * W; i += 32) mywin[i] = make_float2(0.f, 0.f);
+    if (tid == 0) {
+        // one lane spacing for all angles of the block when they share a dominant axis
+        int xd = -1, S = 0;
+        for (int a = 0; a < kn; ++a) {
+            const AngleParam p = ap[k0 + a];
+            const bool x = fabsf(p.c) >= fabsf(p.s);
+            const float dom = x ? fabsf(p.c) : fabsf(p.s);
+            const int Sa = (int)floorf(1.0f / dom) + 1;  // Sa * |dominant step| > 1 bin
+            if (a == 0) { xd = x; S = Sa; }
+            else if (xd != (int)x) S = 0;
+            else S = max(S, Sa);
+        }
+        sMode[0] = xd;
+        sMode[1] = S;
+    }
 
     // register prefetch of a tile: thread covers rows (tid/64) + 4i, column tid%64
     float pre[16];
@@ -64,9 +85,41 @@ radon_direct_kernel(const float *__restrict__ img, float *__restrict__ sino, con
     };
     if (t_begin < t_end) fetch(t_begin);
 
+    // deposit the pixels of lines warp, warp + 8, ... of the tile for angles [a0, a1)
+    auto deposit = [&](int a0, int a1, bool xdom, int S) {
+        for (int line = warp; line < kTile; line += kRWarps) {
+            for (int base = 0; base < kTile; base += 32 * S) {
+                for (int ph = 0; ph < S; ++ph) {
+                    const int pos = base + ph + S * lane;
+                    const bool act = pos < kTile;
+                    const int x = xdom ? pos : line, y = xdom ? line : pos;
+                    const float f = act ? tile[y * (kTile + 1) + x] : 0.f;
+#pragma unroll
+                    for (int a = 0; a < kAngMax; ++a) {
+                        if (a0 + a < a1) {
+                            const float4 P = sp[a0 + a];
+                            const float q = fmaf((float)y, P.z, fmaf((float)x, P.y, P.x));
+                            const float r = q + kMagic;
+                            const int m = __float_as_int(r) - kMagicInt;  // rint(q)
+                            const float dq = q - (r - kMagic);            // q - m, in [-1/2, 1/2]
+                            if (act && f != 0.f) {
+                                float2 *cell = mywin + (a0 + a) * W + C + m;
+                                float2 v = *cell;
+                                v.x += f;
+                                v.y = fmaf(f, dq, v.y);
+                                *cell = v;
+                            }
+                        }
+                    }
+                    __syncwarp();
+                }
+            }
+        }
+    };
+
     for (int t = t_begin; t < t_end; ++t) {
         const int ty = t / tiles, tx = t % tiles;
-        __syncthreads();  // previous tile fully consumed (tile buffer, params, windows reduced)
+        __syncthreads();  // previous tile fully consumed (tile buffer, params, windows folded)
 #pragma unroll
         for (int i = 0; i < 16; ++i) tile[((tid >> 6) + 4 * i) * (kTile + 1) + (tid & 63)] = pre[i];
         if (tid < kn) {
@@ -76,55 +129,45 @@ radon_direct_kernel(const float *__restrict__ img, float *__restrict__ sino, con
             const float frac = (float)(unsigned)(U & 0xffffffffLL) * 2.3283064365386963e-10f;
             const float emin = (float)(kTile - 1) * (fminf(p.c, 0.f) + fminf(p.s, 0.f));
             const int J0 = Ji + (int)floorf(emin) - 1;
-            const float q0 = (float)(Ji - J0 - C) + (frac - 0.5f);
-            const bool xdom = fabsf(p.c) >= fabsf(p.s);
-            const float dom = xdom ? fabsf(p.c) : fabsf(p.s);
             sJ0[tid] = J0;
-            sS[tid] = (int)floorf(1.0f / dom) + 1;  // S * |dominant step| > 1 bin
-            sX[tid] = xdom ? 1 : 0;
-            sp[tid] = make_float4(q0, p.c, p.s, 0.f);
+            sp[tid] = make_float4((float)(Ji - J0 - C) + (frac - 0.5f), p.c, p.s, 0.f);
         }
         __syncthreads();
         if (t + 1 < t_end) fetch(t + 1);
 
-        for (int a = 0; a < kn; ++a) {
-            const float4 P = sp[a];
-            const int S = sS[a];
-            const bool xdom = sX[a] != 0;
-            float *wa = mywin + a * W + C;
-            // lines along the dominant axis: warp w takes lines w, w+8, ...; lane l takes
-            // positions phase + S*l on the line.
-            for (int line = warp; line < kTile; line += kRWarps) {
-                for (int ph = 0; ph < S; ++ph) {
-                    const int pos = ph + S * lane;
-                    const bool act = pos < kTile;  // all lanes reach both __syncwarp calls
-                    const int x = xdom ? pos : line, y = xdom ? line : pos;
-                    const float f = act ? tile[y * (kTile + 1) + x] : 0.f;
-                    const float q = fmaf((float)y, P.z, fmaf((float)x, P.y, P.x));
-                    const float r = q + kMagic;
-                    const int m = __float_as_int(r) - kMagicInt;  // rint(q)
-                    const float fr = (q - (r - kMagic)) + 0.5f;    // u - floor(u)
-                    const float hi = fr * f;
-                    if (act) wa[m] += f - hi;
-                    __syncwarp();
-                    if (act) wa[m + 1] += hi;
-                    __syncwarp();
-                }
+        if (sMode[1] > 0) {
+            deposit(0, kn, sMode[0] != 0, sMode[1]);
+        } else {
+            for (int a = 0; a < kn; ++a) {  // mixed dominant axes: one angle at a time
+                const float4 P = sp[a];
+                const bool x = fabsf(P.y) >= fabsf(P.z);
+                const float dom = x ? fabsf(P.y) : fabsf(P.z);
+                deposit(a, a + 1, x, (int)floorf(1.0f / dom) + 1);
             }
         }
         __syncthreads();
-        // sum the warp windows into the detector rows and clear them
+        // fold the warp windows into the detector rows: bin m takes interval m (lower part)
+        // and interval m - 1 (upper part); clear the windows
         for (int i = tid; i < kn * W; i += kRThreads) {
             const int a = i / W, m = i - a * W;
             float s = 0.f;
 #pragma unroll
             for (int w = 0; w < kRWarps; ++w) {
-                float *cell = win + (w * kAng + a) * W + m;
-                s += *cell;
-                *cell = 0.f;
+                const float2 *wa = win + (w * kAng + a) * W;
+                const float2 lo = wa[m];
+                s += 0.5f * lo.x - lo.y;
+                if (m > 0) {
+                    const float2 up = wa[m - 1];
+                    s += 0.5f * up.x + up.y;
+                }
             }
             const int j = sJ0[a] + m;
             if (j >= 0 && j < n_det) rows[a * n_det + j] += s;
+        }
+        __syncthreads();
+        for (int i = tid; i < kRWarps * kn * W; i += kRThreads) {
+            const int w = i / (kn * W), r = i - w * kn * W;
+            win[w * kAng * W + r] = make_float2(0.f, 0.f);
         }
     }
     __syncthreads();
@@ -148,7 +191,8 @@ bp_status launch_radon_direct(bp_plan *p, const float *img, float *sino, int bat
     const int ntiles = tiles * tiles;
     int kAng = kAngMax;
     while (kAng > 1 && (size_t)kAng * p->n_det * 4 > 64 * 1024) kAng >>= 1;
-    const size_t smem = sizeof(float) * ((size_t)kAng * p->n_det + kTile * (kTile + 1) + (size_t)kRWarps * kAng * p->W);
+    const size_t smem = sizeof(float) * ((((size_t)kAng * p->n_det + 3) & ~(size_t)3) + kTile * (kTile + 1)) +
+                        sizeof(float2) * (size_t)kRWarps * kAng * p->W;
     if (smem > 200 * 1024) return fail(BP_ERR_UNSUPPORTED, "radon: n_det or window too large for shared memory");
     // bands: enough CTAs to fill the GPU about twice, at most one band per tile
     const int ablocks = (p->n_theta + kAng - 1) / kAng;
