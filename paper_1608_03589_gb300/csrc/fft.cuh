@@ -40,15 +40,22 @@ __device__ __constant__ const float kS16[8] = {0.0f, 0.38268343236508977f, 0.707
                                                1.0f, 0.92387953251128674f, 0.70710678118654752f,
                                                0.38268343236508977f};
 
+template <int R> struct Log2R;
+template <> struct Log2R<2> { static constexpr int v = 1; };
+template <> struct Log2R<4> { static constexpr int v = 2; };
+template <> struct Log2R<8> { static constexpr int v = 3; };
+template <> struct Log2R<16> { static constexpr int v = 4; };
+
 // In-register R-point DFT (R = 2, 4, 8, 16), iterative radix-2 on the register array,
-// natural order in and out.
+// natural order in and out.  All loops have compile-time trip counts (fully unrolled).
 template <int R>
-__device__ __forceinline__ void dft_reg(float2 *a, bool inverse) {
+__device__ __forceinline__ void dft_reg(float2 (&a)[R], bool inverse) {
+    constexpr int LR = Log2R<R>::v;
 #pragma unroll
     for (int i = 0; i < R; ++i) {
         int j = 0;
 #pragma unroll
-        for (int b = 1, t = i; b < R; b <<= 1, t >>= 1) j = (j << 1) | (t & 1);
+        for (int b = 0; b < LR; ++b) j |= ((i >> b) & 1) << (LR - 1 - b);
         if (j > i) {
             const float2 tmp = a[i];
             a[i] = a[j];
@@ -56,14 +63,14 @@ __device__ __forceinline__ void dft_reg(float2 *a, bool inverse) {
         }
     }
 #pragma unroll
-    for (int len = 2; len <= R; len <<= 1) {
-        const int h = len >> 1;
+    for (int st = 0; st < LR; ++st) {
+        const int h = 1 << st;
 #pragma unroll
         for (int k = 0; k < h; ++k) {
-            const int idx = k * (16 / len);
+            const int idx = k * (8 >> st);
             const float2 w = make_float2(kC16[idx], inverse ? kS16[idx] : -kS16[idx]);
 #pragma unroll
-            for (int i = k; i < R; i += len) {
+            for (int i = k; i < R; i += 2 * h) {
                 const float2 u = a[i];
                 const float2 v = (k == 0) ? a[i + h] : cmul(a[i + h], w);
                 a[i] = cadd(u, v);
@@ -73,18 +80,18 @@ __device__ __forceinline__ void dft_reg(float2 *a, bool inverse) {
     }
 }
 
-// One Stockham pass of radix R over sub-transforms of length L (L R <= P).  Each thread
-// handles G = 16 / R butterflies groups; the block must have at least P / 16 threads.
-template <int R>
+// One Stockham pass of radix R over sub-transforms of length L (L R <= P).  Each of the nthr
+// threads handles G = E / R butterfly groups (E elements per thread); nthr = P / E.
+template <int R, int E>
 __device__ __forceinline__ void stockham_pass(float2 *z, int logP, int L, const float2 *__restrict__ tw, int twstride,
-                                              bool inverse) {
-    constexpr int G = 16 / R;
+                                              bool inverse, int tid, int nthr) {
+    constexpr int G = E / R;
     const int P = 1 << logP;
     const int m = P / R;
     float2 a[G][R];
 #pragma unroll
     for (int g = 0; g < G; ++g) {
-        const int t = threadIdx.x + g * blockDim.x;
+        const int t = tid + g * nthr;
         if (t < m) {
 #pragma unroll
             for (int r = 0; r < R; ++r) a[g][r] = z[t + r * m];
@@ -93,7 +100,7 @@ __device__ __forceinline__ void stockham_pass(float2 *z, int logP, int L, const 
     __syncthreads();
 #pragma unroll
     for (int g = 0; g < G; ++g) {
-        const int t = threadIdx.x + g * blockDim.x;
+        const int t = tid + g * nthr;
         if (t < m) {
             const int k = t & (L - 1);
             const int j = t / L;
@@ -110,35 +117,51 @@ __device__ __forceinline__ void stockham_pass(float2 *z, int logP, int L, const 
     __syncthreads();
 }
 
-// Threads per block for a length-P transform.
+// Elements per thread and threads per transform of length P: 8 per thread (radix <= 8
+// passes, fits 64 registers) up to P = 8192, 16 per thread above.
+__host__ __device__ inline int fft_elems(int P) { return P > 8192 ? 16 : 8; }
 __host__ __device__ inline int fft_threads(int P) {
-    const int t = P / 16;
-    return t < 32 ? 32 : (t > 1024 ? 1024 : t);
+    const int t = P / fft_elems(P);
+    return t < 32 ? 32 : t;
 }
 
-// Whole transform (blockDim.x >= P/16, see fft_threads); z ends synchronised.
-__device__ __forceinline__ void stockham_fft(float2 *z, int logP, const float2 *__restrict__ tw, int twstride,
-                                             bool inverse) {
+template <int E>
+__device__ __forceinline__ void stockham_fft_e(float2 *z, int logP, const float2 *__restrict__ tw, int twstride,
+                                               bool inverse, int tid, int nthr) {
     int L = 1, rem = logP;
     while (rem > 0) {
-        if (rem >= 4) {
-            stockham_pass<16>(z, logP, L, tw, twstride, inverse);
-            L <<= 4;
-            rem -= 4;
-        } else if (rem == 3) {
-            stockham_pass<8>(z, logP, L, tw, twstride, inverse);
+        if constexpr (E >= 16) {
+            if (rem >= 4) {
+                stockham_pass<16, E>(z, logP, L, tw, twstride, inverse, tid, nthr);
+                L <<= 4;
+                rem -= 4;
+                continue;
+            }
+        }
+        if (rem >= 3) {
+            stockham_pass<8, E>(z, logP, L, tw, twstride, inverse, tid, nthr);
             L <<= 3;
             rem -= 3;
         } else if (rem == 2) {
-            stockham_pass<4>(z, logP, L, tw, twstride, inverse);
+            stockham_pass<4, E>(z, logP, L, tw, twstride, inverse, tid, nthr);
             L <<= 2;
             rem -= 2;
         } else {
-            stockham_pass<2>(z, logP, L, tw, twstride, inverse);
+            stockham_pass<2, E>(z, logP, L, tw, twstride, inverse, tid, nthr);
             L <<= 1;
             rem -= 1;
         }
     }
+}
+
+// Whole transform by a group of nthr = fft_threads(P) threads (tid in [0, nthr)), E =
+// fft_elems(P).  Every thread of the block must make the same sequence of calls (block
+// barriers inside: several groups can transform several arrays of the same length
+// together).  z ends synchronised.
+template <int E>
+__device__ __forceinline__ void stockham_fft(float2 *z, int logP, const float2 *__restrict__ tw, int twstride,
+                                             bool inverse, int tid, int nthr) {
+    stockham_fft_e<E>(z, logP, tw, twstride, inverse, tid, nthr);
 }
 
 __device__ __forceinline__ int bitrev(int v, int logP) { return (int)(__brev((unsigned)v) >> (32 - logP)); }

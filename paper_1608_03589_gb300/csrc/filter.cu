@@ -17,8 +17,8 @@ namespace bp {
 
 namespace {
 
-template <typename Tin>
-__global__ void __launch_bounds__(1024)
+template <typename Tin, int E>
+__global__ void __launch_bounds__(1024, 1)
 filter_kernel(const Tin *__restrict__ in, float *__restrict__ out, const float *__restrict__ H,
               const float2 *__restrict__ tw, long long rows, int n_det, int logP) {
     extern __shared__ __align__(16) float2 z[];
@@ -36,14 +36,14 @@ filter_kernel(const Tin *__restrict__ in, float *__restrict__ out, const float *
         z[j] = make_float2(va, vb);
     }
     __syncthreads();
-    stockham_fft(z, logP, tw, 1, false);
+    stockham_fft<E>(z, logP, tw, 1, false, threadIdx.x, blockDim.x);
     for (int j = threadIdx.x; j < P; j += blockDim.x) {
         const float h = __ldg(H + j);
         const float2 v = z[j];
         z[j] = make_float2(v.x * h, v.y * h);
     }
     __syncthreads();
-    stockham_fft(z, logP, tw, 1, true);
+    stockham_fft<E>(z, logP, tw, 1, true, threadIdx.x, blockDim.x);
     float *oa = out + r0 * n_det;
     float *ob = out + r1 * n_det;
     for (int j = threadIdx.x; j < n_det; j += blockDim.x) {
@@ -124,10 +124,17 @@ bp_status launch_filter(bp_plan *p, const void *in, bp_dtype dt, float *out, int
     const unsigned blocks = (unsigned)((rows + 1) / 2);
 #define BP_FILTER_LAUNCH(T)                                                                               \
     do {                                                                                                  \
-        BP_CUDA_TRY(cudaFuncSetAttribute(filter_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
-                                         (int)smem));                                                     \
-        filter_kernel<T><<<blocks, threads, smem, st>>>((const T *)in, out, p->d_H[kind], p->d_twP, rows, \
-                                                        p->n_det, logP);                                  \
+        if (fft_elems(p->P) == 16) {                                                                      \
+            BP_CUDA_TRY(cudaFuncSetAttribute(filter_kernel<T, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                             (int)smem));                                                 \
+            filter_kernel<T, 16><<<blocks, threads, smem, st>>>((const T *)in, out, p->d_H[kind], p->d_twP, \
+                                                                rows, p->n_det, logP);                    \
+        } else {                                                                                          \
+            BP_CUDA_TRY(cudaFuncSetAttribute(filter_kernel<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                             (int)smem));                                                 \
+            filter_kernel<T, 8><<<blocks, threads, smem, st>>>((const T *)in, out, p->d_H[kind], p->d_twP,  \
+                                                               rows, p->n_det, logP);                     \
+        }                                                                                                 \
     } while (0)
     switch (dt) {
         case BP_F32: BP_FILTER_LAUNCH(float); break;
@@ -151,10 +158,17 @@ bp_status launch_filter_response(bp_plan *p, const void *in, bp_dtype dt, float 
     const unsigned blocks = (unsigned)((rows + 1) / 2);
 #define BP_FILTER_LAUNCH_H(T)                                                                             \
     do {                                                                                                  \
-        BP_CUDA_TRY(cudaFuncSetAttribute(filter_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
-                                         (int)smem));                                                     \
-        filter_kernel<T><<<blocks, threads, smem, st>>>((const T *)in, out, H, p->d_twP, rows, p->n_det,   \
-                                                        logP);                                            \
+        if (fft_elems(p->P) == 16) {                                                                      \
+            BP_CUDA_TRY(cudaFuncSetAttribute(filter_kernel<T, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                             (int)smem));                                                 \
+            filter_kernel<T, 16><<<blocks, threads, smem, st>>>((const T *)in, out, H, p->d_twP, rows,     \
+                                                                p->n_det, logP);                          \
+        } else {                                                                                          \
+            BP_CUDA_TRY(cudaFuncSetAttribute(filter_kernel<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                             (int)smem));                                                 \
+            filter_kernel<T, 8><<<blocks, threads, smem, st>>>((const T *)in, out, H, p->d_twP, rows,      \
+                                                               p->n_det, logP);                           \
+        }                                                                                                 \
     } while (0)
     switch (dt) {
         case BP_F32: BP_FILTER_LAUNCH_H(float); break;

@@ -29,14 +29,15 @@
 
 #include "common.cuh"
 #include "fft.cuh"
+#include "tma.cuh"
 
 namespace bp {
 
 namespace {
 
 constexpr int kW = 6;          // kernel width (grid cells)
-constexpr int kTS = 32;        // grid tile side
-constexpr int kMaxItem = 4096; // samples per gridding work item
+constexpr int kTS = 64;        // grid tile side
+constexpr int kMaxItem = 2048; // samples per gridding work item
 constexpr int kGridThreads = 256;
 
 struct GridSeg {
@@ -46,16 +47,32 @@ struct GridItem {
     int x0, y0, seg_begin, seg_end;
 };
 
+// Modified Bessel function I0 for x >= 0 by the polynomial approximations of Abramowitz &
+// Stegun, Handbook of Mathematical Functions, 9.8.1 (x <= 3.75) and 9.8.2 (x >= 3.75),
+// relative error below 2e-7.  Both branches are evaluated (no divergence).
+__device__ __forceinline__ float bessel_i0(float x) {
+    const float a = x * (1.0f / 3.75f);
+    const float a2 = a * a;
+    const float small =
+        1.0f + a2 * (3.5156229f + a2 * (3.0899424f + a2 * (1.2067492f + a2 * (0.2659732f + a2 * (0.0360768f +
+        a2 * 0.0045813f)))));
+    const float t = 3.75f / fmaxf(x, 3.75f);
+    const float p = 0.39894228f + t * (0.01328592f + t * (0.00225319f + t * (-0.00157565f + t * (0.00916281f +
+                    t * (-0.02057706f + t * (0.02635537f + t * (-0.01647633f + t * 0.00392377f)))))));
+    const float large = p * __expf(x) * rsqrtf(fmaxf(x, 3.75f));
+    return x < 3.75f ? small : large;
+}
+
 __device__ __forceinline__ float kb_weight(float t, float beta) {
     // I0(beta sqrt(1 - (2t/W)^2)) for |t| <= W/2
     const float a = t * (2.0f / kW);
     const float r = fmaxf(0.f, 1.f - a * a);
-    return cyl_bessel_i0f(beta * sqrtf(r));
+    return bessel_i0(beta * sqrtf(r));
 }
 
 // ---------------------------------------------------------------------------------- (1) spectra
-template <typename Tin>
-__global__ void __launch_bounds__(1024)
+template <typename Tin, int E>
+__global__ void __launch_bounds__(1024, 1)
 fourier_spectra_kernel(const Tin *__restrict__ sino, float2 *__restrict__ spec, const float *__restrict__ wk,
                        const float2 *__restrict__ tw, int n_theta, int n_det, int logP) {
     extern __shared__ __align__(16) float2 z[];
@@ -73,7 +90,7 @@ fourier_spectra_kernel(const Tin *__restrict__ sino, float2 *__restrict__ spec, 
         z[j] = make_float2(va, vb);
     }
     __syncthreads();
-    stockham_fft(z, logP, tw, 1, false);
+    stockham_fft<E>(z, logP, tw, 1, false, threadIdx.x, blockDim.x);
     // A[m] = (Z[m] + conj Z[P-m]) / 2,  B[m] = (Z[m] - conj Z[P-m]) / (2i)
     const float wa = __ldg(wk + k0) / (float)P;
     const float wb = has1 ? __ldg(wk + k1) / (float)P : 0.f;
@@ -96,8 +113,11 @@ fourier_spectra_kernel(const Tin *__restrict__ sino, float2 *__restrict__ spec, 
 }
 
 // ---------------------------------------------------------------------------------- (2) gridding
-// G[l_x][l_y] (l mod M).  One CTA per work item; groups of 6 lanes spread one sample each.
-__global__ void __launch_bounds__(kGridThreads)
+// G[l_x][l_y] (l mod M).  One CTA per work item (segments of rays crossing one 64 x 64
+// tile); a warp takes one segment at a time, one sample per lane (consecutive samples of
+// the ray), and deposits the sample's 6 x 6 footprint cells that fall in the tile into the
+// shared-memory tile with shared atomics.
+__global__ void __launch_bounds__(kGridThreads, 3)
 grid_spread_kernel(const float2 *__restrict__ spec, const long long *__restrict__ ray, const GridSeg *__restrict__ segs,
                    const GridItem *__restrict__ items, float2 *__restrict__ grid, int M, int H, float beta,
                    float delta2_over_M, int accumulate) {
@@ -106,44 +126,38 @@ grid_spread_kernel(const float2 *__restrict__ spec, const long long *__restrict_
     for (int i = threadIdx.x; i < kTS * kTS; i += kGridThreads) acc[i / kTS][i % kTS] = make_float2(0.f, 0.f);
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int grp = lane / 6, tx = lane - 6 * grp;   // grp 5 = idle lanes 30, 31
-    const unsigned gmask = 0x3fu << (6 * min(grp, 4));
     const int Mmask = M - 1;
     for (int j = it.seg_begin + warp; j < it.seg_end; j += kGridThreads / 32) {
         const GridSeg sg = segs[j];
         const long long ax = ray[2 * sg.k], ay = ray[2 * sg.k + 1];
-        for (int mb = sg.m_lo; mb <= sg.m_hi; mb += 5) {
-            const int m = mb + grp;
-            const bool act = (grp < 5) && (m <= sg.m_hi);
-            // all 6 lanes of a group agree on act; idle lanes still join the shuffles of their group
-            long long zx = (long long)m * ax, zy = (long long)m * ay;
+        const float2 *sk = spec + (long long)sg.k * H;
+        for (int m = sg.m_lo + lane; m <= sg.m_hi; m += 32) {
+            const long long zx = (long long)m * ax, zy = (long long)m * ay;
             const int fx = (int)(zx >> 32), fy = (int)(zy >> 32);
             const float rx = (float)(unsigned)(zx & 0xffffffffLL) * 2.3283064365386963e-10f;
             const float ry = (float)(unsigned)(zy & 0xffffffffLL) * 2.3283064365386963e-10f;
-            const float wx = kb_weight((float)(tx - 2) - rx, beta);
-            const float wyown = kb_weight((float)(tx - 2) - ry, beta);
-            float2 v = make_float2(0.f, 0.f);
-            if (act) {
-                v = __ldg(spec + (long long)sg.k * H + m);
-                float sn, cs;
-                sincospif(((float)(fx + fy) + (rx + ry)) * delta2_over_M, &sn, &cs);
-                v = cmul(v, make_float2(cs, sn));
-            }
-            const int cx = (fx - 2 + tx) & Mmask;
-            const int lx = cx - it.x0;
-            const bool inx = act && lx >= 0 && lx < kTS;
+            float2 v = __ldg(sk + m);
+            float sn, cs;
+            sincospif(((float)(fx + fy) + (rx + ry)) * delta2_over_M, &sn, &cs);
+            v = cmul(v, make_float2(cs, sn));
+            float wy[kW];
 #pragma unroll
-            for (int ty = 0; ty < kW; ++ty) {
-                const float wy = __shfl_sync(0xffffffffu, wyown, 6 * min(grp, 4) + ty);
-                const int cy = (fy - 2 + ty) & Mmask;
-                const int ly = cy - it.y0;
-                if (inx && ly >= 0 && ly < kTS) {
-                    const float w = wx * wy;
-                    atomicAdd(&acc[lx][ly].x, w * v.x);
-                    atomicAdd(&acc[lx][ly].y, w * v.y);
+            for (int t = 0; t < kW; ++t) wy[t] = kb_weight((float)(t - 2) - ry, beta);
+#pragma unroll
+            for (int tx = 0; tx < kW; ++tx) {
+                const int lx = ((fx - 2 + tx) & Mmask) - it.x0;
+                if (lx < 0 || lx >= kTS) continue;
+                const float wx = kb_weight((float)(tx - 2) - rx, beta);
+                const float2 vx = make_float2(wx * v.x, wx * v.y);
+#pragma unroll
+                for (int ty = 0; ty < kW; ++ty) {
+                    const int ly = ((fy - 2 + ty) & Mmask) - it.y0;
+                    if (ly >= 0 && ly < kTS) {
+                        atomicAdd(&acc[lx][ly].x, wy[ty] * vx.x);
+                        atomicAdd(&acc[lx][ly].y, wy[ty] * vx.y);
+                    }
                 }
             }
-            (void)gmask;
         }
     }
     __syncthreads();
@@ -161,15 +175,37 @@ grid_spread_kernel(const float2 *__restrict__ spec, const long long *__restrict_
 }
 
 // ---------------------------------------------------------------------------------- (3) inverse FFT passes
-// Pass along y: rows l_x of G (contiguous in l_y), keep i_y in [0, N), write inter[i_y][l_x] * dy[i_y].
-__global__ void __launch_bounds__(1024)
-ifft_pass_y_kernel(const float2 *__restrict__ grid, float2 *__restrict__ inter, const float *__restrict__ deap,
-                   const float2 *__restrict__ tw, int M, int logM, int N, int R) {
-    extern __shared__ __align__(16) float2 z[];
-    const int lx0 = blockIdx.x * R;
-    for (int i = threadIdx.x; i < R * M; i += blockDim.x) z[i] = grid[(long long)lx0 * M + i];
+// R contiguous rows per CTA arrive with one bulk asynchronous copy; blockDim / fft_threads(M)
+// thread groups transform them in rounds.
+__device__ __forceinline__ bool load_rows_async(float2 *z, const float2 *src, int count, unsigned long long *bar) {
+    const uint32_t b = smem_u32(bar);
+    if (threadIdx.x == 0) {
+        mbar_init(b, 1);
+        mbar_fence_init();
+    }
     __syncthreads();
-    for (int r = 0; r < R; ++r) stockham_fft(z + r * M, logM, tw, 1, true);
+    if (threadIdx.x == 0) {
+        mbar_expect_tx(b, (uint32_t)(count * sizeof(float2)));
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+            ::"r"(smem_u32(z)), "l"(src), "r"((uint32_t)(count * sizeof(float2))), "r"(b)
+            : "memory");
+    }
+    return mbar_wait(b, 0);
+}
+
+// Pass along y: rows l_x of G (contiguous in l_y), keep i_y in [0, N), write inter[i_y][l_x] * dy[i_y].
+template <int E>
+__global__ void __launch_bounds__(1024, 1)
+ifft_pass_y_kernel(const float2 *__restrict__ grid, float2 *__restrict__ inter, const float *__restrict__ deap,
+                   const float2 *__restrict__ tw, int M, int logM, int N, int R, int *__restrict__ err) {
+    extern __shared__ __align__(128) float2 z[];
+    __shared__ __align__(8) unsigned long long bar;
+    const int lx0 = blockIdx.x * R;
+    const int nthr = fft_threads(M), groups = blockDim.x / nthr;
+    const int g = threadIdx.x / nthr, tid = threadIdx.x - g * nthr;
+    if (!load_rows_async(z, grid + (long long)lx0 * M, R * M, &bar) && threadIdx.x == 0) atomicExch(err, 1);
+    for (int r0 = 0; r0 < R; r0 += groups) stockham_fft<E>(z + (r0 + g) * M, logM, tw, 1, true, tid, nthr);
     const int h = N / 2;
     for (int i = threadIdx.x; i < N * R; i += blockDim.x) {
         const int iy = i / R, r = i - iy * R;
@@ -181,15 +217,19 @@ ifft_pass_y_kernel(const float2 *__restrict__ grid, float2 *__restrict__ inter, 
 }
 
 // Pass along x: rows i_y of inter (contiguous in l_x), keep i_x in [0, N), img = Re * dx[i_x].
-__global__ void __launch_bounds__(1024)
+template <int E>
+__global__ void __launch_bounds__(1024, 1)
 ifft_pass_x_kernel(const float2 *__restrict__ inter, float *__restrict__ img, const float *__restrict__ deap,
-                   const float2 *__restrict__ tw, int M, int logM, int N, int R) {
-    extern __shared__ __align__(16) float2 z[];
+                   const float2 *__restrict__ tw, int M, int logM, int N, int R, int *__restrict__ err) {
+    extern __shared__ __align__(128) float2 z[];
+    __shared__ __align__(8) unsigned long long bar;
     const int iy0 = blockIdx.x * R;
     const int rows = min(R, N - iy0);
-    for (int i = threadIdx.x; i < rows * M; i += blockDim.x) z[i] = inter[(long long)iy0 * M + i];
-    __syncthreads();
-    for (int r = 0; r < rows; ++r) stockham_fft(z + r * M, logM, tw, 1, true);
+    const int nthr = fft_threads(M), groups = blockDim.x / nthr;
+    const int g = threadIdx.x / nthr, tid = threadIdx.x - g * nthr;
+    if (!load_rows_async(z, inter + (long long)iy0 * M, rows * M, &bar) && threadIdx.x == 0) atomicExch(err, 1);
+    // rows beyond the last image row hold stale data that is transformed but never written out
+    for (int r0 = 0; r0 < R; r0 += groups) stockham_fft<E>(z + (r0 + g) * M, logM, tw, 1, true, tid, nthr);
     const int h = N / 2;
     for (int i = threadIdx.x; i < rows * N; i += blockDim.x) {
         const int r = i / N, ix = i - r * N;
@@ -352,11 +392,11 @@ template <typename Tin>
 static bp_status spectra_t(bp_plan *p, const Tin *sino, cudaStream_t st) {
     const int logP = ilog2(p->P);
     const size_t smem = sizeof(float2) * p->P;
-    BP_CUDA_TRY(cudaFuncSetAttribute(fourier_spectra_kernel<Tin>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem));
     const int threads = fft_threads(p->P);
-    fourier_spectra_kernel<Tin><<<(p->n_theta + 1) / 2, threads, smem, st>>>(sino, p->four.spec, p->four.wk,
-                                                                              p->d_twP, p->n_theta, p->n_det, logP);
+    auto kern = fft_elems(p->P) == 16 ? fourier_spectra_kernel<Tin, 16> : fourier_spectra_kernel<Tin, 8>;
+    BP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<(p->n_theta + 1) / 2, threads, smem, st>>>(sino, p->four.spec, p->four.wk, p->d_twP, p->n_theta, p->n_det,
+                                                      logP);
     return BP_OK;
 }
 
@@ -370,9 +410,13 @@ bp_status launch_fourier(bp_plan *p, const void *sino, bp_dtype dt, float *img, 
     const size_t esz = dt == BP_F32 ? 4 : 2;
     const int R = rows_per_cta(M);
     const size_t smemR = sizeof(float2) * (size_t)R * M;
-    BP_CUDA_TRY(cudaFuncSetAttribute(ifft_pass_y_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smemR));
-    BP_CUDA_TRY(cudaFuncSetAttribute(ifft_pass_x_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smemR));
+    auto pass_y = fft_elems(M) == 16 ? ifft_pass_y_kernel<16> : ifft_pass_y_kernel<8>;
+    auto pass_x = fft_elems(M) == 16 ? ifft_pass_x_kernel<16> : ifft_pass_x_kernel<8>;
+    BP_CUDA_TRY(cudaFuncSetAttribute(pass_y, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smemR));
+    BP_CUDA_TRY(cudaFuncSetAttribute(pass_x, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smemR));
     const int nthr = fft_threads(M);
+    int groups = 1;
+    while (groups * 2 <= R && nthr * groups * 2 <= 1024) groups *= 2;
     const float delta2 = (N % 2 == 0) ? 1.0f / (float)M : 0.0f;  // 2 delta / M
     for (int b = 0; b < batch; ++b) {
         const char *sb = (const char *)sino + esz * (size_t)b * p->n_theta * p->n_det;
@@ -388,9 +432,10 @@ bp_status launch_fourier(bp_plan *p, const void *sino, bp_dtype dt, float *img, 
         if (f.n_extra > 0)
             grid_spread_kernel<<<f.n_extra, kGridThreads, 0, st>>>(f.spec, f.ray, (const GridSeg *)f.segs,
                                                                    items + f.n_owner, f.grid, M, H, f.beta, delta2, 1);
-        ifft_pass_y_kernel<<<M / R, nthr, smemR, st>>>(f.grid, f.mid, f.deapod, f.twM, M, f.logM, N, R);
-        ifft_pass_x_kernel<<<(N + R - 1) / R, nthr, smemR, st>>>(f.mid, img + (size_t)b * N * N, f.deapod,
-                                                                       f.twM, M, f.logM, N, R);
+        pass_y<<<M / R, nthr * groups, smemR, st>>>(f.grid, f.mid, f.deapod, f.twM, M, f.logM, N, R,
+                                                           p->d_err);
+        pass_x<<<(N + R - 1) / R, nthr * groups, smemR, st>>>(f.mid, img + (size_t)b * N * N, f.deapod,
+                                                                     f.twM, M, f.logM, N, R, p->d_err);
         BP_CUDA_TRY(cudaGetLastError());
     }
     return BP_OK;
