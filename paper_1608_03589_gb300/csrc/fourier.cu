@@ -238,6 +238,138 @@ ifft_pass_x_kernel(const float2 *__restrict__ inter, float *__restrict__ img, co
     }
 }
 
+// ---------------------------------------------------------------------------------- adjoint (R_F)
+// R_F = (dx^2/dt) diag(1/w) A_F^T with A_F the Fourier-path R* above.  Transposing every
+// linear step in reverse order: deapodise and embed the image, forward 2D FFT (pruned:
+// N nonzero input rows and columns), Kaiser-Bessel interpolation at the polar samples
+// (the transpose of spreading), conjugate sample factors, and per angle the Hermitian
+// inverse P-point FFT whose first n_det outputs are the projection.
+
+// Pass along x: image rows i_y (R per CTA) embedded at (i - floor(N/2)) mod M, times the
+// deapodisation, forward FFT, written to T[i_y][l_x].
+template <int E>
+__global__ void __launch_bounds__(1024, 1)
+adj_fft_x_kernel(const float *__restrict__ img, float2 *__restrict__ T, const float *__restrict__ deap,
+                 const float2 *__restrict__ tw, int M, int logM, int N, int R) {
+    extern __shared__ __align__(128) float2 z[];
+    const int iy0 = blockIdx.x * R;
+    const int rows = min(R, N - iy0);
+    const int nthr = fft_threads(M), groups = blockDim.x / nthr;
+    const int g = threadIdx.x / nthr, tid = threadIdx.x - g * nthr;
+    const int h = N / 2;
+    for (int i = threadIdx.x; i < R * M; i += blockDim.x) z[i] = make_float2(0.f, 0.f);
+    __syncthreads();
+    for (int i = threadIdx.x; i < rows * N; i += blockDim.x) {
+        const int r = i / N, ix = i - r * N;
+        const float v = __ldg(img + (long long)(iy0 + r) * N + ix) * __ldg(deap + ix) * __ldg(deap + iy0 + r);
+        z[r * M + ((ix - h) & (M - 1))] = make_float2(v, 0.f);
+    }
+    __syncthreads();
+    for (int r0 = 0; r0 < R; r0 += groups) stockham_fft<E>(z + (r0 + g) * M, logM, tw, 1, false, tid, nthr);
+    for (int i = threadIdx.x; i < rows * M; i += blockDim.x) T[(long long)iy0 * M + i] = z[i];
+}
+
+// Pass along y: columns l_x (R per CTA) of T, embedded at (i_y - floor(N/2)) mod M, forward
+// FFT, written to G[l_x][l_y].
+template <int E>
+__global__ void __launch_bounds__(1024, 1)
+adj_fft_y_kernel(const float2 *__restrict__ T, float2 *__restrict__ grid, const float2 *__restrict__ tw, int M,
+                 int logM, int N, int R) {
+    extern __shared__ __align__(128) float2 z[];
+    const int lx0 = blockIdx.x * R;
+    const int nthr = fft_threads(M), groups = blockDim.x / nthr;
+    const int g = threadIdx.x / nthr, tid = threadIdx.x - g * nthr;
+    const int h = N / 2;
+    for (int i = threadIdx.x; i < R * M; i += blockDim.x) z[i] = make_float2(0.f, 0.f);
+    __syncthreads();
+    for (int i = threadIdx.x; i < N * R; i += blockDim.x) {
+        const int iy = i / R, r = i - iy * R;
+        z[r * M + ((iy - h) & (M - 1))] = T[(long long)iy * M + lx0 + r];
+    }
+    __syncthreads();
+    for (int r0 = 0; r0 < R; r0 += groups) stockham_fft<E>(z + (r0 + g) * M, logM, tw, 1, false, tid, nthr);
+    for (int i = threadIdx.x; i < R * M; i += blockDim.x) grid[(long long)lx0 * M + i] = z[i];
+}
+
+// Interpolation at the polar samples (transpose of the spreading): one thread per sample,
+// consecutive samples of one ray in consecutive lanes; result times the conjugate sample
+// factor (1/P)(m ? 2 : 1) exp(-i pi m (n_det-1)/P) exp(-2 pi i delta (z_x + z_y)/M) and dx^2/dt.
+__global__ void __launch_bounds__(256)
+adj_interp_kernel(const float2 *__restrict__ grid, float2 *__restrict__ spec, const long long *__restrict__ ray,
+                  int M, int H, int P, int n_det, float beta, float delta2_over_M, float scale) {
+    const int k = blockIdx.y;
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= H) return;
+    const long long zx = (long long)m * ray[2 * k], zy = (long long)m * ray[2 * k + 1];
+    const int fx = (int)(zx >> 32), fy = (int)(zy >> 32);
+    const float rx = (float)(unsigned)(zx & 0xffffffffLL) * 2.3283064365386963e-10f;
+    const float ry = (float)(unsigned)(zy & 0xffffffffLL) * 2.3283064365386963e-10f;
+    const int Mmask = M - 1;
+    float wy[kW];
+#pragma unroll
+    for (int t = 0; t < kW; ++t) wy[t] = kb_weight((float)(t - 2) - ry, beta);
+    float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int tx = 0; tx < kW; ++tx) {
+        const float wx = kb_weight((float)(tx - 2) - rx, beta);
+        const float2 *row = grid + (long long)((fx - 2 + tx) & Mmask) * M;
+        float2 r = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int ty = 0; ty < kW; ++ty) {
+            const float2 v = __ldg(row + ((fy - 2 + ty) & Mmask));
+            r.x = fmaf(wy[ty], v.x, r.x);
+            r.y = fmaf(wy[ty], v.y, r.y);
+        }
+        acc.x = fmaf(wx, r.x, acc.x);
+        acc.y = fmaf(wx, r.y, acc.y);
+    }
+    float sn, cs;
+    sincospif(-((float)(fx + fy) + (rx + ry)) * delta2_over_M, &sn, &cs);
+    acc = cmul(acc, make_float2(cs, sn));
+    const long long ph = ((long long)m * (n_det - 1)) % (2LL * P);
+    sincospif(-(float)ph / (float)P, &sn, &cs);
+    acc = cmul(acc, make_float2(cs, sn));
+    const float f = (m == 0 ? 1.f : 2.f) * scale / (float)P;
+    spec[(long long)k * H + m] = make_float2(f * acc.x, f * acc.y);
+}
+
+// Per projection pair: y_j = Re sum_{m < P/2} s_m exp(2 pi i m j / P) = (1/2) IFFT(Hermitian(s))_j;
+// two real outputs share one complex transform (Z = H_a + i H_b).
+template <int E>
+__global__ void __launch_bounds__(1024, 1)
+adj_rows_kernel(const float2 *__restrict__ spec, float *__restrict__ sino, const float2 *__restrict__ tw,
+                int n_theta, int n_det, int logP) {
+    extern __shared__ __align__(16) float2 z[];
+    const int P = 1 << logP, H = P >> 1;
+    const int k0 = 2 * blockIdx.x, k1 = k0 + 1;
+    const bool has1 = k1 < n_theta;
+    const float2 *sa = spec + (long long)k0 * H, *sb = spec + (long long)k1 * H;
+    for (int m = threadIdx.x; m < P; m += blockDim.x) {
+        float2 ha, hb;  // Hermitian completions
+        if (m == 0) {
+            ha = make_float2(2.f * sa[0].x, 0.f);
+            hb = make_float2(has1 ? 2.f * sb[0].x : 0.f, 0.f);
+        } else if (m < H) {
+            ha = sa[m];
+            hb = has1 ? sb[m] : make_float2(0.f, 0.f);
+        } else if (m == H) {
+            ha = hb = make_float2(0.f, 0.f);
+        } else {
+            const float2 a = sa[P - m];
+            const float2 b = has1 ? sb[P - m] : make_float2(0.f, 0.f);
+            ha = make_float2(a.x, -a.y);
+            hb = make_float2(b.x, -b.y);
+        }
+        z[m] = make_float2(ha.x - hb.y, ha.y + hb.x);  // H_a + i H_b
+    }
+    __syncthreads();
+    stockham_fft<E>(z, logP, tw, 1, true, threadIdx.x, blockDim.x);
+    for (int j = threadIdx.x; j < n_det; j += blockDim.x) {
+        sino[(long long)k0 * n_det + j] = 0.5f * z[j].x;
+        if (has1) sino[(long long)k1 * n_det + j] = 0.5f * z[j].y;
+    }
+}
+
 double kb_hat(double f, double beta) {
     // Fourier transform of I0(beta sqrt(1 - (2t/W)^2)) on |t| <= W/2 at frequency f (cycles per cell)
     const double x = M_PI * kW * f;
@@ -441,8 +573,36 @@ bp_status launch_fourier(bp_plan *p, const void *sino, bp_dtype dt, float *img, 
     return BP_OK;
 }
 
-bp_status launch_radon_fourier(bp_plan *, const float *, float *, int, cudaStream_t) {
-    return fail(BP_ERR_UNSUPPORTED, "Fourier adjoint not built yet");
+bp_status launch_radon_fourier(bp_plan *p, const float *img, float *sino, int batch, cudaStream_t st) {
+    bp_status s = ensure_fourier(p);
+    if (s != BP_OK) return s;
+    FourierWork &f = p->four;
+    const int N = p->N, M = f.M, P = p->P, H = P / 2;
+    const int R = rows_per_cta(M);
+    const size_t smemR = sizeof(float2) * (size_t)R * M;
+    const int nthr = fft_threads(M);
+    int groups = 1;
+    while (groups * 2 <= R && nthr * groups * 2 <= 1024) groups *= 2;
+    const bool e16 = fft_elems(M) == 16;
+    auto kx = e16 ? adj_fft_x_kernel<16> : adj_fft_x_kernel<8>;
+    auto ky = e16 ? adj_fft_y_kernel<16> : adj_fft_y_kernel<8>;
+    auto kr = fft_elems(P) == 16 ? adj_rows_kernel<16> : adj_rows_kernel<8>;
+    BP_CUDA_TRY(cudaFuncSetAttribute(kx, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smemR));
+    BP_CUDA_TRY(cudaFuncSetAttribute(ky, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smemR));
+    BP_CUDA_TRY(cudaFuncSetAttribute(kr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(float2) * P)));
+    const float delta2 = (N % 2 == 0) ? 1.0f / (float)M : 0.0f;
+    const float scale = (float)(p->dx * p->dx / p->dt);
+    for (int b = 0; b < batch; ++b) {
+        kx<<<(N + R - 1) / R, nthr * groups, smemR, st>>>(img + (size_t)b * N * N, f.mid, f.deapod, f.twM, M, f.logM,
+                                                         N, R);
+        ky<<<M / R, nthr * groups, smemR, st>>>(f.mid, f.grid, f.twM, M, f.logM, N, R);
+        adj_interp_kernel<<<dim3((H + 255) / 256, p->n_theta), 256, 0, st>>>(f.grid, f.spec, f.ray, M, H, P, p->n_det,
+                                                                              f.beta, delta2, scale);
+        kr<<<(p->n_theta + 1) / 2, fft_threads(P), sizeof(float2) * P, st>>>(
+            f.spec, sino + (size_t)b * p->n_theta * p->n_det, p->d_twP, p->n_theta, p->n_det, ilog2(P));
+        BP_CUDA_TRY(cudaGetLastError());
+    }
+    return BP_OK;
 }
 
 }  // namespace bp

@@ -70,3 +70,56 @@ def test_fourier_batch_and_low_precision():
     img16 = plan.backproject_fourier(g16)
     ref = oracle.bp_trig_dirichlet(rounded(g16[0]), N, theta, 2.0 / n_det)
     assert oracle.rel_l2(img16[0].cpu().numpy(), ref) <= TOL_FOURIER
+
+
+# ----------------------------------------------------------------------------------- adjoint R_F
+@pytest.mark.parametrize("N,n_det,n_theta,dt_scale,seed", [
+    (32, 32, 24, 1.0, 0), (37, 41, 7, 1.0, 1), (20, 30, 11, 1.3, 2), (33, 24, 9, 0.6, 3), (1, 1, 1, 1.0, 4)])
+def test_fourier_adjoint_vs_oracle(N, n_det, n_theta, dt_scale, seed):
+    rng = np.random.default_rng(seed)
+    theta = random_theta(rng, n_theta)
+    dt = dt_scale * 2.0 / n_det
+    f = to_dev(rng.normal(size=(N, N)))
+    plan = bp.Plan(N, n_det, theta, dt)
+    g = plan.radon(f, fourier=True)
+    kj = np.arange(n_theta * n_det)
+    ref = oracle.radon_trig_points(rounded(f), n_det, theta, dt, kj).reshape(n_theta, n_det)
+    err = oracle.rel_l2(g.cpu().numpy(), ref)
+    print(f"R_F N={N}: rel-L2 {err:.2e}")
+    assert err <= TOL_FOURIER
+
+
+def test_fourier_adjoint_identity_on_device():
+    # eq "adjoint", discrete, for the Fourier pair: sum_k w_k dt <R_F f, g>_k = dx^2 <f, B_F g>
+    rng = np.random.default_rng(31)
+    N, n_det, n_theta = 200, 181, 97
+    theta = random_theta(rng, n_theta)
+    dt = 1.1 * 2.0 / n_det
+    plan = bp.Plan(N, n_det, theta, dt)
+    f = to_dev(rng.normal(size=(N, N)))
+    g = to_dev(rng.normal(size=(n_theta, n_det)))
+    Rf = rounded(plan.radon(f, fourier=True))
+    Bg = rounded(plan.backproject_fourier(g))
+    w = oracle.weights(theta)
+    lhs = float(np.sum(w[:, None] * dt * Rf * rounded(g)))
+    rhs = float((2.0 / N) ** 2 * np.sum(rounded(f) * Bg))
+    scale = float(np.linalg.norm(w[:, None] * dt * Rf) * np.linalg.norm(rounded(g)))
+    print(f"Fourier adjoint identity: |lhs - rhs| / scale = {abs(lhs - rhs) / scale:.2e}")
+    assert abs(lhs - rhs) <= 1e-5 * scale
+
+
+def test_fourier_adjoint_full_size_sampled():
+    wl = synth.LARGE
+    e = synth.random_ellipses(wl.n_ellipses, wl.seed)
+    f = to_dev(synth.ellipse_image(e, wl.N))
+    plan = bp.Plan(wl.N, wl.n_det, wl.theta, wl.det_spacing)
+    g = plan.radon(f, fourier=True)
+    rng = np.random.default_rng(5)
+    ks = rng.choice(wl.n_theta, 6, replace=False)
+    js = rng.choice(wl.n_det, 4, replace=False)
+    kj = np.array([k * wl.n_det + j for k in ks for j in js])
+    ref = oracle.radon_trig_points(rounded(f), wl.n_det, wl.theta, wl.det_spacing, kj)
+    got = g.reshape(-1)[torch.from_numpy(kj).to(dev())].cpu().numpy()
+    err = oracle.rel_l2(got, ref)
+    print(f"R_F 2048^2 x 1800 sampled rel-L2 {err:.2e}")
+    assert err <= TOL_FOURIER
