@@ -136,6 +136,26 @@ bp_status bp_radon(bp_plan *plan, const float *img, float *sino, int batch, int 
                    void *stream);
 
 /*
+ * bp_radon_transpose -- img = R^T sino, the exact Euclidean transpose of bp_radon (the
+ * gradient of <R f, sino> with respect to f).  Since R = (dx^2/dt) diag(1/w) A^T, this is
+ * R* (A) with every quadrature weight w_k replaced by dx^2/dt.  fourier selects the direct
+ * or the Fourier-path pair.  sino: device, batch x n_theta x n_det float32; img: device,
+ * batch x N x N float32 (overwritten).
+ */
+bp_status bp_radon_transpose(bp_plan *plan, const float *sino, float *img, int batch, int fourier,
+                             void *stream);
+
+/*
+ * bp_backproject_transpose -- sino = A^T img, the exact Euclidean transpose of R* (the
+ * gradient of <R* g, img> with respect to g): A^T = (dt/dx^2) diag(w_k) R, i.e. R with
+ * projection k scaled by w_k instead of dx^2/dt.  fourier selects the direct or the
+ * Fourier-path pair.  img: device, batch x N x N float32; sino: device,
+ * batch x n_theta x n_det float32 (overwritten).
+ */
+bp_status bp_backproject_transpose(bp_plan *plan, const float *img, float *sino, int batch, int fourier,
+                                   void *stream);
+
+/*
  * bp_fbp_host -- filtered backprojection from HOST memory to HOST memory:
  * copy sino (host, batch x n_theta x n_det float32) to the device, bp_filter(kind, param),
  * bp_backproject_direct, copy the image back into img (host, batch x N x N float32),

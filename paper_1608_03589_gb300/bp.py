@@ -25,7 +25,8 @@ _DTYPES = {torch.float32: BP_F32, torch.bfloat16: BP_BF16, torch.float16: BP_F16
 
 # Every symbol the header declares (checked by the ABI test).
 SYMBOLS = ("bp_plan_create", "bp_destroy", "bp_filter", "bp_backproject_direct", "bp_backproject_fourier",
-           "bp_radon", "bp_fbp_host", "bp_backproject_batched", "bp_fbp_static", "bp_check", "bp_last_error", "bp_version")
+           "bp_radon", "bp_fbp_host", "bp_backproject_batched", "bp_fbp_static", "bp_check", "bp_radon_transpose", "bp_backproject_transpose", "bp_last_error",
+           "bp_version")
 
 
 class BPError(RuntimeError):
@@ -56,10 +57,13 @@ def lib() -> ctypes.CDLL:
             L.bp_fbp_host.argtypes = [vp, vp, vp, i, f, i, vp]
             L.bp_fbp_static.argtypes = [vp, vp, i, vp, i, i, vp]
             L.bp_check.argtypes = [vp, vp]
+            L.bp_radon_transpose.argtypes = [vp, vp, vp, i, i, vp]
+            L.bp_backproject_transpose.argtypes = [vp, vp, vp, i, i, vp]
             L.bp_backproject_batched.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(i),
                                                  ctypes.POINTER(vp), i, vp]
             for name in ("bp_filter", "bp_backproject_direct", "bp_backproject_fourier", "bp_radon",
-                         "bp_fbp_host", "bp_backproject_batched", "bp_fbp_static", "bp_check"):
+                         "bp_fbp_host", "bp_backproject_batched", "bp_fbp_static", "bp_check",
+                         "bp_radon_transpose", "bp_backproject_transpose"):
                 getattr(L, name).restype = i
             L.bp_last_error.argtypes = []
             L.bp_last_error.restype = ctypes.c_char_p
@@ -184,6 +188,40 @@ class Plan:
         with torch.cuda.device(self.device):
             _check(lib().bp_radon(self.handle, img.data_ptr(), out.data_ptr(), b, int(bool(fourier)), _stream(img)),
                    "bp_radon")
+        return out
+
+    def radon_transpose(self, sino: torch.Tensor, out: torch.Tensor | None = None,
+                        fourier: bool = False) -> torch.Tensor:
+        """R^T sino: exact Euclidean transpose of radon() (bp_radon_transpose)."""
+        _cuda(sino, "sino")
+        b = self._batch(sino, (self.n_theta, self.n_det), "sino")
+        if sino.dtype != torch.float32:
+            raise BPError("sino must be float32")
+        if out is None:
+            out = torch.empty((*sino.shape[:-2], self.N, self.N), dtype=torch.float32, device=sino.device)
+        _cuda(out, "out")
+        if out.dtype != torch.float32 or out.numel() != b * self.N * self.N:
+            raise BPError("out must be float32 with batch x N x N elements")
+        with torch.cuda.device(self.device):
+            _check(lib().bp_radon_transpose(self.handle, sino.data_ptr(), out.data_ptr(), b, int(bool(fourier)),
+                                            _stream(sino)), "bp_radon_transpose")
+        return out
+
+    def backproject_transpose(self, img: torch.Tensor, out: torch.Tensor | None = None,
+                              fourier: bool = False) -> torch.Tensor:
+        """A^T img: exact Euclidean transpose of backproject() / backproject_fourier()."""
+        _cuda(img, "img")
+        b = self._batch(img, (self.N, self.N), "img")
+        if img.dtype != torch.float32:
+            raise BPError("img must be float32")
+        if out is None:
+            out = torch.empty((*img.shape[:-2], self.n_theta, self.n_det), dtype=torch.float32, device=img.device)
+        _cuda(out, "out")
+        if out.dtype != torch.float32 or out.numel() != b * self.n_theta * self.n_det:
+            raise BPError("out must be float32 with batch x n_theta x n_det elements")
+        with torch.cuda.device(self.device):
+            _check(lib().bp_backproject_transpose(self.handle, img.data_ptr(), out.data_ptr(), b,
+                                                  int(bool(fourier)), _stream(img)), "bp_backproject_transpose")
         return out
 
     def fbp_host(self, sino: torch.Tensor, kind: str | int = "ramlak", param: float = 0.0,

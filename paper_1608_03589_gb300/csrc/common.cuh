@@ -96,13 +96,18 @@ bool aligned16(const void *ptr);
 int ilog2(int v);
 
 // launchers implemented in the kernel translation units
+// wuni > 0 replaces every quadrature weight w_k by wuni; per_angle_w = 1 scales angle k of R
+// by w_k instead of dx^2/dt (the two weightings of the Euclidean transposes).
 bp_status launch_direct(bp_plan *p, const void *sino, bp_dtype dt, float *img, int batch, int accumulate,
-                        cudaStream_t st);
+                        cudaStream_t st, float wuni = 0.f);
 bp_status launch_filter(bp_plan *p, const void *in, bp_dtype dt, float *out, int kind, float param, int batch,
                         cudaStream_t st);
-bp_status launch_radon_direct(bp_plan *p, const float *img, float *sino, int batch, cudaStream_t st);
-bp_status launch_fourier(bp_plan *p, const void *sino, bp_dtype dt, float *img, int batch, cudaStream_t st);
-bp_status launch_radon_fourier(bp_plan *p, const float *img, float *sino, int batch, cudaStream_t st);
+bp_status launch_radon_direct(bp_plan *p, const float *img, float *sino, int batch, cudaStream_t st,
+                              int per_angle_w = 0);
+bp_status launch_fourier(bp_plan *p, const void *sino, bp_dtype dt, float *img, int batch, cudaStream_t st,
+                         float wuni = 0.f);
+bp_status launch_radon_fourier(bp_plan *p, const float *img, float *sino, int batch, cudaStream_t st,
+                               int per_angle_w = 0);
 bp_status ensure_filter(bp_plan *p, int kind, float param);
 bp_status launch_filter_response(bp_plan *p, const void *in, bp_dtype dt, float *out, const float *Hbr, int batch,
                                  cudaStream_t st);

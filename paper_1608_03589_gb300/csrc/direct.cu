@@ -39,7 +39,7 @@ template <typename Tin>
 __global__ void __launch_bounds__(kThreads, 2)
 bp_direct_kernel(const Tin *__restrict__ sino, float *__restrict__ img, const AngleParam *__restrict__ ap,
                  int N, int n_det, int n_theta, int W, int C, int accumulate,
-                 long long sino_stride, long long img_stride) {
+                 long long sino_stride, long long img_stride, float wuni) {
     extern __shared__ __align__(16) float2 tab[];  // [kStage][W] (e, d) pairs
     __shared__ float4 sp[kStage];                  // q0, c, s, table base (bits)
     __shared__ int sJ0[kStage];
@@ -74,7 +74,7 @@ bp_direct_kernel(const Tin *__restrict__ sino, float *__restrict__ img, const An
             const int J0 = Ji + (int)floorf(emin) - 1;
             const float q0 = (float)(Ji - J0 - C) + (frac - 0.5f);
             sJ0[tid] = J0;
-            sw[tid] = p.w;
+            sw[tid] = wuni > 0.f ? wuni : p.w;
             const unsigned base = tab_u32 + (unsigned)(tid * W) * 8u + 8u * (unsigned)C - (kMagicBits << 3);
             sp[tid] = make_float4(q0, p.c, p.s, __uint_as_float(base));
         }
@@ -164,7 +164,7 @@ template <typename Tin>
 __global__ void __launch_bounds__(kThreads, 3)
 bp_direct_tma_kernel(const __grid_constant__ CUtensorMap tmap, float *__restrict__ img,
                      const AngleParam *__restrict__ ap, int N, int n_theta, int W, int C, int Wb, int RS,
-                     int accumulate, long long img_stride, int *__restrict__ err) {
+                     int accumulate, long long img_stride, int *__restrict__ err, float wuni) {
     extern __shared__ __align__(128) unsigned char dsm[];
     unsigned char *raw = dsm;                                              // [2][kStage] rows of RS bytes
     float2 *tab = reinterpret_cast<float2 *>(dsm + 2 * kStage * RS);     // [2][kStage][W]
@@ -207,7 +207,7 @@ bp_direct_tma_kernel(const __grid_constant__ CUtensorMap tmap, float *__restrict
                                   (kMagicBits << 3);
             sp[slot][tid] = make_float4(q0, p.c, p.s, __uint_as_float(base));
             sof[slot][tid] = J0 - J0r;
-            sw[slot][tid] = p.w;
+            sw[slot][tid] = wuni > 0.f ? wuni : p.w;
             tma_load_3d(smem_u32(raw + (b * kStage + tid) * RS), &tmap, J0r, k0 + tid, bz, bar0 + 8 * b);
         }
     };
@@ -305,7 +305,8 @@ template <> constexpr CUtensorMapDataType tmap_type<__nv_bfloat16>() { return CU
 template <> constexpr CUtensorMapDataType tmap_type<__half>() { return CU_TENSOR_MAP_DATA_TYPE_FLOAT16; }
 
 template <typename Tin>
-bp_status launch_direct_t(bp_plan *p, const Tin *sino, float *img, int batch, int accumulate, cudaStream_t st) {
+bp_status launch_direct_t(bp_plan *p, const Tin *sino, float *img, int batch, int accumulate, cudaStream_t st,
+                          float wuni) {
     const int tiles = (p->N + kTile - 1) / kTile;
     const int esz = (int)sizeof(Tin);
     const int Wb = (p->W + 8 + 7) & ~7;
@@ -326,7 +327,7 @@ bp_status launch_direct_t(bp_plan *p, const Tin *sino, float *img, int batch, in
             BP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             dim3 grid(tiles, tiles, batch);
             kern<<<grid, kThreads, smem, st>>>(map, img, p->d_ang, p->N, p->n_theta, p->W, p->C, Wb, RS, accumulate,
-                                               (long long)p->N * p->N, p->d_err);
+                                               (long long)p->N * p->N, p->d_err, wuni);
             BP_CUDA_TRY(cudaGetLastError());
             return BP_OK;
         }
@@ -336,7 +337,7 @@ bp_status launch_direct_t(bp_plan *p, const Tin *sino, float *img, int batch, in
     BP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 grid(tiles, tiles, batch);
     kern<<<grid, kThreads, smem, st>>>(sino, img, p->d_ang, p->N, p->n_det, p->n_theta, p->W, p->C, accumulate,
-                                       (long long)p->n_theta * p->n_det, (long long)p->N * p->N);
+                                       (long long)p->n_theta * p->n_det, (long long)p->N * p->N, wuni);
     BP_CUDA_TRY(cudaGetLastError());
     return BP_OK;
 }
@@ -344,11 +345,11 @@ bp_status launch_direct_t(bp_plan *p, const Tin *sino, float *img, int batch, in
 }  // namespace
 
 bp_status launch_direct(bp_plan *p, const void *sino, bp_dtype dt, float *img, int batch, int accumulate,
-                        cudaStream_t st) {
+                        cudaStream_t st, float wuni) {
     switch (dt) {
-        case BP_F32: return launch_direct_t(p, (const float *)sino, img, batch, accumulate, st);
-        case BP_BF16: return launch_direct_t(p, (const __nv_bfloat16 *)sino, img, batch, accumulate, st);
-        case BP_F16: return launch_direct_t(p, (const __half *)sino, img, batch, accumulate, st);
+        case BP_F32: return launch_direct_t(p, (const float *)sino, img, batch, accumulate, st, wuni);
+        case BP_BF16: return launch_direct_t(p, (const __nv_bfloat16 *)sino, img, batch, accumulate, st, wuni);
+        case BP_F16: return launch_direct_t(p, (const __half *)sino, img, batch, accumulate, st, wuni);
     }
     return fail(BP_ERR_INVALID_ARG, "invalid dtype");
 }

@@ -74,7 +74,7 @@ __device__ __forceinline__ float kb_weight(float t, float beta) {
 template <typename Tin, int E>
 __global__ void __launch_bounds__(1024, 1)
 fourier_spectra_kernel(const Tin *__restrict__ sino, float2 *__restrict__ spec, const float *__restrict__ wk,
-                       const float2 *__restrict__ tw, int n_theta, int n_det, int logP) {
+                       const float2 *__restrict__ tw, int n_theta, int n_det, int logP, float wuni) {
     extern __shared__ __align__(16) float2 z[];
     const int P = 1 << logP, H = P >> 1;
     const int k0 = 2 * blockIdx.x, k1 = k0 + 1;
@@ -92,8 +92,8 @@ fourier_spectra_kernel(const Tin *__restrict__ sino, float2 *__restrict__ spec, 
     __syncthreads();
     stockham_fft<E>(z, logP, tw, 1, false, threadIdx.x, blockDim.x);
     // A[m] = (Z[m] + conj Z[P-m]) / 2,  B[m] = (Z[m] - conj Z[P-m]) / (2i)
-    const float wa = __ldg(wk + k0) / (float)P;
-    const float wb = has1 ? __ldg(wk + k1) / (float)P : 0.f;
+    const float wa = (wuni > 0.f ? wuni : __ldg(wk + k0)) / (float)P;
+    const float wb = has1 ? (wuni > 0.f ? wuni : __ldg(wk + k1)) / (float)P : 0.f;
     const long long twoP = 2LL * P;
     for (int m = threadIdx.x; m < H; m += blockDim.x) {
         const float2 zm = z[m];
@@ -296,7 +296,8 @@ adj_fft_y_kernel(const float2 *__restrict__ T, float2 *__restrict__ grid, const 
 // factor (1/P)(m ? 2 : 1) exp(-i pi m (n_det-1)/P) exp(-2 pi i delta (z_x + z_y)/M) and dx^2/dt.
 __global__ void __launch_bounds__(256)
 adj_interp_kernel(const float2 *__restrict__ grid, float2 *__restrict__ spec, const long long *__restrict__ ray,
-                  int M, int H, int P, int n_det, float beta, float delta2_over_M, float scale) {
+                  int M, int H, int P, int n_det, float beta, float delta2_over_M, float scale,
+                  const float *__restrict__ wk) {
     const int k = blockIdx.y;
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= H) return;
@@ -329,7 +330,7 @@ adj_interp_kernel(const float2 *__restrict__ grid, float2 *__restrict__ spec, co
     const long long ph = ((long long)m * (n_det - 1)) % (2LL * P);
     sincospif(-(float)ph / (float)P, &sn, &cs);
     acc = cmul(acc, make_float2(cs, sn));
-    const float f = (m == 0 ? 1.f : 2.f) * scale / (float)P;
+    const float f = (m == 0 ? 1.f : 2.f) * (wk ? __ldg(wk + k) : scale) / (float)P;
     spec[(long long)k * H + m] = make_float2(f * acc.x, f * acc.y);
 }
 
@@ -521,20 +522,21 @@ bp_status ensure_fourier(bp_plan *p) {
 }
 
 template <typename Tin>
-static bp_status spectra_t(bp_plan *p, const Tin *sino, cudaStream_t st) {
+static bp_status spectra_t(bp_plan *p, const Tin *sino, cudaStream_t st, float wuni) {
     const int logP = ilog2(p->P);
     const size_t smem = sizeof(float2) * p->P;
     const int threads = fft_threads(p->P);
     auto kern = fft_elems(p->P) == 16 ? fourier_spectra_kernel<Tin, 16> : fourier_spectra_kernel<Tin, 8>;
     BP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     kern<<<(p->n_theta + 1) / 2, threads, smem, st>>>(sino, p->four.spec, p->four.wk, p->d_twP, p->n_theta, p->n_det,
-                                                      logP);
+                                                      logP, wuni);
     return BP_OK;
 }
 
 static int rows_per_cta(int M) { return std::max(1, std::min(4, (int)(131072 / (sizeof(float2) * M)))); }
 
-bp_status launch_fourier(bp_plan *p, const void *sino, bp_dtype dt, float *img, int batch, cudaStream_t st) {
+bp_status launch_fourier(bp_plan *p, const void *sino, bp_dtype dt, float *img, int batch, cudaStream_t st,
+                         float wuni) {
     bp_status s = ensure_fourier(p);
     if (s != BP_OK) return s;
     FourierWork &f = p->four;
@@ -553,9 +555,9 @@ bp_status launch_fourier(bp_plan *p, const void *sino, bp_dtype dt, float *img, 
     for (int b = 0; b < batch; ++b) {
         const char *sb = (const char *)sino + esz * (size_t)b * p->n_theta * p->n_det;
         switch (dt) {
-            case BP_F32: s = spectra_t(p, (const float *)sb, st); break;
-            case BP_BF16: s = spectra_t(p, (const __nv_bfloat16 *)sb, st); break;
-            case BP_F16: s = spectra_t(p, (const __half *)sb, st); break;
+            case BP_F32: s = spectra_t(p, (const float *)sb, st, wuni); break;
+            case BP_BF16: s = spectra_t(p, (const __nv_bfloat16 *)sb, st, wuni); break;
+            case BP_F16: s = spectra_t(p, (const __half *)sb, st, wuni); break;
         }
         if (s != BP_OK) return s;
         const GridItem *items = (const GridItem *)f.items;
@@ -573,7 +575,8 @@ bp_status launch_fourier(bp_plan *p, const void *sino, bp_dtype dt, float *img, 
     return BP_OK;
 }
 
-bp_status launch_radon_fourier(bp_plan *p, const float *img, float *sino, int batch, cudaStream_t st) {
+bp_status launch_radon_fourier(bp_plan *p, const float *img, float *sino, int batch, cudaStream_t st,
+                               int per_angle_w) {
     bp_status s = ensure_fourier(p);
     if (s != BP_OK) return s;
     FourierWork &f = p->four;
@@ -597,7 +600,8 @@ bp_status launch_radon_fourier(bp_plan *p, const float *img, float *sino, int ba
                                                          N, R);
         ky<<<M / R, nthr * groups, smemR, st>>>(f.mid, f.grid, f.twM, M, f.logM, N, R);
         adj_interp_kernel<<<dim3((H + 255) / 256, p->n_theta), 256, 0, st>>>(f.grid, f.spec, f.ray, M, H, P, p->n_det,
-                                                                              f.beta, delta2, scale);
+                                                                              f.beta, delta2, scale,
+                                                                              per_angle_w ? f.wk : nullptr);
         kr<<<(p->n_theta + 1) / 2, fft_threads(P), sizeof(float2) * P, st>>>(
             f.spec, sino + (size_t)b * p->n_theta * p->n_det, p->d_twP, p->n_theta, p->n_det, ilog2(P));
         BP_CUDA_TRY(cudaGetLastError());

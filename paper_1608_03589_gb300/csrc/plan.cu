@@ -317,3 +317,26 @@ extern "C" bp_status bp_check(bp_plan *p, void *stream) {
     }
     return BP_OK;
 }
+
+extern "C" bp_status bp_radon_transpose(bp_plan *p, const float *sino, float *img, int batch, int fourier,
+                                        void *stream) {
+    set_error("");
+    bp_status st = check_common(p, sino, img, batch);
+    if (st != BP_OK) return st;
+    if ((const void *)img == (const void *)sino) return fail(BP_ERR_INVALID_ARG, "img and sino must not alias");
+    // R = (dx^2/dt) diag(1/w) A^T  =>  R^T = (dx^2/dt) A diag(1/w): R* with every weight dx^2/dt
+    const float wu = (float)(p->dx * p->dx / p->dt);
+    if (fourier) return launch_fourier(p, sino, BP_F32, img, batch, (cudaStream_t)stream, wu);
+    return launch_direct(p, sino, BP_F32, img, batch, 0, (cudaStream_t)stream, wu);
+}
+
+extern "C" bp_status bp_backproject_transpose(bp_plan *p, const float *img, float *sino, int batch, int fourier,
+                                              void *stream) {
+    set_error("");
+    bp_status st = check_common(p, img, sino, batch);
+    if (st != BP_OK) return st;
+    if ((const void *)img == (const void *)sino) return fail(BP_ERR_INVALID_ARG, "img and sino must not alias");
+    // A^T = (dt/dx^2) diag(w) R: R with angle k scaled by w_k instead of dx^2/dt
+    if (fourier) return launch_radon_fourier(p, img, sino, batch, (cudaStream_t)stream, 1);
+    return launch_radon_direct(p, img, sino, batch, (cudaStream_t)stream, 1);
+}

@@ -35,7 +35,7 @@ constexpr int kAngMax = 4;
 __global__ void __launch_bounds__(kRThreads, 2)
 radon_direct_kernel(const float *__restrict__ img, float *__restrict__ sino, const AngleParam *__restrict__ ap,
                     int N, int n_det, int n_theta, int W, int C, int kAng, int tiles_per_band, float scale,
-                    int use_atomic, long long img_stride, long long sino_stride) {
+                    int use_atomic, long long img_stride, long long sino_stride, int per_angle_w) {
     extern __shared__ __align__(16) float rsm[];
     float *rows = rsm;                                                   // [kAng][n_det] detector rows
     float2 *win = reinterpret_cast<float2 *>(rows + ((kAng * n_det + 3) & ~3));  // [warps][kAng][W] (A, B)
@@ -174,7 +174,7 @@ radon_direct_kernel(const float *__restrict__ img, float *__restrict__ sino, con
     for (int i = tid; i < kn * n_det; i += kRThreads) {
         const int a = i / n_det, j = i - a * n_det;
         float *dst = sino + (long long)(k0 + a) * n_det + j;
-        const float v = scale * rows[i];
+        const float v = (per_angle_w ? __ldg(&ap[k0 + a].w) : scale) * rows[i];
         if (use_atomic) {
             if (v != 0.f) atomicAdd(dst, v);
         } else {
@@ -185,7 +185,7 @@ radon_direct_kernel(const float *__restrict__ img, float *__restrict__ sino, con
 
 }  // namespace
 
-bp_status launch_radon_direct(bp_plan *p, const float *img, float *sino, int batch, cudaStream_t st) {
+bp_status launch_radon_direct(bp_plan *p, const float *img, float *sino, int batch, cudaStream_t st, int per_angle_w) {
     const size_t sino_n = (size_t)p->n_theta * p->n_det;
     const int tiles = (p->N + kTile - 1) / kTile;
     const int ntiles = tiles * tiles;
@@ -206,7 +206,7 @@ bp_status launch_radon_direct(bp_plan *p, const float *img, float *sino, int bat
     dim3 grid(ablocks, bands, batch);
     radon_direct_kernel<<<grid, kRThreads, smem, st>>>(img, sino, p->d_ang, p->N, p->n_det, p->n_theta, p->W, p->C,
                                                        kAng, per_band, scale, use_atomic, (long long)p->N * p->N,
-                                                       (long long)sino_n);
+                                                       (long long)sino_n, per_angle_w);
     BP_CUDA_TRY(cudaGetLastError());
     return BP_OK;
 }
