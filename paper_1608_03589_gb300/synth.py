@@ -155,3 +155,38 @@ class Workload:
 SMALL = Workload("slice256_bins256_ang180", 256, 256, 180, 10, 0.0, 1000)
 # Single slice, 2048^2 image, 2048 bins, 1800 angles, 50 ellipses + 1% noise (Shepp-Logan).
 LARGE = Workload("slice2048_bins2048_ang1800", 2048, 2048, 1800, 50, 0.01, 2000)
+
+
+def ellipse_sinogram_torch(e: Ellipses, theta: np.ndarray, n_det: int, det_spacing: float | None = None,
+                           device="cuda"):
+    """ellipse_sinogram evaluated with torch in float64 on `device` (same formula, for large batches)."""
+    import torch
+
+    dt = default_det_spacing(n_det) if det_spacing is None else float(det_spacing)
+    th = torch.as_tensor(np.asarray(theta, dtype=np.float64), device=device)
+    t = (torch.arange(n_det, dtype=torch.float64, device=device) - (n_det - 1) / 2.0) * dt
+    g = torch.zeros((th.shape[0], n_det), dtype=torch.float64, device=device)
+    ct = torch.cos(th)[:, None]
+    st = torch.sin(th)[:, None]
+    for i in range(len(e)):
+        a, b = float(e.a[i]), float(e.b[i])
+        ang = th[:, None] - float(e.alpha[i])
+        A2 = (a * torch.cos(ang)) ** 2 + (b * torch.sin(ang)) ** 2
+        tp = t[None, :] - (float(e.cx[i]) * ct + float(e.cy[i]) * st)
+        rad = torch.clamp(A2 - tp * tp, min=0.0)
+        g += float(e.rho[i]) * (2.0 * a * b) * torch.sqrt(rad) / A2
+    return g
+
+
+# 256 slices of 2048^2 from 2048 bins x 1800 angles, BF16 storage, 30 ellipses per slice.
+VOLUME = Workload("volume256_slice2048_bins2048_ang1800_bf16", 2048, 2048, 1800, 30, 0.0, 3000)
+VOLUME_SLICES = 256
+
+
+def mixed_batch_geometries(n: int = 64, seed: int = 5000):
+    """Uneven batch: image side = detector width drawn from {512, 1024, 2048, 4096}, angle
+    counts uniform in [360, 3000] (uniform angles on [0, pi))."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    sizes = rng.choice([512, 1024, 2048, 4096], size=n)
+    angles = rng.integers(360, 3001, size=n)
+    return [(int(s), int(s), int(a)) for s, a in zip(sizes, angles)]
