@@ -28,6 +28,7 @@ sys.path.insert(0, ROOT)
 FLOPS_PER_UPDATE = 7          # coordinate FMA (2) + fraction (1) + lerp sub and FMA (3) + accumulate (1)
 FP32_LANES_PER_SM = 128       # FP32 FMA lanes per SM
 L2_FLUSH_BYTES = 256 << 20    # > 129 MB L2
+SMEM_UPDATES_PER_CLK = 16     # 128 B/clk/SM of shared-memory wavefronts / 8 B per update
 
 
 def _peaks():
@@ -198,6 +199,149 @@ def cpu_baseline():
                       f"({t1 - t0:.1f} s) + oracle R* on all {wl.N}x{wl.N} pixels ({t2 - t1:.1f} s)"}
 
 
+# ----------------------------------------------------------------------------------------------- other paths
+def _timed(fn, stream, flush, reps):
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    tot = 0.0
+    for _ in range(reps):
+        flush.zero_()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        fn()
+        e.record(stream)
+        torch.cuda.synchronize()
+        tot += s.elapsed_time(e)
+    return tot / reps
+
+
+def other_paths(plan, q, img, flush, stream, dev):
+    """Every other row of the path on its own workload, each timed with CUDA events."""
+    import numpy as np
+    import torch
+
+    from paper_1608_03589_gb300 import autograd as ag
+    from paper_1608_03589_gb300 import bp, synth
+
+    wl = synth.LARGE
+    out = {}
+
+    def guard(name, fn):
+        try:
+            out[name] = fn()
+        except Exception as exc:  # reported, never hidden
+            out[name] = {"unavailable": f"{type(exc).__name__}: {str(exc)[:160]}"}
+        torch.cuda.empty_cache()
+
+    # 2048^2 x 1800 slice: Fourier R*, R (direct and Fourier adjoint), BF16 storage
+    def fourier():
+        ms = _timed(lambda: plan.backproject_fourier(q, out=img), stream, flush, 10)
+        return {"ms": ms, "equiv_Gupdates_s": wl.updates / ms / 1e6}
+    guard("fourier_backprojection_2048", fourier)
+
+    def radon():
+        ms = _timed(lambda: plan.radon(img, out=q), stream, flush, 5)
+        return {"ms": ms, "Gupdates_s": wl.updates / ms / 1e6}
+    guard("radon_direct_2048", radon)
+
+    def radon_f():
+        ms = _timed(lambda: plan.radon(img, out=q, fourier=True), stream, flush, 10)
+        return {"ms": ms, "equiv_Gupdates_s": wl.updates / ms / 1e6}
+    guard("radon_fourier_2048", radon_f)
+
+    def bf16():
+        q16 = q.to(torch.bfloat16)
+        ms = _timed(lambda: plan.backproject(q16, out=img), stream, flush, 10)
+        return {"ms": ms, "Gupdates_s": wl.updates / ms / 1e6}
+    guard("direct_bf16_storage_2048", bf16)
+
+    # volume: 256 slices of 2048^2 from BF16 sinograms, one batched launch replayed from a CUDA graph
+    def volume():
+        V = synth.VOLUME
+        n = synth.VOLUME_SLICES
+        vol = torch.empty((n, V.n_theta, V.n_det), dtype=torch.bfloat16, device=dev)
+        chunk = 32
+        tmp = torch.empty((chunk, V.n_theta, V.n_det), dtype=torch.float32, device=dev)
+        for c0 in range(0, n, chunk):
+            for i in range(chunk):
+                e = synth.random_ellipses(V.n_ellipses, V.seed + c0 + i)
+                tmp[i] = synth.ellipse_sinogram_torch(e, V.theta, V.n_det, V.det_spacing, dev).float()
+            plan.filter(tmp, "shepp-logan", out=tmp)
+            vol[c0:c0 + chunk] = tmp.to(torch.bfloat16)
+        del tmp
+        imgs = torch.empty((n, V.N, V.N), dtype=torch.float32, device=dev)
+        plan.backproject(vol, out=imgs)
+        s2 = torch.cuda.Stream(dev)
+        s2.wait_stream(torch.cuda.current_stream(dev))
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=s2):
+            plan.backproject(vol, out=imgs)
+        ms = _timed(graph.replay, stream, flush, 3)
+        return {"slices": n, "ms": ms, "Gupdates_s": n * V.updates / ms / 1e6, "storage": "bf16",
+                "launch": "one batched launch replayed from a CUDA graph"}
+    guard("volume256_bf16_graph", volume)
+
+    # differentiable reconstruction: 8 x 1024^2, 1024 bins, 720 angles, 50 GD iterations on ||Rf-g||^2 + 1e-3 TV
+    def tv():
+        N, nd, nt, B = 1024, 1024, 720, 8
+        p2 = bp.Plan(N, nd, synth.uniform_theta(nt))
+        g = torch.stack([synth.ellipse_sinogram_torch(synth.random_ellipses(30, 4000 + i), synth.uniform_theta(nt),
+                                                      nd, 2.0 / nd, dev).float() for i in range(B)])
+        step = 1.0 / (2.0 * ag.lipschitz_estimate(p2, (B, N, N), dev) + 1e-3 * 8.0 / 1e-3)
+        ag.tv_reconstruct(g, p2, iters=2, step=step)
+        torch.cuda.synchronize()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        st = ag.tv_reconstruct(g, p2, iters=50, step=step)
+        e.record(stream)
+        torch.cuda.synchronize()
+        ms = s.elapsed_time(e)
+        p2.close()
+        return {"batch": B, "iterations": 50, "ms": ms, "ms_per_iteration": ms / 50,
+                "loss_first_last": [st.losses[0], st.losses[-1]],
+                "Gupdates_s": 2 * 50 * B * N * N * nt / ms / 1e6}
+    guard("tv_reconstruction_8x1024", tv)
+
+    # uneven batch: 64 slices, widths in {512..4096}, 360-3000 angles, FP16, one persistent launch
+    def mixed():
+        geo = synth.mixed_batch_geometries()
+        plans, sinos, imgs2 = [], [], []
+        upd = 0
+        for i, (N, nd, nt) in enumerate(geo):
+            th = synth.uniform_theta(nt)
+            pi = bp.Plan(N, nd, th)
+            e = synth.random_ellipses(30, 5000 + i)
+            g = synth.ellipse_sinogram_torch(e, th, nd, 2.0 / nd, dev).float()
+            sinos.append(pi.filter(g, "shepp-logan").to(torch.float16))
+            plans.append(pi)
+            imgs2.append(torch.empty((N, N), dtype=torch.float32, device=dev))
+            upd += N * N * nt
+        ms = _timed(lambda: bp.backproject_batched(plans, sinos, imgs2), stream, flush, 3)
+        for pi in plans:
+            pi.close()
+        return {"slices": len(geo), "updates": upd, "ms": ms, "Gupdates_s": upd / ms / 1e6, "storage": "fp16",
+                "launch": "one persistent launch (dynamic tile queue)"}
+    guard("mixed64_fp16_persistent", mixed)
+
+    # single 8192^2 slice, 8192 bins, 6000 angles: direct and Fourier
+    def big():
+        N, nd, nt = 8192, 8192, 6000
+        th = synth.uniform_theta(nt)
+        pb = bp.Plan(N, nd, th)
+        g = synth.ellipse_sinogram_torch(synth.random_ellipses(30, 5999), th, nd, 2.0 / nd, dev).float()
+        qb = pb.filter(g, "shepp-logan")
+        del g
+        ib = torch.empty((N, N), dtype=torch.float32, device=dev)
+        msd = _timed(lambda: pb.backproject(qb, out=ib), stream, flush, 2)
+        msf = _timed(lambda: pb.backproject_fourier(qb, out=ib), stream, flush, 2)
+        pb.close()
+        return {"direct_ms": msd, "direct_Gupdates_s": N * N * nt / msd / 1e6, "fourier_ms": msf,
+                "fourier_equiv_Gupdates_s": N * N * nt / msf / 1e6}
+    guard("slice8192_bins8192_ang6000", big)
+    return out
+
+
 # ----------------------------------------------------------------------------------------------- GPU arm
 def run_gpu(args, world, rank, local):
     import torch
@@ -292,38 +436,8 @@ def run_gpu(args, world, rank, local):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_t = float(t.item())
 
-    # other operators of the path on the same slice (reported, not part of the step)
-    extra = {}
-    def timed(fn, reps=10):
-        fn()
-        torch.cuda.synchronize()
-        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        tot = 0.0
-        for _ in range(reps):
-            flush.zero_()
-            s.record(stream)
-            fn()
-            e.record(stream)
-            torch.cuda.synchronize()
-            tot += s.elapsed_time(e)
-        return tot / reps
-    try:
-        ms = timed(lambda: plan.backproject_fourier(q, out=img))
-        extra["fourier_backprojection"] = {"ms": ms, "equiv_Gupdates_s": wl.updates / ms / 1e6}
-    except bp.BPError as exc:
-        extra["fourier_backprojection"] = {"unavailable": str(exc)[:120]}
-    try:
-        ms = timed(lambda: plan.radon(img, out=q))
-        extra["radon_direct"] = {"ms": ms, "Gupdates_s": wl.updates / ms / 1e6}
-    except bp.BPError as exc:
-        extra["radon_direct"] = {"unavailable": str(exc)[:120]}
-    try:
-        q16 = q.to(torch.bfloat16)
-        ms = timed(lambda: plan.backproject(q16, out=img))
-        extra["direct_bf16_storage"] = {"ms": ms, "Gupdates_s": wl.updates / ms / 1e6}
-    except bp.BPError as exc:
-        extra["direct_bf16_storage"] = {"unavailable": str(exc)[:120]}
-
+    # other operators and workloads of the path (reported under "paths", not part of the step)
+    extra = {} if args.no_paths else other_paths(plan, q, img, flush, stream, dev)
     if rank != 0:
         if dist:
             dist.barrier()
@@ -356,7 +470,13 @@ def run_gpu(args, world, rank, local):
                                    f"{sm_max_mhz:.0f} MHz (max SM clock)",
                      "traffic": (traffic["dram_bytes_per_launch"] if traffic else None),
                      "algorithmic_bytes": wl.n_theta * wl.n_det * 4 + wl.N * wl.N * 4,
-                     "kernel_ms": bp_avg_s * 1e3, "filter_ms": statistics.mean(filt_ms)},
+                     "kernel_ms": bp_avg_s * 1e3, "filter_ms": statistics.mean(filt_ms),
+                     "binding_limit": {
+                         "resource": "shared-memory wavefronts (one 8-byte table pair per update; 64-bit warp "
+                                     "load = 2 wavefronts; 1 wavefront/clk/SM)",
+                         "cap_Gupdates_s": SMEM_UPDATES_PER_CLK * props.multi_processor_count * sm_max_mhz / 1e3,
+                         "frac": wl.updates / bp_avg_s / (SMEM_UPDATES_PER_CLK * props.multi_processor_count *
+                                                          sm_max_mhz * 1e6)}},
         "e2e": {"value": wl.updates * world * n_e2e / e2e_t / 1e9, "unit": "Gupdates/s",
                 "h2d_bytes_per_step": g_host.nbytes, "d2h_bytes_per_step": wl.N * wl.N * 4,
                 "call": "bp_fbp_host (pinned host in/out)"},
@@ -384,6 +504,7 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the e2e and other-operator timings")
+    ap.add_argument("--no-paths", action="store_true", help="skip the other workloads under 'paths'")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     world, rank, local = _dist_init()
