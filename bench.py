@@ -216,7 +216,7 @@ def _timed(fn, stream, flush, reps):
     return tot / reps
 
 
-def other_paths(plan, q, img, flush, stream, dev):
+def other_paths(plan, q, img, flush, stream, dev, only=()):
     """Every other row of the path on its own workload, each timed with CUDA events."""
     import numpy as np
     import torch
@@ -228,6 +228,8 @@ def other_paths(plan, q, img, flush, stream, dev):
     out = {}
 
     def guard(name, fn):
+        if only and name not in only:
+            return
         try:
             out[name] = fn()
         except Exception as exc:  # reported, never hidden
@@ -379,6 +381,13 @@ def run_gpu(args, world, rank, local):
         step()
         flush.zero_()
     torch.cuda.synchronize()
+    if args.only:
+        only = tuple(x for x in args.only.split(",") if x)
+        res = other_paths(plan, q, img, flush, stream, dev, only)
+        if rank == 0:
+            print(json.dumps({"only": list(only), "paths": res}), flush=True)
+        plan.close()
+        return
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
            torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
@@ -437,7 +446,8 @@ def run_gpu(args, world, rank, local):
         e2e_t = float(t.item())
 
     # other operators and workloads of the path (reported under "paths", not part of the step)
-    extra = {} if args.no_paths else other_paths(plan, q, img, flush, stream, dev)
+    extra = {} if args.no_paths else other_paths(plan, q, img, flush, stream, dev,
+                                                 tuple(x for x in args.only.split(",") if x))
     if rank != 0:
         if dist:
             dist.barrier()
@@ -505,6 +515,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the e2e and other-operator timings")
     ap.add_argument("--no-paths", action="store_true", help="skip the other workloads under 'paths'")
+    ap.add_argument("--only", default="", help="comma-separated path names: run only these (profiling)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     world, rank, local = _dist_init()
