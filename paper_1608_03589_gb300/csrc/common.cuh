@@ -47,6 +47,7 @@ static_assert(sizeof(AngleParam) == 40, "AngleParam layout");
 struct FourierWork {
     int M = 0, logM = 0;        // oversampled grid side (power of two >= 2N)
     float beta = 0.f;           // Kaiser-Bessel shape for W = 6 and oversampling M/N
+    float rho = 0.f;            // radial sample spacing in grid cells
     float2 *spec = nullptr;     // [n_theta][P/2] sample values c_{k,m}
     float2 *grid = nullptr;     // [M][M] gridded spectrum, G[l_x][l_y]
     float2 *mid = nullptr;      // [N][M] after the first inverse-FFT pass

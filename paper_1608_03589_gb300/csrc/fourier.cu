@@ -36,9 +36,9 @@ namespace bp {
 namespace {
 
 constexpr int kW = 6;          // kernel width (grid cells)
-constexpr int kTS = 64;        // grid tile side
-constexpr int kMaxItem = 2048; // samples per gridding work item
-constexpr int kGridThreads = 256;
+constexpr int kTS = 32;        // grid tile side
+constexpr int kMaxItem = 1024; // samples per gridding work item
+constexpr int kGridThreads = 128;
 
 struct GridSeg {
     int k, m_lo, m_hi, pad;
@@ -113,48 +113,68 @@ fourier_spectra_kernel(const Tin *__restrict__ sino, float2 *__restrict__ spec, 
 }
 
 // ---------------------------------------------------------------------------------- (2) gridding
-// G[l_x][l_y] (l mod M).  One CTA per work item (segments of rays crossing one 64 x 64
-// tile); a warp takes one segment at a time, one sample per lane (consecutive samples of
-// the ray), and deposits the sample's 6 x 6 footprint cells that fall in the tile into the
-// shared-memory tile with shared atomics.
+// G[l_x][l_y] (l mod M).  One CTA per work item (segments of rays crossing one 32 x 32
+// tile).  Each warp accumulates into its own copy of the tile with plain read-modify-writes:
+// it takes one ray segment at a time, its lanes holding samples S apart on the ray, where
+// S * rho * max(|cos|, |sin|) > 1 so that the lanes' base cells differ along the ray's
+// dominant axis; for every footprint offset (tx, ty) the 32 lanes then touch 32 different
+// cells.  The warp copies are summed at the end; the tile's first item stores the sum, later
+// items add it with global reductions (second launch).
 __global__ void __launch_bounds__(kGridThreads, 3)
 grid_spread_kernel(const float2 *__restrict__ spec, const long long *__restrict__ ray, const GridSeg *__restrict__ segs,
                    const GridItem *__restrict__ items, float2 *__restrict__ grid, int M, int H, float beta,
-                   float delta2_over_M, int accumulate) {
-    __shared__ float2 acc[kTS][kTS + 1];
+                   float delta2_over_M, float rho, int accumulate) {
+    __shared__ float2 acc[kGridThreads / 32][kTS][kTS + 1];
     const GridItem it = items[blockIdx.x];
-    for (int i = threadIdx.x; i < kTS * kTS; i += kGridThreads) acc[i / kTS][i % kTS] = make_float2(0.f, 0.f);
-    __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float2(*mine)[kTS + 1] = acc[warp];
+    for (int i = lane; i < kTS * kTS; i += 32) mine[i / kTS][i % kTS] = make_float2(0.f, 0.f);
+    __syncwarp();
     const int Mmask = M - 1;
     for (int j = it.seg_begin + warp; j < it.seg_end; j += kGridThreads / 32) {
         const GridSeg sg = segs[j];
         const long long ax = ray[2 * sg.k], ay = ray[2 * sg.k + 1];
         const float2 *sk = spec + (long long)sg.k * H;
-        for (int m = sg.m_lo + lane; m <= sg.m_hi; m += 32) {
-            const long long zx = (long long)m * ax, zy = (long long)m * ay;
-            const int fx = (int)(zx >> 32), fy = (int)(zy >> 32);
-            const float rx = (float)(unsigned)(zx & 0xffffffffLL) * 2.3283064365386963e-10f;
-            const float ry = (float)(unsigned)(zy & 0xffffffffLL) * 2.3283064365386963e-10f;
-            float2 v = __ldg(sk + m);
-            float sn, cs;
-            sincospif(((float)(fx + fy) + (rx + ry)) * delta2_over_M, &sn, &cs);
-            v = cmul(v, make_float2(cs, sn));
-            float wy[kW];
+        const float step = fmaxf(fabsf((float)ax), fabsf((float)ay)) * 2.3283064365386963e-10f;  // rho max(|c|,|s|)
+        const int S = (int)floorf(1.0f / fmaxf(step, 1e-6f)) + 1;
+        for (int base = sg.m_lo; base <= sg.m_hi; base += 32 * S) {
+            for (int ph = 0; ph < S; ++ph) {
+                const int m = base + ph + S * lane;
+                const bool act = m <= sg.m_hi;
+                float wy[kW], wx[kW];
+                float2 v = make_float2(0.f, 0.f);
+                int fx = 0, fy = 0;
+                if (act) {
+                    const long long zx = (long long)m * ax, zy = (long long)m * ay;
+                    fx = (int)(zx >> 32);
+                    fy = (int)(zy >> 32);
+                    const float rx = (float)(unsigned)(zx & 0xffffffffLL) * 2.3283064365386963e-10f;
+                    const float ry = (float)(unsigned)(zy & 0xffffffffLL) * 2.3283064365386963e-10f;
+                    v = __ldg(sk + m);
+                    float sn, cs;
+                    sincospif(((float)(fx + fy) + (rx + ry)) * delta2_over_M, &sn, &cs);
+                    v = cmul(v, make_float2(cs, sn));
 #pragma unroll
-            for (int t = 0; t < kW; ++t) wy[t] = kb_weight((float)(t - 2) - ry, beta);
+                    for (int t = 0; t < kW; ++t) {
+                        wy[t] = kb_weight((float)(t - 2) - ry, beta);
+                        wx[t] = kb_weight((float)(t - 2) - rx, beta);
+                    }
+                }
 #pragma unroll
-            for (int tx = 0; tx < kW; ++tx) {
-                const int lx = ((fx - 2 + tx) & Mmask) - it.x0;
-                if (lx < 0 || lx >= kTS) continue;
-                const float wx = kb_weight((float)(tx - 2) - rx, beta);
-                const float2 vx = make_float2(wx * v.x, wx * v.y);
+                for (int tx = 0; tx < kW; ++tx) {
+                    const int lx = ((fx - 2 + tx) & Mmask) - it.x0;
+                    const bool inx = act && lx >= 0 && lx < kTS;
+                    const float2 vx = make_float2(wx[tx] * v.x, wx[tx] * v.y);
 #pragma unroll
-                for (int ty = 0; ty < kW; ++ty) {
-                    const int ly = ((fy - 2 + ty) & Mmask) - it.y0;
-                    if (ly >= 0 && ly < kTS) {
-                        atomicAdd(&acc[lx][ly].x, wy[ty] * vx.x);
-                        atomicAdd(&acc[lx][ly].y, wy[ty] * vx.y);
+                    for (int ty = 0; ty < kW; ++ty) {
+                        const int ly = ((fy - 2 + ty) & Mmask) - it.y0;
+                        if (inx && ly >= 0 && ly < kTS) {
+                            float2 c = mine[lx][ly];
+                            c.x = fmaf(wy[ty], vx.x, c.x);
+                            c.y = fmaf(wy[ty], vx.y, c.y);
+                            mine[lx][ly] = c;
+                        }
+                        __syncwarp();
                     }
                 }
             }
@@ -163,8 +183,13 @@ grid_spread_kernel(const float2 *__restrict__ spec, const long long *__restrict_
     __syncthreads();
     for (int i = threadIdx.x; i < kTS * kTS; i += kGridThreads) {
         const int lx = i / kTS, ly = i % kTS;
+        float2 v = acc[0][lx][ly];
+#pragma unroll
+        for (int w = 1; w < kGridThreads / 32; ++w) {
+            v.x += acc[w][lx][ly].x;
+            v.y += acc[w][lx][ly].y;
+        }
         float2 *dst = grid + (long long)(it.x0 + lx) * M + (it.y0 + ly);
-        const float2 v = acc[lx][ly];
         if (accumulate) {
             if (v.x != 0.f) atomicAdd(&dst->x, v.x);
             if (v.y != 0.f) atomicAdd(&dst->y, v.y);
@@ -490,6 +515,7 @@ bp_status ensure_fourier(bp_plan *p) {
     f.M = M;
     f.logM = ilog2(M);
     f.beta = (float)beta;
+    f.rho = (float)rho;
     f.n_segs = (int)sorted.size();
     f.n_owner = (int)owners.size();
     f.n_extra = (int)extras.size();
@@ -562,10 +588,11 @@ bp_status launch_fourier(bp_plan *p, const void *sino, bp_dtype dt, float *img, 
         if (s != BP_OK) return s;
         const GridItem *items = (const GridItem *)f.items;
         grid_spread_kernel<<<f.n_owner, kGridThreads, 0, st>>>(f.spec, f.ray, (const GridSeg *)f.segs, items, f.grid,
-                                                               M, H, f.beta, delta2, 0);
+                                                               M, H, f.beta, delta2, f.rho, 0);
         if (f.n_extra > 0)
             grid_spread_kernel<<<f.n_extra, kGridThreads, 0, st>>>(f.spec, f.ray, (const GridSeg *)f.segs,
-                                                                   items + f.n_owner, f.grid, M, H, f.beta, delta2, 1);
+                                                                   items + f.n_owner, f.grid, M, H, f.beta, delta2,
+                                                                   f.rho, 1);
         pass_y<<<M / R, nthr * groups, smemR, st>>>(f.grid, f.mid, f.deapod, f.twM, M, f.logM, N, R,
                                                            p->d_err);
         pass_x<<<(N + R - 1) / R, nthr * groups, smemR, st>>>(f.mid, img + (size_t)b * N * N, f.deapod,
