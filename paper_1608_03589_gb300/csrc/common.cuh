@@ -55,9 +55,10 @@ struct FourierWork {
     float *wk = nullptr;        // [n_theta] quadrature weights (float)
     float2 *twM = nullptr;      // M/2 twiddles exp(-2 pi i r / M)
     long long *ray = nullptr;   // [n_theta][2] rho cos, rho sin in 32.32 fixed point
-    void *segs = nullptr;       // gridding ray segments
-    void *items = nullptr;      // gridding work items (owners first, then extras)
-    int n_segs = 0, n_owner = 0, n_extra = 0;
+    void *sray = nullptr;       // rays sorted by angle (gather gridding)
+    float *sphi = nullptr;      // sorted ray angles in [0, 2 pi)
+    float2 *kbtab = nullptr;    // Kaiser-Bessel kernel table
+    float rmax = 0.f;           // largest sample radius (grid cells) plus a margin
     size_t bytes = 0;
 };
 

@@ -17,12 +17,14 @@
 // transform (deapodisation) removes the kernel.
 //
 // Kernels: (1) fourier_spectra: one CTA per projection pair, P-point FFT in shared memory,
-// the two half spectra scaled into c_{k,m};  (2) grid_spread: one CTA per work item of a
-// 32 x 32 grid tile (host-built list of ray segments that touch the tile, split so no
-// item exceeds a fixed sample count), warp groups of 6 lanes spread one sample each into
-// the shared-memory tile; the tile's first item stores it, later items add with global
-// reductions (second launch);  (3) ifft_pass_y / ifft_pass_x: M-point inverse FFTs of R
-// rows per CTA with output pruning to N points, transposed intermediate, fused
+// the two half spectra scaled into c'_{k,m} (quadrature weight, Hermitian factor, detector
+// and half-pixel phases);  (2) gridding as a gather: one thread per grid cell (a warp per
+// cell near the origin, where every ray passes) walks only the rays whose angle falls in the
+// cell's 6 x 6 footprint as seen from the origin (binary search in the sorted angles), and
+// on each ray only the samples inside the footprint; the separable kernel comes from an
+// FP64-built table with linear interpolation.  No atomics, deterministic, one store per
+// cell;  (3) ifft_pass_y / ifft_pass_x: M-point inverse FFTs of R rows per CTA (bulk
+// asynchronous loads) with output pruning to N points, transposed intermediate, fused
 // deapodisation and real part.
 #include <algorithm>
 #include <cmath>
@@ -35,47 +37,42 @@ namespace bp {
 
 namespace {
 
-constexpr int kW = 6;          // kernel width (grid cells)
-constexpr int kTS = 32;        // grid tile side
-constexpr int kMaxItem = 1024; // samples per gridding work item
-constexpr int kGridThreads = 128;
+constexpr int kW = 6;            // kernel width (grid cells)
+constexpr int kKB = 2048;         // kernel table intervals on [0, W/2]
+constexpr int kCore = 32;         // cells with max(|u_x|, |u_y|) < kCore are gathered by a warp each
 
-struct GridSeg {
-    int k, m_lo, m_hi, pad;
-};
-struct GridItem {
-    int x0, y0, seg_begin, seg_end;
+struct SortedRay {                // one ray, in increasing angle order
+    long long ax, ay;             // rho cos(phi), rho sin(phi) in 32.32 fixed point (grid cells per sample)
+    float sx, sy;                 // same, float
+    int k;                        // original projection index
+    int pad;
 };
 
-// Modified Bessel function I0 for x >= 0 by the polynomial approximations of Abramowitz &
-// Stegun, Handbook of Mathematical Functions, 9.8.1 (x <= 3.75) and 9.8.2 (x >= 3.75),
-// relative error below 2e-7.  Both branches are evaluated (no divergence).
-__device__ __forceinline__ float bessel_i0(float x) {
-    const float a = x * (1.0f / 3.75f);
-    const float a2 = a * a;
-    const float small =
-        1.0f + a2 * (3.5156229f + a2 * (3.0899424f + a2 * (1.2067492f + a2 * (0.2659732f + a2 * (0.0360768f +
-        a2 * 0.0045813f)))));
-    const float t = 3.75f / fmaxf(x, 3.75f);
-    const float p = 0.39894228f + t * (0.01328592f + t * (0.00225319f + t * (-0.00157565f + t * (0.00916281f +
-                    t * (-0.02057706f + t * (0.02635537f + t * (-0.01647633f + t * 0.00392377f)))))));
-    const float large = p * __expf(x) * rsqrtf(fmaxf(x, 3.75f));
-    return x < 3.75f ? small : large;
+// Kaiser-Bessel kernel phi(d) = I0(beta sqrt(1 - (2d/W)^2)) on |d| <= W/2 from the table
+// tab[i] = (phi(i h), phi((i+1) h) - phi(i h)), h = (W/2)/kKB, built in FP64 on the host.
+__device__ __forceinline__ float kb_tab(const float2 *__restrict__ tab, float d) {
+    const float x = fminf(fabsf(d) * (kKB / (0.5f * kW)), (float)kKB - 1e-3f);
+    const int i = (int)x;
+    const float2 v = __ldg(tab + i);
+    return fmaf(x - (float)i, v.y, v.x);
 }
 
-__device__ __forceinline__ float kb_weight(float t, float beta) {
-    // I0(beta sqrt(1 - (2t/W)^2)) for |t| <= W/2
-    const float a = t * (2.0f / kW);
-    const float r = fmaxf(0.f, 1.f - a * a);
-    return bessel_i0(beta * sqrtf(r));
+__device__ __forceinline__ float2 half_pixel_phase(const long long *__restrict__ r, int m, float delta2_over_M) {
+    const long long zx = (long long)m * r[0], zy = (long long)m * r[1];
+    const float rx = (float)(unsigned)(zx & 0xffffffffLL) * 2.3283064365386963e-10f;
+    const float ry = (float)(unsigned)(zy & 0xffffffffLL) * 2.3283064365386963e-10f;
+    float sn, cs;
+    sincospif(((float)((int)(zx >> 32) + (int)(zy >> 32)) + (rx + ry)) * delta2_over_M, &sn, &cs);
+    return make_float2(cs, sn);
 }
 
 // ---------------------------------------------------------------------------------- (1) spectra
 template <typename Tin, int E>
 __global__ void __launch_bounds__(1024, 1)
 fourier_spectra_kernel(const Tin *__restrict__ sino, float2 *__restrict__ spec, const float *__restrict__ wk,
-                       const float2 *__restrict__ tw, int n_theta, int n_det, int logP, float wuni) {
-    extern __shared__ __align__(16) float2 z[];
+                       const float2 *__restrict__ tw, int n_theta, int n_det, int logP, float wuni,
+                       const long long *__restrict__ ray, float delta2_over_M) {
+    extern __shared__ __align__(128) float2 z[];
     const int P = 1 << logP, H = P >> 1;
     const int k0 = 2 * blockIdx.x, k1 = k0 + 1;
     const bool has1 = k1 < n_theta;
@@ -104,99 +101,174 @@ fourier_spectra_kernel(const Tin *__restrict__ sino, float2 *__restrict__ spec, 
         const long long r = ((long long)m * (n_det - 1)) % twoP;
         float sn, cs;
         sincospif((float)r / (float)P, &sn, &cs);
-        const float2 ph = make_float2(cs, sn);
+        float2 pa = make_float2(cs, sn), pb = pa;
+        if (delta2_over_M != 0.f) {
+            // half-pixel phase exp(2 pi i delta (z_x + z_y) / M) of sample (k, m), z = m rho xi_k
+            pa = cmul(pa, half_pixel_phase(ray + 2 * k0, m, delta2_over_M));
+            if (has1) pb = cmul(pb, half_pixel_phase(ray + 2 * k1, m, delta2_over_M));
+        }
         const float f = (m == 0) ? 1.f : 2.f;
-        const float2 ca = cmul(A, ph), cb = cmul(B, ph);
+        const float2 ca = cmul(A, pa), cb = cmul(B, pb);
         spec[(long long)k0 * H + m] = make_float2(f * wa * ca.x, f * wa * ca.y);
         if (has1) spec[(long long)k1 * H + m] = make_float2(f * wb * cb.x, f * wb * cb.y);
     }
 }
 
 // ---------------------------------------------------------------------------------- (2) gridding
-// G[l_x][l_y] (l mod M).  One CTA per work item (segments of rays crossing one 32 x 32
-// tile).  Each warp accumulates into its own copy of the tile with plain read-modify-writes:
-// it takes one ray segment at a time, its lanes holding samples S apart on the ray, where
-// S * rho * max(|cos|, |sin|) > 1 so that the lanes' base cells differ along the ray's
-// dominant axis; for every footprint offset (tx, ty) the 32 lanes then touch 32 different
-// cells.  The warp copies are summed at the end; the tile's first item stores the sum, later
-// items add it with global reductions (second launch).
-__global__ void __launch_bounds__(kGridThreads, 3)
-grid_spread_kernel(const float2 *__restrict__ spec, const long long *__restrict__ ray, const GridSeg *__restrict__ segs,
-                   const GridItem *__restrict__ items, float2 *__restrict__ grid, int M, int H, float beta,
-                   float delta2_over_M, float rho, int accumulate) {
-    __shared__ float2 acc[kGridThreads / 32][kTS][kTS + 1];
-    const GridItem it = items[blockIdx.x];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    float2(*mine)[kTS + 1] = acc[warp];
-    for (int i = lane; i < kTS * kTS; i += 32) mine[i / kTS][i % kTS] = make_float2(0.f, 0.f);
-    __syncwarp();
-    const int Mmask = M - 1;
-    for (int j = it.seg_begin + warp; j < it.seg_end; j += kGridThreads / 32) {
-        const GridSeg sg = segs[j];
-        const long long ax = ray[2 * sg.k], ay = ray[2 * sg.k + 1];
-        const float2 *sk = spec + (long long)sg.k * H;
-        const float step = fmaxf(fabsf((float)ax), fabsf((float)ay)) * 2.3283064365386963e-10f;  // rho max(|c|,|s|)
-        const int S = (int)floorf(1.0f / fmaxf(step, 1e-6f)) + 1;
-        for (int base = sg.m_lo; base <= sg.m_hi; base += 32 * S) {
-            for (int ph = 0; ph < S; ++ph) {
-                const int m = base + ph + S * lane;
-                const bool act = m <= sg.m_hi;
-                float wy[kW], wx[kW];
-                float2 v = make_float2(0.f, 0.f);
-                int fx = 0, fy = 0;
-                if (act) {
-                    const long long zx = (long long)m * ax, zy = (long long)m * ay;
-                    fx = (int)(zx >> 32);
-                    fy = (int)(zy >> 32);
-                    const float rx = (float)(unsigned)(zx & 0xffffffffLL) * 2.3283064365386963e-10f;
-                    const float ry = (float)(unsigned)(zy & 0xffffffffLL) * 2.3283064365386963e-10f;
-                    v = __ldg(sk + m);
-                    float sn, cs;
-                    sincospif(((float)(fx + fy) + (rx + ry)) * delta2_over_M, &sn, &cs);
-                    v = cmul(v, make_float2(cs, sn));
+// Cell l (G[l_x][l_y], l mod M) sums c'_s phi(u_x - z_x) phi(u_y - z_y) over the samples z
+// with floor(z) in [u - 3, u + 2] per axis (the 6-cell footprint of the spreading form),
+// u ranging over the periodic images of the cell's centred coordinate.
+
+// Sorted-ray index range [lo, lo + count) (indices taken mod n) whose angle lies in the
+// angular extent of the box [ux - 3, ux + 3) x [uy - 3, uy + 3); all rays if the box holds
+// the origin.
+__device__ __forceinline__ void ray_range(const float *__restrict__ sphi, int n, float ux, float uy, int &lo,
+                                          int &count) {
+    const float x0 = ux - 3.f, x1 = ux + 3.f, y0 = uy - 3.f, y1 = uy + 3.f;
+    if (x0 <= 0.f && x1 >= 0.f && y0 <= 0.f && y1 >= 0.f) {
+        lo = 0;
+        count = n;
+        return;
+    }
+    const float twopi = 6.2831853071795865f;
+    const float pc = atan2f(uy, ux);
+    float dmin = 0.f, dmax = 0.f;
+    const float cx[4] = {x0, x1, x0, x1}, cy[4] = {y0, y0, y1, y1};
 #pragma unroll
-                    for (int t = 0; t < kW; ++t) {
-                        wy[t] = kb_weight((float)(t - 2) - ry, beta);
-                        wx[t] = kb_weight((float)(t - 2) - rx, beta);
-                    }
-                }
-#pragma unroll
-                for (int tx = 0; tx < kW; ++tx) {
-                    const int lx = ((fx - 2 + tx) & Mmask) - it.x0;
-                    const bool inx = act && lx >= 0 && lx < kTS;
-                    const float2 vx = make_float2(wx[tx] * v.x, wx[tx] * v.y);
-#pragma unroll
-                    for (int ty = 0; ty < kW; ++ty) {
-                        const int ly = ((fy - 2 + ty) & Mmask) - it.y0;
-                        if (inx && ly >= 0 && ly < kTS) {
-                            float2 c = mine[lx][ly];
-                            c.x = fmaf(wy[ty], vx.x, c.x);
-                            c.y = fmaf(wy[ty], vx.y, c.y);
-                            mine[lx][ly] = c;
-                        }
-                        __syncwarp();
-                    }
-                }
-            }
+    for (int i = 0; i < 4; ++i) {
+        float d = atan2f(cy[i], cx[i]) - pc;
+        d -= twopi * rintf(d * (1.f / twopi));
+        dmin = fminf(dmin, d);
+        dmax = fmaxf(dmax, d);
+    }
+    float a = pc + dmin - 1e-5f, b = pc + dmax + 1e-5f;
+    a -= twopi * floorf(a * (1.f / twopi));  // a in [0, 2 pi)
+    const float span = b - (pc + dmin - 1e-5f);
+    // first sorted angle >= a
+    int l = 0, h = n;
+    while (l < h) {
+        const int mid = (l + h) >> 1;
+        if (__ldg(sphi + mid) < a) l = mid + 1;
+        else h = mid;
+    }
+    // count of sorted angles in [a, a + span] (wrapping past 2 pi)
+    const float e = a + span;
+    int l2 = l, h2 = n;
+    const float e1 = fminf(e, twopi);
+    while (l2 < h2) {
+        const int mid = (l2 + h2) >> 1;
+        if (__ldg(sphi + mid) <= e1) l2 = mid + 1;
+        else h2 = mid;
+    }
+    count = l2 - l;
+    if (e > twopi) {
+        const float e2 = e - twopi;
+        int l3 = 0, h3 = n;
+        while (l3 < h3) {
+            const int mid = (l3 + h3) >> 1;
+            if (__ldg(sphi + mid) <= e2) l3 = mid + 1;
+            else h3 = mid;
+        }
+        count += min(l3, l);
+    }
+    lo = l;
+}
+
+// Sum of the contributions of sorted rays lo + j (j = j0, j0 + dj, ...) < lo + count to
+// the cell image (ux, uy).
+__device__ __forceinline__ float2 gather_rays(const float2 *__restrict__ spec, const SortedRay *__restrict__ sray,
+                                              const float2 *__restrict__ tab, int n, int H, int ux, int uy, int lo,
+                                              int count, int j0, int dj) {
+    float2 acc = make_float2(0.f, 0.f);
+    const float fx0 = (float)ux - 3.f, fx1 = (float)ux + 3.f, fy0 = (float)uy - 3.f, fy1 = (float)uy + 3.f;
+    for (int j = j0; j < count; j += dj) {
+        int i = lo + j;
+        if (i >= n) i -= n;
+        const SortedRay r = sray[i];
+        // samples m with z = m (sx, sy) inside the box (one spare sample each side)
+        float mlo = 0.f, mhi = (float)(H - 1);
+        if (r.sx > 0.f) { mlo = fmaxf(mlo, fx0 / r.sx); mhi = fminf(mhi, fx1 / r.sx); }
+        else if (r.sx < 0.f) { mlo = fmaxf(mlo, fx1 / r.sx); mhi = fminf(mhi, fx0 / r.sx); }
+        else if (fx0 > 0.f || fx1 <= 0.f) continue;
+        if (r.sy > 0.f) { mlo = fmaxf(mlo, fy0 / r.sy); mhi = fminf(mhi, fy1 / r.sy); }
+        else if (r.sy < 0.f) { mlo = fmaxf(mlo, fy1 / r.sy); mhi = fminf(mhi, fy0 / r.sy); }
+        else if (fy0 > 0.f || fy1 <= 0.f) continue;
+        const int m0 = max(0, (int)floorf(mlo) - 1), m1 = min(H - 1, (int)ceilf(mhi) + 1);
+        if (m0 > m1) continue;
+        const float2 *sk = spec + (long long)r.k * H;
+        long long zx = (long long)m0 * r.ax, zy = (long long)m0 * r.ay;
+        for (int m = m0; m <= m1; ++m, zx += r.ax, zy += r.ay) {
+            const int dx = ux - (int)(zx >> 32), dy = uy - (int)(zy >> 32);
+            if (dx < -2 || dx > 3 || dy < -2 || dy > 3) continue;
+            const float rx = (float)(unsigned)(zx & 0xffffffffLL) * 2.3283064365386963e-10f;
+            const float ry = (float)(unsigned)(zy & 0xffffffffLL) * 2.3283064365386963e-10f;
+            const float w = kb_tab(tab, (float)dx - rx) * kb_tab(tab, (float)dy - ry);
+            const float2 v = __ldg(sk + m);
+            acc.x = fmaf(w, v.x, acc.x);
+            acc.y = fmaf(w, v.y, acc.y);
         }
     }
-    __syncthreads();
-    for (int i = threadIdx.x; i < kTS * kTS; i += kGridThreads) {
-        const int lx = i / kTS, ly = i % kTS;
-        float2 v = acc[0][lx][ly];
-#pragma unroll
-        for (int w = 1; w < kGridThreads / 32; ++w) {
-            v.x += acc[w][lx][ly].x;
-            v.y += acc[w][lx][ly].y;
-        }
-        float2 *dst = grid + (long long)(it.x0 + lx) * M + (it.y0 + ly);
-        if (accumulate) {
-            if (v.x != 0.f) atomicAdd(&dst->x, v.x);
-            if (v.y != 0.f) atomicAdd(&dst->y, v.y);
-        } else {
-            *dst = v;
+    return acc;
+}
+
+// One thread per cell outside the core square; 32 x 8 cells per block (stores along l_y).
+__global__ void __launch_bounds__(256)
+grid_gather_kernel(const float2 *__restrict__ spec, const SortedRay *__restrict__ sray,
+                   const float *__restrict__ sphi, const float2 *__restrict__ tab, float2 *__restrict__ grid, int M,
+                   int H, int n, float rmax) {
+    const int ly = blockIdx.x * 32 + (threadIdx.x & 31);
+    const int lx = blockIdx.y * 8 + (threadIdx.x >> 5);
+    if (lx >= M || ly >= M) return;
+    const int cx = lx < M / 2 ? lx : lx - M, cy = ly < M / 2 ? ly : ly - M;
+    if (max(abs(cx), abs(cy)) < kCore) return;  // the core kernel owns this cell
+    float2 acc = make_float2(0.f, 0.f);
+    for (int a = -1; a <= 1; ++a) {
+        for (int b = -1; b <= 1; ++b) {
+            const int ux = cx + a * M, uy = cy + b * M;
+            // skip images whose box cannot reach the sample disk |z| <= rmax
+            const float qx = fmaxf(0.f, fmaxf((float)ux - 3.f, -3.f - (float)ux));
+            const float qy = fmaxf(0.f, fmaxf((float)uy - 3.f, -3.f - (float)uy));
+            if (qx * qx + qy * qy > rmax * rmax) continue;
+            int lo, count;
+            ray_range(sphi, n, (float)ux, (float)uy, lo, count);
+            const float2 v = gather_rays(spec, sray, tab, n, H, ux, uy, lo, count, 0, 1);
+            acc.x += v.x;
+            acc.y += v.y;
         }
     }
+    grid[(long long)lx * M + ly] = acc;
+}
+
+// One warp per core cell (max(|u_x|, |u_y|) < kCore): lanes split the rays, warp sum.
+__global__ void __launch_bounds__(256)
+grid_gather_core_kernel(const float2 *__restrict__ spec, const SortedRay *__restrict__ sray,
+                        const float *__restrict__ sphi, const float2 *__restrict__ tab, float2 *__restrict__ grid,
+                        int M, int H, int n, float rmax, int core) {
+    const int cell = blockIdx.x * 8 + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    const int side = 2 * core - 1;
+    if (cell >= side * side) return;
+    const int cx = cell / side - (core - 1), cy = cell % side - (core - 1);
+    float2 acc = make_float2(0.f, 0.f);
+    for (int a = -1; a <= 1; ++a) {
+        for (int b = -1; b <= 1; ++b) {
+            const int ux = cx + a * M, uy = cy + b * M;
+            const float qx = fmaxf(0.f, fmaxf((float)ux - 3.f, -3.f - (float)ux));
+            const float qy = fmaxf(0.f, fmaxf((float)uy - 3.f, -3.f - (float)uy));
+            if (qx * qx + qy * qy > rmax * rmax) continue;
+            int lo, count;
+            ray_range(sphi, n, (float)ux, (float)uy, lo, count);
+            const float2 v = gather_rays(spec, sray, tab, n, H, ux, uy, lo, count, lane, 32);
+            acc.x += v.x;
+            acc.y += v.y;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+    }
+    if (lane == 0) grid[(long long)(cx & (M - 1)) * M + (cy & (M - 1))] = acc;
 }
 
 // ---------------------------------------------------------------------------------- (3) inverse FFT passes
@@ -321,7 +393,7 @@ adj_fft_y_kernel(const float2 *__restrict__ T, float2 *__restrict__ grid, const 
 // factor (1/P)(m ? 2 : 1) exp(-i pi m (n_det-1)/P) exp(-2 pi i delta (z_x + z_y)/M) and dx^2/dt.
 __global__ void __launch_bounds__(256)
 adj_interp_kernel(const float2 *__restrict__ grid, float2 *__restrict__ spec, const long long *__restrict__ ray,
-                  int M, int H, int P, int n_det, float beta, float delta2_over_M, float scale,
+                  int M, int H, int P, int n_det, const float2 *__restrict__ tab, float delta2_over_M, float scale,
                   const float *__restrict__ wk) {
     const int k = blockIdx.y;
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
@@ -333,11 +405,11 @@ adj_interp_kernel(const float2 *__restrict__ grid, float2 *__restrict__ spec, co
     const int Mmask = M - 1;
     float wy[kW];
 #pragma unroll
-    for (int t = 0; t < kW; ++t) wy[t] = kb_weight((float)(t - 2) - ry, beta);
+    for (int t = 0; t < kW; ++t) wy[t] = kb_tab(tab, (float)(t - 2) - ry);
     float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
     for (int tx = 0; tx < kW; ++tx) {
-        const float wx = kb_weight((float)(tx - 2) - rx, beta);
+        const float wx = kb_tab(tab, (float)(tx - 2) - rx);
         const float2 *row = grid + (long long)((fx - 2 + tx) & Mmask) * M;
         float2 r = make_float2(0.f, 0.f);
 #pragma unroll
@@ -365,7 +437,7 @@ template <int E>
 __global__ void __launch_bounds__(1024, 1)
 adj_rows_kernel(const float2 *__restrict__ spec, float *__restrict__ sino, const float2 *__restrict__ tw,
                 int n_theta, int n_det, int logP) {
-    extern __shared__ __align__(16) float2 z[];
+    extern __shared__ __align__(128) float2 z[];
     const int P = 1 << logP, H = P >> 1;
     const int k0 = 2 * blockIdx.x, k1 = k0 + 1;
     const bool has1 = k1 < n_theta;
@@ -419,20 +491,22 @@ void free_fourier(bp_plan *p) {
     cudaFree(f.wk);
     cudaFree(f.twM);
     cudaFree(f.ray);
-    cudaFree(f.segs);
-    cudaFree(f.items);
+    cudaFree(f.sray);
+    cudaFree(f.sphi);
+    cudaFree(f.kbtab);
     f = FourierWork();
 }
 
-// Host (FP64) geometry of the gridding step: per-angle ray steps in 32.32 fixed point,
-// the ray segments that touch every 32 x 32 grid tile, and balanced work items.
+// Host (FP64) tables of the Fourier path: per-angle ray steps in 32.32 fixed point (original
+// order, for the spectra and the adjoint) and sorted by ray angle (for the gather), the
+// Kaiser-Bessel table and the deapodisation.
 bp_status ensure_fourier(bp_plan *p) {
     FourierWork &f = p->four;
     if (f.grid) return BP_OK;
     const int N = p->N, n_theta = p->n_theta, P = p->P, H = P / 2;
     int M = 1;
     while (M < 2 * N) M <<= 1;
-    M = std::max(M, kTS);
+    M = std::max(M, 2 * kCore);
     if ((size_t)M * sizeof(float2) > 128u * 1024u)
         return fail(BP_ERR_UNSUPPORTED, "Fourier path: N too large for the shared-memory FFT (N <= 8192)");
     if ((size_t)P * sizeof(float2) > 200u * 1024u)
@@ -442,63 +516,42 @@ bp_status ensure_fourier(bp_plan *p) {
     const double beta = M_PI * std::sqrt(std::max(b2, 1.0));
     const double rho = (double)M * p->dx / ((double)P * p->dt);
 
-    // ray steps and the sample walk that builds the tile segments
     std::vector<long long> ray(2 * (size_t)n_theta);
-    const int tiles1 = M / kTS;
-    std::vector<int> last(tiles1 * tiles1, -1);
-    std::vector<GridSeg> segs;
-    std::vector<int> seg_tile;
-    segs.reserve((size_t)n_theta * 4 * (H / kTS + 2));
+    std::vector<std::pair<double, int>> order(n_theta);
     for (int k = 0; k < n_theta; ++k) {
-        const long long ax = (long long)std::llround(std::ldexp(rho * std::cos(p->theta[k]), 32));
-        const long long ay = (long long)std::llround(std::ldexp(rho * std::sin(p->theta[k]), 32));
-        ray[2 * k] = ax;
-        ray[2 * k + 1] = ay;
-        for (int m = 0; m < H; ++m) {
-            const int fx = (int)(((long long)m * ax) >> 32), fy = (int)(((long long)m * ay) >> 32);
-            const int tx0 = ((fx - 2) & (M - 1)) / kTS, tx1 = ((fx + 3) & (M - 1)) / kTS;
-            const int ty0 = ((fy - 2) & (M - 1)) / kTS, ty1 = ((fy + 3) & (M - 1)) / kTS;
-            const int txs[2] = {tx0, tx1}, tys[2] = {ty0, ty1};
-            for (int a = 0; a < (tx0 == tx1 ? 1 : 2); ++a)
-                for (int b = 0; b < (ty0 == ty1 ? 1 : 2); ++b) {
-                    const int t = txs[a] * tiles1 + tys[b];
-                    const int li = last[t];
-                    if (li >= 0 && segs[li].k == k && segs[li].m_hi == m - 1) {
-                        segs[li].m_hi = m;
-                    } else {
-                        last[t] = (int)segs.size();
-                        segs.push_back(GridSeg{k, m, m, 0});
-                        seg_tile.push_back(t);
-                    }
-                }
-        }
+        const double c = std::cos(p->theta[k]), sn = std::sin(p->theta[k]);
+        ray[2 * k] = (long long)std::llround(std::ldexp(rho * c, 32));
+        ray[2 * k + 1] = (long long)std::llround(std::ldexp(rho * sn, 32));
+        double phi = std::atan2(sn, c);
+        if (phi < 0) phi += 2.0 * M_PI;
+        if (phi >= 2.0 * M_PI) phi = 0.0;
+        order[k] = {phi, k};
     }
-    // group segments by tile (counting sort), split each tile's list into items
-    const int ntiles = tiles1 * tiles1;
-    std::vector<int> cnt(ntiles + 1, 0);
-    for (int t : seg_tile) cnt[t + 1]++;
-    for (int t = 0; t < ntiles; ++t) cnt[t + 1] += cnt[t];
-    std::vector<GridSeg> sorted(segs.size());
-    {
-        std::vector<int> pos(cnt.begin(), cnt.end() - 1);
-        for (size_t i = 0; i < segs.size(); ++i) sorted[pos[seg_tile[i]]++] = segs[i];
+    std::sort(order.begin(), order.end());
+    std::vector<SortedRay> sray(n_theta);
+    std::vector<float> sphi(n_theta);
+    for (int i = 0; i < n_theta; ++i) {
+        const int k = order[i].second;
+        sray[i].ax = ray[2 * k];
+        sray[i].ay = ray[2 * k + 1];
+        sray[i].sx = (float)std::ldexp((double)ray[2 * k], -32);
+        sray[i].sy = (float)std::ldexp((double)ray[2 * k + 1], -32);
+        sray[i].k = k;
+        sray[i].pad = 0;
+        // the float angle must stay sorted and in [0, 2 pi) after rounding
+        sphi[i] = std::min((float)order[i].first, std::nextafter((float)(2.0 * M_PI), 0.f));
+        if (i > 0 && sphi[i] < sphi[i - 1]) sphi[i] = sphi[i - 1];
     }
-    std::vector<GridItem> owners, extras;
-    owners.reserve(ntiles);
-    for (int t = 0; t < ntiles; ++t) {
-        const int x0 = (t / tiles1) * kTS, y0 = (t % tiles1) * kTS;
-        int b = cnt[t], e = cnt[t + 1];
-        bool first = true;
-        do {
-            int s = b, load = 0;
-            while (s < e && (load == 0 || load + (sorted[s].m_hi - sorted[s].m_lo + 1) <= kMaxItem)) {
-                load += sorted[s].m_hi - sorted[s].m_lo + 1;
-                ++s;
-            }
-            (first ? owners : extras).push_back(GridItem{x0, y0, b, s});
-            first = false;
-            b = s;
-        } while (b < e);
+    // kernel table: (phi(i h), phi((i+1) h) - phi(i h)), h = (W/2) / kKB
+    std::vector<float2> tab(kKB + 1);
+    auto phi = [&](double d) {
+        const double a = 2.0 * d / kW;
+        return std::cyl_bessel_i(0.0, beta * std::sqrt(std::max(0.0, 1.0 - a * a)));
+    };
+    for (int i = 0; i <= kKB; ++i) {
+        const double d0 = 0.5 * kW * i / kKB, d1 = 0.5 * kW * (i + 1) / kKB;
+        const double v0 = phi(d0), v1 = i < kKB ? phi(d1) : v0;
+        tab[i] = make_float2((float)v0, (float)(v1 - v0));
     }
     // deapodisation 1 / phi_hat(i - floor(N/2)) (separable), weights, twiddles
     std::vector<float> deap(N), wk(n_theta);
@@ -506,19 +559,15 @@ bp_status ensure_fourier(bp_plan *p) {
     for (int k = 0; k < n_theta; ++k) wk[k] = (float)p->w[k];
     std::vector<float2> tw(M / 2);
     for (int i = 0; i < M / 2; ++i) {
-        const double a = -2.0 * M_PI * (double)i / (double)M;
-        tw[i] = make_float2((float)std::cos(a), (float)std::sin(a));
+        const double an = -2.0 * M_PI * (double)i / (double)M;
+        tw[i] = make_float2((float)std::cos(an), (float)std::sin(an));
     }
-    std::vector<GridItem> all(owners);
-    all.insert(all.end(), extras.begin(), extras.end());
 
     f.M = M;
     f.logM = ilog2(M);
     f.beta = (float)beta;
     f.rho = (float)rho;
-    f.n_segs = (int)sorted.size();
-    f.n_owner = (int)owners.size();
-    f.n_extra = (int)extras.size();
+    f.rmax = (float)(rho * (H - 1)) + 1.0f;
     cudaError_t e = cudaSuccess;
     auto alloc = [&](void **ptr, size_t bytes) {
         if (e == cudaSuccess) e = cudaMalloc(ptr, std::max<size_t>(bytes, 16));
@@ -531,15 +580,17 @@ bp_status ensure_fourier(bp_plan *p) {
     alloc((void **)&f.wk, sizeof(float) * n_theta);
     alloc((void **)&f.twM, sizeof(float2) * tw.size());
     alloc((void **)&f.ray, sizeof(long long) * ray.size());
-    alloc(&f.segs, sizeof(GridSeg) * sorted.size());
-    alloc(&f.items, sizeof(GridItem) * all.size());
+    alloc(&f.sray, sizeof(SortedRay) * sray.size());
+    alloc((void **)&f.sphi, sizeof(float) * sphi.size());
+    alloc((void **)&f.kbtab, sizeof(float2) * tab.size());
     if (e == cudaSuccess) e = cudaMemcpy(f.deapod, deap.data(), sizeof(float) * N, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(f.wk, wk.data(), sizeof(float) * n_theta, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(f.twM, tw.data(), sizeof(float2) * tw.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(f.ray, ray.data(), sizeof(long long) * ray.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && !sorted.empty())
-        e = cudaMemcpy(f.segs, sorted.data(), sizeof(GridSeg) * sorted.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(f.items, all.data(), sizeof(GridItem) * all.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(f.sray, sray.data(), sizeof(SortedRay) * sray.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(f.sphi, sphi.data(), sizeof(float) * sphi.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(f.kbtab, tab.data(), sizeof(float2) * tab.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         free_fourier(p);
         return cuda_fail(e, "Fourier workspace");
@@ -548,14 +599,14 @@ bp_status ensure_fourier(bp_plan *p) {
 }
 
 template <typename Tin>
-static bp_status spectra_t(bp_plan *p, const Tin *sino, cudaStream_t st, float wuni) {
+static bp_status spectra_t(bp_plan *p, const Tin *sino, cudaStream_t st, float wuni, float delta2) {
     const int logP = ilog2(p->P);
     const size_t smem = sizeof(float2) * p->P;
     const int threads = fft_threads(p->P);
     auto kern = fft_elems(p->P) == 16 ? fourier_spectra_kernel<Tin, 16> : fourier_spectra_kernel<Tin, 8>;
     BP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     kern<<<(p->n_theta + 1) / 2, threads, smem, st>>>(sino, p->four.spec, p->four.wk, p->d_twP, p->n_theta, p->n_det,
-                                                      logP, wuni);
+                                                      logP, wuni, p->four.ray, delta2);
     return BP_OK;
 }
 
@@ -581,18 +632,21 @@ bp_status launch_fourier(bp_plan *p, const void *sino, bp_dtype dt, float *img, 
     for (int b = 0; b < batch; ++b) {
         const char *sb = (const char *)sino + esz * (size_t)b * p->n_theta * p->n_det;
         switch (dt) {
-            case BP_F32: s = spectra_t(p, (const float *)sb, st, wuni); break;
-            case BP_BF16: s = spectra_t(p, (const __nv_bfloat16 *)sb, st, wuni); break;
-            case BP_F16: s = spectra_t(p, (const __half *)sb, st, wuni); break;
+            case BP_F32: s = spectra_t(p, (const float *)sb, st, wuni, delta2); break;
+            case BP_BF16: s = spectra_t(p, (const __nv_bfloat16 *)sb, st, wuni, delta2); break;
+            case BP_F16: s = spectra_t(p, (const __half *)sb, st, wuni, delta2); break;
         }
         if (s != BP_OK) return s;
-        const GridItem *items = (const GridItem *)f.items;
-        grid_spread_kernel<<<f.n_owner, kGridThreads, 0, st>>>(f.spec, f.ray, (const GridSeg *)f.segs, items, f.grid,
-                                                               M, H, f.beta, delta2, f.rho, 0);
-        if (f.n_extra > 0)
-            grid_spread_kernel<<<f.n_extra, kGridThreads, 0, st>>>(f.spec, f.ray, (const GridSeg *)f.segs,
-                                                                   items + f.n_owner, f.grid, M, H, f.beta, delta2,
-                                                                   f.rho, 1);
+        {
+            const dim3 g((M + 31) / 32, (M + 7) / 8);
+            grid_gather_kernel<<<g, 256, 0, st>>>(f.spec, (const SortedRay *)f.sray, f.sphi, f.kbtab, f.grid, M, H,
+                                                  p->n_theta, f.rmax);
+            const int core = std::min(kCore, M / 2);
+            const int side = 2 * core - 1;
+            grid_gather_core_kernel<<<(side * side + 7) / 8, 256, 0, st>>>(f.spec, (const SortedRay *)f.sray, f.sphi,
+                                                                           f.kbtab, f.grid, M, H, p->n_theta, f.rmax,
+                                                                           core);
+        }
         pass_y<<<M / R, nthr * groups, smemR, st>>>(f.grid, f.mid, f.deapod, f.twM, M, f.logM, N, R,
                                                            p->d_err);
         pass_x<<<(N + R - 1) / R, nthr * groups, smemR, st>>>(f.mid, img + (size_t)b * N * N, f.deapod,
@@ -627,7 +681,7 @@ bp_status launch_radon_fourier(bp_plan *p, const float *img, float *sino, int ba
                                                          N, R);
         ky<<<M / R, nthr * groups, smemR, st>>>(f.mid, f.grid, f.twM, M, f.logM, N, R);
         adj_interp_kernel<<<dim3((H + 255) / 256, p->n_theta), 256, 0, st>>>(f.grid, f.spec, f.ray, M, H, P, p->n_det,
-                                                                              f.beta, delta2, scale,
+                                                                              f.kbtab, delta2, scale,
                                                                               per_angle_w ? f.wk : nullptr);
         kr<<<(p->n_theta + 1) / 2, fft_threads(P), sizeof(float2) * P, st>>>(
             f.spec, sino + (size_t)b * p->n_theta * p->n_det, p->d_twP, p->n_theta, p->n_det, ilog2(P));
