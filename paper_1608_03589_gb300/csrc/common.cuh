@@ -43,6 +43,13 @@ struct AngleParam {
 };
 static_assert(sizeof(AngleParam) == 40, "AngleParam layout");
 
+// Lookup into the ray angles sorted in [0, 2 pi).
+struct RayIndex {
+    int n = 0;
+    int uniform = 0;              // angles phi_i = phi0 + i dphi exactly (to 1e-9)
+    float phi0 = 0.f, dphi = 0.f;
+};
+
 // Fourier-path workspace and gridding geometry (allocated on first use).
 struct FourierWork {
     int M = 0, logM = 0;        // oversampled grid side (power of two >= 2N)
@@ -59,6 +66,7 @@ struct FourierWork {
     float *sphi = nullptr;      // sorted ray angles in [0, 2 pi)
     float2 *kbtab = nullptr;    // Kaiser-Bessel kernel table
     float rmax = 0.f;           // largest sample radius (grid cells) plus a margin
+    RayIndex ri;                // sorted-angle lookup (gather gridding)
     size_t bytes = 0;
 };
 

@@ -43,7 +43,7 @@ constexpr int kCore = 32;         // cells with max(|u_x|, |u_y|) < kCore are ga
 
 struct SortedRay {                // one ray, in increasing angle order
     long long ax, ay;             // rho cos(phi), rho sin(phi) in 32.32 fixed point (grid cells per sample)
-    float sx, sy;                 // same, float
+    float isx, isy;               // 1 / (rho cos), 1 / (rho sin) (infinite for a zero component)
     int k;                        // original projection index
     int pad;
 };
@@ -119,59 +119,37 @@ fourier_spectra_kernel(const Tin *__restrict__ sino, float2 *__restrict__ spec, 
 // with floor(z) in [u - 3, u + 2] per axis (the 6-cell footprint of the spreading form),
 // u ranging over the periodic images of the cell's centred coordinate.
 
-// Sorted-ray index range [lo, lo + count) (indices taken mod n) whose angle lies in the
-// angular extent of the box [ux - 3, ux + 3) x [uy - 3, uy + 3); all rays if the box holds
-// the origin.
-__device__ __forceinline__ void ray_range(const float *__restrict__ sphi, int n, float ux, float uy, int &lo,
-                                          int &count) {
-    const float x0 = ux - 3.f, x1 = ux + 3.f, y0 = uy - 3.f, y1 = uy + 3.f;
-    if (x0 <= 0.f && x1 >= 0.f && y0 <= 0.f && y1 >= 0.f) {
-        lo = 0;
-        count = n;
-        return;
-    }
-    const float twopi = 6.2831853071795865f;
-    const float pc = atan2f(uy, ux);
-    float dmin = 0.f, dmax = 0.f;
-    const float cx[4] = {x0, x1, x0, x1}, cy[4] = {y0, y0, y1, y1};
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        float d = atan2f(cy[i], cx[i]) - pc;
-        d -= twopi * rintf(d * (1.f / twopi));
-        dmin = fminf(dmin, d);
-        dmax = fmaxf(dmax, d);
-    }
-    float a = pc + dmin - 1e-5f, b = pc + dmax + 1e-5f;
-    a -= twopi * floorf(a * (1.f / twopi));  // a in [0, 2 pi)
-    const float span = b - (pc + dmin - 1e-5f);
-    // first sorted angle >= a
-    int l = 0, h = n;
+// Sorted-ray index range [lo, lo + count) (indices taken mod n) whose angle lies within the
+// angular window of the cell's footprint box [ux - 3, ux + 3) x [uy - 3, uy + 3): the disc of
+// radius 3 sqrt(2) around u seen from the origin; all rays if that disc holds the origin.
+__device__ __forceinline__ int first_at_least(const float *__restrict__ sphi, const RayIndex &ri, float a) {
+    if (ri.uniform) return min(ri.n, max(0, (int)ceilf((a - ri.phi0) / ri.dphi - 1e-4f)));
+    int l = 0, h = ri.n;
     while (l < h) {
         const int mid = (l + h) >> 1;
         if (__ldg(sphi + mid) < a) l = mid + 1;
         else h = mid;
     }
-    // count of sorted angles in [a, a + span] (wrapping past 2 pi)
-    const float e = a + span;
-    int l2 = l, h2 = n;
-    const float e1 = fminf(e, twopi);
-    while (l2 < h2) {
-        const int mid = (l2 + h2) >> 1;
-        if (__ldg(sphi + mid) <= e1) l2 = mid + 1;
-        else h2 = mid;
+    return l;
+}
+
+__device__ __forceinline__ void ray_range(const float *__restrict__ sphi, const RayIndex &ri, float ux, float uy,
+                                          int &lo, int &count) {
+    const float R = 4.2427f;  // 3 sqrt(2) plus rounding margin
+    const float r2 = ux * ux + uy * uy;
+    if (r2 <= R * R) {
+        lo = 0;
+        count = ri.n;
+        return;
     }
-    count = l2 - l;
-    if (e > twopi) {
-        const float e2 = e - twopi;
-        int l3 = 0, h3 = n;
-        while (l3 < h3) {
-            const int mid = (l3 + h3) >> 1;
-            if (__ldg(sphi + mid) <= e2) l3 = mid + 1;
-            else h3 = mid;
-        }
-        count += min(l3, l);
-    }
-    lo = l;
+    const float twopi = 6.2831853071795865f;
+    const float half = asinf(R * rsqrtf(r2)) + 1e-4f;
+    float a = atan2f(uy, ux) - half;
+    a -= twopi * floorf(a * (1.f / twopi));  // [0, 2 pi)
+    const float e = a + 2.f * half;
+    lo = first_at_least(sphi, ri, a);
+    count = first_at_least(sphi, ri, fminf(e, twopi) + 1e-7f) - lo;
+    if (e > twopi) count += min(lo, first_at_least(sphi, ri, e - twopi + 1e-7f));
 }
 
 // Sum of the contributions of sorted rays lo + j (j = j0, j0 + dj, ...) < lo + count to
@@ -186,24 +164,20 @@ __device__ __forceinline__ float2 gather_rays(const float2 *__restrict__ spec, c
         if (i >= n) i -= n;
         const SortedRay r = sray[i];
         // samples m with z = m (sx, sy) inside the box (one spare sample each side)
-        float mlo = 0.f, mhi = (float)(H - 1);
-        if (r.sx > 0.f) { mlo = fmaxf(mlo, fx0 / r.sx); mhi = fminf(mhi, fx1 / r.sx); }
-        else if (r.sx < 0.f) { mlo = fmaxf(mlo, fx1 / r.sx); mhi = fminf(mhi, fx0 / r.sx); }
-        else if (fx0 > 0.f || fx1 <= 0.f) continue;
-        if (r.sy > 0.f) { mlo = fmaxf(mlo, fy0 / r.sy); mhi = fminf(mhi, fy1 / r.sy); }
-        else if (r.sy < 0.f) { mlo = fmaxf(mlo, fy1 / r.sy); mhi = fminf(mhi, fy0 / r.sy); }
-        else if (fy0 > 0.f || fy1 <= 0.f) continue;
-        const int m0 = max(0, (int)floorf(mlo) - 1), m1 = min(H - 1, (int)ceilf(mhi) + 1);
-        if (m0 > m1) continue;
+        const float ax0 = fx0 * r.isx, ax1 = fx1 * r.isx, ay0 = fy0 * r.isy, ay1 = fy1 * r.isy;
+        float mlo = fmaxf(0.f, fmaxf(fminf(ax0, ax1), fminf(ay0, ay1)));
+        float mhi = fminf((float)(H - 1), fminf(fmaxf(ax0, ax1), fmaxf(ay0, ay1)));
+        if (!(mlo <= mhi + 2.f)) continue;  // also rejects NaN (0 * inf on a zero component)
+        const int m0 = max(0, (int)mlo - 1), m1 = min(H - 1, (int)mhi + 1);
         const float2 *sk = spec + (long long)r.k * H;
         long long zx = (long long)m0 * r.ax, zy = (long long)m0 * r.ay;
         for (int m = m0; m <= m1; ++m, zx += r.ax, zy += r.ay) {
+            const float2 v = __ldg(sk + m);
             const int dx = ux - (int)(zx >> 32), dy = uy - (int)(zy >> 32);
             if (dx < -2 || dx > 3 || dy < -2 || dy > 3) continue;
             const float rx = (float)(unsigned)(zx & 0xffffffffLL) * 2.3283064365386963e-10f;
             const float ry = (float)(unsigned)(zy & 0xffffffffLL) * 2.3283064365386963e-10f;
             const float w = kb_tab(tab, (float)dx - rx) * kb_tab(tab, (float)dy - ry);
-            const float2 v = __ldg(sk + m);
             acc.x = fmaf(w, v.x, acc.x);
             acc.y = fmaf(w, v.y, acc.y);
         }
@@ -215,23 +189,23 @@ __device__ __forceinline__ float2 gather_rays(const float2 *__restrict__ spec, c
 __global__ void __launch_bounds__(256)
 grid_gather_kernel(const float2 *__restrict__ spec, const SortedRay *__restrict__ sray,
                    const float *__restrict__ sphi, const float2 *__restrict__ tab, float2 *__restrict__ grid, int M,
-                   int H, int n, float rmax) {
+                   int H, RayIndex ri, float rmax, int amax) {
     const int ly = blockIdx.x * 32 + (threadIdx.x & 31);
     const int lx = blockIdx.y * 8 + (threadIdx.x >> 5);
     if (lx >= M || ly >= M) return;
     const int cx = lx < M / 2 ? lx : lx - M, cy = ly < M / 2 ? ly : ly - M;
     if (max(abs(cx), abs(cy)) < kCore) return;  // the core kernel owns this cell
     float2 acc = make_float2(0.f, 0.f);
-    for (int a = -1; a <= 1; ++a) {
-        for (int b = -1; b <= 1; ++b) {
+    for (int a = -amax; a <= amax; ++a) {
+        for (int b = -amax; b <= amax; ++b) {
             const int ux = cx + a * M, uy = cy + b * M;
             // skip images whose box cannot reach the sample disk |z| <= rmax
             const float qx = fmaxf(0.f, fmaxf((float)ux - 3.f, -3.f - (float)ux));
             const float qy = fmaxf(0.f, fmaxf((float)uy - 3.f, -3.f - (float)uy));
             if (qx * qx + qy * qy > rmax * rmax) continue;
             int lo, count;
-            ray_range(sphi, n, (float)ux, (float)uy, lo, count);
-            const float2 v = gather_rays(spec, sray, tab, n, H, ux, uy, lo, count, 0, 1);
+            ray_range(sphi, ri, (float)ux, (float)uy, lo, count);
+            const float2 v = gather_rays(spec, sray, tab, ri.n, H, ux, uy, lo, count, 0, 1);
             acc.x += v.x;
             acc.y += v.y;
         }
@@ -243,22 +217,22 @@ grid_gather_kernel(const float2 *__restrict__ spec, const SortedRay *__restrict_
 __global__ void __launch_bounds__(256)
 grid_gather_core_kernel(const float2 *__restrict__ spec, const SortedRay *__restrict__ sray,
                         const float *__restrict__ sphi, const float2 *__restrict__ tab, float2 *__restrict__ grid,
-                        int M, int H, int n, float rmax, int core) {
+                        int M, int H, RayIndex ri, float rmax, int amax, int core) {
     const int cell = blockIdx.x * 8 + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     const int side = 2 * core - 1;
     if (cell >= side * side) return;
     const int cx = cell / side - (core - 1), cy = cell % side - (core - 1);
     float2 acc = make_float2(0.f, 0.f);
-    for (int a = -1; a <= 1; ++a) {
-        for (int b = -1; b <= 1; ++b) {
+    for (int a = -amax; a <= amax; ++a) {
+        for (int b = -amax; b <= amax; ++b) {
             const int ux = cx + a * M, uy = cy + b * M;
             const float qx = fmaxf(0.f, fmaxf((float)ux - 3.f, -3.f - (float)ux));
             const float qy = fmaxf(0.f, fmaxf((float)uy - 3.f, -3.f - (float)uy));
             if (qx * qx + qy * qy > rmax * rmax) continue;
             int lo, count;
-            ray_range(sphi, n, (float)ux, (float)uy, lo, count);
-            const float2 v = gather_rays(spec, sray, tab, n, H, ux, uy, lo, count, lane, 32);
+            ray_range(sphi, ri, (float)ux, (float)uy, lo, count);
+            const float2 v = gather_rays(spec, sray, tab, ri.n, H, ux, uy, lo, count, lane, 32);
             acc.x += v.x;
             acc.y += v.y;
         }
@@ -534,13 +508,28 @@ bp_status ensure_fourier(bp_plan *p) {
         const int k = order[i].second;
         sray[i].ax = ray[2 * k];
         sray[i].ay = ray[2 * k + 1];
-        sray[i].sx = (float)std::ldexp((double)ray[2 * k], -32);
-        sray[i].sy = (float)std::ldexp((double)ray[2 * k + 1], -32);
+        const double sxd = std::ldexp((double)ray[2 * k], -32), syd = std::ldexp((double)ray[2 * k + 1], -32);
+        sray[i].isx = sxd != 0.0 ? (float)(1.0 / sxd) : INFINITY;
+        sray[i].isy = syd != 0.0 ? (float)(1.0 / syd) : INFINITY;
         sray[i].k = k;
         sray[i].pad = 0;
         // the float angle must stay sorted and in [0, 2 pi) after rounding
         sphi[i] = std::min((float)order[i].first, std::nextafter((float)(2.0 * M_PI), 0.f));
         if (i > 0 && sphi[i] < sphi[i - 1]) sphi[i] = sphi[i - 1];
+    }
+    // uniform spacing of the sorted angles gives an O(1) index lookup
+    f.ri.n = n_theta;
+    f.ri.uniform = 0;
+    if (n_theta > 1) {
+        const double d = (order[n_theta - 1].first - order[0].first) / (n_theta - 1);
+        bool uni = d > 0;
+        for (int i = 0; i < n_theta && uni; ++i)
+            uni = std::fabs(order[i].first - (order[0].first + i * d)) < 1e-9;
+        if (uni) {
+            f.ri.uniform = 1;
+            f.ri.phi0 = (float)order[0].first;
+            f.ri.dphi = (float)d;
+        }
     }
     // kernel table: (phi(i h), phi((i+1) h) - phi(i h)), h = (W/2) / kKB
     std::vector<float2> tab(kKB + 1);
@@ -639,12 +628,13 @@ bp_status launch_fourier(bp_plan *p, const void *sino, bp_dtype dt, float *img, 
         if (s != BP_OK) return s;
         {
             const dim3 g((M + 31) / 32, (M + 7) / 8);
+            const int amax = (int)std::ceil((f.rmax + 4.25 + M / 2) / M);
             grid_gather_kernel<<<g, 256, 0, st>>>(f.spec, (const SortedRay *)f.sray, f.sphi, f.kbtab, f.grid, M, H,
-                                                  p->n_theta, f.rmax);
+                                                  f.ri, f.rmax, amax);
             const int core = std::min(kCore, M / 2);
             const int side = 2 * core - 1;
             grid_gather_core_kernel<<<(side * side + 7) / 8, 256, 0, st>>>(f.spec, (const SortedRay *)f.sray, f.sphi,
-                                                                           f.kbtab, f.grid, M, H, p->n_theta, f.rmax,
+                                                                           f.kbtab, f.grid, M, H, f.ri, f.rmax, amax,
                                                                            core);
         }
         pass_y<<<M / R, nthr * groups, smemR, st>>>(f.grid, f.mid, f.deapod, f.twM, M, f.logM, N, R,
