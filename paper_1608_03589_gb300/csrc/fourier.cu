@@ -185,99 +185,32 @@ __device__ __forceinline__ float2 gather_rays(const float2 *__restrict__ spec, c
     return acc;
 }
 
-// Outside the core square: one thread per run of 8 cells along x (u_x0 .. u_x0 + 7, fixed
-// u_y); lanes along y so the 8 stores of a warp are contiguous.  The run shares the angular
-// window, the ray setup and, per sample, the y-weight; x offsets advance in float from an
-// exact fixed-point base at the first sample of each ray.
-constexpr int kRun = 8;
-
-__device__ __forceinline__ void gather_run(const float2 *__restrict__ spec, const SortedRay *__restrict__ sray,
-                                           const float *__restrict__ sphi, const float2 *__restrict__ tab,
-                                           const RayIndex &ri, int H, int ux0, int uy, float2 (&acc)[kRun]) {
-    // angular window of the run's box [ux0 - 3, ux0 + kRun + 2) x [uy - 3, uy + 3)
-    const float cxm = (float)ux0 + 0.5f * (kRun - 1), cym = (float)uy;
-    const float R = 7.2f;  // circumscribed radius of the run's box plus margin
-    const float r2 = cxm * cxm + cym * cym;
-    int lo, count;
-    if (r2 <= R * R) {
-        lo = 0;
-        count = ri.n;
-    } else {
-        const float twopi = 6.2831853071795865f;
-        const float half = asinf(R * rsqrtf(r2)) + 1e-4f;
-        float a = atan2f(cym, cxm) - half;
-        a -= twopi * floorf(a * (1.f / twopi));
-        const float e = a + 2.f * half;
-        lo = first_at_least(sphi, ri, a);
-        count = first_at_least(sphi, ri, fminf(e, twopi) + 1e-7f) - lo;
-        if (e > twopi) count += min(lo, first_at_least(sphi, ri, e - twopi + 1e-7f));
-    }
-    const float fx0 = (float)ux0 - 3.f, fx1 = (float)(ux0 + kRun) + 2.f, fy0 = (float)uy - 3.f, fy1 = (float)uy + 3.f;
-    for (int j = 0; j < count; ++j) {
-        int i = lo + j;
-        if (i >= ri.n) i -= ri.n;
-        const SortedRay r = sray[i];
-        const float ax0 = fx0 * r.isx, ax1 = fx1 * r.isx, ay0 = fy0 * r.isy, ay1 = fy1 * r.isy;
-        const float mlo = fmaxf(0.f, fmaxf(fminf(ax0, ax1), fminf(ay0, ay1)));
-        const float mhi = fminf((float)(H - 1), fminf(fmaxf(ax0, ax1), fmaxf(ay0, ay1)));
-        if (!(mlo <= mhi + 2.f)) continue;
-        const int m0 = max(0, (int)mlo - 1), m1 = min(H - 1, (int)mhi + 1);
-        // exact offsets at m0: d = u - z with z = m0 (ax, ay) 2^-32
-        const long long zx = (long long)m0 * r.ax, zy = (long long)m0 * r.ay;
-        const float dx0 = (float)(ux0 - (int)(zx >> 32)) - (float)(unsigned)(zx & 0xffffffffLL) * 2.3283064365386963e-10f;
-        const float dy0 = (float)(uy - (int)(zy >> 32)) - (float)(unsigned)(zy & 0xffffffffLL) * 2.3283064365386963e-10f;
-        const float sx = (float)((double)r.ax * 2.3283064365386963e-10), sy = (float)((double)r.ay * 2.3283064365386963e-10);
-        const float2 *sk = spec + (long long)r.k * H;
-        for (int m = m0; m <= m1; ++m) {
-            const float t = (float)(m - m0);
-            const float dy = fmaf(-t, sy, dy0);
-            if (!(dy > -3.f && dy <= 3.f)) continue;
-            const float dxb = fmaf(-t, sx, dx0);  // offset of cell ux0; cell ux0 + i has dxb + i
-            if (!(dxb + (float)(kRun - 1) > -3.f && dxb <= 3.f)) continue;
-            const float2 v = __ldg(sk + m);
-            const float wy = kb_tab(tab, dy);
-            const float2 wv = make_float2(wy * v.x, wy * v.y);
-#pragma unroll
-            for (int c = 0; c < kRun; ++c) {
-                const float dx = dxb + (float)c;
-                if (dx > -3.f && dx <= 3.f) {
-                    const float wx = kb_tab(tab, dx);
-                    acc[c].x = fmaf(wx, wv.x, acc[c].x);
-                    acc[c].y = fmaf(wx, wv.y, acc[c].y);
-                }
-            }
-        }
-    }
-}
-
+// One thread per cell outside the core square; 32 x 8 cells per block (stores along l_y).
 __global__ void __launch_bounds__(256)
 grid_gather_kernel(const float2 *__restrict__ spec, const SortedRay *__restrict__ sray,
                    const float *__restrict__ sphi, const float2 *__restrict__ tab, float2 *__restrict__ grid, int M,
-                   int H, RayIndex ri, float rmax, int amax, int core) {
+                   int H, RayIndex ri, float rmax, int amax) {
     const int ly = blockIdx.x * 32 + (threadIdx.x & 31);
-    const int lx0 = (blockIdx.y * 8 + (threadIdx.x >> 5)) * kRun;
-    if (lx0 >= M || ly >= M) return;
-    const int cy = ly < M / 2 ? ly : ly - M;
-    // centred x of the run (a run never straddles M/2: kRun divides M/2)
-    const int cx0 = lx0 < M / 2 ? lx0 : lx0 - M;
-    float2 acc[kRun];
-#pragma unroll
-    for (int c = 0; c < kRun; ++c) acc[c] = make_float2(0.f, 0.f);
+    const int lx = blockIdx.y * 8 + (threadIdx.x >> 5);
+    if (lx >= M || ly >= M) return;
+    const int cx = lx < M / 2 ? lx : lx - M, cy = ly < M / 2 ? ly : ly - M;
+    if (max(abs(cx), abs(cy)) < kCore) return;  // the core kernel owns this cell
+    float2 acc = make_float2(0.f, 0.f);
     for (int a = -amax; a <= amax; ++a) {
         for (int b = -amax; b <= amax; ++b) {
-            const int ux0 = cx0 + a * M, uy = cy + b * M;
-            const float qx = fmaxf(0.f, fmaxf((float)ux0 - 3.f, -3.f - (float)(ux0 + kRun - 1)));
+            const int ux = cx + a * M, uy = cy + b * M;
+            // skip images whose box cannot reach the sample disk |z| <= rmax
+            const float qx = fmaxf(0.f, fmaxf((float)ux - 3.f, -3.f - (float)ux));
             const float qy = fmaxf(0.f, fmaxf((float)uy - 3.f, -3.f - (float)uy));
             if (qx * qx + qy * qy > rmax * rmax) continue;
-            gather_run(spec, sray, sphi, tab, ri, H, ux0, uy, acc);
+            int lo, count;
+            ray_range(sphi, ri, (float)ux, (float)uy, lo, count);
+            const float2 v = gather_rays(spec, sray, tab, ri.n, H, ux, uy, lo, count, 0, 1);
+            acc.x += v.x;
+            acc.y += v.y;
         }
     }
-#pragma unroll
-    for (int c = 0; c < kRun; ++c) {
-        const int cx = cx0 + c;
-        if (max(abs(cx), abs(cy)) < core) continue;  // the core kernel owns this cell
-        grid[(long long)(lx0 + c) * M + ly] = acc[c];
-    }
+    grid[(long long)lx * M + ly] = acc;
 }
 
 // One warp per core cell (max(|u_x|, |u_y|) < kCore): lanes split the rays, warp sum.
@@ -694,11 +627,11 @@ bp_status launch_fourier(bp_plan *p, const void *sino, bp_dtype dt, float *img, 
         }
         if (s != BP_OK) return s;
         {
+            const dim3 g((M + 31) / 32, (M + 7) / 8);
             const int amax = (int)std::ceil((f.rmax + 4.25 + M / 2) / M);
-            const int core = std::min(kCore, M / 2);
-            const dim3 g((M + 31) / 32, (M / kRun + 7) / 8);
             grid_gather_kernel<<<g, 256, 0, st>>>(f.spec, (const SortedRay *)f.sray, f.sphi, f.kbtab, f.grid, M, H,
-                                                  f.ri, f.rmax, amax, core);
+                                                  f.ri, f.rmax, amax);
+            const int core = std::min(kCore, M / 2);
             const int side = 2 * core - 1;
             grid_gather_core_kernel<<<(side * side + 7) / 8, 256, 0, st>>>(f.spec, (const SortedRay *)f.sray, f.sphi,
                                                                            f.kbtab, f.grid, M, H, f.ri, f.rmax, amax,
