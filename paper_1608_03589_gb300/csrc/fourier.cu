@@ -170,14 +170,18 @@ __device__ __forceinline__ float2 gather_rays(const float2 *__restrict__ spec, c
         if (!(mlo <= mhi + 2.f)) continue;  // also rejects NaN (0 * inf on a zero component)
         const int m0 = max(0, (int)mlo - 1), m1 = min(H - 1, (int)mhi + 1);
         const float2 *sk = spec + (long long)r.k * H;
-        long long zx = (long long)m0 * r.ax, zy = (long long)m0 * r.ay;
-        for (int m = m0; m <= m1; ++m, zx += r.ax, zy += r.ay) {
+        // exact offsets d = u - z at m0 from the fixed-point ray, then float steps (|m - m0| small)
+        const long long zx = (long long)m0 * r.ax, zy = (long long)m0 * r.ay;
+        const float dx0 = (float)(ux - (int)(zx >> 32)) - (float)(unsigned)(zx & 0xffffffffLL) * 2.3283064365386963e-10f;
+        const float dy0 = (float)(uy - (int)(zy >> 32)) - (float)(unsigned)(zy & 0xffffffffLL) * 2.3283064365386963e-10f;
+        const float sx = (float)((double)r.ax * 2.3283064365386963e-10), sy = (float)((double)r.ay * 2.3283064365386963e-10);
+        for (int m = m0; m <= m1; ++m) {
+            const float t = (float)(m - m0);
+            const float dx = fmaf(-t, sx, dx0), dy = fmaf(-t, sy, dy0);
+            // footprint rule of the spreading form: u - z in (-3, 3] per axis
+            if (!(dx > -3.f && dx <= 3.f && dy > -3.f && dy <= 3.f)) continue;
             const float2 v = __ldg(sk + m);
-            const int dx = ux - (int)(zx >> 32), dy = uy - (int)(zy >> 32);
-            if (dx < -2 || dx > 3 || dy < -2 || dy > 3) continue;
-            const float rx = (float)(unsigned)(zx & 0xffffffffLL) * 2.3283064365386963e-10f;
-            const float ry = (float)(unsigned)(zy & 0xffffffffLL) * 2.3283064365386963e-10f;
-            const float w = kb_tab(tab, (float)dx - rx) * kb_tab(tab, (float)dy - ry);
+            const float w = kb_tab(tab, dx) * kb_tab(tab, dy);
             acc.x = fmaf(w, v.x, acc.x);
             acc.y = fmaf(w, v.y, acc.y);
         }
