@@ -42,6 +42,7 @@ radon_direct_kernel(const float *__restrict__ img, float *__restrict__ sino, con
     float *tile = reinterpret_cast<float *>(win + kRWarps * kAng * W);  // [64][65] pixel tile
     __shared__ float4 sp[kAngMax];  // q0, c, s, -
     __shared__ int sJ0[kAngMax];
+    __shared__ int sMode[2];        // common (x-dominant, S) of the block's angles, or S = 0 if mixed
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int k0 = blockIdx.x * kAng;
@@ -55,6 +56,22 @@ radon_direct_kernel(const float *__restrict__ img, float *__restrict__ sino, con
     for (int i = tid; i < kAng * n_det; i += kRThreads) rows[i] = 0.f;
     float2 *mywin = win + warp * kAng * W;
     for (int i = lane; i < kAng * W; i += 32) mywin[i] = make_float2(0.f, 0.f);
+    if (tid == 0) {
+        // one lane spacing for all angles of the block when they share a dominant axis
+        int xd = -1, S = 0;
+        for (int a = 0; a < kn; ++a) {
+            const AngleParam p = ap[k0 + a];
+            const bool x = fabsf(p.c) >= fabsf(p.s);
+            const float dom = x ? fabsf(p.c) : fabsf(p.s);
+            const int Sa = (int)floorf(1.0f / dom) + 1;  // Sa * |dominant step| > 1 bin
+            if (a == 0) { xd = x; S = Sa; }
+            else if (xd != (int)x) S = 0;
+            else S = max(S, Sa);
+        }
+        sMode[0] = xd;
+        sMode[1] = S;
+    }
+
     // register prefetch of a tile: thread covers rows (tid/64) + 4i, column tid%64
     float pre[16];
     auto fetch = [&](int t) {
@@ -68,47 +85,34 @@ radon_direct_kernel(const float *__restrict__ img, float *__restrict__ sino, con
     };
     if (t_begin < t_end) fetch(t_begin);
 
-    // Deposit the tile for angle a: lanes take the positions ph, ph + S, ... along the major
-    // axis (S |major step| > 1 bin, so at any common minor coordinate the 32 lanes sit in 32
-    // different intervals) and walk the 64 minor coordinates in lockstep.  Each lane keeps
-    // the running sums of its current interval in registers and adds them to the warp's
-    // window only when its interval changes.
-    auto deposit_walk = [&](int a, bool xdom, int S, int task0, int tstride) {
-        const float4 P = sp[a];
-        const float cmaj = xdom ? P.y : P.z, cmin = xdom ? P.z : P.y;
-        float2 *wa = mywin + a * W + C;
-        const int per = (kTile + S - 1) / S;  // positions per phase
-        for (int task = task0; task < S * ((per + 31) / 32); task += tstride) {
-            const int ph = task % S, chunk = task / S;
-            const int pos = ph + S * (lane + 32 * chunk);
-            const bool act = pos < kTile;
-            const float qmaj = fmaf((float)pos, cmaj, P.x);
-            int mcur = 0x7fffffff;
-            float A = 0.f, B = 0.f;
-            for (int t = 0; t <= kTile; ++t) {
-                float f = 0.f, q = 0.f;
-                int m = 0x7ffffffe;
-                if (t < kTile) {
-                    f = act ? tile[(xdom ? t * (kTile + 1) + pos : pos * (kTile + 1) + t)] : 0.f;
-                    q = fmaf((float)t, cmin, qmaj);
-                    const float r = q + kMagic;
-                    m = __float_as_int(r) - kMagicInt;  // rint(q)
-                    q -= (r - kMagic);                  // q - m, in [-1/2, 1/2]
-                }
-                if (act && m != mcur) {
-                    if (mcur != 0x7fffffff && (A != 0.f || B != 0.f)) {
-                        float2 c = wa[mcur];
-                        c.x += A;
-                        c.y += B;
-                        wa[mcur] = c;
+    // deposit the pixels of lines warp, warp + 8, ... of the tile for angles [a0, a1)
+    auto deposit = [&](int a0, int a1, bool xdom, int S) {
+        for (int line = warp; line < kTile; line += kRWarps) {
+            for (int base = 0; base < kTile; base += 32 * S) {
+                for (int ph = 0; ph < S; ++ph) {
+                    const int pos = base + ph + S * lane;
+                    const bool act = pos < kTile;
+                    const int x = xdom ? pos : line, y = xdom ? line : pos;
+                    const float f = act ? tile[y * (kTile + 1) + x] : 0.f;
+#pragma unroll
+                    for (int a = 0; a < kAngMax; ++a) {
+                        if (a0 + a < a1) {
+                            const float4 P = sp[a0 + a];
+                            const float q = fmaf((float)y, P.z, fmaf((float)x, P.y, P.x));
+                            const float r = q + kMagic;
+                            const int m = __float_as_int(r) - kMagicInt;  // rint(q)
+                            const float dq = q - (r - kMagic);            // q - m, in [-1/2, 1/2]
+                            if (act && f != 0.f) {
+                                float2 *cell = mywin + (a0 + a) * W + C + m;
+                                float2 v = *cell;
+                                v.x += f;
+                                v.y = fmaf(f, dq, v.y);
+                                *cell = v;
+                            }
+                        }
                     }
-                    mcur = m;
-                    A = 0.f;
-                    B = 0.f;
+                    __syncwarp();
                 }
-                __syncwarp();
-                A += f;
-                B = fmaf(f, q, B);
             }
         }
     };
@@ -131,17 +135,15 @@ radon_direct_kernel(const float *__restrict__ img, float *__restrict__ sino, con
         __syncthreads();
         if (t + 1 < t_end) fetch(t + 1);
 
-        // tasks (angle, lane phase, chunk) spread over the warps; each warp deposits into its
-        // own window of the task's angle
-        for (int a = 0; a < kn; ++a) {
-            const float4 P = sp[a];
-            const bool x = fabsf(P.y) >= fabsf(P.z);
-            const float dom = x ? fabsf(P.y) : fabsf(P.z);
-            const int S = (int)floorf(1.0f / dom) + 1;
-            const int ntask = S * (((kTile + S - 1) / S + 31) / 32);
-            // spread angle a's tasks over the warps, rotating the starting warp with a
-            const int w0 = (warp - a * ntask % kRWarps + kRWarps) % kRWarps;
-            deposit_walk(a, x, S, w0, kRWarps);
+        if (sMode[1] > 0) {
+            deposit(0, kn, sMode[0] != 0, sMode[1]);
+        } else {
+            for (int a = 0; a < kn; ++a) {  // mixed dominant axes: one angle at a time
+                const float4 P = sp[a];
+                const bool x = fabsf(P.y) >= fabsf(P.z);
+                const float dom = x ? fabsf(P.y) : fabsf(P.z);
+                deposit(a, a + 1, x, (int)floorf(1.0f / dom) + 1);
+            }
         }
         __syncthreads();
         // fold the warp windows into the detector rows: bin m takes interval m (lower part)
