@@ -87,6 +87,11 @@ radon_direct_kernel(const float *__restrict__ img, float *__restrict__ sino, con
 
     // deposit the pixels of lines warp, warp + 8, ... of the tile for angles [a0, a1)
     auto deposit = [&](int a0, int a1, bool xdom, int S) {
+        // the angles' parameters live in registers (shared memory would be re-read after
+        // every window store, which may alias it)
+        float4 Pa[kAngMax];
+#pragma unroll
+        for (int a = 0; a < kAngMax; ++a) Pa[a] = (a0 + a < a1) ? sp[a0 + a] : make_float4(0.f, 0.f, 0.f, 0.f);
         for (int line = warp; line < kTile; line += kRWarps) {
             for (int base = 0; base < kTile; base += 32 * S) {
                 for (int ph = 0; ph < S; ++ph) {
@@ -97,7 +102,7 @@ radon_direct_kernel(const float *__restrict__ img, float *__restrict__ sino, con
 #pragma unroll
                     for (int a = 0; a < kAngMax; ++a) {
                         if (a0 + a < a1) {
-                            const float4 P = sp[a0 + a];
+                            const float4 P = Pa[a];
                             const float q = fmaf((float)y, P.z, fmaf((float)x, P.y, P.x));
                             const float r = q + kMagic;
                             const int m = __float_as_int(r) - kMagicInt;  // rint(q)
