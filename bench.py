@@ -243,8 +243,10 @@ def other_paths(plan, q, img, flush, stream, dev, only=()):
     guard("fourier_backprojection_2048", fourier)
 
     def radon():
+        shape, _ = plan.autotune("radon", batch=1)
         ms = _timed(lambda: plan.radon(img, out=q), stream, flush, 5)
-        return {"ms": ms, "Gupdates_s": wl.updates / ms / 1e6}
+        return {"ms": ms, "Gupdates_s": wl.updates / ms / 1e6, "launch_shape": {"angles_per_cta": shape[0],
+                                                                               "bands": shape[1]}}
     guard("radon_direct_2048", radon)
 
     def radon_f():
@@ -254,9 +256,34 @@ def other_paths(plan, q, img, flush, stream, dev, only=()):
 
     def bf16():
         q16 = q.to(torch.bfloat16)
+        shape, _ = plan.autotune("direct", torch.bfloat16, 1)
         ms = _timed(lambda: plan.backproject(q16, out=img), stream, flush, 10)
-        return {"ms": ms, "Gupdates_s": wl.updates / ms / 1e6}
+        return {"ms": ms, "Gupdates_s": wl.updates / ms / 1e6, "launch_shape": {"stage": shape[0],
+                                                                               "angle_groups": shape[1]}}
     guard("direct_bf16_storage_2048", bf16)
+
+    # 256^2 slice, 256 bins, 180 angles (16 pixel tiles): default launch shape vs autotuned
+    def small():
+        S = synth.SMALL
+        ps = bp.Plan(S.N, S.n_det, S.theta, S.det_spacing)
+        gs = torch.from_numpy(S.sinogram().astype(np.float32)).to(dev)
+        qs = ps.filter(gs, "ramlak")
+        ims = torch.empty((S.N, S.N), dtype=torch.float32, device=dev)
+        res = {}
+        for label, shp in (("one_cta_per_tile", (16, 1)), ("default", None)):
+            if shp:
+                ps.set_shape(shp, "direct", torch.float32, 1)
+            else:
+                ps = bp.Plan(S.N, S.n_det, S.theta, S.det_spacing)
+            used = ps.get_shape("direct", torch.float32, 1)
+            ms = _timed(lambda: ps.backproject(qs, out=ims), stream, flush, 20)
+            res[label] = {"ms": ms, "Gupdates_s": S.updates / ms / 1e6, "launch_shape": list(used)}
+        shape, _ = ps.autotune("direct", torch.float32, 1)
+        ms = _timed(lambda: ps.backproject(qs, out=ims), stream, flush, 20)
+        res["autotuned"] = {"ms": ms, "Gupdates_s": S.updates / ms / 1e6, "launch_shape": list(shape)}
+        ps.close()
+        return res
+    guard("slice256_bins256_ang180_shapes", small)
 
     # volume: 256 slices of 2048^2 from BF16 sinograms, one batched launch replayed from a CUDA graph
     def volume():
@@ -290,6 +317,8 @@ def other_paths(plan, q, img, flush, stream, dev, only=()):
         p2 = bp.Plan(N, nd, synth.uniform_theta(nt))
         g = torch.stack([synth.ellipse_sinogram_torch(synth.random_ellipses(30, 4000 + i), synth.uniform_theta(nt),
                                                       nd, 2.0 / nd, dev).float() for i in range(B)])
+        p2.autotune("radon", batch=B)
+        p2.autotune("direct", torch.float32, B)  # R^T runs the direct R* kernel
         step = 1.0 / (2.0 * ag.lipschitz_estimate(p2, (B, N, N), dev) + 1e-3 * 8.0 / 1e-3)
         ag.tv_reconstruct(g, p2, iters=2, step=step)
         torch.cuda.synchronize()
@@ -335,6 +364,7 @@ def other_paths(plan, q, img, flush, stream, dev, only=()):
         qb = pb.filter(g, "shepp-logan")
         del g
         ib = torch.empty((N, N), dtype=torch.float32, device=dev)
+        pb.autotune("direct", torch.float32, 1)
         msd = _timed(lambda: pb.backproject(qb, out=ib), stream, flush, 2)
         msf = _timed(lambda: pb.backproject_fourier(qb, out=ib), stream, flush, 2)
         pb.close()
@@ -376,6 +406,12 @@ def run_gpu(args, world, rank, local):
     def step():
         plan.filter(g, "shepp-logan", out=q)
         plan.backproject(q, out=img)
+
+    # launch shape of the direct R* picked by the library's autotuner (untimed setup)
+    if args.no_tune:
+        shape = plan.get_shape("direct", torch.float32, 1)
+    else:
+        shape, _ = plan.autotune("direct", torch.float32, 1)
 
     for _ in range(max(3, args.warmup)):
         step()
@@ -472,6 +508,8 @@ def run_gpu(args, world, rank, local):
         "config": {"workload": wl.name, "N": wl.N, "n_det": wl.n_det, "n_theta": wl.n_theta,
                    "phantom": "50 seeded random ellipses + 1% Gaussian noise", "filter": "shepp-logan",
                    "step": "bp_filter + bp_backproject_direct", "l2": "flushed (256 MiB write) between steps",
+                   "launch_shape": {"stage": shape[0], "angle_groups": shape[1],
+                                    "picked_by": "default rule" if args.no_tune else "bp_autotune"},
                    "parallelism": f"independent slice per GPU x{world}"},
         "roofline": {"bound": "alu", "kernel": "bp_direct_kernel", "achieved": achieved,
                      "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
@@ -516,6 +554,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the e2e and other-operator timings")
     ap.add_argument("--no-paths", action="store_true", help="skip the other workloads under 'paths'")
     ap.add_argument("--only", default="", help="comma-separated path names: run only these (profiling)")
+    ap.add_argument("--no-tune", action="store_true", help="time the direct R* with its default launch shape")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     world, rank, local = _dist_init()

@@ -209,6 +209,54 @@ bp_status bp_fbp_static(bp_plan *plan, const void *sino, bp_dtype dtype, float *
  */
 bp_status bp_check(bp_plan *plan, void *stream);
 
+/*
+ * Launch shapes and autotuning.  Neither changes what an operator computes, only how its
+ * work is split across the GPU (no counterpart in the paper).
+ *
+ * BP_OP_DIRECT  direct R* (bp_backproject_direct, bp_radon_transpose with fourier = 0,
+ *               bp_fbp_host, bp_fbp_static): shape[0] = angles per shared-memory stage
+ *               (8, 16 or 32); shape[1] = angle groups (>= 1): each 64 x 64 pixel tile is
+ *               backprojected by shape[1] CTAs over disjoint angle ranges whose partial sums
+ *               are added atomically (the summation order then varies between runs, within
+ *               FP32 rounding).
+ * BP_OP_RADON   direct R (bp_radon and bp_backproject_transpose with the direct form):
+ *               shape[0] = angles per CTA (1, 2 or 4); shape[1] = image bands per angle block
+ *               (>= 1; partial sinograms added atomically when > 1).
+ *
+ * A call (op, dtype, batch) takes the plan's own shape for (op, dtype, batch), else the
+ * process-wide tuning cache entry for the plan's geometry (N, n_det, n_theta, window, SM
+ * count), else the default rule: stage 16 and enough angle groups for about two waves of
+ * three CTAs per SM; Radon: 4 angles per CTA (2 or 1 when their detector rows exceed
+ * 64 KB) and enough bands for four CTAs per SM.  Out-of-range values are clamped at launch
+ * (stage lowered when its shared memory does not fit, groups kept <= the number of stages).
+ */
+typedef enum { BP_OP_DIRECT = 0, BP_OP_RADON = 1 } bp_op;
+
+/*
+ * bp_autotune -- time the candidate shapes of `op` for this plan at (dtype, batch) on
+ * `stream` with CUDA events (scratch device buffers are allocated, filled with a fixed
+ * pattern and freed inside the call; the stream is synchronised) and keep the fastest for
+ * the plan and in the process-wide cache.  dtype is ignored for BP_OP_RADON.  shape
+ * (nullable, 2 ints) receives the chosen shape, ms (nullable) the best time of one call in
+ * milliseconds.  Not allowed while `stream` is being captured.
+ */
+bp_status bp_autotune(bp_plan *plan, bp_op op, bp_dtype dtype, int batch, void *stream, int *shape, float *ms);
+
+/* bp_get_shape -- the shape (2 ints, after clamping) a call (op, dtype, batch) uses now. */
+bp_status bp_get_shape(const bp_plan *plan, bp_op op, bp_dtype dtype, int batch, int *shape);
+
+/* bp_set_shape -- fix the shape (2 ints) of calls (op, dtype, batch) on this plan. */
+bp_status bp_set_shape(bp_plan *plan, bp_op op, bp_dtype dtype, int batch, const int *shape);
+
+/*
+ * bp_tune_cache_save / bp_tune_cache_load -- write / merge the process-wide tuning cache as
+ * text, one entry per line: "op dtype batch N n_det n_theta W sm_count shape0 shape1".
+ * Loading skips malformed lines; BP_ERR_INVALID_ARG if the file cannot be opened or holds
+ * no valid entry.  Both are thread-safe and need no GPU.
+ */
+bp_status bp_tune_cache_save(const char *path);
+bp_status bp_tune_cache_load(const char *path);
+
 /* Last error message of the calling thread ("" if none). */
 const char *bp_last_error(void);
 

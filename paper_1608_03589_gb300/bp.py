@@ -25,8 +25,10 @@ _DTYPES = {torch.float32: BP_F32, torch.bfloat16: BP_BF16, torch.float16: BP_F16
 
 # Every symbol the header declares (checked by the ABI test).
 SYMBOLS = ("bp_plan_create", "bp_destroy", "bp_filter", "bp_backproject_direct", "bp_backproject_fourier",
-           "bp_radon", "bp_fbp_host", "bp_backproject_batched", "bp_fbp_static", "bp_check", "bp_radon_transpose", "bp_backproject_transpose", "bp_last_error",
-           "bp_version")
+           "bp_radon", "bp_fbp_host", "bp_backproject_batched", "bp_fbp_static", "bp_check", "bp_radon_transpose",
+           "bp_backproject_transpose", "bp_autotune", "bp_get_shape", "bp_set_shape", "bp_tune_cache_save",
+           "bp_tune_cache_load", "bp_last_error", "bp_version")
+OPS = {"direct": 0, "radon": 1}
 
 
 class BPError(RuntimeError):
@@ -61,9 +63,16 @@ def lib() -> ctypes.CDLL:
             L.bp_backproject_transpose.argtypes = [vp, vp, vp, i, i, vp]
             L.bp_backproject_batched.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(i),
                                                  ctypes.POINTER(vp), i, vp]
+            ip = ctypes.POINTER(i)
+            L.bp_autotune.argtypes = [vp, i, i, i, vp, ip, ctypes.POINTER(f)]
+            L.bp_get_shape.argtypes = [vp, i, i, i, ip]
+            L.bp_set_shape.argtypes = [vp, i, i, i, ip]
+            L.bp_tune_cache_save.argtypes = [ctypes.c_char_p]
+            L.bp_tune_cache_load.argtypes = [ctypes.c_char_p]
             for name in ("bp_filter", "bp_backproject_direct", "bp_backproject_fourier", "bp_radon",
                          "bp_fbp_host", "bp_backproject_batched", "bp_fbp_static", "bp_check",
-                         "bp_radon_transpose", "bp_backproject_transpose"):
+                         "bp_radon_transpose", "bp_backproject_transpose", "bp_autotune", "bp_get_shape",
+                         "bp_set_shape", "bp_tune_cache_save", "bp_tune_cache_load"):
                 getattr(L, name).restype = i
             L.bp_last_error.argtypes = []
             L.bp_last_error.restype = ctypes.c_char_p
@@ -246,6 +255,43 @@ class Plan:
         with torch.cuda.device(self.device):
             _check(lib().bp_check(self.handle, torch.cuda.current_stream(self.device).cuda_stream), "bp_check")
 
+    # ------------------------------------------------------------------ launch shapes
+    @staticmethod
+    def _op_dtype(op: str, dtype) -> tuple[int, int]:
+        if op not in OPS:
+            raise BPError(f"op must be one of {sorted(OPS)}")
+        if isinstance(dtype, torch.dtype):
+            if dtype not in _DTYPES:
+                raise BPError(f"unsupported dtype {dtype}")
+            dtype = _DTYPES[dtype]
+        return OPS[op], int(dtype)
+
+    def autotune(self, op: str = "direct", dtype=torch.float32, batch: int = 1) -> tuple[tuple[int, int], float]:
+        """Time the candidate launch shapes of op ("direct" R* or "radon" R) and keep the
+        fastest for calls with this (dtype, batch); returns (shape, milliseconds)."""
+        o, d = self._op_dtype(op, dtype)
+        shape = (ctypes.c_int * 2)()
+        ms = ctypes.c_float()
+        with torch.cuda.device(self.device):
+            _check(lib().bp_autotune(self.handle, o, d, int(batch), torch.cuda.current_stream(self.device).cuda_stream,
+                                     shape, ctypes.byref(ms)), "bp_autotune")
+        return (shape[0], shape[1]), float(ms.value)
+
+    def get_shape(self, op: str = "direct", dtype=torch.float32, batch: int = 1) -> tuple[int, int]:
+        """Launch shape (after clamping) a call (op, dtype, batch) uses now."""
+        o, d = self._op_dtype(op, dtype)
+        shape = (ctypes.c_int * 2)()
+        with torch.cuda.device(self.device):
+            _check(lib().bp_get_shape(self.handle, o, d, int(batch), shape), "bp_get_shape")
+        return shape[0], shape[1]
+
+    def set_shape(self, shape: tuple[int, int], op: str = "direct", dtype=torch.float32, batch: int = 1) -> None:
+        """Fix the launch shape of calls (op, dtype, batch) on this plan."""
+        o, d = self._op_dtype(op, dtype)
+        arr = (ctypes.c_int * 2)(int(shape[0]), int(shape[1]))
+        with torch.cuda.device(self.device):
+            _check(lib().bp_set_shape(self.handle, o, d, int(batch), arr), "bp_set_shape")
+
     def close(self) -> None:
         if getattr(self, "_h", None) is not None:
             lib().bp_destroy(self._h)
@@ -289,3 +335,13 @@ def backproject_batched(plans: Sequence[Plan], sinos: Sequence[torch.Tensor],
     with torch.cuda.device(plans[0].device):
         _check(lib().bp_backproject_batched(P, S, D, O, n, _stream(sinos[0])), "bp_backproject_batched")
     return list(imgs)
+
+
+def tune_cache_save(path: str) -> None:
+    """Write the process-wide tuning cache (bp_tune_cache_save)."""
+    _check(lib().bp_tune_cache_save(os.fsencode(path)), "bp_tune_cache_save")
+
+
+def tune_cache_load(path: str) -> None:
+    """Merge a tuning cache file into the process-wide cache (bp_tune_cache_load)."""
+    _check(lib().bp_tune_cache_load(os.fsencode(path)), "bp_tune_cache_load")

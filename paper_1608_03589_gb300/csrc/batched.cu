@@ -54,16 +54,16 @@ bp_batched_kernel(const __grid_constant__ BatchParams bpm, int *__restrict__ cou
         const int ty = t / d.tiles1, tx = t - ty * d.tiles1;
         switch (d.dtype) {
             case BP_F32:
-                direct_tile_sync<float>((const float *)d.sino, d.img, d.ap, d.N, d.n_det, d.n_theta, d.W, d.C, tx, ty,
-                                        0, 0.f, tab, sm);
+                direct_tile_sync<float>((const float *)d.sino, d.img, d.ap, d.N, d.n_det, 0, d.n_theta, d.W, d.C, tx,
+                                        ty, 0, 0, 0.f, tab, sm);
                 break;
             case BP_BF16:
-                direct_tile_sync<__nv_bfloat16>((const __nv_bfloat16 *)d.sino, d.img, d.ap, d.N, d.n_det, d.n_theta,
-                                                d.W, d.C, tx, ty, 0, 0.f, tab, sm);
+                direct_tile_sync<__nv_bfloat16>((const __nv_bfloat16 *)d.sino, d.img, d.ap, d.N, d.n_det, 0,
+                                                d.n_theta, d.W, d.C, tx, ty, 0, 0, 0.f, tab, sm);
                 break;
             default:
-                direct_tile_sync<__half>((const __half *)d.sino, d.img, d.ap, d.N, d.n_det, d.n_theta, d.W, d.C, tx,
-                                         ty, 0, 0.f, tab, sm);
+                direct_tile_sync<__half>((const __half *)d.sino, d.img, d.ap, d.N, d.n_det, 0, d.n_theta, d.W, d.C,
+                                         tx, ty, 0, 0, 0.f, tab, sm);
                 break;
         }
     }

@@ -48,6 +48,7 @@ struct RayIndex {
     int n = 0;
     int uniform = 0;              // angles phi_i = phi0 + i dphi exactly (to 1e-9)
     float phi0 = 0.f, dphi = 0.f;
+    int upper = 0;                // every ray has a non-negative y step (angles in [0, pi])
 };
 
 // Fourier-path workspace and gridding geometry (allocated on first use).
@@ -68,6 +69,24 @@ struct FourierWork {
     float rmax = 0.f;           // largest sample radius (grid cells) plus a margin
     RayIndex ri;                // sorted-angle lookup (gather gridding)
     size_t bytes = 0;
+};
+
+// Launch shapes.  The direct R* takes `stage` angles per shared-memory stage (8, 16 or 32)
+// and splits the angles into `asplit` groups, each a separate CTA per tile that adds its
+// partial sum into the image; the direct R takes `kang` angles per CTA (1, 2 or 4) and
+// `bands` image bands per angle block (0 = the default rules).  They are picked by
+// bp_autotune (tune.cu) or by the default rules there.
+struct DirectShape {
+    int stage = kStage;
+    int asplit = 1;
+};
+struct RadonShape {
+    int kang = 0;   // 0 = the default rule
+    int bands = 0;
+};
+struct TuneEntry {
+    int op, dtype, batch;
+    int v[2];
 };
 
 }  // namespace bp
@@ -98,6 +117,9 @@ struct bp_plan {
     int *d_status = nullptr;
     // device-side error word: set to non-zero by a kernel whose bounded wait gave up
     int *d_err = nullptr;
+    // launch shapes chosen for this plan (bp_autotune / bp_set_shape), and the SM count
+    std::vector<bp::TuneEntry> shapes;
+    int sm_count = 0;
 };
 
 namespace bp {
@@ -110,10 +132,24 @@ int ilog2(int v);
 // by w_k instead of dx^2/dt (the two weightings of the Euclidean transposes).
 bp_status launch_direct(bp_plan *p, const void *sino, bp_dtype dt, float *img, int batch, int accumulate,
                         cudaStream_t st, float wuni = 0.f);
+bp_status launch_direct_shape(bp_plan *p, const void *sino, bp_dtype dt, float *img, int batch, int accumulate,
+                              cudaStream_t st, float wuni, DirectShape shape);
 bp_status launch_filter(bp_plan *p, const void *in, bp_dtype dt, float *out, int kind, float param, int batch,
                         cudaStream_t st);
 bp_status launch_radon_direct(bp_plan *p, const float *img, float *sino, int batch, cudaStream_t st,
                               int per_angle_w = 0);
+bp_status launch_radon_shape(bp_plan *p, const float *img, float *sino, int batch, cudaStream_t st, int per_angle_w,
+                             RadonShape shape);
+// shape lookup: the plan's own entry for (op, dtype, batch), else the process-wide tuning
+// cache for the plan's geometry, else the default rule
+DirectShape direct_shape(const bp_plan *p, bp_dtype dt, int batch);
+RadonShape radon_shape(const bp_plan *p, int batch);
+int direct_max_asplit(const bp_plan *p, int stage);
+DirectShape direct_shape_used(const bp_plan *p, bp_dtype dt, int batch);  // after clamping
+RadonShape radon_shape_used(const bp_plan *p, int batch);                  // after clamping
+DirectShape direct_clamp(const bp_plan *p, bp_dtype dt, DirectShape shape);
+RadonShape radon_clamp(const bp_plan *p, RadonShape shape);
+int radon_max_kang(const bp_plan *p);
 bp_status launch_fourier(bp_plan *p, const void *sino, bp_dtype dt, float *img, int batch, cudaStream_t st,
                          float wuni = 0.f);
 bp_status launch_radon_fourier(bp_plan *p, const float *img, float *sino, int batch, cudaStream_t st,

@@ -23,6 +23,7 @@
 // fallback (synchronous window loads) for other strides.
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "common.cuh"
@@ -33,15 +34,25 @@ namespace bp {
 
 namespace {
 
+constexpr size_t kMaxDirectSmem = 200 * 1024;
+
+// Stage range [s0, s1) of angle group g out of `asplit` over S stages (balanced, non-empty
+// when asplit <= S).
+__device__ __forceinline__ int group_stage(int g, int S, int asplit) { return (int)((long long)g * S / asplit); }
+
 template <typename Tin>
 __global__ void __launch_bounds__(kThreads, 2)
 bp_direct_kernel(const Tin *__restrict__ sino, float *__restrict__ img, const AngleParam *__restrict__ ap,
-                 int N, int n_det, int n_theta, int W, int C, int accumulate,
+                 int N, int n_det, int n_theta, int W, int C, int accumulate, int tiles, int asplit,
                  long long sino_stride, long long img_stride, float wuni) {
     extern __shared__ __align__(16) float2 tab[];  // [kStage][W] (e, d) pairs
     __shared__ DirectStageSmem sm;
+    const int ty = blockIdx.y % tiles, grp = blockIdx.y / tiles;
+    const int S = (n_theta + kStage - 1) / kStage;
+    const int k_begin = group_stage(grp, S, asplit) * kStage;
+    const int k_end = min(n_theta, group_stage(grp + 1, S, asplit) * kStage);
     direct_tile_sync<Tin>(sino + (long long)blockIdx.z * sino_stride, img + (long long)blockIdx.z * img_stride, ap,
-                          N, n_det, n_theta, W, C, blockIdx.x, blockIdx.y, accumulate, wuni, tab, sm);
+                          N, n_det, k_begin, k_end, W, C, blockIdx.x, ty, accumulate, asplit > 1, wuni, tab, sm);
 }
 
 __device__ __forceinline__ unsigned long long pk2(float a, float b) {
@@ -75,28 +86,33 @@ template <> __device__ __forceinline__ float smem_f<__half>(const unsigned char 
     return __half2float(reinterpret_cast<const __half *>(p)[i]);
 }
 
-template <typename Tin>
+// STAGE angles per stage; the table of each angle is built by kThreads / STAGE threads.
+template <typename Tin, int STAGE>
 __global__ void __launch_bounds__(kThreads, 3)
 bp_direct_tma_kernel(const __grid_constant__ CUtensorMap tmap, float *__restrict__ img,
                      const AngleParam *__restrict__ ap, int N, int n_theta, int W, int C, int Wb, int RS,
-                     int accumulate, long long img_stride, int *__restrict__ err, float wuni) {
+                     int accumulate, int tiles, int asplit, long long img_stride, int *__restrict__ err, float wuni) {
+    constexpr int TPA = kThreads / STAGE;
     extern __shared__ __align__(128) unsigned char dsm[];
-    unsigned char *raw = dsm;                                              // [2][kStage] rows of RS bytes
-    float2 *tab = reinterpret_cast<float2 *>(dsm + 2 * kStage * RS);     // [2][kStage][W]
-    __shared__ float4 sp[3][kStage];   // q0, c, s, table base bits
-    __shared__ int sof[3][kStage];     // J0 - J0r (TMA box starts at the 8-aligned J0r)
-    __shared__ float sw[3][kStage];
+    unsigned char *raw = dsm;                                              // [2][STAGE] rows of RS bytes
+    float2 *tab = reinterpret_cast<float2 *>(dsm + 2 * STAGE * RS);      // [2][STAGE][W]
+    __shared__ float4 sp[3][STAGE];   // q0, c, s, table base bits
+    __shared__ int sof[3][STAGE];     // J0 - J0r (TMA box starts at the 8-aligned J0r)
+    __shared__ float sw[3][STAGE];
     __shared__ __align__(8) unsigned long long bars[2];
 
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     const int lx = lane & 7;
     const int ly = warp * 8 + (lane >> 3);
-    const int tx = blockIdx.x, ty = blockIdx.y, bz = blockIdx.z;
+    const int tx = blockIdx.x, ty = blockIdx.y % tiles, grp = blockIdx.y / tiles, bz = blockIdx.z;
     img += (long long)bz * img_stride;
     const uint32_t bar0 = smem_u32(&bars[0]);
     const unsigned tab_u32 = smem_u32(tab);
-    const int S = (n_theta + kStage - 1) / kStage;
+    // this CTA's stages: [s0, s0 + S) of the (n_theta / STAGE) stages
+    const int S_all = (n_theta + STAGE - 1) / STAGE;
+    const int s0 = group_stage(grp, S_all, asplit);
+    const int S = group_stage(grp + 1, S_all, asplit) - s0;
 
     if (tid == 0) {
         mbar_init(bar0, 1);
@@ -105,9 +121,9 @@ bp_direct_tma_kernel(const __grid_constant__ CUtensorMap tmap, float *__restrict
     }
     __syncthreads();
 
-    // Stage parameters and TMA issue for stage s: thread kk < kn handles angle k0 + kk.
-    auto prepare = [&](int s) {
-        const int k0 = s * kStage, kn = min(kStage, n_theta - k0), b = s & 1, slot = s % 3;
+    // Stage parameters and TMA issue for local stage i: thread kk < kn handles angle k0 + kk.
+    auto prepare = [&](int i) {
+        const int k0 = (s0 + i) * STAGE, kn = min(STAGE, n_theta - k0), b = i & 1, slot = i % 3;
         if (tid == 0) mbar_expect_tx(bar0 + 8 * b, (uint32_t)(kn * Wb * (int)sizeof(Tin)));
         if (tid < kn) {
             const AngleParam p = ap[k0 + tid];
@@ -118,12 +134,12 @@ bp_direct_tma_kernel(const __grid_constant__ CUtensorMap tmap, float *__restrict
             const int J0 = Ji + (int)floorf(emin) - 1;
             const int J0r = J0 & ~7;
             const float q0 = (float)(Ji - J0 - C) + (frac - 0.5f);
-            const unsigned base = tab_u32 + (unsigned)((b * kStage + tid) * W) * 8u + 8u * (unsigned)C -
+            const unsigned base = tab_u32 + (unsigned)((b * STAGE + tid) * W) * 8u + 8u * (unsigned)C -
                                   (kMagicBits << 3);
             sp[slot][tid] = make_float4(q0, p.c, p.s, __uint_as_float(base));
             sof[slot][tid] = J0 - J0r;
             sw[slot][tid] = wuni > 0.f ? wuni : p.w;
-            tma_load_3d(smem_u32(raw + (b * kStage + tid) * RS), &tmap, J0r, k0 + tid, bz, bar0 + 8 * b);
+            tma_load_3d(smem_u32(raw + (b * STAGE + tid) * RS), &tmap, J0r, k0 + tid, bz, bar0 + 8 * b);
         }
     };
 
@@ -139,19 +155,19 @@ bp_direct_tma_kernel(const __grid_constant__ CUtensorMap tmap, float *__restrict
     if (S > 1) prepare(1);
     __syncthreads();
     bool ok = true;
-    for (int s = 0; s < S; ++s) {
-        const int b = s & 1, slot = s % 3;
-        const int kn = min(kStage, n_theta - s * kStage);
-        ok &= mbar_wait(bar0 + 8 * b, (uint32_t)((s >> 1) & 1));
+    for (int i = 0; i < S; ++i) {
+        const int b = i & 1, slot = i % 3;
+        const int kn = min(STAGE, n_theta - (s0 + i) * STAGE);
+        ok &= mbar_wait(bar0 + 8 * b, (uint32_t)((i >> 1) & 1));
         {
-            // build the (e, d) table of stage s from its raw windows: 16 threads per angle
-            const int kk = tid >> 4, r = tid & 15;
+            // build the (e, d) table of stage i from its raw windows: TPA threads per angle
+            const int kk = tid / TPA, r = tid % TPA;
             if (kk < kn) {
-                const unsigned char *row = raw + (b * kStage + kk) * RS;
+                const unsigned char *row = raw + (b * STAGE + kk) * RS;
                 const int off = sof[slot][kk];
                 const float w = sw[slot][kk];
-                float2 *dst = tab + (b * kStage + kk) * W;
-                for (int m = r; m < W; m += 16) {
+                float2 *dst = tab + (b * STAGE + kk) * W;
+                for (int m = r; m < W; m += TPA) {
                     const float g0 = smem_f<Tin>(row, off + m);
                     const float g1 = smem_f<Tin>(row, off + m + 1);
                     const float d = w * (g1 - g0);
@@ -160,9 +176,9 @@ bp_direct_tma_kernel(const __grid_constant__ CUtensorMap tmap, float *__restrict
             }
         }
         __syncthreads();
-        if (s + 2 < S) {
-            if (tid < kStage) fence_proxy_async_smem();
-            prepare(s + 2);
+        if (i + 2 < S) {
+            if (tid < STAGE) fence_proxy_async_smem();
+            prepare(i + 2);
         }
         for (int kk = 0; kk < kn; ++kk) {
             const float4 P = sp[slot][kk];
@@ -194,7 +210,8 @@ bp_direct_tma_kernel(const __grid_constant__ CUtensorMap tmap, float *__restrict
             const int x = tx * kTile + lx + 8 * a;
             if (x < N && y < N) {
                 float *dst = img + (long long)y * N + x;
-                *dst = accumulate ? (*dst + acc[b][a]) : acc[b][a];
+                if (asplit > 1) atomicAdd(dst, acc[b][a]);
+                else *dst = accumulate ? (*dst + acc[b][a]) : acc[b][a];
             }
         }
     }
@@ -219,54 +236,124 @@ template <> constexpr CUtensorMapDataType tmap_type<float>() { return CU_TENSOR_
 template <> constexpr CUtensorMapDataType tmap_type<__nv_bfloat16>() { return CU_TENSOR_MAP_DATA_TYPE_BFLOAT16; }
 template <> constexpr CUtensorMapDataType tmap_type<__half>() { return CU_TENSOR_MAP_DATA_TYPE_FLOAT16; }
 
+// Dynamic shared memory of the TMA kernel for `stage` angles per stage.
+size_t tma_smem(const bp_plan *p, int stage, int esz) {
+    const int Wb = (p->W + 8 + 7) & ~7;
+    const size_t RS = ((size_t)Wb * esz + 127) & ~(size_t)127;
+    return 2 * (size_t)stage * RS + 2 * sizeof(float2) * (size_t)stage * p->W;
+}
+
+bool tma_eligible(const bp_plan *p, int esz) {
+    const int Wb = (p->W + 8 + 7) & ~7;
+    return ((long long)p->n_det * esz) % 16 == 0 && Wb <= 256;
+}
+
+// The shape a direct launch really uses: on the TMA path the stage is lowered until its
+// shared memory fits; the synchronous path always stages kStage angles; groups are clamped.
+DirectShape direct_effective(const bp_plan *p, int esz, bool tma, DirectShape shape) {
+    DirectShape e;
+    e.stage = kStage;
+    if (tma) {
+        e.stage = (shape.stage == 8 || shape.stage == 32) ? shape.stage : kStage;
+        while (e.stage > 8 && tma_smem(p, e.stage, esz) > kMaxDirectSmem) e.stage >>= 1;
+        if (tma_smem(p, e.stage, esz) > kMaxDirectSmem) e.stage = kStage;
+    }
+    e.asplit = std::max(1, std::min(shape.asplit, direct_max_asplit(p, e.stage)));
+    return e;
+}
+
+template <typename Tin, int STAGE>
+bp_status launch_tma(bp_plan *p, const CUtensorMap &map, float *img, int batch, int accumulate, int asplit,
+                     cudaStream_t st, float wuni) {
+    const int tiles = (p->N + kTile - 1) / kTile;
+    const int esz = (int)sizeof(Tin);
+    const int Wb = (p->W + 8 + 7) & ~7;
+    const int RS = (Wb * esz + 127) & ~127;
+    const size_t smem = tma_smem(p, STAGE, esz);
+    auto kern = bp_direct_tma_kernel<Tin, STAGE>;
+    BP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    dim3 grid(tiles, tiles * asplit, batch);
+    kern<<<grid, kThreads, smem, st>>>(map, img, p->d_ang, p->N, p->n_theta, p->W, p->C, Wb, RS, accumulate, tiles,
+                                       asplit, (long long)p->N * p->N, p->d_err, wuni);
+    BP_CUDA_TRY(cudaGetLastError());
+    return BP_OK;
+}
+
 template <typename Tin>
 bp_status launch_direct_t(bp_plan *p, const Tin *sino, float *img, int batch, int accumulate, cudaStream_t st,
-                          float wuni) {
+                          float wuni, DirectShape shape) {
     const int tiles = (p->N + kTile - 1) / kTile;
     const int esz = (int)sizeof(Tin);
     const int Wb = (p->W + 8 + 7) & ~7;
     PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
-    if (enc && ((long long)p->n_det * esz) % 16 == 0 && Wb <= 256) {
-        CUtensorMap map;
+    bool tma = enc && tma_eligible(p, esz);
+    CUtensorMap map;
+    if (tma) {
         const cuuint64_t dims[3] = {(cuuint64_t)p->n_det, (cuuint64_t)p->n_theta, (cuuint64_t)batch};
         const cuuint64_t strides[2] = {(cuuint64_t)p->n_det * esz, (cuuint64_t)p->n_det * p->n_theta * esz};
         const cuuint32_t box[3] = {(cuuint32_t)Wb, 1, 1};
         const cuuint32_t estr[3] = {1, 1, 1};
-        CUresult r = enc(&map, tmap_type<Tin>(), 3, const_cast<Tin *>(sino), dims, strides, box, estr,
-                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        if (r == CUDA_SUCCESS) {
-            const int RS = (Wb * esz + 127) & ~127;
-            const size_t smem = 2 * (size_t)kStage * RS + 2 * sizeof(float2) * (size_t)kStage * p->W;
-            auto kern = bp_direct_tma_kernel<Tin>;
-            BP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            dim3 grid(tiles, tiles, batch);
-            kern<<<grid, kThreads, smem, st>>>(map, img, p->d_ang, p->N, p->n_theta, p->W, p->C, Wb, RS, accumulate,
-                                               (long long)p->N * p->N, p->d_err, wuni);
-            BP_CUDA_TRY(cudaGetLastError());
-            return BP_OK;
+        tma = enc(&map, tmap_type<Tin>(), 3, const_cast<Tin *>(sino), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    }
+    const DirectShape eff = direct_effective(p, esz, tma, shape);
+    if (tma && tma_smem(p, eff.stage, esz) > kMaxDirectSmem) tma = false;
+    const int stage = eff.stage, asplit = eff.asplit;
+    if (asplit > 1 && !accumulate)
+        BP_CUDA_TRY(cudaMemsetAsync(img, 0, sizeof(float) * (size_t)p->N * p->N * batch, st));
+    if (tma) {
+        switch (stage) {
+            case 8: return launch_tma<Tin, 8>(p, map, img, batch, accumulate, asplit, st, wuni);
+            case 32: return launch_tma<Tin, 32>(p, map, img, batch, accumulate, asplit, st, wuni);
+            default: return launch_tma<Tin, 16>(p, map, img, batch, accumulate, asplit, st, wuni);
         }
     }
     const size_t smem = sizeof(float2) * (size_t)kStage * p->W;
+    if (smem > kMaxDirectSmem) return fail(BP_ERR_UNSUPPORTED, "direct R*: window too large for shared memory");
     auto kern = bp_direct_kernel<Tin>;
     BP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    dim3 grid(tiles, tiles, batch);
+    dim3 grid(tiles, tiles * asplit, batch);
     kern<<<grid, kThreads, smem, st>>>(sino, img, p->d_ang, p->N, p->n_det, p->n_theta, p->W, p->C, accumulate,
-                                       (long long)p->n_theta * p->n_det, (long long)p->N * p->N, wuni);
+                                       tiles, asplit, (long long)p->n_theta * p->n_det, (long long)p->N * p->N,
+                                       wuni);
     BP_CUDA_TRY(cudaGetLastError());
     return BP_OK;
 }
 
 }  // namespace
 
-bp_status launch_direct(bp_plan *p, const void *sino, bp_dtype dt, float *img, int batch, int accumulate,
-                        cudaStream_t st, float wuni) {
+bp_status launch_direct_shape(bp_plan *p, const void *sino, bp_dtype dt, float *img, int batch, int accumulate,
+                              cudaStream_t st, float wuni, DirectShape shape) {
     switch (dt) {
-        case BP_F32: return launch_direct_t(p, (const float *)sino, img, batch, accumulate, st, wuni);
-        case BP_BF16: return launch_direct_t(p, (const __nv_bfloat16 *)sino, img, batch, accumulate, st, wuni);
-        case BP_F16: return launch_direct_t(p, (const __half *)sino, img, batch, accumulate, st, wuni);
+        case BP_F32: return launch_direct_t(p, (const float *)sino, img, batch, accumulate, st, wuni, shape);
+        case BP_BF16:
+            return launch_direct_t(p, (const __nv_bfloat16 *)sino, img, batch, accumulate, st, wuni, shape);
+        case BP_F16: return launch_direct_t(p, (const __half *)sino, img, batch, accumulate, st, wuni, shape);
     }
     return fail(BP_ERR_INVALID_ARG, "invalid dtype");
+}
+
+bp_status launch_direct(bp_plan *p, const void *sino, bp_dtype dt, float *img, int batch, int accumulate,
+                        cudaStream_t st, float wuni) {
+    return launch_direct_shape(p, sino, dt, img, batch, accumulate, st, wuni, direct_shape(p, dt, batch));
+}
+
+DirectShape direct_clamp(const bp_plan *p, bp_dtype dt, DirectShape shape) {
+    const int esz = dt == BP_F32 ? 4 : 2;
+    return direct_effective(p, esz, tensor_map_encoder() != nullptr && tma_eligible(p, esz), shape);
+}
+
+DirectShape direct_shape_used(const bp_plan *p, bp_dtype dt, int batch) {
+    return direct_clamp(p, dt, direct_shape(p, dt, batch));
+}
+
+// Largest useful angle split: every group keeps at least one stage, and the grid's y
+// dimension (tiles x asplit) stays within 65535.
+int direct_max_asplit(const bp_plan *p, int stage) {
+    const int tiles = (p->N + kTile - 1) / kTile;
+    const int S = (p->n_theta + stage - 1) / stage;
+    return std::max(1, std::min(S, 65535 / tiles));
 }
 
 }  // namespace bp

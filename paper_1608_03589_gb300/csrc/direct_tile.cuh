@@ -16,12 +16,14 @@ struct DirectStageSmem {
     float w[kStage];
 };
 
+// Angles [k_begin, k_end) of tile (tx, ty); the partial sum is added atomically when
+// atomic_out (angle-split launches), else stored (or added, with accumulate).
 // tab: kStage * W float2 of shared memory.  All threads of the block must call it.
 template <typename Tin>
 __device__ __forceinline__ void direct_tile_sync(const Tin *__restrict__ sino, float *__restrict__ img,
-                                                 const AngleParam *__restrict__ ap, int N, int n_det, int n_theta,
-                                                 int W, int C, int tx, int ty, int accumulate, float wuni,
-                                                 float2 *tab, DirectStageSmem &sm) {
+                                                 const AngleParam *__restrict__ ap, int N, int n_det, int k_begin,
+                                                 int k_end, int W, int C, int tx, int ty, int accumulate,
+                                                 int atomic_out, float wuni, float2 *tab, DirectStageSmem &sm) {
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     const int lx = lane & 7;
@@ -36,8 +38,8 @@ __device__ __forceinline__ void direct_tile_sync(const Tin *__restrict__ sino, f
     const float fx = (float)lx, fy = (float)ly;
     const unsigned tab_u32 = smem_u32(tab);
 
-    for (int k0 = 0; k0 < n_theta; k0 += kStage) {
-        const int kn = min(kStage, n_theta - k0);
+    for (int k0 = k_begin; k0 < k_end; k0 += kStage) {
+        const int kn = min(kStage, k_end - k0);
         __syncthreads();
         if (tid < kn) {
             const AngleParam p = ap[k0 + tid];
@@ -97,7 +99,8 @@ __device__ __forceinline__ void direct_tile_sync(const Tin *__restrict__ sino, f
             const int x = tx * kTile + lx + 8 * a;
             if (x < N && y < N) {
                 float *dst = img + (long long)y * N + x;
-                *dst = accumulate ? (*dst + acc[b][a]) : acc[b][a];
+                if (atomic_out) atomicAdd(dst, acc[b][a]);
+                else *dst = accumulate ? (*dst + acc[b][a]) : acc[b][a];
             }
         }
     }

@@ -7,7 +7,8 @@
 // barriers per pass separate the loads from the stores, so the transform runs in place.
 // Natural order in, natural order out.  Forward = exp(-2 pi i jk/P), inverse = exp(+...),
 // both unnormalised.  Twiddles: tw[r] = exp(-2 pi i r / P0), r < P0/2, built in FP64 on the
-// host for a length P0 >= P (both powers of two); the transform reads stride P0/P.
+// host for a length P0 >= P (both powers of two) and staged in shared memory; the transform
+// reads stride P0/P.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -24,9 +25,10 @@ __device__ __forceinline__ float2 cmulc(float2 a, float2 b) {  // a * conj(b)
 }
 
 // exp(-+2 pi i r / P) from the half table (r in [0, P)), sign: forward (-) or inverse (+).
-__device__ __forceinline__ float2 twiddle(const float2 *__restrict__ tw, int r, int logP, int twstride, bool inverse) {
+// The table lives in shared memory (stage_twiddles), next to the transformed rows.
+__device__ __forceinline__ float2 twiddle(const float2 *tw, int r, int logP, int twstride, bool inverse) {
     const int half = 1 << (logP - 1);
-    float2 w = __ldg(tw + (r & (half - 1)) * twstride);
+    float2 w = tw[(r & (half - 1)) * twstride];
     if (r & half) w = make_float2(-w.x, -w.y);
     if (inverse) w.y = -w.y;
     return w;
@@ -80,11 +82,26 @@ __device__ __forceinline__ void dft_reg(float2 (&a)[R], bool inverse) {
     }
 }
 
+// Shared-memory bank swizzle of the intermediate passes.  A float2 covers two of the 32
+// banks, so a half warp is conflict-free when its 16 indices differ mod 16.  The stores of
+// the first passes go to stride-R indices (and, for radix 8, to groups of 8 contiguous
+// entries 8 R apart), which all fall on a few banks; XOR-ing the low four index bits with a
+// function of the 16-entry row spreads them over all banks, while contiguous runs of 16
+// stay contiguous within their row.  The first pass reads and the last pass writes the
+// plain layout, so callers never see the swizzle.
+template <int E>
+__device__ __forceinline__ int fft_swz(int i) {
+    const int row = i >> 4;
+    const int f = (E >= 16) ? (row & 15) : ((row & 7) | ((row & 4) << 1));
+    return i ^ f;
+}
+
 // One Stockham pass of radix R over sub-transforms of length L (L R <= P).  Each of the nthr
 // threads handles G = E / R butterfly groups (E elements per thread); nthr = P / E.
+// in_sw / out_sw: the input / output array uses the swizzled layout.
 template <int R, int E>
-__device__ __forceinline__ void stockham_pass(float2 *z, int logP, int L, const float2 *__restrict__ tw, int twstride,
-                                              bool inverse, int tid, int nthr) {
+__device__ __forceinline__ void stockham_pass(float2 *z, int logP, int L, const float2 *tw, int twstride,
+                                              bool inverse, int tid, int nthr, bool in_sw, bool out_sw) {
     constexpr int G = E / R;
     const int P = 1 << logP;
     const int m = P / R;
@@ -94,7 +111,10 @@ __device__ __forceinline__ void stockham_pass(float2 *z, int logP, int L, const 
         const int t = tid + g * nthr;
         if (t < m) {
 #pragma unroll
-            for (int r = 0; r < R; ++r) a[g][r] = z[t + r * m];
+            for (int r = 0; r < R; ++r) {
+                const int i = t + r * m;
+                a[g][r] = z[in_sw ? fft_swz<E>(i) : i];
+            }
         }
     }
     __syncthreads();
@@ -111,7 +131,10 @@ __device__ __forceinline__ void stockham_pass(float2 *z, int logP, int L, const 
             dft_reg<R>(a[g], inverse);
             const int base = j * L * R + k;
 #pragma unroll
-            for (int q = 0; q < R; ++q) z[base + q * L] = a[g][q];
+            for (int q = 0; q < R; ++q) {
+                const int i = base + q * L;
+                z[out_sw ? fft_swz<E>(i) : i] = a[g][q];
+            }
         }
     }
     __syncthreads();
@@ -126,31 +149,34 @@ __host__ __device__ inline int fft_threads(int P) {
 }
 
 template <int E>
-__device__ __forceinline__ void stockham_fft_e(float2 *z, int logP, const float2 *__restrict__ tw, int twstride,
+__device__ __forceinline__ void stockham_fft_e(float2 *z, int logP, const float2 *tw, int twstride,
                                                bool inverse, int tid, int nthr) {
     int L = 1, rem = logP;
+    bool in_sw = false;
     while (rem > 0) {
         if constexpr (E >= 16) {
             if (rem >= 4) {
-                stockham_pass<16, E>(z, logP, L, tw, twstride, inverse, tid, nthr);
+                stockham_pass<16, E>(z, logP, L, tw, twstride, inverse, tid, nthr, in_sw, rem > 4);
                 L <<= 4;
                 rem -= 4;
+                in_sw = true;
                 continue;
             }
         }
         if (rem >= 3) {
-            stockham_pass<8, E>(z, logP, L, tw, twstride, inverse, tid, nthr);
+            stockham_pass<8, E>(z, logP, L, tw, twstride, inverse, tid, nthr, in_sw, rem > 3);
             L <<= 3;
             rem -= 3;
         } else if (rem == 2) {
-            stockham_pass<4, E>(z, logP, L, tw, twstride, inverse, tid, nthr);
+            stockham_pass<4, E>(z, logP, L, tw, twstride, inverse, tid, nthr, in_sw, false);
             L <<= 2;
             rem -= 2;
         } else {
-            stockham_pass<2, E>(z, logP, L, tw, twstride, inverse, tid, nthr);
+            stockham_pass<2, E>(z, logP, L, tw, twstride, inverse, tid, nthr, in_sw, false);
             L <<= 1;
             rem -= 1;
         }
+        in_sw = true;
     }
 }
 
@@ -159,9 +185,15 @@ __device__ __forceinline__ void stockham_fft_e(float2 *z, int logP, const float2
 // barriers inside: several groups can transform several arrays of the same length
 // together).  z ends synchronised.
 template <int E>
-__device__ __forceinline__ void stockham_fft(float2 *z, int logP, const float2 *__restrict__ tw, int twstride,
+__device__ __forceinline__ void stockham_fft(float2 *z, int logP, const float2 *tw, int twstride,
                                              bool inverse, int tid, int nthr) {
     stockham_fft_e<E>(z, logP, tw, twstride, inverse, tid, nthr);
+}
+
+// Copy n twiddles from global to shared memory (all threads of the block; a block barrier
+// must separate it from the first transform).
+__device__ __forceinline__ void stage_twiddles(float2 *dst, const float2 *__restrict__ src, int n) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = __ldg(src + i);
 }
 
 __device__ __forceinline__ int bitrev(int v, int logP) { return (int)(__brev((unsigned)v) >> (32 - logP)); }

@@ -23,6 +23,8 @@ filter_kernel(const Tin *__restrict__ in, float *__restrict__ out, const float *
               const float2 *__restrict__ tw, long long rows, int n_det, int logP) {
     extern __shared__ __align__(16) float2 z[];
     const int P = 1 << logP;
+    float2 *tws = z + P;  // P/2 twiddles
+    stage_twiddles(tws, tw, P / 2);
     const long long r0 = 2 * (long long)blockIdx.x, r1 = r0 + 1;
     const bool has1 = r1 < rows;
     const Tin *a = in + r0 * n_det;
@@ -36,14 +38,14 @@ filter_kernel(const Tin *__restrict__ in, float *__restrict__ out, const float *
         z[j] = make_float2(va, vb);
     }
     __syncthreads();
-    stockham_fft<E>(z, logP, tw, 1, false, threadIdx.x, blockDim.x);
+    stockham_fft<E>(z, logP, tws, 1, false, threadIdx.x, blockDim.x);
     for (int j = threadIdx.x; j < P; j += blockDim.x) {
         const float h = __ldg(H + j);
         const float2 v = z[j];
         z[j] = make_float2(v.x * h, v.y * h);
     }
     __syncthreads();
-    stockham_fft<E>(z, logP, tw, 1, true, threadIdx.x, blockDim.x);
+    stockham_fft<E>(z, logP, tws, 1, true, threadIdx.x, blockDim.x);
     float *oa = out + r0 * n_det;
     float *ob = out + r1 * n_det;
     for (int j = threadIdx.x; j < n_det; j += blockDim.x) {
@@ -113,14 +115,14 @@ bp_status ensure_filter(bp_plan *p, int kind, float param) {
 
 bp_status launch_filter(bp_plan *p, const void *in, bp_dtype dt, float *out, int kind, float param, int batch,
                         cudaStream_t st) {
-    if ((size_t)p->P * sizeof(float2) > 200u * 1024u)
+    if ((size_t)(p->P + p->P / 2) * sizeof(float2) > 200u * 1024u)
         return fail(BP_ERR_UNSUPPORTED, "filter: n_det too large for the shared-memory FFT (n_det <= 8192)");
     bp_status s = ensure_filter(p, kind, param);
     if (s != BP_OK) return s;
     const long long rows = (long long)batch * p->n_theta;
     const int logP = ilog2(p->P);
     const int threads = fft_threads(p->P);
-    const size_t smem = sizeof(float2) * p->P;
+    const size_t smem = sizeof(float2) * (p->P + p->P / 2);
     const unsigned blocks = (unsigned)((rows + 1) / 2);
 #define BP_FILTER_LAUNCH(T)                                                                               \
     do {                                                                                                  \
@@ -149,12 +151,12 @@ bp_status launch_filter(bp_plan *p, const void *in, bp_dtype dt, float *out, int
 // Row filter with a caller-supplied response (P floats, natural order, already scaled by dt/P).
 bp_status launch_filter_response(bp_plan *p, const void *in, bp_dtype dt, float *out, const float *H, int batch,
                                  cudaStream_t st) {
-    if ((size_t)p->P * sizeof(float2) > 200u * 1024u)
+    if ((size_t)(p->P + p->P / 2) * sizeof(float2) > 200u * 1024u)
         return fail(BP_ERR_UNSUPPORTED, "filter: n_det too large for the shared-memory FFT (n_det <= 8192)");
     const long long rows = (long long)batch * p->n_theta;
     const int logP = ilog2(p->P);
     const int threads = fft_threads(p->P);
-    const size_t smem = sizeof(float2) * p->P;
+    const size_t smem = sizeof(float2) * (p->P + p->P / 2);
     const unsigned blocks = (unsigned)((rows + 1) / 2);
 #define BP_FILTER_LAUNCH_H(T)                                                                             \
     do {                                                                                                  \

@@ -44,6 +44,7 @@ constexpr int kCore = 32;         // cells with max(|u_x|, |u_y|) < kCore are ga
 struct SortedRay {                // one ray, in increasing angle order
     long long ax, ay;             // rho cos(phi), rho sin(phi) in 32.32 fixed point (grid cells per sample)
     float isx, isy;               // 1 / (rho cos), 1 / (rho sin) (infinite for a zero component)
+    float sx, sy;                 // ax, ay as float (per-sample steps)
     int k;                        // original projection index
     int pad;
 };
@@ -74,6 +75,8 @@ fourier_spectra_kernel(const Tin *__restrict__ sino, float2 *__restrict__ spec, 
                        const long long *__restrict__ ray, float delta2_over_M) {
     extern __shared__ __align__(128) float2 z[];
     const int P = 1 << logP, H = P >> 1;
+    float2 *tws = z + P;  // P/2 twiddles
+    stage_twiddles(tws, tw, H);
     const int k0 = 2 * blockIdx.x, k1 = k0 + 1;
     const bool has1 = k1 < n_theta;
     const Tin *a = sino + (long long)k0 * n_det;
@@ -87,7 +90,7 @@ fourier_spectra_kernel(const Tin *__restrict__ sino, float2 *__restrict__ spec, 
         z[j] = make_float2(va, vb);
     }
     __syncthreads();
-    stockham_fft<E>(z, logP, tw, 1, false, threadIdx.x, blockDim.x);
+    stockham_fft<E>(z, logP, tws, 1, false, threadIdx.x, blockDim.x);
     // A[m] = (Z[m] + conj Z[P-m]) / 2,  B[m] = (Z[m] - conj Z[P-m]) / (2i)
     const float wa = (wuni > 0.f ? wuni : __ldg(wk + k0)) / (float)P;
     const float wb = has1 ? (wuni > 0.f ? wuni : __ldg(wk + k1)) / (float)P : 0.f;
@@ -174,7 +177,7 @@ __device__ __forceinline__ float2 gather_rays(const float2 *__restrict__ spec, c
         const long long zx = (long long)m0 * r.ax, zy = (long long)m0 * r.ay;
         const float dx0 = (float)(ux - (int)(zx >> 32)) - (float)(unsigned)(zx & 0xffffffffLL) * 2.3283064365386963e-10f;
         const float dy0 = (float)(uy - (int)(zy >> 32)) - (float)(unsigned)(zy & 0xffffffffLL) * 2.3283064365386963e-10f;
-        const float sx = (float)((double)r.ax * 2.3283064365386963e-10), sy = (float)((double)r.ay * 2.3283064365386963e-10);
+        const float sx = r.sx, sy = r.sy;
         for (int m = m0; m <= m1; ++m) {
             const float t = (float)(m - m0);
             const float dx = fmaf(-t, sx, dx0), dy = fmaf(-t, sy, dy0);
@@ -200,8 +203,16 @@ grid_gather_kernel(const float2 *__restrict__ spec, const SortedRay *__restrict_
     const int cx = lx < M / 2 ? lx : lx - M, cy = ly < M / 2 ? ly : ly - M;
     if (max(abs(cx), abs(cy)) < kCore) return;  // the core kernel owns this cell
     float2 acc = make_float2(0.f, 0.f);
-    for (int a = -amax; a <= amax; ++a) {
-        for (int b = -amax; b <= amax; ++b) {
+    // periodic images u = c + (a, b) M whose footprint box can reach the sample disc
+    // |z| <= rmax; with every ray in the upper half plane (z_y >= 0) also u_y > -3
+    const float lim = rmax + 3.f, iM = 1.f / (float)M;
+    const int a_lo = max(-amax, (int)ceilf((-lim - (float)cx) * iM));
+    const int a_hi = min(amax, (int)floorf((lim - (float)cx) * iM));
+    int b_lo = max(-amax, (int)ceilf((-lim - (float)cy) * iM));
+    if (ri.upper) b_lo = max(b_lo, (int)ceilf((-2.f - (float)cy) * iM));
+    const int b_hi = min(amax, (int)floorf((lim - (float)cy) * iM));
+    for (int a = a_lo; a <= a_hi; ++a) {
+        for (int b = b_lo; b <= b_hi; ++b) {
             const int ux = cx + a * M, uy = cy + b * M;
             // skip images whose box cannot reach the sample disk |z| <= rmax
             const float qx = fmaxf(0.f, fmaxf((float)ux - 3.f, -3.f - (float)ux));
@@ -231,6 +242,7 @@ grid_gather_core_kernel(const float2 *__restrict__ spec, const SortedRay *__rest
     for (int a = -amax; a <= amax; ++a) {
         for (int b = -amax; b <= amax; ++b) {
             const int ux = cx + a * M, uy = cy + b * M;
+            if (ri.upper && uy <= -3) continue;  // no sample has z_y < u_y + 3
             const float qx = fmaxf(0.f, fmaxf((float)ux - 3.f, -3.f - (float)ux));
             const float qy = fmaxf(0.f, fmaxf((float)uy - 3.f, -3.f - (float)uy));
             if (qx * qx + qy * qy > rmax * rmax) continue;
@@ -276,11 +288,13 @@ ifft_pass_y_kernel(const float2 *__restrict__ grid, float2 *__restrict__ inter, 
                    const float2 *__restrict__ tw, int M, int logM, int N, int R, int *__restrict__ err) {
     extern __shared__ __align__(128) float2 z[];
     __shared__ __align__(8) unsigned long long bar;
+    float2 *tws = z + R * M;  // M/2 twiddles
+    stage_twiddles(tws, tw, M / 2);
     const int lx0 = blockIdx.x * R;
     const int nthr = fft_threads(M), groups = blockDim.x / nthr;
     const int g = threadIdx.x / nthr, tid = threadIdx.x - g * nthr;
     if (!load_rows_async(z, grid + (long long)lx0 * M, R * M, &bar) && threadIdx.x == 0) atomicExch(err, 1);
-    for (int r0 = 0; r0 < R; r0 += groups) stockham_fft<E>(z + (r0 + g) * M, logM, tw, 1, true, tid, nthr);
+    for (int r0 = 0; r0 < R; r0 += groups) stockham_fft<E>(z + (r0 + g) * M, logM, tws, 1, true, tid, nthr);
     const int h = N / 2;
     for (int i = threadIdx.x; i < N * R; i += blockDim.x) {
         const int iy = i / R, r = i - iy * R;
@@ -298,13 +312,15 @@ ifft_pass_x_kernel(const float2 *__restrict__ inter, float *__restrict__ img, co
                    const float2 *__restrict__ tw, int M, int logM, int N, int R, int *__restrict__ err) {
     extern __shared__ __align__(128) float2 z[];
     __shared__ __align__(8) unsigned long long bar;
+    float2 *tws = z + R * M;  // M/2 twiddles
+    stage_twiddles(tws, tw, M / 2);
     const int iy0 = blockIdx.x * R;
     const int rows = min(R, N - iy0);
     const int nthr = fft_threads(M), groups = blockDim.x / nthr;
     const int g = threadIdx.x / nthr, tid = threadIdx.x - g * nthr;
     if (!load_rows_async(z, inter + (long long)iy0 * M, rows * M, &bar) && threadIdx.x == 0) atomicExch(err, 1);
     // rows beyond the last image row hold stale data that is transformed but never written out
-    for (int r0 = 0; r0 < R; r0 += groups) stockham_fft<E>(z + (r0 + g) * M, logM, tw, 1, true, tid, nthr);
+    for (int r0 = 0; r0 < R; r0 += groups) stockham_fft<E>(z + (r0 + g) * M, logM, tws, 1, true, tid, nthr);
     const int h = N / 2;
     for (int i = threadIdx.x; i < rows * N; i += blockDim.x) {
         const int r = i / N, ix = i - r * N;
@@ -327,6 +343,8 @@ __global__ void __launch_bounds__(1024, 1)
 adj_fft_x_kernel(const float *__restrict__ img, float2 *__restrict__ T, const float *__restrict__ deap,
                  const float2 *__restrict__ tw, int M, int logM, int N, int R) {
     extern __shared__ __align__(128) float2 z[];
+    float2 *tws = z + R * M;  // M/2 twiddles
+    stage_twiddles(tws, tw, M / 2);
     const int iy0 = blockIdx.x * R;
     const int rows = min(R, N - iy0);
     const int nthr = fft_threads(M), groups = blockDim.x / nthr;
@@ -340,7 +358,7 @@ adj_fft_x_kernel(const float *__restrict__ img, float2 *__restrict__ T, const fl
         z[r * M + ((ix - h) & (M - 1))] = make_float2(v, 0.f);
     }
     __syncthreads();
-    for (int r0 = 0; r0 < R; r0 += groups) stockham_fft<E>(z + (r0 + g) * M, logM, tw, 1, false, tid, nthr);
+    for (int r0 = 0; r0 < R; r0 += groups) stockham_fft<E>(z + (r0 + g) * M, logM, tws, 1, false, tid, nthr);
     for (int i = threadIdx.x; i < rows * M; i += blockDim.x) T[(long long)iy0 * M + i] = z[i];
 }
 
@@ -351,6 +369,8 @@ __global__ void __launch_bounds__(1024, 1)
 adj_fft_y_kernel(const float2 *__restrict__ T, float2 *__restrict__ grid, const float2 *__restrict__ tw, int M,
                  int logM, int N, int R) {
     extern __shared__ __align__(128) float2 z[];
+    float2 *tws = z + R * M;  // M/2 twiddles
+    stage_twiddles(tws, tw, M / 2);
     const int lx0 = blockIdx.x * R;
     const int nthr = fft_threads(M), groups = blockDim.x / nthr;
     const int g = threadIdx.x / nthr, tid = threadIdx.x - g * nthr;
@@ -362,7 +382,7 @@ adj_fft_y_kernel(const float2 *__restrict__ T, float2 *__restrict__ grid, const 
         z[r * M + ((iy - h) & (M - 1))] = T[(long long)iy * M + lx0 + r];
     }
     __syncthreads();
-    for (int r0 = 0; r0 < R; r0 += groups) stockham_fft<E>(z + (r0 + g) * M, logM, tw, 1, false, tid, nthr);
+    for (int r0 = 0; r0 < R; r0 += groups) stockham_fft<E>(z + (r0 + g) * M, logM, tws, 1, false, tid, nthr);
     for (int i = threadIdx.x; i < R * M; i += blockDim.x) grid[(long long)lx0 * M + i] = z[i];
 }
 
@@ -417,6 +437,8 @@ adj_rows_kernel(const float2 *__restrict__ spec, float *__restrict__ sino, const
                 int n_theta, int n_det, int logP) {
     extern __shared__ __align__(128) float2 z[];
     const int P = 1 << logP, H = P >> 1;
+    float2 *tws = z + P;  // P/2 twiddles
+    stage_twiddles(tws, tw, H);
     const int k0 = 2 * blockIdx.x, k1 = k0 + 1;
     const bool has1 = k1 < n_theta;
     const float2 *sa = spec + (long long)k0 * H, *sb = spec + (long long)k1 * H;
@@ -439,7 +461,7 @@ adj_rows_kernel(const float2 *__restrict__ spec, float *__restrict__ sino, const
         z[m] = make_float2(ha.x - hb.y, ha.y + hb.x);  // H_a + i H_b
     }
     __syncthreads();
-    stockham_fft<E>(z, logP, tw, 1, true, threadIdx.x, blockDim.x);
+    stockham_fft<E>(z, logP, tws, 1, true, threadIdx.x, blockDim.x);
     for (int j = threadIdx.x; j < n_det; j += blockDim.x) {
         sino[(long long)k0 * n_det + j] = 0.5f * z[j].x;
         if (has1) sino[(long long)k1 * n_det + j] = 0.5f * z[j].y;
@@ -515,6 +537,8 @@ bp_status ensure_fourier(bp_plan *p) {
         const double sxd = std::ldexp((double)ray[2 * k], -32), syd = std::ldexp((double)ray[2 * k + 1], -32);
         sray[i].isx = sxd != 0.0 ? (float)(1.0 / sxd) : INFINITY;
         sray[i].isy = syd != 0.0 ? (float)(1.0 / syd) : INFINITY;
+        sray[i].sx = (float)sxd;
+        sray[i].sy = (float)syd;
         sray[i].k = k;
         sray[i].pad = 0;
         // the float angle must stay sorted and in [0, 2 pi) after rounding
@@ -523,6 +547,9 @@ bp_status ensure_fourier(bp_plan *p) {
     }
     // uniform spacing of the sorted angles gives an O(1) index lookup
     f.ri.n = n_theta;
+    f.ri.upper = 1;
+    for (int k = 0; k < n_theta; ++k)
+        if (ray[2 * k + 1] < 0) f.ri.upper = 0;
     f.ri.uniform = 0;
     if (n_theta > 1) {
         const double d = (order[n_theta - 1].first - order[0].first) / (n_theta - 1);
@@ -594,7 +621,7 @@ bp_status ensure_fourier(bp_plan *p) {
 template <typename Tin>
 static bp_status spectra_t(bp_plan *p, const Tin *sino, cudaStream_t st, float wuni, float delta2) {
     const int logP = ilog2(p->P);
-    const size_t smem = sizeof(float2) * p->P;
+    const size_t smem = sizeof(float2) * (p->P + p->P / 2);
     const int threads = fft_threads(p->P);
     auto kern = fft_elems(p->P) == 16 ? fourier_spectra_kernel<Tin, 16> : fourier_spectra_kernel<Tin, 8>;
     BP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -613,7 +640,7 @@ bp_status launch_fourier(bp_plan *p, const void *sino, bp_dtype dt, float *img, 
     const int N = p->N, M = f.M, H = p->P / 2;
     const size_t esz = dt == BP_F32 ? 4 : 2;
     const int R = rows_per_cta(M);
-    const size_t smemR = sizeof(float2) * (size_t)R * M;
+    const size_t smemR = sizeof(float2) * ((size_t)R * M + M / 2);
     auto pass_y = fft_elems(M) == 16 ? ifft_pass_y_kernel<16> : ifft_pass_y_kernel<8>;
     auto pass_x = fft_elems(M) == 16 ? ifft_pass_x_kernel<16> : ifft_pass_x_kernel<8>;
     BP_CUDA_TRY(cudaFuncSetAttribute(pass_y, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smemR));
@@ -657,7 +684,7 @@ bp_status launch_radon_fourier(bp_plan *p, const float *img, float *sino, int ba
     FourierWork &f = p->four;
     const int N = p->N, M = f.M, P = p->P, H = P / 2;
     const int R = rows_per_cta(M);
-    const size_t smemR = sizeof(float2) * (size_t)R * M;
+    const size_t smemR = sizeof(float2) * ((size_t)R * M + M / 2);
     const int nthr = fft_threads(M);
     int groups = 1;
     while (groups * 2 <= R && nthr * groups * 2 <= 1024) groups *= 2;
@@ -667,7 +694,7 @@ bp_status launch_radon_fourier(bp_plan *p, const float *img, float *sino, int ba
     auto kr = fft_elems(P) == 16 ? adj_rows_kernel<16> : adj_rows_kernel<8>;
     BP_CUDA_TRY(cudaFuncSetAttribute(kx, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smemR));
     BP_CUDA_TRY(cudaFuncSetAttribute(ky, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smemR));
-    BP_CUDA_TRY(cudaFuncSetAttribute(kr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(float2) * P)));
+    BP_CUDA_TRY(cudaFuncSetAttribute(kr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(float2) * (P + P / 2))));
     const float delta2 = (N % 2 == 0) ? 1.0f / (float)M : 0.0f;
     const float scale = (float)(p->dx * p->dx / p->dt);
     for (int b = 0; b < batch; ++b) {
@@ -677,7 +704,7 @@ bp_status launch_radon_fourier(bp_plan *p, const float *img, float *sino, int ba
         adj_interp_kernel<<<dim3((H + 255) / 256, p->n_theta), 256, 0, st>>>(f.grid, f.spec, f.ray, M, H, P, p->n_det,
                                                                               f.kbtab, delta2, scale,
                                                                               per_angle_w ? f.wk : nullptr);
-        kr<<<(p->n_theta + 1) / 2, fft_threads(P), sizeof(float2) * P, st>>>(
+        kr<<<(p->n_theta + 1) / 2, fft_threads(P), sizeof(float2) * (P + P / 2), st>>>(
             f.spec, sino + (size_t)b * p->n_theta * p->n_det, p->d_twP, p->n_theta, p->n_det, ilog2(P));
         BP_CUDA_TRY(cudaGetLastError());
     }

@@ -133,6 +133,8 @@ extern "C" bp_plan *bp_plan_create(int N, int n_det, int n_theta, const double *
     p->N = N; p->n_det = n_det; p->n_theta = n_theta;
     p->dt = det_spacing; p->dx = 2.0 / N;
     if (cudaGetDevice(&p->device) != cudaSuccess) { fail(BP_ERR_CUDA, "cudaGetDevice failed"); delete p; return nullptr; }
+    if (cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess)
+        p->sm_count = 0;
     p->theta.assign(theta, theta + n_theta);
     angle_weights(p->theta, p->w);
 

@@ -31,6 +31,7 @@ constexpr int kMagicInt = 0x4B400000;
 constexpr int kRThreads = 256;
 constexpr int kRWarps = kRThreads / 32;
 constexpr int kAngMax = 4;
+constexpr size_t kMaxRadonSmem = 200 * 1024;
 
 __global__ void __launch_bounds__(kRThreads, 2)
 radon_direct_kernel(const float *__restrict__ img, float *__restrict__ sino, const AngleParam *__restrict__ ap,
@@ -190,20 +191,58 @@ radon_direct_kernel(const float *__restrict__ img, float *__restrict__ sino, con
 
 }  // namespace
 
-bp_status launch_radon_direct(bp_plan *p, const float *img, float *sino, int batch, cudaStream_t st, int per_angle_w) {
-    const size_t sino_n = (size_t)p->n_theta * p->n_det;
+size_t radon_smem(const bp_plan *p, int kAng) {
+    return sizeof(float) * ((((size_t)kAng * p->n_det + 3) & ~(size_t)3) + kTile * (kTile + 1)) +
+           sizeof(float2) * (size_t)kRWarps * kAng * p->W;
+}
+
+int radon_max_kang(const bp_plan *p) {
+    int kAng = kAngMax;
+    while (kAng > 1 && radon_smem(p, kAng) > kMaxRadonSmem) kAng >>= 1;
+    return kAng;
+}
+
+// The shape a launch really uses (defaults resolved, values clamped); bands is the number
+// of bands after rounding the tiles per band up.
+RadonShape radon_effective(const bp_plan *p, RadonShape shape) {
     const int tiles = (p->N + kTile - 1) / kTile;
     const int ntiles = tiles * tiles;
     int kAng = kAngMax;
-    while (kAng > 1 && (size_t)kAng * p->n_det * 4 > 64 * 1024) kAng >>= 1;
-    const size_t smem = sizeof(float) * ((((size_t)kAng * p->n_det + 3) & ~(size_t)3) + kTile * (kTile + 1)) +
-                        sizeof(float2) * (size_t)kRWarps * kAng * p->W;
-    if (smem > 200 * 1024) return fail(BP_ERR_UNSUPPORTED, "radon: n_det or window too large for shared memory");
-    // bands: enough CTAs to fill the GPU about twice, at most one band per tile
+    if (shape.kang == 1 || shape.kang == 2 || shape.kang == 4) {
+        kAng = shape.kang;
+    } else {  // default: detector rows of the block's angles within 64 KB
+        while (kAng > 1 && (size_t)kAng * p->n_det * 4 > 64 * 1024) kAng >>= 1;
+    }
+    kAng = std::min(kAng, radon_max_kang(p));
     const int ablocks = (p->n_theta + kAng - 1) / kAng;
-    int bands = std::max(1, std::min(ntiles, (2 * 152 * 2 + ablocks - 1) / ablocks));
+    int bands = shape.bands;
+    if (bands <= 0) {
+        // default: enough CTAs to fill the GPU about twice (2 CTAs per SM)
+        const int target = 2 * 2 * std::max(1, p->sm_count);
+        bands = (target + ablocks - 1) / ablocks;
+    }
+    bands = std::max(1, std::min(ntiles, bands));
     const int per_band = (ntiles + bands - 1) / bands;
-    bands = (ntiles + per_band - 1) / per_band;
+    RadonShape e;
+    e.kang = kAng;
+    e.bands = (ntiles + per_band - 1) / per_band;
+    return e;
+}
+
+RadonShape radon_clamp(const bp_plan *p, RadonShape shape) { return radon_effective(p, shape); }
+RadonShape radon_shape_used(const bp_plan *p, int batch) { return radon_effective(p, radon_shape(p, batch)); }
+
+bp_status launch_radon_shape(bp_plan *p, const float *img, float *sino, int batch, cudaStream_t st, int per_angle_w,
+                             RadonShape shape) {
+    const size_t sino_n = (size_t)p->n_theta * p->n_det;
+    const int tiles = (p->N + kTile - 1) / kTile;
+    const int ntiles = tiles * tiles;
+    const RadonShape eff = radon_effective(p, shape);
+    const int kAng = eff.kang, bands = eff.bands;
+    const size_t smem = radon_smem(p, kAng);
+    if (smem > kMaxRadonSmem) return fail(BP_ERR_UNSUPPORTED, "radon: n_det or window too large for shared memory");
+    const int ablocks = (p->n_theta + kAng - 1) / kAng;
+    const int per_band = (ntiles + bands - 1) / bands;
     const int use_atomic = bands > 1;
     if (use_atomic) BP_CUDA_TRY(cudaMemsetAsync(sino, 0, sizeof(float) * sino_n * batch, st));
     BP_CUDA_TRY(cudaFuncSetAttribute(radon_direct_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -214,6 +253,10 @@ bp_status launch_radon_direct(bp_plan *p, const float *img, float *sino, int bat
                                                        (long long)sino_n, per_angle_w);
     BP_CUDA_TRY(cudaGetLastError());
     return BP_OK;
+}
+
+bp_status launch_radon_direct(bp_plan *p, const float *img, float *sino, int batch, cudaStream_t st, int per_angle_w) {
+    return launch_radon_shape(p, img, sino, batch, st, per_angle_w, radon_shape(p, batch));
 }
 
 }  // namespace bp

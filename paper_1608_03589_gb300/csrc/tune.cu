@@ -1,0 +1,322 @@
+// Launch-shape autotuner and tuning cache of the direct R* and R kernels.
+//
+// Neither operator's result depends on the shape; only how the work is spread over the GPU
+// does.  The direct R* has two knobs: the angles per shared-memory stage (8, 16 or 32: more
+// angles per block barrier and per TMA batch against more shared memory per CTA, hence
+// fewer resident CTAs) and the number of angle groups per pixel tile (more CTAs for images
+// with few 64 x 64 tiles, paid for with atomic partial-sum adds).  The direct R has the
+// angles per CTA (1, 2 or 4: each pixel read serves more angles against more shared memory)
+// and the image bands per angle block (parallelism against atomic adds into the sinogram).
+//
+// bp_autotune times every candidate with CUDA events on the caller's stream and keeps the
+// fastest per (op, dtype, batch) in the plan and in a process-wide cache keyed by the
+// geometry and the SM count, which can be saved to and merged from a text file.
+#include <algorithm>
+#include <cstdio>
+#include <map>
+#include <mutex>
+#include <tuple>
+
+#include "common.cuh"
+
+namespace bp {
+
+namespace {
+
+using CacheKey = std::tuple<int, int, int, int, int, int, int, int>;  // op dtype batch N n_det n_theta W sm
+std::mutex g_cache_mu;
+std::map<CacheKey, std::pair<int, int>> g_cache;
+
+int norm_dtype(int op, int dtype) { return op == BP_OP_RADON ? 0 : dtype; }
+
+CacheKey cache_key(const bp_plan *p, int op, int dtype, int batch) {
+    return CacheKey{op, norm_dtype(op, dtype), batch, p->N, p->n_det, p->n_theta, p->W, p->sm_count};
+}
+
+bool lookup(const bp_plan *p, int op, int dtype, int batch, int v[2]) {
+    const int dt = norm_dtype(op, dtype);
+    for (const TuneEntry &e : p->shapes)
+        if (e.op == op && e.dtype == dt && e.batch == batch) {
+            v[0] = e.v[0];
+            v[1] = e.v[1];
+            return true;
+        }
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    auto it = g_cache.find(cache_key(p, op, dtype, batch));
+    if (it == g_cache.end()) return false;
+    v[0] = it->second.first;
+    v[1] = it->second.second;
+    return true;
+}
+
+void store(bp_plan *p, int op, int dtype, int batch, const int v[2], bool to_cache) {
+    const int dt = norm_dtype(op, dtype);
+    bool found = false;
+    for (TuneEntry &e : p->shapes)
+        if (e.op == op && e.dtype == dt && e.batch == batch) {
+            e.v[0] = v[0];
+            e.v[1] = v[1];
+            found = true;
+        }
+    if (!found) p->shapes.push_back(TuneEntry{op, dt, batch, {v[0], v[1]}});
+    if (to_cache) {
+        std::lock_guard<std::mutex> lk(g_cache_mu);
+        g_cache[cache_key(p, op, dtype, batch)] = {v[0], v[1]};
+    }
+}
+
+int tiles_of(const bp_plan *p) { return (p->N + kTile - 1) / kTile; }
+
+// Default direct shape: 16 angles per stage; angle groups so that the grid gives about two
+// waves of three CTAs per SM.
+DirectShape direct_default(const bp_plan *p, int batch) {
+    DirectShape s;
+    const long long ctas = (long long)tiles_of(p) * tiles_of(p) * batch;
+    const long long slots = 3LL * std::max(1, p->sm_count);
+    if (ctas < 2 * slots) s.asplit = (int)((2 * slots + ctas - 1) / ctas);
+    return s;
+}
+
+// Time one call: one warm-up, then `reps` calls (more for short calls); the minimum.
+template <typename F>
+bp_status time_call(F &&call, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1, float *best) {
+    bp_status r = call();
+    if (r != BP_OK) return r;
+    BP_CUDA_TRY(cudaEventRecord(e0, st));
+    r = call();
+    if (r != BP_OK) return r;
+    BP_CUDA_TRY(cudaEventRecord(e1, st));
+    BP_CUDA_TRY(cudaEventSynchronize(e1));
+    float t = 0.f;
+    BP_CUDA_TRY(cudaEventElapsedTime(&t, e0, e1));
+    *best = t;
+    const int reps = t > 20.f ? 0 : (t > 2.f ? 2 : 4);
+    for (int i = 0; i < reps; ++i) {
+        BP_CUDA_TRY(cudaEventRecord(e0, st));
+        r = call();
+        if (r != BP_OK) return r;
+        BP_CUDA_TRY(cudaEventRecord(e1, st));
+        BP_CUDA_TRY(cudaEventSynchronize(e1));
+        BP_CUDA_TRY(cudaEventElapsedTime(&t, e0, e1));
+        *best = std::min(*best, t);
+    }
+    return BP_OK;
+}
+
+struct Scratch {
+    void *a = nullptr, *b = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    ~Scratch() {
+        cudaFree(a);
+        cudaFree(b);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    }
+};
+
+const int kSplits[] = {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256};
+
+}  // namespace
+
+DirectShape direct_shape(const bp_plan *p, bp_dtype dt, int batch) {
+    int v[2];
+    if (lookup(p, BP_OP_DIRECT, dt, batch, v)) {
+        DirectShape s;
+        s.stage = v[0];
+        s.asplit = v[1];
+        return s;
+    }
+    return direct_default(p, batch);
+}
+
+RadonShape radon_shape(const bp_plan *p, int batch) {
+    int v[2];
+    RadonShape s;
+    if (lookup(p, BP_OP_RADON, 0, batch, v)) {
+        s.kang = v[0];
+        s.bands = v[1];
+    }
+    return s;
+}
+
+}  // namespace bp
+
+using namespace bp;
+
+static bp_status check_op(bp_op op, bp_dtype dtype, int batch) {
+    if (op != BP_OP_DIRECT && op != BP_OP_RADON) return fail(BP_ERR_INVALID_ARG, "invalid op");
+    if (op == BP_OP_DIRECT && dtype != BP_F32 && dtype != BP_BF16 && dtype != BP_F16)
+        return fail(BP_ERR_INVALID_ARG, "invalid dtype");
+    if (batch < 1 || batch > 65535) return fail(BP_ERR_INVALID_ARG, "batch out of range [1, 65535]");
+    return BP_OK;
+}
+
+extern "C" bp_status bp_get_shape(const bp_plan *p, bp_op op, bp_dtype dtype, int batch, int *shape) {
+    set_error("");
+    bp_status st = check_plan(p);
+    if (st != BP_OK) return st;
+    if ((st = check_op(op, dtype, batch)) != BP_OK) return st;
+    if (!shape) return fail(BP_ERR_INVALID_ARG, "shape is NULL");
+    if (op == BP_OP_DIRECT) {
+        const DirectShape s = direct_shape_used(p, dtype, batch);
+        shape[0] = s.stage;
+        shape[1] = s.asplit;
+    } else {
+        const RadonShape s = radon_shape_used(p, batch);
+        shape[0] = s.kang;
+        shape[1] = s.bands;
+    }
+    return BP_OK;
+}
+
+extern "C" bp_status bp_set_shape(bp_plan *p, bp_op op, bp_dtype dtype, int batch, const int *shape) {
+    set_error("");
+    bp_status st = check_plan(p);
+    if (st != BP_OK) return st;
+    if ((st = check_op(op, dtype, batch)) != BP_OK) return st;
+    if (!shape) return fail(BP_ERR_INVALID_ARG, "shape is NULL");
+    if (op == BP_OP_DIRECT && !(shape[0] == 8 || shape[0] == 16 || shape[0] == 32))
+        return fail(BP_ERR_INVALID_ARG, "direct stage must be 8, 16 or 32");
+    if (op == BP_OP_RADON && !(shape[0] == 1 || shape[0] == 2 || shape[0] == 4))
+        return fail(BP_ERR_INVALID_ARG, "radon angles per CTA must be 1, 2 or 4");
+    if (shape[1] < 1) return fail(BP_ERR_INVALID_ARG, "shape[1] must be >= 1");
+    store(p, op, dtype, batch, shape, false);
+    return BP_OK;
+}
+
+extern "C" bp_status bp_autotune(bp_plan *p, bp_op op, bp_dtype dtype, int batch, void *stream, int *shape,
+                                 float *ms) {
+    set_error("");
+    bp_status st = check_plan(p);
+    if (st != BP_OK) return st;
+    if ((st = check_op(op, dtype, batch)) != BP_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    BP_CUDA_TRY(cudaStreamIsCapturing(s, &cap));
+    if (cap != cudaStreamCaptureStatusNone) return fail(BP_ERR_INVALID_ARG, "bp_autotune during stream capture");
+
+    const size_t sino_n = (size_t)p->n_theta * p->n_det * batch, img_n = (size_t)p->N * p->N * batch;
+    const size_t esz = (op == BP_OP_RADON || dtype == BP_F32) ? 4 : 2;
+    Scratch sc;
+    BP_CUDA_TRY(cudaMalloc(&sc.a, esz * sino_n + 16));
+    BP_CUDA_TRY(cudaMalloc(&sc.b, 4 * std::max(sino_n, img_n) + 16));
+    // a fixed non-zero pattern (0x3c bytes: 0.0115 in float32 and bfloat16, 1.06 in float16)
+    BP_CUDA_TRY(cudaMemsetAsync(sc.a, 0x3c, esz * sino_n, s));
+    BP_CUDA_TRY(cudaMemsetAsync(sc.b, 0x3c, 4 * std::max(sino_n, img_n), s));
+    BP_CUDA_TRY(cudaEventCreate(&sc.e0));
+    BP_CUDA_TRY(cudaEventCreate(&sc.e1));
+
+    int best[2] = {0, 0};
+    float best_ms = -1.f;
+    auto consider = [&](const int v[2], float t) {
+        if (best_ms < 0.f || t < best_ms) {
+            best_ms = t;
+            best[0] = v[0];
+            best[1] = v[1];
+        }
+    };
+
+    const int tiles = (p->N + kTile - 1) / kTile;
+    const long long slots = 3LL * std::max(1, p->sm_count);
+    if (op == BP_OP_DIRECT) {
+        const long long ctas = (long long)tiles * tiles * batch;
+        std::vector<std::pair<int, int>> tried;
+        const DirectShape def = direct_default(p, batch);
+        for (int stage : {16, 8, 32}) {
+            for (int a : kSplits) {
+                // more groups than about 16 waves only adds atomic traffic; always try the default
+                if (a > 1 && a != def.asplit && ctas * a > 16 * slots) continue;
+                DirectShape cand;
+                cand.stage = stage;
+                cand.asplit = a;
+                const DirectShape eff = direct_clamp(p, dtype, cand);
+                if (std::find(tried.begin(), tried.end(), std::make_pair(eff.stage, eff.asplit)) != tried.end())
+                    continue;
+                tried.emplace_back(eff.stage, eff.asplit);
+                float t = 0.f;
+                st = time_call(
+                    [&] { return launch_direct_shape(p, sc.a, dtype, (float *)sc.b, batch, 0, s, 0.f, eff); }, s,
+                    sc.e0, sc.e1, &t);
+                if (st != BP_OK) return st;
+                const int v[2] = {eff.stage, eff.asplit};
+                consider(v, t);
+            }
+        }
+    } else {
+        std::vector<std::pair<int, int>> tried;
+        for (int kang : {4, 2, 1}) {
+            RadonShape probe;
+            probe.kang = kang;
+            const RadonShape base = radon_clamp(p, probe);  // bands from the default rule for this kang
+            for (int mul : {1, 2, 4, -2, -4}) {
+                RadonShape cand;
+                cand.kang = base.kang;
+                cand.bands = mul > 0 ? base.bands * mul : std::max(1, base.bands / -mul);
+                const RadonShape eff = radon_clamp(p, cand);
+                if (std::find(tried.begin(), tried.end(), std::make_pair(eff.kang, eff.bands)) != tried.end())
+                    continue;
+                tried.emplace_back(eff.kang, eff.bands);
+                float t = 0.f;
+                st = time_call(
+                    [&] { return launch_radon_shape(p, (const float *)sc.b, (float *)sc.a, batch, s, 0, eff); }, s,
+                    sc.e0, sc.e1, &t);
+                if (st != BP_OK) return st;
+                const int v[2] = {eff.kang, eff.bands};
+                consider(v, t);
+            }
+        }
+    }
+    BP_CUDA_TRY(cudaStreamSynchronize(s));
+    if (best_ms < 0.f) return fail(BP_ERR_UNSUPPORTED, "autotune: no candidate shape ran");
+    store(p, op, dtype, batch, best, true);
+    if (shape) {
+        shape[0] = best[0];
+        shape[1] = best[1];
+    }
+    if (ms) *ms = best_ms;
+    return BP_OK;
+}
+
+extern "C" bp_status bp_tune_cache_save(const char *path) {
+    set_error("");
+    if (!path) return fail(BP_ERR_INVALID_ARG, "path is NULL");
+    FILE *f = std::fopen(path, "w");
+    if (!f) return fail(BP_ERR_INVALID_ARG, std::string("cannot open ") + path);
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    for (const auto &kv : g_cache) {
+        const CacheKey &k = kv.first;
+        std::fprintf(f, "%d %d %d %d %d %d %d %d %d %d\n", std::get<0>(k), std::get<1>(k), std::get<2>(k),
+                     std::get<3>(k), std::get<4>(k), std::get<5>(k), std::get<6>(k), std::get<7>(k), kv.second.first,
+                     kv.second.second);
+    }
+    const bool ok = std::fclose(f) == 0;
+    return ok ? BP_OK : fail(BP_ERR_INVALID_ARG, std::string("write failed: ") + path);
+}
+
+extern "C" bp_status bp_tune_cache_load(const char *path) {
+    set_error("");
+    if (!path) return fail(BP_ERR_INVALID_ARG, "path is NULL");
+    FILE *f = std::fopen(path, "r");
+    if (!f) return fail(BP_ERR_INVALID_ARG, std::string("cannot open ") + path);
+    char line[512];
+    int n = 0;
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    while (std::fgets(line, sizeof line, f)) {
+        int v[10];
+        char extra = 0;
+        if (std::sscanf(line, "%d %d %d %d %d %d %d %d %d %d %c", &v[0], &v[1], &v[2], &v[3], &v[4], &v[5], &v[6],
+                        &v[7], &v[8], &v[9], &extra) != 10)
+            continue;
+        const bool direct = v[0] == BP_OP_DIRECT, radon = v[0] == BP_OP_RADON;
+        if (!direct && !radon) continue;
+        if (direct && !(v[8] == 8 || v[8] == 16 || v[8] == 32)) continue;
+        if (radon && !(v[8] == 1 || v[8] == 2 || v[8] == 4)) continue;
+        if (v[1] < 0 || v[1] > 2 || v[2] < 1 || v[3] < 1 || v[4] < 1 || v[5] < 1 || v[6] < 1 || v[7] < 0 || v[9] < 1)
+            continue;
+        g_cache[CacheKey{v[0], radon ? 0 : v[1], v[2], v[3], v[4], v[5], v[6], v[7]}] = {v[8], v[9]};
+        ++n;
+    }
+    std::fclose(f);
+    if (n == 0) return fail(BP_ERR_INVALID_ARG, std::string("no valid tuning entry in ") + path);
+    return BP_OK;
+}

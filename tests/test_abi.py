@@ -75,3 +75,45 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(bp, "_lib", None)
     with pytest.raises(bp.BPError, match="not built"):
         bp.lib()
+
+
+def test_shape_calls_reject_null_plan(lib):
+    shape = (ctypes.c_int * 2)(16, 1)
+    assert lib.bp_autotune(None, 0, 0, 1, None, shape, None) == 1
+    assert lib.bp_get_shape(None, 0, 0, 1, shape) == 1
+    assert lib.bp_set_shape(None, 0, 0, 1, shape) == 1
+
+
+def test_tuning_cache_round_trip(lib, tmp_path):
+    # "op dtype batch N n_det n_theta W sm_count shape0 shape1"; malformed lines are skipped
+    src = tmp_path / "tune.txt"
+    good = ["0 0 1 2048 2048 1800 96 152 16 2", "0 1 256 2048 2048 1800 96 152 32 1",
+            "1 0 8 1024 1024 720 96 152 4 3"]
+    bad = ["0 0 1 2048 2048 1800 96 152 12 2",   # stage 12 invalid
+           "1 0 1 64 64 48 96 152 3 1",           # 3 angles per CTA invalid
+           "7 0 1 64 64 48 96 152 4 1",           # unknown op
+           "0 0 1 2048 2048 1800 96 152 16",      # too short
+           "0 0 1 2048 2048 1800 96 152 16 2 9",  # trailing field
+           "garbage"]
+    src.write_text("\n".join(good[:2] + bad + good[2:]) + "\n")
+    bp.tune_cache_load(str(src))
+    out = tmp_path / "saved.txt"
+    bp.tune_cache_save(str(out))
+    saved = set(out.read_text().split("\n")) - {""}
+    assert set(good) <= saved
+    assert not any(b in saved for b in bad)
+    # a radon entry's dtype is normalised to 0
+    src2 = tmp_path / "radon.txt"
+    src2.write_text("1 2 4 512 512 360 96 152 2 5\n")
+    bp.tune_cache_load(str(src2))
+    bp.tune_cache_save(str(out))
+    assert "1 0 4 512 512 360 96 152 2 5" in out.read_text()
+
+
+def test_tuning_cache_load_errors(lib, tmp_path):
+    with pytest.raises(bp.BPError, match="cannot open"):
+        bp.tune_cache_load(str(tmp_path / "absent.txt"))
+    junk = tmp_path / "junk.txt"
+    junk.write_text("not a tuning line\n")
+    with pytest.raises(bp.BPError, match="no valid tuning entry"):
+        bp.tune_cache_load(str(junk))

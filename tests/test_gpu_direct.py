@@ -59,8 +59,10 @@ def test_direct_accumulate_and_batch():
     g = to_dev(rng.normal(size=(3, n_theta, n_det)))
     out = plan.backproject(g)
     for i in range(3):
+        # small images split the angles over several CTAs per tile whose partial sums are
+        # added atomically: equal up to the summation order
         single = plan.backproject(g[i].contiguous())
-        assert torch.equal(single, out[i])
+        assert oracle.rel_l2(single.cpu().numpy(), out[i].cpu().numpy()) <= 1e-6
     base = to_dev(rng.normal(size=(3, N, N)))
     acc = base.clone()
     plan.backproject(g, out=acc, accumulate=True)
@@ -186,7 +188,7 @@ def test_fbp_host_matches_device_calls():
     plan = bp.Plan(wl.N, wl.n_det, wl.theta, wl.det_spacing)
     out = plan.fbp_host(g.pin_memory(), "shepp-logan")
     dev_img = plan.backproject(plan.filter(g.to(dev()), "shepp-logan"))
-    assert torch.equal(out, dev_img.cpu())
+    assert oracle.rel_l2(out.numpy(), dev_img.cpu().numpy()) <= 1e-6  # atomic summation order
     out2 = plan.fbp_host(torch.stack([g, 2 * g]), "shepp-logan")
     assert torch.allclose(out2[1], 2 * out2[0], rtol=1e-6, atol=1e-6)
 
@@ -237,7 +239,7 @@ def test_fbp_pipeline_in_cuda_graph():
         plan.backproject(q, out=img)
     graph.replay()
     torch.cuda.synchronize()
-    assert torch.equal(img, eager)
+    assert oracle.rel_l2(img.cpu().numpy(), eager.cpu().numpy()) <= 1e-6  # atomic summation order
     plans = [plan, bp.Plan(96, 80, synth.uniform_theta(40))]
     sinos = [q[0].contiguous(), to_dev(np.random.default_rng(1).normal(size=(40, 80)))]
     outs = [torch.empty((p.N, p.N), device=dev()) for p in plans]
