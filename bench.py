@@ -41,20 +41,20 @@ def _peaks():
 
 def _kernel_hash() -> str:
     h = hashlib.sha256()
-    for fn in ("direct.cu", "common.cuh"):
+    for fn in ("direct.cu", "direct_tile.cuh", "tma.cuh", "common.cuh"):
         with open(os.path.join(ROOT, "paper_1608_03589_gb300", "csrc", fn), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
-def _traffic_record():
+def _traffic_record(shape):
     """DRAM bytes per launch of the direct kernel from the committed ncu summary, if the
-    kernel source is unchanged since that capture; else None."""
+    kernel source is unchanged since that capture and it used the same launch shape; else None."""
     path = os.path.join(ROOT, "profiles", "bp_direct_kernel_traffic.json")
     try:
         with open(path) as f:
             rec = json.load(f)
-        if rec.get("kernel_hash") == _kernel_hash():
+        if rec.get("kernel_hash") == _kernel_hash() and list(rec.get("launch_shape", [])) == list(shape):
             return rec
     except Exception:
         pass
@@ -242,6 +242,14 @@ def other_paths(plan, q, img, flush, stream, dev, only=()):
         return {"ms": ms, "equiv_Gupdates_s": wl.updates / ms / 1e6}
     guard("fourier_backprojection_2048", fourier)
 
+    def fbp_fourier():
+        tmp = torch.empty_like(q)
+        fused = _timed(lambda: plan.fbp_fourier(q, "shepp-logan", out=img), stream, flush, 10)
+        two = _timed(lambda: (plan.filter(q, "shepp-logan", out=tmp), plan.backproject_fourier(tmp, out=img)),
+                     stream, flush, 10)
+        return {"fused_ms": fused, "filter_then_fourier_ms": two, "equiv_Gupdates_s": wl.updates / fused / 1e6}
+    guard("fbp_fourier_fused_2048", fbp_fourier)
+
     def radon():
         shape, _ = plan.autotune("radon", batch=1)
         ms = _timed(lambda: plan.radon(img, out=q), stream, flush, 5)
@@ -407,11 +415,15 @@ def run_gpu(args, world, rank, local):
         plan.filter(g, "shepp-logan", out=q)
         plan.backproject(q, out=img)
 
-    # launch shape of the direct R* picked by the library's autotuner (untimed setup)
-    if args.no_tune:
-        shape = plan.get_shape("direct", torch.float32, 1)
+    # launch shape of the direct R* picked by the library's autotuner (untimed setup), or fixed
+    if args.shape:
+        plan.set_shape(tuple(int(v) for v in args.shape.split(",")), "direct", torch.float32, 1)
+        shape, picked = plan.get_shape("direct", torch.float32, 1), "--shape"
+    elif args.no_tune:
+        shape, picked = plan.get_shape("direct", torch.float32, 1), "default rule"
     else:
         shape, _ = plan.autotune("direct", torch.float32, 1)
+        picked = "bp_autotune"
 
     for _ in range(max(3, args.warmup)):
         step()
@@ -496,7 +508,7 @@ def run_gpu(args, world, rank, local):
     peak_tflops = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12
     bp_avg_s = statistics.mean(bp_ms) / 1e3
     achieved = wl.updates * FLOPS_PER_UPDATE / bp_avg_s / 1e12
-    traffic = _traffic_record()
+    traffic = _traffic_record(shape)
     updates_all = wl.updates * world * args.steps
     line = {
         "metric": "backprojection G pixel·angle updates/s at 2048²×1800; % of roofline",
@@ -509,7 +521,7 @@ def run_gpu(args, world, rank, local):
                    "phantom": "50 seeded random ellipses + 1% Gaussian noise", "filter": "shepp-logan",
                    "step": "bp_filter + bp_backproject_direct", "l2": "flushed (256 MiB write) between steps",
                    "launch_shape": {"stage": shape[0], "angle_groups": shape[1],
-                                    "picked_by": "default rule" if args.no_tune else "bp_autotune"},
+                                    "picked_by": picked},
                    "parallelism": f"independent slice per GPU x{world}"},
         "roofline": {"bound": "alu", "kernel": "bp_direct_kernel", "achieved": achieved,
                      "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
@@ -555,6 +567,7 @@ def main():
     ap.add_argument("--no-paths", action="store_true", help="skip the other workloads under 'paths'")
     ap.add_argument("--only", default="", help="comma-separated path names: run only these (profiling)")
     ap.add_argument("--no-tune", action="store_true", help="time the direct R* with its default launch shape")
+    ap.add_argument("--shape", default="", help="fixed direct R* launch shape 'stage,angle_groups' (no tuning)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     world, rank, local = _dist_init()

@@ -125,6 +125,23 @@ bp_status bp_backproject_fourier(bp_plan *plan, const void *sino, bp_dtype dtype
                                  int batch, void *stream);
 
 /*
+ * bp_fbp_fourier -- filtered backprojection in the Fourier form: the filter `kind` (param =
+ * Tikhonov lambda, else ignored) applied inside the projection transforms of
+ * bp_backproject_fourier (Section 3 Remark 1 (ii) eq "fbp" with Section 5.3 Step 2.2: one
+ * transform of each projection serves both), saving bp_filter's launch and its round trip
+ * of the filtered sinogram through memory.  It performs bp_filter's steps (transform, times
+ * the response, inverse transform, cut to the detector) followed by
+ * bp_backproject_fourier's, in the same floating-point operations, so the image equals
+ * bp_filter followed by bp_backproject_fourier up to rounding (bit for bit when batch is 1
+ * or n_theta is even: the two then transform the same pairs of projections together).
+ *   sino  device [batch][n_theta][n_det] of dtype (not modified);  img  device [batch][N][N].
+ * Limits and errors as bp_filter and bp_backproject_fourier; the first call with a kind
+ * (or a new lambda) builds its response, as bp_filter does.
+ */
+bp_status bp_fbp_fourier(bp_plan *plan, const void *sino, bp_dtype dtype, float *img, bp_filter_kind kind,
+                         float param, int batch, void *stream);
+
+/*
  * bp_radon -- R, the forward Radon transform (Section 1 eq "P_theta"), as the scaled
  * exact transpose of a discrete R*:  R = (dx^2/dt) diag(1/w_k) A^T  where A is the
  * matrix of R*.  With fourier_adjoint = 0, A is the direct (linear-interpolation) R*;

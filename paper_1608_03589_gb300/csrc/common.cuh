@@ -150,8 +150,9 @@ RadonShape radon_shape_used(const bp_plan *p, int batch);                  // af
 DirectShape direct_clamp(const bp_plan *p, bp_dtype dt, DirectShape shape);
 RadonShape radon_clamp(const bp_plan *p, RadonShape shape);
 int radon_max_kang(const bp_plan *p);
+// filter_kind >= 0 fuses that FBP filter (bp_filter's steps) into the projection transforms.
 bp_status launch_fourier(bp_plan *p, const void *sino, bp_dtype dt, float *img, int batch, cudaStream_t st,
-                         float wuni = 0.f);
+                         float wuni = 0.f, int filter_kind = -1, float filter_param = 0.f);
 bp_status launch_radon_fourier(bp_plan *p, const float *img, float *sino, int batch, cudaStream_t st,
                                int per_angle_w = 0);
 bp_status ensure_filter(bp_plan *p, int kind, float param);

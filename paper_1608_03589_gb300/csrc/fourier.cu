@@ -72,7 +72,7 @@ template <typename Tin, int E>
 __global__ void __launch_bounds__(1024, 1)
 fourier_spectra_kernel(const Tin *__restrict__ sino, float2 *__restrict__ spec, const float *__restrict__ wk,
                        const float2 *__restrict__ tw, int n_theta, int n_det, int logP, float wuni,
-                       const long long *__restrict__ ray, float delta2_over_M) {
+                       const long long *__restrict__ ray, float delta2_over_M, const float *__restrict__ Hf) {
     extern __shared__ __align__(128) float2 z[];
     const int P = 1 << logP, H = P >> 1;
     float2 *tws = z + P;  // P/2 twiddles
@@ -91,6 +91,24 @@ fourier_spectra_kernel(const Tin *__restrict__ sino, float2 *__restrict__ spec, 
     }
     __syncthreads();
     stockham_fft<E>(z, logP, tws, 1, false, threadIdx.x, blockDim.x);
+    if (Hf) {
+        // fused FBP filter, the same steps as bp_filter: times the response (dt/P included),
+        // inverse transform, the filtered rows cut to the detector, transformed again
+        for (int j = threadIdx.x; j < P; j += blockDim.x) {
+            const float h = __ldg(Hf + j);
+            const float2 v = z[j];
+            z[j] = make_float2(v.x * h, v.y * h);
+        }
+        __syncthreads();
+        stockham_fft<E>(z, logP, tws, 1, true, threadIdx.x, blockDim.x);
+        // an unpaired last projection keeps an exactly zero partner row, as when reloaded
+        for (int j = threadIdx.x; j < P; j += blockDim.x) {
+            if (j >= n_det) z[j] = make_float2(0.f, 0.f);
+            else if (!has1) z[j].y = 0.f;
+        }
+        __syncthreads();
+        stockham_fft<E>(z, logP, tws, 1, false, threadIdx.x, blockDim.x);
+    }
     // A[m] = (Z[m] + conj Z[P-m]) / 2,  B[m] = (Z[m] - conj Z[P-m]) / (2i)
     const float wa = (wuni > 0.f ? wuni : __ldg(wk + k0)) / (float)P;
     const float wb = has1 ? (wuni > 0.f ? wuni : __ldg(wk + k1)) / (float)P : 0.f;
@@ -193,7 +211,7 @@ __device__ __forceinline__ float2 gather_rays(const float2 *__restrict__ spec, c
 }
 
 // One thread per cell outside the core square; 32 x 8 cells per block (stores along l_y).
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 6)
 grid_gather_kernel(const float2 *__restrict__ spec, const SortedRay *__restrict__ sray,
                    const float *__restrict__ sphi, const float2 *__restrict__ tab, float2 *__restrict__ grid, int M,
                    int H, RayIndex ri, float rmax, int amax) {
@@ -619,23 +637,28 @@ bp_status ensure_fourier(bp_plan *p) {
 }
 
 template <typename Tin>
-static bp_status spectra_t(bp_plan *p, const Tin *sino, cudaStream_t st, float wuni, float delta2) {
+static bp_status spectra_t(bp_plan *p, const Tin *sino, cudaStream_t st, float wuni, float delta2, const float *Hf) {
     const int logP = ilog2(p->P);
     const size_t smem = sizeof(float2) * (p->P + p->P / 2);
     const int threads = fft_threads(p->P);
     auto kern = fft_elems(p->P) == 16 ? fourier_spectra_kernel<Tin, 16> : fourier_spectra_kernel<Tin, 8>;
     BP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     kern<<<(p->n_theta + 1) / 2, threads, smem, st>>>(sino, p->four.spec, p->four.wk, p->d_twP, p->n_theta, p->n_det,
-                                                      logP, wuni, p->four.ray, delta2);
+                                                      logP, wuni, p->four.ray, delta2, Hf);
     return BP_OK;
 }
 
 static int rows_per_cta(int M) { return std::max(1, std::min(4, (int)(131072 / (sizeof(float2) * M)))); }
 
 bp_status launch_fourier(bp_plan *p, const void *sino, bp_dtype dt, float *img, int batch, cudaStream_t st,
-                         float wuni) {
+                         float wuni, int filter_kind, float filter_param) {
     bp_status s = ensure_fourier(p);
     if (s != BP_OK) return s;
+    const float *Hf = nullptr;
+    if (filter_kind >= 0) {
+        if ((s = ensure_filter(p, filter_kind, filter_param)) != BP_OK) return s;
+        Hf = p->d_H[filter_kind];
+    }
     FourierWork &f = p->four;
     const int N = p->N, M = f.M, H = p->P / 2;
     const size_t esz = dt == BP_F32 ? 4 : 2;
@@ -652,9 +675,9 @@ bp_status launch_fourier(bp_plan *p, const void *sino, bp_dtype dt, float *img, 
     for (int b = 0; b < batch; ++b) {
         const char *sb = (const char *)sino + esz * (size_t)b * p->n_theta * p->n_det;
         switch (dt) {
-            case BP_F32: s = spectra_t(p, (const float *)sb, st, wuni, delta2); break;
-            case BP_BF16: s = spectra_t(p, (const __nv_bfloat16 *)sb, st, wuni, delta2); break;
-            case BP_F16: s = spectra_t(p, (const __half *)sb, st, wuni, delta2); break;
+            case BP_F32: s = spectra_t(p, (const float *)sb, st, wuni, delta2, Hf); break;
+            case BP_BF16: s = spectra_t(p, (const __nv_bfloat16 *)sb, st, wuni, delta2, Hf); break;
+            case BP_F16: s = spectra_t(p, (const __half *)sb, st, wuni, delta2, Hf); break;
         }
         if (s != BP_OK) return s;
         {

@@ -251,6 +251,19 @@ extern "C" bp_status bp_backproject_fourier(bp_plan *p, const void *sino, bp_dty
     return launch_fourier(p, sino, dtype, img, batch, (cudaStream_t)stream);
 }
 
+extern "C" bp_status bp_fbp_fourier(bp_plan *p, const void *sino, bp_dtype dtype, float *img, bp_filter_kind kind,
+                                    float param, int batch, void *stream) {
+    set_error("");
+    bp_status st = check_common(p, sino, img, batch);
+    if (st != BP_OK) return st;
+    if (!valid_dtype(dtype)) return fail(BP_ERR_INVALID_ARG, "invalid dtype");
+    if (kind != BP_RAMLAK && kind != BP_SHEPP_LOGAN && kind != BP_TIKHONOV)
+        return fail(BP_ERR_INVALID_ARG, "invalid filter kind");
+    if (kind == BP_TIKHONOV && !(param >= 0.f && std::isfinite(param)))
+        return fail(BP_ERR_INVALID_ARG, "Tikhonov lambda must be finite and >= 0");
+    return launch_fourier(p, sino, dtype, img, batch, (cudaStream_t)stream, 0.f, (int)kind, param);
+}
+
 extern "C" bp_status bp_radon(bp_plan *p, const float *img, float *sino, int batch, int fourier_adjoint,
                               void *stream) {
     set_error("");

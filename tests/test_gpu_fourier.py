@@ -123,3 +123,47 @@ def test_fourier_adjoint_full_size_sampled():
     err = oracle.rel_l2(got, ref)
     print(f"R_F 2048^2 x 1800 sampled rel-L2 {err:.2e}")
     assert err <= TOL_FOURIER
+
+
+# ----------------------------------------------------------------------------------- FBP fused into the Fourier path
+@pytest.mark.parametrize("kind,okind,param", [("ramlak", oracle.RAMLAK, 0.0), ("shepp-logan", oracle.SHEPP_LOGAN, 0.0),
+                                              ("tikhonov", oracle.TIKHONOV, 0.05)])
+@pytest.mark.parametrize("N,n_det,n_theta,dt_scale,seed", [(64, 64, 90, 1.0, 10), (37, 41, 7, 1.3, 11),
+                                                            (96, 128, 64, 0.8, 12)])
+def test_fbp_fourier_vs_oracle(kind, okind, param, N, n_det, n_theta, dt_scale, seed):
+    rng = np.random.default_rng(seed)
+    theta = random_theta(rng, n_theta) if seed % 2 else synth.uniform_theta(n_theta)
+    dt = dt_scale * 2.0 / n_det
+    g = to_dev(rng.normal(size=(n_theta, n_det)))
+    plan = bp.Plan(N, n_det, theta, dt)
+    fused = plan.fbp_fourier(g, kind, param)
+    # oracle: the filter's linear convolution, then the band-limited R*
+    ref = oracle.bp_trig_dirichlet(oracle.filter_rows(rounded(g), dt, okind, param), N, theta, dt)
+    assert oracle.rel_l2(fused.cpu().numpy(), ref) <= TOL_FOURIER
+    # the same floating-point steps as bp_filter followed by bp_backproject_fourier
+    two_step = plan.backproject_fourier(plan.filter(g, kind, param))
+    assert torch.equal(fused, two_step)
+
+
+def test_fbp_fourier_batch_low_precision_and_full_size():
+    rng = np.random.default_rng(13)
+    N, n_det, n_theta = 48, 48, 41  # odd angle count: batch slices pair rows differently
+    plan = bp.Plan(N, n_det, synth.uniform_theta(n_theta))
+    g = to_dev(rng.normal(size=(3, n_theta, n_det)), torch.bfloat16)
+    fused = plan.fbp_fourier(g, "shepp-logan")
+    for i in range(3):
+        ref = oracle.bp_trig_dirichlet(oracle.filter_rows(rounded(g[i]), plan.det_spacing, oracle.SHEPP_LOGAN),
+                                       N, plan.theta, plan.det_spacing)
+        assert oracle.rel_l2(fused[i].cpu().numpy(), ref) <= TOL_FOURIER
+    two_step = plan.backproject_fourier(plan.filter(g, "shepp-logan"))
+    assert oracle.rel_l2(fused.cpu().numpy(), two_step.cpu().numpy()) <= 1e-6
+    # 2048^2, 2048 bins, 1800 angles, sampled pixels against the oracle
+    wl = synth.LARGE
+    big = bp.Plan(wl.N, wl.n_det, wl.theta, wl.det_spacing)
+    gd = to_dev(wl.sinogram())
+    img = big.fbp_fourier(gd, "shepp-logan")
+    pix = sample_pixels(wl.N, 100, seed=14)
+    q = oracle.filter_rows(rounded(gd), wl.det_spacing, oracle.SHEPP_LOGAN)
+    ref = oracle.bp_trig_points(q, wl.N, wl.theta, wl.det_spacing, pix)
+    got = img.reshape(-1)[torch.from_numpy(pix).to(dev())].cpu().numpy()
+    assert oracle.rel_l2(got, ref) <= TOL_FOURIER
