@@ -8,7 +8,9 @@ this module only builds it with gcc and marshals numpy arrays.  The one library
 primitive used here is numpy's FFT, to form the projection spectra G_k[m] that the
 spectral Fourier-path oracle sums (Section 5.3, Step 2.2).
 
-Each wrapped function cites the passage of arXiv:1608.03589 it follows in oracle.c.
+Each wrapped function cites the passage of arXiv:1608.03589 it follows in oracle.c.  The
+paper's own BST algorithm (polar-to-Cartesian interpolation in frequency) is plain numpy in
+``bst_interp.py`` (``bp_bst_interp`` below).
 """
 from __future__ import annotations
 
@@ -218,3 +220,6 @@ def rel_l2(a, b) -> float:
     b = np.asarray(b, dtype=np.float64).ravel()
     nb = float(np.linalg.norm(b))
     return float(np.linalg.norm(a - b)) / (nb if nb > 0 else 1.0)
+
+
+from .bst_interp import bp_bst_interp, bst_full_period  # noqa: E402  (numpy oracle of Section 5.3)
