@@ -250,6 +250,14 @@ def other_paths(plan, q, img, flush, stream, dev, only=()):
         return {"fused_ms": fused, "filter_then_fourier_ms": two, "equiv_Gupdates_s": wl.updates / fused / 1e6}
     guard("fbp_fourier_fused_2048", fbp_fourier)
 
+    def bst():
+        res = {}
+        for os in (1, 4):
+            ms = _timed(lambda: plan.backproject_bst(q, os, out=img), stream, flush, 10)
+            res[f"oversampling_{os}"] = {"ms": ms, "equiv_Gupdates_s": wl.updates / ms / 1e6}
+        return res
+    guard("bst_interpolation_2048", bst)
+
     def radon():
         shape, _ = plan.autotune("radon", batch=1)
         ms = _timed(lambda: plan.radon(img, out=q), stream, flush, 5)

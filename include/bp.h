@@ -125,6 +125,28 @@ bp_status bp_backproject_fourier(bp_plan *plan, const void *sino, bp_dtype dtype
                                  int batch, void *stream);
 
 /*
+ * bp_backproject_bst -- R* by the paper's own Backprojection-Slice-Theorem algorithm
+ * (Section 5.3, Steps 1-4; eq "bst"; eq "kernel"): each projection zero-padded to
+ * Pb = radial_oversampling * P points (P = 2^ceil(log2(2 n_det))) and transformed; the
+ * transform times K^sigma = 1/|sigma| (1/dsigma at sigma = 0) gives the backprojection's
+ * transform on the polar rays theta_k and theta_k + pi; it is interpolated linearly in
+ * radius and in angle to the M x M Cartesian frequency grid (M = max(2^ceil(log2(2N)),
+ * 64); the origin node takes the mean over the rays), and a 2D inverse FFT (the Riemann sum
+ * of the inverse Fourier integral) gives the N x N image.
+ * An approximation of R*, cheaper than bp_backproject_fourier and less accurate: linear
+ * interpolation of oscillating spectra needs radial_oversampling of 4 or more for errors of
+ * a few percent on filtered data, and the value 1/dsigma that K^sigma puts at the origin
+ * shifts the mean of unfiltered backprojections.
+ *   sino  device [batch][n_theta][n_det] of dtype;  img  device [batch][N][N] float32.
+ *   radial_oversampling  1, 2, 4 or 8, with Pb <= 16384, else BP_ERR_INVALID_ARG /
+ *   BP_ERR_UNSUPPORTED.  The first call (or one with another oversampling) allocates the
+ *   plan's workspace for it (polar values n_theta x Pb/2 complex, besides the Fourier path's
+ *   grid).
+ */
+bp_status bp_backproject_bst(bp_plan *plan, const void *sino, bp_dtype dtype, float *img, int radial_oversampling,
+                             int batch, void *stream);
+
+/*
  * bp_fbp_fourier -- filtered backprojection in the Fourier form: the filter `kind` (param =
  * Tikhonov lambda, else ignored) applied inside the projection transforms of
  * bp_backproject_fourier (Section 3 Remark 1 (ii) eq "fbp" with Section 5.3 Step 2.2: one

@@ -71,6 +71,22 @@ struct FourierWork {
     size_t bytes = 0;
 };
 
+// Workspace of the paper's own BST algorithm (polar-to-Cartesian interpolation, bst.cu);
+// the Cartesian grid and the inverse-FFT intermediate are the Fourier path's.
+struct BstWork {
+    int os = 0;                 // radial oversampling: Pb = os P
+    int Pb = 0;                 // projection transform length
+    float2 *polar = nullptr;    // [n_theta][Pb/2] polar values of the backprojection's transform
+    float2 *twPb = nullptr;     // Pb/2 twiddles
+    float *ang = nullptr;       // [2 n_theta] ray angles theta_k, theta_k + pi in [0, 2 pi), sorted
+    int *ray = nullptr;         // [2 n_theta] projection index, bit 30 set for the opposite ray
+    float *ones = nullptr;      // [N] unit deapodisation
+    float4 *dir = nullptr;      // [2 n_theta] ray directions (cos, sin) as high and low floats
+    float *igap = nullptr;      // [2 n_theta] 1 / angular gap to the next ray
+    RayIndex ri;                // lookup into ang (n = 2 n_theta)
+    size_t bytes = 0;
+};
+
 // Launch shapes.  The direct R* takes `stage` angles per shared-memory stage (8, 16 or 32)
 // and splits the angles into `asplit` groups, each a separate CTA per tile that adds its
 // partial sum into the image; the direct R takes `kang` angles per CTA (1, 2 or 4) and
@@ -107,6 +123,7 @@ struct bp_plan {
     float H_param[3] = {0.f, 0.f, 0.f};
     // Fourier path
     bp::FourierWork four;
+    bp::BstWork bst;
     // host-buffer entry point staging
     float *d_stage = nullptr;
     size_t stage_batch = 0;
@@ -160,6 +177,9 @@ bp_status launch_filter_response(bp_plan *p, const void *in, bp_dtype dt, float 
                                  cudaStream_t st);
 bp_status ensure_fourier(bp_plan *p);
 void free_fourier(bp_plan *p);
+void free_bst(bp_plan *p);
+bp_status launch_grid_to_image(bp_plan *p, const float *deap, float *img, cudaStream_t st);
+bp_status launch_bst(bp_plan *p, const void *sino, bp_dtype dt, float *img, int os, int batch, cudaStream_t st);
 bp_status launch_batched(bp_plan *const *plans, const void *const *sinos, const bp_dtype *dtypes,
                          float *const *imgs, int n, cudaStream_t st);
 

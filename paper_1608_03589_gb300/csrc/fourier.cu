@@ -650,6 +650,26 @@ static bp_status spectra_t(bp_plan *p, const Tin *sino, cudaStream_t st, float w
 
 static int rows_per_cta(int M) { return std::max(1, std::min(4, (int)(131072 / (sizeof(float2) * M)))); }
 
+// Inverse 2D FFT of the M x M grid (f.grid), pruned to the N x N image, times deap[i_x]
+// deap[i_y] (the deapodisation; ones for no correction), real part into img.
+bp_status launch_grid_to_image(bp_plan *p, const float *deap, float *img, cudaStream_t st) {
+    FourierWork &f = p->four;
+    const int N = p->N, M = f.M;
+    const int R = rows_per_cta(M);
+    const size_t smemR = sizeof(float2) * ((size_t)R * M + M / 2);
+    auto pass_y = fft_elems(M) == 16 ? ifft_pass_y_kernel<16> : ifft_pass_y_kernel<8>;
+    auto pass_x = fft_elems(M) == 16 ? ifft_pass_x_kernel<16> : ifft_pass_x_kernel<8>;
+    BP_CUDA_TRY(cudaFuncSetAttribute(pass_y, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smemR));
+    BP_CUDA_TRY(cudaFuncSetAttribute(pass_x, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smemR));
+    const int nthr = fft_threads(M);
+    int groups = 1;
+    while (groups * 2 <= R && nthr * groups * 2 <= 1024) groups *= 2;
+    pass_y<<<M / R, nthr * groups, smemR, st>>>(f.grid, f.mid, deap, f.twM, M, f.logM, N, R, p->d_err);
+    pass_x<<<(N + R - 1) / R, nthr * groups, smemR, st>>>(f.mid, img, deap, f.twM, M, f.logM, N, R, p->d_err);
+    BP_CUDA_TRY(cudaGetLastError());
+    return BP_OK;
+}
+
 bp_status launch_fourier(bp_plan *p, const void *sino, bp_dtype dt, float *img, int batch, cudaStream_t st,
                          float wuni, int filter_kind, float filter_param) {
     bp_status s = ensure_fourier(p);
@@ -662,15 +682,6 @@ bp_status launch_fourier(bp_plan *p, const void *sino, bp_dtype dt, float *img, 
     FourierWork &f = p->four;
     const int N = p->N, M = f.M, H = p->P / 2;
     const size_t esz = dt == BP_F32 ? 4 : 2;
-    const int R = rows_per_cta(M);
-    const size_t smemR = sizeof(float2) * ((size_t)R * M + M / 2);
-    auto pass_y = fft_elems(M) == 16 ? ifft_pass_y_kernel<16> : ifft_pass_y_kernel<8>;
-    auto pass_x = fft_elems(M) == 16 ? ifft_pass_x_kernel<16> : ifft_pass_x_kernel<8>;
-    BP_CUDA_TRY(cudaFuncSetAttribute(pass_y, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smemR));
-    BP_CUDA_TRY(cudaFuncSetAttribute(pass_x, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smemR));
-    const int nthr = fft_threads(M);
-    int groups = 1;
-    while (groups * 2 <= R && nthr * groups * 2 <= 1024) groups *= 2;
     const float delta2 = (N % 2 == 0) ? 1.0f / (float)M : 0.0f;  // 2 delta / M
     for (int b = 0; b < batch; ++b) {
         const char *sb = (const char *)sino + esz * (size_t)b * p->n_theta * p->n_det;
@@ -680,22 +691,17 @@ bp_status launch_fourier(bp_plan *p, const void *sino, bp_dtype dt, float *img, 
             case BP_F16: s = spectra_t(p, (const __half *)sb, st, wuni, delta2, Hf); break;
         }
         if (s != BP_OK) return s;
-        {
-            const dim3 g((M + 31) / 32, (M + 7) / 8);
-            const int amax = (int)std::ceil((f.rmax + 4.25 + M / 2) / M);
-            grid_gather_kernel<<<g, 256, 0, st>>>(f.spec, (const SortedRay *)f.sray, f.sphi, f.kbtab, f.grid, M, H,
-                                                  f.ri, f.rmax, amax);
-            const int core = std::min(kCore, M / 2);
-            const int side = 2 * core - 1;
-            grid_gather_core_kernel<<<(side * side + 7) / 8, 256, 0, st>>>(f.spec, (const SortedRay *)f.sray, f.sphi,
-                                                                           f.kbtab, f.grid, M, H, f.ri, f.rmax, amax,
-                                                                           core);
-        }
-        pass_y<<<M / R, nthr * groups, smemR, st>>>(f.grid, f.mid, f.deapod, f.twM, M, f.logM, N, R,
-                                                           p->d_err);
-        pass_x<<<(N + R - 1) / R, nthr * groups, smemR, st>>>(f.mid, img + (size_t)b * N * N, f.deapod,
-                                                                     f.twM, M, f.logM, N, R, p->d_err);
+        const dim3 g((M + 31) / 32, (M + 7) / 8);
+        const int amax = (int)std::ceil((f.rmax + 4.25 + M / 2) / M);
+        grid_gather_kernel<<<g, 256, 0, st>>>(f.spec, (const SortedRay *)f.sray, f.sphi, f.kbtab, f.grid, M, H, f.ri,
+                                              f.rmax, amax);
+        const int core = std::min(kCore, M / 2);
+        const int side = 2 * core - 1;
+        grid_gather_core_kernel<<<(side * side + 7) / 8, 256, 0, st>>>(f.spec, (const SortedRay *)f.sray, f.sphi,
+                                                                       f.kbtab, f.grid, M, H, f.ri, f.rmax, amax,
+                                                                       core);
         BP_CUDA_TRY(cudaGetLastError());
+        if ((s = launch_grid_to_image(p, f.deapod, img + (size_t)b * N * N, st)) != BP_OK) return s;
     }
     return BP_OK;
 }
