@@ -41,7 +41,7 @@ def _peaks():
 
 def _kernel_hash() -> str:
     h = hashlib.sha256()
-    for fn in ("direct.cu", "direct_tile.cuh", "tma.cuh", "common.cuh"):
+    for fn in ("direct.cu", "direct_tile.cuh", "tma.cuh", "geometry.cuh"):
         with open(os.path.join(ROOT, "paper_1608_03589_gb300", "csrc", fn), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -257,6 +257,11 @@ def other_paths(plan, q, img, flush, stream, dev, only=()):
             res[f"oversampling_{os}"] = {"ms": ms, "equiv_Gupdates_s": wl.updates / ms / 1e6}
         return res
     guard("bst_interpolation_2048", bst)
+
+    def logpolar():
+        ms = _timed(lambda: plan.backproject_logpolar(q, out=img), stream, flush, 5)
+        return {"ms": ms, "equiv_Gupdates_s": wl.updates / ms / 1e6}
+    guard("logpolar_2048", logpolar)
 
     def radon():
         shape, _ = plan.autotune("radon", batch=1)

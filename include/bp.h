@@ -147,6 +147,27 @@ bp_status bp_backproject_bst(bp_plan *plan, const void *sino, bp_dtype dtype, fl
                              int batch, void *stream);
 
 /*
+ * bp_backproject_logpolar -- R* by Andersson's log-polar convolution as the paper implements
+ * it (Section 5.1 Steps 1-4 with the adaptive rho_0 of Section 5.2; eq "andersson"): the
+ * sinogram resampled (linear interpolation) onto a log-polar mesh mu_i = rho_0 + i drho,
+ * phi_j = 2 pi j / N_phi with rho_0 = ln(dx/2), the outermost step at most the detector
+ * pitch (eq "N_rho") and N_phi = 2^ceil(log2(2 n_theta)); convolved with the kernel
+ * delta(1 - e^rho cos theta) (a unit point mass on the mesh, eq "and_kernel") by 2D FFTs
+ * (linear in rho, circular in theta); the result interpolated bilinearly at the pixel
+ * centres.  An approximation of R*: the lines passing within e^{rho_0} of the origin are
+ * missing (the origin problem of Section 5.2), so the error grows toward the image centre
+ * (the centre of an odd image takes the mean over the angles at rho_0); away from it the
+ * error falls at first order with the resolution.
+ *   sino  device [batch][n_theta][n_det] of dtype;  img  device [batch][N][N] float32.
+ *   Needs n_det >= 2 and transforms of at most 16384 points (N_rho + N_out, N_phi), i.e.
+ *   about N <= 2048 at the default pitch, else BP_ERR_UNSUPPORTED.  The first call builds
+ *   the plan's workspace: FP64 interpolation tables (16 bytes per pixel), two N_phi x L
+ *   complex arrays (the kernel transform and the work array; 2 x 512 MiB at 2048^2 x 1800).
+ */
+bp_status bp_backproject_logpolar(bp_plan *plan, const void *sino, bp_dtype dtype, float *img, int batch,
+                                  void *stream);
+
+/*
  * bp_fbp_fourier -- filtered backprojection in the Fourier form: the filter `kind` (param =
  * Tikhonov lambda, else ignored) applied inside the projection transforms of
  * bp_backproject_fourier (Section 3 Remark 1 (ii) eq "fbp" with Section 5.3 Step 2.2: one

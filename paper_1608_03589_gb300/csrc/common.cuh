@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "bp.h"
+#include "geometry.cuh"
 
 namespace bp {
 
@@ -23,25 +24,6 @@ bp_status cuda_fail(cudaError_t e, const char *what);
         cudaError_t _e = (expr);                                  \
         if (_e != cudaSuccess) return ::bp::cuda_fail(_e, #expr); \
     } while (0)
-
-// ------------------------------------------------------------------------------ geometry
-// Direct kernels work on square pixel tiles; the per-angle table below gives the
-// detector coordinate u (in bins) of pixel (0,0) and its change per tile, in 32.32
-// fixed point (exact integer tile stepping), plus the per-pixel steps in float.
-constexpr int kTile = 64;         // pixel tile side of the direct R* / R kernels
-constexpr int kStage = 16;        // angles per shared-memory stage
-constexpr int kThreads = 256;     // threads per CTA of the direct kernels
-
-struct AngleParam {
-    long long U00;  // u(pixel 0,0) * 2^32
-    long long CT;   // u step per tile along x (kTile pixels) * 2^32
-    long long ST;   // u step per tile along y * 2^32
-    float c;        // u step per pixel along x = cos(theta) dx/dt
-    float s;        // u step per pixel along y = sin(theta) dx/dt
-    float w;        // quadrature weight w_k
-    float pad;
-};
-static_assert(sizeof(AngleParam) == 40, "AngleParam layout");
 
 // Lookup into the ray angles sorted in [0, 2 pi).
 struct RayIndex {
@@ -87,6 +69,21 @@ struct BstWork {
     size_t bytes = 0;
 };
 
+// Workspace of Andersson's log-polar backprojection (logpolar.cu).
+struct LogPolarWork {
+    int n_rho = 0, n_phi = 0, n_out = 0, L = 0;  // meshes (see logpolar.cu)
+    double rho0 = 0.0, drho = 0.0;
+    int4 *rtab = nullptr;      // [n_rho] detector bin and fraction of s_i (signs +, -)
+    int4 *atab = nullptr;      // [n_phi] bracketing projections, detector signs, weight
+    float2 *kfrac = nullptr;   // [n_phi] kernel node and fraction of -ln cos(theta') / drho
+    int4 *pix = nullptr;       // [N*N] pixel -> (rho node, fraction, theta node, fraction)
+    float2 *twL = nullptr, *twPhi = nullptr;
+    float2 *T = nullptr;       // [n_phi][L] complex work array
+    float2 *Khat = nullptr;    // [n_phi][L] kernel transform (scaled)
+    float *B = nullptr;        // [n_phi][n_out] backprojection on the log-polar mesh
+    size_t bytes = 0;
+};
+
 // Launch shapes.  The direct R* takes `stage` angles per shared-memory stage (8, 16 or 32)
 // and splits the angles into `asplit` groups, each a separate CTA per tile that adds its
 // partial sum into the image; the direct R takes `kang` angles per CTA (1, 2 or 4) and
@@ -124,6 +121,7 @@ struct bp_plan {
     // Fourier path
     bp::FourierWork four;
     bp::BstWork bst;
+    bp::LogPolarWork lp;
     // host-buffer entry point staging
     float *d_stage = nullptr;
     size_t stage_batch = 0;
@@ -178,6 +176,8 @@ bp_status launch_filter_response(bp_plan *p, const void *in, bp_dtype dt, float 
 bp_status ensure_fourier(bp_plan *p);
 void free_fourier(bp_plan *p);
 void free_bst(bp_plan *p);
+void free_logpolar(bp_plan *p);
+bp_status launch_logpolar(bp_plan *p, const void *sino, bp_dtype dt, float *img, int batch, cudaStream_t st);
 bp_status launch_grid_to_image(bp_plan *p, const float *deap, float *img, cudaStream_t st);
 bp_status launch_bst(bp_plan *p, const void *sino, bp_dtype dt, float *img, int os, int batch, cudaStream_t st);
 bp_status launch_batched(bp_plan *const *plans, const void *const *sinos, const bp_dtype *dtypes,

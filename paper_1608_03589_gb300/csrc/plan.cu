@@ -112,6 +112,7 @@ static void plan_free_device(bp_plan *p) {
     for (auto &h : p->d_H) cudaFree(h);
     free_fourier(p);
     free_bst(p);
+    free_logpolar(p);
     cudaFree(p->d_stage);
     cudaFree(p->d_desc);
     cudaFree(p->d_counter);
@@ -275,6 +276,15 @@ extern "C" bp_status bp_backproject_bst(bp_plan *p, const void *sino, bp_dtype d
     if (os != 1 && os != 2 && os != 4 && os != 8)
         return fail(BP_ERR_INVALID_ARG, "radial_oversampling must be 1, 2, 4 or 8");
     return launch_bst(p, sino, dtype, img, os, batch, (cudaStream_t)stream);
+}
+
+extern "C" bp_status bp_backproject_logpolar(bp_plan *p, const void *sino, bp_dtype dtype, float *img, int batch,
+                                             void *stream) {
+    set_error("");
+    bp_status st = check_common(p, sino, img, batch);
+    if (st != BP_OK) return st;
+    if (!valid_dtype(dtype)) return fail(BP_ERR_INVALID_ARG, "invalid dtype");
+    return launch_logpolar(p, sino, dtype, img, batch, (cudaStream_t)stream);
 }
 
 extern "C" bp_status bp_radon(bp_plan *p, const float *img, float *sino, int batch, int fourier_adjoint,
