@@ -41,7 +41,7 @@ def _peaks():
 
 def _kernel_hash() -> str:
     h = hashlib.sha256()
-    for fn in ("direct.cu", "direct_tile.cuh", "tma.cuh", "geometry.cuh"):
+    for fn in ("direct.cu", "direct_tile.cuh", "tma.cuh", "geometry.cuh", "f32x2.cuh"):
         with open(os.path.join(ROOT, "paper_1608_03589_gb300", "csrc", fn), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]

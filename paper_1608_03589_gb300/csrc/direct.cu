@@ -28,6 +28,7 @@
 
 #include "common.cuh"
 #include "direct_tile.cuh"
+#include "f32x2.cuh"
 #include "tma.cuh"
 
 namespace bp {
@@ -53,26 +54,6 @@ bp_direct_kernel(const Tin *__restrict__ sino, float *__restrict__ img, const An
     const int k_end = min(n_theta, group_stage(grp + 1, S, asplit) * kStage);
     direct_tile_sync<Tin>(sino + (long long)blockIdx.z * sino_stride, img + (long long)blockIdx.z * img_stride, ap,
                           N, n_det, k_begin, k_end, W, C, blockIdx.x, ty, accumulate, asplit > 1, wuni, tab, sm);
-}
-
-__device__ __forceinline__ unsigned long long pk2(float a, float b) {
-    unsigned long long r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-    return r;
-}
-__device__ __forceinline__ void upk2(unsigned long long r, float &a, float &b) {
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
-}
-__device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsigned long long b,
-                                                    unsigned long long c) {
-    unsigned long long d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-    return d;
-}
-__device__ __forceinline__ unsigned long long fadd2(unsigned long long a, unsigned long long b) {
-    unsigned long long d;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
 }
 
 template <typename T> __device__ __forceinline__ float smem_f(const unsigned char *p, int i);

@@ -14,13 +14,15 @@
 // along the dominant axis of the block's angles, with S |dominant step| > 1 bin, so the 32
 // lanes of one instruction always hit 32 different intervals: each deposit is one plain
 // float2 shared-memory read-modify-write, no atomics; a pixel value is read once and
-// deposited for all angles of the block (independent windows, so their latencies
-// overlap).  After each tile the warp windows are folded into the detector rows (each bin
+// deposited for all angles of the block (independent windows: the reads of all angles are
+// issued before the writes, and the coordinates of two angles share one packed f32x2
+// instruction).  After each tile the warp windows are folded into the detector rows (each bin
 // owned by one thread).  The window origin J0 and the tile-local coordinate come from the
 // same 32.32 fixed-point tile stepping as R*.
 #include <algorithm>
 
 #include "common.cuh"
+#include "f32x2.cuh"
 
 namespace bp {
 
@@ -33,7 +35,7 @@ constexpr int kRWarps = kRThreads / 32;
 constexpr int kAngMax = 4;
 constexpr size_t kMaxRadonSmem = 200 * 1024;
 
-__global__ void __launch_bounds__(kRThreads, 2)
+__global__ void __launch_bounds__(kRThreads, 3)
 radon_direct_kernel(const float *__restrict__ img, float *__restrict__ sino, const AngleParam *__restrict__ ap,
                     int N, int n_det, int n_theta, int W, int C, int kAng, int tiles_per_band, float scale,
                     int use_atomic, long long img_stride, long long sino_stride, int per_angle_w) {
@@ -87,12 +89,25 @@ radon_direct_kernel(const float *__restrict__ img, float *__restrict__ sino, con
     if (t_begin < t_end) fetch(t_begin);
 
     // deposit the pixels of lines warp, warp + 8, ... of the tile for angles [a0, a1)
+    const unsigned win_u32 = smem_u32(mywin);
+    const unsigned long long MM = pk2(kMagic, kMagic);
     auto deposit = [&](int a0, int a1, bool xdom, int S) {
-        // the angles' parameters live in registers (shared memory would be re-read after
-        // every window store, which may alias it)
-        float4 Pa[kAngMax];
+        // per pair of angles (2p, 2p + 1): base coordinates and steps packed for the paired
+        // FP32 instructions, and the window byte addresses offset so that the rounding's bit
+        // pattern (magic + m) indexes the window directly
+        unsigned long long Q0[kAngMax / 2], CX[kAngMax / 2], SY[kAngMax / 2];
+        unsigned wb[kAngMax];
 #pragma unroll
-        for (int a = 0; a < kAngMax; ++a) Pa[a] = (a0 + a < a1) ? sp[a0 + a] : make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int p2 = 0; p2 < kAngMax / 2; ++p2) {
+            const float4 Pa = (a0 + 2 * p2 < a1) ? sp[a0 + 2 * p2] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 Pb = (a0 + 2 * p2 + 1 < a1) ? sp[a0 + 2 * p2 + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
+            Q0[p2] = pk2(Pa.x, Pb.x);
+            CX[p2] = pk2(Pa.y, Pb.y);
+            SY[p2] = pk2(Pa.z, Pb.z);
+        }
+#pragma unroll
+        for (int a = 0; a < kAngMax; ++a)
+            wb[a] = win_u32 + 8u * (unsigned)((a0 + a) * W + C) - ((unsigned)kMagicInt << 3);
         for (int line = warp; line < kTile; line += kRWarps) {
             for (int base = 0; base < kTile; base += 32 * S) {
                 for (int ph = 0; ph < S; ++ph) {
@@ -100,21 +115,33 @@ radon_direct_kernel(const float *__restrict__ img, float *__restrict__ sino, con
                     const bool act = pos < kTile;
                     const int x = xdom ? pos : line, y = xdom ? line : pos;
                     const float f = act ? tile[y * (kTile + 1) + x] : 0.f;
+                    const unsigned long long X2 = pk2((float)x, (float)x), Y2 = pk2((float)y, (float)y);
+                    // all angles' window cells are read before any is written back (different
+                    // angles never share a cell), so the reads are in flight together
+                    unsigned cell[kAngMax];
+                    float dq[kAngMax];
+#pragma unroll
+                    for (int p2 = 0; p2 < kAngMax / 2; ++p2) {
+                        const unsigned long long Q = ffma2(Y2, SY[p2], ffma2(X2, CX[p2], Q0[p2]));
+                        const unsigned long long R = fadd2(Q, MM);            // magic + rint(q)
+                        const unsigned long long D = fsub2(Q, fsub2(R, MM));  // q - rint(q)
+                        float r0, r1;
+                        upk2(R, r0, r1);
+                        upk2(D, dq[2 * p2], dq[2 * p2 + 1]);
+                        cell[2 * p2] = wb[2 * p2] + (__float_as_uint(r0) << 3);
+                        cell[2 * p2 + 1] = wb[2 * p2 + 1] + (__float_as_uint(r1) << 3);
+                    }
+                    const int na = act ? a1 - a0 : 0;
+                    float2 v[kAngMax];
+#pragma unroll
+                    for (int a = 0; a < kAngMax; ++a)
+                        if (a < na) v[a] = lds64(cell[a]);
 #pragma unroll
                     for (int a = 0; a < kAngMax; ++a) {
-                        if (a0 + a < a1) {
-                            const float4 P = Pa[a];
-                            const float q = fmaf((float)y, P.z, fmaf((float)x, P.y, P.x));
-                            const float r = q + kMagic;
-                            const int m = __float_as_int(r) - kMagicInt;  // rint(q)
-                            const float dq = q - (r - kMagic);            // q - m, in [-1/2, 1/2]
-                            if (act && f != 0.f) {
-                                float2 *cell = mywin + (a0 + a) * W + C + m;
-                                float2 v = *cell;
-                                v.x += f;
-                                v.y = fmaf(f, dq, v.y);
-                                *cell = v;
-                            }
+                        if (a < na) {
+                            v[a].x += f;
+                            v[a].y = fmaf(f, dq[a], v[a].y);
+                            sts64(cell[a], v[a]);
                         }
                     }
                     __syncwarp();
