@@ -18,10 +18,11 @@
 //
 // Kernels: (1) fourier_spectra: one CTA per projection pair, P-point FFT in shared memory,
 // the two half spectra scaled into c'_{k,m} (quadrature weight, Hermitian factor, detector
-// and half-pixel phases);  (2) gridding as a gather: one thread per grid cell (a warp per
-// cell near the origin, where every ray passes) walks only the rays whose angle falls in the
-// cell's 6 x 6 footprint as seen from the origin (binary search in the sorted angles), and
-// on each ray only the samples inside the footprint; the separable kernel comes from an
+// and half-pixel phases);  (2) gridding as a gather: one thread per pair of adjacent grid
+// cells (a warp per cell near the origin, where every ray passes) walks only the rays whose
+// angle falls in the pair's footprint as seen from the origin (O(1) lookup for uniform angle
+// sets, else binary search in the sorted angles), and on each ray only the samples inside
+// the footprint, sharing the sample value and the x weight between the two cells; the separable kernel comes from an
 // FP64-built table with linear interpolation.  No atomics, deterministic, one store per
 // cell;  (3) ifft_pass_y / ifft_pass_x: M-point inverse FFTs of R rows per CTA (bulk
 // asynchronous loads) with output pruning to N points, transposed intermediate, fused
@@ -155,8 +156,7 @@ __device__ __forceinline__ int first_at_least(const float *__restrict__ sphi, co
 }
 
 __device__ __forceinline__ void ray_range(const float *__restrict__ sphi, const RayIndex &ri, float ux, float uy,
-                                          int &lo, int &count) {
-    const float R = 4.2427f;  // 3 sqrt(2) plus rounding margin
+                                          int &lo, int &count, float R = 4.2427f /* 3 sqrt(2) + margin */) {
     const float r2 = ux * ux + uy * uy;
     if (r2 <= R * R) {
         lo = 0;
@@ -210,40 +210,89 @@ __device__ __forceinline__ float2 gather_rays(const float2 *__restrict__ spec, c
     return acc;
 }
 
-// One thread per cell outside the core square; 32 x 8 cells per block (stores along l_y).
+// The pair of cells (u_x, u_y) and (u_x, u_y + 1): they share the rays of the angular window
+// of their union box [u_x - 3, u_x + 3) x [u_y - 3, u_y + 4) and, per sample, the spectrum
+// value and the x weight.
+__device__ __forceinline__ void gather_rays_pair(const float2 *__restrict__ spec,
+                                                 const SortedRay *__restrict__ sray, const float2 *__restrict__ tab,
+                                                 int n, int H, int ux, int uy, int lo, int count, float2 &acc0,
+                                                 float2 &acc1) {
+    const float fx0 = (float)ux - 3.f, fx1 = (float)ux + 3.f, fy0 = (float)uy - 3.f, fy1 = (float)uy + 4.f;
+    for (int j = 0; j < count; ++j) {
+        int i = lo + j;
+        if (i >= n) i -= n;
+        const SortedRay r = sray[i];
+        // samples m with z = m (sx, sy) inside the union box (one spare sample each side)
+        const float ax0 = fx0 * r.isx, ax1 = fx1 * r.isx, ay0 = fy0 * r.isy, ay1 = fy1 * r.isy;
+        float mlo = fmaxf(0.f, fmaxf(fminf(ax0, ax1), fminf(ay0, ay1)));
+        float mhi = fminf((float)(H - 1), fminf(fmaxf(ax0, ax1), fmaxf(ay0, ay1)));
+        if (!(mlo <= mhi + 2.f)) continue;  // also rejects NaN (0 * inf on a zero component)
+        const int m0 = max(0, (int)mlo - 1), m1 = min(H - 1, (int)mhi + 1);
+        const float2 *sk = spec + (long long)r.k * H;
+        // exact offsets d = u - z at m0 from the fixed-point ray, then float steps (|m - m0| small)
+        const long long zx = (long long)m0 * r.ax, zy = (long long)m0 * r.ay;
+        const float dx0 = (float)(ux - (int)(zx >> 32)) - (float)(unsigned)(zx & 0xffffffffLL) * 2.3283064365386963e-10f;
+        const float dy0 = (float)(uy - (int)(zy >> 32)) - (float)(unsigned)(zy & 0xffffffffLL) * 2.3283064365386963e-10f;
+        const float sx = r.sx, sy = r.sy;
+        for (int m = m0; m <= m1; ++m) {
+            const float t = (float)(m - m0);
+            const float dx = fmaf(-t, sx, dx0), dy = fmaf(-t, sy, dy0), dy1 = dy + 1.f;
+            // footprint rule of the spreading form: u - z in (-3, 3] per axis
+            if (!(dx > -3.f && dx <= 3.f)) continue;
+            const bool in0 = dy > -3.f && dy <= 3.f, in1 = dy1 > -3.f && dy1 <= 3.f;
+            if (!(in0 || in1)) continue;
+            const float2 v = __ldg(sk + m);
+            const float kx = kb_tab(tab, dx);
+            if (in0) {
+                const float w = kx * kb_tab(tab, dy);
+                acc0.x = fmaf(w, v.x, acc0.x);
+                acc0.y = fmaf(w, v.y, acc0.y);
+            }
+            if (in1) {
+                const float w = kx * kb_tab(tab, dy1);
+                acc1.x = fmaf(w, v.x, acc1.x);
+                acc1.y = fmaf(w, v.y, acc1.y);
+            }
+        }
+    }
+}
+
+// One thread per pair of cells (l_y even, l_y + 1) outside the core square; 64 x 8 cells per
+// block (stores along l_y).  A pair never straddles the l_y = M/2 wrap (M/2 is even).
 __global__ void __launch_bounds__(256, 6)
-grid_gather_kernel(const float2 *__restrict__ spec, const SortedRay *__restrict__ sray,
-                   const float *__restrict__ sphi, const float2 *__restrict__ tab, float2 *__restrict__ grid, int M,
-                   int H, RayIndex ri, float rmax, int amax) {
-    const int ly = blockIdx.x * 32 + (threadIdx.x & 31);
+grid_gather_pair_kernel(const float2 *__restrict__ spec, const SortedRay *__restrict__ sray,
+                        const float *__restrict__ sphi, const float2 *__restrict__ tab, float2 *__restrict__ grid,
+                        int M, int H, RayIndex ri, float rmax, int amax) {
+    const int ly = blockIdx.x * 64 + 2 * (threadIdx.x & 31);
     const int lx = blockIdx.y * 8 + (threadIdx.x >> 5);
     if (lx >= M || ly >= M) return;
     const int cx = lx < M / 2 ? lx : lx - M, cy = ly < M / 2 ? ly : ly - M;
-    if (max(abs(cx), abs(cy)) < kCore) return;  // the core kernel owns this cell
-    float2 acc = make_float2(0.f, 0.f);
-    // periodic images u = c + (a, b) M whose footprint box can reach the sample disc
-    // |z| <= rmax; with every ray in the upper half plane (z_y >= 0) also u_y > -3
-    const float lim = rmax + 3.f, iM = 1.f / (float)M;
+    const bool own0 = max(abs(cx), abs(cy)) >= kCore, own1 = max(abs(cx), abs(cy + 1)) >= kCore;
+    if (!own0 && !own1) return;  // the core kernel owns both cells
+    float2 acc0 = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
+    // periodic images whose union box can reach the sample disc |z| <= rmax; with every ray
+    // in the upper half plane (z_y >= 0) also u_y + 1 > -3
+    const float lim = rmax + 4.f, iM = 1.f / (float)M;
     const int a_lo = max(-amax, (int)ceilf((-lim - (float)cx) * iM));
     const int a_hi = min(amax, (int)floorf((lim - (float)cx) * iM));
     int b_lo = max(-amax, (int)ceilf((-lim - (float)cy) * iM));
-    if (ri.upper) b_lo = max(b_lo, (int)ceilf((-2.f - (float)cy) * iM));
+    if (ri.upper) b_lo = max(b_lo, (int)ceilf((-3.f - (float)cy) * iM));
     const int b_hi = min(amax, (int)floorf((lim - (float)cy) * iM));
     for (int a = a_lo; a <= a_hi; ++a) {
         for (int b = b_lo; b <= b_hi; ++b) {
             const int ux = cx + a * M, uy = cy + b * M;
-            // skip images whose box cannot reach the sample disk |z| <= rmax
+            if (ri.upper && uy <= -4) continue;  // no sample has z_y < u_y + 4
             const float qx = fmaxf(0.f, fmaxf((float)ux - 3.f, -3.f - (float)ux));
-            const float qy = fmaxf(0.f, fmaxf((float)uy - 3.f, -3.f - (float)uy));
+            const float qy = fmaxf(0.f, fmaxf((float)uy - 3.f, -4.f - (float)uy));
             if (qx * qx + qy * qy > rmax * rmax) continue;
             int lo, count;
-            ray_range(sphi, ri, (float)ux, (float)uy, lo, count);
-            const float2 v = gather_rays(spec, sray, tab, ri.n, H, ux, uy, lo, count, 0, 1);
-            acc.x += v.x;
-            acc.y += v.y;
+            // the disc of radius sqrt(3^2 + 3.5^2) (+ margin) around the pair's centre holds both boxes
+            ray_range(sphi, ri, (float)ux, (float)uy + 0.5f, lo, count, 4.6199f);
+            gather_rays_pair(spec, sray, tab, ri.n, H, ux, uy, lo, count, acc0, acc1);
         }
     }
-    grid[(long long)lx * M + ly] = acc;
+    if (own0) grid[(long long)lx * M + ly] = acc0;
+    if (own1) grid[(long long)lx * M + ly + 1] = acc1;
 }
 
 // One warp per core cell (max(|u_x|, |u_y|) < kCore): lanes split the rays, warp sum.
@@ -691,10 +740,10 @@ bp_status launch_fourier(bp_plan *p, const void *sino, bp_dtype dt, float *img, 
             case BP_F16: s = spectra_t(p, (const __half *)sb, st, wuni, delta2, Hf); break;
         }
         if (s != BP_OK) return s;
-        const dim3 g((M + 31) / 32, (M + 7) / 8);
+        const dim3 g((M + 63) / 64, (M + 7) / 8);
         const int amax = (int)std::ceil((f.rmax + 4.25 + M / 2) / M);
-        grid_gather_kernel<<<g, 256, 0, st>>>(f.spec, (const SortedRay *)f.sray, f.sphi, f.kbtab, f.grid, M, H, f.ri,
-                                              f.rmax, amax);
+        grid_gather_pair_kernel<<<g, 256, 0, st>>>(f.spec, (const SortedRay *)f.sray, f.sphi, f.kbtab, f.grid, M, H,
+                                                   f.ri, f.rmax, amax);
         const int core = std::min(kCore, M / 2);
         const int side = 2 * core - 1;
         grid_gather_core_kernel<<<(side * side + 7) / 8, 256, 0, st>>>(f.spec, (const SortedRay *)f.sray, f.sphi,
