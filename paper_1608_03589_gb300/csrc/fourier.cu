@@ -697,7 +697,10 @@ static bp_status spectra_t(bp_plan *p, const Tin *sino, cudaStream_t st, float w
     return BP_OK;
 }
 
-static int rows_per_cta(int M) { return std::max(1, std::min(4, (int)(131072 / (sizeof(float2) * M)))); }
+// Row passes of the 2D transforms: two rows per CTA transformed one after the other by
+// fft_threads(M) threads, so that two CTAs (2 x 32 KB rows + twiddles, 2 x 512 threads at 64
+// registers for M = 4096) share an SM and one's loads overlap the other's transforms.
+static int rows_per_cta(int M) { return M <= 8192 ? 2 : 1; }
 
 // Inverse 2D FFT of the M x M grid (f.grid), pruned to the N x N image, times deap[i_x]
 // deap[i_y] (the deapodisation; ones for no correction), real part into img.
@@ -711,8 +714,7 @@ bp_status launch_grid_to_image(bp_plan *p, const float *deap, float *img, cudaSt
     BP_CUDA_TRY(cudaFuncSetAttribute(pass_y, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smemR));
     BP_CUDA_TRY(cudaFuncSetAttribute(pass_x, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smemR));
     const int nthr = fft_threads(M);
-    int groups = 1;
-    while (groups * 2 <= R && nthr * groups * 2 <= 1024) groups *= 2;
+    const int groups = 1;
     pass_y<<<M / R, nthr * groups, smemR, st>>>(f.grid, f.mid, deap, f.twM, M, f.logM, N, R, p->d_err);
     pass_x<<<(N + R - 1) / R, nthr * groups, smemR, st>>>(f.mid, img, deap, f.twM, M, f.logM, N, R, p->d_err);
     BP_CUDA_TRY(cudaGetLastError());
@@ -764,8 +766,7 @@ bp_status launch_radon_fourier(bp_plan *p, const float *img, float *sino, int ba
     const int R = rows_per_cta(M);
     const size_t smemR = sizeof(float2) * ((size_t)R * M + M / 2);
     const int nthr = fft_threads(M);
-    int groups = 1;
-    while (groups * 2 <= R && nthr * groups * 2 <= 1024) groups *= 2;
+    const int groups = 1;
     const bool e16 = fft_elems(M) == 16;
     auto kx = e16 ? adj_fft_x_kernel<16> : adj_fft_x_kernel<8>;
     auto ky = e16 ? adj_fft_y_kernel<16> : adj_fft_y_kernel<8>;
