@@ -133,6 +133,27 @@ def _dist_init():
     return world, rank, local
 
 
+def replica_slice(rank: int) -> int:
+    """Slice of the workload a rank backprojects: replicas only, each rank its own slice (seed
+    offset by the rank), no data exchanged between ranks."""
+    return rank
+
+
+def max_over_ranks(value: float, dist, device) -> float:
+    """The job's time for a quantity each rank measured: the maximum over ranks (all-reduce MAX)."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def throughput(updates_per_rank: int, world: int, steps: int, total_ms: float) -> float:
+    """Whole-job G updates/s: the updates of all ranks over the slowest rank's time."""
+    return updates_per_rank * world * steps / (total_ms / 1e3) / 1e9
+
+
 # ----------------------------------------------------------------------------------------------- oracle arm
 def run_reference(args, world, rank):
     """FP64 CPU oracle on the host cores: each step backprojects a bounded pixel sample and
@@ -416,7 +437,7 @@ def run_gpu(args, world, rank, local):
     torch.cuda.set_device(dev)
 
     wl = synth.LARGE
-    g_host = wl.sinogram(slice_id=rank).astype(np.float32)
+    g_host = wl.sinogram(slice_id=replica_slice(rank)).astype(np.float32)
     plan = bp.Plan(wl.N, wl.n_det, wl.theta, wl.det_spacing)
     g = torch.from_numpy(g_host).to(dev)
     q = torch.empty_like(g)
@@ -474,17 +495,14 @@ def run_gpu(args, world, rank, local):
     bp_ms = [b.elapsed_time(c) for a, b, c in ev]
     filt_ms = [a.elapsed_time(b) for a, b, c in ev]
     total_ms = sum(step_ms)
-    if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, dist, dev)
 
     if args.no_extras:
         if dist:
             dist.barrier()
             dist.destroy_process_group()
         if rank == 0:
-            print(json.dumps({"value": wl.updates * world * args.steps / (total_ms / 1e3) / 1e9,
+            print(json.dumps({"value": throughput(wl.updates, world, args.steps, total_ms),
                               "unit": "Gupdates/s", "kernel_ms": statistics.mean(bp_ms), "partial": True}))
         return
     # end to end through the host-buffer C-ABI call: pinned host sinogram in, host image out
@@ -501,10 +519,7 @@ def run_gpu(args, world, rank, local):
         t0 = time.perf_counter()
         plan.fbp_host(g_pin, "shepp-logan", out=img_pin)
         e2e_t += time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_t], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_t = float(t.item())
+    e2e_t = max_over_ranks(e2e_t, dist, dev)
 
     # other operators and workloads of the path (reported under "paths", not part of the step)
     extra = {} if args.no_paths else other_paths(plan, q, img, flush, stream, dev,
@@ -522,10 +537,9 @@ def run_gpu(args, world, rank, local):
     bp_avg_s = statistics.mean(bp_ms) / 1e3
     achieved = wl.updates * FLOPS_PER_UPDATE / bp_avg_s / 1e12
     traffic = _traffic_record(shape)
-    updates_all = wl.updates * world * args.steps
     line = {
         "metric": "backprojection G pixel·angle updates/s at 2048²×1800; % of roofline",
-        "value": updates_all / (total_ms / 1e3) / 1e9,
+        "value": throughput(wl.updates, world, args.steps, total_ms),
         "unit": "Gupdates/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms / args.steps,
