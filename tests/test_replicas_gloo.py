@@ -31,7 +31,7 @@ def _worker(rank, world, port, out):
 
 def test_two_replicas_max_timing_and_distinct_slices():
     world, port = 2, 29500 + (os.getpid() % 2000)
-    with mp.Manager() as mgr:
+    with mp.get_context("spawn").Manager() as mgr:
         out = mgr.dict()
         mp.start_processes(_worker, args=(world, port, out), nprocs=world, start_method="spawn")
         res = dict(out)
