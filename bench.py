@@ -167,7 +167,7 @@ def run_reference(args, world, rank):
     g = wl.sinogram()
     q = oracle.filter_rows(g[:8], wl.det_spacing, oracle.SHEPP_LOGAN)  # warm the library
     q_full = g  # timing only: the per-pixel cost does not depend on the values
-    n_pix, n_rows = 2048, 60
+    n_pix, n_rows = 65536, 240  # about 30 ms of 16-core oracle work per step
     rng = np.random.default_rng(0)
     times, upd = [], 0
     for s in range(args.warmup + args.steps):
