@@ -260,7 +260,11 @@ def other_paths(plan, q, img, flush, stream, dev, only=()):
     # 2048^2 x 1800 slice: Fourier R*, R (direct and Fourier adjoint), BF16 storage
     def fourier():
         ms = _timed(lambda: plan.backproject_fourier(q, out=img), stream, flush, 10)
-        return {"ms": ms, "equiv_Gupdates_s": wl.updates / ms / 1e6}
+        plan.set_fourier_width(4)
+        ms4 = _timed(lambda: plan.backproject_fourier(q, out=img), stream, flush, 10)
+        plan.set_fourier_width(6)
+        return {"ms": ms, "equiv_Gupdates_s": wl.updates / ms / 1e6, "kernel_width": 6,
+                "width4_ms": ms4, "width4_equiv_Gupdates_s": wl.updates / ms4 / 1e6}
     guard("fourier_backprojection_2048", fourier)
 
     def fbp_fourier():

@@ -168,6 +168,17 @@ bp_status bp_backproject_logpolar(bp_plan *plan, const void *sino, bp_dtype dtyp
                                   void *stream);
 
 /*
+ * bp_set_fourier_width -- Kaiser-Bessel kernel width W (grid cells) of the gridding in
+ * bp_backproject_fourier, bp_fbp_fourier and the Fourier-path R (Section 5.3 Step 3): 6 (the
+ * default) or 4.  The gridding error falls roughly as exp(-pi W sqrt(1 - 1/sigma)) with the
+ * oversampling sigma = M/N = 2: about 1e-6 relative at W = 6, about 1e-4 at W = 4, which does
+ * (36 - 16)/36 less gridding work per sample.  Synchronises the device and releases the
+ * Fourier workspace (rebuilt by the next Fourier call) when the width changes.
+ * BP_ERR_INVALID_ARG for other widths.
+ */
+bp_status bp_set_fourier_width(bp_plan *plan, int width);
+
+/*
  * bp_fbp_fourier -- filtered backprojection in the Fourier form: the filter `kind` (param =
  * Tikhonov lambda, else ignored) applied inside the projection transforms of
  * bp_backproject_fourier (Section 3 Remark 1 (ii) eq "fbp" with Section 5.3 Step 2.2: one

@@ -288,6 +288,7 @@ bp_status launch_bst(bp_plan *p, const void *sino, bp_dtype dt, float *img, int 
     if ((size_t)p->P * os * sizeof(float2) * 3 / 2 > 200u * 1024u)
         return fail(BP_ERR_UNSUPPORTED, "BST: n_det x oversampling too large for the shared-memory FFT");
     bp_status s = ensure_bst(p, os);
+    if (s == BP_OK) s = ensure_fourier(p);  // its grid may have been released (bp_set_fourier_width)
     if (s != BP_OK) return s;
     BstWork &w = p->bst;
     FourierWork &f = p->four;

@@ -36,6 +36,7 @@ struct RayIndex {
 // Fourier-path workspace and gridding geometry (allocated on first use).
 struct FourierWork {
     int M = 0, logM = 0;        // oversampled grid side (power of two >= 2N)
+    int W = 6;                  // Kaiser-Bessel width (grid cells)
     float beta = 0.f;           // Kaiser-Bessel shape for W = 6 and oversampling M/N
     float rho = 0.f;            // radial sample spacing in grid cells
     float2 *spec = nullptr;     // [n_theta][P/2] sample values c_{k,m}
@@ -119,6 +120,7 @@ struct bp_plan {
     float *d_H[3] = {nullptr, nullptr, nullptr};   // bit-reversed scaled responses per kind
     float H_param[3] = {0.f, 0.f, 0.f};
     // Fourier path
+    int fourier_W = 6;          // Kaiser-Bessel width of the gridding (bp_set_fourier_width)
     bp::FourierWork four;
     bp::BstWork bst;
     bp::LogPolarWork lp;

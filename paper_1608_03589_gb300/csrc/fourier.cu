@@ -38,7 +38,6 @@ namespace bp {
 
 namespace {
 
-constexpr int kW = 6;            // kernel width (grid cells)
 constexpr int kKB = 2048;         // kernel table intervals on [0, W/2]
 constexpr int kCore = 32;         // cells with max(|u_x|, |u_y|) < kCore are gathered by a warp each
 
@@ -50,10 +49,12 @@ struct SortedRay {                // one ray, in increasing angle order
     int pad;
 };
 
-// Kaiser-Bessel kernel phi(d) = I0(beta sqrt(1 - (2d/W)^2)) on |d| <= W/2 from the table
-// tab[i] = (phi(i h), phi((i+1) h) - phi(i h)), h = (W/2)/kKB, built in FP64 on the host.
+// Kaiser-Bessel kernel phi(d) = I0(beta sqrt(1 - (2d/W)^2)) on |d| <= W/2 = HW from the table
+// tab[i] = (phi(i h), phi((i+1) h) - phi(i h)), h = HW/kKB, built in FP64 on the host.  The
+// width W = 2 HW is 6 (the default) or 4 (bp_set_fourier_width).
+template <int HW>
 __device__ __forceinline__ float kb_tab(const float2 *__restrict__ tab, float d) {
-    const float x = fminf(fabsf(d) * (kKB / (0.5f * kW)), (float)kKB - 1e-3f);
+    const float x = fminf(fabsf(d) * ((float)kKB / (float)HW), (float)kKB - 1e-3f);
     const int i = (int)x;
     const float2 v = __ldg(tab + i);
     return fmaf(x - (float)i, v.y, v.x);
@@ -175,11 +176,13 @@ __device__ __forceinline__ void ray_range(const float *__restrict__ sphi, const 
 
 // Sum of the contributions of sorted rays lo + j (j = j0, j0 + dj, ...) < lo + count to
 // the cell image (ux, uy).
+template <int HW>
 __device__ __forceinline__ float2 gather_rays(const float2 *__restrict__ spec, const SortedRay *__restrict__ sray,
                                               const float2 *__restrict__ tab, int n, int H, int ux, int uy, int lo,
                                               int count, int j0, int dj) {
     float2 acc = make_float2(0.f, 0.f);
-    const float fx0 = (float)ux - 3.f, fx1 = (float)ux + 3.f, fy0 = (float)uy - 3.f, fy1 = (float)uy + 3.f;
+    const float h = (float)HW;
+    const float fx0 = (float)ux - h, fx1 = (float)ux + h, fy0 = (float)uy - h, fy1 = (float)uy + h;
     for (int j = j0; j < count; j += dj) {
         int i = lo + j;
         if (i >= n) i -= n;
@@ -199,10 +202,10 @@ __device__ __forceinline__ float2 gather_rays(const float2 *__restrict__ spec, c
         for (int m = m0; m <= m1; ++m) {
             const float t = (float)(m - m0);
             const float dx = fmaf(-t, sx, dx0), dy = fmaf(-t, sy, dy0);
-            // footprint rule of the spreading form: u - z in (-3, 3] per axis
-            if (!(dx > -3.f && dx <= 3.f && dy > -3.f && dy <= 3.f)) continue;
+            // footprint rule of the spreading form: u - z in (-HW, HW] per axis
+            if (!(dx > -h && dx <= h && dy > -h && dy <= h)) continue;
             const float2 v = __ldg(sk + m);
-            const float w = kb_tab(tab, dx) * kb_tab(tab, dy);
+            const float w = kb_tab<HW>(tab, dx) * kb_tab<HW>(tab, dy);
             acc.x = fmaf(w, v.x, acc.x);
             acc.y = fmaf(w, v.y, acc.y);
         }
@@ -211,13 +214,15 @@ __device__ __forceinline__ float2 gather_rays(const float2 *__restrict__ spec, c
 }
 
 // The pair of cells (u_x, u_y) and (u_x, u_y + 1): they share the rays of the angular window
-// of their union box [u_x - 3, u_x + 3) x [u_y - 3, u_y + 4) and, per sample, the spectrum
-// value and the x weight.
+// of their union box [u_x - HW, u_x + HW) x [u_y - HW, u_y + HW + 1) and, per sample, the
+// spectrum value and the x weight.
+template <int HW>
 __device__ __forceinline__ void gather_rays_pair(const float2 *__restrict__ spec,
                                                  const SortedRay *__restrict__ sray, const float2 *__restrict__ tab,
                                                  int n, int H, int ux, int uy, int lo, int count, float2 &acc0,
                                                  float2 &acc1) {
-    const float fx0 = (float)ux - 3.f, fx1 = (float)ux + 3.f, fy0 = (float)uy - 3.f, fy1 = (float)uy + 4.f;
+    const float h = (float)HW;
+    const float fx0 = (float)ux - h, fx1 = (float)ux + h, fy0 = (float)uy - h, fy1 = (float)uy + h + 1.f;
     for (int j = 0; j < count; ++j) {
         int i = lo + j;
         if (i >= n) i -= n;
@@ -237,19 +242,19 @@ __device__ __forceinline__ void gather_rays_pair(const float2 *__restrict__ spec
         for (int m = m0; m <= m1; ++m) {
             const float t = (float)(m - m0);
             const float dx = fmaf(-t, sx, dx0), dy = fmaf(-t, sy, dy0), dy1 = dy + 1.f;
-            // footprint rule of the spreading form: u - z in (-3, 3] per axis
-            if (!(dx > -3.f && dx <= 3.f)) continue;
-            const bool in0 = dy > -3.f && dy <= 3.f, in1 = dy1 > -3.f && dy1 <= 3.f;
+            // footprint rule of the spreading form: u - z in (-HW, HW] per axis
+            if (!(dx > -h && dx <= h)) continue;
+            const bool in0 = dy > -h && dy <= h, in1 = dy1 > -h && dy1 <= h;
             if (!(in0 || in1)) continue;
             const float2 v = __ldg(sk + m);
-            const float kx = kb_tab(tab, dx);
+            const float kx = kb_tab<HW>(tab, dx);
             if (in0) {
-                const float w = kx * kb_tab(tab, dy);
+                const float w = kx * kb_tab<HW>(tab, dy);
                 acc0.x = fmaf(w, v.x, acc0.x);
                 acc0.y = fmaf(w, v.y, acc0.y);
             }
             if (in1) {
-                const float w = kx * kb_tab(tab, dy1);
+                const float w = kx * kb_tab<HW>(tab, dy1);
                 acc1.x = fmaf(w, v.x, acc1.x);
                 acc1.y = fmaf(w, v.y, acc1.y);
             }
@@ -259,6 +264,7 @@ __device__ __forceinline__ void gather_rays_pair(const float2 *__restrict__ spec
 
 // One thread per pair of cells (l_y even, l_y + 1) outside the core square; 64 x 8 cells per
 // block (stores along l_y).  A pair never straddles the l_y = M/2 wrap (M/2 is even).
+template <int HW>
 __global__ void __launch_bounds__(256, 6)
 grid_gather_pair_kernel(const float2 *__restrict__ spec, const SortedRay *__restrict__ sray,
                         const float *__restrict__ sphi, const float2 *__restrict__ tab, float2 *__restrict__ grid,
@@ -271,24 +277,25 @@ grid_gather_pair_kernel(const float2 *__restrict__ spec, const SortedRay *__rest
     if (!own0 && !own1) return;  // the core kernel owns both cells
     float2 acc0 = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
     // periodic images whose union box can reach the sample disc |z| <= rmax; with every ray
-    // in the upper half plane (z_y >= 0) also u_y + 1 > -3
-    const float lim = rmax + 4.f, iM = 1.f / (float)M;
+    // in the upper half plane (z_y >= 0) also u_y + 1 > -HW
+    const float h = (float)HW;
+    const float lim = rmax + h + 1.f, iM = 1.f / (float)M;
     const int a_lo = max(-amax, (int)ceilf((-lim - (float)cx) * iM));
     const int a_hi = min(amax, (int)floorf((lim - (float)cx) * iM));
-    int b_lo = max(-amax, (int)ceilf((-lim - (float)cy) * iM));
-    if (ri.upper) b_lo = max(b_lo, (int)ceilf((-3.f - (float)cy) * iM));
+    const int b_lo = max(-amax, (int)ceilf(((ri.upper ? -h : -lim) - (float)cy) * iM));
     const int b_hi = min(amax, (int)floorf((lim - (float)cy) * iM));
+    // the disc of radius sqrt(HW^2 + (HW + 1/2)^2) (+ margin) around the pair's centre holds both boxes
+    const float R = sqrtf(h * h + (h + 0.5f) * (h + 0.5f)) + 0.01f;
     for (int a = a_lo; a <= a_hi; ++a) {
         for (int b = b_lo; b <= b_hi; ++b) {
             const int ux = cx + a * M, uy = cy + b * M;
-            if (ri.upper && uy <= -4) continue;  // no sample has z_y < u_y + 4
-            const float qx = fmaxf(0.f, fmaxf((float)ux - 3.f, -3.f - (float)ux));
-            const float qy = fmaxf(0.f, fmaxf((float)uy - 3.f, -4.f - (float)uy));
+            if (ri.upper && uy <= -HW - 1) continue;  // no sample has z_y < u_y + HW + 1
+            const float qx = fmaxf(0.f, fmaxf((float)ux - h, -h - (float)ux));
+            const float qy = fmaxf(0.f, fmaxf((float)uy - h, -h - 1.f - (float)uy));
             if (qx * qx + qy * qy > rmax * rmax) continue;
             int lo, count;
-            // the disc of radius sqrt(3^2 + 3.5^2) (+ margin) around the pair's centre holds both boxes
-            ray_range(sphi, ri, (float)ux, (float)uy + 0.5f, lo, count, 4.6199f);
-            gather_rays_pair(spec, sray, tab, ri.n, H, ux, uy, lo, count, acc0, acc1);
+            ray_range(sphi, ri, (float)ux, (float)uy + 0.5f, lo, count, R);
+            gather_rays_pair<HW>(spec, sray, tab, ri.n, H, ux, uy, lo, count, acc0, acc1);
         }
     }
     if (own0) grid[(long long)lx * M + ly] = acc0;
@@ -296,6 +303,7 @@ grid_gather_pair_kernel(const float2 *__restrict__ spec, const SortedRay *__rest
 }
 
 // One warp per core cell (max(|u_x|, |u_y|) < kCore): lanes split the rays, warp sum.
+template <int HW>
 __global__ void __launch_bounds__(256)
 grid_gather_core_kernel(const float2 *__restrict__ spec, const SortedRay *__restrict__ sray,
                         const float *__restrict__ sphi, const float2 *__restrict__ tab, float2 *__restrict__ grid,
@@ -309,13 +317,15 @@ grid_gather_core_kernel(const float2 *__restrict__ spec, const SortedRay *__rest
     for (int a = -amax; a <= amax; ++a) {
         for (int b = -amax; b <= amax; ++b) {
             const int ux = cx + a * M, uy = cy + b * M;
-            if (ri.upper && uy <= -3) continue;  // no sample has z_y < u_y + 3
-            const float qx = fmaxf(0.f, fmaxf((float)ux - 3.f, -3.f - (float)ux));
-            const float qy = fmaxf(0.f, fmaxf((float)uy - 3.f, -3.f - (float)uy));
+            const float h = (float)HW;
+            if (ri.upper && uy <= -HW) continue;  // no sample has z_y < u_y + HW
+            const float qx = fmaxf(0.f, fmaxf((float)ux - h, -h - (float)ux));
+            const float qy = fmaxf(0.f, fmaxf((float)uy - h, -h - (float)uy));
             if (qx * qx + qy * qy > rmax * rmax) continue;
             int lo, count;
-            ray_range(sphi, ri, (float)ux, (float)uy, lo, count);
-            const float2 v = gather_rays(spec, sray, tab, ri.n, H, ux, uy, lo, count, lane, 32);
+            // the disc of radius HW sqrt(2) (+ margin) around the cell holds its box
+            ray_range(sphi, ri, (float)ux, (float)uy, lo, count, h * 1.41421356f + 0.0002f);
+            const float2 v = gather_rays<HW>(spec, sray, tab, ri.n, H, ux, uy, lo, count, lane, 32);
             acc.x += v.x;
             acc.y += v.y;
         }
@@ -456,6 +466,7 @@ adj_fft_y_kernel(const float2 *__restrict__ T, float2 *__restrict__ grid, const 
 // Interpolation at the polar samples (transpose of the spreading): one thread per sample,
 // consecutive samples of one ray in consecutive lanes; result times the conjugate sample
 // factor (1/P)(m ? 2 : 1) exp(-i pi m (n_det-1)/P) exp(-2 pi i delta (z_x + z_y)/M) and dx^2/dt.
+template <int HW>
 __global__ void __launch_bounds__(256)
 adj_interp_kernel(const float2 *__restrict__ grid, float2 *__restrict__ spec, const long long *__restrict__ ray,
                   int M, int H, int P, int n_det, const float2 *__restrict__ tab, float delta2_over_M, float scale,
@@ -468,18 +479,20 @@ adj_interp_kernel(const float2 *__restrict__ grid, float2 *__restrict__ spec, co
     const float rx = (float)(unsigned)(zx & 0xffffffffLL) * 2.3283064365386963e-10f;
     const float ry = (float)(unsigned)(zy & 0xffffffffLL) * 2.3283064365386963e-10f;
     const int Mmask = M - 1;
-    float wy[kW];
+    // the 2 HW cells u with z - u in [-HW, HW): u = floor(z) - (HW - 1) .. floor(z) + HW
+    constexpr int W = 2 * HW;
+    float wy[W];
 #pragma unroll
-    for (int t = 0; t < kW; ++t) wy[t] = kb_tab(tab, (float)(t - 2) - ry);
+    for (int t = 0; t < W; ++t) wy[t] = kb_tab<HW>(tab, (float)(t - (HW - 1)) - ry);
     float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int tx = 0; tx < kW; ++tx) {
-        const float wx = kb_tab(tab, (float)(tx - 2) - rx);
-        const float2 *row = grid + (long long)((fx - 2 + tx) & Mmask) * M;
+    for (int tx = 0; tx < W; ++tx) {
+        const float wx = kb_tab<HW>(tab, (float)(tx - (HW - 1)) - rx);
+        const float2 *row = grid + (long long)((fx - (HW - 1) + tx) & Mmask) * M;
         float2 r = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int ty = 0; ty < kW; ++ty) {
-            const float2 v = __ldg(row + ((fy - 2 + ty) & Mmask));
+        for (int ty = 0; ty < W; ++ty) {
+            const float2 v = __ldg(row + ((fy - (HW - 1) + ty) & Mmask));
             r.x = fmaf(wy[ty], v.x, r.x);
             r.y = fmaf(wy[ty], v.y, r.y);
         }
@@ -535,8 +548,9 @@ adj_rows_kernel(const float2 *__restrict__ spec, float *__restrict__ sino, const
     }
 }
 
-double kb_hat(double f, double beta) {
+double kb_hat(double f, double beta, int width) {
     // Fourier transform of I0(beta sqrt(1 - (2t/W)^2)) on |t| <= W/2 at frequency f (cycles per cell)
+    const double kW = width;
     const double x = M_PI * kW * f;
     const double a2 = beta * beta - x * x;
     if (a2 > 0) {
@@ -578,6 +592,7 @@ bp_status ensure_fourier(bp_plan *p) {
         return fail(BP_ERR_UNSUPPORTED, "Fourier path: N too large for the shared-memory FFT (N <= 8192)");
     if ((size_t)P * sizeof(float2) > 200u * 1024u)
         return fail(BP_ERR_UNSUPPORTED, "Fourier path: n_det too large for the shared-memory FFT (n_det <= 8192)");
+    const int kW = p->fourier_W;  // kernel width, 6 or 4
     const double sigma = (double)M / N;
     double b2 = (kW / sigma) * (kW / sigma) * (sigma - 0.5) * (sigma - 0.5) - 0.8;
     const double beta = M_PI * std::sqrt(std::max(b2, 1.0));
@@ -642,7 +657,7 @@ bp_status ensure_fourier(bp_plan *p) {
     }
     // deapodisation 1 / phi_hat(i - floor(N/2)) (separable), weights, twiddles
     std::vector<float> deap(N), wk(n_theta);
-    for (int i = 0; i < N; ++i) deap[i] = (float)(1.0 / kb_hat((double)(i - N / 2) / M, beta));
+    for (int i = 0; i < N; ++i) deap[i] = (float)(1.0 / kb_hat((double)(i - N / 2) / M, beta, kW));
     for (int k = 0; k < n_theta; ++k) wk[k] = (float)p->w[k];
     std::vector<float2> tw(M / 2);
     for (int i = 0; i < M / 2; ++i) {
@@ -651,6 +666,7 @@ bp_status ensure_fourier(bp_plan *p) {
     }
 
     f.M = M;
+    f.W = kW;
     f.logM = ilog2(M);
     f.beta = (float)beta;
     f.rho = (float)rho;
@@ -744,13 +760,20 @@ bp_status launch_fourier(bp_plan *p, const void *sino, bp_dtype dt, float *img, 
         if (s != BP_OK) return s;
         const dim3 g((M + 63) / 64, (M + 7) / 8);
         const int amax = (int)std::ceil((f.rmax + 4.25 + M / 2) / M);
-        grid_gather_pair_kernel<<<g, 256, 0, st>>>(f.spec, (const SortedRay *)f.sray, f.sphi, f.kbtab, f.grid, M, H,
-                                                   f.ri, f.rmax, amax);
         const int core = std::min(kCore, M / 2);
         const int side = 2 * core - 1;
-        grid_gather_core_kernel<<<(side * side + 7) / 8, 256, 0, st>>>(f.spec, (const SortedRay *)f.sray, f.sphi,
-                                                                       f.kbtab, f.grid, M, H, f.ri, f.rmax, amax,
-                                                                       core);
+        const SortedRay *sr = (const SortedRay *)f.sray;
+        if (f.W == 4) {
+            grid_gather_pair_kernel<2><<<g, 256, 0, st>>>(f.spec, sr, f.sphi, f.kbtab, f.grid, M, H, f.ri, f.rmax,
+                                                          amax);
+            grid_gather_core_kernel<2><<<(side * side + 7) / 8, 256, 0, st>>>(f.spec, sr, f.sphi, f.kbtab, f.grid,
+                                                                              M, H, f.ri, f.rmax, amax, core);
+        } else {
+            grid_gather_pair_kernel<3><<<g, 256, 0, st>>>(f.spec, sr, f.sphi, f.kbtab, f.grid, M, H, f.ri, f.rmax,
+                                                          amax);
+            grid_gather_core_kernel<3><<<(side * side + 7) / 8, 256, 0, st>>>(f.spec, sr, f.sphi, f.kbtab, f.grid,
+                                                                              M, H, f.ri, f.rmax, amax, core);
+        }
         BP_CUDA_TRY(cudaGetLastError());
         if ((s = launch_grid_to_image(p, f.deapod, img + (size_t)b * N * N, st)) != BP_OK) return s;
     }
@@ -780,9 +803,9 @@ bp_status launch_radon_fourier(bp_plan *p, const float *img, float *sino, int ba
         kx<<<(N + R - 1) / R, nthr * groups, smemR, st>>>(img + (size_t)b * N * N, f.mid, f.deapod, f.twM, M, f.logM,
                                                          N, R);
         ky<<<M / R, nthr * groups, smemR, st>>>(f.mid, f.grid, f.twM, M, f.logM, N, R);
-        adj_interp_kernel<<<dim3((H + 255) / 256, p->n_theta), 256, 0, st>>>(f.grid, f.spec, f.ray, M, H, P, p->n_det,
-                                                                              f.kbtab, delta2, scale,
-                                                                              per_angle_w ? f.wk : nullptr);
+        auto ki = f.W == 4 ? adj_interp_kernel<2> : adj_interp_kernel<3>;
+        ki<<<dim3((H + 255) / 256, p->n_theta), 256, 0, st>>>(f.grid, f.spec, f.ray, M, H, P, p->n_det, f.kbtab, delta2,
+                                                               scale, per_angle_w ? f.wk : nullptr);
         kr<<<(p->n_theta + 1) / 2, fft_threads(P), sizeof(float2) * (P + P / 2), st>>>(
             f.spec, sino + (size_t)b * p->n_theta * p->n_det, p->d_twP, p->n_theta, p->n_det, ilog2(P));
         BP_CUDA_TRY(cudaGetLastError());

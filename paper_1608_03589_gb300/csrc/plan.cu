@@ -287,6 +287,18 @@ extern "C" bp_status bp_backproject_logpolar(bp_plan *p, const void *sino, bp_dt
     return launch_logpolar(p, sino, dtype, img, batch, (cudaStream_t)stream);
 }
 
+extern "C" bp_status bp_set_fourier_width(bp_plan *p, int width) {
+    set_error("");
+    bp_status st = check_plan(p);
+    if (st != BP_OK) return st;
+    if (width != 4 && width != 6) return fail(BP_ERR_INVALID_ARG, "Fourier kernel width must be 4 or 6");
+    if (width == p->fourier_W) return BP_OK;
+    BP_CUDA_TRY(cudaDeviceSynchronize());  // no call of this plan may still use the workspace
+    free_fourier(p);
+    p->fourier_W = width;
+    return BP_OK;
+}
+
 extern "C" bp_status bp_radon(bp_plan *p, const float *img, float *sino, int batch, int fourier_adjoint,
                               void *stream) {
     set_error("");

@@ -167,3 +167,55 @@ def test_fbp_fourier_batch_low_precision_and_full_size():
     ref = oracle.bp_trig_points(q, wl.N, wl.theta, wl.det_spacing, pix)
     got = img.reshape(-1)[torch.from_numpy(pix).to(dev())].cpu().numpy()
     assert oracle.rel_l2(got, ref) <= TOL_FOURIER
+
+
+# ----------------------------------------------------------------------------------- gridding kernel width 4
+@pytest.mark.parametrize("N,n_det,n_theta,dt_scale,seed", [(64, 64, 90, 1.0, 20), (37, 41, 7, 1.3, 21),
+                                                            (96, 128, 64, 0.8, 22)])
+def test_fourier_width4_vs_oracle(N, n_det, n_theta, dt_scale, seed):
+    rng = np.random.default_rng(seed)
+    theta = random_theta(rng, n_theta) if seed % 2 else synth.uniform_theta(n_theta)
+    dt = dt_scale * 2.0 / n_det
+    g = to_dev(rng.normal(size=(n_theta, n_det)))
+    plan = bp.Plan(N, n_det, theta, dt)
+    ref = oracle.bp_trig_dirichlet(rounded(g), N, theta, dt)
+    e6 = oracle.rel_l2(plan.backproject_fourier(g).cpu().numpy(), ref)
+    plan.set_fourier_width(4)
+    e4 = oracle.rel_l2(plan.backproject_fourier(g).cpu().numpy(), ref)
+    plan.set_fourier_width(6)
+    e6b = oracle.rel_l2(plan.backproject_fourier(g).cpu().numpy(), ref)
+    print(f"N={N}: gridding error W=6 {e6:.2e}, W=4 {e4:.2e}")
+    assert e4 <= TOL_FOURIER and e6 < e4 and abs(e6b - e6) <= 1e-3 * e6 + 1e-9
+    with pytest.raises(bp.BPError, match="width"):
+        plan.set_fourier_width(5)
+
+
+def test_fourier_width4_adjoint_and_full_size():
+    # the Fourier R stays the exact transpose of the Fourier R* at W = 4
+    rng = np.random.default_rng(33)
+    N, n_det, n_theta = 200, 181, 97
+    theta = random_theta(rng, n_theta)
+    dt = 1.1 * 2.0 / n_det
+    plan = bp.Plan(N, n_det, theta, dt)
+    plan.set_fourier_width(4)
+    f = to_dev(rng.normal(size=(N, N)))
+    g = to_dev(rng.normal(size=(n_theta, n_det)))
+    Rf = rounded(plan.radon(f, fourier=True))
+    Bg = rounded(plan.backproject_fourier(g))
+    w = oracle.weights(theta)
+    lhs = float(np.sum(w[:, None] * dt * Rf * rounded(g)))
+    rhs = float((2.0 / N) ** 2 * np.sum(rounded(f) * Bg))
+    scale = float(np.linalg.norm(w[:, None] * dt * Rf) * np.linalg.norm(rounded(g)))
+    assert abs(lhs - rhs) <= 1e-5 * scale
+    # 2048^2 x 1800, sampled pixels against the band-limited oracle
+    wl = synth.LARGE
+    big = bp.Plan(wl.N, wl.n_det, wl.theta, wl.det_spacing)
+    big.set_fourier_width(4)
+    q = big.filter(to_dev(wl.sinogram()), "shepp-logan")
+    img = big.backproject_fourier(q)
+    pix = sample_pixels(wl.N, 150, seed=34)
+    ref = oracle.bp_trig_points(rounded(q), wl.N, wl.theta, wl.det_spacing, pix)
+    got = img.reshape(-1)[torch.from_numpy(pix).to(dev())].cpu().numpy()
+    err = oracle.rel_l2(got, ref)
+    print(f"2048^2 x 1800 at W=4: Fourier vs band-limited oracle rel-L2 {err:.2e}")
+    assert err <= TOL_FOURIER
