@@ -51,7 +51,7 @@ typedef enum {
     BP_ERR_INVALID_ARG = 1,  /* null pointer, bad size, bad enum, misaligned pointer */
     BP_ERR_CUDA = 2,         /* a CUDA runtime call or kernel launch failed */
     BP_ERR_OOM = 3,          /* device or host allocation failed (nothing leaked) */
-    BP_ERR_UNSUPPORTED = 4,  /* valid request outside this build's limits */
+    BP_ERR_UNSUPPORTED = 4,  /* valid request outside the library's limits */
     BP_ERR_TIMEOUT = 5       /* a bounded device-side wait gave up (batched path) */
 } bp_status;
 
@@ -63,7 +63,7 @@ typedef enum {
     BP_TIKHONOV = 2      /* |nu| / (1 + param |nu|), Section 6 (nu in cycles per unit t) */
 } bp_filter_kind;
 
-/* Limits of this build (BP_ERR_UNSUPPORTED beyond them). */
+/* Limits of the library (BP_ERR_UNSUPPORTED beyond them). */
 #define BP_MAX_N 16384
 #define BP_MAX_NDET 16384
 #define BP_MAX_NTHETA 65536
