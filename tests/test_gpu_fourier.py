@@ -219,3 +219,31 @@ def test_fourier_width4_adjoint_and_full_size():
     err = oracle.rel_l2(got, ref)
     print(f"2048^2 x 1800 at W=4: Fourier vs band-limited oracle rel-L2 {err:.2e}")
     assert err <= TOL_FOURIER
+
+
+def test_transform_paths_replay_from_cuda_graph():
+    # after one call (which builds the plan's workspaces) the Fourier FBP, the BST interpolation
+    # and the log-polar R* are recorded in a CUDA graph and replay to the same bits
+    rng = np.random.default_rng(40)
+    N, n_det, n_theta = 96, 96, 60
+    plan = bp.Plan(N, n_det, synth.uniform_theta(n_theta))
+    g = to_dev(rng.normal(size=(2, n_theta, n_det)))
+    outs = [torch.empty((2, N, N), device=dev()) for _ in range(3)]
+    calls = [lambda: plan.fbp_fourier(g, "shepp-logan", out=outs[0]),
+             lambda: plan.backproject_bst(g, 4, out=outs[1]),
+             lambda: plan.backproject_logpolar(g, out=outs[2])]
+    for c in calls:
+        c()
+    eager = [o.clone() for o in outs]
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        for c in calls:
+            c()
+    for o in outs:
+        o.fill_(-1.0)
+    graph.replay()
+    torch.cuda.synchronize()
+    for o, e in zip(outs, eager):
+        assert torch.equal(o, e)
