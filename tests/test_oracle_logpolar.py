@@ -4,6 +4,7 @@ brute force of each step on tiny meshes, the point-mass property of the kernel, 
 quarter-turn symmetry, and first-order convergence to closed forms and to the independent
 C oracle of R*.  CPU only."""
 import math
+import os
 
 import numpy as np
 import pytest
@@ -14,12 +15,18 @@ from oracle import logpolar as lp
 from paper_1608_03589_gb300 import synth
 
 
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "logpolar_mesh_example.txt")
+
+
 def test_mesh_matches_the_paper_size_rule():
-    # the paper's example: 1024 bins on [-1, 1] (ds = 2/1024) and a 1024^2 image give
-    # N_rho = ln(1/1024) / ln(1 - ds) ~ 3546 nodes; our mesh adds the half-pixel below rho_0
-    # and the last half bin of the detector (a few nodes more)
-    m = lp.mesh(1024, 1024, 720, 2.0 / 1024)
-    assert 3546 <= m.n_rho <= 3546 + 10
+    # the paper's worked example (tests/golden): 1024 bins on [-1, 1] (ds = 2/1024) and a
+    # 1024^2 image give N_rho = ln(1/1024) / ln(1 - ds) = 3546 nodes; our mesh adds the
+    # half-pixel below rho_0 and the last half bin of the detector (a few nodes more)
+    n_s, n_x, n_y, n_rho = [int(v) for v in open(GOLDEN).read().split("\n")[-2].split()]
+    ds = 2.0 / n_s
+    assert math.ceil(math.log(min(1.0 / n_x, 1.0 / n_y)) / math.log(1.0 - ds)) == n_rho
+    m = lp.mesh(n_x, n_s, 720, ds)
+    assert n_rho <= m.n_rho <= n_rho + 10
     s_max = 0.5 * 1023 * (2.0 / 1024) + 2.0 / 1024
     assert s_max * (1.0 - math.exp(-m.drho)) <= 2.0 / 1024 + 1e-15  # outer step <= pitch
     assert m.L >= m.n_rho + m.n_out and m.n_phi == 2048
