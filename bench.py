@@ -28,7 +28,9 @@ sys.path.insert(0, ROOT)
 FLOPS_PER_UPDATE = 7          # coordinate FMA (2) + fraction (1) + lerp sub and FMA (3) + accumulate (1)
 FP32_LANES_PER_SM = 128       # FP32 FMA lanes per SM
 L2_FLUSH_BYTES = 256 << 20    # > 129 MB L2
-SMEM_UPDATES_PER_CLK = 16     # 128 B/clk/SM of shared-memory wavefronts / 8 B per update
+# shared-memory wavefront caps (128 B/clk/SM): the pair-table kernel reads 8 B per update,
+# the 2 x 2-block kernel one 16-byte entry per 4 updates
+SMEM_UPDATES_PER_CLK = {"bp_direct_tma_kernel": 16, "bp_direct_quad_kernel": 32}
 
 
 def _peaks():
@@ -541,6 +543,11 @@ def run_gpu(args, world, rank, local):
     bp_avg_s = statistics.mean(bp_ms) / 1e3
     achieved = wl.updates * FLOPS_PER_UPDATE / bp_avg_s / 1e12
     traffic = _traffic_record(shape)
+    # the library takes the 2 x 2-block kernel when every pixel step |c|, |s| = |cos|, |sin| dx/dt <= 1
+    ratio = (2.0 / wl.N) / wl.det_spacing
+    steps = np.abs(np.stack([np.cos(wl.theta), np.sin(wl.theta)])) * ratio
+    kernel = "bp_direct_quad_kernel" if float(np.max(steps.astype(np.float32))) <= 1.0 else "bp_direct_tma_kernel"
+    smem_cap = SMEM_UPDATES_PER_CLK[kernel] * props.multi_processor_count * sm_max_mhz * 1e6
     line = {
         "metric": "backprojection G pixel·angle updates/s at 2048²×1800; % of roofline",
         "value": throughput(wl.updates, world, args.steps, total_ms),
@@ -554,7 +561,7 @@ def run_gpu(args, world, rank, local):
                    "launch_shape": {"stage": shape[0], "angle_groups": shape[1],
                                     "picked_by": picked},
                    "parallelism": f"independent slice per GPU x{world}"},
-        "roofline": {"bound": "alu", "kernel": "bp_direct_kernel", "achieved": achieved,
+        "roofline": {"bound": "alu", "kernel": kernel, "achieved": achieved,
                      "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
                      "flops_per_update": FLOPS_PER_UPDATE,
                      "peak_basis": f"{props.multi_processor_count} SM x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
@@ -562,12 +569,20 @@ def run_gpu(args, world, rank, local):
                      "traffic": (traffic["dram_bytes_per_launch"] if traffic else None),
                      "algorithmic_bytes": wl.n_theta * wl.n_det * 4 + wl.N * wl.N * 4,
                      "kernel_ms": bp_avg_s * 1e3, "filter_ms": statistics.mean(filt_ms),
-                     "binding_limit": {
-                         "resource": "shared-memory wavefronts (one 8-byte table pair per update; 64-bit warp "
-                                     "load = 2 wavefronts; 1 wavefront/clk/SM)",
-                         "cap_Gupdates_s": SMEM_UPDATES_PER_CLK * props.multi_processor_count * sm_max_mhz / 1e3,
-                         "frac": wl.updates / bp_avg_s / (SMEM_UPDATES_PER_CLK * props.multi_processor_count *
-                                                          sm_max_mhz * 1e6)}},
+                     "smem_limit": {
+                         "resource": "shared-memory wavefronts, 1/clk/SM (" + (
+                             "one 16-byte table entry per 2 x 2 pixel block" if kernel == "bp_direct_quad_kernel"
+                             else "one 8-byte table pair per update") + ")",
+                         "cap_Gupdates_s": smem_cap / 1e9,
+                         "frac": wl.updates / bp_avg_s / smem_cap},
+                     "issue_limit": ({
+                         "resource": "instruction issue, 1 warp instruction/clk per SM sub-partition",
+                         "warp_inst_per_update_ncu": traffic["warp_inst_per_update"],
+                         "cap_Gupdates_s": 4 * 32 / traffic["warp_inst_per_update"] * props.multi_processor_count *
+                                           sm_max_mhz / 1e3,
+                         "frac": wl.updates / bp_avg_s / (4 * 32 / traffic["warp_inst_per_update"] *
+                                                          props.multi_processor_count * sm_max_mhz * 1e6)}
+                                     if traffic and "warp_inst_per_update" in traffic else None)},
         "e2e": {"value": wl.updates * world * n_e2e / e2e_t / 1e9, "unit": "Gupdates/s",
                 "h2d_bytes_per_step": g_host.nbytes, "d2h_bytes_per_step": wl.N * wl.N * 4,
                 "call": "bp_fbp_host (pinned host in/out)"},

@@ -114,6 +114,7 @@ struct bp_plan {
     bp::AngleParam *d_ang = nullptr;
     int W = 0;   // shared-memory window (entries) per (tile, angle)
     int C = 0;   // window centre offset
+    float step_max = 0.f;  // max over the angles of max(|c|, |s|), the u step per pixel
     // filter
     int P = 0;                 // FFT length for the filter (power of two >= 2 n_det)
     float2 *d_twP = nullptr;   // P/2 twiddles exp(-2 pi i r / P)
@@ -201,6 +202,11 @@ __device__ __forceinline__ unsigned smem_u32(const void *p) {
 }
 __device__ __forceinline__ void sts64(unsigned addr, float2 v) {
     asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(addr), "f"(v.x), "f"(v.y) : "memory");
+}
+__device__ __forceinline__ float4 lds128(unsigned addr) {
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(addr));
+    return v;
 }
 __device__ __forceinline__ float2 lds64(unsigned addr) {
     float2 v;

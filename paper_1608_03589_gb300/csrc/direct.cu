@@ -15,7 +15,9 @@
 // FADD.  The per-tile window origin J0 and base coordinate come from exact 32.32 fixed-
 // point tile stepping, so float32 only ever holds tile-local coordinates (|q| <= W/2).
 //
-// Two variants.  bp_direct_tma_kernel (used whenever the sinogram rows are 16-byte strided):
+// Three variants.  bp_direct_quad_kernel (pixels no larger than detector bins, 16-byte strided
+// rows): the TMA pipeline below with a 2 x 2-block table, described at the kernel.
+// bp_direct_tma_kernel (other geometries with 16-byte strided rows):
 // the raw windows of stage s+2 are fetched by TMA (one 3D box per angle, zero-filled off the
 // detector) into a double buffer while stage s computes; the (e, d) table is double
 // buffered too, so each stage has a single block barrier; coordinates and the magic-number
@@ -198,6 +200,223 @@ bp_direct_tma_kernel(const __grid_constant__ CUtensorMap tmap, float *__restrict
     }
 }
 
+// Saturated add: min(max(a + b, 0), 1).
+__device__ __forceinline__ float add_sat(float a, float b) {
+    float d;
+    asm("add.sat.f32 %0, %1, %2;" : "=f"(d) : "f"(a), "f"(b));
+    return d;
+}
+
+// v[i] <- v[i ^ m] for the four corner roles of a block (bit 0: x flipped, bit 1: y flipped),
+// with compile-time indices only.
+__device__ __forceinline__ void xor_permute(float (&v)[4], int m) {
+    if (m & 1) {
+        float t = v[0]; v[0] = v[1]; v[1] = t;
+        t = v[2]; v[2] = v[3]; v[3] = t;
+    }
+    if (m & 2) {
+        float t = v[0]; v[0] = v[2]; v[2] = t;
+        t = v[1]; v[1] = v[3]; v[3] = t;
+    }
+}
+
+// Quad variant of the TMA kernel, used when |c|, |s| <= 1 (pixels no larger than detector
+// bins): a thread owns four 2 x 2 pixel blocks, and one float4 table entry serves all four
+// pixels of a block.  Over a 2 x 2 block the detector coordinate spans |c| + |s| <= 2 bins,
+// so with j = floor(u at the block's lowest corner) and r = u - j the four pixels need only
+// g_j .. g_{j+3}, and the linear interpolant is exactly the sum of clamped ramps
+//     w g(u) = w g_j + sum_{i=0..2} w (g_{j+i+1} - g_{j+i}) sat(r - i),   sat = clamp to [0, 1]
+// (ramps above r vanish, those below are 1).  The entry (w g_j, w dg_j, w dg_{j+1}, w dg_{j+2})
+// is one 16-byte load per block instead of one 8-byte load per pixel, which halves the
+// shared-memory traffic that bounds the pair-table kernel; the common term w g_j goes into
+// one accumulator per block.  The lowest corner has r in [0, 1] (one FFMA), the two side
+// corners r + |c|, r + |s| <= 2 (two ramps), the far corner r + |c| + |s| (three ramps, two
+// when |c| + |s| >= 1); the clamps are FADD.SAT.  j comes from the magic-number floor (paired
+// add rounded toward minus infinity) whose bits index shared memory.  Which pixel of a block
+// is its lowest corner depends on the signs of (c, s): the accumulators are kept per role and
+// exchanged when the signs change between angles.
+template <typename Tin, int STAGE>
+__global__ void __launch_bounds__(kThreads, 3)
+bp_direct_quad_kernel(const __grid_constant__ CUtensorMap tmap, float *__restrict__ img,
+                      const AngleParam *__restrict__ ap, int N, int n_theta, int W, int C, int Wb, int RS,
+                      int accumulate, int tiles, int asplit, long long img_stride, int *__restrict__ err, float wuni) {
+    constexpr int TPA = kThreads / STAGE;
+    extern __shared__ __align__(128) unsigned char dsm[];
+    unsigned char *raw = dsm;                                           // [2][STAGE] rows of RS bytes
+    float4 *tab = reinterpret_cast<float4 *>(dsm + 2 * STAGE * RS);    // [2][STAGE][W]
+    __shared__ float4 sq[3][STAGE];   // q at the lowest corner of block (0,0), c, s, table base bits
+    __shared__ float4 sr[3][STAGE];   // |c|, |c| - 1, |s|, |s| - 1: ramp offsets of the side corners
+    __shared__ float4 sf[3][STAGE];   // |c| + |s| - {0, 1, 2}: far corner; corner-role bits
+    __shared__ int sof[3][STAGE];     // J0 - J0r (TMA box starts at the 8-aligned J0r)
+    __shared__ float sw[3][STAGE];
+    __shared__ __align__(8) unsigned long long bars[2];
+
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    // each group of 8 lanes covers 4 x 2 blocks (8 x 4 pixels): their table entries lie
+    // within 8 consecutive bins, so the 128-bit loads of a quarter warp are conflict-free
+    const int qtr = lane >> 3;
+    const int X0 = (lane & 3) + 4 * (qtr & 1);                  // block column (+ 8 a, a < 4)
+    const int Y0 = ((lane >> 2) & 1) + 2 * (qtr >> 1) + 4 * warp;  // block row
+    const int tx = blockIdx.x, ty = blockIdx.y % tiles, grp = blockIdx.y / tiles, bz = blockIdx.z;
+    img += (long long)bz * img_stride;
+    const uint32_t bar0 = smem_u32(&bars[0]);
+    const unsigned tab_u32 = smem_u32(tab);
+    const int S_all = (n_theta + STAGE - 1) / STAGE;
+    const int s0 = group_stage(grp, S_all, asplit);
+    const int S = group_stage(grp + 1, S_all, asplit) - s0;
+
+    if (tid == 0) {
+        mbar_init(bar0, 1);
+        mbar_init(bar0 + 8, 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+
+    auto prepare = [&](int i) {
+        const int k0 = (s0 + i) * STAGE, kn = min(STAGE, n_theta - k0), b = i & 1, slot = i % 3;
+        if (tid == 0) mbar_expect_tx(bar0 + 8 * b, (uint32_t)(kn * Wb * (int)sizeof(Tin)));
+        if (tid < kn) {
+            const AngleParam p = ap[k0 + tid];
+            const long long U = p.U00 + (long long)tx * p.CT + (long long)ty * p.ST;
+            const int Ji = (int)(U >> 32);
+            const float frac = (float)(unsigned)(U & 0xffffffffLL) * 2.3283064365386963e-10f;
+            const float lo = fminf(p.c, 0.f) + fminf(p.s, 0.f);
+            const int J0 = Ji + (int)floorf((float)(kTile - 1) * lo) - 1;
+            const int J0r = J0 & ~7;
+            const float q0 = (float)(Ji - J0 - C) + frac + lo;
+            const unsigned base = tab_u32 + (unsigned)((b * STAGE + tid) * W) * 16u + 16u * (unsigned)C -
+                                  (kMagicBits << 4);
+            const float ac = fabsf(p.c), as = fabsf(p.s), af = ac + as;
+            const int role = (p.c < 0.f ? 1 : 0) | (p.s < 0.f ? 2 : 0);
+            sq[slot][tid] = make_float4(q0, p.c, p.s, __uint_as_float(base));
+            sr[slot][tid] = make_float4(ac, ac - 1.f, as, as - 1.f);
+            sf[slot][tid] = make_float4(af, af - 1.f, af - 2.f, __int_as_float(role));
+            sof[slot][tid] = J0 - J0r;
+            sw[slot][tid] = wuni > 0.f ? wuni : p.w;
+            tma_load_3d(smem_u32(raw + (b * STAGE + tid) * RS), &tmap, J0r, k0 + tid, bz, bar0 + 8 * b);
+        }
+    };
+
+    // per block: the four corner sums in role order (lowest, side x, side y, far) and the
+    // common term sum_k w g_j
+    float acc[4][4], G[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        G[a] = 0.f;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) acc[a][r] = 0.f;
+    }
+    int role = 0;
+    const float fx = (float)(2 * X0), fy = (float)(2 * Y0);
+    const unsigned long long MM = pk2(kMagic, kMagic);
+    // table build: TPA threads per angle, each a run of consecutive entries (bins reused)
+    const int run = (W + TPA - 1) / TPA;
+
+    prepare(0);
+    if (S > 1) prepare(1);
+    __syncthreads();
+    bool ok = true;
+    for (int i = 0; i < S; ++i) {
+        const int b = i & 1, slot = i % 3;
+        const int kn = min(STAGE, n_theta - (s0 + i) * STAGE);
+        ok &= mbar_wait(bar0 + 8 * b, (uint32_t)((i >> 1) & 1));
+        {
+            const int kk = tid / TPA, r = tid % TPA;
+            if (kk < kn) {
+                const unsigned char *row = raw + (b * STAGE + kk) * RS;
+                const int off = sof[slot][kk];
+                const float w = sw[slot][kk];
+                float4 *dst = tab + (b * STAGE + kk) * W;
+                const int m0 = r * run, m1 = min(W, m0 + run);
+                if (m0 < m1) {
+                    float g0 = smem_f<Tin>(row, off + m0), g1 = smem_f<Tin>(row, off + m0 + 1);
+                    float g2 = smem_f<Tin>(row, off + m0 + 2);
+                    float d0 = w * (g1 - g0), d1 = w * (g2 - g1);
+                    for (int m = m0; m < m1; ++m) {
+                        const float g3 = smem_f<Tin>(row, off + m + 3);
+                        const float d2 = w * (g3 - g2);
+                        dst[m] = make_float4(w * g0, d0, d1, d2);
+                        g0 = g1;
+                        g1 = g2;
+                        g2 = g3;
+                        d0 = d1;
+                        d1 = d2;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if (i + 2 < S) {
+            if (tid < STAGE) fence_proxy_async_smem();
+            prepare(i + 2);
+        }
+        for (int kk = 0; kk < kn; ++kk) {
+            const float4 A = sq[slot][kk];
+            const float4 R2 = sr[slot][kk];
+            const float4 F = sf[slot][kk];
+            const int rl = __float_as_int(F.w);
+            if (rl != role) {
+                // the corner roles follow the signs of (c, s): move each pixel's sum to its new role
+#pragma unroll
+                for (int a = 0; a < 4; ++a) xor_permute(acc[a], rl ^ role);
+                role = rl;
+            }
+            const float qt = fmaf(fy, A.z, fmaf(fx, A.y, A.x));
+            const unsigned long long Q = pk2(qt, fmaf(16.f, A.y, qt));
+            const unsigned long long CC = pk2(A.y, A.y);
+            const unsigned base = __float_as_uint(A.w);
+            // far corner: with |c| + |s| >= 1 its lowest ramp is always 1 (two ramps suffice)
+            const bool far2 = F.y >= 0.f;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const unsigned long long qa = h ? ffma2(pk2(32.f, 32.f), CC, Q) : Q;  // blocks 2h, 2h + 1
+                const unsigned long long Rf = fadd2_rm(qa, MM);                      // magic + floor(q)
+                const unsigned long long RB = fsub2(qa, fsub2(Rf, MM));              // r = q - floor(q)
+                float v0, v1, rb[2];
+                upk2(Rf, v0, v1);
+                upk2(RB, rb[0], rb[1]);
+                float4 T[2];
+                T[0] = lds128(base + (__float_as_uint(v0) << 4));
+                T[1] = lds128(base + (__float_as_uint(v1) << 4));
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    float(&q)[4] = acc[2 * h + e];
+                    const float r = rb[e];
+                    const float4 t = T[e];  // w g_j, w dg_j, w dg_{j+1}, w dg_{j+2}
+                    G[2 * h + e] += t.x;
+                    q[0] = fmaf(t.y, r, q[0]);
+                    q[1] = fmaf(t.z, add_sat(r, R2.y), fmaf(t.y, add_sat(r, R2.x), q[1]));
+                    q[2] = fmaf(t.z, add_sat(r, R2.w), fmaf(t.y, add_sat(r, R2.z), q[2]));
+                    if (far2)
+                        q[3] = fmaf(t.w, add_sat(r, F.z), fmaf(t.z, add_sat(r, F.y), q[3] + t.y));
+                    else
+                        q[3] = fmaf(t.w, add_sat(r, F.z),
+                                    fmaf(t.z, add_sat(r, F.y), fmaf(t.y, add_sat(r, F.x), q[3])));
+                }
+            }
+        }
+    }
+    if (!ok && lane == 0) atomicExch(err, 1);
+
+    // position px + 2 py of a block has role (px + 2 py) ^ role: back to position order
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        xor_permute(acc[a], role);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int x = tx * kTile + 2 * X0 + 16 * a + (r & 1);
+            const int y = ty * kTile + 2 * Y0 + (r >> 1);
+            if (x < N && y < N) {
+                float *dst = img + (long long)y * N + x;
+                const float val = acc[a][r] + G[a];
+                if (asplit > 1) atomicAdd(dst, val);
+                else *dst = accumulate ? (*dst + val) : val;
+            }
+        }
+    }
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     static std::once_flag once;
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -228,6 +447,22 @@ bool tma_eligible(const bp_plan *p, int esz) {
     const int Wb = (p->W + 8 + 7) & ~7;
     return ((long long)p->n_det * esz) % 16 == 0 && Wb <= 256;
 }
+
+// Quad kernel: raw box of W + 3 bins after the up-to-7-bin alignment offset, and its shared
+// memory (raw double buffer + float4 table double buffer).
+int quad_box(const bp_plan *p) { return (p->W + 10 + 7) & ~7; }
+
+size_t quad_smem(const bp_plan *p, int stage, int esz) {
+    const size_t RS = ((size_t)quad_box(p) * esz + 127) & ~(size_t)127;
+    return 2 * (size_t)stage * RS + 2 * sizeof(float4) * (size_t)stage * p->W;
+}
+
+// The quad kernel needs |c|, |s| <= 1 (a 2 x 2 block spans at most g_j .. g_{j+3}).
+bool quad_eligible(const bp_plan *p, int esz, int stage) {
+    return p->step_max <= 1.0f && ((long long)p->n_det * esz) % 16 == 0 && quad_box(p) <= 256 &&
+           quad_smem(p, stage, esz) <= kMaxDirectSmem;
+}
+
 
 // The shape a direct launch really uses: on the TMA path the stage is lowered until its
 // shared memory fits; the synchronous path always stages kStage angles; groups are clamped.
@@ -260,29 +495,58 @@ bp_status launch_tma(bp_plan *p, const CUtensorMap &map, float *img, int batch, 
     return BP_OK;
 }
 
+template <typename Tin, int STAGE>
+bp_status launch_quad(bp_plan *p, const CUtensorMap &map, float *img, int batch, int accumulate, int asplit,
+                      cudaStream_t st, float wuni) {
+    const int tiles = (p->N + kTile - 1) / kTile;
+    const int esz = (int)sizeof(Tin);
+    const int Wb = quad_box(p);
+    const int RS = (Wb * esz + 127) & ~127;
+    const size_t smem = quad_smem(p, STAGE, esz);
+    auto kern = bp_direct_quad_kernel<Tin, STAGE>;
+    BP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    dim3 grid(tiles, tiles * asplit, batch);
+    kern<<<grid, kThreads, smem, st>>>(map, img, p->d_ang, p->N, p->n_theta, p->W, p->C, Wb, RS, accumulate, tiles,
+                                       asplit, (long long)p->N * p->N, p->d_err, wuni);
+    BP_CUDA_TRY(cudaGetLastError());
+    return BP_OK;
+}
+
+template <typename Tin>
+bool encode_rows(const bp_plan *p, const Tin *sino, int batch, int box, CUtensorMap *map) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return false;
+    const int esz = (int)sizeof(Tin);
+    const cuuint64_t dims[3] = {(cuuint64_t)p->n_det, (cuuint64_t)p->n_theta, (cuuint64_t)batch};
+    const cuuint64_t strides[2] = {(cuuint64_t)p->n_det * esz, (cuuint64_t)p->n_det * p->n_theta * esz};
+    const cuuint32_t boxd[3] = {(cuuint32_t)box, 1, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return enc(map, tmap_type<Tin>(), 3, const_cast<Tin *>(sino), dims, strides, boxd, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 template <typename Tin>
 bp_status launch_direct_t(bp_plan *p, const Tin *sino, float *img, int batch, int accumulate, cudaStream_t st,
                           float wuni, DirectShape shape) {
     const int tiles = (p->N + kTile - 1) / kTile;
     const int esz = (int)sizeof(Tin);
-    const int Wb = (p->W + 8 + 7) & ~7;
-    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
-    bool tma = enc && tma_eligible(p, esz);
-    CUtensorMap map;
-    if (tma) {
-        const cuuint64_t dims[3] = {(cuuint64_t)p->n_det, (cuuint64_t)p->n_theta, (cuuint64_t)batch};
-        const cuuint64_t strides[2] = {(cuuint64_t)p->n_det * esz, (cuuint64_t)p->n_det * p->n_theta * esz};
-        const cuuint32_t box[3] = {(cuuint32_t)Wb, 1, 1};
-        const cuuint32_t estr[3] = {1, 1, 1};
-        tma = enc(&map, tmap_type<Tin>(), 3, const_cast<Tin *>(sino), dims, strides, box, estr,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-    }
-    const DirectShape eff = direct_effective(p, esz, tma, shape);
-    if (tma && tma_smem(p, eff.stage, esz) > kMaxDirectSmem) tma = false;
+    const bool have_enc = tensor_map_encoder() != nullptr;
+    const DirectShape eff = direct_effective(p, esz, have_enc && tma_eligible(p, esz), shape);
     const int stage = eff.stage, asplit = eff.asplit;
+    CUtensorMap map;
+    const bool quad = have_enc && quad_eligible(p, esz, stage) && encode_rows(p, sino, batch, quad_box(p), &map);
+    const bool tma = !quad && have_enc && tma_eligible(p, esz) && tma_smem(p, stage, esz) <= kMaxDirectSmem &&
+                     encode_rows(p, sino, batch, (p->W + 8 + 7) & ~7, &map);
     if (asplit > 1 && !accumulate)
         BP_CUDA_TRY(cudaMemsetAsync(img, 0, sizeof(float) * (size_t)p->N * p->N * batch, st));
+    if (quad) {
+        switch (stage) {
+            case 8: return launch_quad<Tin, 8>(p, map, img, batch, accumulate, asplit, st, wuni);
+            case 32: return launch_quad<Tin, 32>(p, map, img, batch, accumulate, asplit, st, wuni);
+            default: return launch_quad<Tin, 16>(p, map, img, batch, accumulate, asplit, st, wuni);
+        }
+    }
     if (tma) {
         switch (stage) {
             case 8: return launch_tma<Tin, 8>(p, map, img, batch, accumulate, asplit, st, wuni);

@@ -29,4 +29,12 @@ __device__ __forceinline__ unsigned long long fsub2(unsigned long long a, unsign
     return d;
 }
 
+// Paired add rounded toward minus infinity: with the magic constant 1.5 * 2^23 as b, the
+// result's low mantissa bits hold floor(a) exactly (|a| < 2^22).
+__device__ __forceinline__ unsigned long long fadd2_rm(unsigned long long a, unsigned long long b) {
+    unsigned long long d;
+    asm("add.rm.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
 }  // namespace bp

@@ -156,6 +156,7 @@ extern "C" bp_plan *bp_plan_create(int N, int n_det, int n_theta, const double *
         ap[k].w = (float)p->w[k];
         ap[k].pad = 0.f;
         ext = std::max(ext, std::fabs((double)ap[k].c) + std::fabs((double)ap[k].s));
+        p->step_max = std::max(p->step_max, std::max(std::fabs(ap[k].c), std::fabs(ap[k].s)));
     }
     // Window: all bins touched by a kTile x kTile tile plus a rounding margin on each side.
     int W = (int)std::ceil((kTile - 1) * ext) + 4;
