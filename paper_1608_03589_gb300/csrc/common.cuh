@@ -118,6 +118,7 @@ struct bp_plan {
     // filter
     int P = 0;                 // FFT length for the filter (power of two >= 2 n_det)
     float2 *d_twP = nullptr;   // P/2 twiddles exp(-2 pi i r / P)
+    float2 *d_twpass = nullptr;  // per-pass twiddles of the persistent filter kernel (512 <= P <= 4096)
     float *d_H[3] = {nullptr, nullptr, nullptr};   // bit-reversed scaled responses per kind
     float H_param[3] = {0.f, 0.f, 0.f};
     // Fourier path
@@ -188,6 +189,8 @@ bp_status launch_batched(bp_plan *const *plans, const void *const *sinos, const 
 
 // host FP64 FFT (plan tables only): in-place radix-2, sign -1 forward
 void host_fft(std::vector<double> &re, std::vector<double> &im, bool inverse);
+void build_pass_twiddles(int logP, std::vector<float2> &T);
+bool filter_pt_supported(int P);
 
 // element loads, widened to float
 template <typename T> __device__ __forceinline__ float load_f(const T *p);

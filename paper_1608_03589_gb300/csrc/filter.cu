@@ -55,6 +55,203 @@ filter_kernel(const Tin *__restrict__ in, float *__restrict__ out, const float *
     }
 }
 
+// ------------------------------------------------------------------ per-pass-twiddle kernel
+// Transform lengths P = 2^9 .. 2^12 (n_det <= 2048) take a persistent kernel instead: each CTA
+// stages H and a per-pass twiddle table in shared memory once and then walks row pairs.  The
+// passes are the Stockham radix-8 passes of fft.cuh (a radix-4 or radix-2 pass last when
+// log2 P is not a multiple of 3) with P / 8 threads, but
+//  * pass twiddles come from a table laid out per pass as T[(r - 1) L + k] = W_{LR}^{rk}, so
+//    the lanes of a warp (consecutive k) read consecutive entries, free of bank conflicts;
+//  * the first forward pass reads the two rows straight from global memory (the upper half
+//    of the zero-padded row is known to be zero) and the next pair's loads are in flight
+//    while the current pair is transformed;
+//  * the outputs of the last forward pass that a thread holds are exactly the inputs of its
+//    first inverse pass, so H is applied and that pass computed in registers;
+//  * the last inverse pass writes the first n_det outputs straight to global memory.
+constexpr int kPassE = 8;  // elements per thread
+
+template <int R>
+__device__ __forceinline__ void pt_twiddle_dft(float2 (&a)[R], const float2 *__restrict__ T, int L, int k,
+                                               bool inverse) {
+    if (L > 1) {
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+            float2 w = T[(r - 1) * L + k];
+            if (inverse) w.y = -w.y;
+            a[r] = cmul(a[r], w);
+        }
+    }
+    dft_reg<R>(a, inverse);
+}
+
+// One middle pass, shared memory to shared memory (swizzled layout both ways).
+template <int R, int LOGP>
+__device__ __forceinline__ void pt_pass(float2 *z, const float2 *T, int L, int t, bool inverse) {
+    constexpr int P = 1 << LOGP, NT = P / kPassE, G = kPassE / R, m = P / R;
+    float2 a[G][R];
+#pragma unroll
+    for (int g = 0; g < G; ++g)
+#pragma unroll
+        for (int r = 0; r < R; ++r) a[g][r] = z[fft_swz<kPassE>(t + g * NT + r * m)];
+    __syncthreads();
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        const int tg = t + g * NT, k = tg & (L - 1), j = tg / L;
+        pt_twiddle_dft<R>(a[g], T, L, k, inverse);
+#pragma unroll
+        for (int q = 0; q < R; ++q) z[fft_swz<kPassE>(j * L * R + k + q * L)] = a[g][q];
+    }
+    __syncthreads();
+}
+
+// Pass structure of a length-2^LOGP transform: radix-8 passes, then one of radix 2^(LOGP % 3).
+template <int LOGP> struct PtPlan {
+    static constexpr int n8 = LOGP / 3;
+    static constexpr int rb = LOGP % 3;
+    static constexpr int Rl = rb == 0 ? 8 : (1 << rb);           // radix of the last pass
+    static constexpr int npass = n8 + (rb ? 1 : 0);
+};
+
+// Offset of pass p's twiddles in the table (passes with L = 1 have none).
+template <int LOGP>
+__host__ __device__ constexpr int pt_offset(int p) {
+    int off = 0, L = 1;
+    for (int i = 0; i < p; ++i) {
+        const int R = (i < PtPlan<LOGP>::n8) ? 8 : PtPlan<LOGP>::Rl;
+        if (L > 1) off += (R - 1) * L;
+        L *= R;
+    }
+    return off;
+}
+
+template <typename Tin, int LOGP>
+__global__ void __launch_bounds__((1 << LOGP) / kPassE, 1024 / ((1 << LOGP) / kPassE))
+filter_pt_kernel(const Tin *__restrict__ in, float *__restrict__ out, const float *__restrict__ H,
+                 const float2 *__restrict__ twp, long long rows, int n_det) {
+    using PL = PtPlan<LOGP>;
+    constexpr int P = 1 << LOGP, NT = P / kPassE, Rl = PL::Rl, Gl = kPassE / Rl;
+    constexpr int TWN = pt_offset<LOGP>(PL::npass);
+    static_assert(TWN % 2 == 0, "per-pass twiddle count");
+    extern __shared__ __align__(16) float2 pz[];
+    float2 *z = pz;                                           // [P] work array
+    float2 *T = z + P;                                        // [TWN] per-pass twiddles
+    float *Hs = reinterpret_cast<float *>(T + ((TWN + 1) & ~1));  // [P] response
+    const int t = threadIdx.x;
+    const long long npairs = (rows + 1) / 2;
+    // inputs of the first forward pass: x[t + r NT], r < 4 (r >= 4 lies in the zero padding)
+    float2 nxt[4];
+    auto fetch = [&](long long pair) {
+        const long long r0 = 2 * pair;
+        const bool has1 = r0 + 1 < rows;
+        const Tin *a = in + r0 * n_det, *b = a + n_det;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int i = t + r * NT;
+            float va = 0.f, vb = 0.f;
+            if (i < n_det) {
+                va = load_f(a + i);
+                if (has1) vb = load_f(b + i);
+            }
+            nxt[r] = make_float2(va, vb);
+        }
+    };
+    long long pair = blockIdx.x;
+    if (pair < npairs) fetch(pair);
+    // stage the twiddles and H (16-byte loads, all in flight together; T and Hs start
+    // 16-byte aligned, TWN is even and P a multiple of 4)
+    {
+        constexpr int n4t = TWN / 2, n4h = P / 4;
+        const float4 *ts = reinterpret_cast<const float4 *>(twp);
+        const float4 *hs = reinterpret_cast<const float4 *>(H);
+        float4 *td = reinterpret_cast<float4 *>(T);
+        float4 *hd = reinterpret_cast<float4 *>(Hs);
+#pragma unroll
+        for (int i = 0; i < (n4t + NT - 1) / NT; ++i)
+            if (t + i * NT < n4t) td[t + i * NT] = __ldg(ts + t + i * NT);
+#pragma unroll
+        for (int i = 0; i < (n4h + NT - 1) / NT; ++i)
+            if (t + i * NT < n4h) hd[t + i * NT] = __ldg(hs + t + i * NT);
+    }
+    for (; pair < npairs; pair += gridDim.x) {
+        float2 a[8];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) a[r] = nxt[r];
+#pragma unroll
+        for (int r = 4; r < 8; ++r) a[r] = make_float2(0.f, 0.f);
+        if (pair + gridDim.x < npairs) fetch(pair + gridDim.x);
+        __syncthreads();  // previous pair's last reads of z (and the staged tables) are done
+        // forward pass 0 (L = 1, radix 8) from registers
+        dft_reg<8>(a, false);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) z[fft_swz<kPassE>(t * 8 + q)] = a[q];
+        __syncthreads();
+        int L = 8;
+#pragma unroll
+        for (int p = 1; p < PL::n8; ++p) {
+            if (p == PL::npass - 1) break;
+            pt_pass<8, LOGP>(z, T + pt_offset<LOGP>(p), L, t, false);
+            L *= 8;
+        }
+        // last forward pass into registers, times H, first inverse pass (L = 1, radix 8)
+        float2 b[8];
+        {
+            constexpr int lp = PL::npass - 1, m = P / Rl;
+            float2 c[Gl][Rl];
+#pragma unroll
+            for (int g = 0; g < Gl; ++g)
+#pragma unroll
+                for (int r = 0; r < Rl; ++r) c[g][r] = z[fft_swz<kPassE>(t + g * NT + r * m)];
+#pragma unroll
+            for (int g = 0; g < Gl; ++g) {
+                // here L * Rl = P: k = t + g NT, j = 0, outputs at k + q L = t + (g + q Gl) NT
+                pt_twiddle_dft<Rl>(c[g], T + pt_offset<LOGP>(lp), L, t + g * NT, false);
+#pragma unroll
+                for (int q = 0; q < Rl; ++q) {
+                    const int r = g + q * Gl;
+                    const float h = Hs[t + r * NT];
+                    b[r] = make_float2(c[g][q].x * h, c[g][q].y * h);
+                }
+            }
+        }
+        dft_reg<8>(b, true);
+        __syncthreads();  // all reads of the last forward pass done before z is overwritten
+#pragma unroll
+        for (int q = 0; q < 8; ++q) z[fft_swz<kPassE>(t * 8 + q)] = b[q];
+        __syncthreads();
+        L = 8;
+#pragma unroll
+        for (int p = 1; p < PL::n8; ++p) {
+            if (p == PL::npass - 1) break;
+            pt_pass<8, LOGP>(z, T + pt_offset<LOGP>(p), L, t, true);
+            L *= 8;
+        }
+        // last inverse pass: outputs t + (g + q Gl) NT straight to global memory
+        {
+            constexpr int lp = PL::npass - 1, m = P / Rl;
+            float2 c[Gl][Rl];
+#pragma unroll
+            for (int g = 0; g < Gl; ++g)
+#pragma unroll
+                for (int r = 0; r < Rl; ++r) c[g][r] = z[fft_swz<kPassE>(t + g * NT + r * m)];
+            const long long r0 = 2 * pair;
+            const bool has1 = r0 + 1 < rows;
+            float *oa = out + r0 * n_det, *ob = oa + n_det;
+#pragma unroll
+            for (int g = 0; g < Gl; ++g) {
+                pt_twiddle_dft<Rl>(c[g], T + pt_offset<LOGP>(lp), L, t + g * NT, true);
+#pragma unroll
+                for (int q = 0; q < Rl; ++q) {
+                    const int i = t + (g + q * Gl) * NT;
+                    if (i < n_det) {
+                        oa[i] = c[g][q].x;
+                        if (has1) ob[i] = c[g][q].y;
+                    }
+                }
+            }
+        }
+    }
+}
+
 // Spatial taps h(n), |n| < n_det, of the three filters (host, FP64).
 void filter_taps(int kind, double dt, double lam, int n_det, std::vector<double> &h /* index n + n_det - 1 */) {
     h.assign(2 * n_det - 1, 0.0);
@@ -94,6 +291,26 @@ void filter_taps(int kind, double dt, double lam, int n_det, std::vector<double>
 
 }  // namespace
 
+// Per-pass twiddle table of filter_pt_kernel for P = 2^logP (FP64 -> float):
+// for each pass with L > 1, T[(r - 1) L + k] = exp(-2 pi i r k / (L R)).
+void build_pass_twiddles(int logP, std::vector<float2> &T) {
+    T.clear();
+    int L = 1, rem = logP;
+    while (rem > 0) {
+        const int R = rem >= 3 ? 8 : (1 << rem);
+        rem -= rem >= 3 ? 3 : rem;
+        if (L > 1)
+            for (int r = 1; r < R; ++r)
+                for (int k = 0; k < L; ++k) {
+                    const double a = -2.0 * M_PI * (double)r * (double)k / ((double)L * R);
+                    T.push_back(make_float2((float)std::cos(a), (float)std::sin(a)));
+                }
+        L *= R;
+    }
+}
+
+bool filter_pt_supported(int P) { return P >= 512 && P <= 4096; }
+
 bp_status ensure_filter(bp_plan *p, int kind, float param) {
     if (p->d_H[kind] && (kind != BP_TIKHONOV || p->H_param[kind] == param)) return BP_OK;
     const int P = p->P, n = p->n_det, logP = ilog2(P);
@@ -113,6 +330,47 @@ bp_status ensure_filter(bp_plan *p, int kind, float param) {
     return BP_OK;
 }
 
+namespace {
+
+template <typename Tin, int LOGP>
+bp_status launch_pt(bp_plan *p, const Tin *in, float *out, const float *H, long long rows, cudaStream_t st) {
+    constexpr int P = 1 << LOGP, NT = P / kPassE;
+    constexpr int TWN = pt_offset<LOGP>(PtPlan<LOGP>::npass);
+    const size_t smem = sizeof(float2) * (P + ((TWN + 1) & ~1)) + sizeof(float) * P;
+    auto kern = filter_pt_kernel<Tin, LOGP>;
+    BP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    BP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem));
+    const long long npairs = (rows + 1) / 2;
+    const long long grid = std::max(1LL, std::min(npairs, (long long)std::max(1, per_sm) * std::max(1, p->sm_count)));
+    kern<<<(unsigned)grid, NT, smem, st>>>(in, out, H, p->d_twpass, rows, p->n_det);
+    BP_CUDA_TRY(cudaGetLastError());
+    return BP_OK;
+}
+
+template <typename Tin>
+bp_status launch_pt_t(bp_plan *p, const Tin *in, float *out, const float *H, long long rows, cudaStream_t st) {
+    switch (ilog2(p->P)) {
+        case 9: return launch_pt<Tin, 9>(p, in, out, H, rows, st);
+        case 10: return launch_pt<Tin, 10>(p, in, out, H, rows, st);
+        case 11: return launch_pt<Tin, 11>(p, in, out, H, rows, st);
+        default: return launch_pt<Tin, 12>(p, in, out, H, rows, st);
+    }
+}
+
+bp_status launch_pt_any(bp_plan *p, const void *in, bp_dtype dt, float *out, const float *H, long long rows,
+                        cudaStream_t st) {
+    if (!aligned16(H) || !aligned16(p->d_twpass)) return fail(BP_ERR_INVALID_ARG, "filter response not 16-byte aligned");
+    switch (dt) {
+        case BP_F32: return launch_pt_t(p, (const float *)in, out, H, rows, st);
+        case BP_BF16: return launch_pt_t(p, (const __nv_bfloat16 *)in, out, H, rows, st);
+        case BP_F16: return launch_pt_t(p, (const __half *)in, out, H, rows, st);
+    }
+    return fail(BP_ERR_INVALID_ARG, "invalid dtype");
+}
+
+}  // namespace
+
 bp_status launch_filter(bp_plan *p, const void *in, bp_dtype dt, float *out, int kind, float param, int batch,
                         cudaStream_t st) {
     if ((size_t)(p->P + p->P / 2) * sizeof(float2) > 200u * 1024u)
@@ -120,6 +378,7 @@ bp_status launch_filter(bp_plan *p, const void *in, bp_dtype dt, float *out, int
     bp_status s = ensure_filter(p, kind, param);
     if (s != BP_OK) return s;
     const long long rows = (long long)batch * p->n_theta;
+    if (p->d_twpass) return launch_pt_any(p, in, dt, out, p->d_H[kind], rows, st);
     const int logP = ilog2(p->P);
     const int threads = fft_threads(p->P);
     const size_t smem = sizeof(float2) * (p->P + p->P / 2);
@@ -154,6 +413,7 @@ bp_status launch_filter_response(bp_plan *p, const void *in, bp_dtype dt, float 
     if ((size_t)(p->P + p->P / 2) * sizeof(float2) > 200u * 1024u)
         return fail(BP_ERR_UNSUPPORTED, "filter: n_det too large for the shared-memory FFT (n_det <= 8192)");
     const long long rows = (long long)batch * p->n_theta;
+    if (p->d_twpass) return launch_pt_any(p, in, dt, out, H, rows, st);
     const int logP = ilog2(p->P);
     const int threads = fft_threads(p->P);
     const size_t smem = sizeof(float2) * (p->P + p->P / 2);

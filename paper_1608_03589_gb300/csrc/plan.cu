@@ -109,6 +109,7 @@ extern "C" const char *bp_version(void) { return "bp 0.1 sm_103a"; }
 static void plan_free_device(bp_plan *p) {
     cudaFree(p->d_ang);
     cudaFree(p->d_twP);
+    cudaFree(p->d_twpass);
     for (auto &h : p->d_H) cudaFree(h);
     free_fourier(p);
     free_bst(p);
@@ -189,6 +190,12 @@ extern "C" bp_plan *bp_plan_create(int N, int n_det, int n_theta, const double *
         }
         e = cudaMalloc(&p->d_twP, sizeof(float2) * tw.size());
         if (e == cudaSuccess) e = cudaMemcpy(p->d_twP, tw.data(), sizeof(float2) * tw.size(), cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess && filter_pt_supported(p->P)) {
+        std::vector<float2> tp;
+        build_pass_twiddles(ilog2(p->P), tp);
+        e = cudaMalloc(&p->d_twpass, sizeof(float2) * tp.size());
+        if (e == cudaSuccess) e = cudaMemcpy(p->d_twpass, tp.data(), sizeof(float2) * tp.size(), cudaMemcpyHostToDevice);
     }
     if (e != cudaSuccess) {
         cuda_fail(e, "bp_plan_create device tables");
