@@ -285,6 +285,14 @@ def other_paths(plan, q, img, flush, stream, dev, only=()):
         return res
     guard("bst_interpolation_2048", bst)
 
+    def bst_windowed():
+        res = {}
+        for os in (1, 4):
+            ms = _timed(lambda: plan.backproject_bst_windowed(q, 6.0, os, out=img), stream, flush, 10)
+            res[f"oversampling_{os}"] = {"ms": ms, "equiv_Gupdates_s": wl.updates / ms / 1e6, "beta": 6.0}
+        return res
+    guard("bst_windowed_2048", bst_windowed)
+
     def logpolar():
         ms = _timed(lambda: plan.backproject_logpolar(q, out=img), stream, flush, 5)
         return {"ms": ms, "equiv_Gupdates_s": wl.updates / ms / 1e6}

@@ -147,6 +147,27 @@ bp_status bp_backproject_bst(bp_plan *plan, const void *sino, bp_dtype dtype, fl
                              int batch, void *stream);
 
 /*
+ * bp_backproject_bst_windowed -- the paper's BST algorithm on semi-polar half-lines with the
+ * Kaiser-Bessel window (Section 5.3, Steps 1-4 with Step 2.1; eq "w"): each projection becomes
+ * the half-lines s >= 0 at theta_k and theta_k + pi, sampled at s_i = i dt (i < ns =
+ * floor(n_det/2) + 1) by linear interpolation between detector centres; each half-line is
+ * multiplied by w_i = I0(beta sqrt(1 - ((2i - ns + 1)/(ns - 1))^2)) / I0(beta), which tapers
+ * both ends of the half-line; the ray at theta carries K^sigma times the transform of the line
+ * through its two windowed half-lines (their one-sided transforms, the opposite one
+ * conjugated; the sample at s = 0 counted once); then Steps 3-4 as bp_backproject_bst.
+ * An accuracy variant, not R*: it is R* of the windowed projections g(t, theta) w(|t|)
+ * computed by the BST algorithm; beta = 0 is the identity window (for odd n_det the result
+ * is then bp_backproject_bst's; for even n_det the half-line samples lie between detector
+ * centres, which averages neighbouring bins).
+ *   sino  device [batch][n_theta][n_det] of dtype;  img  device [batch][N][N] float32.
+ *   radial_oversampling  1, 2, 4 or 8 (as bp_backproject_bst);  beta  >= 0 and finite,
+ *   else BP_ERR_INVALID_ARG.  Besides bp_backproject_bst's workspace the first call
+ *   allocates n_theta x (2 ns - 1) floats for the windowed lines.
+ */
+bp_status bp_backproject_bst_windowed(bp_plan *plan, const void *sino, bp_dtype dtype, float *img,
+                                      int radial_oversampling, float beta, int batch, void *stream);
+
+/*
  * bp_backproject_logpolar -- R* by Andersson's log-polar convolution as the paper implements
  * it (Section 5.1 Steps 1-4 with the adaptive rho_0 of Section 5.2; eq "andersson"): the
  * sinogram resampled (linear interpolation) onto a log-polar mesh mu_i = rho_0 + i drho,

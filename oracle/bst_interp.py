@@ -82,15 +82,12 @@ def full_circle_rays(theta) -> tuple[np.ndarray, np.ndarray, np.ndarray]:
     return ang[order], k[order], conj[order]
 
 
-def cartesian_grid(B: np.ndarray, theta, N: int, det_spacing: float, n_det: int, M: int | None = None,
-                   P: int | None = None) -> np.ndarray:
-    """Step 3: bhat on the Cartesian nodes, as an M x M array indexed [l_x mod M][l_y mod M]."""
-    M = grid_size(N) if M is None else int(M)
-    P = _pad(n_det) if P is None else int(P)
+def cartesian_grid_rays(ang: np.ndarray, V: np.ndarray, N: int, det_spacing: float, M: int, P: int) -> np.ndarray:
+    """Step 3 for explicit rays: ang [R] sorted in [0, 2 pi), V [R][P/2] the values on each ray
+    at kappa_m; returns the M x M grid indexed [l_x mod M][l_y mod M]."""
     H = P // 2
     dx = 2.0 / N
     rho = M * dx / (P * det_spacing)  # grid cells per radial sample
-    ang, kk, cj = full_circle_rays(theta)
     R = ang.shape[0]
     out = np.zeros((M, M), dtype=np.complex128)
     l = np.arange(-M // 2, M // 2)
@@ -116,16 +113,24 @@ def cartesian_grid(B: np.ndarray, theta, N: int, det_spacing: float, n_det: int,
 
         def sample(j, m):
             ok = m < H
-            mm = np.where(ok, m, 0)
-            v = B[kk[j], mm]
-            v = np.where(cj[j], np.conj(v), v)
-            return np.where(ok, v, 0.0)
+            return np.where(ok, V[j, np.where(ok, m, 0)], 0.0)
 
         va = (1.0 - tm) * sample(a, m0) + tm * sample(a, m0 + 1)
         vb = (1.0 - tm) * sample(b, m0) + tm * sample(b, m0 + 1)
         out[lx % M, (l % M)] = (1.0 - tphi) * va + tphi * vb
-    out[0, 0] = np.mean(B[:, 0])
+    out[0, 0] = np.mean(V[:, 0])  # the origin node belongs to every ray
     return out
+
+
+def cartesian_grid(B: np.ndarray, theta, N: int, det_spacing: float, n_det: int, M: int | None = None,
+                   P: int | None = None) -> np.ndarray:
+    """Step 3: bhat on the Cartesian nodes, as an M x M array indexed [l_x mod M][l_y mod M]
+    (ray theta_k carries B[k], ray theta_k + pi its complex conjugate)."""
+    M = grid_size(N) if M is None else int(M)
+    P = _pad(n_det) if P is None else int(P)
+    ang, kk, cj = full_circle_rays(theta)
+    V = np.where(cj[:, None], np.conj(B[kk]), B[kk])
+    return cartesian_grid_rays(ang, V, N, det_spacing, M, P)
 
 
 def bst_full_period(g, N: int, theta, det_spacing: float, M: int | None = None, P: int | None = None) -> np.ndarray:

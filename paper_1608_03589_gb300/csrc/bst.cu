@@ -77,6 +77,36 @@ bst_polar_kernel(const Tin *__restrict__ sino, float2 *__restrict__ polar, const
     }
 }
 
+// Steps 1 and 2.1 on semi-polar half-lines with the window of eq "w": the half-lines of
+// projection k sampled at s_i = i dt (linear interpolation between detector centres, zero
+// off the detector) times w_i, joined into one line t = i dt, |i| < ns, whose centre sample
+// is shared by the two half-lines.  By linearity the transform of this line is the sum of the
+// two half-lines' one-sided transforms (conjugated for the opposite one), which is what
+// Step 2.2 needs on each ray, so the full-line kernels below do the rest.
+template <typename Tin>
+__global__ void __launch_bounds__(256)
+bst_window_rows_kernel(const Tin *__restrict__ sino, float *__restrict__ rows, const float *__restrict__ win,
+                       int n_theta, int n_det, int ns) {
+    const int np = 2 * ns - 1;
+    const long long total = (long long)n_theta * np;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(idx / np), i = (int)(idx - (long long)k * np) - (ns - 1);  // t = i dt
+        const Tin *row = sino + (long long)k * n_det;
+        float v;
+        if (n_det & 1) {  // u = i + (n_det - 1) / 2 is a detector centre
+            const int j = i + (n_det - 1) / 2;
+            v = (j >= 0 && j < n_det) ? load_f(row + j) : 0.f;
+        } else {          // u is half-way between centres j0 and j0 + 1
+            const int j0 = i + n_det / 2 - 1;
+            const float a = (j0 >= 0 && j0 < n_det) ? load_f(row + j0) : 0.f;
+            const float b = (j0 + 1 >= 0 && j0 + 1 < n_det) ? load_f(row + j0 + 1) : 0.f;
+            v = 0.5f * (a + b);
+        }
+        rows[idx] = v * __ldg(win + (i < 0 ? -i : i));
+    }
+}
+
 // Index of the last sorted angle <= phi (-1 if none).
 __device__ __forceinline__ int last_at_most(const float *__restrict__ ang, const RayIndex &ri, float phi) {
     if (ri.uniform) return min(ri.n - 1, max(-1, (int)floorf((phi - ri.phi0) / ri.dphi)));
@@ -172,15 +202,16 @@ bst_interp_kernel(const float2 *__restrict__ polar, const float *__restrict__ an
     grid[(long long)lx * M + ly] = v;
 }
 
+// Rows of n_det samples (n_det <= Pb) centred on t = 0.
 template <typename Tin>
-bp_status polar_t(bp_plan *p, const Tin *sino, cudaStream_t st) {
+bp_status polar_t(bp_plan *p, const Tin *sino, int n_det, cudaStream_t st) {
     BstWork &w = p->bst;
     const int logP = ilog2(w.Pb);
     const size_t smem = sizeof(float2) * (w.Pb + w.Pb / 2);
     auto kern = fft_elems(w.Pb) == 16 ? bst_polar_kernel<Tin, 16> : bst_polar_kernel<Tin, 8>;
     BP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const float scale = (float)((double)w.Pb * p->dt * p->dt);
-    kern<<<(p->n_theta + 1) / 2, fft_threads(w.Pb), smem, st>>>(sino, w.polar, w.twPb, p->n_theta, p->n_det, logP,
+    kern<<<(p->n_theta + 1) / 2, fft_threads(w.Pb), smem, st>>>(sino, w.polar, w.twPb, p->n_theta, n_det, logP,
                                                                 scale);
     BP_CUDA_TRY(cudaGetLastError());
     return BP_OK;
@@ -189,7 +220,7 @@ bp_status polar_t(bp_plan *p, const Tin *sino, cudaStream_t st) {
 bp_status ensure_bst(bp_plan *p, int os) {
     BstWork &w = p->bst;
     if (w.polar && w.os == os) return BP_OK;
-    free_bst(p);
+    free_bst(p);  // (also the windowed form's rows: ensure_bst_window makes them again)
     bp_status s = ensure_fourier(p);
     if (s != BP_OK) return s;
     const int n = p->n_theta, Pb = p->P * os, H = Pb / 2;
@@ -270,10 +301,42 @@ bp_status ensure_bst(bp_plan *p, int os) {
     return BP_OK;
 }
 
+// Window of eq "w" on the ns = floor(n_det/2) + 1 half-line samples (FP64) and the joined
+// rows of the windowed semi-polar form.
+bp_status ensure_bst_window(bp_plan *p, float beta) {
+    BstWork &w = p->bst;
+    const int ns = p->n_det / 2 + 1, np = 2 * ns - 1;
+    if (!w.wrows) {
+        cudaError_t e = cudaMalloc(&w.wrows, sizeof(float) * (size_t)p->n_theta * np);
+        if (e == cudaSuccess) e = cudaMalloc(&w.win, sizeof(float) * ns);
+        if (e != cudaSuccess) {
+            cudaFree(w.wrows);
+            cudaFree(w.win);
+            w.wrows = nullptr;
+            w.win = nullptr;
+            return cuda_fail(e, "windowed BST workspace");
+        }
+        w.bytes += sizeof(float) * ((size_t)p->n_theta * np + ns);
+        w.beta = -1.f;
+    }
+    if (w.beta == beta) return BP_OK;
+    std::vector<float> win(ns, 1.0f);
+    const double b = beta, i0b = std::cyl_bessel_i(0.0, b);
+    for (int i = 0; i < ns && ns > 1; ++i) {
+        const double x = (2.0 * i - ns + 1.0) / (ns - 1.0);
+        win[i] = (float)(std::cyl_bessel_i(0.0, b * std::sqrt(std::max(0.0, 1.0 - x * x))) / i0b);
+    }
+    BP_CUDA_TRY(cudaMemcpy(w.win, win.data(), sizeof(float) * ns, cudaMemcpyHostToDevice));
+    w.beta = beta;
+    return BP_OK;
+}
+
 }  // namespace
 
 void free_bst(bp_plan *p) {
     BstWork &w = p->bst;
+    cudaFree(w.wrows);
+    cudaFree(w.win);
     cudaFree(w.polar);
     cudaFree(w.twPb);
     cudaFree(w.ang);
@@ -301,11 +364,56 @@ bp_status launch_bst(bp_plan *p, const void *sino, bp_dtype dt, float *img, int 
     for (int b = 0; b < batch; ++b) {
         const char *sb = (const char *)sino + esz * (size_t)b * p->n_theta * p->n_det;
         switch (dt) {
-            case BP_F32: s = polar_t(p, (const float *)sb, st); break;
-            case BP_BF16: s = polar_t(p, (const __nv_bfloat16 *)sb, st); break;
-            case BP_F16: s = polar_t(p, (const __half *)sb, st); break;
+            case BP_F32: s = polar_t(p, (const float *)sb, p->n_det, st); break;
+            case BP_BF16: s = polar_t(p, (const __nv_bfloat16 *)sb, p->n_det, st); break;
+            case BP_F16: s = polar_t(p, (const __half *)sb, p->n_det, st); break;
         }
         if (s != BP_OK) return s;
+        const dim3 g((M + 31) / 32, (M + 7) / 8);
+        bst_interp_kernel<<<g, 256, 0, st>>>(w.polar, w.ang, w.ray, w.dir, w.igap, w.ri, f.grid, M, H, ih, il, scale,
+                                             delta2, p->n_theta);
+        BP_CUDA_TRY(cudaGetLastError());
+        if ((s = launch_grid_to_image(p, w.ones, img + (size_t)b * N * N, st)) != BP_OK) return s;
+    }
+    return BP_OK;
+}
+
+bp_status launch_bst_windowed(bp_plan *p, const void *sino, bp_dtype dt, float *img, int os, float beta, int batch,
+                              cudaStream_t st) {
+    if ((size_t)p->P * os * sizeof(float2) * 3 / 2 > 200u * 1024u)
+        return fail(BP_ERR_UNSUPPORTED, "BST: n_det x oversampling too large for the shared-memory FFT");
+    bp_status s = ensure_bst(p, os);
+    if (s == BP_OK) s = ensure_fourier(p);
+    if (s == BP_OK) s = ensure_bst_window(p, beta);
+    if (s != BP_OK) return s;
+    BstWork &w = p->bst;
+    FourierWork &f = p->four;
+    const int N = p->N, M = f.M, H = w.Pb / 2;
+    const int ns = p->n_det / 2 + 1, np = 2 * ns - 1;  // np <= n_det + 1 <= P
+    const size_t esz = dt == BP_F32 ? 4 : 2;
+    const double inv_rho = (double)w.Pb * p->dt / ((double)M * p->dx);
+    const float ih = (float)inv_rho, il = (float)(inv_rho - (double)ih);
+    const float scale = (float)(1.0 / (((double)M * p->dx) * ((double)M * p->dx)));
+    const float delta2 = (N % 2 == 0) ? 1.0f / (float)M : 0.0f;
+    const long long total = (long long)p->n_theta * np;
+    const unsigned blocks = (unsigned)std::min<long long>((total + 255) / 256, 8LL * std::max(1, p->sm_count));
+    for (int b = 0; b < batch; ++b) {
+        const char *sb = (const char *)sino + esz * (size_t)b * p->n_theta * p->n_det;
+        switch (dt) {
+            case BP_F32:
+                bst_window_rows_kernel<<<blocks, 256, 0, st>>>((const float *)sb, w.wrows, w.win, p->n_theta, p->n_det, ns);
+                break;
+            case BP_BF16:
+                bst_window_rows_kernel<<<blocks, 256, 0, st>>>((const __nv_bfloat16 *)sb, w.wrows, w.win, p->n_theta,
+                                                               p->n_det, ns);
+                break;
+            case BP_F16:
+                bst_window_rows_kernel<<<blocks, 256, 0, st>>>((const __half *)sb, w.wrows, w.win, p->n_theta, p->n_det,
+                                                               ns);
+                break;
+        }
+        BP_CUDA_TRY(cudaGetLastError());
+        if ((s = polar_t(p, (const float *)w.wrows, np, st)) != BP_OK) return s;
         const dim3 g((M + 31) / 32, (M + 7) / 8);
         bst_interp_kernel<<<g, 256, 0, st>>>(w.polar, w.ang, w.ray, w.dir, w.igap, w.ri, f.grid, M, H, ih, il, scale,
                                              delta2, p->n_theta);

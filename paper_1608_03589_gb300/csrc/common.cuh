@@ -67,6 +67,9 @@ struct BstWork {
     float4 *dir = nullptr;      // [2 n_theta] ray directions (cos, sin) as high and low floats
     float *igap = nullptr;      // [2 n_theta] 1 / angular gap to the next ray
     RayIndex ri;                // lookup into ang (n = 2 n_theta)
+    float *wrows = nullptr;     // [n_theta][2 ns - 1] windowed semi-polar lines (ns = n_det/2 + 1)
+    float *win = nullptr;       // [ns] window of eq "w"
+    float beta = -1.f;          // its beta (-1: not computed)
     size_t bytes = 0;
 };
 
@@ -184,6 +187,8 @@ void free_logpolar(bp_plan *p);
 bp_status launch_logpolar(bp_plan *p, const void *sino, bp_dtype dt, float *img, int batch, cudaStream_t st);
 bp_status launch_grid_to_image(bp_plan *p, const float *deap, float *img, cudaStream_t st);
 bp_status launch_bst(bp_plan *p, const void *sino, bp_dtype dt, float *img, int os, int batch, cudaStream_t st);
+bp_status launch_bst_windowed(bp_plan *p, const void *sino, bp_dtype dt, float *img, int os, float beta, int batch,
+                              cudaStream_t st);
 bp_status launch_batched(bp_plan *const *plans, const void *const *sinos, const bp_dtype *dtypes,
                          float *const *imgs, int n, cudaStream_t st);
 

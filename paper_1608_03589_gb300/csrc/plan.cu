@@ -286,6 +286,19 @@ extern "C" bp_status bp_backproject_bst(bp_plan *p, const void *sino, bp_dtype d
     return launch_bst(p, sino, dtype, img, os, batch, (cudaStream_t)stream);
 }
 
+extern "C" bp_status bp_backproject_bst_windowed(bp_plan *p, const void *sino, bp_dtype dtype, float *img,
+                                                 int radial_oversampling, float beta, int batch, void *stream) {
+    set_error("");
+    bp_status st = check_common(p, sino, img, batch);
+    if (st != BP_OK) return st;
+    if (!valid_dtype(dtype)) return fail(BP_ERR_INVALID_ARG, "invalid dtype");
+    const int os = radial_oversampling;
+    if (os != 1 && os != 2 && os != 4 && os != 8)
+        return fail(BP_ERR_INVALID_ARG, "radial_oversampling must be 1, 2, 4 or 8");
+    if (!(beta >= 0.f) || !std::isfinite(beta)) return fail(BP_ERR_INVALID_ARG, "beta must be finite and >= 0");
+    return launch_bst_windowed(p, sino, dtype, img, os, beta, batch, (cudaStream_t)stream);
+}
+
 extern "C" bp_status bp_backproject_logpolar(bp_plan *p, const void *sino, bp_dtype dtype, float *img, int batch,
                                              void *stream) {
     set_error("");
