@@ -298,6 +298,12 @@ def other_paths(plan, q, img, flush, stream, dev, only=()):
         return {"ms": ms, "equiv_Gupdates_s": wl.updates / ms / 1e6}
     guard("logpolar_2048", logpolar)
 
+    def logpolar_partial():
+        plan.backproject_logpolar_partial(q, 8, 0.25, out=img)  # workspace and pixel tables (untimed)
+        ms = _timed(lambda: plan.backproject_logpolar_partial(q, 8, 0.25, out=img), stream, flush, 5)
+        return {"ms": ms, "equiv_Gupdates_s": wl.updates / ms / 1e6, "sectors": 8, "a_r": 0.25}
+    guard("logpolar_partial_2048", logpolar_partial)
+
     def radon():
         shape, _ = plan.autotune("radon", batch=1)
         ms = _timed(lambda: plan.radon(img, out=q), stream, flush, 5)

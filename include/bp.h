@@ -189,6 +189,29 @@ bp_status bp_backproject_logpolar(bp_plan *plan, const void *sino, bp_dtype dtyp
                                   void *stream);
 
 /*
+ * bp_backproject_logpolar_partial -- R* by partial (sector) log-polar backprojections
+ * (Section 5.2, "Partial Backprojections"; shifting property eq "sh_prop"; per sector the
+ * convolution of bp_backproject_logpolar, Section 5.1 Steps 1-4).  The half-line angles
+ * phi in [0, pi) (every line once) are split into `sectors` sectors of the mesh phi_j = j pi /
+ * n_half (n_half = 2^ceil(log2 n_theta)); sector q moves the origin to -d xi_{phi_c}
+ * (phi_c its centre, d = sqrt(2) (1 - a_r) / a_r: the object rescaled to a_r and shifted by
+ * 1 - a_r), where every line of the sector lies at s > 0, so its log-polar mesh starts at a
+ * finite rho_0 and no line is lost; the shifted sinogram g(s - d cos(phi - phi_c), phi) is
+ * resampled (linear), convolved with the point-mass kernel by zero-padded 2D FFTs (linear in
+ * rho and angle) and interpolated bilinearly at the pixels; the sectors add up.
+ * An approximation of R* (first order in the meshes), free of the origin problem of
+ * bp_backproject_logpolar.
+ *   sino  device [batch][n_theta][n_det] of dtype;  img  device [batch][N][N] float32.
+ *   sectors  a power of two dividing n_half, with the sector narrow enough for the shift
+ *   (asin(1/((1 - a_r)/a_r)) + half the sector width + 3 dphi < pi/2), else BP_ERR_INVALID_ARG;
+ *   a_r in (0, 1/2).  Transforms of at most 16384 points, else BP_ERR_UNSUPPORTED.  The
+ *   first call (or one with other sectors / a_r) builds the plan's workspace: per-sector FP64
+ *   pixel tables (16 bytes per pixel and sector) and two complex work arrays.
+ */
+bp_status bp_backproject_logpolar_partial(bp_plan *plan, const void *sino, bp_dtype dtype, float *img, int sectors,
+                                          float a_r, int batch, void *stream);
+
+/*
  * bp_set_fourier_width -- Kaiser-Bessel kernel width W (grid cells) of the gridding in
  * bp_backproject_fourier, bp_fbp_fourier and the Fourier-path R (Section 5.3 Step 3): 6 (the
  * default) or 4.  The gridding error falls roughly as exp(-pi W sqrt(1 - 1/sigma)) with the

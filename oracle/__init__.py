@@ -12,7 +12,8 @@ Each wrapped function cites the passage of arXiv:1608.03589 it follows in oracle
 paper's own BST algorithm (polar-to-Cartesian interpolation in frequency) is plain numpy in
 ``bst_interp.py`` (``bp_bst_interp`` below), the same algorithm on windowed semi-polar
 half-lines in ``bst_semipolar.py`` (``bp_bst_semipolar``), Andersson's log-polar
-backprojection in ``logpolar.py`` (``bp_logpolar``).
+backprojection in ``logpolar.py`` (``bp_logpolar``) and its partial (sector) form in
+``logpolar_partial.py`` (``bp_logpolar_partial``).
 """
 from __future__ import annotations
 
@@ -227,3 +228,4 @@ def rel_l2(a, b) -> float:
 from .bst_interp import bp_bst_interp, bst_full_period  # noqa: E402  (numpy oracle of Section 5.3)
 from .logpolar import bp_logpolar  # noqa: E402  (numpy oracle of Sections 5.1-5.2)
 from .bst_semipolar import bp_bst_semipolar  # noqa: E402  (numpy oracle of Section 5.3 with eq "w")
+from .logpolar_partial import bp_logpolar_partial  # noqa: E402  (numpy oracle of Section 5.2, sectors)

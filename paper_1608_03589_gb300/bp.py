@@ -26,7 +26,7 @@ _DTYPES = {torch.float32: BP_F32, torch.bfloat16: BP_BF16, torch.float16: BP_F16
 # Every symbol the header declares (checked by the ABI test).
 SYMBOLS = ("bp_plan_create", "bp_destroy", "bp_filter", "bp_backproject_direct", "bp_backproject_fourier",
            "bp_radon", "bp_fbp_host", "bp_fbp_fourier", "bp_backproject_bst", "bp_backproject_bst_windowed",
-           "bp_backproject_logpolar", "bp_set_fourier_width", "bp_backproject_batched", "bp_fbp_static", "bp_check", "bp_radon_transpose",
+           "bp_backproject_logpolar", "bp_backproject_logpolar_partial", "bp_set_fourier_width", "bp_backproject_batched", "bp_fbp_static", "bp_check", "bp_radon_transpose",
            "bp_backproject_transpose", "bp_autotune", "bp_get_shape", "bp_set_shape", "bp_tune_cache_save",
            "bp_tune_cache_load", "bp_last_error", "bp_version")
 OPS = {"direct": 0, "radon": 1}
@@ -63,6 +63,7 @@ def lib() -> ctypes.CDLL:
             L.bp_backproject_bst.argtypes = [vp, vp, i, vp, i, i, vp]
             L.bp_backproject_bst_windowed.argtypes = [vp, vp, i, vp, i, f, i, vp]
             L.bp_backproject_logpolar.argtypes = [vp, vp, i, vp, i, vp]
+            L.bp_backproject_logpolar_partial.argtypes = [vp, vp, i, vp, i, f, i, vp]
             L.bp_set_fourier_width.argtypes = [vp, i]
             L.bp_check.argtypes = [vp, vp]
             L.bp_radon_transpose.argtypes = [vp, vp, vp, i, i, vp]
@@ -77,7 +78,7 @@ def lib() -> ctypes.CDLL:
             L.bp_tune_cache_load.argtypes = [ctypes.c_char_p]
             for name in ("bp_filter", "bp_backproject_direct", "bp_backproject_fourier", "bp_radon",
                          "bp_fbp_host", "bp_fbp_fourier", "bp_backproject_bst", "bp_backproject_bst_windowed",
-                         "bp_backproject_logpolar",
+                         "bp_backproject_logpolar", "bp_backproject_logpolar_partial",
                          "bp_set_fourier_width",
                          "bp_backproject_batched", "bp_fbp_static",
                          "bp_check",
@@ -229,6 +230,25 @@ class Plan:
             _check(lib().bp_backproject_bst_windowed(self.handle, sino.data_ptr(), _DTYPES[sino.dtype],
                                                      out.data_ptr(), int(oversampling), float(beta), b,
                                                      _stream(sino)), "bp_backproject_bst_windowed")
+        return out
+
+    def backproject_logpolar_partial(self, sino: torch.Tensor, sectors: int = 8, a_r: float = 0.25,
+                                     out: torch.Tensor | None = None) -> torch.Tensor:
+        """R* by partial (sector) log-polar backprojections with a shifted origin (Section 5.2,
+        eq "sh_prop"; bp_backproject_logpolar_partial)."""
+        _cuda(sino, "sino")
+        b = self._batch(sino, (self.n_theta, self.n_det), "sino")
+        if sino.dtype not in _DTYPES:
+            raise BPError(f"unsupported sinogram dtype {sino.dtype}")
+        if out is None:
+            out = torch.empty((*sino.shape[:-2], self.N, self.N), dtype=torch.float32, device=sino.device)
+        _cuda(out, "out")
+        if out.dtype != torch.float32 or out.numel() != b * self.N * self.N:
+            raise BPError("out must be float32 with batch x N x N elements")
+        with torch.cuda.device(self.device):
+            _check(lib().bp_backproject_logpolar_partial(self.handle, sino.data_ptr(), _DTYPES[sino.dtype],
+                                                         out.data_ptr(), int(sectors), float(a_r), b,
+                                                         _stream(sino)), "bp_backproject_logpolar_partial")
         return out
 
     def backproject_logpolar(self, sino: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:

@@ -88,6 +88,24 @@ struct LogPolarWork {
     size_t bytes = 0;
 };
 
+// Workspace of the partial (sector) log-polar backprojection (logpolar_partial.cu).
+struct LppWork {
+    int Q = 0;                 // sectors over [0, pi)
+    float a_r = 0.f;           // rescaling ratio of the shift
+    int K = 0, n_half = 0;     // angle nodes per sector, over [0, pi)
+    int n_rho = 0, c_lo = 0, n_out = 0, a_lo = 0, n_aout = 0, Lr = 0, Lp = 0;  // meshes
+    int2 *stab = nullptr;      // [n_rho] s_i / dt as (integer, fraction bits)
+    int4 *rowtab = nullptr;    // [K] -D_j + c0 and D_j + c0 split (D_j = d cos(phi_j - phi_c) / dt)
+    int4 *atab = nullptr;      // [n_half] bracketing projections, flip bits, weight
+    float2 *kfrac = nullptr;   // [Lp] kernel node and fraction per angular-transform row
+    float2 *twLr = nullptr, *twLp = nullptr;
+    float2 *T = nullptr;       // [Lp][Lr] complex work array
+    float2 *Khat = nullptr;    // [Lp][Lr] kernel transform (scaled)
+    float *B = nullptr;        // [n_aout + 1][n_out] one sector's output mesh
+    int4 *pix = nullptr;       // [Q][N*N] per-sector pixel -> (rho node, fraction, angle node, fraction)
+    size_t bytes = 0;
+};
+
 // Launch shapes.  The direct R* takes `stage` angles per shared-memory stage (8, 16 or 32)
 // and splits the angles into `asplit` groups, each a separate CTA per tile that adds its
 // partial sum into the image; the direct R takes `kang` angles per CTA (1, 2 or 4) and
@@ -129,6 +147,7 @@ struct bp_plan {
     bp::FourierWork four;
     bp::BstWork bst;
     bp::LogPolarWork lp;
+    bp::LppWork lpp;
     // host-buffer entry point staging
     float *d_stage = nullptr;
     size_t stage_batch = 0;
@@ -184,6 +203,9 @@ bp_status ensure_fourier(bp_plan *p);
 void free_fourier(bp_plan *p);
 void free_bst(bp_plan *p);
 void free_logpolar(bp_plan *p);
+void free_logpolar_partial(bp_plan *p);
+bp_status launch_logpolar_partial(bp_plan *p, const void *sino, bp_dtype dt, float *img, int batch, int sectors,
+                                  float a_r, cudaStream_t st);
 bp_status launch_logpolar(bp_plan *p, const void *sino, bp_dtype dt, float *img, int batch, cudaStream_t st);
 bp_status launch_grid_to_image(bp_plan *p, const float *deap, float *img, cudaStream_t st);
 bp_status launch_bst(bp_plan *p, const void *sino, bp_dtype dt, float *img, int os, int batch, cudaStream_t st);

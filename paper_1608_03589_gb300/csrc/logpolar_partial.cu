@@ -1,0 +1,487 @@
+// Partial (sector) log-polar backprojection (Section 5.2, "Partial Backprojections", with the
+// shifting property eq "sh_prop"; per sector Andersson's convolution of Section 5.1 Steps 1-4,
+// eq "andersson", kernel eq "and_kernel").
+//
+// The half-line angles phi in [0, pi) count every line once; they are split into Q sectors of
+// K nodes (phi_j = j dphi, dphi = pi / n_half, n_half = 2^ceil(log2 n_theta)).  Sector q, centre
+// phi_c, moves the origin to -d xi_{phi_c} (d = R (1 - a_r) / a_r, R = sqrt 2 the radius of the
+// image disk): the shifted sinogram g(s - d cos(phi - phi_c), phi) has every line of the
+// sector at s > 0, so its log-polar mesh mu_i = rho_0 + i drho starts at a finite rho_0 (the
+// lowest line any output node sees, ln((d - R) cos gamma) - 2 drho) and ends at ln(d + R),
+// with the outermost step at most the detector pitch (eq "N_rho").  Per sector:
+//   Step 1 (fused into the first transform): the shifted sinogram on the (mu, phi) mesh by
+//   linear interpolation along the detector and between the bracketing projections; the
+//   detector coordinate is split on the host (FP64) into integer and fraction per mu node and
+//   per sector row, so float32 only adds fractions;
+//   Step 2: the unit-mass hat of the point mass at -ln cos(b dphi) / drho per angular lag b,
+//   transformed once per plan (same kernels), scaled by dphi / (Lp Lr);
+//   Step 3: linear convolution in rho and in angle by zero-padded 2D FFTs: rows along rho
+//   (two real rows packed per complex transform), columns along phi (only the K sector rows
+//   are read; only the output angle rows are written back), rows along rho inverse (only the
+//   output rho window is kept);
+//   Step 4: bilinear interpolation at the pixel centres from per-sector FP64-built tables,
+//   summed over the sectors.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "common.cuh"
+#include "fft.cuh"
+
+namespace bp {
+
+namespace {
+
+constexpr int kMaxLPP = 16384;  // longest transform held in shared memory
+
+__device__ __forceinline__ void norm_frac(int &k, float &f) {
+    if (f >= 1.f) {
+        k += 1;
+        f -= 1.f;
+    }
+}
+
+// g at detector index u = k + f of row `row` (zero off the detector), linear interpolation.
+template <typename Tin>
+__device__ __forceinline__ float lpp_lerp(const Tin *__restrict__ row, int n_det, int k, float f) {
+    const float g0 = (k >= 0 && k < n_det) ? load_f(row + k) : 0.f;
+    const float g1 = (k + 1 >= 0 && k + 1 < n_det) ? load_f(row + k + 1) : 0.f;
+    return fmaf(f, g1 - g0, g0);
+}
+
+// Step 1 sample of sector row j (bracket a, row split r) at mu node i (split s):
+// u = +(s_i/dt) + (-D_j + c0) for an unflipped projection, -(s_i/dt) + (D_j + c0) for a flipped one.
+template <typename Tin>
+__device__ __forceinline__ float lpp_sample(const Tin *__restrict__ sino, int n_det, const int4 a, const int4 r,
+                                            const int2 s) {
+    const float sf = __int_as_float(s.y);
+    float v[2];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const int code = e == 0 ? a.x : a.y;
+        const int kproj = code & 0x3fffffff;
+        const bool neg = (code >> 30) & 1;
+        int k;
+        float f;
+        if (!neg) {
+            k = s.x + r.x;
+            f = sf + __int_as_float(r.y);
+        } else {
+            k = r.z - s.x - 1;
+            f = (1.f - sf) + __int_as_float(r.w);
+        }
+        norm_frac(k, f);
+        v[e] = lpp_lerp(sino + (long long)kproj * n_det, n_det, k, f);
+    }
+    const float w = __int_as_float(a.z);
+    return fmaf(w, v[1] - v[0], v[0]);
+}
+
+// Forward transform along rho of rows (2b, 2b+1) < n_rows: the sector's Step 1 samples
+// (kernel_src = 0) or the kernel hat rows (kernel_src = 1).
+template <typename Tin, int E>
+__global__ void __launch_bounds__(1024, 1)
+lpp_rows_fwd_kernel(const Tin *__restrict__ sino, int n_det, const int4 *__restrict__ atab,
+                    const int4 *__restrict__ rowtab, const int2 *__restrict__ stab, const float2 *__restrict__ kfrac,
+                    int kernel_src, int n_rho, int n_rows, float2 *__restrict__ T, const float2 *__restrict__ tw,
+                    int logL) {
+    extern __shared__ __align__(128) float2 z[];
+    const int L = 1 << logL;
+    float2 *tws = z + L;
+    stage_twiddles(tws, tw, L / 2);
+    const int q0 = 2 * blockIdx.x, q1 = q0 + 1;
+    const bool has1 = q1 < n_rows;
+    if (kernel_src) {
+        const float2 k0 = __ldg(kfrac + q0), k1 = has1 ? __ldg(kfrac + q1) : make_float2(-1.f, 0.f);
+        const int a0 = (int)k0.x, a1 = (int)k1.x;
+        for (int i = threadIdx.x; i < L; i += blockDim.x) {
+            float va = 0.f, vb = 0.f;
+            if (k0.x >= 0.f) va = (i == a0) ? 1.f - k0.y : ((i == a0 + 1) ? k0.y : 0.f);
+            if (k1.x >= 0.f) vb = (i == a1) ? 1.f - k1.y : ((i == a1 + 1) ? k1.y : 0.f);
+            z[i] = make_float2(va, vb);
+        }
+    } else {
+        const int4 a0 = __ldg(atab + q0), r0 = __ldg(rowtab + q0);
+        const int4 a1 = has1 ? __ldg(atab + q1) : a0, r1 = has1 ? __ldg(rowtab + q1) : r0;
+        for (int i = threadIdx.x; i < L; i += blockDim.x) {
+            float va = 0.f, vb = 0.f;
+            if (i < n_rho) {
+                const int2 s = __ldg(stab + i);
+                va = lpp_sample(sino, n_det, a0, r0, s);
+                if (has1) vb = lpp_sample(sino, n_det, a1, r1, s);
+            }
+            z[i] = make_float2(va, vb);
+        }
+    }
+    __syncthreads();
+    stockham_fft<E>(z, logL, tws, 1, false, threadIdx.x, blockDim.x);
+    float2 *ta = T + (long long)q0 * L, *tb = T + (long long)q1 * L;
+    for (int k = threadIdx.x; k < L; k += blockDim.x) {
+        const float2 zm = z[k];
+        const float2 zc = z[(L - k) & (L - 1)];
+        ta[k] = make_float2(0.5f * (zm.x + zc.x), 0.5f * (zm.y - zc.y));
+        if (has1) tb[k] = make_float2(0.5f * (zm.y + zc.y), -0.5f * (zm.x - zc.x));
+    }
+}
+
+// Transforms along phi (length Lp) of columns [k0, k0 + C) of T (rows of length Lr): rows
+// >= n_in are zero.  prep = 1: forward, times `scale`, into Khat (all Lp rows).  prep = 0:
+// forward, times Khat, inverse; output row a_lo + r (mod Lp) goes to row r of T, r < n_aout.
+template <int E>
+__global__ void __launch_bounds__(1024, 1)
+lpp_cols_kernel(float2 *__restrict__ T, float2 *__restrict__ Khat, const float2 *__restrict__ tw, int logLp, int Lr,
+                int C, int n_in, int prep, float scale, int a_lo, int n_aout) {
+    extern __shared__ __align__(128) float2 z[];
+    const int Lp = 1 << logLp;
+    float2 *tws = z + (size_t)C * Lp;
+    stage_twiddles(tws, tw, Lp / 2);
+    const long long k0 = (long long)blockIdx.x * C;
+    for (int e = threadIdx.x; e < C * Lp; e += blockDim.x) {
+        const int q = e / C, c = e - q * C;
+        z[c * Lp + q] = q < n_in ? T[(long long)q * Lr + k0 + c] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    const int nthr = fft_threads(Lp), groups = blockDim.x / nthr;
+    const int g = threadIdx.x / nthr, tid = threadIdx.x - g * nthr;
+    for (int c0 = 0; c0 < C; c0 += groups) stockham_fft<E>(z + (c0 + g) * Lp, logLp, tws, 1, false, tid, nthr);
+    if (prep) {
+        for (int e = threadIdx.x; e < C * Lp; e += blockDim.x) {
+            const int q = e / C, c = e - q * C;
+            const float2 v = z[c * Lp + q];
+            Khat[(long long)q * Lr + k0 + c] = make_float2(scale * v.x, scale * v.y);
+        }
+        return;
+    }
+    for (int e = threadIdx.x; e < C * Lp; e += blockDim.x) {
+        const int q = e / C, c = e - q * C;
+        z[c * Lp + q] = cmul(z[c * Lp + q], __ldg(Khat + (long long)q * Lr + k0 + c));
+    }
+    __syncthreads();
+    for (int c0 = 0; c0 < C; c0 += groups) stockham_fft<E>(z + (c0 + g) * Lp, logLp, tws, 1, true, tid, nthr);
+    for (int e = threadIdx.x; e < C * n_aout; e += blockDim.x) {
+        const int r = e / C, c = e - r * C;
+        const int q = (a_lo + r) & (Lp - 1);
+        T[(long long)r * Lr + k0 + c] = z[c * Lp + q];
+    }
+}
+
+// Inverse transform along rho of output rows (2b, 2b+1) < n_rows (both real, packed as
+// T_a + i T_b); outputs c_lo .. c_lo + n_out - 1 go to B.
+template <int E>
+__global__ void __launch_bounds__(1024, 1)
+lpp_rows_inv_kernel(const float2 *__restrict__ T, float *__restrict__ B, const float2 *__restrict__ tw, int logL,
+                    int n_rows, int c_lo, int n_out) {
+    extern __shared__ __align__(128) float2 z[];
+    const int L = 1 << logL;
+    float2 *tws = z + L;
+    stage_twiddles(tws, tw, L / 2);
+    const int q0 = 2 * blockIdx.x, q1 = q0 + 1;
+    const bool has1 = q1 < n_rows;
+    const float2 *ta = T + (long long)q0 * L, *tb = T + (long long)q1 * L;
+    for (int k = threadIdx.x; k < L; k += blockDim.x) {
+        const float2 a = ta[k], b = has1 ? tb[k] : make_float2(0.f, 0.f);
+        z[k] = make_float2(a.x - b.y, a.y + b.x);
+    }
+    __syncthreads();
+    stockham_fft<E>(z, logL, tws, 1, true, threadIdx.x, blockDim.x);
+    for (int c = threadIdx.x; c < n_out; c += blockDim.x) {
+        const float2 v = z[c_lo + c];
+        B[(long long)q0 * n_out + c] = v.x;
+        if (has1) B[(long long)q1 * n_out + c] = v.y;
+    }
+}
+
+// Step 4 for one sector: pixel p adds B at its (rho node + fraction, angle node + fraction).
+__global__ void __launch_bounds__(256)
+lpp_cart_kernel(const float *__restrict__ B, const int4 *__restrict__ pix, float *__restrict__ img, int NN, int n_out,
+                int accumulate) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= NN) return;
+    const int4 t = __ldg(pix + p);
+    const float fc = __int_as_float(t.y), fa = __int_as_float(t.w);
+    const float *r0 = B + (long long)t.z * n_out + t.x, *r1 = r0 + n_out;
+    const float v0 = fmaf(fc, __ldg(r0 + 1) - __ldg(r0), __ldg(r0));
+    const float v1 = fmaf(fc, __ldg(r1 + 1) - __ldg(r1), __ldg(r1));
+    const float v = fmaf(fa, v1 - v0, v0);
+    img[p] = accumulate ? img[p] + v : v;
+}
+
+// Per-sector pixel tables in FP64: (c0, fc, a0, fa) of ln |x - O'| and of the angle of x - O'.
+struct PixGeom {
+    double dx, d, rho0, drho, dphi;
+    int N, K, c_lo, a_lo, n_out, n_aout, Q;
+};
+
+__global__ void __launch_bounds__(256)
+lpp_pix_kernel(int4 *__restrict__ pix, PixGeom G) {
+    const long long NN = (long long)G.N * G.N;
+    const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (e >= NN * G.Q) return;
+    const int q = (int)(e / NN);
+    const long long p = e - (long long)q * NN;
+    const int iy = (int)(p / G.N), ix = (int)(p - (long long)iy * G.N);
+    const double x = -1.0 + (ix + 0.5) * G.dx, y = -1.0 + (iy + 0.5) * G.dx;
+    const double phic = (q * (double)G.K + 0.5 * (G.K - 1)) * G.dphi;
+    const double ux = cos(phic), uy = sin(phic);
+    const double px = x + G.d * ux, py = y + G.d * uy;
+    const double rho = 0.5 * log(px * px + py * py);
+    const double ang = phic + atan2(-uy * px + ux * py, ux * px + uy * py);
+    const double c = (rho - G.rho0) / G.drho - G.c_lo;
+    const double a = ang / G.dphi - ((double)q * G.K + G.a_lo);
+    double c0 = floor(c), a0 = floor(a);
+    c0 = fmin(fmax(c0, 0.0), (double)(G.n_out - 2));
+    a0 = fmin(fmax(a0, 0.0), (double)(G.n_aout - 2));
+    pix[e] = make_int4((int)c0, __float_as_int((float)(c - c0)), (int)a0, __float_as_int((float)(a - a0)));
+}
+
+int pow2_ge(long long n) {
+    int p = 1;
+    while (p < n) p <<= 1;
+    return p;
+}
+
+std::vector<float2> half_twiddles(int n) {
+    std::vector<float2> tw(std::max(1, n / 2));
+    for (int i = 0; i < n / 2; ++i) {
+        const double an = -2.0 * M_PI * (double)i / (double)n;
+        tw[i] = make_float2((float)std::cos(an), (float)std::sin(an));
+    }
+    return tw;
+}
+
+int fbits(float f) {
+    int i;
+    std::memcpy(&i, &f, sizeof i);
+    return i;
+}
+
+// value = k + f with integer k and f in [0, 1)
+void split(double v, int &k, float &f) {
+    const double fl = std::floor(v);
+    k = (int)fl;
+    f = (float)(v - fl);
+    if (f >= 1.0f) {  // rounding up to 1
+        k += 1;
+        f = 0.f;
+    }
+}
+
+int cols_per_cta_lpp(int Lp) { return std::max(1, std::min(8, (int)(131072 / (sizeof(float2) * Lp)))); }
+
+template <typename Tin>
+bp_status rows_fwd_lpp(bp_plan *p, const Tin *sino, int q, int kernel_src, cudaStream_t st) {
+    LppWork &w = p->lpp;
+    const size_t smem = sizeof(float2) * ((size_t)w.Lr + w.Lr / 2);
+    auto kern = fft_elems(w.Lr) == 16 ? lpp_rows_fwd_kernel<Tin, 16> : lpp_rows_fwd_kernel<Tin, 8>;
+    BP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int n_rows = kernel_src ? w.Lp : w.K;
+    kern<<<(n_rows + 1) / 2, fft_threads(w.Lr), smem, st>>>(sino, p->n_det, w.atab + (size_t)q * w.K, w.rowtab,
+                                                            w.stab, w.kfrac, kernel_src, w.n_rho, n_rows, w.T, w.twLr,
+                                                            ilog2(w.Lr));
+    BP_CUDA_TRY(cudaGetLastError());
+    return BP_OK;
+}
+
+bp_status cols_lpp(bp_plan *p, int prep, float scale, cudaStream_t st) {
+    LppWork &w = p->lpp;
+    const int C = cols_per_cta_lpp(w.Lp);
+    const size_t smem = sizeof(float2) * ((size_t)C * w.Lp + w.Lp / 2);
+    auto kern = fft_elems(w.Lp) == 16 ? lpp_cols_kernel<16> : lpp_cols_kernel<8>;
+    BP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int nthr = fft_threads(w.Lp);
+    int groups = 1;
+    while (groups * 2 <= C && nthr * groups * 2 <= 1024) groups *= 2;
+    kern<<<w.Lr / C, nthr * groups, smem, st>>>(w.T, w.Khat, w.twLp, ilog2(w.Lp), w.Lr, C, prep ? w.Lp : w.K, prep,
+                                                scale, w.a_lo, w.n_aout);
+    BP_CUDA_TRY(cudaGetLastError());
+    return BP_OK;
+}
+
+bp_status ensure_lpp(bp_plan *p, int Q, float a_r, cudaStream_t st) {
+    LppWork &w = p->lpp;
+    if (w.T && w.Q == Q && w.a_r == a_r) return BP_OK;
+    free_logpolar_partial(p);
+    const int N = p->N, n_det = p->n_det, n_theta = p->n_theta;
+    const double dx = 2.0 / N, dt = p->dt, R = std::sqrt(2.0);
+    const int n_half = pow2_ge(std::max(n_theta, 1));
+    if (Q < 1 || n_half % Q) return fail(BP_ERR_INVALID_ARG, "sectors must be a power of two dividing the angle nodes");
+    const int K = n_half / Q;
+    const double dphi = M_PI / n_half, d = R * (1.0 - a_r) / a_r;
+    const double beta = 0.5 * (K - 1) * dphi, alpha = std::asin(R / d), gamma = alpha + beta + 3.0 * dphi;
+    if (!(gamma < 0.5 * M_PI))
+        return fail(BP_ERR_INVALID_ARG, "sector too wide for the shift: use more sectors or a smaller a_r");
+    const double step = -std::log(1.0 - dt / (d + R));
+    const double rho0 = std::log((d - R) * std::cos(gamma)) - 2.0 * step, top = std::log(d + R);
+    const long long n_rho = (long long)std::ceil((top - rho0) / step) + 1;
+    const double drho = (top - rho0) / (double)(n_rho - 1);
+    const int c_lo = (int)std::floor((std::log(d - R) - rho0) / drho);
+    const long long n_out = n_rho - c_lo;
+    const double A = alpha / dphi;
+    const int a_lo = (int)std::floor(0.5 * (K - 1) - A) - 1, a_hi = (int)std::ceil(0.5 * (K - 1) + A) + 1;
+    const int n_aout = a_hi - a_lo + 1;
+    const int b_lo = a_lo - (K - 1), b_hi = a_hi;
+    const int kmax = (int)std::floor(-std::log(std::cos(std::max(-b_lo, b_hi) * dphi)) / drho) + 1;
+    const long long Lr_req = n_rho + kmax + 1;
+    const long long Lp_req = std::max<long long>({(long long)(b_hi - b_lo + 1), (long long)n_aout, (long long)K});
+    if (Lr_req > kMaxLPP || Lp_req > kMaxLPP)
+        return fail(BP_ERR_UNSUPPORTED, "partial log-polar: mesh too fine for the shared-memory transforms");
+    w.Q = Q;
+    w.a_r = a_r;
+    w.K = K;
+    w.n_half = n_half;
+    w.n_rho = (int)n_rho;
+    w.c_lo = c_lo;
+    w.n_out = (int)n_out;
+    w.a_lo = a_lo;
+    w.n_aout = n_aout;
+    w.Lr = pow2_ge(Lr_req);
+    w.Lp = pow2_ge(Lp_req);
+    // Step 1 tables: s_i / dt split per mu node; the shift d cos(phi_j - phi_c) / dt split per
+    // sector row (the same for every sector); bracketing projections per angle node
+    const double c0 = 0.5 * (n_det - 1);
+    std::vector<int2> stab(n_rho);
+    for (long long i = 0; i < n_rho; ++i) {
+        int k;
+        float f;
+        split(std::exp(rho0 + (double)i * drho) / dt, k, f);
+        stab[i] = make_int2(k, fbits(f));
+    }
+    std::vector<int4> rowtab(K);
+    for (int jp = 0; jp < K; ++jp) {
+        const double D = d * std::cos((jp - 0.5 * (K - 1)) * dphi) / dt;
+        int kp, kn;
+        float fp, fn;
+        split(-D + c0, kp, fp);
+        split(D + c0, kn, fn);
+        rowtab[jp] = make_int4(kp, fbits(fp), kn, fbits(fn));
+    }
+    std::vector<std::pair<double, int>> th(n_theta);
+    for (int k = 0; k < n_theta; ++k) {
+        double a = std::fmod(p->theta[k], M_PI);
+        if (a < 0) a += M_PI;
+        if (a >= M_PI) a = 0.0;
+        th[k] = {a, k};
+    }
+    std::stable_sort(th.begin(), th.end(),
+                     [](const std::pair<double, int> &x, const std::pair<double, int> &y) { return x.first < y.first; });
+    std::vector<int4> atab(n_half);
+    for (int j = 0; j < n_half; ++j) {
+        const double tq = j * dphi;  // in [0, pi)
+        const int a = (int)(std::upper_bound(th.begin(), th.end(), std::make_pair(tq, 0x7fffffff),
+                                             [](const std::pair<double, int> &x, const std::pair<double, int> &y) {
+                                                 return x.first < y.first;
+                                             }) - th.begin()) - 1;
+        int lo, hi, slo, shi;
+        double alo, ahi;
+        if (a < 0) {
+            lo = n_theta - 1; alo = th[lo].first - M_PI; slo = 1;
+            hi = 0; ahi = th[0].first; shi = 0;
+        } else if (a == n_theta - 1) {
+            lo = n_theta - 1; alo = th[lo].first; slo = 0;
+            hi = 0; ahi = th[0].first + M_PI; shi = 1;
+        } else {
+            lo = a; alo = th[a].first; slo = 0;
+            hi = a + 1; ahi = th[a + 1].first; shi = 0;
+        }
+        atab[j] = make_int4(th[lo].second | (slo << 30), th[hi].second | (shi << 30),
+                            fbits((float)((tq - alo) / (ahi - alo))), 0);
+    }
+    // Step 2: kernel node and fraction per row of the angular transform (lag b at row b mod Lp)
+    std::vector<float2> kfrac(w.Lp, make_float2(-1.f, 0.f));
+    for (int b = b_lo; b <= b_hi; ++b) {
+        const double r = -std::log(std::cos(b * dphi)) / drho;
+        const double a0 = std::floor(r);
+        kfrac[((b % w.Lp) + w.Lp) % w.Lp] = make_float2((float)a0, (float)(r - a0));
+    }
+    const std::vector<float2> twr = half_twiddles(w.Lr), twp = half_twiddles(w.Lp);
+    const size_t NN = (size_t)N * N;
+    cudaError_t e = cudaSuccess;
+    auto alloc = [&](void **ptr, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMalloc(ptr, std::max<size_t>(bytes, 16));
+        if (e == cudaSuccess) w.bytes += bytes;
+    };
+    alloc((void **)&w.stab, sizeof(int2) * stab.size());
+    alloc((void **)&w.rowtab, sizeof(int4) * rowtab.size());
+    alloc((void **)&w.atab, sizeof(int4) * atab.size());
+    alloc((void **)&w.kfrac, sizeof(float2) * kfrac.size());
+    alloc((void **)&w.twLr, sizeof(float2) * twr.size());
+    alloc((void **)&w.twLp, sizeof(float2) * twp.size());
+    alloc((void **)&w.T, sizeof(float2) * (size_t)w.Lp * w.Lr);
+    alloc((void **)&w.Khat, sizeof(float2) * (size_t)w.Lp * w.Lr);
+    alloc((void **)&w.B, sizeof(float) * (size_t)(n_aout + 1) * w.n_out);
+    alloc((void **)&w.pix, sizeof(int4) * NN * Q);
+    auto up = [&](void *dst, const void *src, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
+    };
+    up(w.stab, stab.data(), sizeof(int2) * stab.size());
+    up(w.rowtab, rowtab.data(), sizeof(int4) * rowtab.size());
+    up(w.atab, atab.data(), sizeof(int4) * atab.size());
+    up(w.kfrac, kfrac.data(), sizeof(float2) * kfrac.size());
+    up(w.twLr, twr.data(), sizeof(float2) * twr.size());
+    up(w.twLp, twp.data(), sizeof(float2) * twp.size());
+    if (e != cudaSuccess) {
+        free_logpolar_partial(p);
+        return cuda_fail(e, "partial log-polar workspace");
+    }
+    PixGeom G{dx, d, rho0, drho, dphi, N, K, c_lo, a_lo, (int)n_out, n_aout, Q};
+    const long long total = (long long)NN * Q;
+    lpp_pix_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(w.pix, G);
+    bp_status s = cudaGetLastError() == cudaSuccess ? BP_OK : fail(BP_ERR_CUDA, "partial log-polar pixel tables");
+    // kernel transform, scaled by dphi / (Lp Lr) (the two inverse transforms are unnormalised)
+    if (s == BP_OK) s = rows_fwd_lpp<float>(p, nullptr, 0, 1, st);
+    if (s == BP_OK) s = cols_lpp(p, 1, (float)(dphi / ((double)w.Lp * w.Lr)), st);
+    if (s != BP_OK) {
+        free_logpolar_partial(p);
+        return s;
+    }
+    return BP_OK;
+}
+
+}  // namespace
+
+void free_logpolar_partial(bp_plan *p) {
+    LppWork &w = p->lpp;
+    cudaFree(w.stab);
+    cudaFree(w.rowtab);
+    cudaFree(w.atab);
+    cudaFree(w.kfrac);
+    cudaFree(w.twLr);
+    cudaFree(w.twLp);
+    cudaFree(w.T);
+    cudaFree(w.Khat);
+    cudaFree(w.B);
+    cudaFree(w.pix);
+    w = LppWork();
+}
+
+bp_status launch_logpolar_partial(bp_plan *p, const void *sino, bp_dtype dt, float *img, int batch, int sectors,
+                                  float a_r, cudaStream_t st) {
+    bp_status s = ensure_lpp(p, sectors, a_r, st);
+    if (s != BP_OK) return s;
+    LppWork &w = p->lpp;
+    const int N = p->N, NN = N * N;
+    const size_t esz = dt == BP_F32 ? 4 : 2;
+    const size_t smemL = sizeof(float2) * ((size_t)w.Lr + w.Lr / 2);
+    auto kinv = fft_elems(w.Lr) == 16 ? lpp_rows_inv_kernel<16> : lpp_rows_inv_kernel<8>;
+    BP_CUDA_TRY(cudaFuncSetAttribute(kinv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smemL));
+    for (int b = 0; b < batch; ++b) {
+        const char *sb = (const char *)sino + esz * (size_t)b * p->n_theta * p->n_det;
+        float *ib = img + (size_t)b * NN;
+        for (int q = 0; q < w.Q; ++q) {
+            switch (dt) {
+                case BP_F32: s = rows_fwd_lpp(p, (const float *)sb, q, 0, st); break;
+                case BP_BF16: s = rows_fwd_lpp(p, (const __nv_bfloat16 *)sb, q, 0, st); break;
+                case BP_F16: s = rows_fwd_lpp(p, (const __half *)sb, q, 0, st); break;
+            }
+            if (s != BP_OK) return s;
+            if ((s = cols_lpp(p, 0, 1.f, st)) != BP_OK) return s;
+            kinv<<<(w.n_aout + 1) / 2, fft_threads(w.Lr), smemL, st>>>(w.T, w.B, w.twLr, ilog2(w.Lr), w.n_aout,
+                                                                       w.c_lo, w.n_out);
+            lpp_cart_kernel<<<(NN + 255) / 256, 256, 0, st>>>(w.B, w.pix + (size_t)q * NN, ib, NN, w.n_out, q > 0);
+            BP_CUDA_TRY(cudaGetLastError());
+        }
+    }
+    return BP_OK;
+}
+
+}  // namespace bp

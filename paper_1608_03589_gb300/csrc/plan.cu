@@ -114,6 +114,7 @@ static void plan_free_device(bp_plan *p) {
     free_fourier(p);
     free_bst(p);
     free_logpolar(p);
+    free_logpolar_partial(p);
     cudaFree(p->d_stage);
     cudaFree(p->d_desc);
     cudaFree(p->d_counter);
@@ -306,6 +307,17 @@ extern "C" bp_status bp_backproject_logpolar(bp_plan *p, const void *sino, bp_dt
     if (st != BP_OK) return st;
     if (!valid_dtype(dtype)) return fail(BP_ERR_INVALID_ARG, "invalid dtype");
     return launch_logpolar(p, sino, dtype, img, batch, (cudaStream_t)stream);
+}
+
+extern "C" bp_status bp_backproject_logpolar_partial(bp_plan *p, const void *sino, bp_dtype dtype, float *img,
+                                                     int sectors, float a_r, int batch, void *stream) {
+    set_error("");
+    bp_status st = check_common(p, sino, img, batch);
+    if (st != BP_OK) return st;
+    if (!valid_dtype(dtype)) return fail(BP_ERR_INVALID_ARG, "invalid dtype");
+    if (sectors < 1 || (sectors & (sectors - 1))) return fail(BP_ERR_INVALID_ARG, "sectors must be a power of two");
+    if (!(a_r > 0.f && a_r < 0.5f)) return fail(BP_ERR_INVALID_ARG, "a_r must lie in (0, 1/2)");
+    return launch_logpolar_partial(p, sino, dtype, img, batch, sectors, a_r, (cudaStream_t)stream);
 }
 
 extern "C" bp_status bp_set_fourier_width(bp_plan *p, int width) {
