@@ -27,6 +27,7 @@
 
 #include <algorithm>
 #include <mutex>
+#include <type_traits>
 
 #include "common.cuh"
 #include "direct_tile.cuh"
@@ -249,6 +250,7 @@ bp_direct_quad_kernel(const __grid_constant__ CUtensorMap tmap, float *__restric
     __shared__ float4 sf[3][STAGE];   // |c| + |s| - {0, 1, 2}: far corner; corner-role bits
     __shared__ int sof[3][STAGE];     // J0 - J0r (TMA box starts at the 8-aligned J0r)
     __shared__ float sw[3][STAGE];
+    __shared__ int su[3];             // stage-uniform corner roles: role | 4, plus 8 if every far corner has two ramps
     __shared__ __align__(8) unsigned long long bars[2];
 
     const int tid = threadIdx.x;
@@ -295,6 +297,20 @@ bp_direct_quad_kernel(const __grid_constant__ CUtensorMap tmap, float *__restric
             sof[slot][tid] = J0 - J0r;
             sw[slot][tid] = wuni > 0.f ? wuni : p.w;
             tma_load_3d(smem_u32(raw + (b * STAGE + tid) * RS), &tmap, J0r, k0 + tid, bz, bar0 + 8 * b);
+        }
+        if (warp == 0) {  // the stage's angles are lanes < kn <= 32 of warp 0
+            const bool act = tid < kn;
+            int rl = 0;
+            bool f2 = true;
+            if (act) {
+                const AngleParam p = ap[k0 + tid];
+                rl = (p.c < 0.f ? 1 : 0) | (p.s < 0.f ? 2 : 0);
+                f2 = fabsf(p.c) + fabsf(p.s) - 1.f >= 0.f;
+            }
+            const int r0 = __shfl_sync(0xffffffffu, rl, 0);
+            const bool same = __all_sync(0xffffffffu, !act || rl == r0);
+            const bool all2 = __all_sync(0xffffffffu, f2);
+            if (tid == 0) su[slot] = same ? (r0 | 4 | (all2 ? 8 : 0)) : 0;
         }
     };
 
@@ -351,23 +367,29 @@ bp_direct_quad_kernel(const __grid_constant__ CUtensorMap tmap, float *__restric
             if (tid < STAGE) fence_proxy_async_smem();
             prepare(i + 2);
         }
-        for (int kk = 0; kk < kn; ++kk) {
+        // one angle: CHECK = per-angle role check, FAR = 0 per-angle far-corner test, 1 two ramps,
+        // 2 three ramps
+        auto angle = [&](int kk, auto check_tag, auto far_tag) {
+            constexpr bool CHECK = decltype(check_tag)::value;
+            constexpr int FAR = decltype(far_tag)::value;
             const float4 A = sq[slot][kk];
             const float4 R2 = sr[slot][kk];
             const float4 F = sf[slot][kk];
-            const int rl = __float_as_int(F.w);
-            if (rl != role) {
-                // the corner roles follow the signs of (c, s): move each pixel's sum to its new role
+            if (CHECK) {
+                const int rl = __float_as_int(F.w);
+                if (rl != role) {
+                    // the corner roles follow the signs of (c, s): move each pixel's sum to its new role
 #pragma unroll
-                for (int a = 0; a < 4; ++a) xor_permute(acc[a], rl ^ role);
-                role = rl;
+                    for (int a = 0; a < 4; ++a) xor_permute(acc[a], rl ^ role);
+                    role = rl;
+                }
             }
             const float qt = fmaf(fy, A.z, fmaf(fx, A.y, A.x));
             const unsigned long long Q = pk2(qt, fmaf(16.f, A.y, qt));
             const unsigned long long CC = pk2(A.y, A.y);
             const unsigned base = __float_as_uint(A.w);
             // far corner: with |c| + |s| >= 1 its lowest ramp is always 1 (two ramps suffice)
-            const bool far2 = F.y >= 0.f;
+            const bool far2 = FAR == 1 || (FAR == 0 && F.y >= 0.f);
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const unsigned long long qa = h ? ffma2(pk2(32.f, 32.f), CC, Q) : Q;  // blocks 2h, 2h + 1
@@ -395,6 +417,25 @@ bp_direct_quad_kernel(const __grid_constant__ CUtensorMap tmap, float *__restric
                                     fmaf(t.z, add_sat(r, F.y), fmaf(t.y, add_sat(r, F.x), q[3])));
                 }
             }
+        };
+        using True_ = std::integral_constant<bool, true>;
+        using False_ = std::integral_constant<bool, false>;
+        const int u = su[slot];
+        if (u & 4) {
+            // every angle of the stage has the same corner roles: exchange once, no checks
+            const int rl = u & 3;
+            if (rl != role) {
+#pragma unroll
+                for (int a = 0; a < 4; ++a) xor_permute(acc[a], rl ^ role);
+                role = rl;
+            }
+            if (u & 8) {
+                for (int kk = 0; kk < kn; ++kk) angle(kk, False_(), std::integral_constant<int, 1>());
+            } else {
+                for (int kk = 0; kk < kn; ++kk) angle(kk, False_(), std::integral_constant<int, 2>());
+            }
+        } else {
+            for (int kk = 0; kk < kn; ++kk) angle(kk, True_(), std::integral_constant<int, 0>());
         }
     }
     if (!ok && lane == 0) atomicExch(err, 1);
