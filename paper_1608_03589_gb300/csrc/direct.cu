@@ -278,38 +278,34 @@ bp_direct_quad_kernel(const __grid_constant__ CUtensorMap tmap, float *__restric
     auto prepare = [&](int i) {
         const int k0 = (s0 + i) * STAGE, kn = min(STAGE, n_theta - k0), b = i & 1, slot = i % 3;
         if (tid == 0) mbar_expect_tx(bar0 + 8 * b, (uint32_t)(kn * Wb * (int)sizeof(Tin)));
-        if (tid < kn) {
-            const AngleParam p = ap[k0 + tid];
-            const long long U = p.U00 + (long long)tx * p.CT + (long long)ty * p.ST;
-            const int Ji = (int)(U >> 32);
-            const float frac = (float)(unsigned)(U & 0xffffffffLL) * 2.3283064365386963e-10f;
-            const float lo = fminf(p.c, 0.f) + fminf(p.s, 0.f);
-            const int J0 = Ji + (int)floorf((float)(kTile - 1) * lo) - 1;
-            const int J0r = J0 & ~7;
-            const float q0 = (float)(Ji - J0 - C) + frac + lo;
-            const unsigned base = tab_u32 + (unsigned)((b * STAGE + tid) * W) * 16u + 16u * (unsigned)C -
-                                  (kMagicBits << 4);
-            const float ac = fabsf(p.c), as = fabsf(p.s), af = ac + as;
-            const int role = (p.c < 0.f ? 1 : 0) | (p.s < 0.f ? 2 : 0);
-            sq[slot][tid] = make_float4(q0, p.c, p.s, __uint_as_float(base));
-            sr[slot][tid] = make_float4(ac, ac - 1.f, as, as - 1.f);
-            sf[slot][tid] = make_float4(af, af - 1.f, af - 2.f, __int_as_float(role));
-            sof[slot][tid] = J0 - J0r;
-            sw[slot][tid] = wuni > 0.f ? wuni : p.w;
-            tma_load_3d(smem_u32(raw + (b * STAGE + tid) * RS), &tmap, J0r, k0 + tid, bz, bar0 + 8 * b);
-        }
         if (warp == 0) {  // the stage's angles are lanes < kn <= 32 of warp 0
             const bool act = tid < kn;
-            int rl = 0;
-            bool f2 = true;
+            int role = 0;
+            bool far2 = true;
             if (act) {
                 const AngleParam p = ap[k0 + tid];
-                rl = (p.c < 0.f ? 1 : 0) | (p.s < 0.f ? 2 : 0);
-                f2 = fabsf(p.c) + fabsf(p.s) - 1.f >= 0.f;
+                const long long U = p.U00 + (long long)tx * p.CT + (long long)ty * p.ST;
+                const int Ji = (int)(U >> 32);
+                const float frac = (float)(unsigned)(U & 0xffffffffLL) * 2.3283064365386963e-10f;
+                const float lo = fminf(p.c, 0.f) + fminf(p.s, 0.f);
+                const int J0 = Ji + (int)floorf((float)(kTile - 1) * lo) - 1;
+                const int J0r = J0 & ~7;
+                const float q0 = (float)(Ji - J0 - C) + frac + lo;
+                const unsigned base = tab_u32 + (unsigned)((b * STAGE + tid) * W) * 16u + 16u * (unsigned)C -
+                                      (kMagicBits << 4);
+                const float ac = fabsf(p.c), as = fabsf(p.s), af = ac + as;
+                role = (p.c < 0.f ? 1 : 0) | (p.s < 0.f ? 2 : 0);
+                far2 = af - 1.f >= 0.f;
+                sq[slot][tid] = make_float4(q0, p.c, p.s, __uint_as_float(base));
+                sr[slot][tid] = make_float4(ac, ac - 1.f, as, as - 1.f);
+                sf[slot][tid] = make_float4(af, af - 1.f, af - 2.f, __int_as_float(role));
+                sof[slot][tid] = J0 - J0r;
+                sw[slot][tid] = wuni > 0.f ? wuni : p.w;
+                tma_load_3d(smem_u32(raw + (b * STAGE + tid) * RS), &tmap, J0r, k0 + tid, bz, bar0 + 8 * b);
             }
-            const int r0 = __shfl_sync(0xffffffffu, rl, 0);
-            const bool same = __all_sync(0xffffffffu, !act || rl == r0);
-            const bool all2 = __all_sync(0xffffffffu, f2);
+            const int r0 = __shfl_sync(0xffffffffu, role, 0);
+            const bool same = __all_sync(0xffffffffu, !act || role == r0);
+            const bool all2 = __all_sync(0xffffffffu, far2);
             if (tid == 0) su[slot] = same ? (r0 | 4 | (all2 ? 8 : 0)) : 0;
         }
     };

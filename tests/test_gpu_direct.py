@@ -114,6 +114,22 @@ def test_direct_full_size_sampled():
     assert oracle.rel_l2(got, ref) <= TOL_DIRECT
 
 
+def test_direct_full_size_shuffled_angles():
+    # 2048^2, 2048 bins, 1800 angles over the whole circle in random order: nearly every
+    # 16-angle stage mixes the signs of (cos, sin), so the 2x2-block kernel runs its checked
+    # loop with role exchanges between angles (sorted angle sets take the stage-uniform loop)
+    wl = synth.LARGE
+    rng = np.random.default_rng(17)
+    theta = rng.permutation(rng.uniform(0.0, 2.0 * np.pi, wl.n_theta))
+    plan = bp.Plan(wl.N, wl.n_det, theta, wl.det_spacing)
+    q = to_dev(rng.normal(size=(wl.n_theta, wl.n_det)))
+    img = plan.backproject(q)
+    pix = sample_pixels(wl.N, 3000, seed=2)
+    ref = oracle.bp_linear_points(rounded(q), wl.N, theta, wl.det_spacing, pix)
+    got = img.reshape(-1)[torch.from_numpy(pix).to(dev())].cpu().numpy()
+    assert oracle.rel_l2(got, ref) <= TOL_DIRECT
+
+
 # ----------------------------------------------------------------------------------- filter
 @pytest.mark.parametrize("kind,param", [("ramlak", 0.0), ("shepp-logan", 0.0), ("tikhonov", 0.02)])
 @pytest.mark.parametrize("n_det,rows", [(256, 180), (41, 7), (1, 3), (2048, 64)])
