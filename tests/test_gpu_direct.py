@@ -101,11 +101,15 @@ def test_direct_low_precision_storage(dtype):
     print(f"{dtype}: storage-rounding error vs FP64 input {oracle.rel_l2(img.cpu().numpy(), full):.2e}")
 
 
-def test_direct_full_size_sampled():
+@pytest.mark.parametrize("shape", ["default", "autotuned"])
+def test_direct_full_size_sampled(shape):
     # 2048^2 image, 2048 bins, 1800 angles, Shepp-Logan-filtered noisy 50-ellipse sinogram:
-    # the full launch, checked on sampled pixels that the oracle evaluates one by one.
+    # the full launch, in the default launch shape and in the one the autotuner picks (the
+    # benchmark's), checked on sampled pixels that the oracle evaluates one by one.
     wl = synth.LARGE
     plan = bp.Plan(wl.N, wl.n_det, wl.theta, wl.det_spacing)
+    if shape == "autotuned":
+        plan.autotune("direct", torch.float32, 1)
     q = plan.filter(to_dev(wl.sinogram()), "shepp-logan")
     img = plan.backproject(q)
     pix = sample_pixels(wl.N, 400, seed=1)
@@ -122,6 +126,7 @@ def test_direct_full_size_shuffled_angles():
     rng = np.random.default_rng(17)
     theta = rng.permutation(rng.uniform(0.0, 2.0 * np.pi, wl.n_theta))
     plan = bp.Plan(wl.N, wl.n_det, theta, wl.det_spacing)
+    plan.set_shape((16, 4), "direct", torch.float32, 1)  # the benchmark's launch shape
     q = to_dev(rng.normal(size=(wl.n_theta, wl.n_det)))
     img = plan.backproject(q)
     pix = sample_pixels(wl.N, 3000, seed=2)
