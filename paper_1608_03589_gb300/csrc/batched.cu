@@ -7,7 +7,8 @@
 // SMs.  The per-slice descriptors travel by value in the kernel parameters (captured with
 // the launch, so the call can be recorded in a CUDA graph); the counter is reset by a
 // stream-ordered memset before each launch.  Each tile is the direct kernel's tile
-// (direct_tile.cuh).  No thread ever waits on another: the queue is one atomicAdd per item.
+// (direct_tile.cuh): the 2 x 2-block form for slices whose pixels are no larger than their
+// detector bins, else the pair-table form.  No thread ever waits on another: the queue is one atomicAdd per item.
 #include <algorithm>
 
 #include "common.cuh"
@@ -24,6 +25,7 @@ struct SliceDesc {
     float *img;
     const AngleParam *ap;
     int N, n_det, n_theta, W, C, dtype, tiles1, item0;  // tiles1: tiles per side; item0: first item
+    int quad;  // |c|, |s| <= 1: the 2 x 2-block tile
 };
 struct BatchParams {
     SliceDesc d[kMaxSlices];
@@ -33,8 +35,10 @@ static_assert(sizeof(BatchParams) <= 31 * 1024, "kernel parameter block too larg
 
 __global__ void __launch_bounds__(kThreads, 2)
 bp_batched_kernel(const __grid_constant__ BatchParams bpm, int *__restrict__ counter) {
-    extern __shared__ __align__(16) float2 tab[];
+    extern __shared__ __align__(16) float4 tab4[];  // [kStage][W] float4 (2 x 2-block tile) or float2 (pair tile)
+    float2 *tab = reinterpret_cast<float2 *>(tab4);
     __shared__ DirectStageSmem sm;
+    __shared__ QuadStageSmem qsm;
     __shared__ int item_s;
     for (;;) {
         __syncthreads();
@@ -52,6 +56,23 @@ bp_batched_kernel(const __grid_constant__ BatchParams bpm, int *__restrict__ cou
         const SliceDesc &d = bpm.d[lo];
         const int t = item - d.item0;
         const int ty = t / d.tiles1, tx = t - ty * d.tiles1;
+        if (d.quad) {
+            switch (d.dtype) {
+                case BP_F32:
+                    direct_tile_quad_sync<float>((const float *)d.sino, d.img, d.ap, d.N, d.n_det, 0, d.n_theta, d.W,
+                                                 d.C, tx, ty, 0, 0, 0.f, tab4, qsm);
+                    break;
+                case BP_BF16:
+                    direct_tile_quad_sync<__nv_bfloat16>((const __nv_bfloat16 *)d.sino, d.img, d.ap, d.N, d.n_det, 0,
+                                                         d.n_theta, d.W, d.C, tx, ty, 0, 0, 0.f, tab4, qsm);
+                    break;
+                default:
+                    direct_tile_quad_sync<__half>((const __half *)d.sino, d.img, d.ap, d.N, d.n_det, 0, d.n_theta,
+                                                  d.W, d.C, tx, ty, 0, 0, 0.f, tab4, qsm);
+                    break;
+            }
+            continue;
+        }
         switch (d.dtype) {
             case BP_F32:
                 direct_tile_sync<float>((const float *)d.sino, d.img, d.ap, d.N, d.n_det, 0, d.n_theta, d.W, d.C, tx,
@@ -98,8 +119,9 @@ bp_status launch_batched(bp_plan *const *plans, const void *const *sinos, const 
             d.dtype = (int)dtypes[base + i];
             d.tiles1 = (p->N + kTile - 1) / kTile;
             d.item0 = items;
+            d.quad = p->step_max <= 1.0f ? 1 : 0;
             items += d.tiles1 * d.tiles1;
-            Wmax = std::max(Wmax, p->W);
+            Wmax = std::max(Wmax, p->W * (d.quad ? 2 : 1));  // float4 entries count twice
         }
         bpm.n = cnt;
         bpm.items = items;

@@ -21,8 +21,9 @@
 // the raw windows of stage s+2 are fetched by TMA (one 3D box per angle, zero-filled off the
 // detector) into a double buffer while stage s computes; the (e, d) table is double
 // buffered too, so each stage has a single block barrier; coordinates and the magic-number
-// rounding of two pixels share one packed f32x2 instruction.  bp_direct_kernel is the plain
-// fallback (synchronous window loads) for other strides.
+// rounding of two pixels share one packed f32x2 instruction.  bp_direct_quad_sync_kernel and
+// bp_direct_kernel are the plain fallbacks (synchronous window loads) of the two forms for
+// other strides.
 #include <cudaTypedefs.h>
 
 #include <algorithm>
@@ -57,6 +58,23 @@ bp_direct_kernel(const Tin *__restrict__ sino, float *__restrict__ img, const An
     const int k_end = min(n_theta, group_stage(grp + 1, S, asplit) * kStage);
     direct_tile_sync<Tin>(sino + (long long)blockIdx.z * sino_stride, img + (long long)blockIdx.z * img_stride, ap,
                           N, n_det, k_begin, k_end, W, C, blockIdx.x, ty, accumulate, asplit > 1, wuni, tab, sm);
+}
+
+// Plain fallback of the 2 x 2-block form (synchronous window loads) for |c|, |s| <= 1.
+template <typename Tin>
+__global__ void __launch_bounds__(kThreads, 2)
+bp_direct_quad_sync_kernel(const Tin *__restrict__ sino, float *__restrict__ img, const AngleParam *__restrict__ ap,
+                           int N, int n_det, int n_theta, int W, int C, int accumulate, int tiles, int asplit,
+                           long long sino_stride, long long img_stride, float wuni) {
+    extern __shared__ __align__(16) float4 qtab[];  // [kStage][W]
+    __shared__ QuadStageSmem qsm;
+    const int ty = blockIdx.y % tiles, grp = blockIdx.y / tiles;
+    const int S = (n_theta + kStage - 1) / kStage;
+    const int k_begin = group_stage(grp, S, asplit) * kStage;
+    const int k_end = min(n_theta, group_stage(grp + 1, S, asplit) * kStage);
+    direct_tile_quad_sync<Tin>(sino + (long long)blockIdx.z * sino_stride, img + (long long)blockIdx.z * img_stride,
+                               ap, N, n_det, k_begin, k_end, W, C, blockIdx.x, ty, accumulate, asplit > 1, wuni, qtab,
+                               qsm);
 }
 
 template <typename T> __device__ __forceinline__ float smem_f(const unsigned char *p, int i);
@@ -201,26 +219,6 @@ bp_direct_tma_kernel(const __grid_constant__ CUtensorMap tmap, float *__restrict
     }
 }
 
-// Saturated add: min(max(a + b, 0), 1).
-__device__ __forceinline__ float add_sat(float a, float b) {
-    float d;
-    asm("add.sat.f32 %0, %1, %2;" : "=f"(d) : "f"(a), "f"(b));
-    return d;
-}
-
-// v[i] <- v[i ^ m] for the four corner roles of a block (bit 0: x flipped, bit 1: y flipped),
-// with compile-time indices only.
-__device__ __forceinline__ void xor_permute(float (&v)[4], int m) {
-    if (m & 1) {
-        float t = v[0]; v[0] = v[1]; v[1] = t;
-        t = v[2]; v[2] = v[3]; v[3] = t;
-    }
-    if (m & 2) {
-        float t = v[0]; v[0] = v[2]; v[2] = t;
-        t = v[1]; v[1] = v[3]; v[3] = t;
-    }
-}
-
 // Quad variant of the TMA kernel, used when |c|, |s| <= 1 (pixels no larger than detector
 // bins): a thread owns four 2 x 2 pixel blocks, and one float4 table entry serves all four
 // pixels of a block.  Over a 2 x 2 block the detector coordinate spans |c| + |s| <= 2 bins,
@@ -255,11 +253,8 @@ bp_direct_quad_kernel(const __grid_constant__ CUtensorMap tmap, float *__restric
 
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
-    // each group of 8 lanes covers 4 x 2 blocks (8 x 4 pixels): their table entries lie
-    // within 8 consecutive bins, so the 128-bit loads of a quarter warp are conflict-free
-    const int qtr = lane >> 3;
-    const int X0 = (lane & 3) + 4 * (qtr & 1);                  // block column (+ 8 a, a < 4)
-    const int Y0 = ((lane >> 2) & 1) + 2 * (qtr >> 1) + 4 * warp;  // block row
+    int X0, Y0;  // the thread's blocks (X0 + 8 a, Y0), a < 4
+    quad_thread_blocks(tid, X0, Y0);
     const int tx = blockIdx.x, ty = blockIdx.y % tiles, grp = blockIdx.y / tiles, bz = blockIdx.z;
     img += (long long)bz * img_stride;
     const uint32_t bar0 = smem_u32(&bars[0]);
@@ -284,29 +279,19 @@ bp_direct_quad_kernel(const __grid_constant__ CUtensorMap tmap, float *__restric
             bool far2 = true;
             if (act) {
                 const AngleParam p = ap[k0 + tid];
-                const long long U = p.U00 + (long long)tx * p.CT + (long long)ty * p.ST;
-                const int Ji = (int)(U >> 32);
-                const float frac = (float)(unsigned)(U & 0xffffffffLL) * 2.3283064365386963e-10f;
-                const float lo = fminf(p.c, 0.f) + fminf(p.s, 0.f);
-                const int J0 = Ji + (int)floorf((float)(kTile - 1) * lo) - 1;
-                const int J0r = J0 & ~7;
-                const float q0 = (float)(Ji - J0 - C) + frac + lo;
-                const unsigned base = tab_u32 + (unsigned)((b * STAGE + tid) * W) * 16u + 16u * (unsigned)C -
-                                      (kMagicBits << 4);
-                const float ac = fabsf(p.c), as = fabsf(p.s), af = ac + as;
-                role = (p.c < 0.f ? 1 : 0) | (p.s < 0.f ? 2 : 0);
-                far2 = af - 1.f >= 0.f;
-                sq[slot][tid] = make_float4(q0, p.c, p.s, __uint_as_float(base));
-                sr[slot][tid] = make_float4(ac, ac - 1.f, as, as - 1.f);
-                sf[slot][tid] = make_float4(af, af - 1.f, af - 2.f, __int_as_float(role));
-                sof[slot][tid] = J0 - J0r;
+                const QuadAngle o = quad_angle(p, tx, ty, C, tab_u32 + (unsigned)((b * STAGE + tid) * W) * 16u);
+                const int J0r = o.J0 & ~7;
+                sq[slot][tid] = o.sq;
+                sr[slot][tid] = o.sr;
+                sf[slot][tid] = o.sf;
+                sof[slot][tid] = o.J0 - J0r;
                 sw[slot][tid] = wuni > 0.f ? wuni : p.w;
+                role = o.role;
+                far2 = o.far2;
                 tma_load_3d(smem_u32(raw + (b * STAGE + tid) * RS), &tmap, J0r, k0 + tid, bz, bar0 + 8 * b);
             }
-            const int r0 = __shfl_sync(0xffffffffu, role, 0);
-            const bool same = __all_sync(0xffffffffu, !act || role == r0);
-            const bool all2 = __all_sync(0xffffffffu, far2);
-            if (tid == 0) su[slot] = same ? (r0 | 4 | (all2 ? 8 : 0)) : 0;
+            const int u = quad_uniform(act, role, far2);
+            if (tid == 0) su[slot] = u;
         }
     };
 
@@ -321,7 +306,6 @@ bp_direct_quad_kernel(const __grid_constant__ CUtensorMap tmap, float *__restric
     }
     int role = 0;
     const float fx = (float)(2 * X0), fy = (float)(2 * Y0);
-    const unsigned long long MM = pk2(kMagic, kMagic);
     // table build: TPA threads per angle, each a run of consecutive entries (bins reused)
     const int run = (W + TPA - 1) / TPA;
 
@@ -363,95 +347,10 @@ bp_direct_quad_kernel(const __grid_constant__ CUtensorMap tmap, float *__restric
             if (tid < STAGE) fence_proxy_async_smem();
             prepare(i + 2);
         }
-        // one angle: CHECK = per-angle role check, FAR = 0 per-angle far-corner test, 1 two ramps,
-        // 2 three ramps
-        auto angle = [&](int kk, auto check_tag, auto far_tag) {
-            constexpr bool CHECK = decltype(check_tag)::value;
-            constexpr int FAR = decltype(far_tag)::value;
-            const float4 A = sq[slot][kk];
-            const float4 R2 = sr[slot][kk];
-            const float4 F = sf[slot][kk];
-            if (CHECK) {
-                const int rl = __float_as_int(F.w);
-                if (rl != role) {
-                    // the corner roles follow the signs of (c, s): move each pixel's sum to its new role
-#pragma unroll
-                    for (int a = 0; a < 4; ++a) xor_permute(acc[a], rl ^ role);
-                    role = rl;
-                }
-            }
-            const float qt = fmaf(fy, A.z, fmaf(fx, A.y, A.x));
-            const unsigned long long Q = pk2(qt, fmaf(16.f, A.y, qt));
-            const unsigned long long CC = pk2(A.y, A.y);
-            const unsigned base = __float_as_uint(A.w);
-            // far corner: with |c| + |s| >= 1 its lowest ramp is always 1 (two ramps suffice)
-            const bool far2 = FAR == 1 || (FAR == 0 && F.y >= 0.f);
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const unsigned long long qa = h ? ffma2(pk2(32.f, 32.f), CC, Q) : Q;  // blocks 2h, 2h + 1
-                const unsigned long long Rf = fadd2_rm(qa, MM);                      // magic + floor(q)
-                const unsigned long long RB = fsub2(qa, fsub2(Rf, MM));              // r = q - floor(q)
-                float v0, v1, rb[2];
-                upk2(Rf, v0, v1);
-                upk2(RB, rb[0], rb[1]);
-                float4 T[2];
-                T[0] = lds128(base + (__float_as_uint(v0) << 4));
-                T[1] = lds128(base + (__float_as_uint(v1) << 4));
-#pragma unroll
-                for (int e = 0; e < 2; ++e) {
-                    float(&q)[4] = acc[2 * h + e];
-                    const float r = rb[e];
-                    const float4 t = T[e];  // w g_j, w dg_j, w dg_{j+1}, w dg_{j+2}
-                    G[2 * h + e] += t.x;
-                    q[0] = fmaf(t.y, r, q[0]);
-                    q[1] = fmaf(t.z, add_sat(r, R2.y), fmaf(t.y, add_sat(r, R2.x), q[1]));
-                    q[2] = fmaf(t.z, add_sat(r, R2.w), fmaf(t.y, add_sat(r, R2.z), q[2]));
-                    if (far2)
-                        q[3] = fmaf(t.w, add_sat(r, F.z), fmaf(t.z, add_sat(r, F.y), q[3] + t.y));
-                    else
-                        q[3] = fmaf(t.w, add_sat(r, F.z),
-                                    fmaf(t.z, add_sat(r, F.y), fmaf(t.y, add_sat(r, F.x), q[3])));
-                }
-            }
-        };
-        using True_ = std::integral_constant<bool, true>;
-        using False_ = std::integral_constant<bool, false>;
-        const int u = su[slot];
-        if (u & 4) {
-            // every angle of the stage has the same corner roles: exchange once, no checks
-            const int rl = u & 3;
-            if (rl != role) {
-#pragma unroll
-                for (int a = 0; a < 4; ++a) xor_permute(acc[a], rl ^ role);
-                role = rl;
-            }
-            if (u & 8) {
-                for (int kk = 0; kk < kn; ++kk) angle(kk, False_(), std::integral_constant<int, 1>());
-            } else {
-                for (int kk = 0; kk < kn; ++kk) angle(kk, False_(), std::integral_constant<int, 2>());
-            }
-        } else {
-            for (int kk = 0; kk < kn; ++kk) angle(kk, True_(), std::integral_constant<int, 0>());
-        }
+        quad_stage(acc, G, role, sq[slot], sr[slot], sf[slot], su[slot], kn, fx, fy);
     }
     if (!ok && lane == 0) atomicExch(err, 1);
-
-    // position px + 2 py of a block has role (px + 2 py) ^ role: back to position order
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-        xor_permute(acc[a], role);
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const int x = tx * kTile + 2 * X0 + 16 * a + (r & 1);
-            const int y = ty * kTile + 2 * Y0 + (r >> 1);
-            if (x < N && y < N) {
-                float *dst = img + (long long)y * N + x;
-                const float val = acc[a][r] + G[a];
-                if (asplit > 1) atomicAdd(dst, val);
-                else *dst = accumulate ? (*dst + val) : val;
-            }
-        }
-    }
+    quad_write(acc, G, role, img, N, tx, ty, X0, Y0, accumulate, asplit > 1);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
@@ -590,6 +489,17 @@ bp_status launch_direct_t(bp_plan *p, const Tin *sino, float *img, int batch, in
             case 32: return launch_tma<Tin, 32>(p, map, img, batch, accumulate, asplit, st, wuni);
             default: return launch_tma<Tin, 16>(p, map, img, batch, accumulate, asplit, st, wuni);
         }
+    }
+    if (p->step_max <= 1.0f && sizeof(float4) * (size_t)kStage * p->W <= kMaxDirectSmem) {
+        const size_t qsmem = sizeof(float4) * (size_t)kStage * p->W;
+        auto qk = bp_direct_quad_sync_kernel<Tin>;
+        BP_CUDA_TRY(cudaFuncSetAttribute(qk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qsmem));
+        dim3 grid(tiles, tiles * asplit, batch);
+        qk<<<grid, kThreads, qsmem, st>>>(sino, img, p->d_ang, p->N, p->n_det, p->n_theta, p->W, p->C, accumulate,
+                                          tiles, asplit, (long long)p->n_theta * p->n_det, (long long)p->N * p->N,
+                                          wuni);
+        BP_CUDA_TRY(cudaGetLastError());
+        return BP_OK;
     }
     const size_t smem = sizeof(float2) * (size_t)kStage * p->W;
     if (smem > kMaxDirectSmem) return fail(BP_ERR_UNSUPPORTED, "direct R*: window too large for shared memory");

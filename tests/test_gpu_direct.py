@@ -243,8 +243,9 @@ def test_batched_mixed_geometries_match_single_calls():
         sinos.append(to_dev(rng.normal(size=(nt, nd)), dt))
     imgs = bp.backproject_batched(plans, sinos)
     for p, s, img, (N, nd, nt, sc, dt) in zip(plans, sinos, imgs, specs):
-        # the persistent batched kernel interpolates pixel by pixel; single calls take the
-        # 2 x 2-block kernel where |c|, |s| <= 1: two FP32 roundings of the same sum
+        # the persistent batched kernel's synchronous tiles and the single calls' TMA kernels
+        # compute the same sum with different FP32 roundings (and, where the stride rules
+        # differ, in different forms: 2 x 2-block or pair table)
         single = p.backproject(s)
         assert oracle.rel_l2(img.cpu().numpy(), single.cpu().numpy()) <= TOL_DIRECT
         ref = oracle.bp_linear(rounded(s), N, p.theta, p.det_spacing)
