@@ -30,7 +30,7 @@ FP32_LANES_PER_SM = 128       # FP32 FMA lanes per SM
 L2_FLUSH_BYTES = 256 << 20    # > 129 MB L2
 # shared-memory wavefront caps (128 B/clk/SM): the pair-table kernel reads 8 B per update,
 # the 2 x 2-block kernel one 16-byte entry per 4 updates
-SMEM_UPDATES_PER_CLK = {"bp_direct_tma_kernel": 16, "bp_direct_quad_kernel": 32}
+SMEM_UPDATES_PER_CLK = {"bp_direct_tma_kernel": 16, "bp_direct_quad_sync_kernel": 32}
 
 
 def _peaks():
@@ -560,7 +560,7 @@ def run_gpu(args, world, rank, local):
     # the library takes the 2 x 2-block kernel when every pixel step |c|, |s| = |cos|, |sin| dx/dt <= 1
     ratio = (2.0 / wl.N) / wl.det_spacing
     steps = np.abs(np.stack([np.cos(wl.theta), np.sin(wl.theta)])) * ratio
-    kernel = "bp_direct_quad_kernel" if float(np.max(steps.astype(np.float32))) <= 1.0 else "bp_direct_tma_kernel"
+    kernel = "bp_direct_quad_sync_kernel" if float(np.max(steps.astype(np.float32))) <= 1.0 else "bp_direct_tma_kernel"
     smem_cap = SMEM_UPDATES_PER_CLK[kernel] * props.multi_processor_count * sm_max_mhz * 1e6
     line = {
         "metric": "backprojection G pixel·angle updates/s at 2048²×1800; % of roofline",
@@ -585,7 +585,7 @@ def run_gpu(args, world, rank, local):
                      "kernel_ms": bp_avg_s * 1e3, "filter_ms": statistics.mean(filt_ms),
                      "smem_limit": {
                          "resource": "shared-memory wavefronts, 1/clk/SM (" + (
-                             "one 16-byte table entry per 2 x 2 pixel block" if kernel == "bp_direct_quad_kernel"
+                             "one 16-byte table entry per 2 x 2 pixel block" if kernel == "bp_direct_quad_sync_kernel"
                              else "one 8-byte table pair per update") + ")",
                          "cap_Gupdates_s": smem_cap / 1e9,
                          "frac": wl.updates / bp_avg_s / smem_cap},

@@ -33,12 +33,12 @@ struct BatchParams {
 };
 static_assert(sizeof(BatchParams) <= 31 * 1024, "kernel parameter block too large");
 
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, 4)
 bp_batched_kernel(const __grid_constant__ BatchParams bpm, int *__restrict__ counter) {
     extern __shared__ __align__(16) float4 tab4[];  // [kStage][W] float4 (2 x 2-block tile) or float2 (pair tile)
     float2 *tab = reinterpret_cast<float2 *>(tab4);
     __shared__ DirectStageSmem sm;
-    __shared__ QuadStageSmem qsm;
+    __shared__ QuadStageSmem<> qsm;
     __shared__ int item_s;
     for (;;) {
         __syncthreads();

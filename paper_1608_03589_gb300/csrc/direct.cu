@@ -4,26 +4,38 @@
 // j = floor(u), f = u - j, zero outside the detector.
 //
 // Design (GB300): a CTA owns a 64 x 64 pixel tile (16 pixels per thread) and walks the
-// angles in stages of kStage.  For each (tile, angle) it stages the W detector bins the
-// tile can touch into shared memory, pre-weighted and pre-differenced as pairs
+// angles in stages.  For each (tile, angle) it stages the W detector bins the tile can touch
+// into shared memory as a pre-weighted table, in one of two forms.
+//
+// 2 x 2-block form (bp_direct_quad_sync_kernel; pixels no larger than detector bins, i.e.
+// |c|, |s| <= 1, every benchmark workload): a thread owns four 2 x 2 pixel blocks; over a
+// block u spans |c| + |s| <= 2 bins, so with j = floor(u at the block's lowest corner) and
+// r = u - j the four pixels need only g_j .. g_{j+3}, and the linear interpolant is exactly
+// the sum of clamped ramps
+//     w g(u) = w g_j + sum_{i=0..2} w (g_{j+i+1} - g_{j+i}) sat(r - i),   sat = clamp to [0, 1]
+// (ramps above r vanish, those below are 1).  One 16-byte entry (w g_j, w dg_j, w dg_{j+1},
+// w dg_{j+2}) serves all four pixels of a block; the common w g_j is summed once per block;
+// the lowest corner needs one FFMA, the side corners two ramps, the far corner two or three
+// (FADD.SAT clamps).  j comes from a paired add rounded toward minus infinity of the magic
+// constant 1.5 * 2^23, whose bits index shared memory.  The corner roles follow the signs of
+// (c, s): the accumulators are kept per role and exchanged when the signs change; stages
+// whose angles share the signs skip the per-angle tests.  The table is built from global
+// memory each stage (the single float4 table takes 24 KB, so four CTAs share an SM and
+// cover the loads' latency); the stage arithmetic lives in direct_tile.cuh.
+//
+// Pair form (other geometries): entries
 //     d_m = w_k (g_{J0+m+1} - g_{J0+m}),   e_m = w_k g_{J0+m} + (1/2 - (m - C)) d_m,
 // so that with the tile-local, half-bin-shifted coordinate q = u - J0 - C - 1/2 the
-// interpolated, weighted sample is the single FMA  e_m + q d_m  with m - C = rint(q).
-// rint(q) comes from the float "magic number" rounding (q + 1.5 * 2^23 keeps the integer
-// in its low mantissa bits), whose bit pattern indexes shared memory directly.  Per
-// pixel-angle update: FFMA (coordinate), FADD (rounding), LEA (address), LDS.64, FFMA,
-// FADD.  The per-tile window origin J0 and base coordinate come from exact 32.32 fixed-
-// point tile stepping, so float32 only ever holds tile-local coordinates (|q| <= W/2).
+// interpolated, weighted sample is the single FMA  e_m + q d_m  with m - C = rint(q)
+// (magic-number rounding again).  bp_direct_tma_kernel (16-byte strided rows): the raw
+// windows of stage s+2 are fetched by TMA (one 3D box per angle, zero-filled off the
+// detector) into a double buffer while stage s computes; the (e, d) table is double buffered
+// too, so each stage has a single block barrier; coordinates and the rounding of two pixels
+// share one packed f32x2 instruction.  bp_direct_kernel: synchronous window loads for other
+// strides.
 //
-// Three variants.  bp_direct_quad_kernel (pixels no larger than detector bins, 16-byte strided
-// rows): the TMA pipeline below with a 2 x 2-block table, described at the kernel.
-// bp_direct_tma_kernel (other geometries with 16-byte strided rows):
-// the raw windows of stage s+2 are fetched by TMA (one 3D box per angle, zero-filled off the
-// detector) into a double buffer while stage s computes; the (e, d) table is double
-// buffered too, so each stage has a single block barrier; coordinates and the magic-number
-// rounding of two pixels share one packed f32x2 instruction.  bp_direct_quad_sync_kernel and
-// bp_direct_kernel are the plain fallbacks (synchronous window loads) of the two forms for
-// other strides.
+// In both forms the per-tile window origin J0 and base coordinate come from exact 32.32
+// fixed-point tile stepping, so float32 only ever holds tile-local coordinates (|q| <= W/2).
 #include <cudaTypedefs.h>
 
 #include <algorithm>
@@ -60,21 +72,22 @@ bp_direct_kernel(const Tin *__restrict__ sino, float *__restrict__ img, const An
                           N, n_det, k_begin, k_end, W, C, blockIdx.x, ty, accumulate, asplit > 1, wuni, tab, sm);
 }
 
-// Plain fallback of the 2 x 2-block form (synchronous window loads) for |c|, |s| <= 1.
-template <typename Tin>
-__global__ void __launch_bounds__(kThreads, 2)
+// The 2 x 2-block form with synchronous window loads (|c|, |s| <= 1): STAGE angles per stage,
+// MINB CTAs per SM.
+template <typename Tin, int STAGE, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB)
 bp_direct_quad_sync_kernel(const Tin *__restrict__ sino, float *__restrict__ img, const AngleParam *__restrict__ ap,
                            int N, int n_det, int n_theta, int W, int C, int accumulate, int tiles, int asplit,
                            long long sino_stride, long long img_stride, float wuni) {
-    extern __shared__ __align__(16) float4 qtab[];  // [kStage][W]
-    __shared__ QuadStageSmem qsm;
+    extern __shared__ __align__(16) float4 qtab[];  // [STAGE][W]
+    __shared__ QuadStageSmem<STAGE> qsm;
     const int ty = blockIdx.y % tiles, grp = blockIdx.y / tiles;
-    const int S = (n_theta + kStage - 1) / kStage;
-    const int k_begin = group_stage(grp, S, asplit) * kStage;
-    const int k_end = min(n_theta, group_stage(grp + 1, S, asplit) * kStage);
-    direct_tile_quad_sync<Tin>(sino + (long long)blockIdx.z * sino_stride, img + (long long)blockIdx.z * img_stride,
-                               ap, N, n_det, k_begin, k_end, W, C, blockIdx.x, ty, accumulate, asplit > 1, wuni, qtab,
-                               qsm);
+    const int S = (n_theta + STAGE - 1) / STAGE;
+    const int k_begin = group_stage(grp, S, asplit) * STAGE;
+    const int k_end = min(n_theta, group_stage(grp + 1, S, asplit) * STAGE);
+    direct_tile_quad_sync<Tin, STAGE>(sino + (long long)blockIdx.z * sino_stride,
+                                      img + (long long)blockIdx.z * img_stride, ap, N, n_det, k_begin, k_end, W, C,
+                                      blockIdx.x, ty, accumulate, asplit > 1, wuni, qtab, qsm);
 }
 
 template <typename T> __device__ __forceinline__ float smem_f(const unsigned char *p, int i);
@@ -219,140 +232,6 @@ bp_direct_tma_kernel(const __grid_constant__ CUtensorMap tmap, float *__restrict
     }
 }
 
-// Quad variant of the TMA kernel, used when |c|, |s| <= 1 (pixels no larger than detector
-// bins): a thread owns four 2 x 2 pixel blocks, and one float4 table entry serves all four
-// pixels of a block.  Over a 2 x 2 block the detector coordinate spans |c| + |s| <= 2 bins,
-// so with j = floor(u at the block's lowest corner) and r = u - j the four pixels need only
-// g_j .. g_{j+3}, and the linear interpolant is exactly the sum of clamped ramps
-//     w g(u) = w g_j + sum_{i=0..2} w (g_{j+i+1} - g_{j+i}) sat(r - i),   sat = clamp to [0, 1]
-// (ramps above r vanish, those below are 1).  The entry (w g_j, w dg_j, w dg_{j+1}, w dg_{j+2})
-// is one 16-byte load per block instead of one 8-byte load per pixel, which halves the
-// shared-memory traffic that bounds the pair-table kernel; the common term w g_j goes into
-// one accumulator per block.  The lowest corner has r in [0, 1] (one FFMA), the two side
-// corners r + |c|, r + |s| <= 2 (two ramps), the far corner r + |c| + |s| (three ramps, two
-// when |c| + |s| >= 1); the clamps are FADD.SAT.  j comes from the magic-number floor (paired
-// add rounded toward minus infinity) whose bits index shared memory.  Which pixel of a block
-// is its lowest corner depends on the signs of (c, s): the accumulators are kept per role and
-// exchanged when the signs change between angles.
-template <typename Tin, int STAGE>
-__global__ void __launch_bounds__(kThreads, 3)
-bp_direct_quad_kernel(const __grid_constant__ CUtensorMap tmap, float *__restrict__ img,
-                      const AngleParam *__restrict__ ap, int N, int n_theta, int W, int C, int Wb, int RS,
-                      int accumulate, int tiles, int asplit, long long img_stride, int *__restrict__ err, float wuni) {
-    constexpr int TPA = kThreads / STAGE;
-    extern __shared__ __align__(128) unsigned char dsm[];
-    unsigned char *raw = dsm;                                           // [2][STAGE] rows of RS bytes
-    float4 *tab = reinterpret_cast<float4 *>(dsm + 2 * STAGE * RS);    // [2][STAGE][W]
-    __shared__ float4 sq[3][STAGE];   // q at the lowest corner of block (0,0), c, s, table base bits
-    __shared__ float4 sr[3][STAGE];   // |c|, |c| - 1, |s|, |s| - 1: ramp offsets of the side corners
-    __shared__ float4 sf[3][STAGE];   // |c| + |s| - {0, 1, 2}: far corner; corner-role bits
-    __shared__ int sof[3][STAGE];     // J0 - J0r (TMA box starts at the 8-aligned J0r)
-    __shared__ float sw[3][STAGE];
-    __shared__ int su[3];             // stage-uniform corner roles: role | 4, plus 8 if every far corner has two ramps
-    __shared__ __align__(8) unsigned long long bars[2];
-
-    const int tid = threadIdx.x;
-    const int lane = tid & 31, warp = tid >> 5;
-    int X0, Y0;  // the thread's blocks (X0 + 8 a, Y0), a < 4
-    quad_thread_blocks(tid, X0, Y0);
-    const int tx = blockIdx.x, ty = blockIdx.y % tiles, grp = blockIdx.y / tiles, bz = blockIdx.z;
-    img += (long long)bz * img_stride;
-    const uint32_t bar0 = smem_u32(&bars[0]);
-    const unsigned tab_u32 = smem_u32(tab);
-    const int S_all = (n_theta + STAGE - 1) / STAGE;
-    const int s0 = group_stage(grp, S_all, asplit);
-    const int S = group_stage(grp + 1, S_all, asplit) - s0;
-
-    if (tid == 0) {
-        mbar_init(bar0, 1);
-        mbar_init(bar0 + 8, 1);
-        mbar_fence_init();
-    }
-    __syncthreads();
-
-    auto prepare = [&](int i) {
-        const int k0 = (s0 + i) * STAGE, kn = min(STAGE, n_theta - k0), b = i & 1, slot = i % 3;
-        if (tid == 0) mbar_expect_tx(bar0 + 8 * b, (uint32_t)(kn * Wb * (int)sizeof(Tin)));
-        if (warp == 0) {  // the stage's angles are lanes < kn <= 32 of warp 0
-            const bool act = tid < kn;
-            int role = 0;
-            bool far2 = true;
-            if (act) {
-                const AngleParam p = ap[k0 + tid];
-                const QuadAngle o = quad_angle(p, tx, ty, C, tab_u32 + (unsigned)((b * STAGE + tid) * W) * 16u);
-                const int J0r = o.J0 & ~7;
-                sq[slot][tid] = o.sq;
-                sr[slot][tid] = o.sr;
-                sf[slot][tid] = o.sf;
-                sof[slot][tid] = o.J0 - J0r;
-                sw[slot][tid] = wuni > 0.f ? wuni : p.w;
-                role = o.role;
-                far2 = o.far2;
-                tma_load_3d(smem_u32(raw + (b * STAGE + tid) * RS), &tmap, J0r, k0 + tid, bz, bar0 + 8 * b);
-            }
-            const int u = quad_uniform(act, role, far2);
-            if (tid == 0) su[slot] = u;
-        }
-    };
-
-    // per block: the four corner sums in role order (lowest, side x, side y, far) and the
-    // common term sum_k w g_j
-    float acc[4][4], G[4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-        G[a] = 0.f;
-#pragma unroll
-        for (int r = 0; r < 4; ++r) acc[a][r] = 0.f;
-    }
-    int role = 0;
-    const float fx = (float)(2 * X0), fy = (float)(2 * Y0);
-    // table build: TPA threads per angle, each a run of consecutive entries (bins reused)
-    const int run = (W + TPA - 1) / TPA;
-
-    prepare(0);
-    if (S > 1) prepare(1);
-    __syncthreads();
-    bool ok = true;
-    for (int i = 0; i < S; ++i) {
-        const int b = i & 1, slot = i % 3;
-        const int kn = min(STAGE, n_theta - (s0 + i) * STAGE);
-        ok &= mbar_wait(bar0 + 8 * b, (uint32_t)((i >> 1) & 1));
-        {
-            const int kk = tid / TPA, r = tid % TPA;
-            if (kk < kn) {
-                const unsigned char *row = raw + (b * STAGE + kk) * RS;
-                const int off = sof[slot][kk];
-                const float w = sw[slot][kk];
-                float4 *dst = tab + (b * STAGE + kk) * W;
-                const int m0 = r * run, m1 = min(W, m0 + run);
-                if (m0 < m1) {
-                    float g0 = smem_f<Tin>(row, off + m0), g1 = smem_f<Tin>(row, off + m0 + 1);
-                    float g2 = smem_f<Tin>(row, off + m0 + 2);
-                    float d0 = w * (g1 - g0), d1 = w * (g2 - g1);
-                    for (int m = m0; m < m1; ++m) {
-                        const float g3 = smem_f<Tin>(row, off + m + 3);
-                        const float d2 = w * (g3 - g2);
-                        dst[m] = make_float4(w * g0, d0, d1, d2);
-                        g0 = g1;
-                        g1 = g2;
-                        g2 = g3;
-                        d0 = d1;
-                        d1 = d2;
-                    }
-                }
-            }
-        }
-        __syncthreads();
-        if (i + 2 < S) {
-            if (tid < STAGE) fence_proxy_async_smem();
-            prepare(i + 2);
-        }
-        quad_stage(acc, G, role, sq[slot], sr[slot], sf[slot], su[slot], kn, fx, fy);
-    }
-    if (!ok && lane == 0) atomicExch(err, 1);
-    quad_write(acc, G, role, img, N, tx, ty, X0, Y0, accumulate, asplit > 1);
-}
-
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     static std::once_flag once;
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -384,28 +263,18 @@ bool tma_eligible(const bp_plan *p, int esz) {
     return ((long long)p->n_det * esz) % 16 == 0 && Wb <= 256;
 }
 
-// Quad kernel: raw box of W + 3 bins after the up-to-7-bin alignment offset, and its shared
-// memory (raw double buffer + float4 table double buffer).
-int quad_box(const bp_plan *p) { return (p->W + 10 + 7) & ~7; }
-
-size_t quad_smem(const bp_plan *p, int stage, int esz) {
-    const size_t RS = ((size_t)quad_box(p) * esz + 127) & ~(size_t)127;
-    return 2 * (size_t)stage * RS + 2 * sizeof(float4) * (size_t)stage * p->W;
+// The 2 x 2-block form needs |c|, |s| <= 1 (a block spans at most g_j .. g_{j+3}) and its
+// float4 table of kStage x W entries in shared memory.
+bool quad_form(const bp_plan *p) {
+    return p->step_max <= 1.0f && sizeof(float4) * (size_t)kStage * p->W <= kMaxDirectSmem;
 }
-
-// The quad kernel needs |c|, |s| <= 1 (a 2 x 2 block spans at most g_j .. g_{j+3}).
-bool quad_eligible(const bp_plan *p, int esz, int stage) {
-    return p->step_max <= 1.0f && ((long long)p->n_det * esz) % 16 == 0 && quad_box(p) <= 256 &&
-           quad_smem(p, stage, esz) <= kMaxDirectSmem;
-}
-
 
 // The shape a direct launch really uses: on the TMA path the stage is lowered until its
 // shared memory fits; the synchronous path always stages kStage angles; groups are clamped.
 DirectShape direct_effective(const bp_plan *p, int esz, bool tma, DirectShape shape) {
     DirectShape e;
     e.stage = kStage;
-    if (tma) {
+    if (tma && !quad_form(p)) {
         e.stage = (shape.stage == 8 || shape.stage == 32) ? shape.stage : kStage;
         while (e.stage > 8 && tma_smem(p, e.stage, esz) > kMaxDirectSmem) e.stage >>= 1;
         if (tma_smem(p, e.stage, esz) > kMaxDirectSmem) e.stage = kStage;
@@ -423,23 +292,6 @@ bp_status launch_tma(bp_plan *p, const CUtensorMap &map, float *img, int batch, 
     const int RS = (Wb * esz + 127) & ~127;
     const size_t smem = tma_smem(p, STAGE, esz);
     auto kern = bp_direct_tma_kernel<Tin, STAGE>;
-    BP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    dim3 grid(tiles, tiles * asplit, batch);
-    kern<<<grid, kThreads, smem, st>>>(map, img, p->d_ang, p->N, p->n_theta, p->W, p->C, Wb, RS, accumulate, tiles,
-                                       asplit, (long long)p->N * p->N, p->d_err, wuni);
-    BP_CUDA_TRY(cudaGetLastError());
-    return BP_OK;
-}
-
-template <typename Tin, int STAGE>
-bp_status launch_quad(bp_plan *p, const CUtensorMap &map, float *img, int batch, int accumulate, int asplit,
-                      cudaStream_t st, float wuni) {
-    const int tiles = (p->N + kTile - 1) / kTile;
-    const int esz = (int)sizeof(Tin);
-    const int Wb = quad_box(p);
-    const int RS = (Wb * esz + 127) & ~127;
-    const size_t smem = quad_smem(p, STAGE, esz);
-    auto kern = bp_direct_quad_kernel<Tin, STAGE>;
     BP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 grid(tiles, tiles * asplit, batch);
     kern<<<grid, kThreads, smem, st>>>(map, img, p->d_ang, p->N, p->n_theta, p->W, p->C, Wb, RS, accumulate, tiles,
@@ -468,21 +320,25 @@ bp_status launch_direct_t(bp_plan *p, const Tin *sino, float *img, int batch, in
     const int tiles = (p->N + kTile - 1) / kTile;
     const int esz = (int)sizeof(Tin);
     const bool have_enc = tensor_map_encoder() != nullptr;
-    const DirectShape eff = direct_effective(p, esz, have_enc && tma_eligible(p, esz), shape);
+    const bool quad = quad_form(p);
+    const DirectShape eff = direct_effective(p, esz, !quad && have_enc && tma_eligible(p, esz), shape);
     const int stage = eff.stage, asplit = eff.asplit;
-    CUtensorMap map;
-    const bool quad = have_enc && quad_eligible(p, esz, stage) && encode_rows(p, sino, batch, quad_box(p), &map);
-    const bool tma = !quad && have_enc && tma_eligible(p, esz) && tma_smem(p, stage, esz) <= kMaxDirectSmem &&
-                     encode_rows(p, sino, batch, (p->W + 8 + 7) & ~7, &map);
     if (asplit > 1 && !accumulate)
         BP_CUDA_TRY(cudaMemsetAsync(img, 0, sizeof(float) * (size_t)p->N * p->N * batch, st));
+    dim3 grid(tiles, tiles * asplit, batch);
     if (quad) {
-        switch (stage) {
-            case 8: return launch_quad<Tin, 8>(p, map, img, batch, accumulate, asplit, st, wuni);
-            case 32: return launch_quad<Tin, 32>(p, map, img, batch, accumulate, asplit, st, wuni);
-            default: return launch_quad<Tin, 16>(p, map, img, batch, accumulate, asplit, st, wuni);
-        }
+        const size_t qsmem = sizeof(float4) * (size_t)kStage * p->W;
+        auto qk = bp_direct_quad_sync_kernel<Tin, kStage, 4>;
+        BP_CUDA_TRY(cudaFuncSetAttribute(qk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qsmem));
+        qk<<<grid, kThreads, qsmem, st>>>(sino, img, p->d_ang, p->N, p->n_det, p->n_theta, p->W, p->C, accumulate,
+                                          tiles, asplit, (long long)p->n_theta * p->n_det, (long long)p->N * p->N,
+                                          wuni);
+        BP_CUDA_TRY(cudaGetLastError());
+        return BP_OK;
     }
+    CUtensorMap map;
+    const bool tma = have_enc && tma_eligible(p, esz) && tma_smem(p, stage, esz) <= kMaxDirectSmem &&
+                     encode_rows(p, sino, batch, (p->W + 8 + 7) & ~7, &map);
     if (tma) {
         switch (stage) {
             case 8: return launch_tma<Tin, 8>(p, map, img, batch, accumulate, asplit, st, wuni);
@@ -490,22 +346,10 @@ bp_status launch_direct_t(bp_plan *p, const Tin *sino, float *img, int batch, in
             default: return launch_tma<Tin, 16>(p, map, img, batch, accumulate, asplit, st, wuni);
         }
     }
-    if (p->step_max <= 1.0f && sizeof(float4) * (size_t)kStage * p->W <= kMaxDirectSmem) {
-        const size_t qsmem = sizeof(float4) * (size_t)kStage * p->W;
-        auto qk = bp_direct_quad_sync_kernel<Tin>;
-        BP_CUDA_TRY(cudaFuncSetAttribute(qk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qsmem));
-        dim3 grid(tiles, tiles * asplit, batch);
-        qk<<<grid, kThreads, qsmem, st>>>(sino, img, p->d_ang, p->N, p->n_det, p->n_theta, p->W, p->C, accumulate,
-                                          tiles, asplit, (long long)p->n_theta * p->n_det, (long long)p->N * p->N,
-                                          wuni);
-        BP_CUDA_TRY(cudaGetLastError());
-        return BP_OK;
-    }
     const size_t smem = sizeof(float2) * (size_t)kStage * p->W;
     if (smem > kMaxDirectSmem) return fail(BP_ERR_UNSUPPORTED, "direct R*: window too large for shared memory");
     auto kern = bp_direct_kernel<Tin>;
     BP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    dim3 grid(tiles, tiles * asplit, batch);
     kern<<<grid, kThreads, smem, st>>>(sino, img, p->d_ang, p->N, p->n_det, p->n_theta, p->W, p->C, accumulate,
                                        tiles, asplit, (long long)p->n_theta * p->n_det, (long long)p->N * p->N,
                                        wuni);

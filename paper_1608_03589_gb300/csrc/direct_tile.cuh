@@ -273,23 +273,24 @@ __device__ __forceinline__ void quad_write(float (&acc)[4][4], const float (&G)[
     }
 }
 
+template <int STAGE = kStage>
 struct QuadStageSmem {
-    float4 sq[kStage], sr[kStage], sf[kStage];
-    int J0[kStage];
-    float w[kStage];
+    float4 sq[STAGE], sr[STAGE], sf[STAGE];
+    int J0[STAGE];
+    float w[STAGE];
     int u;
 };
 
 // 2 x 2-block form of direct_tile_sync (|c|, |s| <= 1): angles [k_begin, k_end) of tile
-// (tx, ty) in stages of kStage; each stage's float4 table (w g_j, w dg_j, w dg_{j+1},
-// w dg_{j+2}) is built from global memory by 16 threads per angle, each a run of entries.
-// tab: kStage * W float4 of shared memory.  All threads of the block must call it.
-template <typename Tin>
+// (tx, ty) in stages of STAGE; each stage's float4 table (w g_j, w dg_j, w dg_{j+1},
+// w dg_{j+2}) is built from global memory by kThreads / STAGE threads per angle, each a run of
+// entries.  tab: STAGE * W float4 of shared memory.  All threads of the block must call it.
+template <typename Tin, int STAGE = kStage>
 __device__ __forceinline__ void direct_tile_quad_sync(const Tin *__restrict__ sino, float *__restrict__ img,
                                                       const AngleParam *__restrict__ ap, int N, int n_det,
                                                       int k_begin, int k_end, int W, int C, int tx, int ty,
                                                       int accumulate, int atomic_out, float wuni, float4 *tab,
-                                                      QuadStageSmem &sm) {
+                                                      QuadStageSmem<STAGE> &sm) {
     const int tid = threadIdx.x, warp = tid >> 5;
     int X0, Y0;
     quad_thread_blocks(tid, X0, Y0);
@@ -303,10 +304,10 @@ __device__ __forceinline__ void direct_tile_quad_sync(const Tin *__restrict__ si
     int role = 0;
     const float fx = (float)(2 * X0), fy = (float)(2 * Y0);
     const unsigned tab_u32 = smem_u32(tab);
-    constexpr int TPA = kThreads / kStage;
+    constexpr int TPA = kThreads / STAGE;
     const int run = (W + TPA - 1) / TPA;
-    for (int k0 = k_begin; k0 < k_end; k0 += kStage) {
-        const int kn = min(kStage, k_end - k0);
+    for (int k0 = k_begin; k0 < k_end; k0 += STAGE) {
+        const int kn = min(STAGE, k_end - k0);
         __syncthreads();  // the previous stage's table and parameters are no longer read
         if (warp == 0) {
             const bool act = tid < kn;
