@@ -63,17 +63,18 @@ radon_direct_kernel(const float *__restrict__ img, float *__restrict__ sino, con
     if (tid == 0) {
         // one lane spacing for all angles of the block when they share a dominant axis
         int xd = -1, S = 0;
+        bool mixed = false;  // once two axes are seen, the block stays mixed
         for (int a = 0; a < kn; ++a) {
             const AngleParam p = ap[k0 + a];
             const bool x = fabsf(p.c) >= fabsf(p.s);
             const float dom = x ? fabsf(p.c) : fabsf(p.s);
             const int Sa = (int)floorf(1.0f / dom) + 1;  // Sa * |dominant step| > 1 bin
             if (a == 0) { xd = x; S = Sa; }
-            else if (xd != (int)x) S = 0;
+            else if (xd != (int)x) mixed = true;
             else S = max(S, Sa);
         }
         sMode[0] = xd;
-        sMode[1] = S;
+        sMode[1] = mixed ? 0 : S;
     }
 
     // register prefetch of a tile: thread covers rows (tid/64) + 4i, column tid%64
@@ -271,11 +272,241 @@ radon_direct_kernel(const float *__restrict__ img, float *__restrict__ sino, con
     }
 }
 
+// ---------------------------------------------------------------- 2 x 2-block form
+// Transpose of the 2 x 2-block R* (|c|, |s| <= 1).  In the forward form each corner of a block
+// whose lowest corner sits at window coordinate q (entry e = floor(q) + C, r = q - floor(q))
+// takes g_j + sum_k ramp_k dg_{j+k}, ramp_k = sat(r + o - k), o the corner's offset in
+// {0, |c|, |s|, |c| + |s|}.  The transpose adds the block's four pixels into entry e of a
+// window table as
+//     (X, Y, Z, V) += (sum f, sum f ramp_0, sum f ramp_1, sum f ramp_2),
+// and once the tile is done, bin J0 + m takes X_m - Y_m + Y_{m-1} - Z_{m-1} + Z_{m-2} - V_{m-2}
+// + V_{m-3} (dg_{j+k} = g_{j+k+1} - g_{j+k}).  The 8 / kAng warps of an angle each own a table
+// and take interleaved lines of blocks along the angle's minor axis; lanes take blocks S apart
+// along the dominant axis with 2 S |dominant step| > 1 bin, so the 32 entries of one
+// read-modify-write are distinct: one float4 read-modify-write per block and angle.  The
+// pixel tile keeps its 8-byte pairs XOR-swizzled per line pair (slot = pair ^ (line / 2 mod
+// 16)), so that lanes walking a row or a column of blocks read it without bank conflicts.  The
+// fold turns an angle's tables into bins with three warp shuffles per 32 bins and adds them
+// into the angle's detector row.
+constexpr int kQGuard = 1;  // unused guard entries on each side of a warp table
+
+__device__ __forceinline__ float add_sat(float a, float b) {  // min(max(a + b, 0), 1)
+    float d;
+    asm("add.sat.f32 %0, %1, %2;" : "=f"(d) : "f"(a), "f"(b));
+    return d;
+}
+// a + b rounded toward minus infinity: with b = 1.5 * 2^23 the low mantissa bits hold floor(a)
+__device__ __forceinline__ float add_rm(float a, float b) {
+    float d;
+    asm("add.rm.f32 %0, %1, %2;" : "=f"(d) : "f"(a), "f"(b));
+    return d;
+}
+
+struct QuadRamp {
+    float ac, ac1, as, as1, af, af1, af2;  // |c|, |c| - 1, |s|, |s| - 1, |c| + |s|, minus 1, minus 2
+};
+
+// The warp's lines of blocks for one angle: block (L, I) along (dominant, minor) axes with
+// I = h + wpa i; lanes with act false compute but do not deposit.
+template <bool SX, bool FAR2>
+__device__ __forceinline__ void radon_quad_lines(unsigned tile_u32, unsigned tab, float qL, float qstep, int n_it,
+                                                 int h, int wpa, int L, bool xdom, int rowoff, int rowdelta,
+                                                 const QuadRamp &k, bool act) {
+#pragma unroll 2
+    for (int i = 0; i < n_it; ++i) {
+        const int I = h + wpa * i;
+        const int bx = xdom ? L : I, by = xdom ? I : L;
+        const unsigned pa = tile_u32 + 4u * (unsigned)((by << 7) + ((bx ^ (by & 15)) << 1) + rowoff);
+        const float2 plo = lds64(pa), phi = lds64(pa + (unsigned)rowdelta);
+        const float f0 = SX ? plo.y : plo.x, fc = SX ? plo.x : plo.y;  // lowest corner, x neighbour
+        const float fs = SX ? phi.y : phi.x, ff = SX ? phi.x : phi.y;  // y neighbour, far corner
+        const float q = fmaf((float)i, qstep, qL);
+        const float Rf = add_rm(q, kMagic);
+        const float r = q - (Rf - kMagic);
+        const unsigned ea = tab + (__float_as_uint(Rf) << 4);
+        float dy = fmaf(fc, add_sat(r, k.ac), fmaf(fs, add_sat(r, k.as), f0 * r));
+        float dz = fmaf(fc, add_sat(r, k.ac1), fs * add_sat(r, k.as1));
+        float dw = 0.f;
+        if (FAR2) {  // |c| + |s| >= 1: the far corner's first ramp is 1
+            dy += ff;
+            dz = fmaf(ff, add_sat(r, k.af1), dz);
+            dw = ff * add_sat(r, k.af2);
+        } else {     // |c| + |s| < 1: its third ramp is 0
+            dy = fmaf(ff, add_sat(r, k.af), dy);
+            dz = fmaf(ff, add_sat(r, k.af1), dz);
+        }
+        const float F = (f0 + fc) + (fs + ff);
+        if (act) {
+            float4 t = lds128(ea);
+            t.x += F;
+            t.y += dy;
+            t.z += dz;
+            if (FAR2) t.w += dw;
+            sts128(ea, t);
+        }
+        __syncwarp();  // the next line's read-modify-writes see this line's
+    }
+}
+
+__global__ void __launch_bounds__(kRThreads, 3)
+radon_quad_kernel(const float *__restrict__ img, float *__restrict__ sino, const AngleParam *__restrict__ ap, int N,
+                  int n_det, int n_theta, int W, int C, int kAng, int tiles_per_band, float scale, int use_atomic,
+                  long long img_stride, long long sino_stride, int per_angle_w) {
+    extern __shared__ __align__(16) float rsm[];
+    const int rows_n = (kAng * n_det + 3) & ~3;
+    const int Wt = W + 2 * kQGuard;
+    float *rows = rsm;                                                       // [kAng][n_det] detector rows
+    float4 *tabs = reinterpret_cast<float4 *>(rsm + rows_n);                 // [warps][Wt] window tables
+    float *tile = reinterpret_cast<float *>(tabs + kRWarps * Wt);           // [64 * 64] swizzled pixel tile
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int k0 = blockIdx.x * kAng;
+    const int kn = min(kAng, n_theta - k0);
+    const int tiles = (N + kTile - 1) / kTile;
+    const int t_begin = blockIdx.y * tiles_per_band;
+    const int t_end = min(tiles * tiles, t_begin + tiles_per_band);
+    img += (long long)blockIdx.z * img_stride;
+    sino += (long long)blockIdx.z * sino_stride;
+
+    for (int i = tid; i < rows_n; i += kRThreads) rows[i] = 0.f;
+    for (int i = tid; i < kRWarps * Wt; i += kRThreads) tabs[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+
+    // the warp's angle a (of the block's kAng) and its share h of the angle's block lines
+    const int wpa = kRWarps / kAng;
+    const int a = warp % kAng, h = warp / kAng;
+    const bool live = a < kn;
+    AngleParam P = {};
+    if (live) P = ap[k0 + a];
+    const float c = P.c, s = P.s;
+    QuadRamp k;
+    k.ac = fabsf(c);
+    k.as = fabsf(s);
+    k.ac1 = k.ac - 1.f;
+    k.as1 = k.as - 1.f;
+    k.af = k.ac + k.as;
+    k.af1 = k.af - 1.f;
+    k.af2 = k.af - 2.f;
+    const bool xdom = k.ac >= k.as;
+    const float d1 = xdom ? c : s, d2 = xdom ? s : c;  // u steps per pixel along the dominant, minor axes
+    const int S = live ? max(1, min(32, (int)ceilf(1.001f / (2.f * fabsf(d1))))) : 1;
+    const bool SX = c < 0.f, SY = s < 0.f, FAR2 = k.af1 >= 0.f;
+    const float lo = fminf(c, 0.f) + fminf(s, 0.f);
+    const int F63 = (int)floorf((float)(kTile - 1) * lo);
+    const int rowoff = SY ? kTile : 0;           // line of the lowest corner within the block (floats)
+    const int rowdelta = SY ? -4 * kTile : 4 * kTile;  // bytes to the block's other line
+    const int n_it = kTile / 2 / wpa;
+    const float qstep = (float)(2 * wpa) * d2;
+    const unsigned tile_u32 = smem_u32(tile);
+    const unsigned tab = smem_u32(tabs + warp * Wt + kQGuard) + 16u * (unsigned)C - ((unsigned)kMagicInt << 4);
+
+    float pre[16];
+    auto fetch = [&](int t) {
+        const int ty = t / tiles, tx = t % tiles;
+        const int x = tx * kTile + (tid & 63);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const int y = ty * kTile + (tid >> 6) + 4 * i;
+            pre[i] = (x < N && y < N) ? __ldg(img + (long long)y * N + x) : 0.f;
+        }
+    };
+    if (t_begin < t_end) fetch(t_begin);
+
+    // warp h = 0 of angle a: the angle's tables -> bins J0 .. J0 + W + 2 of its row; tables cleared
+    auto fold = [&](int J0) {
+        float k1 = 0.f, k2 = 0.f, k3 = 0.f;  // c1, c2, c3 of the previous 32 entries' last lanes
+        for (int m0 = 0; m0 < W + 3; m0 += 32) {
+            const int m = m0 + lane;
+            float4 T = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (m < W) {
+                for (int hh = 0; hh < wpa; ++hh) {
+                    const unsigned ad = smem_u32(tabs + (a + kAng * hh) * Wt + kQGuard + m);
+                    const float4 t = lds128(ad);
+                    T.x += t.x;
+                    T.y += t.y;
+                    T.z += t.z;
+                    T.w += t.w;
+                    sts128(ad, make_float4(0.f, 0.f, 0.f, 0.f));
+                }
+            }
+            // entry m adds (X - Y, Y - Z, Z - V, V) to bins m .. m + 3
+            const float c0 = T.x - T.y, c1 = T.y - T.z, c2 = T.z - T.w, c3 = T.w;
+            const float s1 = __shfl_sync(0xffffffffu, c1, (lane + 31) & 31);
+            const float s2 = __shfl_sync(0xffffffffu, c2, (lane + 30) & 31);
+            const float s3 = __shfl_sync(0xffffffffu, c3, (lane + 29) & 31);
+            const float v = c0 + (lane >= 1 ? s1 : k1) + (lane >= 2 ? s2 : k2) + (lane >= 3 ? s3 : k3);
+            k1 = s1;
+            k2 = s2;
+            k3 = s3;
+            const int j = J0 + m;
+            if (j >= 0 && j < n_det) rows[a * n_det + j] += v;
+        }
+    };
+
+    int J0prev = 0;
+    for (int t = t_begin; t < t_end; ++t) {
+        const int ty = t / tiles, tx = t % tiles;
+        __syncthreads();  // every block of the previous tile deposited; initial clears done
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const int y = (tid >> 6) + 4 * i, x = tid & 63;
+            tile[y * kTile + 2 * ((x >> 1) ^ ((y >> 1) & 15)) + (x & 1)] = pre[i];
+        }
+        if (h == 0 && live && t > t_begin) fold(J0prev);
+        __syncthreads();  // tile stored, tables cleared
+        if (t + 1 < t_end) fetch(t + 1);
+        if (live) {
+            const long long U = P.U00 + (long long)tx * P.CT + (long long)ty * P.ST;
+            const int Ji = (int)(U >> 32);
+            const float frac = (float)(unsigned)(U & 0xffffffffLL) * 2.3283064365386963e-10f;
+            J0prev = Ji + F63 - 1;  // window start: entry e is bin J0 + e
+            const float q0 = (float)(1 - F63 - C) + frac + lo;
+            for (int ph = 0; ph < S; ++ph) {
+                const int L = ph + S * lane;
+                const bool act = L < kTile / 2;
+                const int Lc = act ? L : kTile / 2 - 1;
+                const float qL = fmaf(2.f * (float)Lc, d1, fmaf(2.f * (float)h, d2, q0));
+                if (SX) {
+                    if (FAR2) radon_quad_lines<true, true>(tile_u32, tab, qL, qstep, n_it, h, wpa, Lc, xdom, rowoff, rowdelta, k, act);
+                    else radon_quad_lines<true, false>(tile_u32, tab, qL, qstep, n_it, h, wpa, Lc, xdom, rowoff, rowdelta, k, act);
+                } else {
+                    if (FAR2) radon_quad_lines<false, true>(tile_u32, tab, qL, qstep, n_it, h, wpa, Lc, xdom, rowoff, rowdelta, k, act);
+                    else radon_quad_lines<false, false>(tile_u32, tab, qL, qstep, n_it, h, wpa, Lc, xdom, rowoff, rowdelta, k, act);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (h == 0 && live && t_begin < t_end) fold(J0prev);
+    __syncthreads();
+    for (int i = tid; i < kn * n_det; i += kRThreads) {
+        const int aa = i / n_det, j = i - aa * n_det;
+        float *dst = sino + (long long)(k0 + aa) * n_det + j;
+        const float v = (per_angle_w ? __ldg(&ap[k0 + aa].w) : scale) * rows[i];
+        if (use_atomic) {
+            if (v != 0.f) atomicAdd(dst, v);
+        } else {
+            *dst = v;
+        }
+    }
+}
+
 }  // namespace
 
-size_t radon_smem(const bp_plan *p, int kAng) {
+// The 2 x 2-block form needs |c|, |s| <= 1 (a block spans at most four bins).
+static bool radon_quad_form(const bp_plan *p) { return p->step_max <= 1.0f; }
+
+static size_t radon_pair_smem(const bp_plan *p, int kAng) {
     return sizeof(float) * ((((size_t)kAng * p->n_det + 3) & ~(size_t)3) + kTile * (kTile + 1)) +
            sizeof(float2) * (size_t)kRWarps * kAng * p->W;
+}
+
+static size_t radon_quad_smem(const bp_plan *p, int kAng) {
+    return sizeof(float) * ((((size_t)kAng * p->n_det + 3) & ~(size_t)3) + (size_t)kTile * kTile) +
+           sizeof(float4) * (size_t)kRWarps * (p->W + 2 * kQGuard);
+}
+
+size_t radon_smem(const bp_plan *p, int kAng) {
+    return radon_quad_form(p) ? radon_quad_smem(p, kAng) : radon_pair_smem(p, kAng);
 }
 
 int radon_max_kang(const bp_plan *p) {
@@ -327,12 +558,19 @@ bp_status launch_radon_shape(bp_plan *p, const float *img, float *sino, int batc
     const int per_band = (ntiles + bands - 1) / bands;
     const int use_atomic = bands > 1;
     if (use_atomic) BP_CUDA_TRY(cudaMemsetAsync(sino, 0, sizeof(float) * sino_n * batch, st));
-    BP_CUDA_TRY(cudaFuncSetAttribute(radon_direct_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const float scale = (float)(p->dx * p->dx / p->dt);
     dim3 grid(ablocks, bands, batch);
-    radon_direct_kernel<<<grid, kRThreads, smem, st>>>(img, sino, p->d_ang, p->N, p->n_det, p->n_theta, p->W, p->C,
-                                                       kAng, per_band, scale, use_atomic, (long long)p->N * p->N,
-                                                       (long long)sino_n, per_angle_w);
+    if (radon_quad_form(p)) {
+        BP_CUDA_TRY(cudaFuncSetAttribute(radon_quad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        radon_quad_kernel<<<grid, kRThreads, smem, st>>>(img, sino, p->d_ang, p->N, p->n_det, p->n_theta, p->W, p->C,
+                                                         kAng, per_band, scale, use_atomic, (long long)p->N * p->N,
+                                                         (long long)sino_n, per_angle_w);
+    } else {
+        BP_CUDA_TRY(cudaFuncSetAttribute(radon_direct_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        radon_direct_kernel<<<grid, kRThreads, smem, st>>>(img, sino, p->d_ang, p->N, p->n_det, p->n_theta, p->W,
+                                                           p->C, kAng, per_band, scale, use_atomic,
+                                                           (long long)p->N * p->N, (long long)sino_n, per_angle_w);
+    }
     BP_CUDA_TRY(cudaGetLastError());
     return BP_OK;
 }

@@ -190,6 +190,34 @@ def test_radon_ragged(N, n_det, n_theta, dt_scale, seed):
         assert oracle.rel_l2(g[i].cpu().numpy(), ref) <= TOL_DIRECT
 
 
+@pytest.mark.parametrize("N,n_det,dt_scale,seed", [
+    (96, 96, 1.0, 6), (129, 140, 1.0, 7), (70, 30, 1.0, 8), (130, 20, 1.0, 9), (64, 45, 1.0, 10),
+    (80, 100, 0.5, 11)])
+def test_radon_shuffled_whole_circle(N, n_det, dt_scale, seed):
+    # Angles over the whole circle in shuffled order: all four corner roles and both dominant
+    # axes, mixed within one CTA's angles in any pattern; exact axis angles and diagonals put
+    # corners on bin edges.  Steps |c|, |s| <= 1 run the 2 x 2-block R (pixels down to a sixth of
+    # a bin: lanes several blocks apart), larger steps (129 / 140, 80 / 100 at half pitch) the
+    # pair form.  Every angles-per-CTA count, one and several bands, a batch of two and the
+    # per-angle-weight variant (the transpose of R*).
+    rng = np.random.default_rng(seed)
+    special = np.array([0.0, 1.25, 0.5, 1.75]) * np.pi
+    theta = rng.permutation(np.concatenate([rng.uniform(-np.pi, 2 * np.pi, 29), special]))
+    dt = dt_scale * 2.0 / n_det
+    plan = bp.Plan(N, n_det, theta, dt)
+    fd = to_dev(rng.normal(size=(2, N, N)))
+    refs = [oracle.radon(rounded(fd[i]), n_det, theta, dt) for i in range(2)]
+    for kang, bands in ((1, 1), (2, 3), (4, 1), (4, 4)):
+        plan.set_shape((kang, bands), "radon", batch=2)
+        g = plan.radon(fd)
+        for i in range(2):
+            assert oracle.rel_l2(g[i].cpu().numpy(), refs[i]) <= TOL_DIRECT, (kang, bands)
+    w = oracle.weights(theta)
+    at = plan.backproject_transpose(fd[0])
+    ref = w[:, None] * dt / (2.0 / N) ** 2 * refs[0]
+    assert oracle.rel_l2(at.cpu().numpy(), ref) <= TOL_DIRECT
+
+
 def test_radon_full_size_sampled_angles():
     wl = synth.LARGE
     e = synth.random_ellipses(wl.n_ellipses, wl.seed)
