@@ -285,9 +285,9 @@ radon_direct_kernel(const float *__restrict__ img, float *__restrict__ sino, con
 // along the dominant axis with 2 S |dominant step| > 1 bin, so the 32 entries of one
 // read-modify-write are distinct: one float4 read-modify-write per block and angle.  The
 // pixel tile keeps its 8-byte pairs XOR-swizzled per line pair (slot = pair ^ (line / 2 mod
-// 16)), so that lanes walking a row or a column of blocks read it without bank conflicts.  The
-// fold turns an angle's tables into bins with three warp shuffles per 32 bins and adds them
-// into the angle's detector row.
+// 16)), so that lanes walking a row or a column of blocks read it without bank conflicts.  Each
+// warp folds its own table into bins with three warp shuffles per 32 bins and adds them into
+// the angle's detector row (shared-memory atomics: the angle's warps fold at the same time).
 constexpr int kQGuard = 1;  // unused guard entries on each side of a warp table
 
 __device__ __forceinline__ float add_sat(float a, float b) {  // min(max(a + b, 0), 1)
@@ -411,22 +411,19 @@ radon_quad_kernel(const float *__restrict__ img, float *__restrict__ sino, const
     };
     if (t_begin < t_end) fetch(t_begin);
 
-    // warp h = 0 of angle a: the angle's tables -> bins J0 .. J0 + W + 2 of its row; tables cleared
+    // the warp's table -> bins J0 .. J0 + m_end - 1 of the angle's row (added atomically: the
+    // angle's warps fold together), table cleared.  Entries above 3 + 62 (|c| + |s|) stay zero (a
+    // margin of two bins is kept).
+    const int m_end = min(W + 3, (int)(62.f * k.af) + 9);
+    const unsigned tab0 = smem_u32(tabs + warp * Wt + kQGuard);
     auto fold = [&](int J0) {
         float k1 = 0.f, k2 = 0.f, k3 = 0.f;  // c1, c2, c3 of the previous 32 entries' last lanes
-        for (int m0 = 0; m0 < W + 3; m0 += 32) {
+        for (int m0 = 0; m0 < m_end; m0 += 32) {
             const int m = m0 + lane;
             float4 T = make_float4(0.f, 0.f, 0.f, 0.f);
             if (m < W) {
-                for (int hh = 0; hh < wpa; ++hh) {
-                    const unsigned ad = smem_u32(tabs + (a + kAng * hh) * Wt + kQGuard + m);
-                    const float4 t = lds128(ad);
-                    T.x += t.x;
-                    T.y += t.y;
-                    T.z += t.z;
-                    T.w += t.w;
-                    sts128(ad, make_float4(0.f, 0.f, 0.f, 0.f));
-                }
+                T = lds128(tab0 + 16u * (unsigned)m);
+                sts128(tab0 + 16u * (unsigned)m, make_float4(0.f, 0.f, 0.f, 0.f));
             }
             // entry m adds (X - Y, Y - Z, Z - V, V) to bins m .. m + 3
             const float c0 = T.x - T.y, c1 = T.y - T.z, c2 = T.z - T.w, c3 = T.w;
@@ -438,7 +435,7 @@ radon_quad_kernel(const float *__restrict__ img, float *__restrict__ sino, const
             k2 = s2;
             k3 = s3;
             const int j = J0 + m;
-            if (j >= 0 && j < n_det) rows[a * n_det + j] += v;
+            if (m < m_end && j >= 0 && j < n_det) atomicAdd(rows + a * n_det + j, v);
         }
     };
 
@@ -451,7 +448,7 @@ radon_quad_kernel(const float *__restrict__ img, float *__restrict__ sino, const
             const int y = (tid >> 6) + 4 * i, x = tid & 63;
             tile[y * kTile + 2 * ((x >> 1) ^ ((y >> 1) & 15)) + (x & 1)] = pre[i];
         }
-        if (h == 0 && live && t > t_begin) fold(J0prev);
+        if (live && t > t_begin) fold(J0prev);
         __syncthreads();  // tile stored, tables cleared
         if (t + 1 < t_end) fetch(t + 1);
         if (live) {
@@ -476,7 +473,7 @@ radon_quad_kernel(const float *__restrict__ img, float *__restrict__ sino, const
         }
     }
     __syncthreads();
-    if (h == 0 && live && t_begin < t_end) fold(J0prev);
+    if (live && t_begin < t_end) fold(J0prev);
     __syncthreads();
     for (int i = tid; i < kn * n_det; i += kRThreads) {
         const int aa = i / n_det, j = i - aa * n_det;
