@@ -32,6 +32,7 @@
 
 #include "common.cuh"
 #include "fft.cuh"
+#include "fft_pt.cuh"
 #include "tma.cuh"
 
 namespace bp {
@@ -406,6 +407,83 @@ ifft_pass_x_kernel(const float2 *__restrict__ inter, float *__restrict__ img, co
     }
 }
 
+// Persistent form of the two passes for M = 2^9 .. 2^13: each CTA stages the per-pass twiddle
+// table of the M-point transform once and walks rows; the next row's loads are in flight while
+// the current row is transformed (first pass from registers, radix-8 passes in shared memory,
+// last pass from registers straight to the pruned outputs).  Output i of a row is position
+// pos = i of the transform, i.e. image index (i + floor(N/2)) mod M when that is below N.
+//   XPASS false: rows l_x of G, inter[i_y][l_x] = z * deap[i_y];
+//   XPASS true:  rows i_y of inter, img[i_y][i_x] = Re z * deap[i_x].
+template <int LOGM, bool XPASS>
+__global__ void __launch_bounds__((1 << LOGM) / kPassE, 1024 / ((1 << LOGM) / kPassE))
+ifft_pt_kernel(const float2 *__restrict__ in, float2 *__restrict__ inter, float *__restrict__ img,
+               const float *__restrict__ deap, const float2 *__restrict__ twp, int rows, int N) {
+    using PL = PtPlan<LOGM>;
+    constexpr int M = 1 << LOGM, NT = M / kPassE, Rl = PL::Rl, Gl = kPassE / Rl;
+    constexpr int TWN = pt_offset<LOGM>(PL::npass);
+    static_assert(TWN % 2 == 0, "per-pass twiddle count");
+    extern __shared__ __align__(16) float2 pz[];
+    float2 *z = pz;      // [M] work array
+    float2 *T = z + M;   // [TWN] per-pass twiddles
+    const int t = threadIdx.x;
+    const int h = N / 2;
+    float2 nxt[kPassE];  // inputs of the first pass: x[t + r NT]
+    auto fetch = [&](int row) {
+        const float2 *src = in + (long long)row * M;
+#pragma unroll
+        for (int r = 0; r < kPassE; ++r) nxt[r] = __ldg(src + t + r * NT);
+    };
+    int row = blockIdx.x;
+    if (row < rows) fetch(row);
+    {
+        constexpr int n4t = TWN / 2;  // float4 loads; T starts 16-byte aligned (M even)
+        const float4 *ts = reinterpret_cast<const float4 *>(twp);
+        float4 *td = reinterpret_cast<float4 *>(T);
+#pragma unroll
+        for (int i = 0; i < (n4t + NT - 1) / NT; ++i)
+            if (t + i * NT < n4t) td[t + i * NT] = __ldg(ts + t + i * NT);
+    }
+    for (; row < rows; row += gridDim.x) {
+        float2 a[kPassE];
+#pragma unroll
+        for (int r = 0; r < kPassE; ++r) a[r] = nxt[r];
+        if (row + gridDim.x < rows) fetch(row + gridDim.x);
+        __syncthreads();  // previous row's last reads of z (and the staged table) are done
+        dft_reg<8>(a, true);  // pass 0 (L = 1, radix 8)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) z[fft_swz<kPassE>(t * 8 + q)] = a[q];
+        __syncthreads();
+        int L = 8;
+#pragma unroll
+        for (int p = 1; p < PL::n8; ++p) {
+            if (p == PL::npass - 1) break;
+            pt_pass<8, LOGM>(z, T + pt_offset<LOGM>(p), L, t, true);
+            L *= 8;
+        }
+        // last pass: outputs t + (g + q Gl) NT
+        constexpr int lp = PL::npass - 1, m = M / Rl;
+        float2 c[Gl][Rl];
+#pragma unroll
+        for (int g = 0; g < Gl; ++g)
+#pragma unroll
+            for (int r = 0; r < Rl; ++r) c[g][r] = z[fft_swz<kPassE>(t + g * NT + r * m)];
+#pragma unroll
+        for (int g = 0; g < Gl; ++g) {
+            pt_twiddle_dft<Rl>(c[g], T + pt_offset<LOGM>(lp), L, t + g * NT, true);
+#pragma unroll
+            for (int q = 0; q < Rl; ++q) {
+                const int i = t + (g + q * Gl) * NT;
+                const int o = i < N - h ? i + h : i - (M - h);  // image index, valid in [0, N)
+                if (o >= 0 && o < N) {
+                    const float d = __ldg(deap + o);
+                    if (XPASS) img[(long long)row * N + o] = c[g][q].x * d;
+                    else inter[(long long)o * M + row] = make_float2(c[g][q].x * d, c[g][q].y * d);
+                }
+            }
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------------- adjoint (R_F)
 // R_F = (dx^2/dt) diag(1/w) A_F^T with A_F the Fourier-path R* above.  Transposing every
 // linear step in reverse order: deapodise and embed the image, forward 2D FFT (pruned:
@@ -571,6 +649,7 @@ void free_fourier(bp_plan *p) {
     cudaFree(f.deapod);
     cudaFree(f.wk);
     cudaFree(f.twM);
+    cudaFree(f.twpassM);
     cudaFree(f.ray);
     cudaFree(f.sray);
     cudaFree(f.sphi);
@@ -665,6 +744,10 @@ bp_status ensure_fourier(bp_plan *p) {
         tw[i] = make_float2((float)std::cos(an), (float)std::sin(an));
     }
 
+    std::vector<float2> twp;
+    build_pass_twiddles(ilog2(M), twp);
+    twp.resize((twp.size() + 1) & ~(size_t)1);  // a whole number of float4 loads
+
     f.M = M;
     f.W = kW;
     f.logM = ilog2(M);
@@ -682,6 +765,7 @@ bp_status ensure_fourier(bp_plan *p) {
     alloc((void **)&f.deapod, sizeof(float) * N);
     alloc((void **)&f.wk, sizeof(float) * n_theta);
     alloc((void **)&f.twM, sizeof(float2) * tw.size());
+    alloc((void **)&f.twpassM, sizeof(float2) * twp.size());
     alloc((void **)&f.ray, sizeof(long long) * ray.size());
     alloc(&f.sray, sizeof(SortedRay) * sray.size());
     alloc((void **)&f.sphi, sizeof(float) * sphi.size());
@@ -689,6 +773,8 @@ bp_status ensure_fourier(bp_plan *p) {
     if (e == cudaSuccess) e = cudaMemcpy(f.deapod, deap.data(), sizeof(float) * N, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(f.wk, wk.data(), sizeof(float) * n_theta, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(f.twM, tw.data(), sizeof(float2) * tw.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(f.twpassM, twp.data(), sizeof(float2) * twp.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(f.ray, ray.data(), sizeof(long long) * ray.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(f.sray, sray.data(), sizeof(SortedRay) * sray.size(), cudaMemcpyHostToDevice);
@@ -720,7 +806,7 @@ static int rows_per_cta(int M) { return M <= 8192 ? 2 : 1; }
 
 // Inverse 2D FFT of the M x M grid (f.grid), pruned to the N x N image, times deap[i_x]
 // deap[i_y] (the deapodisation; ones for no correction), real part into img.
-bp_status launch_grid_to_image(bp_plan *p, const float *deap, float *img, cudaStream_t st) {
+static bp_status launch_grid_to_image_rows(bp_plan *p, const float *deap, float *img, cudaStream_t st) {
     FourierWork &f = p->four;
     const int N = p->N, M = f.M;
     const int R = rows_per_cta(M);
@@ -735,6 +821,36 @@ bp_status launch_grid_to_image(bp_plan *p, const float *deap, float *img, cudaSt
     pass_x<<<(N + R - 1) / R, nthr * groups, smemR, st>>>(f.mid, img, deap, f.twM, M, f.logM, N, R, p->d_err);
     BP_CUDA_TRY(cudaGetLastError());
     return BP_OK;
+}
+
+// The persistent passes for one M: grid of (CTAs per SM) x SMs, capped by the rows.
+template <int LOGM>
+static bp_status launch_ifft_pt(bp_plan *p, const float *deap, float *img, cudaStream_t st) {
+    FourierWork &f = p->four;
+    constexpr int M = 1 << LOGM, NT = M / kPassE;
+    constexpr size_t smem = sizeof(float2) * (M + pt_offset<LOGM>(PtPlan<LOGM>::npass));
+    auto ky = ifft_pt_kernel<LOGM, false>;
+    auto kx = ifft_pt_kernel<LOGM, true>;
+    BP_CUDA_TRY(cudaFuncSetAttribute(ky, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    BP_CUDA_TRY(cudaFuncSetAttribute(kx, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    BP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ky, NT, smem));
+    const int ctas = std::max(1, per_sm) * std::max(1, p->sm_count);
+    ky<<<std::min(ctas, M), NT, smem, st>>>(f.grid, f.mid, nullptr, deap, f.twpassM, M, p->N);
+    kx<<<std::min(ctas, p->N), NT, smem, st>>>(f.mid, nullptr, img, deap, f.twpassM, p->N, p->N);
+    BP_CUDA_TRY(cudaGetLastError());
+    return BP_OK;
+}
+
+bp_status launch_grid_to_image(bp_plan *p, const float *deap, float *img, cudaStream_t st) {
+    switch (p->four.logM) {
+        case 9: return launch_ifft_pt<9>(p, deap, img, st);
+        case 10: return launch_ifft_pt<10>(p, deap, img, st);
+        case 11: return launch_ifft_pt<11>(p, deap, img, st);
+        case 12: return launch_ifft_pt<12>(p, deap, img, st);
+        case 13: return launch_ifft_pt<13>(p, deap, img, st);
+        default: return launch_grid_to_image_rows(p, deap, img, st);
+    }
 }
 
 bp_status launch_fourier(bp_plan *p, const void *sino, bp_dtype dt, float *img, int batch, cudaStream_t st,
