@@ -541,6 +541,83 @@ adj_fft_y_kernel(const float2 *__restrict__ T, float2 *__restrict__ grid, const 
     for (int i = threadIdx.x; i < R * M; i += blockDim.x) grid[(long long)lx0 * M + i] = z[i];
 }
 
+// Persistent form of the two adjoint passes for M = 2^9 .. 2^13 (the transpose of
+// ifft_pt_kernel; same row walk, table and pass structure, forward transforms).  Input
+// position pos of a row holds image index (pos + floor(N/2)) mod M when that is below N, else
+// zero (the padding is never loaded); all M outputs are written.
+//   YPASS false: rows i_y of the image times deap[i_x] deap[i_y] -> T[i_y][l_x];
+//   YPASS true:  columns l_x of T -> G[l_x][l_y].
+template <int LOGM, bool YPASS>
+__global__ void __launch_bounds__((1 << LOGM) / kPassE, 1024 / ((1 << LOGM) / kPassE))
+fft_pt_fwd_kernel(const float *__restrict__ img, const float2 *__restrict__ Tin, float2 *__restrict__ out,
+                  const float *__restrict__ deap, const float2 *__restrict__ twp, int rows, int N) {
+    using PL = PtPlan<LOGM>;
+    constexpr int M = 1 << LOGM, NT = M / kPassE, Rl = PL::Rl, Gl = kPassE / Rl;
+    constexpr int TWN = pt_offset<LOGM>(PL::npass);
+    static_assert(TWN % 2 == 0, "per-pass twiddle count");
+    extern __shared__ __align__(16) float2 pz[];
+    float2 *z = pz;      // [M] work array
+    float2 *T = z + M;   // [TWN] per-pass twiddles
+    const int t = threadIdx.x;
+    const int h = N / 2;
+    float2 nxt[kPassE];  // inputs of the first pass: x[t + r NT]
+    auto fetch = [&](int row) {
+        const float dy = YPASS ? 1.f : __ldg(deap + row);
+#pragma unroll
+        for (int r = 0; r < kPassE; ++r) {
+            const int pos = t + r * NT;
+            const int o = pos < N - h ? pos + h : pos - (M - h);  // image index, valid in [0, N)
+            float2 v = make_float2(0.f, 0.f);
+            if (o >= 0 && o < N) {
+                if (YPASS) v = __ldg(Tin + (long long)o * M + row);
+                else v.x = __ldg(img + (long long)row * N + o) * __ldg(deap + o) * dy;
+            }
+            nxt[r] = v;
+        }
+    };
+    int row = blockIdx.x;
+    if (row < rows) fetch(row);
+    {
+        constexpr int n4t = TWN / 2;
+        const float4 *ts = reinterpret_cast<const float4 *>(twp);
+        float4 *td = reinterpret_cast<float4 *>(T);
+#pragma unroll
+        for (int i = 0; i < (n4t + NT - 1) / NT; ++i)
+            if (t + i * NT < n4t) td[t + i * NT] = __ldg(ts + t + i * NT);
+    }
+    for (; row < rows; row += gridDim.x) {
+        float2 a[kPassE];
+#pragma unroll
+        for (int r = 0; r < kPassE; ++r) a[r] = nxt[r];
+        if (row + gridDim.x < rows) fetch(row + gridDim.x);
+        __syncthreads();  // previous row's last reads of z (and the staged table) are done
+        dft_reg<8>(a, false);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) z[fft_swz<kPassE>(t * 8 + q)] = a[q];
+        __syncthreads();
+        int L = 8;
+#pragma unroll
+        for (int p = 1; p < PL::n8; ++p) {
+            if (p == PL::npass - 1) break;
+            pt_pass<8, LOGM>(z, T + pt_offset<LOGM>(p), L, t, false);
+            L *= 8;
+        }
+        constexpr int lp = PL::npass - 1, m = M / Rl;
+        float2 c[Gl][Rl];
+#pragma unroll
+        for (int g = 0; g < Gl; ++g)
+#pragma unroll
+            for (int r = 0; r < Rl; ++r) c[g][r] = z[fft_swz<kPassE>(t + g * NT + r * m)];
+        float2 *dst = out + (long long)row * M;
+#pragma unroll
+        for (int g = 0; g < Gl; ++g) {
+            pt_twiddle_dft<Rl>(c[g], T + pt_offset<LOGM>(lp), L, t + g * NT, false);
+#pragma unroll
+            for (int q = 0; q < Rl; ++q) dst[t + (g + q * Gl) * NT] = c[g][q];
+        }
+    }
+}
+
 // Interpolation at the polar samples (transpose of the spreading): one thread per sample,
 // consecutive samples of one ray in consecutive lanes; result times the conjugate sample
 // factor (1/P)(m ? 2 : 1) exp(-i pi m (n_det-1)/P) exp(-2 pi i delta (z_x + z_y)/M) and dx^2/dt.
@@ -896,6 +973,25 @@ bp_status launch_fourier(bp_plan *p, const void *sino, bp_dtype dt, float *img, 
     return BP_OK;
 }
 
+// The persistent adjoint passes for one M (grid as in launch_ifft_pt).
+template <int LOGM>
+static bp_status launch_fft_pt_fwd(bp_plan *p, const float *img, cudaStream_t st) {
+    FourierWork &f = p->four;
+    constexpr int M = 1 << LOGM, NT = M / kPassE;
+    constexpr size_t smem = sizeof(float2) * (M + pt_offset<LOGM>(PtPlan<LOGM>::npass));
+    auto kx = fft_pt_fwd_kernel<LOGM, false>;
+    auto ky = fft_pt_fwd_kernel<LOGM, true>;
+    BP_CUDA_TRY(cudaFuncSetAttribute(kx, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    BP_CUDA_TRY(cudaFuncSetAttribute(ky, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    BP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kx, NT, smem));
+    const int ctas = std::max(1, per_sm) * std::max(1, p->sm_count);
+    kx<<<std::min(ctas, p->N), NT, smem, st>>>(img, nullptr, f.mid, f.deapod, f.twpassM, p->N, p->N);
+    ky<<<std::min(ctas, M), NT, smem, st>>>(nullptr, f.mid, f.grid, f.deapod, f.twpassM, M, p->N);
+    BP_CUDA_TRY(cudaGetLastError());
+    return BP_OK;
+}
+
 bp_status launch_radon_fourier(bp_plan *p, const float *img, float *sino, int batch, cudaStream_t st,
                                int per_angle_w) {
     bp_status s = ensure_fourier(p);
@@ -916,9 +1012,18 @@ bp_status launch_radon_fourier(bp_plan *p, const float *img, float *sino, int ba
     const float delta2 = (N % 2 == 0) ? 1.0f / (float)M : 0.0f;
     const float scale = (float)(p->dx * p->dx / p->dt);
     for (int b = 0; b < batch; ++b) {
-        kx<<<(N + R - 1) / R, nthr * groups, smemR, st>>>(img + (size_t)b * N * N, f.mid, f.deapod, f.twM, M, f.logM,
-                                                         N, R);
-        ky<<<M / R, nthr * groups, smemR, st>>>(f.mid, f.grid, f.twM, M, f.logM, N, R);
+        const float *ib = img + (size_t)b * N * N;
+        switch (f.logM) {
+            case 9: s = launch_fft_pt_fwd<9>(p, ib, st); break;
+            case 10: s = launch_fft_pt_fwd<10>(p, ib, st); break;
+            case 11: s = launch_fft_pt_fwd<11>(p, ib, st); break;
+            case 12: s = launch_fft_pt_fwd<12>(p, ib, st); break;
+            case 13: s = launch_fft_pt_fwd<13>(p, ib, st); break;
+            default:
+                kx<<<(N + R - 1) / R, nthr * groups, smemR, st>>>(ib, f.mid, f.deapod, f.twM, M, f.logM, N, R);
+                ky<<<M / R, nthr * groups, smemR, st>>>(f.mid, f.grid, f.twM, M, f.logM, N, R);
+        }
+        if (s != BP_OK) return s;
         auto ki = f.W == 4 ? adj_interp_kernel<2> : adj_interp_kernel<3>;
         ki<<<dim3((H + 255) / 256, p->n_theta), 256, 0, st>>>(f.grid, f.spec, f.ray, M, H, P, p->n_det, f.kbtab, delta2,
                                                                scale, per_angle_w ? f.wk : nullptr);
