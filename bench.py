@@ -525,21 +525,24 @@ def run_gpu(args, world, rank, local):
             print(json.dumps({"value": throughput(wl.updates, world, args.steps, total_ms),
                               "unit": "Gupdates/s", "kernel_ms": statistics.mean(bp_ms), "partial": True}))
         return
-    # end to end through the host-buffer C-ABI call: pinned host sinogram in, host image out
-    g_pin = torch.from_numpy(g_host).pin_memory()
-    img_pin = torch.empty((wl.N, wl.N), dtype=torch.float32).pin_memory()
-    plan.fbp_host(g_pin, "shepp-logan", out=img_pin)
+    # end to end through the host-buffer C-ABI call: n_e2e steps as one call over n_e2e pinned
+    # host sinograms (each step's copy in and copy out inside the timed region; the call
+    # overlaps the copies of neighbouring slices with the kernels of the current one)
     n_e2e = max(3, min(args.steps, 20))
+    g_pin = torch.from_numpy(np.broadcast_to(g_host, (n_e2e, *g_host.shape)).copy()).pin_memory()
+    img_pin = torch.empty((n_e2e, wl.N, wl.N), dtype=torch.float32).pin_memory()
+    plan.fbp_host(g_pin, "shepp-logan", out=img_pin)
     if dist:
         dist.barrier()
-    e2e_t = 0.0
-    for _ in range(n_e2e):
+    e2e_t, e2e_reps = 0.0, 2
+    for _ in range(e2e_reps):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         plan.fbp_host(g_pin, "shepp-logan", out=img_pin)
         e2e_t += time.perf_counter() - t0
     e2e_t = max_over_ranks(e2e_t, dist, dev)
+    n_e2e *= e2e_reps
 
     # other operators and workloads of the path (reported under "paths", not part of the step)
     extra = {} if args.no_paths else other_paths(plan, q, img, flush, stream, dev,
@@ -599,7 +602,8 @@ def run_gpu(args, world, rank, local):
                                      if traffic and "warp_inst_per_update" in traffic else None)},
         "e2e": {"value": wl.updates * world * n_e2e / e2e_t / 1e9, "unit": "Gupdates/s",
                 "h2d_bytes_per_step": g_host.nbytes, "d2h_bytes_per_step": wl.N * wl.N * 4,
-                "call": "bp_fbp_host (pinned host in/out)"},
+                "call": "bp_fbp_host over %d pinned host slices per call (copies of neighbouring slices "
+                        "overlap the kernels)" % (n_e2e // e2e_reps)},
         "gpu_launches": 2 * args.steps,
         "clocks": clocks,
         "paths": extra,

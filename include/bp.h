@@ -272,11 +272,15 @@ bp_status bp_backproject_transpose(bp_plan *plan, const float *img, float *sino,
 
 /*
  * bp_fbp_host -- filtered backprojection from HOST memory to HOST memory:
- * copy sino (host, batch x n_theta x n_det float32) to the device, bp_filter(kind, param),
- * bp_backproject_direct, copy the image back into img (host, batch x N x N float32),
- * and synchronise the stream before returning.  Pinned host memory gives asynchronous
- * copies; pageable memory also works.  Device staging buffers are owned by the plan
- * and allocated on the first call (sized for `batch`; a larger batch reallocates).
+ * for each slice of sino (host, batch x n_theta x n_det float32): copy it to the device,
+ * bp_filter(kind, param), bp_backproject_direct, copy the image back into img (host,
+ * batch x N x N float32); synchronise before returning.  The slices go through three device
+ * slots: slice i + 1 is copied in and slice i - 1 copied out (on two internal streams of the
+ * plan) while slice i is filtered and backprojected on `stream`, so with pinned host memory
+ * a batch runs at the kernels' rate; pageable memory also works, without the overlap.  The
+ * kind and param are checked before any copy is queued (same rules as bp_filter).  Slots,
+ * streams and events are owned by the plan, created on the first call and released by
+ * bp_destroy.
  */
 bp_status bp_fbp_host(bp_plan *plan, const float *sino, float *img, bp_filter_kind kind,
                       float param, int batch, void *stream);

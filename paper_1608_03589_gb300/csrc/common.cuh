@@ -120,6 +120,10 @@ struct RadonShape {
     int kang = 0;   // 0 = the default rule
     int bands = 0;
 };
+// Device slots of the host-buffer entry point: slice i + 1 is copied in and slice i - 1 copied
+// out while slice i is filtered and backprojected.
+constexpr int kHostSlots = 3;
+
 struct TuneEntry {
     int op, dtype, batch;
     int v[2];
@@ -149,9 +153,12 @@ struct bp_plan {
     bp::BstWork bst;
     bp::LogPolarWork lp;
     bp::LppWork lpp;
-    // host-buffer entry point staging
+    // host-buffer entry point: a ring of device slots (one sinogram and one image each), the
+    // copy streams and the events that order the reuse of a slot
     float *d_stage = nullptr;
-    size_t stage_batch = 0;
+    size_t stage_batch = 0;                 // slots allocated
+    cudaStream_t s_h2d = nullptr, s_d2h = nullptr;
+    cudaEvent_t ev_h2d[bp::kHostSlots] = {}, ev_comp[bp::kHostSlots] = {}, ev_d2h[bp::kHostSlots] = {};
     // batched descriptors
     void *d_desc = nullptr;
     size_t desc_cap = 0;

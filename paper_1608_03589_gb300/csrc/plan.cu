@@ -116,6 +116,13 @@ static void plan_free_device(bp_plan *p) {
     free_logpolar(p);
     free_logpolar_partial(p);
     cudaFree(p->d_stage);
+    for (int k = 0; k < kHostSlots; ++k) {
+        if (p->ev_h2d[k]) cudaEventDestroy(p->ev_h2d[k]);
+        if (p->ev_comp[k]) cudaEventDestroy(p->ev_comp[k]);
+        if (p->ev_d2h[k]) cudaEventDestroy(p->ev_d2h[k]);
+    }
+    if (p->s_h2d) cudaStreamDestroy(p->s_h2d);
+    if (p->s_d2h) cudaStreamDestroy(p->s_d2h);
     cudaFree(p->d_desc);
     cudaFree(p->d_counter);
     cudaFree(p->d_status);
@@ -342,6 +349,11 @@ extern "C" bp_status bp_radon(bp_plan *p, const float *img, float *sino, int bat
     return launch_radon_direct(p, img, sino, batch, (cudaStream_t)stream);
 }
 
+// Slices go through a ring of kHostSlots device slots: slice i's sinogram is copied in on
+// s_h2d, filtered and backprojected on the caller's stream, and its image copied out on s_d2h,
+// so that the copies of slices i + 1 and i - 1 overlap the kernels of slice i.  Events order
+// the reuse of a slot: its next copy-in waits for its kernels, its next kernels for its
+// copy-out.
 extern "C" bp_status bp_fbp_host(bp_plan *p, const float *sino, float *img, bp_filter_kind kind, float param,
                                  int batch, void *stream) {
     set_error("");
@@ -349,25 +361,52 @@ extern "C" bp_status bp_fbp_host(bp_plan *p, const float *sino, float *img, bp_f
     if (st != BP_OK) return st;
     if (!sino || !img) return fail(BP_ERR_INVALID_ARG, "host pointer is NULL");
     if (batch < 1 || batch > 65535) return fail(BP_ERR_INVALID_ARG, "batch out of range [1, 65535]");
+    // everything the per-slice calls check is checked here, before any copy is queued
+    if (kind != BP_RAMLAK && kind != BP_SHEPP_LOGAN && kind != BP_TIKHONOV)
+        return fail(BP_ERR_INVALID_ARG, "invalid filter kind");
+    if (kind == BP_TIKHONOV && !(param >= 0.f && std::isfinite(param)))
+        return fail(BP_ERR_INVALID_ARG, "Tikhonov lambda must be finite and >= 0");
     cudaStream_t s = (cudaStream_t)stream;
     const size_t sino_n = (size_t)p->n_theta * p->n_det, img_n = (size_t)p->N * p->N;
     const size_t sino_pad = (sino_n + 3) & ~(size_t)3, img_pad = (img_n + 3) & ~(size_t)3;
-    if ((size_t)batch > p->stage_batch) {
+    const int S = std::min(batch, kHostSlots);
+    if ((size_t)S > p->stage_batch) {
         BP_CUDA_TRY(cudaStreamSynchronize(s));
         cudaFree(p->d_stage);
         p->d_stage = nullptr;
         p->stage_batch = 0;
-        BP_CUDA_TRY(cudaMalloc(&p->d_stage, sizeof(float) * (sino_pad + img_pad) * batch));
-        p->stage_batch = (size_t)batch;
+        BP_CUDA_TRY(cudaMalloc(&p->d_stage, sizeof(float) * (sino_pad + img_pad) * S));
+        p->stage_batch = (size_t)S;
     }
-    float *d_sino = p->d_stage;
-    float *d_img = p->d_stage + sino_pad * batch;
-    BP_CUDA_TRY(cudaMemcpyAsync(d_sino, sino, sizeof(float) * sino_n * batch, cudaMemcpyHostToDevice, s));
-    st = bp_filter(p, d_sino, BP_F32, d_sino, kind, param, batch, stream);
-    if (st != BP_OK) return st;
-    st = bp_backproject_direct(p, d_sino, BP_F32, d_img, batch, 0, stream);
-    if (st != BP_OK) return st;
-    BP_CUDA_TRY(cudaMemcpyAsync(img, d_img, sizeof(float) * img_n * batch, cudaMemcpyDeviceToHost, s));
+    if (!p->s_h2d) {
+        BP_CUDA_TRY(cudaStreamCreateWithFlags(&p->s_h2d, cudaStreamNonBlocking));
+        BP_CUDA_TRY(cudaStreamCreateWithFlags(&p->s_d2h, cudaStreamNonBlocking));
+        for (int k = 0; k < kHostSlots; ++k) {
+            BP_CUDA_TRY(cudaEventCreateWithFlags(&p->ev_h2d[k], cudaEventDisableTiming));
+            BP_CUDA_TRY(cudaEventCreateWithFlags(&p->ev_comp[k], cudaEventDisableTiming));
+            BP_CUDA_TRY(cudaEventCreateWithFlags(&p->ev_d2h[k], cudaEventDisableTiming));
+        }
+    }
+    for (int i = 0; i < batch; ++i) {
+        const int k = i % S;
+        float *d_sino = p->d_stage + (sino_pad + img_pad) * k;
+        float *d_img = d_sino + sino_pad;
+        if (i >= S) BP_CUDA_TRY(cudaStreamWaitEvent(p->s_h2d, p->ev_comp[k], 0));
+        BP_CUDA_TRY(cudaMemcpyAsync(d_sino, sino + sino_n * i, sizeof(float) * sino_n, cudaMemcpyHostToDevice,
+                                    p->s_h2d));
+        BP_CUDA_TRY(cudaEventRecord(p->ev_h2d[k], p->s_h2d));
+        BP_CUDA_TRY(cudaStreamWaitEvent(s, p->ev_h2d[k], 0));
+        if (i >= S) BP_CUDA_TRY(cudaStreamWaitEvent(s, p->ev_d2h[k], 0));
+        st = bp_filter(p, d_sino, BP_F32, d_sino, kind, param, 1, stream);
+        if (st != BP_OK) return st;
+        st = bp_backproject_direct(p, d_sino, BP_F32, d_img, 1, 0, stream);
+        if (st != BP_OK) return st;
+        BP_CUDA_TRY(cudaEventRecord(p->ev_comp[k], s));
+        BP_CUDA_TRY(cudaStreamWaitEvent(p->s_d2h, p->ev_comp[k], 0));
+        BP_CUDA_TRY(cudaMemcpyAsync(img + img_n * i, d_img, sizeof(float) * img_n, cudaMemcpyDeviceToHost, p->s_d2h));
+        BP_CUDA_TRY(cudaEventRecord(p->ev_d2h[k], p->s_d2h));
+    }
+    BP_CUDA_TRY(cudaStreamSynchronize(p->s_d2h));
     BP_CUDA_TRY(cudaStreamSynchronize(s));
     return BP_OK;
 }

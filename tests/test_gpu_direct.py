@@ -257,6 +257,16 @@ def test_fbp_host_matches_device_calls():
     assert oracle.rel_l2(out.numpy(), dev_img.cpu().numpy()) <= 1e-6  # atomic summation order
     out2 = plan.fbp_host(torch.stack([g, 2 * g]), "shepp-logan")
     assert torch.allclose(out2[1], 2 * out2[0], rtol=1e-6, atol=1e-6)
+    # five slices through the three-slot ring (copies of neighbouring slices overlap the
+    # kernels), pinned and pageable, each slice distinct
+    gs = torch.stack([g * (i + 1) + i for i in range(5)])
+    refs = [plan.backproject(plan.filter(gs[i].to(dev()), "shepp-logan")).cpu() for i in range(5)]
+    for src in (gs.pin_memory(), gs):
+        out5 = plan.fbp_host(src, "shepp-logan")
+        for i in range(5):
+            assert oracle.rel_l2(out5[i].numpy(), refs[i].numpy()) <= 1e-6, i
+    with pytest.raises(bp.BPError, match="lambda"):
+        plan.fbp_host(gs.pin_memory(), "tikhonov", -1.0)
 
 
 # ----------------------------------------------------------------------------------- persistent batched launch
