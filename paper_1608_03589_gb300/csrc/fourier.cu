@@ -412,8 +412,45 @@ ifft_pass_x_kernel(const float2 *__restrict__ inter, float *__restrict__ img, co
 // the current row is transformed (first pass from registers, radix-8 passes in shared memory,
 // last pass from registers straight to the pruned outputs).  Output i of a row is position
 // pos = i of the transform, i.e. image index (i + floor(N/2)) mod M when that is below N.
-//   XPASS false: rows l_x of G, inter[i_y][l_x] = z * deap[i_y];
+//   XPASS false: rows l_x of G in pairs (2p, 2p + 1); the first row's outputs wait in shared
+//                memory and leave with the second's as 16-byte pairs,
+//                inter[i_y][2p .. 2p + 1] = z * deap[i_y];
 //   XPASS true:  rows i_y of inter, img[i_y][i_x] = Re z * deap[i_x].
+template <int LOGM, bool XPASS>
+__host__ __device__ constexpr int ifft_pt_smem_elems() {
+    // work array, per-pass twiddles (even count), held first-row outputs (N <= M/2)
+    return (1 << LOGM) + pt_offset<LOGM>(PtPlan<LOGM>::npass) + (XPASS ? 0 : (1 << LOGM) / 2);
+}
+
+// One transform (inverse when INV) of the row whose first-pass inputs x[t + r NT] are in a:
+// outputs t + (g + q Gl) NT of the last pass in c[g][q].  Begins with a block barrier (the
+// previous row's reads of z are done).
+template <int LOGM, bool INV>
+__device__ __forceinline__ void pt_row(float2 (&a)[kPassE], float2 *z, const float2 *T, int t,
+                                       float2 (&c)[kPassE / PtPlan<LOGM>::Rl][PtPlan<LOGM>::Rl]) {
+    using PL = PtPlan<LOGM>;
+    constexpr int M = 1 << LOGM, NT = M / kPassE, Rl = PL::Rl, Gl = kPassE / Rl;
+    __syncthreads();
+    dft_reg<8>(a, INV);  // pass 0 (L = 1, radix 8)
+#pragma unroll
+    for (int q = 0; q < 8; ++q) z[fft_swz<kPassE>(t * 8 + q)] = a[q];
+    __syncthreads();
+    int L = 8;
+#pragma unroll
+    for (int p = 1; p < PL::n8; ++p) {
+        if (p == PL::npass - 1) break;
+        pt_pass<8, LOGM>(z, T + pt_offset<LOGM>(p), L, t, INV);
+        L *= 8;
+    }
+    constexpr int lp = PL::npass - 1, m = M / Rl;
+#pragma unroll
+    for (int g = 0; g < Gl; ++g)
+#pragma unroll
+        for (int r = 0; r < Rl; ++r) c[g][r] = z[fft_swz<kPassE>(t + g * NT + r * m)];
+#pragma unroll
+    for (int g = 0; g < Gl; ++g) pt_twiddle_dft<Rl>(c[g], T + pt_offset<LOGM>(lp), L, t + g * NT, INV);
+}
+
 template <int LOGM, bool XPASS>
 __global__ void __launch_bounds__((1 << LOGM) / kPassE, 1024 / ((1 << LOGM) / kPassE))
 ifft_pt_kernel(const float2 *__restrict__ in, float2 *__restrict__ inter, float *__restrict__ img,
@@ -423,8 +460,9 @@ ifft_pt_kernel(const float2 *__restrict__ in, float2 *__restrict__ inter, float 
     constexpr int TWN = pt_offset<LOGM>(PL::npass);
     static_assert(TWN % 2 == 0, "per-pass twiddle count");
     extern __shared__ __align__(16) float2 pz[];
-    float2 *z = pz;      // [M] work array
-    float2 *T = z + M;   // [TWN] per-pass twiddles
+    float2 *z = pz;          // [M] work array
+    float2 *T = z + M;       // [TWN] per-pass twiddles
+    float2 *hold = T + TWN;  // [M/2] first row's outputs of a pair, by image index (y pass)
     const int t = threadIdx.x;
     const int h = N / 2;
     float2 nxt[kPassE];  // inputs of the first pass: x[t + r NT]
@@ -433,7 +471,8 @@ ifft_pt_kernel(const float2 *__restrict__ in, float2 *__restrict__ inter, float 
 #pragma unroll
         for (int r = 0; r < kPassE; ++r) nxt[r] = __ldg(src + t + r * NT);
     };
-    int row = blockIdx.x;
+    // the first row's loads are in flight while the twiddle table is staged
+    int row = XPASS ? blockIdx.x : 2 * blockIdx.x;
     if (row < rows) fetch(row);
     {
         constexpr int n4t = TWN / 2;  // float4 loads; T starts 16-byte aligned (M even)
@@ -443,43 +482,52 @@ ifft_pt_kernel(const float2 *__restrict__ in, float2 *__restrict__ inter, float 
         for (int i = 0; i < (n4t + NT - 1) / NT; ++i)
             if (t + i * NT < n4t) td[t + i * NT] = __ldg(ts + t + i * NT);
     }
-    for (; row < rows; row += gridDim.x) {
-        float2 a[kPassE];
+    if constexpr (XPASS) {
+        for (; row < rows; row += gridDim.x) {
+            float2 a[kPassE];
 #pragma unroll
-        for (int r = 0; r < kPassE; ++r) a[r] = nxt[r];
-        if (row + gridDim.x < rows) fetch(row + gridDim.x);
-        __syncthreads();  // previous row's last reads of z (and the staged table) are done
-        dft_reg<8>(a, true);  // pass 0 (L = 1, radix 8)
+            for (int r = 0; r < kPassE; ++r) a[r] = nxt[r];
+            if (row + (int)gridDim.x < rows) fetch(row + gridDim.x);
+            float2 c[Gl][Rl];
+            pt_row<LOGM, true>(a, z, T, t, c);
 #pragma unroll
-        for (int q = 0; q < 8; ++q) z[fft_swz<kPassE>(t * 8 + q)] = a[q];
-        __syncthreads();
-        int L = 8;
+            for (int g = 0; g < Gl; ++g)
 #pragma unroll
-        for (int p = 1; p < PL::n8; ++p) {
-            if (p == PL::npass - 1) break;
-            pt_pass<8, LOGM>(z, T + pt_offset<LOGM>(p), L, t, true);
-            L *= 8;
-        }
-        // last pass: outputs t + (g + q Gl) NT
-        constexpr int lp = PL::npass - 1, m = M / Rl;
-        float2 c[Gl][Rl];
-#pragma unroll
-        for (int g = 0; g < Gl; ++g)
-#pragma unroll
-            for (int r = 0; r < Rl; ++r) c[g][r] = z[fft_swz<kPassE>(t + g * NT + r * m)];
-#pragma unroll
-        for (int g = 0; g < Gl; ++g) {
-            pt_twiddle_dft<Rl>(c[g], T + pt_offset<LOGM>(lp), L, t + g * NT, true);
-#pragma unroll
-            for (int q = 0; q < Rl; ++q) {
-                const int i = t + (g + q * Gl) * NT;
-                const int o = i < N - h ? i + h : i - (M - h);  // image index, valid in [0, N)
-                if (o >= 0 && o < N) {
-                    const float d = __ldg(deap + o);
-                    if (XPASS) img[(long long)row * N + o] = c[g][q].x * d;
-                    else inter[(long long)o * M + row] = make_float2(c[g][q].x * d, c[g][q].y * d);
+                for (int q = 0; q < Rl; ++q) {
+                    const int i = t + (g + q * Gl) * NT;
+                    const int o = i < N - h ? i + h : i - (M - h);  // image index, valid in [0, N)
+                    if (o >= 0 && o < N) img[(long long)row * N + o] = c[g][q].x * __ldg(deap + o);
                 }
-            }
+        }
+    } else {
+        // rows 2p, 2p + 1 (p = b, b + G, ...): the first row's outputs wait in shared memory
+        // (read back by the same thread) and leave with the second's as 16-byte pairs
+        for (; row < rows; row = (row & 1) ? row - 1 + 2 * (int)gridDim.x : row + 1) {
+            float2 a[kPassE];
+#pragma unroll
+            for (int r = 0; r < kPassE; ++r) a[r] = nxt[r];
+            const int nr = (row & 1) ? row - 1 + 2 * (int)gridDim.x : row + 1;
+            if (nr < rows) fetch(nr);
+            float2 c[Gl][Rl];
+            pt_row<LOGM, true>(a, z, T, t, c);
+#pragma unroll
+            for (int g = 0; g < Gl; ++g)
+#pragma unroll
+                for (int q = 0; q < Rl; ++q) {
+                    const int i = t + (g + q * Gl) * NT;
+                    const int o = i < N - h ? i + h : i - (M - h);
+                    if (o >= 0 && o < N) {
+                        const float d = __ldg(deap + o);
+                        const float2 v = make_float2(c[g][q].x * d, c[g][q].y * d);
+                        if (!(row & 1)) {
+                            hold[o] = v;
+                        } else {
+                            const float2 u = hold[o];
+                            *reinterpret_cast<float4 *>(inter + (long long)o * M + row - 1) =
+                                make_float4(u.x, u.y, v.x, v.y);
+                        }
+                    }
+                }
         }
     }
 }
@@ -614,6 +662,75 @@ fft_pt_fwd_kernel(const float *__restrict__ img, const float2 *__restrict__ Tin,
             pt_twiddle_dft<Rl>(c[g], T + pt_offset<LOGM>(lp), L, t + g * NT, false);
 #pragma unroll
             for (int q = 0; q < Rl; ++q) dst[t + (g + q * Gl) * NT] = c[g][q];
+        }
+    }
+}
+
+// The adjoint's column pass when N = M/2 (the usual power-of-two case): columns in pairs
+// (2p, 2p + 1), read as 16-byte pairs T[i_y][2p .. 2p + 1].  Then only the first-pass inputs
+// r = 0, 1, 6, 7 of a thread are inside the image (positions t + r NT below M/4 or from 3M/4
+// on); the second column's values wait in shared memory (the thread's own slots) while the
+// first column is transformed, and the next pair's loads are in flight during both.
+template <int LOGM>
+__global__ void __launch_bounds__((1 << LOGM) / kPassE, 1024 / ((1 << LOGM) / kPassE))
+fft_pt_fwd_cols_kernel(const float2 *__restrict__ Tin, float2 *__restrict__ out, const float2 *__restrict__ twp,
+                       int rows) {
+    using PL = PtPlan<LOGM>;
+    constexpr int M = 1 << LOGM, NT = M / kPassE, Rl = PL::Rl, Gl = kPassE / Rl;
+    constexpr int TWN = pt_offset<LOGM>(PL::npass);
+    constexpr int N = M / 2, h = N / 2;
+    constexpr int RV[4] = {0, 1, kPassE - 2, kPassE - 1};  // the inputs inside the image
+    static_assert(TWN % 2 == 0, "per-pass twiddle count");
+    extern __shared__ __align__(16) float2 pz[];
+    float2 *z = pz;          // [M] work array
+    float2 *T = z + M;       // [TWN] per-pass twiddles
+    float2 *hold = T + TWN;  // [4 NT] second column's inputs
+    const int t = threadIdx.x;
+    float4 nxt[4];
+    auto fetch = [&](int pair) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int pos = t + RV[j] * NT;
+            const int o = pos < N - h ? pos + h : pos - (M - h);
+            nxt[j] = __ldg(reinterpret_cast<const float4 *>(Tin + (long long)o * M + 2 * pair));
+        }
+    };
+    const int npairs = rows / 2;
+    int pair = blockIdx.x;
+    if (pair < npairs) fetch(pair);
+    {
+        constexpr int n4t = TWN / 2;
+        const float4 *ts = reinterpret_cast<const float4 *>(twp);
+        float4 *td = reinterpret_cast<float4 *>(T);
+#pragma unroll
+        for (int i = 0; i < (n4t + NT - 1) / NT; ++i)
+            if (t + i * NT < n4t) td[t + i * NT] = __ldg(ts + t + i * NT);
+    }
+    for (; pair < npairs; pair += gridDim.x) {
+        float2 a[kPassE];
+#pragma unroll
+        for (int r = 0; r < kPassE; ++r) a[r] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            a[RV[j]] = make_float2(nxt[j].x, nxt[j].y);
+            hold[j * NT + t] = make_float2(nxt[j].z, nxt[j].w);
+        }
+        if (pair + (int)gridDim.x < npairs) fetch(pair + gridDim.x);
+#pragma unroll 1
+        for (int half = 0; half < 2; ++half) {
+            if (half) {
+#pragma unroll
+                for (int r = 0; r < kPassE; ++r) a[r] = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) a[RV[j]] = hold[j * NT + t];
+            }
+            float2 c[Gl][Rl];
+            pt_row<LOGM, false>(a, z, T, t, c);
+            float2 *dst = out + (long long)(2 * pair + half) * M;
+#pragma unroll
+            for (int g = 0; g < Gl; ++g)
+#pragma unroll
+                for (int q = 0; q < Rl; ++q) dst[t + (g + q * Gl) * NT] = c[g][q];
         }
     }
 }
@@ -905,16 +1022,21 @@ template <int LOGM>
 static bp_status launch_ifft_pt(bp_plan *p, const float *deap, float *img, cudaStream_t st) {
     FourierWork &f = p->four;
     constexpr int M = 1 << LOGM, NT = M / kPassE;
-    constexpr size_t smem = sizeof(float2) * (M + pt_offset<LOGM>(PtPlan<LOGM>::npass));
+    constexpr size_t smem_y = sizeof(float2) * ifft_pt_smem_elems<LOGM, false>();
+    constexpr size_t smem_x = sizeof(float2) * ifft_pt_smem_elems<LOGM, true>();
     auto ky = ifft_pt_kernel<LOGM, false>;
     auto kx = ifft_pt_kernel<LOGM, true>;
-    BP_CUDA_TRY(cudaFuncSetAttribute(ky, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    BP_CUDA_TRY(cudaFuncSetAttribute(kx, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int per_sm = 0;
-    BP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ky, NT, smem));
-    const int ctas = std::max(1, per_sm) * std::max(1, p->sm_count);
-    ky<<<std::min(ctas, M), NT, smem, st>>>(f.grid, f.mid, nullptr, deap, f.twpassM, M, p->N);
-    kx<<<std::min(ctas, p->N), NT, smem, st>>>(f.mid, nullptr, img, deap, f.twpassM, p->N, p->N);
+    BP_CUDA_TRY(cudaFuncSetAttribute(ky, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_y));
+    BP_CUDA_TRY(cudaFuncSetAttribute(kx, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_x));
+    int per_sm_y = 0, per_sm_x = 0;
+    BP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_y, ky, NT, smem_y));
+    BP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_x, kx, NT, smem_x));
+    const int sms = std::max(1, p->sm_count);
+    // the y pass takes rows in pairs (M is even)
+    ky<<<std::min(std::max(1, per_sm_y) * sms, M / 2), NT, smem_y, st>>>(f.grid, f.mid, nullptr, deap, f.twpassM, M,
+                                                                        p->N);
+    kx<<<std::min(std::max(1, per_sm_x) * sms, p->N), NT, smem_x, st>>>(f.mid, nullptr, img, deap, f.twpassM, p->N,
+                                                                       p->N);
     BP_CUDA_TRY(cudaGetLastError());
     return BP_OK;
 }
@@ -987,7 +1109,18 @@ static bp_status launch_fft_pt_fwd(bp_plan *p, const float *img, cudaStream_t st
     BP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kx, NT, smem));
     const int ctas = std::max(1, per_sm) * std::max(1, p->sm_count);
     kx<<<std::min(ctas, p->N), NT, smem, st>>>(img, nullptr, f.mid, f.deapod, f.twpassM, p->N, p->N);
-    ky<<<std::min(ctas, M), NT, smem, st>>>(nullptr, f.mid, f.grid, f.deapod, f.twpassM, M, p->N);
+    if (2 * p->N == M) {
+        // columns in pairs, 16-byte loads
+        constexpr size_t smem2 = smem + sizeof(float2) * (M / 2);
+        auto kc = fft_pt_fwd_cols_kernel<LOGM>;
+        BP_CUDA_TRY(cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2));
+        int per_sm2 = 0;
+        BP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, kc, NT, smem2));
+        kc<<<std::min(std::max(1, per_sm2) * std::max(1, p->sm_count), M / 2), NT, smem2, st>>>(f.mid, f.grid,
+                                                                                               f.twpassM, M);
+    } else {
+        ky<<<std::min(ctas, M), NT, smem, st>>>(nullptr, f.mid, f.grid, f.deapod, f.twpassM, M, p->N);
+    }
     BP_CUDA_TRY(cudaGetLastError());
     return BP_OK;
 }
