@@ -52,6 +52,9 @@ struct FourierWork {
     float2 *kbtab = nullptr;    // Kaiser-Bessel kernel table
     float rmax = 0.f;           // largest sample radius (grid cells) plus a margin
     RayIndex ri;                // sorted-angle lookup (gather gridding)
+    int4 *adj_items = nullptr;  // adjoint interpolation work items: tile, first segment, segments, samples
+    int4 *adj_segs = nullptr;   // their ray segments: projection, first sample, samples, offset in the item
+    int adj_n_items = 0;
     size_t bytes = 0;
 };
 

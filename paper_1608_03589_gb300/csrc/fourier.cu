@@ -61,6 +61,15 @@ __device__ __forceinline__ float kb_tab(const float2 *__restrict__ tab, float d)
     return fmaf(x - (float)i, v.y, v.x);
 }
 
+// The same lookup from a copy of the table in shared memory.
+template <int HW>
+__device__ __forceinline__ float kb_tab_s(const float2 *tab, float d) {
+    const float x = fminf(fabsf(d) * ((float)kKB / (float)HW), (float)kKB - 1e-3f);
+    const int i = (int)x;
+    const float2 v = tab[i];
+    return fmaf(x - (float)i, v.y, v.x);
+}
+
 __device__ __forceinline__ float2 half_pixel_phase(const long long *__restrict__ r, int m, float delta2_over_M) {
     const long long zx = (long long)m * r[0], zy = (long long)m * r[1];
     const float rx = (float)(unsigned)(zx & 0xffffffffLL) * 2.3283064365386963e-10f;
@@ -735,6 +744,84 @@ fft_pt_fwd_cols_kernel(const float2 *__restrict__ Tin, float2 *__restrict__ out,
     }
 }
 
+// Interpolation at the polar samples by grid tiles (the form used when the work items
+// exist): sample (k, m) belongs to the kAdjTile x kAdjTile tile holding its lowest cell
+// floor(z) (the same 32.32 fixed-point floor as below); one CTA per work item (a run of ray
+// segments of one tile, at most kAdjItemSamples samples) stages the tile and its kernel halo in
+// shared memory with coalesced row loads, and its threads read the 2 HW x 2 HW neighbourhoods
+// from there.  Same result as adj_interp_kernel.
+constexpr int kAdjTile = 64;
+constexpr int kAdjItemSamples = 2048;
+constexpr int kAdjItemSegs = 256;
+
+template <int HW>
+__global__ void __launch_bounds__(256)
+adj_interp_tiled_kernel(const float2 *__restrict__ grid, float2 *__restrict__ spec, const long long *__restrict__ ray,
+                        const int4 *__restrict__ items, const int4 *__restrict__ segs, int M, int H, int P, int n_det,
+                        const float2 *__restrict__ tab, float delta2_over_M, float scale,
+                        const float *__restrict__ wk) {
+    constexpr int W = 2 * HW, S = kAdjTile + W - 1;
+    __shared__ float2 tile[S * S];           // cells x0 .. x0 + S - 1 by y0 .. y0 + S - 1 (mod M)
+    __shared__ int4 sseg[kAdjItemSegs];
+    __shared__ float2 stab[kKB + 1];         // the kernel table (its lookups are scattered)
+    __shared__ unsigned short seg_of[kAdjItemSamples];  // segment of each sample of the item
+    const int4 it = __ldg(items + blockIdx.x);  // tile (tx nt + ty), first segment, segments, samples
+    const int nt = M / kAdjTile;
+    const int tx = it.x / nt, ty = it.x - tx * nt;
+    const int Mmask = M - 1;
+    const int x0 = tx * kAdjTile - (HW - 1), y0 = ty * kAdjTile - (HW - 1);
+    for (int i = threadIdx.x; i < S * S; i += blockDim.x) {
+        const int xi = i / S, yi = i - xi * S;
+        tile[i] = __ldg(grid + (long long)((x0 + xi) & Mmask) * M + ((y0 + yi) & Mmask));
+    }
+    for (int i = threadIdx.x; i < it.z; i += blockDim.x) sseg[i] = __ldg(segs + it.y + i);
+    {
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+        for (int j = warp; j < it.z; j += nw) {
+            const int4 sg = __ldg(segs + it.y + j);
+            for (int i = lane; i < sg.z; i += 32) seg_of[sg.w + i] = (unsigned short)j;
+        }
+    }
+    for (int i = threadIdx.x; i <= kKB; i += blockDim.x) stab[i] = __ldg(tab + i);
+    __syncthreads();
+    for (int sidx = threadIdx.x; sidx < it.w; sidx += blockDim.x) {
+        const int4 sg = sseg[seg_of[sidx]];
+        const int k = sg.x, m = sg.y + (sidx - sg.w);
+        const long long zx = (long long)m * __ldg(ray + 2 * k), zy = (long long)m * __ldg(ray + 2 * k + 1);
+        const int fx = (int)(zx >> 32), fy = (int)(zy >> 32);
+        const float rx = (float)(unsigned)(zx & 0xffffffffLL) * 2.3283064365386963e-10f;
+        const float ry = (float)(unsigned)(zy & 0xffffffffLL) * 2.3283064365386963e-10f;
+        float wy[W];
+#pragma unroll
+        for (int t = 0; t < W; ++t) wy[t] = kb_tab_s<HW>(stab, (float)(t - (HW - 1)) - ry);
+        // tile-local row and column of the window's first cell, in [0, kAdjTile)
+        const int lxl = (fx & Mmask) - tx * kAdjTile, lyl = (fy & Mmask) - ty * kAdjTile;
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int t = 0; t < W; ++t) {
+            const float wx = kb_tab_s<HW>(stab, (float)(t - (HW - 1)) - rx);
+            const float2 *row = tile + (lxl + t) * S + lyl;
+            float2 r = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int u = 0; u < W; ++u) {
+                const float2 v = row[u];
+                r.x = fmaf(wy[u], v.x, r.x);
+                r.y = fmaf(wy[u], v.y, r.y);
+            }
+            acc.x = fmaf(wx, r.x, acc.x);
+            acc.y = fmaf(wx, r.y, acc.y);
+        }
+        float sn, cs;
+        sincospif(-((float)(fx + fy) + (rx + ry)) * delta2_over_M, &sn, &cs);
+        acc = cmul(acc, make_float2(cs, sn));
+        const long long ph = ((long long)m * (n_det - 1)) % (2LL * P);
+        sincospif(-(float)ph / (float)P, &sn, &cs);
+        acc = cmul(acc, make_float2(cs, sn));
+        const float f = (m == 0 ? 1.f : 2.f) * (wk ? __ldg(wk + k) : scale) / (float)P;
+        spec[(long long)k * H + m] = make_float2(f * acc.x, f * acc.y);
+    }
+}
+
 // Interpolation at the polar samples (transpose of the spreading): one thread per sample,
 // consecutive samples of one ray in consecutive lanes; result times the conjugate sample
 // factor (1/P)(m ? 2 : 1) exp(-i pi m (n_det-1)/P) exp(-2 pi i delta (z_x + z_y)/M) and dx^2/dt.
@@ -848,6 +935,8 @@ void free_fourier(bp_plan *p) {
     cudaFree(f.sray);
     cudaFree(f.sphi);
     cudaFree(f.kbtab);
+    cudaFree(f.adj_items);
+    cudaFree(f.adj_segs);
     f = FourierWork();
 }
 
@@ -1095,6 +1184,71 @@ bp_status launch_fourier(bp_plan *p, const void *sino, bp_dtype dt, float *img, 
     return BP_OK;
 }
 
+// Work items of adj_interp_tiled_kernel (once per plan, after ensure_fourier): every sample
+// (k, m), m < H, binned by the tile of floor(z) with the device's fixed-point products, runs
+// of consecutive m on one ray in one tile as segments, a tile's segments cut into items of at
+// most kAdjItemSamples samples and kAdjItemSegs segments.
+static bp_status ensure_adj_items(bp_plan *p) {
+    FourierWork &f = p->four;
+    if (f.adj_items) return BP_OK;
+    const int M = f.M, H = p->P / 2, n = p->n_theta;
+    if (M % kAdjTile) return BP_OK;  // no items: the per-sample kernel runs
+    const int nt = M / kAdjTile;
+    std::vector<long long> ray(2 * (size_t)n);
+    BP_CUDA_TRY(cudaMemcpy(ray.data(), f.ray, sizeof(long long) * ray.size(), cudaMemcpyDeviceToHost));
+    std::vector<std::vector<int4>> per_tile((size_t)nt * nt);  // (k, m0, count, -)
+    for (int k = 0; k < n; ++k) {
+        int cur = -1, m0 = 0;
+        for (int m = 0; m <= H; ++m) {
+            int tile = -1;
+            if (m < H) {
+                const long long zx = (long long)m * ray[2 * k], zy = (long long)m * ray[2 * k + 1];
+                const int fx = (int)(zx >> 32) & (M - 1), fy = (int)(zy >> 32) & (M - 1);
+                tile = (fx / kAdjTile) * nt + fy / kAdjTile;
+            }
+            if (tile != cur) {
+                if (cur >= 0) per_tile[cur].push_back(make_int4(k, m0, m - m0, 0));
+                cur = tile;
+                m0 = m;
+            }
+        }
+    }
+    std::vector<int4> items, segs;
+    for (int t = 0; t < nt * nt; ++t) {
+        int4 item = make_int4(t, (int)segs.size(), 0, 0);
+        auto close = [&]() {
+            if (item.z > 0) items.push_back(item);
+            item = make_int4(t, (int)segs.size(), 0, 0);
+        };
+        for (int4 sg : per_tile[t]) {
+            while (sg.z > 0) {
+                if (item.z == kAdjItemSegs || item.w == kAdjItemSamples) close();
+                const int take = std::min(sg.z, kAdjItemSamples - item.w);
+                segs.push_back(make_int4(sg.x, sg.y, take, item.w));
+                item.z += 1;
+                item.w += take;
+                sg.y += take;
+                sg.z -= take;
+            }
+        }
+        close();
+    }
+    cudaError_t e = cudaMalloc(&f.adj_items, sizeof(int4) * std::max<size_t>(items.size(), 1));
+    if (e == cudaSuccess) e = cudaMalloc(&f.adj_segs, sizeof(int4) * std::max<size_t>(segs.size(), 1));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(f.adj_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(f.adj_segs, segs.data(), sizeof(int4) * segs.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(f.adj_items);
+        cudaFree(f.adj_segs);
+        f.adj_items = f.adj_segs = nullptr;
+        return cuda_fail(e, "adjoint interpolation work items");
+    }
+    f.adj_n_items = (int)items.size();
+    f.bytes += sizeof(int4) * (items.size() + segs.size());
+    return BP_OK;
+}
+
 // The persistent adjoint passes for one M (grid as in launch_ifft_pt).
 template <int LOGM>
 static bp_status launch_fft_pt_fwd(bp_plan *p, const float *img, cudaStream_t st) {
@@ -1129,6 +1283,7 @@ bp_status launch_radon_fourier(bp_plan *p, const float *img, float *sino, int ba
                                int per_angle_w) {
     bp_status s = ensure_fourier(p);
     if (s != BP_OK) return s;
+    if ((s = ensure_adj_items(p)) != BP_OK) return s;
     FourierWork &f = p->four;
     const int N = p->N, M = f.M, P = p->P, H = P / 2;
     const int R = rows_per_cta(M);
@@ -1157,9 +1312,15 @@ bp_status launch_radon_fourier(bp_plan *p, const float *img, float *sino, int ba
                 ky<<<M / R, nthr * groups, smemR, st>>>(f.mid, f.grid, f.twM, M, f.logM, N, R);
         }
         if (s != BP_OK) return s;
-        auto ki = f.W == 4 ? adj_interp_kernel<2> : adj_interp_kernel<3>;
-        ki<<<dim3((H + 255) / 256, p->n_theta), 256, 0, st>>>(f.grid, f.spec, f.ray, M, H, P, p->n_det, f.kbtab, delta2,
-                                                               scale, per_angle_w ? f.wk : nullptr);
+        if (f.adj_items) {
+            auto kt = f.W == 4 ? adj_interp_tiled_kernel<2> : adj_interp_tiled_kernel<3>;
+            kt<<<f.adj_n_items, 256, 0, st>>>(f.grid, f.spec, f.ray, f.adj_items, f.adj_segs, M, H, P, p->n_det,
+                                              f.kbtab, delta2, scale, per_angle_w ? f.wk : nullptr);
+        } else {
+            auto ki = f.W == 4 ? adj_interp_kernel<2> : adj_interp_kernel<3>;
+            ki<<<dim3((H + 255) / 256, p->n_theta), 256, 0, st>>>(f.grid, f.spec, f.ray, M, H, P, p->n_det, f.kbtab,
+                                                                   delta2, scale, per_angle_w ? f.wk : nullptr);
+        }
         kr<<<(p->n_theta + 1) / 2, fft_threads(P), sizeof(float2) * (P + P / 2), st>>>(
             f.spec, sino + (size_t)b * p->n_theta * p->n_det, p->d_twP, p->n_theta, p->n_det, ilog2(P));
         BP_CUDA_TRY(cudaGetLastError());
