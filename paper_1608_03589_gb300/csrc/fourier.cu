@@ -754,6 +754,13 @@ constexpr int kAdjTile = 64;
 constexpr int kAdjItemSamples = 2048;
 constexpr int kAdjItemSegs = 256;
 
+// Dynamic shared memory of adj_interp_tiled_kernel<HW>: segments, tile with halo, kernel
+// table, sample -> segment index.
+__host__ __device__ constexpr size_t adj_tiled_smem(int HW) {
+    return sizeof(int4) * kAdjItemSegs + sizeof(float2) * ((size_t)(kAdjTile + 2 * HW - 1) * (kAdjTile + 2 * HW - 1)) +
+           sizeof(float2) * (kKB + 1) + sizeof(unsigned short) * kAdjItemSamples;
+}
+
 template <int HW>
 __global__ void __launch_bounds__(256)
 adj_interp_tiled_kernel(const float2 *__restrict__ grid, float2 *__restrict__ spec, const long long *__restrict__ ray,
@@ -761,10 +768,11 @@ adj_interp_tiled_kernel(const float2 *__restrict__ grid, float2 *__restrict__ sp
                         const float2 *__restrict__ tab, float delta2_over_M, float scale,
                         const float *__restrict__ wk) {
     constexpr int W = 2 * HW, S = kAdjTile + W - 1;
-    __shared__ float2 tile[S * S];           // cells x0 .. x0 + S - 1 by y0 .. y0 + S - 1 (mod M)
-    __shared__ int4 sseg[kAdjItemSegs];
-    __shared__ float2 stab[kKB + 1];         // the kernel table (its lookups are scattered)
-    __shared__ unsigned short seg_of[kAdjItemSamples];  // segment of each sample of the item
+    extern __shared__ __align__(16) float2 adj_sm[];
+    int4 *sseg = reinterpret_cast<int4 *>(adj_sm);            // [kAdjItemSegs]
+    float2 *tile = adj_sm + 2 * kAdjItemSegs;                 // [S * S] cells x0.., y0.. (mod M)
+    float2 *stab = tile + S * S;                              // [kKB + 1] the kernel table (scattered lookups)
+    unsigned short *seg_of = reinterpret_cast<unsigned short *>(stab + kKB + 1);  // [kAdjItemSamples]
     const int4 it = __ldg(items + blockIdx.x);  // tile (tx nt + ty), first segment, segments, samples
     const int nt = M / kAdjTile;
     const int tx = it.x / nt, ty = it.x - tx * nt;
@@ -1314,8 +1322,10 @@ bp_status launch_radon_fourier(bp_plan *p, const float *img, float *sino, int ba
         if (s != BP_OK) return s;
         if (f.adj_items) {
             auto kt = f.W == 4 ? adj_interp_tiled_kernel<2> : adj_interp_tiled_kernel<3>;
-            kt<<<f.adj_n_items, 256, 0, st>>>(f.grid, f.spec, f.ray, f.adj_items, f.adj_segs, M, H, P, p->n_det,
-                                              f.kbtab, delta2, scale, per_angle_w ? f.wk : nullptr);
+            const size_t sm = adj_tiled_smem(f.W / 2);
+            BP_CUDA_TRY(cudaFuncSetAttribute(kt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+            kt<<<f.adj_n_items, 256, sm, st>>>(f.grid, f.spec, f.ray, f.adj_items, f.adj_segs, M, H, P, p->n_det,
+                                               f.kbtab, delta2, scale, per_angle_w ? f.wk : nullptr);
         } else {
             auto ki = f.W == 4 ? adj_interp_kernel<2> : adj_interp_kernel<3>;
             ki<<<dim3((H + 255) / 256, p->n_theta), 256, 0, st>>>(f.grid, f.spec, f.ray, M, H, P, p->n_det, f.kbtab,
