@@ -66,4 +66,33 @@ __host__ __device__ constexpr int pt_offset(int p) {
     return off;
 }
 
+// One transform (inverse when INV) of the row whose first-pass inputs x[t + r NT] are in a:
+// outputs t + (g + q Gl) NT of the last pass in c[g][q].  Begins with a block barrier (the
+// previous row's reads of z are done).
+template <int LOGM, bool INV>
+__device__ __forceinline__ void pt_row(float2 (&a)[kPassE], float2 *z, const float2 *T, int t,
+                                       float2 (&c)[kPassE / PtPlan<LOGM>::Rl][PtPlan<LOGM>::Rl]) {
+    using PL = PtPlan<LOGM>;
+    constexpr int M = 1 << LOGM, NT = M / kPassE, Rl = PL::Rl, Gl = kPassE / Rl;
+    __syncthreads();
+    dft_reg<8>(a, INV);  // pass 0 (L = 1, radix 8)
+#pragma unroll
+    for (int q = 0; q < 8; ++q) z[fft_swz<kPassE>(t * 8 + q)] = a[q];
+    __syncthreads();
+    int L = 8;
+#pragma unroll
+    for (int p = 1; p < PL::n8; ++p) {
+        if (p == PL::npass - 1) break;
+        pt_pass<8, LOGM>(z, T + pt_offset<LOGM>(p), L, t, INV);
+        L *= 8;
+    }
+    constexpr int lp = PL::npass - 1, m = M / Rl;
+#pragma unroll
+    for (int g = 0; g < Gl; ++g)
+#pragma unroll
+        for (int r = 0; r < Rl; ++r) c[g][r] = z[fft_swz<kPassE>(t + g * NT + r * m)];
+#pragma unroll
+    for (int g = 0; g < Gl; ++g) pt_twiddle_dft<Rl>(c[g], T + pt_offset<LOGM>(lp), L, t + g * NT, INV);
+}
+
 }  // namespace bp

@@ -147,6 +147,127 @@ fourier_spectra_kernel(const Tin *__restrict__ sino, float2 *__restrict__ spec, 
     }
 }
 
+// Persistent form of (1) for P = 2^9 .. 2^12 (per-pass twiddles, next pair's loads in flight
+// during the current transforms).  The rows fill the first half of the zero-padded row, so
+// only the first-pass inputs x[t + r NT], r < 4, are loaded.  With the fused filter the
+// forward transform's outputs, times H, are the inverse transform's first-pass inputs in
+// registers, and the inverse's outputs, cut to the detector, those of the second forward
+// transform.  The last transform's outputs go to shared memory for the split into the two
+// half spectra (as in (1)).
+template <int LOGP>
+__device__ __forceinline__ void pt_regs_to_inputs(float2 (&c)[kPassE / PtPlan<LOGP>::Rl][PtPlan<LOGP>::Rl],
+                                                  float2 (&a)[kPassE]) {
+    constexpr int Rl = PtPlan<LOGP>::Rl, Gl = kPassE / Rl;
+    // last-pass output t + (g + q Gl) NT is first-pass input r = g + q Gl
+#pragma unroll
+    for (int g = 0; g < Gl; ++g)
+#pragma unroll
+        for (int q = 0; q < Rl; ++q) a[g + q * Gl] = c[g][q];
+}
+
+template <typename Tin, int LOGP>
+__global__ void __launch_bounds__((1 << LOGP) / kPassE, 1024 / ((1 << LOGP) / kPassE))
+fourier_spectra_pt_kernel(const Tin *__restrict__ sino, float2 *__restrict__ spec, const float *__restrict__ wk,
+                          const float2 *__restrict__ twp, int n_theta, int n_det, float wuni,
+                          const long long *__restrict__ ray, float delta2_over_M, const float *__restrict__ Hf) {
+    using PL = PtPlan<LOGP>;
+    constexpr int P = 1 << LOGP, H = P / 2, NT = P / kPassE;
+    constexpr int TWN = pt_offset<LOGP>(PL::npass);
+    extern __shared__ __align__(16) float2 sp_sm[];
+    float2 *z = sp_sm;     // [P]
+    float2 *T = z + P;     // [TWN]
+    const int t = threadIdx.x;
+    const int npairs = (n_theta + 1) / 2;
+    float2 nxt[4];
+    auto fetch = [&](int pair) {
+        const int k0 = 2 * pair;
+        const bool has1 = k0 + 1 < n_theta;
+        const Tin *a = sino + (long long)k0 * n_det, *b = a + n_det;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int j = t + r * NT;
+            float va = 0.f, vb = 0.f;
+            if (j < n_det) {
+                va = load_f(a + j);
+                if (has1) vb = load_f(b + j);
+            }
+            nxt[r] = make_float2(va, vb);
+        }
+    };
+    int pair = blockIdx.x;
+    if (pair < npairs) fetch(pair);
+    {
+        constexpr int n4t = TWN / 2;
+        const float4 *ts = reinterpret_cast<const float4 *>(twp);
+        float4 *td = reinterpret_cast<float4 *>(T);
+#pragma unroll
+        for (int i = 0; i < (n4t + NT - 1) / NT; ++i)
+            if (t + i * NT < n4t) td[t + i * NT] = __ldg(ts + t + i * NT);
+    }
+    constexpr int Rl = PL::Rl, Gl = kPassE / Rl;
+    for (; pair < npairs; pair += gridDim.x) {
+        const int k0 = 2 * pair, k1 = k0 + 1;
+        const bool has1 = k1 < n_theta;
+        float2 a[kPassE];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) a[r] = nxt[r];
+#pragma unroll
+        for (int r = 4; r < kPassE; ++r) a[r] = make_float2(0.f, 0.f);
+        if (pair + (int)gridDim.x < npairs) fetch(pair + gridDim.x);
+        float2 c[Gl][Rl];
+        pt_row<LOGP, false>(a, z, T, t, c);
+        if (Hf) {
+            // times the response (dt/P included), inverse transform, cut to the detector (an
+            // unpaired last projection keeps a zero partner row), transformed again
+#pragma unroll
+            for (int g = 0; g < Gl; ++g)
+#pragma unroll
+                for (int q = 0; q < Rl; ++q) {
+                    const float hv = __ldg(Hf + t + (g + q * Gl) * NT);
+                    c[g][q] = make_float2(c[g][q].x * hv, c[g][q].y * hv);
+                }
+            pt_regs_to_inputs<LOGP>(c, a);
+            pt_row<LOGP, true>(a, z, T, t, c);
+            pt_regs_to_inputs<LOGP>(c, a);
+#pragma unroll
+            for (int r = 0; r < kPassE; ++r) {
+                const int j = t + r * NT;
+                if (j >= n_det) a[r] = make_float2(0.f, 0.f);
+                else if (!has1) a[r].y = 0.f;
+            }
+            pt_row<LOGP, false>(a, z, T, t, c);
+        }
+        __syncthreads();  // every thread's last-pass reads of z are done
+#pragma unroll
+        for (int g = 0; g < Gl; ++g)
+#pragma unroll
+            for (int q = 0; q < Rl; ++q) z[t + (g + q * Gl) * NT] = c[g][q];
+        __syncthreads();
+        // A[m] = (Z[m] + conj Z[P-m]) / 2,  B[m] = (Z[m] - conj Z[P-m]) / (2i)
+        const float wa = (wuni > 0.f ? wuni : __ldg(wk + k0)) / (float)P;
+        const float wb = has1 ? (wuni > 0.f ? wuni : __ldg(wk + k1)) / (float)P : 0.f;
+        const long long twoP = 2LL * P;
+        for (int m = t; m < H; m += NT) {
+            const float2 zm = z[m];
+            const float2 zc = z[(P - m) & (P - 1)];
+            const float2 A = make_float2(0.5f * (zm.x + zc.x), 0.5f * (zm.y - zc.y));
+            const float2 B = make_float2(0.5f * (zm.y + zc.y), -0.5f * (zm.x - zc.x));
+            const long long r = ((long long)m * (n_det - 1)) % twoP;
+            float sn, cs;
+            sincospif((float)r / (float)P, &sn, &cs);
+            float2 pa = make_float2(cs, sn), pb = pa;
+            if (delta2_over_M != 0.f) {
+                pa = cmul(pa, half_pixel_phase(ray + 2 * k0, m, delta2_over_M));
+                if (has1) pb = cmul(pb, half_pixel_phase(ray + 2 * k1, m, delta2_over_M));
+            }
+            const float f = (m == 0) ? 1.f : 2.f;
+            const float2 ca = cmul(A, pa), cb = cmul(B, pb);
+            spec[(long long)k0 * H + m] = make_float2(f * wa * ca.x, f * wa * ca.y);
+            if (has1) spec[(long long)k1 * H + m] = make_float2(f * wb * cb.x, f * wb * cb.y);
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------------- (2) gridding
 // Cell l (G[l_x][l_y], l mod M) sums c'_s phi(u_x - z_x) phi(u_y - z_y) over the samples z
 // with floor(z) in [u - 3, u + 2] per axis (the 6-cell footprint of the spreading form),
@@ -429,35 +550,6 @@ template <int LOGM, bool XPASS>
 __host__ __device__ constexpr int ifft_pt_smem_elems() {
     // work array, per-pass twiddles (even count), held first-row outputs (N <= M/2)
     return (1 << LOGM) + pt_offset<LOGM>(PtPlan<LOGM>::npass) + (XPASS ? 0 : (1 << LOGM) / 2);
-}
-
-// One transform (inverse when INV) of the row whose first-pass inputs x[t + r NT] are in a:
-// outputs t + (g + q Gl) NT of the last pass in c[g][q].  Begins with a block barrier (the
-// previous row's reads of z are done).
-template <int LOGM, bool INV>
-__device__ __forceinline__ void pt_row(float2 (&a)[kPassE], float2 *z, const float2 *T, int t,
-                                       float2 (&c)[kPassE / PtPlan<LOGM>::Rl][PtPlan<LOGM>::Rl]) {
-    using PL = PtPlan<LOGM>;
-    constexpr int M = 1 << LOGM, NT = M / kPassE, Rl = PL::Rl, Gl = kPassE / Rl;
-    __syncthreads();
-    dft_reg<8>(a, INV);  // pass 0 (L = 1, radix 8)
-#pragma unroll
-    for (int q = 0; q < 8; ++q) z[fft_swz<kPassE>(t * 8 + q)] = a[q];
-    __syncthreads();
-    int L = 8;
-#pragma unroll
-    for (int p = 1; p < PL::n8; ++p) {
-        if (p == PL::npass - 1) break;
-        pt_pass<8, LOGM>(z, T + pt_offset<LOGM>(p), L, t, INV);
-        L *= 8;
-    }
-    constexpr int lp = PL::npass - 1, m = M / Rl;
-#pragma unroll
-    for (int g = 0; g < Gl; ++g)
-#pragma unroll
-        for (int r = 0; r < Rl; ++r) c[g][r] = z[fft_swz<kPassE>(t + g * NT + r * m)];
-#pragma unroll
-    for (int g = 0; g < Gl; ++g) pt_twiddle_dft<Rl>(c[g], T + pt_offset<LOGM>(lp), L, t + g * NT, INV);
 }
 
 template <int LOGM, bool XPASS>
@@ -915,6 +1007,81 @@ adj_rows_kernel(const float2 *__restrict__ spec, float *__restrict__ sino, const
     }
 }
 
+// Persistent form of adj_rows_kernel for P = 2^9 .. 2^12: the Hermitian completions of the
+// pair's half spectra are built while loading the first-pass inputs, the last pass writes
+// the first n_det outputs straight to the sinogram.
+template <int LOGP>
+__global__ void __launch_bounds__((1 << LOGP) / kPassE, 1024 / ((1 << LOGP) / kPassE))
+adj_rows_pt_kernel(const float2 *__restrict__ spec, float *__restrict__ sino, const float2 *__restrict__ twp,
+                   int n_theta, int n_det) {
+    using PL = PtPlan<LOGP>;
+    constexpr int P = 1 << LOGP, H = P / 2, NT = P / kPassE;
+    constexpr int TWN = pt_offset<LOGP>(PL::npass);
+    constexpr int Rl = PL::Rl, Gl = kPassE / Rl;
+    extern __shared__ __align__(16) float2 ar_sm[];
+    float2 *z = ar_sm;     // [P]
+    float2 *T = z + P;     // [TWN]
+    const int t = threadIdx.x;
+    const int npairs = (n_theta + 1) / 2;
+    float2 nxt[kPassE];
+    auto fetch = [&](int pair) {
+        const int k0 = 2 * pair;
+        const bool has1 = k0 + 1 < n_theta;
+        const float2 *sa = spec + (long long)k0 * H, *sb = sa + H;
+#pragma unroll
+        for (int r = 0; r < kPassE; ++r) {
+            const int j = t + r * NT;
+            float2 ha, hb;  // Hermitian completions
+            if (j == 0) {
+                ha = make_float2(2.f * __ldg(&sa[0].x), 0.f);
+                hb = make_float2(has1 ? 2.f * __ldg(&sb[0].x) : 0.f, 0.f);
+            } else if (j < H) {
+                ha = __ldg(sa + j);
+                hb = has1 ? __ldg(sb + j) : make_float2(0.f, 0.f);
+            } else if (j == H) {
+                ha = hb = make_float2(0.f, 0.f);
+            } else {
+                const float2 va = __ldg(sa + P - j);
+                const float2 vb = has1 ? __ldg(sb + P - j) : make_float2(0.f, 0.f);
+                ha = make_float2(va.x, -va.y);
+                hb = make_float2(vb.x, -vb.y);
+            }
+            nxt[r] = make_float2(ha.x - hb.y, ha.y + hb.x);  // H_a + i H_b
+        }
+    };
+    int pair = blockIdx.x;
+    if (pair < npairs) fetch(pair);
+    {
+        constexpr int n4t = TWN / 2;
+        const float4 *ts = reinterpret_cast<const float4 *>(twp);
+        float4 *td = reinterpret_cast<float4 *>(T);
+#pragma unroll
+        for (int i = 0; i < (n4t + NT - 1) / NT; ++i)
+            if (t + i * NT < n4t) td[t + i * NT] = __ldg(ts + t + i * NT);
+    }
+    for (; pair < npairs; pair += gridDim.x) {
+        const int k0 = 2 * pair;
+        const bool has1 = k0 + 1 < n_theta;
+        float2 a[kPassE];
+#pragma unroll
+        for (int r = 0; r < kPassE; ++r) a[r] = nxt[r];
+        if (pair + (int)gridDim.x < npairs) fetch(pair + gridDim.x);
+        float2 c[Gl][Rl];
+        pt_row<LOGP, true>(a, z, T, t, c);
+        float *oa = sino + (long long)k0 * n_det, *ob = oa + n_det;
+#pragma unroll
+        for (int g = 0; g < Gl; ++g)
+#pragma unroll
+            for (int q = 0; q < Rl; ++q) {
+                const int j = t + (g + q * Gl) * NT;
+                if (j < n_det) {
+                    oa[j] = 0.5f * c[g][q].x;
+                    if (has1) ob[j] = 0.5f * c[g][q].y;
+                }
+            }
+    }
+}
+
 double kb_hat(double f, double beta, int width) {
     // Fourier transform of I0(beta sqrt(1 - (2t/W)^2)) on |t| <= W/2 at frequency f (cycles per cell)
     const double kW = width;
@@ -1078,9 +1245,33 @@ bp_status ensure_fourier(bp_plan *p) {
     return BP_OK;
 }
 
+template <typename Tin, int LOGP>
+static bp_status spectra_pt(bp_plan *p, const Tin *sino, cudaStream_t st, float wuni, float delta2, const float *Hf) {
+    constexpr int NT = (1 << LOGP) / kPassE;
+    constexpr size_t smem = sizeof(float2) * ((1 << LOGP) + pt_offset<LOGP>(PtPlan<LOGP>::npass));
+    auto kern = fourier_spectra_pt_kernel<Tin, LOGP>;
+    BP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    BP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem));
+    const int npairs = (p->n_theta + 1) / 2;
+    const int ctas = std::min(npairs, std::max(1, per_sm) * std::max(1, p->sm_count));
+    kern<<<ctas, NT, smem, st>>>(sino, p->four.spec, p->four.wk, p->d_twpass, p->n_theta, p->n_det, wuni,
+                                 p->four.ray, delta2, Hf);
+    return BP_OK;
+}
+
 template <typename Tin>
 static bp_status spectra_t(bp_plan *p, const Tin *sino, cudaStream_t st, float wuni, float delta2, const float *Hf) {
     const int logP = ilog2(p->P);
+    if (p->d_twpass) {
+        switch (logP) {
+            case 9: return spectra_pt<Tin, 9>(p, sino, st, wuni, delta2, Hf);
+            case 10: return spectra_pt<Tin, 10>(p, sino, st, wuni, delta2, Hf);
+            case 11: return spectra_pt<Tin, 11>(p, sino, st, wuni, delta2, Hf);
+            case 12: return spectra_pt<Tin, 12>(p, sino, st, wuni, delta2, Hf);
+            default: break;
+        }
+    }
     const size_t smem = sizeof(float2) * (p->P + p->P / 2);
     const int threads = fft_threads(p->P);
     auto kern = fft_elems(p->P) == 16 ? fourier_spectra_kernel<Tin, 16> : fourier_spectra_kernel<Tin, 8>;
@@ -1287,6 +1478,20 @@ static bp_status launch_fft_pt_fwd(bp_plan *p, const float *img, cudaStream_t st
     return BP_OK;
 }
 
+template <int LOGP>
+static bp_status launch_adj_rows_pt(bp_plan *p, float *sino, cudaStream_t st) {
+    constexpr int NT = (1 << LOGP) / kPassE;
+    constexpr size_t smem = sizeof(float2) * ((1 << LOGP) + pt_offset<LOGP>(PtPlan<LOGP>::npass));
+    auto kern = adj_rows_pt_kernel<LOGP>;
+    BP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    BP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem));
+    const int npairs = (p->n_theta + 1) / 2;
+    const int ctas = std::min(npairs, std::max(1, per_sm) * std::max(1, p->sm_count));
+    kern<<<ctas, NT, smem, st>>>(p->four.spec, sino, p->d_twpass, p->n_theta, p->n_det);
+    return BP_OK;
+}
+
 bp_status launch_radon_fourier(bp_plan *p, const float *img, float *sino, int batch, cudaStream_t st,
                                int per_angle_w) {
     bp_status s = ensure_fourier(p);
@@ -1331,8 +1536,17 @@ bp_status launch_radon_fourier(bp_plan *p, const float *img, float *sino, int ba
             ki<<<dim3((H + 255) / 256, p->n_theta), 256, 0, st>>>(f.grid, f.spec, f.ray, M, H, P, p->n_det, f.kbtab,
                                                                    delta2, scale, per_angle_w ? f.wk : nullptr);
         }
-        kr<<<(p->n_theta + 1) / 2, fft_threads(P), sizeof(float2) * (P + P / 2), st>>>(
-            f.spec, sino + (size_t)b * p->n_theta * p->n_det, p->d_twP, p->n_theta, p->n_det, ilog2(P));
+        float *sb = sino + (size_t)b * p->n_theta * p->n_det;
+        switch (p->d_twpass ? ilog2(P) : 0) {
+            case 9: s = launch_adj_rows_pt<9>(p, sb, st); break;
+            case 10: s = launch_adj_rows_pt<10>(p, sb, st); break;
+            case 11: s = launch_adj_rows_pt<11>(p, sb, st); break;
+            case 12: s = launch_adj_rows_pt<12>(p, sb, st); break;
+            default:
+                kr<<<(p->n_theta + 1) / 2, fft_threads(P), sizeof(float2) * (P + P / 2), st>>>(
+                    f.spec, sb, p->d_twP, p->n_theta, p->n_det, ilog2(P));
+        }
+        if (s != BP_OK) return s;
         BP_CUDA_TRY(cudaGetLastError());
     }
     return BP_OK;
