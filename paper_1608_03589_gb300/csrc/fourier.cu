@@ -40,7 +40,7 @@ namespace bp {
 namespace {
 
 constexpr int kKB = 2048;         // kernel table intervals on [0, W/2]
-constexpr int kCore = 32;         // cells with max(|u_x|, |u_y|) < kCore are gathered by a warp each
+constexpr int kCore = 64;         // cells with max(|u_x|, |u_y|) < kCore are gathered by a warp each
 
 struct SortedRay {                // one ray, in increasing angle order
     long long ax, ay;             // rho cos(phi), rho sin(phi) in 32.32 fixed point (grid cells per sample)
@@ -394,17 +394,23 @@ __device__ __forceinline__ void gather_rays_pair(const float2 *__restrict__ spec
 }
 
 // One thread per pair of cells (l_y even, l_y + 1) outside the core square; 64 x 8 cells per
-// block (stores along l_y).  A pair never straddles the l_y = M/2 wrap (M/2 is even).
+// block (stores along l_y).  A pair never straddles the l_y = M/2 wrap (M/2 is even).  The work
+// of a cell grows as it nears the origin (more rays cross its footprint), so blocks are
+// dispatched from the origin outwards: even block indices take chunks from the low end of
+// each axis, odd ones from the high (wrapped, negative) end, and the costly blocks start first.
 template <int HW>
 __global__ void __launch_bounds__(256, 6)
 grid_gather_pair_kernel(const float2 *__restrict__ spec, const SortedRay *__restrict__ sray,
                         const float *__restrict__ sphi, const float2 *__restrict__ tab, float2 *__restrict__ grid,
-                        int M, int H, RayIndex ri, float rmax, int amax) {
-    const int ly = blockIdx.x * 64 + 2 * (threadIdx.x & 31);
-    const int lx = blockIdx.y * 8 + (threadIdx.x >> 5);
+                        int M, int H, RayIndex ri, float rmax, int amax, int core) {
+    const int bx = blockIdx.x, by = blockIdx.y;
+    const int ly0 = (bx & 1) ? M - 64 * (1 + (bx >> 1)) : 64 * (bx >> 1);
+    const int lx0 = (by & 1) ? M - 8 * (1 + (by >> 1)) : 8 * (by >> 1);
+    const int ly = ly0 + 2 * (threadIdx.x & 31);
+    const int lx = lx0 + (threadIdx.x >> 5);
     if (lx >= M || ly >= M) return;
     const int cx = lx < M / 2 ? lx : lx - M, cy = ly < M / 2 ? ly : ly - M;
-    const bool own0 = max(abs(cx), abs(cy)) >= kCore, own1 = max(abs(cx), abs(cy + 1)) >= kCore;
+    const bool own0 = max(abs(cx), abs(cy)) >= core, own1 = max(abs(cx), abs(cy + 1)) >= core;
     if (!own0 && !own1) return;  // the core kernel owns both cells
     float2 acc0 = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
     // periodic images whose union box can reach the sample disc |z| <= rmax; with every ray
@@ -433,32 +439,46 @@ grid_gather_pair_kernel(const float2 *__restrict__ spec, const SortedRay *__rest
     if (own1) grid[(long long)lx * M + ly + 1] = acc1;
 }
 
-// One warp per core cell (max(|u_x|, |u_y|) < kCore): lanes split the rays, warp sum.
-template <int HW>
+// WPC warps per core cell (max(|u_x|, |u_y|) < kCore), cells [cell_begin, cell_end) of the ring
+// order: lanes split the rays, warp sums, then (WPC > 1) a sum over the cell's warps.
+template <int HW, int WPC>
 __global__ void __launch_bounds__(256)
 grid_gather_core_kernel(const float2 *__restrict__ spec, const SortedRay *__restrict__ sray,
                         const float *__restrict__ sphi, const float2 *__restrict__ tab, float2 *__restrict__ grid,
-                        int M, int H, RayIndex ri, float rmax, int amax, int core) {
-    const int cell = blockIdx.x * 8 + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    const int side = 2 * core - 1;
-    if (cell >= side * side) return;
-    const int cx = cell / side - (core - 1), cy = cell % side - (core - 1);
+                        int M, int H, RayIndex ri, float rmax, int amax, int cell_begin, int cell_end) {
+    static_assert(WPC == 1 || WPC == 2 || WPC == 4 || WPC == 8, "warps per cell");
+    __shared__ float2 part[8];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int cell = cell_begin + blockIdx.x * (8 / WPC) + warp / WPC;
+    const int sub = warp % WPC;  // this warp's share of the cell's rays
+    const bool live = cell < cell_end;
+    // cells in square rings max(|c_x|, |c_y|) = r from the origin outwards (the inner cells,
+    // crossed by every ray, start first): ring r >= 1 holds cells (2r - 1)^2 .. (2r + 1)^2 - 1
+    int cx = 0, cy = 0;
+    if (live && cell > 0) {
+        const int r = (int)ceilf((sqrtf((float)cell + 1.f) - 1.f) * 0.5f);
+        const int pidx = cell - (2 * r - 1) * (2 * r - 1), sd = pidx / (2 * r), q = pidx - sd * (2 * r);
+        cx = sd == 0 ? -r + q : sd == 1 ? r : sd == 2 ? r - q : -r;
+        cy = sd == 0 ? -r : sd == 1 ? -r + q : sd == 2 ? r : r - q;
+    }
     float2 acc = make_float2(0.f, 0.f);
-    for (int a = -amax; a <= amax; ++a) {
-        for (int b = -amax; b <= amax; ++b) {
-            const int ux = cx + a * M, uy = cy + b * M;
-            const float h = (float)HW;
-            if (ri.upper && uy <= -HW) continue;  // no sample has z_y < u_y + HW
-            const float qx = fmaxf(0.f, fmaxf((float)ux - h, -h - (float)ux));
-            const float qy = fmaxf(0.f, fmaxf((float)uy - h, -h - (float)uy));
-            if (qx * qx + qy * qy > rmax * rmax) continue;
-            int lo, count;
-            // the disc of radius HW sqrt(2) (+ margin) around the cell holds its box
-            ray_range(sphi, ri, (float)ux, (float)uy, lo, count, h * 1.41421356f + 0.0002f);
-            const float2 v = gather_rays<HW>(spec, sray, tab, ri.n, H, ux, uy, lo, count, lane, 32);
-            acc.x += v.x;
-            acc.y += v.y;
+    if (live) {
+        for (int a = -amax; a <= amax; ++a) {
+            for (int b = -amax; b <= amax; ++b) {
+                const int ux = cx + a * M, uy = cy + b * M;
+                const float h = (float)HW;
+                if (ri.upper && uy <= -HW) continue;  // no sample has z_y < u_y + HW
+                const float qx = fmaxf(0.f, fmaxf((float)ux - h, -h - (float)ux));
+                const float qy = fmaxf(0.f, fmaxf((float)uy - h, -h - (float)uy));
+                if (qx * qx + qy * qy > rmax * rmax) continue;
+                int lo, count;
+                // the disc of radius HW sqrt(2) (+ margin) around the cell holds its box
+                ray_range(sphi, ri, (float)ux, (float)uy, lo, count, h * 1.41421356f + 0.0002f);
+                const float2 v = gather_rays<HW>(spec, sray, tab, ri.n, H, ux, uy, lo, count, sub * 32 + lane,
+                                                 32 * WPC);
+                acc.x += v.x;
+                acc.y += v.y;
+            }
         }
     }
 #pragma unroll
@@ -466,7 +486,18 @@ grid_gather_core_kernel(const float2 *__restrict__ spec, const SortedRay *__rest
         acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
         acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
     }
-    if (lane == 0) grid[(long long)(cx & (M - 1)) * M + (cy & (M - 1))] = acc;
+    if (WPC > 1) {
+        if (lane == 0) part[warp] = acc;
+        __syncthreads();
+        if (sub == 0 && lane == 0) {
+#pragma unroll
+            for (int w = 1; w < WPC; ++w) {
+                acc.x += part[warp + w].x;
+                acc.y += part[warp + w].y;
+            }
+        }
+    }
+    if (live && sub == 0 && lane == 0) grid[(long long)(cx & (M - 1)) * M + (cy & (M - 1))] = acc;
 }
 
 // ---------------------------------------------------------------------------------- (3) inverse FFT passes
@@ -1124,7 +1155,7 @@ bp_status ensure_fourier(bp_plan *p) {
     const int N = p->N, n_theta = p->n_theta, P = p->P, H = P / 2;
     int M = 1;
     while (M < 2 * N) M <<= 1;
-    M = std::max(M, 2 * kCore);
+    M = std::max(M, 64);  // the core square (side 2 min(kCore, M/2) - 1) and a 64-cell tile fit
     if ((size_t)M * sizeof(float2) > 128u * 1024u)
         return fail(BP_ERR_UNSUPPORTED, "Fourier path: N too large for the shared-memory FFT (N <= 8192)");
     if ((size_t)P * sizeof(float2) > 200u * 1024u)
@@ -1340,6 +1371,21 @@ bp_status launch_grid_to_image(bp_plan *p, const float *deap, float *img, cudaSt
     }
 }
 
+// The core square in ring order: cells inside ring kCoreInner (crossed by nearly every ray) take
+// four warps each, the others one.
+constexpr int kCoreInner = 16;
+template <int HW>
+static void launch_core(FourierWork &f, const SortedRay *sr, int M, int H, int amax, int core, cudaStream_t st) {
+    const int n = (2 * core - 1) * (2 * core - 1);
+    const int ri = std::min(kCoreInner, core);
+    const int n_in = (2 * ri - 1) * (2 * ri - 1);
+    grid_gather_core_kernel<HW, 4><<<(n_in + 1) / 2, 256, 0, st>>>(f.spec, sr, f.sphi, f.kbtab, f.grid, M, H, f.ri,
+                                                                   f.rmax, amax, 0, n_in);
+    if (n > n_in)
+        grid_gather_core_kernel<HW, 1><<<(n - n_in + 7) / 8, 256, 0, st>>>(f.spec, sr, f.sphi, f.kbtab, f.grid, M, H,
+                                                                           f.ri, f.rmax, amax, n_in, n);
+}
+
 bp_status launch_fourier(bp_plan *p, const void *sino, bp_dtype dt, float *img, int batch, cudaStream_t st,
                          float wuni, int filter_kind, float filter_param) {
     bp_status s = ensure_fourier(p);
@@ -1364,18 +1410,15 @@ bp_status launch_fourier(bp_plan *p, const void *sino, bp_dtype dt, float *img, 
         const dim3 g((M + 63) / 64, (M + 7) / 8);
         const int amax = (int)std::ceil((f.rmax + 4.25 + M / 2) / M);
         const int core = std::min(kCore, M / 2);
-        const int side = 2 * core - 1;
         const SortedRay *sr = (const SortedRay *)f.sray;
         if (f.W == 4) {
             grid_gather_pair_kernel<2><<<g, 256, 0, st>>>(f.spec, sr, f.sphi, f.kbtab, f.grid, M, H, f.ri, f.rmax,
-                                                          amax);
-            grid_gather_core_kernel<2><<<(side * side + 7) / 8, 256, 0, st>>>(f.spec, sr, f.sphi, f.kbtab, f.grid,
-                                                                              M, H, f.ri, f.rmax, amax, core);
+                                                          amax, core);
+            launch_core<2>(f, sr, M, H, amax, core, st);
         } else {
             grid_gather_pair_kernel<3><<<g, 256, 0, st>>>(f.spec, sr, f.sphi, f.kbtab, f.grid, M, H, f.ri, f.rmax,
-                                                          amax);
-            grid_gather_core_kernel<3><<<(side * side + 7) / 8, 256, 0, st>>>(f.spec, sr, f.sphi, f.kbtab, f.grid,
-                                                                              M, H, f.ri, f.rmax, amax, core);
+                                                          amax, core);
+            launch_core<3>(f, sr, M, H, amax, core, st);
         }
         BP_CUDA_TRY(cudaGetLastError());
         if ((s = launch_grid_to_image(p, f.deapod, img + (size_t)b * N * N, st)) != BP_OK) return s;
