@@ -1372,15 +1372,15 @@ bp_status launch_grid_to_image(bp_plan *p, const float *deap, float *img, cudaSt
 }
 
 // The core square in ring order: cells inside ring kCoreInner (crossed by nearly every ray) take
-// four warps each, the others one.
+// eight warps each, the others one.
 constexpr int kCoreInner = 16;
 template <int HW>
 static void launch_core(FourierWork &f, const SortedRay *sr, int M, int H, int amax, int core, cudaStream_t st) {
     const int n = (2 * core - 1) * (2 * core - 1);
     const int ri = std::min(kCoreInner, core);
     const int n_in = (2 * ri - 1) * (2 * ri - 1);
-    grid_gather_core_kernel<HW, 4><<<(n_in + 1) / 2, 256, 0, st>>>(f.spec, sr, f.sphi, f.kbtab, f.grid, M, H, f.ri,
-                                                                   f.rmax, amax, 0, n_in);
+    grid_gather_core_kernel<HW, 8><<<n_in, 256, 0, st>>>(f.spec, sr, f.sphi, f.kbtab, f.grid, M, H, f.ri, f.rmax,
+                                                         amax, 0, n_in);
     if (n > n_in)
         grid_gather_core_kernel<HW, 1><<<(n - n_in + 7) / 8, 256, 0, st>>>(f.spec, sr, f.sphi, f.kbtab, f.grid, M, H,
                                                                            f.ri, f.rmax, amax, n_in, n);
