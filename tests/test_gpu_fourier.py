@@ -72,6 +72,35 @@ def test_fourier_batch_and_low_precision():
     assert oracle.rel_l2(img16[0].cpu().numpy(), ref) <= TOL_FOURIER
 
 
+@pytest.mark.parametrize("N,n_det,n_theta,fused", [(300, 300, 50, False), (600, 700, 40, True), (2100, 1000, 24, False)])
+def test_fourier_pair_at_every_persistent_transform_length(N, n_det, n_theta, fused):
+    # grid sides M = 1024, 2048, 8192 and projection lengths P = 1024, 2048 (the persistent
+    # row transforms are compiled per length): R*_F (or the fused FBP) and R_F on sampled
+    # outputs against the band-limited oracle
+    rng = np.random.default_rng(N)
+    theta = synth.uniform_theta(n_theta)
+    plan = bp.Plan(N, n_det, theta)
+    g = to_dev(rng.normal(size=(n_theta, n_det)))
+    pix = sample_pixels(N, 200, seed=N)
+    if fused:
+        img = plan.fbp_fourier(g, "ramlak")
+        ref = oracle.bp_trig_points(oracle.filter_rows(rounded(g), plan.det_spacing, oracle.RAMLAK), N, theta,
+                                    plan.det_spacing, pix)
+    else:
+        img = plan.backproject_fourier(g)
+        ref = oracle.bp_trig_points(rounded(g), N, theta, plan.det_spacing, pix)
+    got = img.reshape(-1)[torch.from_numpy(pix).to(dev())].cpu().numpy()
+    assert oracle.rel_l2(got, ref) <= TOL_FOURIER
+    f = to_dev(rng.normal(size=(N, N)))
+    sino = plan.radon(f, fourier=True)
+    ks = rng.choice(n_theta, 4, replace=False)
+    js = rng.choice(n_det, 4, replace=False)
+    kj = np.array([k * n_det + j for k in ks for j in js])
+    ref = oracle.radon_trig_points(rounded(f), n_det, theta, plan.det_spacing, kj)
+    got = sino.reshape(-1)[torch.from_numpy(kj).to(dev())].cpu().numpy()
+    assert oracle.rel_l2(got, ref) <= TOL_FOURIER
+
+
 # ----------------------------------------------------------------------------------- adjoint R_F
 @pytest.mark.parametrize("N,n_det,n_theta,dt_scale,seed", [
     (32, 32, 24, 1.0, 0), (37, 41, 7, 1.0, 1), (20, 30, 11, 1.3, 2), (33, 24, 9, 0.6, 3), (1, 1, 1, 1.0, 4)])
