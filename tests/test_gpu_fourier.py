@@ -72,11 +72,12 @@ def test_fourier_batch_and_low_precision():
     assert oracle.rel_l2(img16[0].cpu().numpy(), ref) <= TOL_FOURIER
 
 
-@pytest.mark.parametrize("N,n_det,n_theta,fused", [(300, 300, 50, False), (600, 700, 40, True), (2100, 1000, 24, False)])
+@pytest.mark.parametrize("N,n_det,n_theta,fused", [(300, 300, 50, False), (600, 700, 40, True), (2100, 1000, 24, False),
+                                                    (256, 256, 40, False), (512, 400, 30, True)])
 def test_fourier_pair_at_every_persistent_transform_length(N, n_det, n_theta, fused):
-    # grid sides M = 1024, 2048, 8192 and projection lengths P = 1024, 2048 (the persistent
-    # row transforms are compiled per length): R*_F (or the fused FBP) and R_F on sampled
-    # outputs against the band-limited oracle
+    # grid sides M = 512 ... 8192 and projection lengths P = 512 ... 2048 (the persistent row
+    # transforms are compiled per length; N = M/2 takes the paired column pass of R_F): R*_F
+    # (or the fused FBP) and R_F on sampled outputs against the band-limited oracle
     rng = np.random.default_rng(N)
     theta = synth.uniform_theta(n_theta)
     plan = bp.Plan(N, n_det, theta)
