@@ -340,7 +340,10 @@ bp_status bp_check(bp_plan *plan, void *stream);
  *               FP32 rounding).
  * BP_OP_RADON   direct R (bp_radon and bp_backproject_transpose with the direct form):
  *               shape[0] = angles per CTA (1, 2 or 4); shape[1] = image bands per angle block
- *               (>= 1; partial sinograms added atomically when > 1).
+ *               (>= 1; partial sinograms added atomically when > 1).  When pixels are no
+ *               larger than bins the warps of an angle also fold their tables into the
+ *               detector row with shared-memory atomics, so R's summation order varies
+ *               between runs within FP32 rounding at every shape.
  *
  * A call (op, dtype, batch) takes the plan's own shape for (op, dtype, batch), else the
  * process-wide tuning cache entry for the plan's geometry (N, n_det, n_theta, window, SM
