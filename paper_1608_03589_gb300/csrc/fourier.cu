@@ -867,12 +867,14 @@ fft_pt_fwd_cols_kernel(const float2 *__restrict__ Tin, float2 *__restrict__ out,
     }
 }
 
-// Interpolation at the polar samples by grid tiles (the form used when the work items
-// exist): sample (k, m) belongs to the kAdjTile x kAdjTile tile holding its lowest cell
+// Interpolation at the polar samples (the transpose of the spreading) by grid tiles
+// (after ensure_adj_items): sample (k, m) belongs to the kAdjTile x kAdjTile tile holding its lowest cell
 // floor(z) (the same 32.32 fixed-point floor as below); one CTA per work item (a run of ray
 // segments of one tile, at most kAdjItemSamples samples) stages the tile and its kernel halo in
 // shared memory with coalesced row loads, and its threads read the 2 HW x 2 HW neighbourhoods
-// from there.  Same result as adj_interp_kernel.
+// from there.  Per sample: the interpolation weights (the transpose of the spreading), then the
+// conjugate sample factor (1/P)(m ? 2 : 1) exp(-i pi m (n_det-1)/P) exp(-2 pi i delta (z_x + z_y)/M)
+// and dx^2/dt (or the quadrature weight).
 constexpr int kAdjTile = 64;
 constexpr int kAdjItemSamples = 2048;
 constexpr int kAdjItemSegs = 256;
@@ -953,51 +955,6 @@ adj_interp_tiled_kernel(const float2 *__restrict__ grid, float2 *__restrict__ sp
     }
 }
 
-// Interpolation at the polar samples (transpose of the spreading): one thread per sample,
-// consecutive samples of one ray in consecutive lanes; result times the conjugate sample
-// factor (1/P)(m ? 2 : 1) exp(-i pi m (n_det-1)/P) exp(-2 pi i delta (z_x + z_y)/M) and dx^2/dt.
-template <int HW>
-__global__ void __launch_bounds__(256)
-adj_interp_kernel(const float2 *__restrict__ grid, float2 *__restrict__ spec, const long long *__restrict__ ray,
-                  int M, int H, int P, int n_det, const float2 *__restrict__ tab, float delta2_over_M, float scale,
-                  const float *__restrict__ wk) {
-    const int k = blockIdx.y;
-    const int m = blockIdx.x * blockDim.x + threadIdx.x;
-    if (m >= H) return;
-    const long long zx = (long long)m * ray[2 * k], zy = (long long)m * ray[2 * k + 1];
-    const int fx = (int)(zx >> 32), fy = (int)(zy >> 32);
-    const float rx = (float)(unsigned)(zx & 0xffffffffLL) * 2.3283064365386963e-10f;
-    const float ry = (float)(unsigned)(zy & 0xffffffffLL) * 2.3283064365386963e-10f;
-    const int Mmask = M - 1;
-    // the 2 HW cells u with z - u in [-HW, HW): u = floor(z) - (HW - 1) .. floor(z) + HW
-    constexpr int W = 2 * HW;
-    float wy[W];
-#pragma unroll
-    for (int t = 0; t < W; ++t) wy[t] = kb_tab<HW>(tab, (float)(t - (HW - 1)) - ry);
-    float2 acc = make_float2(0.f, 0.f);
-#pragma unroll
-    for (int tx = 0; tx < W; ++tx) {
-        const float wx = kb_tab<HW>(tab, (float)(tx - (HW - 1)) - rx);
-        const float2 *row = grid + (long long)((fx - (HW - 1) + tx) & Mmask) * M;
-        float2 r = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int ty = 0; ty < W; ++ty) {
-            const float2 v = __ldg(row + ((fy - (HW - 1) + ty) & Mmask));
-            r.x = fmaf(wy[ty], v.x, r.x);
-            r.y = fmaf(wy[ty], v.y, r.y);
-        }
-        acc.x = fmaf(wx, r.x, acc.x);
-        acc.y = fmaf(wx, r.y, acc.y);
-    }
-    float sn, cs;
-    sincospif(-((float)(fx + fy) + (rx + ry)) * delta2_over_M, &sn, &cs);
-    acc = cmul(acc, make_float2(cs, sn));
-    const long long ph = ((long long)m * (n_det - 1)) % (2LL * P);
-    sincospif(-(float)ph / (float)P, &sn, &cs);
-    acc = cmul(acc, make_float2(cs, sn));
-    const float f = (m == 0 ? 1.f : 2.f) * (wk ? __ldg(wk + k) : scale) / (float)P;
-    spec[(long long)k * H + m] = make_float2(f * acc.x, f * acc.y);
-}
 
 // Per projection pair: y_j = Re sum_{m < P/2} s_m exp(2 pi i m j / P) = (1/2) IFFT(Hermitian(s))_j;
 // two real outputs share one complex transform (Z = H_a + i H_b).
@@ -1434,7 +1391,7 @@ static bp_status ensure_adj_items(bp_plan *p) {
     FourierWork &f = p->four;
     if (f.adj_items) return BP_OK;
     const int M = f.M, H = p->P / 2, n = p->n_theta;
-    if (M % kAdjTile) return BP_OK;  // no items: the per-sample kernel runs
+    static_assert(64 % kAdjTile == 0, "the grid side (a power of two >= 64) is a whole number of tiles");
     const int nt = M / kAdjTile;
     std::vector<long long> ray(2 * (size_t)n);
     BP_CUDA_TRY(cudaMemcpy(ray.data(), f.ray, sizeof(long long) * ray.size(), cudaMemcpyDeviceToHost));
@@ -1568,16 +1525,12 @@ bp_status launch_radon_fourier(bp_plan *p, const float *img, float *sino, int ba
                 ky<<<M / R, nthr * groups, smemR, st>>>(f.mid, f.grid, f.twM, M, f.logM, N, R);
         }
         if (s != BP_OK) return s;
-        if (f.adj_items) {
+        {
             auto kt = f.W == 4 ? adj_interp_tiled_kernel<2> : adj_interp_tiled_kernel<3>;
             const size_t sm = adj_tiled_smem(f.W / 2);
             BP_CUDA_TRY(cudaFuncSetAttribute(kt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
             kt<<<f.adj_n_items, 256, sm, st>>>(f.grid, f.spec, f.ray, f.adj_items, f.adj_segs, M, H, P, p->n_det,
                                                f.kbtab, delta2, scale, per_angle_w ? f.wk : nullptr);
-        } else {
-            auto ki = f.W == 4 ? adj_interp_kernel<2> : adj_interp_kernel<3>;
-            ki<<<dim3((H + 255) / 256, p->n_theta), 256, 0, st>>>(f.grid, f.spec, f.ray, M, H, P, p->n_det, f.kbtab,
-                                                                   delta2, scale, per_angle_w ? f.wk : nullptr);
         }
         float *sb = sino + (size_t)b * p->n_theta * p->n_det;
         switch (p->d_twpass ? ilog2(P) : 0) {
