@@ -387,25 +387,39 @@ extern "C" bp_status bp_fbp_host(bp_plan *p, const float *sino, float *img, bp_f
             BP_CUDA_TRY(cudaEventCreateWithFlags(&p->ev_d2h[k], cudaEventDisableTiming));
         }
     }
+    // on a failure the copies already queued still read or write the caller's buffers: drain
+    // the streams before returning, so that the caller may release them
+    auto drain = [&](bp_status fst) {
+        cudaStreamSynchronize(p->s_h2d);
+        cudaStreamSynchronize(p->s_d2h);
+        cudaStreamSynchronize(s);
+        return fst;
+    };
+#define BP_HOST_TRY(expr)                                                  \
+    do {                                                                   \
+        cudaError_t _e = (expr);                                           \
+        if (_e != cudaSuccess) return drain(cuda_fail(_e, #expr));         \
+    } while (0)
     for (int i = 0; i < batch; ++i) {
         const int k = i % S;
         float *d_sino = p->d_stage + (sino_pad + img_pad) * k;
         float *d_img = d_sino + sino_pad;
-        if (i >= S) BP_CUDA_TRY(cudaStreamWaitEvent(p->s_h2d, p->ev_comp[k], 0));
-        BP_CUDA_TRY(cudaMemcpyAsync(d_sino, sino + sino_n * i, sizeof(float) * sino_n, cudaMemcpyHostToDevice,
+        if (i >= S) BP_HOST_TRY(cudaStreamWaitEvent(p->s_h2d, p->ev_comp[k], 0));
+        BP_HOST_TRY(cudaMemcpyAsync(d_sino, sino + sino_n * i, sizeof(float) * sino_n, cudaMemcpyHostToDevice,
                                     p->s_h2d));
-        BP_CUDA_TRY(cudaEventRecord(p->ev_h2d[k], p->s_h2d));
-        BP_CUDA_TRY(cudaStreamWaitEvent(s, p->ev_h2d[k], 0));
-        if (i >= S) BP_CUDA_TRY(cudaStreamWaitEvent(s, p->ev_d2h[k], 0));
+        BP_HOST_TRY(cudaEventRecord(p->ev_h2d[k], p->s_h2d));
+        BP_HOST_TRY(cudaStreamWaitEvent(s, p->ev_h2d[k], 0));
+        if (i >= S) BP_HOST_TRY(cudaStreamWaitEvent(s, p->ev_d2h[k], 0));
         st = bp_filter(p, d_sino, BP_F32, d_sino, kind, param, 1, stream);
-        if (st != BP_OK) return st;
+        if (st != BP_OK) return drain(st);
         st = bp_backproject_direct(p, d_sino, BP_F32, d_img, 1, 0, stream);
-        if (st != BP_OK) return st;
-        BP_CUDA_TRY(cudaEventRecord(p->ev_comp[k], s));
-        BP_CUDA_TRY(cudaStreamWaitEvent(p->s_d2h, p->ev_comp[k], 0));
-        BP_CUDA_TRY(cudaMemcpyAsync(img + img_n * i, d_img, sizeof(float) * img_n, cudaMemcpyDeviceToHost, p->s_d2h));
-        BP_CUDA_TRY(cudaEventRecord(p->ev_d2h[k], p->s_d2h));
+        if (st != BP_OK) return drain(st);
+        BP_HOST_TRY(cudaEventRecord(p->ev_comp[k], s));
+        BP_HOST_TRY(cudaStreamWaitEvent(p->s_d2h, p->ev_comp[k], 0));
+        BP_HOST_TRY(cudaMemcpyAsync(img + img_n * i, d_img, sizeof(float) * img_n, cudaMemcpyDeviceToHost, p->s_d2h));
+        BP_HOST_TRY(cudaEventRecord(p->ev_d2h[k], p->s_d2h));
     }
+#undef BP_HOST_TRY
     BP_CUDA_TRY(cudaStreamSynchronize(p->s_d2h));
     BP_CUDA_TRY(cudaStreamSynchronize(s));
     return BP_OK;
