@@ -3,11 +3,14 @@
 //     (R f)_{kj} = (dx^2 / dt) * sum_p hat(u_pk - j) f_p,
 // i.e. every pixel deposits (1 - fr) f_p into bin floor(u) and fr f_p into bin floor(u) + 1.
 //
-// Design (GB300): a CTA owns kAng consecutive angles and one band of the image; it walks
-// the band's 64 x 64 pixel tiles (the next tile is prefetched into registers while the
-// current one is processed) and keeps the full detector rows of its angles in shared
-// memory, so each sinogram bin is written to global memory once per band.  Within a tile
-// each warp owns a private window per angle of interval sums (A_m, B_m) = (sum f,
+// Two forms share the launch structure (GB300): a CTA owns kAng consecutive angles and one
+// band of the image; it walks the band's 64 x 64 pixel tiles (the next tile is prefetched into
+// registers while the current one is processed) and keeps the full detector rows of its angles
+// in shared memory, so each sinogram bin is written to global memory once per band.  When
+// pixels are no larger than bins (|c|, |s| <= 1) the 2 x 2-block form below runs (the
+// transpose of the 2 x 2-block R*); otherwise the per-pixel form described here.
+//
+// Per-pixel form: within a tile each warp owns a private window per angle of interval sums (A_m, B_m) = (sum f,
 // sum f (q - m)) over the pixels whose tile-local coordinate q rounds to m; the two bins
 // around interval m then receive A/2 - B and A/2 + B (exactly (1 - fr) f and fr f summed),
 // with no cancellation because |q - m| <= 1/2.  Lanes of a warp take pixels S pixels apart
