@@ -16,17 +16,21 @@
 // inverse FFT passes produce the N x N output, and dividing by the kernel's Fourier
 // transform (deapodisation) removes the kernel.
 //
-// Kernels: (1) fourier_spectra: one CTA per projection pair, P-point FFT in shared memory,
-// the two half spectra scaled into c'_{k,m} (quadrature weight, Hermitian factor, detector
-// and half-pixel phases);  (2) gridding as a gather: one thread per pair of adjacent grid
-// cells (a warp per cell near the origin, where every ray passes) walks only the rays whose
-// angle falls in the pair's footprint as seen from the origin (O(1) lookup for uniform angle
-// sets, else binary search in the sorted angles), and on each ray only the samples inside
-// the footprint, sharing the sample value and the x weight between the two cells; the separable kernel comes from an
-// FP64-built table with linear interpolation.  No atomics, deterministic, one store per
-// cell;  (3) ifft_pass_y / ifft_pass_x: M-point inverse FFTs of R rows per CTA (bulk
-// asynchronous loads) with output pruning to N points, transposed intermediate, fused
-// deapodisation and real part.
+// Kernels: (1) the projection spectra: P-point FFTs of projection pairs in shared memory
+// (persistent, per-pass twiddles, for P = 512 ... 4096), the two half spectra scaled into
+// c'_{k,m} (quadrature weight, Hermitian factor, detector and half-pixel phases);
+// (2) gridding as a gather: one thread per pair of adjacent grid cells walks only the rays
+// whose angle falls in the pair's footprint as seen from the origin (O(1) lookup for uniform
+// angle sets, else binary search in the sorted angles), and on each ray only the samples
+// inside the footprint, sharing the sample value and the x weight between the two cells; the
+// separable kernel comes from an FP64-built table with linear interpolation.  A cell's work
+// grows as it nears the origin, so blocks are dispatched from the origin outwards and the
+// core square (where nearly every ray passes) takes one to eight warps per cell in ring order.
+// No atomics, deterministic, one store per cell;  (3) the two pruned inverse-FFT passes
+// (persistent, per-pass twiddles, for M = 512 ... 8192): rows l_x in pairs into a transposed
+// intermediate, then rows i_y with deapodisation and the real part.  The adjoint R_F mirrors
+// them: forward passes (the padding never loaded), interpolation at the polar samples by
+// 64 x 64 grid tiles staged in shared memory, and the Hermitian inverse row transforms.
 #include <algorithm>
 #include <cmath>
 
