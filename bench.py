@@ -4,7 +4,10 @@ One step = the hot path over one synthetic slice: Shepp-Logan row filter (bp_fil
 followed by the direct pixel-driven R* (bp_backproject_direct), both through the C ABI.
 Metric: backprojection pixel-angle updates per second (N^2 * n_theta per step), in G/s.
 
-Prints ONE JSON line on rank 0.  `--impl reference` times the FP64 CPU oracle instead.
+Prints ONE JSON line on rank 0.  `e2e` is the same metric through bp_fbp_host from pinned
+host memory: the e2e steps run as one call over that many slices, each slice copied in and
+its image copied out inside the timed region (the call overlaps the copies of neighbouring
+slices with the kernels).  `--impl reference` times the FP64 CPU oracle instead.
 Multi-GPU (torchrun): each rank backprojects its own independent slice (no data-path
 collective); the barrier and max-over-ranks timing are the only cross-rank traffic.
 """
