@@ -299,18 +299,22 @@ bp_status bp_backproject_batched(bp_plan *const *plans, const void *const *sinos
 /*
  * bp_fbp_static -- the same filtered backprojection as bp_filter followed by
  * bp_backproject_direct (device pointers, BP_RAMLAK or BP_SHEPP_LOGAN), for callers that
- * cannot allocate device memory when they need it: code that runs while a CUDA graph is
- * being captured, code inside a framework that owns every device allocation, or loops
- * where allocation is not allowed.  The paper has no counterpart; it exists only for
- * such callers.
- *   Allocation: none.  Its scratch (the filter response and one filtered slice) lives in
- *   a static device array of BP_STATIC_SCRATCH_BYTES that every GPU which loads the
- *   library holds until the process exits.  P + n_theta * n_det (in floats, P the
- *   filter FFT length) must fit in it, else BP_ERR_UNSUPPORTED; batch slices are done one
- *   after another through the same scratch.
+ * cannot allocate device memory when they need it: code inside a framework that owns
+ * every device allocation (a fixed pool or memory budget, where a private cudaMalloc may
+ * fail or break the budget), or real-time acquisition loops where allocating is not
+ * allowed (cudaMalloc can synchronise the device and has no bounded latency).  The paper
+ * has no counterpart; it exists only for such callers.
+ *   Allocation: none.  Its scratch (one filtered slice) lives in a static device array of
+ *   BP_STATIC_SCRATCH_BYTES that every GPU which loads the library holds until the process
+ *   exits.  n_theta * n_det floats must fit in it (the 2048-bin x 1800-angle slice does),
+ *   else BP_ERR_UNSUPPORTED; batch slices are done one after another through the same
+ *   scratch.  The filter response is the plan's own, made in FP64 on the host by
+ *   bp_plan_create; the call only reads it.
  *   Set-up: the first call on each device looks up the array's device address
- *   (cudaGetSymbolAddress) with that device current; make that first call before any
- *   stream capture.  The plan itself is created beforehand with bp_plan_create.
+ *   (cudaGetSymbolAddress) with that device current and keeps it for the life of the
+ *   process; make that first call before any stream capture.  The address is not valid
+ *   across cudaDeviceReset (nor is any plan).  The plan itself is created beforehand with
+ *   bp_plan_create.
  *   Sharing: every call on a device uses the same array and leaves its last contents
  *   there; calls whose work overlaps on the GPU (different streams, or different host
  *   threads without ordering) race on it and must be serialised by the caller.

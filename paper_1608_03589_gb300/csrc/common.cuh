@@ -148,7 +148,7 @@ struct bp_plan {
     int P = 0;                 // FFT length for the filter (power of two >= 2 n_det)
     float2 *d_twP = nullptr;   // P/2 twiddles exp(-2 pi i r / P)
     float2 *d_twpass = nullptr;  // per-pass twiddles of the persistent filter kernel (512 <= P <= 4096)
-    float *d_H[3] = {nullptr, nullptr, nullptr};   // bit-reversed scaled responses per kind
+    float *d_H[3] = {nullptr, nullptr, nullptr};   // scaled responses (dt/P) DFT_P(h) per kind, natural order
     float H_param[3] = {0.f, 0.f, 0.f};
     // Fourier path
     int fourier_W = 6;          // Kaiser-Bessel width of the gridding (bp_set_fourier_width)

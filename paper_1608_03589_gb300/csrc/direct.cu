@@ -190,7 +190,14 @@ bp_direct_tma_kernel(const __grid_constant__ CUtensorMap tmap, float *__restrict
                 }
             }
         }
-        __syncthreads();
+        if (__syncthreads_or(!ok)) {
+            // a copy did not complete in time: record it, issue no further copy, wait (bounded)
+            // for the copies still in flight (stages i and i + 1) and leave without writing
+            if (tid == 0) atomicExch(err, 1);
+            mbar_wait(bar0 + 8 * b, (uint32_t)((i >> 1) & 1));
+            if (i + 1 < S) mbar_wait(bar0 + 8 * (b ^ 1), (uint32_t)(((i + 1) >> 1) & 1));
+            return;
+        }
         if (i + 2 < S) {
             if (tid < STAGE) fence_proxy_async_smem();
             prepare(i + 2);
@@ -215,8 +222,6 @@ bp_direct_tma_kernel(const __grid_constant__ CUtensorMap tmap, float *__restrict
             }
         }
     }
-    if (!ok && lane == 0) atomicExch(err, 1);
-
 #pragma unroll
     for (int b = 0; b < 2; ++b) {
         const int y = ty * kTile + ly + 4 * b;

@@ -536,7 +536,13 @@ ifft_pass_y_kernel(const float2 *__restrict__ grid, float2 *__restrict__ inter, 
     const int lx0 = blockIdx.x * R;
     const int nthr = fft_threads(M), groups = blockDim.x / nthr;
     const int g = threadIdx.x / nthr, tid = threadIdx.x - g * nthr;
-    if (!load_rows_async(z, grid + (long long)lx0 * M, R * M, &bar) && threadIdx.x == 0) atomicExch(err, 1);
+    if (__syncthreads_or(!load_rows_async(z, grid + (long long)lx0 * M, R * M, &bar))) {
+        // the copy did not complete in time: record it, wait (bounded) for it once more so that
+        // no copy is left in flight, and leave without computing
+        if (threadIdx.x == 0) atomicExch(err, 1);
+        mbar_wait(smem_u32(&bar), 0);
+        return;
+    }
     for (int r0 = 0; r0 < R; r0 += groups) stockham_fft<E>(z + (r0 + g) * M, logM, tws, 1, true, tid, nthr);
     const int h = N / 2;
     for (int i = threadIdx.x; i < N * R; i += blockDim.x) {
@@ -561,7 +567,11 @@ ifft_pass_x_kernel(const float2 *__restrict__ inter, float *__restrict__ img, co
     const int rows = min(R, N - iy0);
     const int nthr = fft_threads(M), groups = blockDim.x / nthr;
     const int g = threadIdx.x / nthr, tid = threadIdx.x - g * nthr;
-    if (!load_rows_async(z, inter + (long long)iy0 * M, rows * M, &bar) && threadIdx.x == 0) atomicExch(err, 1);
+    if (__syncthreads_or(!load_rows_async(z, inter + (long long)iy0 * M, rows * M, &bar))) {
+        if (threadIdx.x == 0) atomicExch(err, 1);  // as in ifft_pass_y_kernel
+        mbar_wait(smem_u32(&bar), 0);
+        return;
+    }
     // rows beyond the last image row hold stale data that is transformed but never written out
     for (int r0 = 0; r0 < R; r0 += groups) stockham_fft<E>(z + (r0 + g) * M, logM, tws, 1, true, tid, nthr);
     const int h = N / 2;

@@ -1,16 +1,18 @@
 // bp_fbp_static: filtered backprojection that allocates no device memory.
 //
 // Some callers cannot call cudaMalloc at the point where they need a reconstruction:
-// code running while a CUDA graph is being captured, code embedded in a host framework
-// that owns every device allocation (a fixed memory pool or budget), or real-time loops
-// in which allocating is not allowed.  For them this entry point keeps its scratch -- the
-// filter's frequency response and the filtered sinogram of one slice -- in one file-scope
-// static device array of fixed size, which every GPU that loads the library holds until
-// the process exits.  The caller still passes its own input and output buffers.
+// code embedded in a host framework that owns every device allocation (a fixed memory
+// pool or budget, where a private cudaMalloc can fail or break the budget), or
+// real-time acquisition loops in which allocating is not allowed (cudaMalloc may
+// synchronise the device and its latency is unbounded).  For them this entry point keeps
+// its scratch -- the filtered sinogram of one slice -- in one file-scope static device
+// array of fixed size, which every GPU that loads the library holds until the process
+// exits.  The filter's frequency response is the plan's own (FP64 on the host, made by
+// bp_plan_create for Ram-Lak and Shepp-Logan), so a call only reads it.  The caller still
+// passes its own input and output buffers.
 #include <mutex>
 
 #include "common.cuh"
-#include "fft.cuh"
 
 namespace bp {
 
@@ -40,30 +42,6 @@ bp_status scratch_address(int device, float **out) {
     return BP_OK;
 }
 
-// Filter response (dt/P) DFT_P(h_circ), h_circ[r] = h(|r|) for |r| < n_det, natural order,
-// evaluated in double precision on the device (the host path uses an FP64 FFT).
-__global__ void static_response_kernel(float *__restrict__ H, int P, int n_det, double dt, int kind) {
-    const int half = P / 2;
-    for (int m = blockIdx.x * blockDim.x + threadIdx.x; m <= half; m += gridDim.x * blockDim.x) {
-        const double pi2dt2 = M_PI * M_PI * dt * dt;
-        double acc = (kind == BP_RAMLAK) ? 1.0 / (4.0 * dt * dt) : 2.0 / pi2dt2;
-        for (int r = 1; r < n_det; ++r) {
-            double h;
-            if (kind == BP_RAMLAK) {
-                if (!(r & 1)) continue;
-                h = -1.0 / (pi2dt2 * (double)r * (double)r);
-            } else {
-                h = -2.0 / (pi2dt2 * (4.0 * (double)r * (double)r - 1.0));
-            }
-            const long long a = (2LL * m * r) % (2LL * P);  // cos(2 pi m r / P) = cospi(a / P)
-            acc += 2.0 * h * cospi((double)a / (double)P);
-        }
-        const float v = (float)(acc * dt / (double)P);
-        H[m] = v;
-        if (m > 0 && m < half) H[P - m] = v;
-    }
-}
-
 }  // namespace
 
 }  // namespace bp
@@ -81,21 +59,18 @@ extern "C" bp_status bp_fbp_static(bp_plan *p, const void *sino, bp_dtype dtype,
     if (dtype != BP_F32 && dtype != BP_BF16 && dtype != BP_F16) return fail(BP_ERR_INVALID_ARG, "invalid dtype");
     if (kind != BP_RAMLAK && kind != BP_SHEPP_LOGAN)
         return fail(BP_ERR_UNSUPPORTED, "bp_fbp_static supports BP_RAMLAK and BP_SHEPP_LOGAN only");
-    const size_t h_floats = ((size_t)p->P + 63) & ~(size_t)63;
     const size_t slice = (size_t)p->n_theta * p->n_det;
-    if (h_floats + slice > kStaticFloats)
-        return fail(BP_ERR_UNSUPPORTED, "bp_fbp_static: P + n_theta * n_det exceeds the static scratch of "
+    if (slice > kStaticFloats)
+        return fail(BP_ERR_UNSUPPORTED, "bp_fbp_static: n_theta * n_det exceeds the static scratch of "
                                         "BP_STATIC_SCRATCH_BYTES / 4 floats");
-    float *scratch = nullptr;
-    st = scratch_address(p->device, &scratch);
+    const float *H = p->d_H[kind];
+    if (!H) return fail(BP_ERR_INVALID_ARG, "bp_fbp_static: the plan has no filter response for this kind");
+    float *q = nullptr;
+    st = scratch_address(p->device, &q);
     if (st != BP_OK) return st;
-    float *H = scratch;
-    float *q = scratch + h_floats;
     cudaStream_t s = (cudaStream_t)stream;
     // Every value the kernels read from the scratch is written earlier in this call, so
     // nothing needs clearing.
-    static_response_kernel<<<(p->P / 2 + 256) / 256, 256, 0, s>>>(H, p->P, p->n_det, p->dt, (int)kind);
-    BP_CUDA_TRY(cudaGetLastError());
     const size_t esz = dtype == BP_F32 ? 4 : 2;
     for (int b = 0; b < batch; ++b) {
         const char *sb = (const char *)sino + esz * slice * b;

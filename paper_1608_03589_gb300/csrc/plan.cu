@@ -211,6 +211,15 @@ extern "C" bp_plan *bp_plan_create(int N, int n_det, int n_theta, const double *
         delete p;
         return nullptr;
     }
+    // Ram-Lak and Shepp-Logan responses (FP64 on the host, eq "fbp"), made here so that
+    // bp_fbp_static only reads them (the Tikhonov response depends on lambda: made on use)
+    for (int kind : {(int)BP_RAMLAK, (int)BP_SHEPP_LOGAN}) {
+        if (ensure_filter(p, kind, 0.f) != BP_OK) {
+            plan_free_device(p);
+            delete p;
+            return nullptr;
+        }
+    }
     return p;
 }
 

@@ -1,8 +1,9 @@
 """bp_fbp_static: the filtered backprojection for callers that cannot allocate device memory
-(graph capture, framework-owned memory pools, allocation-free loops).  Checked through the
-C ABI against the ordinary entry points (bp_filter + bp_backproject_direct) on two calls in
-a row, the second with different data, so a stale static scratch would show.  This file is
-collected last on purpose."""
+when they reconstruct (a framework that owns every device allocation through a fixed pool or
+budget; real-time loops where cudaMalloc's device synchronisation and unbounded latency are
+not allowed).  Checked through the C ABI against the ordinary entry points (bp_filter +
+bp_backproject_direct) on two calls in a row, the second with different data and another
+filter, so a stale static scratch would show.  This file is collected last on purpose."""
 import ctypes
 
 import numpy as np
@@ -49,7 +50,16 @@ def test_static_fbp_batch_and_size_limit():
     ref = plan.backproject(plan.filter(sino, "shepp-logan"))
     torch.cuda.synchronize()
     assert oracle.rel_l2(img.cpu().numpy(), ref.cpu().numpy()) <= TOL_DIRECT
-    big = bp.Plan(64, 4096, synth.uniform_theta(1100), 2.0 / 64)  # 1100 x 4096 floats > 16 MiB
-    small_in = torch.zeros((1100, 4096), dtype=torch.float32, device=dev())
+    # the limit is n_theta * n_det <= 4 Mi floats: 1024 x 4096 fits exactly, 1025 x 4096 does not
+    fits = bp.Plan(64, 4096, synth.uniform_theta(1024), 2.0 / 64)
+    g = to_dev(rng.normal(size=(1024, 4096)))
+    out = torch.empty((64, 64), device=dev())
+    st, msg = _call_static(fits, g, "ramlak", out)
+    assert st == 0, msg
+    ref = fits.backproject(fits.filter(g, "ramlak"))
+    torch.cuda.synchronize()
+    assert oracle.rel_l2(out.cpu().numpy(), ref.cpu().numpy()) <= TOL_DIRECT
+    big = bp.Plan(64, 4096, synth.uniform_theta(1025), 2.0 / 64)
+    small_in = torch.zeros((1025, 4096), dtype=torch.float32, device=dev())
     st, msg = _call_static(big, small_in, "ramlak", torch.empty((64, 64), device=dev()))
     assert st == 4 and "exceeds the static scratch" in msg
