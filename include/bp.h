@@ -333,6 +333,23 @@ bp_status bp_fbp_static(bp_plan *plan, const void *sino, bp_dtype dtype, float *
 bp_status bp_check(bp_plan *plan, void *stream);
 
 /*
+ * Per-kernel timing (no counterpart in the paper; measurement support for the roofline of
+ * each kernel of the path).
+ * bp_stage_timing -- on != 0 starts recording, 0 stops; either way earlier records are
+ *   dropped.  While it is on, every operator call of this plan records a CUDA event on its
+ *   stream when it starts and after each kernel (or memset) it launches.  Off by default;
+ *   with it on, do not capture the plan's calls into a CUDA graph.
+ * bp_stage_times -- wait for the recorded events, then report per kernel name the summed time
+ *   in milliseconds between the event before each launch and the one after it, and the number
+ *   of launches; the records are then dropped (recording continues while on).  names[i] point
+ *   to static strings of the library.  cap = capacity of names, ms and launches; *count = the
+ *   number of distinct names (only the first cap are written).  BP_ERR_UNSUPPORTED when more
+ *   than 8192 events were recorded since the last read (the records are dropped).
+ */
+bp_status bp_stage_timing(bp_plan *plan, int on);
+bp_status bp_stage_times(bp_plan *plan, int cap, const char **names, float *ms, int *launches, int *count);
+
+/*
  * Launch shapes and autotuning.  Neither changes what an operator computes, only how its
  * work is split across the GPU (no counterpart in the paper).
  *

@@ -28,7 +28,7 @@ SYMBOLS = ("bp_plan_create", "bp_destroy", "bp_filter", "bp_backproject_direct",
            "bp_radon", "bp_fbp_host", "bp_fbp_fourier", "bp_backproject_bst", "bp_backproject_bst_windowed",
            "bp_backproject_logpolar", "bp_backproject_logpolar_partial", "bp_set_fourier_width", "bp_backproject_batched", "bp_fbp_static", "bp_check", "bp_radon_transpose",
            "bp_backproject_transpose", "bp_autotune", "bp_get_shape", "bp_set_shape", "bp_tune_cache_save",
-           "bp_tune_cache_load", "bp_last_error", "bp_version")
+           "bp_tune_cache_load", "bp_stage_timing", "bp_stage_times", "bp_last_error", "bp_version")
 OPS = {"direct": 0, "radon": 1}
 
 
@@ -76,6 +76,8 @@ def lib() -> ctypes.CDLL:
             L.bp_set_shape.argtypes = [vp, i, i, i, ip]
             L.bp_tune_cache_save.argtypes = [ctypes.c_char_p]
             L.bp_tune_cache_load.argtypes = [ctypes.c_char_p]
+            L.bp_stage_timing.argtypes = [vp, i]
+            L.bp_stage_times.argtypes = [vp, i, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(f), ip, ip]
             for name in ("bp_filter", "bp_backproject_direct", "bp_backproject_fourier", "bp_radon",
                          "bp_fbp_host", "bp_fbp_fourier", "bp_backproject_bst", "bp_backproject_bst_windowed",
                          "bp_backproject_logpolar", "bp_backproject_logpolar_partial",
@@ -83,7 +85,8 @@ def lib() -> ctypes.CDLL:
                          "bp_backproject_batched", "bp_fbp_static",
                          "bp_check",
                          "bp_radon_transpose", "bp_backproject_transpose", "bp_autotune", "bp_get_shape",
-                         "bp_set_shape", "bp_tune_cache_save", "bp_tune_cache_load"):
+                         "bp_set_shape", "bp_tune_cache_save", "bp_tune_cache_load", "bp_stage_timing",
+                         "bp_stage_times"):
                 getattr(L, name).restype = i
             L.bp_last_error.argtypes = []
             L.bp_last_error.restype = ctypes.c_char_p
@@ -399,6 +402,20 @@ class Plan:
         arr = (ctypes.c_int * 2)(int(shape[0]), int(shape[1]))
         with torch.cuda.device(self.device):
             _check(lib().bp_set_shape(self.handle, o, d, int(batch), arr), "bp_set_shape")
+
+    def stage_timing(self, on: bool = True) -> None:
+        """Start (or stop) recording a CUDA event after every kernel of this plan's calls."""
+        _check(lib().bp_stage_timing(self.handle, 1 if on else 0), "bp_stage_timing")
+
+    def stage_times(self) -> dict[str, tuple[float, int]]:
+        """Per kernel name: (summed milliseconds, launches) since the last read (waits for them)."""
+        cap = 64
+        names = (ctypes.c_char_p * cap)()
+        ms = (ctypes.c_float * cap)()
+        launches = (ctypes.c_int * cap)()
+        count = ctypes.c_int(0)
+        _check(lib().bp_stage_times(self.handle, cap, names, ms, launches, ctypes.byref(count)), "bp_stage_times")
+        return {names[j].decode(): (float(ms[j]), int(launches[j])) for j in range(min(cap, count.value))}
 
     def close(self) -> None:
         if getattr(self, "_h", None) is not None:

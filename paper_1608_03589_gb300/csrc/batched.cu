@@ -101,6 +101,7 @@ bp_status launch_batched(bp_plan *const *plans, const void *const *sinos, const 
         BP_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p0->device));
         dev_of_sms = p0->device;
     }
+    stage_begin(p0, st);
     for (int base = 0; base < n; base += kMaxSlices) {
         const int cnt = std::min(kMaxSlices, n - base);
         BatchParams bpm;
@@ -133,6 +134,7 @@ bp_status launch_batched(bp_plan *const *plans, const void *const *sinos, const 
         BP_CUDA_TRY(cudaMemsetAsync(p0->d_counter, 0, sizeof(int), st));
         bp_batched_kernel<<<grid, kThreads, smem, st>>>(bpm, p0->d_counter);
         BP_CUDA_TRY(cudaGetLastError());
+        stage_mark(p0, st, "bp_batched_kernel");
     }
     return BP_OK;
 }

@@ -214,6 +214,7 @@ bp_status polar_t(bp_plan *p, const Tin *sino, int n_det, cudaStream_t st) {
     kern<<<(p->n_theta + 1) / 2, fft_threads(w.Pb), smem, st>>>(sino, w.polar, w.twPb, p->n_theta, n_det, logP,
                                                                 scale);
     BP_CUDA_TRY(cudaGetLastError());
+    stage_mark(p, st, "bst_polar_kernel");
     return BP_OK;
 }
 
@@ -361,6 +362,7 @@ bp_status launch_bst(bp_plan *p, const void *sino, bp_dtype dt, float *img, int 
     const float ih = (float)inv_rho, il = (float)(inv_rho - (double)ih);
     const float scale = (float)(1.0 / (((double)M * p->dx) * ((double)M * p->dx)));
     const float delta2 = (N % 2 == 0) ? 1.0f / (float)M : 0.0f;  // 2 delta / M
+    stage_begin(p, st);
     for (int b = 0; b < batch; ++b) {
         const char *sb = (const char *)sino + esz * (size_t)b * p->n_theta * p->n_det;
         switch (dt) {
@@ -373,6 +375,7 @@ bp_status launch_bst(bp_plan *p, const void *sino, bp_dtype dt, float *img, int 
         bst_interp_kernel<<<g, 256, 0, st>>>(w.polar, w.ang, w.ray, w.dir, w.igap, w.ri, f.grid, M, H, ih, il, scale,
                                              delta2, p->n_theta);
         BP_CUDA_TRY(cudaGetLastError());
+        stage_mark(p, st, "bst_interp_kernel");
         if ((s = launch_grid_to_image(p, w.ones, img + (size_t)b * N * N, st)) != BP_OK) return s;
     }
     return BP_OK;
@@ -397,6 +400,7 @@ bp_status launch_bst_windowed(bp_plan *p, const void *sino, bp_dtype dt, float *
     const float delta2 = (N % 2 == 0) ? 1.0f / (float)M : 0.0f;
     const long long total = (long long)p->n_theta * np;
     const unsigned blocks = (unsigned)std::min<long long>((total + 255) / 256, 8LL * std::max(1, p->sm_count));
+    stage_begin(p, st);
     for (int b = 0; b < batch; ++b) {
         const char *sb = (const char *)sino + esz * (size_t)b * p->n_theta * p->n_det;
         switch (dt) {
@@ -413,11 +417,13 @@ bp_status launch_bst_windowed(bp_plan *p, const void *sino, bp_dtype dt, float *
                 break;
         }
         BP_CUDA_TRY(cudaGetLastError());
+        stage_mark(p, st, "bst_window_rows_kernel");
         if ((s = polar_t(p, (const float *)w.wrows, np, st)) != BP_OK) return s;
         const dim3 g((M + 31) / 32, (M + 7) / 8);
         bst_interp_kernel<<<g, 256, 0, st>>>(w.polar, w.ang, w.ray, w.dir, w.igap, w.ri, f.grid, M, H, ih, il, scale,
                                              delta2, p->n_theta);
         BP_CUDA_TRY(cudaGetLastError());
+        stage_mark(p, st, "bst_interp_kernel");
         if ((s = launch_grid_to_image(p, w.ones, img + (size_t)b * N * N, st)) != BP_OK) return s;
     }
     return BP_OK;

@@ -127,6 +127,18 @@ struct RadonShape {
 // out while slice i is filtered and backprojected.
 constexpr int kHostSlots = 3;
 
+// Per-kernel timing (bp_stage_timing / bp_stage_times): while it is on, every launcher records a
+// CUDA event on its stream at its start (name nullptr) and after each kernel it launches (the
+// kernel's name); a kernel's time is the interval from the event before it.
+struct StageTimer {
+    bool on = false;
+    bool overflow = false;
+    std::vector<cudaEvent_t> ev;      // created on demand, reused
+    std::vector<const char *> name;   // per recorded event; nullptr marks a call's start
+    int used = 0;
+};
+constexpr int kStageTimerCap = 8192;
+
 struct TuneEntry {
     int op, dtype, batch;
     int v[2];
@@ -172,10 +184,15 @@ struct bp_plan {
     // launch shapes chosen for this plan (bp_autotune / bp_set_shape), and the SM count
     std::vector<bp::TuneEntry> shapes;
     int sm_count = 0;
+    bp::StageTimer timer;
 };
 
 namespace bp {
 bp_status check_plan(const bp_plan *p);
+// stage timing marks (no-ops unless the plan's timer is on): stage_begin at the start of a
+// launcher, stage_mark after each kernel launch with the kernel's name (a string literal)
+void stage_begin(bp_plan *p, cudaStream_t st);
+void stage_mark(bp_plan *p, cudaStream_t st, const char *name);
 bool aligned16(const void *ptr);
 int ilog2(int v);
 

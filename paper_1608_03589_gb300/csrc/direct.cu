@@ -302,6 +302,7 @@ bp_status launch_tma(bp_plan *p, const CUtensorMap &map, float *img, int batch, 
     kern<<<grid, kThreads, smem, st>>>(map, img, p->d_ang, p->N, p->n_theta, p->W, p->C, Wb, RS, accumulate, tiles,
                                        asplit, (long long)p->N * p->N, p->d_err, wuni);
     BP_CUDA_TRY(cudaGetLastError());
+    stage_mark(p, st, "bp_direct_tma_kernel");
     return BP_OK;
 }
 
@@ -328,8 +329,11 @@ bp_status launch_direct_t(bp_plan *p, const Tin *sino, float *img, int batch, in
     const bool quad = quad_form(p);
     const DirectShape eff = direct_effective(p, esz, !quad && have_enc && tma_eligible(p, esz), shape);
     const int stage = eff.stage, asplit = eff.asplit;
-    if (asplit > 1 && !accumulate)
+    stage_begin(p, st);
+    if (asplit > 1 && !accumulate) {
         BP_CUDA_TRY(cudaMemsetAsync(img, 0, sizeof(float) * (size_t)p->N * p->N * batch, st));
+        stage_mark(p, st, "memset (direct R* angle groups)");
+    }
     dim3 grid(tiles, tiles * asplit, batch);
     if (quad) {
         const size_t qsmem = sizeof(float4) * (size_t)kStage * p->W;
@@ -339,6 +343,7 @@ bp_status launch_direct_t(bp_plan *p, const Tin *sino, float *img, int batch, in
                                           tiles, asplit, (long long)p->n_theta * p->n_det, (long long)p->N * p->N,
                                           wuni);
         BP_CUDA_TRY(cudaGetLastError());
+        stage_mark(p, st, "bp_direct_quad_sync_kernel");
         return BP_OK;
     }
     CUtensorMap map;
@@ -359,6 +364,7 @@ bp_status launch_direct_t(bp_plan *p, const Tin *sino, float *img, int batch, in
                                        tiles, asplit, (long long)p->n_theta * p->n_det, (long long)p->N * p->N,
                                        wuni);
     BP_CUDA_TRY(cudaGetLastError());
+    stage_mark(p, st, "bp_direct_kernel");
     return BP_OK;
 }
 

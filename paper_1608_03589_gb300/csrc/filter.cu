@@ -290,6 +290,7 @@ bp_status launch_pt(bp_plan *p, const Tin *in, float *out, const float *H, long 
     const long long grid = std::max(1LL, std::min(npairs, (long long)std::max(1, per_sm) * std::max(1, p->sm_count)));
     kern<<<(unsigned)grid, NT, smem, st>>>(in, out, H, p->d_twpass, rows, p->n_det);
     BP_CUDA_TRY(cudaGetLastError());
+    stage_mark(p, st, "filter_pt_kernel");
     return BP_OK;
 }
 
@@ -322,6 +323,7 @@ bp_status launch_filter(bp_plan *p, const void *in, bp_dtype dt, float *out, int
         return fail(BP_ERR_UNSUPPORTED, "filter: n_det too large for the shared-memory FFT (n_det <= 8192)");
     bp_status s = ensure_filter(p, kind, param);
     if (s != BP_OK) return s;
+    stage_begin(p, st);
     const long long rows = (long long)batch * p->n_theta;
     if (p->d_twpass) return launch_pt_any(p, in, dt, out, p->d_H[kind], rows, st);
     const int logP = ilog2(p->P);
@@ -349,6 +351,7 @@ bp_status launch_filter(bp_plan *p, const void *in, bp_dtype dt, float *out, int
     }
 #undef BP_FILTER_LAUNCH
     BP_CUDA_TRY(cudaGetLastError());
+    stage_mark(p, st, "filter_kernel");
     return BP_OK;
 }
 
@@ -357,6 +360,7 @@ bp_status launch_filter_response(bp_plan *p, const void *in, bp_dtype dt, float 
                                  cudaStream_t st) {
     if ((size_t)(p->P + p->P / 2) * sizeof(float2) > 200u * 1024u)
         return fail(BP_ERR_UNSUPPORTED, "filter: n_det too large for the shared-memory FFT (n_det <= 8192)");
+    stage_begin(p, st);
     const long long rows = (long long)batch * p->n_theta;
     if (p->d_twpass) return launch_pt_any(p, in, dt, out, H, rows, st);
     const int logP = ilog2(p->P);
@@ -384,6 +388,7 @@ bp_status launch_filter_response(bp_plan *p, const void *in, bp_dtype dt, float 
     }
 #undef BP_FILTER_LAUNCH_H
     BP_CUDA_TRY(cudaGetLastError());
+    stage_mark(p, st, "filter_kernel");
     return BP_OK;
 }
 

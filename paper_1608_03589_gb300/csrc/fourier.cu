@@ -1259,6 +1259,7 @@ static bp_status spectra_pt(bp_plan *p, const Tin *sino, cudaStream_t st, float 
     const int ctas = std::min(npairs, std::max(1, per_sm) * std::max(1, p->sm_count));
     kern<<<ctas, NT, smem, st>>>(sino, p->four.spec, p->four.wk, p->d_twpass, p->n_theta, p->n_det, wuni,
                                  p->four.ray, delta2, Hf);
+    stage_mark(p, st, "fourier_spectra_pt_kernel");
     return BP_OK;
 }
 
@@ -1280,6 +1281,7 @@ static bp_status spectra_t(bp_plan *p, const Tin *sino, cudaStream_t st, float w
     BP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     kern<<<(p->n_theta + 1) / 2, threads, smem, st>>>(sino, p->four.spec, p->four.wk, p->d_twP, p->n_theta, p->n_det,
                                                       logP, wuni, p->four.ray, delta2, Hf);
+    stage_mark(p, st, "fourier_spectra_kernel");
     return BP_OK;
 }
 
@@ -1302,7 +1304,9 @@ static bp_status launch_grid_to_image_rows(bp_plan *p, const float *deap, float 
     const int nthr = fft_threads(M);
     const int groups = 1;
     pass_y<<<M / R, nthr * groups, smemR, st>>>(f.grid, f.mid, deap, f.twM, M, f.logM, N, R, p->d_err);
+    stage_mark(p, st, "ifft_pass_y_kernel");
     pass_x<<<(N + R - 1) / R, nthr * groups, smemR, st>>>(f.mid, img, deap, f.twM, M, f.logM, N, R, p->d_err);
+    stage_mark(p, st, "ifft_pass_x_kernel");
     BP_CUDA_TRY(cudaGetLastError());
     return BP_OK;
 }
@@ -1325,8 +1329,10 @@ static bp_status launch_ifft_pt(bp_plan *p, const float *deap, float *img, cudaS
     // the y pass takes rows in pairs (M is even)
     ky<<<std::min(std::max(1, per_sm_y) * sms, M / 2), NT, smem_y, st>>>(f.grid, f.mid, nullptr, deap, f.twpassM, M,
                                                                         p->N);
+    stage_mark(p, st, "ifft_pt_kernel (y pass)");
     kx<<<std::min(std::max(1, per_sm_x) * sms, p->N), NT, smem_x, st>>>(f.mid, nullptr, img, deap, f.twpassM, p->N,
                                                                        p->N);
+    stage_mark(p, st, "ifft_pt_kernel (x pass)");
     BP_CUDA_TRY(cudaGetLastError());
     return BP_OK;
 }
@@ -1369,6 +1375,7 @@ bp_status launch_fourier(bp_plan *p, const void *sino, bp_dtype dt, float *img, 
     FourierWork &f = p->four;
     const int N = p->N, M = f.M, H = p->P / 2;
     const size_t esz = dt == BP_F32 ? 4 : 2;
+    stage_begin(p, st);
     const float delta2 = (N % 2 == 0) ? 1.0f / (float)M : 0.0f;  // 2 delta / M
     for (int b = 0; b < batch; ++b) {
         const char *sb = (const char *)sino + esz * (size_t)b * p->n_theta * p->n_det;
@@ -1385,11 +1392,15 @@ bp_status launch_fourier(bp_plan *p, const void *sino, bp_dtype dt, float *img, 
         if (f.W == 4) {
             grid_gather_pair_kernel<2><<<g, 256, 0, st>>>(f.spec, sr, f.sphi, f.kbtab, f.grid, M, H, f.ri, f.rmax,
                                                           amax, core);
+            stage_mark(p, st, "grid_gather_pair_kernel");
             launch_core<2>(f, sr, M, H, amax, core, st);
+            stage_mark(p, st, "grid_gather_core_kernel");
         } else {
             grid_gather_pair_kernel<3><<<g, 256, 0, st>>>(f.spec, sr, f.sphi, f.kbtab, f.grid, M, H, f.ri, f.rmax,
                                                           amax, core);
+            stage_mark(p, st, "grid_gather_pair_kernel");
             launch_core<3>(f, sr, M, H, amax, core, st);
+            stage_mark(p, st, "grid_gather_core_kernel");
         }
         BP_CUDA_TRY(cudaGetLastError());
         if ((s = launch_grid_to_image(p, f.deapod, img + (size_t)b * N * N, st)) != BP_OK) return s;
@@ -1476,6 +1487,7 @@ static bp_status launch_fft_pt_fwd(bp_plan *p, const float *img, cudaStream_t st
     BP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kx, NT, smem));
     const int ctas = std::max(1, per_sm) * std::max(1, p->sm_count);
     kx<<<std::min(ctas, p->N), NT, smem, st>>>(img, nullptr, f.mid, f.deapod, f.twpassM, p->N, p->N);
+    stage_mark(p, st, "fft_pt_fwd_kernel (x pass)");
     if (2 * p->N == M) {
         // columns in pairs, 16-byte loads
         constexpr size_t smem2 = smem + sizeof(float2) * (M / 2);
@@ -1485,8 +1497,10 @@ static bp_status launch_fft_pt_fwd(bp_plan *p, const float *img, cudaStream_t st
         BP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, kc, NT, smem2));
         kc<<<std::min(std::max(1, per_sm2) * std::max(1, p->sm_count), M / 2), NT, smem2, st>>>(f.mid, f.grid,
                                                                                                f.twpassM, M);
+        stage_mark(p, st, "fft_pt_fwd_cols_kernel");
     } else {
         ky<<<std::min(ctas, M), NT, smem, st>>>(nullptr, f.mid, f.grid, f.deapod, f.twpassM, M, p->N);
+        stage_mark(p, st, "fft_pt_fwd_kernel (y pass)");
     }
     BP_CUDA_TRY(cudaGetLastError());
     return BP_OK;
@@ -1503,6 +1517,7 @@ static bp_status launch_adj_rows_pt(bp_plan *p, float *sino, cudaStream_t st) {
     const int npairs = (p->n_theta + 1) / 2;
     const int ctas = std::min(npairs, std::max(1, per_sm) * std::max(1, p->sm_count));
     kern<<<ctas, NT, smem, st>>>(p->four.spec, sino, p->d_twpass, p->n_theta, p->n_det);
+    stage_mark(p, st, "adj_rows_pt_kernel");
     return BP_OK;
 }
 
@@ -1526,6 +1541,7 @@ bp_status launch_radon_fourier(bp_plan *p, const float *img, float *sino, int ba
     BP_CUDA_TRY(cudaFuncSetAttribute(kr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(float2) * (P + P / 2))));
     const float delta2 = (N % 2 == 0) ? 1.0f / (float)M : 0.0f;
     const float scale = (float)(p->dx * p->dx / p->dt);
+    stage_begin(p, st);
     for (int b = 0; b < batch; ++b) {
         const float *ib = img + (size_t)b * N * N;
         switch (f.logM) {
@@ -1536,7 +1552,9 @@ bp_status launch_radon_fourier(bp_plan *p, const float *img, float *sino, int ba
             case 13: s = launch_fft_pt_fwd<13>(p, ib, st); break;
             default:
                 kx<<<(N + R - 1) / R, nthr * groups, smemR, st>>>(ib, f.mid, f.deapod, f.twM, M, f.logM, N, R);
+                stage_mark(p, st, "adj_fft_x_kernel");
                 ky<<<M / R, nthr * groups, smemR, st>>>(f.mid, f.grid, f.twM, M, f.logM, N, R);
+                stage_mark(p, st, "adj_fft_y_kernel");
         }
         if (s != BP_OK) return s;
         {
@@ -1545,6 +1563,7 @@ bp_status launch_radon_fourier(bp_plan *p, const float *img, float *sino, int ba
             BP_CUDA_TRY(cudaFuncSetAttribute(kt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
             kt<<<f.adj_n_items, 256, sm, st>>>(f.grid, f.spec, f.ray, f.adj_items, f.adj_segs, M, H, P, p->n_det,
                                                f.kbtab, delta2, scale, per_angle_w ? f.wk : nullptr);
+            stage_mark(p, st, "adj_interp_tiled_kernel");
         }
         float *sb = sino + (size_t)b * p->n_theta * p->n_det;
         switch (p->d_twpass ? ilog2(P) : 0) {
@@ -1555,6 +1574,7 @@ bp_status launch_radon_fourier(bp_plan *p, const float *img, float *sino, int ba
             default:
                 kr<<<(p->n_theta + 1) / 2, fft_threads(P), sizeof(float2) * (P + P / 2), st>>>(
                     f.spec, sb, p->d_twP, p->n_theta, p->n_det, ilog2(P));
+                stage_mark(p, st, "adj_rows_kernel");
         }
         if (s != BP_OK) return s;
         BP_CUDA_TRY(cudaGetLastError());

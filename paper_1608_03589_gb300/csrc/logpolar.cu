@@ -422,6 +422,7 @@ bp_status launch_logpolar(bp_plan *p, const void *sino, bp_dtype dt, float *img,
     const size_t smemL = sizeof(float2) * ((size_t)w.L + w.L / 2);
     auto kinv = fft_elems(w.L) == 16 ? lp_rows_inv_kernel<16> : lp_rows_inv_kernel<8>;
     BP_CUDA_TRY(cudaFuncSetAttribute(kinv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smemL));
+    stage_begin(p, st);
     for (int b = 0; b < batch; ++b) {
         const char *sb = (const char *)sino + esz * (size_t)b * p->n_theta * p->n_det;
         switch (dt) {
@@ -430,13 +431,17 @@ bp_status launch_logpolar(bp_plan *p, const void *sino, bp_dtype dt, float *img,
             case BP_F16: s = rows_fwd(p, (const __half *)sb, 0, st); break;
         }
         if (s != BP_OK) return s;
+        stage_mark(p, st, "lp_rows_fwd_kernel");
         if ((s = cols(p, 0, 1.f, st)) != BP_OK) return s;
+        stage_mark(p, st, "lp_cols_kernel");
         kinv<<<w.n_phi / 2, fft_threads(w.L), smemL, st>>>(w.T, w.B, w.twL, ilog2(w.L), w.n_out);
+        stage_mark(p, st, "lp_rows_inv_kernel");
         float *ib = img + (size_t)b * N * N;
         const int NN = N * N;
         lp_cart_kernel<<<(NN + 255) / 256, 256, 0, st>>>(w.B, w.pix, ib, NN, w.n_phi, w.n_out);
         if (N % 2 == 1) lp_centre_kernel<<<1, 256, 0, st>>>(w.B, ib, (N / 2) * N + N / 2, w.n_phi, w.n_out);
         BP_CUDA_TRY(cudaGetLastError());
+        stage_mark(p, st, "lp_cart_kernel");
     }
     return BP_OK;
 }

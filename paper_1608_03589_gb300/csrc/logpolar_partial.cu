@@ -464,6 +464,7 @@ bp_status launch_logpolar_partial(bp_plan *p, const void *sino, bp_dtype dt, flo
     const size_t smemL = sizeof(float2) * ((size_t)w.Lr + w.Lr / 2);
     auto kinv = fft_elems(w.Lr) == 16 ? lpp_rows_inv_kernel<16> : lpp_rows_inv_kernel<8>;
     BP_CUDA_TRY(cudaFuncSetAttribute(kinv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smemL));
+    stage_begin(p, st);
     for (int b = 0; b < batch; ++b) {
         const char *sb = (const char *)sino + esz * (size_t)b * p->n_theta * p->n_det;
         float *ib = img + (size_t)b * NN;
@@ -474,11 +475,15 @@ bp_status launch_logpolar_partial(bp_plan *p, const void *sino, bp_dtype dt, flo
                 case BP_F16: s = rows_fwd_lpp(p, (const __half *)sb, q, 0, st); break;
             }
             if (s != BP_OK) return s;
+            stage_mark(p, st, "lpp_rows_fwd_kernel");
             if ((s = cols_lpp(p, 0, 1.f, st)) != BP_OK) return s;
+            stage_mark(p, st, "lpp_cols_kernel");
             kinv<<<(w.n_aout + 1) / 2, fft_threads(w.Lr), smemL, st>>>(w.T, w.B, w.twLr, ilog2(w.Lr), w.n_aout,
                                                                        w.c_lo, w.n_out);
+            stage_mark(p, st, "lpp_rows_inv_kernel");
             lpp_cart_kernel<<<(NN + 255) / 256, 256, 0, st>>>(w.B, w.pix + (size_t)q * NN, ib, NN, w.n_out, q > 0);
             BP_CUDA_TRY(cudaGetLastError());
+            stage_mark(p, st, "lpp_cart_kernel");
         }
     }
     return BP_OK;

@@ -95,6 +95,32 @@ static void angle_weights(const std::vector<double> &theta, std::vector<double> 
     }
 }
 
+static void timer_record(bp_plan *p, cudaStream_t st, const char *name) {
+    StageTimer &t = p->timer;
+    if (!t.on) return;
+    if (t.used >= kStageTimerCap) {
+        t.overflow = true;
+        return;
+    }
+    if (t.used == (int)t.ev.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            t.overflow = true;
+            return;
+        }
+        t.ev.push_back(e);
+        t.name.push_back(nullptr);
+    }
+    if (cudaEventRecord(t.ev[t.used], st) != cudaSuccess) {
+        t.overflow = true;
+        return;
+    }
+    t.name[t.used++] = name;
+}
+
+void stage_begin(bp_plan *p, cudaStream_t st) { timer_record(p, st, nullptr); }
+void stage_mark(bp_plan *p, cudaStream_t st, const char *name) { timer_record(p, st, name); }
+
 static long long to_fix32(double v) { return (long long)std::llround(std::ldexp(v, 32)); }
 
 }  // namespace bp
@@ -107,6 +133,8 @@ extern "C" const char *bp_last_error(void) { return last_error_cstr(); }
 extern "C" const char *bp_version(void) { return "bp 0.1 sm_103a"; }
 
 static void plan_free_device(bp_plan *p) {
+    for (cudaEvent_t e : p->timer.ev) cudaEventDestroy(e);
+    p->timer.ev.clear();
     cudaFree(p->d_ang);
     cudaFree(p->d_twP);
     cudaFree(p->d_twpass);
@@ -484,4 +512,54 @@ extern "C" bp_status bp_backproject_transpose(bp_plan *p, const float *img, floa
     // A^T = (dt/dx^2) diag(w) R: R with angle k scaled by w_k instead of dx^2/dt
     if (fourier) return launch_radon_fourier(p, img, sino, batch, (cudaStream_t)stream, 1);
     return launch_radon_direct(p, img, sino, batch, (cudaStream_t)stream, 1);
+}
+
+extern "C" bp_status bp_stage_timing(bp_plan *p, int on) {
+    set_error("");
+    bp_status st = check_plan(p);
+    if (st != BP_OK) return st;
+    p->timer.on = on != 0;
+    p->timer.used = 0;
+    p->timer.overflow = false;
+    return BP_OK;
+}
+
+extern "C" bp_status bp_stage_times(bp_plan *p, int cap, const char **names, float *ms, int *launches, int *count) {
+    set_error("");
+    bp_status st = check_plan(p);
+    if (st != BP_OK) return st;
+    if (!count || (cap > 0 && (!names || !ms || !launches)) || cap < 0)
+        return fail(BP_ERR_INVALID_ARG, "bp_stage_times: NULL output or negative capacity");
+    StageTimer &t = p->timer;
+    if (t.overflow) {
+        t.used = 0;
+        t.overflow = false;
+        return fail(BP_ERR_UNSUPPORTED, "bp_stage_times: more launches than the timer records; read it more often");
+    }
+    struct Agg {
+        const char *name;
+        double ms;
+        int launches;
+    };
+    std::vector<Agg> agg;
+    if (t.used > 0) BP_CUDA_TRY(cudaEventSynchronize(t.ev[t.used - 1]));
+    for (int i = 1; i < t.used; ++i) {
+        if (!t.name[i]) continue;
+        float dt_ms = 0.f;
+        BP_CUDA_TRY(cudaEventElapsedTime(&dt_ms, t.ev[i - 1], t.ev[i]));
+        size_t j = 0;
+        while (j < agg.size() && std::strcmp(agg[j].name, t.name[i]) != 0) ++j;
+        if (j == agg.size()) agg.push_back({t.name[i], 0.0, 0});
+        agg[j].ms += dt_ms;
+        agg[j].launches += 1;
+    }
+    const int n = (int)agg.size();
+    for (int j = 0; j < n && j < cap; ++j) {
+        names[j] = agg[j].name;
+        ms[j] = (float)agg[j].ms;
+        launches[j] = agg[j].launches;
+    }
+    t.used = 0;
+    *count = n;
+    return BP_OK;
 }

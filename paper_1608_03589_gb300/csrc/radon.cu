@@ -557,7 +557,11 @@ bp_status launch_radon_shape(bp_plan *p, const float *img, float *sino, int batc
     const int ablocks = (p->n_theta + kAng - 1) / kAng;
     const int per_band = (ntiles + bands - 1) / bands;
     const int use_atomic = bands > 1;
-    if (use_atomic) BP_CUDA_TRY(cudaMemsetAsync(sino, 0, sizeof(float) * sino_n * batch, st));
+    stage_begin(p, st);
+    if (use_atomic) {
+        BP_CUDA_TRY(cudaMemsetAsync(sino, 0, sizeof(float) * sino_n * batch, st));
+        stage_mark(p, st, "memset (R image bands)");
+    }
     const float scale = (float)(p->dx * p->dx / p->dt);
     dim3 grid(ablocks, bands, batch);
     if (radon_quad_form(p)) {
@@ -565,11 +569,13 @@ bp_status launch_radon_shape(bp_plan *p, const float *img, float *sino, int batc
         radon_quad_kernel<<<grid, kRThreads, smem, st>>>(img, sino, p->d_ang, p->N, p->n_det, p->n_theta, p->W, p->C,
                                                          kAng, per_band, scale, use_atomic, (long long)p->N * p->N,
                                                          (long long)sino_n, per_angle_w);
+        stage_mark(p, st, "radon_quad_kernel");
     } else {
         BP_CUDA_TRY(cudaFuncSetAttribute(radon_direct_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         radon_direct_kernel<<<grid, kRThreads, smem, st>>>(img, sino, p->d_ang, p->N, p->n_det, p->n_theta, p->W,
                                                            p->C, kAng, per_band, scale, use_atomic,
                                                            (long long)p->N * p->N, (long long)sino_n, per_angle_w);
+        stage_mark(p, st, "radon_direct_kernel");
     }
     BP_CUDA_TRY(cudaGetLastError());
     return BP_OK;

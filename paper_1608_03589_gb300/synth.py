@@ -183,6 +183,10 @@ VOLUME = Workload("volume256_slice2048_bins2048_ang1800_bf16", 2048, 2048, 1800,
 VOLUME_SLICES = 256
 
 
+# Single high-resolution slice: 8192^2 image, 8192 bins, 6000 angles, 30 ellipses.
+HIRES = Workload("slice8192_bins8192_ang6000", 8192, 8192, 6000, 30, 0.0, 5999)
+
+
 def mixed_batch_geometries(n: int = 64, seed: int = 5000):
     """Uneven batch: image side = detector width drawn from {512, 1024, 2048, 4096}, angle
     counts uniform in [360, 3000] (uniform angles on [0, pi))."""

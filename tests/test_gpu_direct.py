@@ -337,3 +337,35 @@ def test_fbp_pipeline_in_cuda_graph():
     torch.cuda.synchronize()
     for o, r in zip(outs, ref):
         assert torch.equal(o, r)
+
+
+def test_stage_timer_reports_each_kernel():
+    # bp_stage_timing / bp_stage_times: one record per kernel launch, names of the kernels that ran,
+    # times that add up to the calls' own CUDA-event time
+    wl = synth.SMALL
+    plan = bp.Plan(wl.N, wl.n_det, wl.theta, wl.det_spacing)
+    g = to_dev(wl.sinogram())
+    q = plan.filter(g, "ramlak")
+    plan.backproject(q)
+    plan.backproject_fourier(q)
+    torch.cuda.synchronize()
+    plan.stage_timing(True)
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record()
+    for _ in range(3):
+        plan.filter(g, "ramlak", out=q)
+        img = plan.backproject(q)
+        plan.backproject_fourier(q)
+    e.record()
+    times = plan.stage_times()
+    plan.stage_timing(False)
+    torch.cuda.synchronize()
+    assert times["filter_pt_kernel"][1] == 3
+    assert any(k.startswith("bp_direct") for k in times)
+    assert times["grid_gather_pair_kernel"][1] == 3 and times["fourier_spectra_pt_kernel"][1] == 3
+    assert all(ms > 0 for ms, _ in times.values())
+    total = sum(ms for ms, _ in times.values())
+    assert total <= s.elapsed_time(e) * 1.01 + 0.01
+    assert plan.stage_times() == {}  # records dropped after a read
+    ref = oracle.bp_linear(rounded(q), wl.N, wl.theta, wl.det_spacing)
+    assert oracle.rel_l2(img.cpu().numpy(), ref) <= TOL_DIRECT
