@@ -358,7 +358,14 @@ bp_status bp_stage_times(bp_plan *plan, int cap, const char **names, float *ms, 
  *               (8, 16 or 32); shape[1] = angle groups (>= 1): each 64 x 64 pixel tile is
  *               backprojected by shape[1] CTAs over disjoint angle ranges whose partial sums
  *               are added atomically (the summation order then varies between runs, within
- *               FP32 rounding).
+ *               FP32 rounding).  Geometries with N even, pixels no larger than bins and an
+ *               angle set closed under theta -> pi - theta (every uniform set) take the
+ *               four-image form instead (one thread serves a pixel block and its three mirror
+ *               images; per-call row tables in a plan workspace allocated on first use):
+ *               shape[0] = 8 selects two CTAs per SM, else three; shape[1] = angle groups of
+ *               its persistent schedule (<= 64); its partial sums are always added atomically,
+ *               so its summation order varies between runs within FP32 rounding.
+ *               bp_fbp_static never takes it (it allocates nothing).
  * BP_OP_RADON   direct R (bp_radon and bp_backproject_transpose with the direct form):
  *               shape[0] = angles per CTA (1, 2 or 4); shape[1] = image bands per angle block
  *               (>= 1; partial sinograms added atomically when > 1).  When pixels are no

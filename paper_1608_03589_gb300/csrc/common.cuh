@@ -117,7 +117,18 @@ struct LppWork {
 // bp_autotune (tune.cu) or by the default rules there.
 struct DirectShape {
     int stage = kStage;
-    int asplit = 1;
+    int asplit = 1;      // angle groups (the four-image form: groups of its persistent schedule)
+    int workspace = 1;   // 0: never take a form that needs a plan workspace (allocation-free calls)
+};
+// The four-image form of the direct R* (direct_klein.cu): eligibility and per-angle data made
+// on the host at plan creation; the per-angle table and the row-table workspace (one slice,
+// 2 x n_theta x L float4) are allocated on first use.
+struct KleinWork {
+    bool eligible = false;
+    int jlo = 0, L = 0, nr = 0;          // table extent (bins jlo .. jlo + L - 1), regions per side
+    std::vector<unsigned char> host;     // per-angle records (KleinAngle)
+    void *d_ang = nullptr;
+    float4 *tab = nullptr;
 };
 struct RadonShape {
     int kang = 0;   // 0 = the default rule
@@ -185,6 +196,7 @@ struct bp_plan {
     std::vector<bp::TuneEntry> shapes;
     int sm_count = 0;
     bp::StageTimer timer;
+    bp::KleinWork klein;
 };
 
 namespace bp {
@@ -228,6 +240,12 @@ bp_status ensure_filter(bp_plan *p, int kind, float param);
 bp_status launch_filter_response(bp_plan *p, const void *in, bp_dtype dt, float *out, const float *Hbr, int batch,
                                  cudaStream_t st);
 bp_status ensure_fourier(bp_plan *p);
+void klein_plan(bp_plan *p);
+void free_klein(bp_plan *p);
+int klein_default_groups(const bp_plan *p);
+int klein_clamp_groups(const bp_plan *p, int S);
+bp_status launch_direct_klein(bp_plan *p, const void *sino, bp_dtype dt, float *img, int batch, int accumulate,
+                              cudaStream_t st, float wuni, int stage, int S);
 void free_fourier(bp_plan *p);
 void free_bst(bp_plan *p);
 void free_logpolar(bp_plan *p);

@@ -36,6 +36,11 @@
 //
 // In both forms the per-tile window origin J0 and base coordinate come from exact 32.32
 // fixed-point tile stepping, so float32 only ever holds tile-local coordinates (|q| <= W/2).
+//
+// When N is even, pixels are no larger than bins and the angle set is closed under
+// theta -> pi - theta (every uniform set), launch_direct_shape takes the four-image form of
+// direct_klein.cu instead (it needs a plan workspace; calls that must not allocate keep the forms
+// here).
 #include <cudaTypedefs.h>
 
 #include <algorithm>
@@ -279,6 +284,12 @@ bool quad_form(const bp_plan *p) {
 DirectShape direct_effective(const bp_plan *p, int esz, bool tma, DirectShape shape) {
     DirectShape e;
     e.stage = kStage;
+    e.workspace = shape.workspace;
+    if (shape.workspace && p->klein.eligible) {
+        e.stage = shape.stage == 8 ? 8 : kStage;  // the four-image form: 2 or 3 CTAs per SM
+        e.asplit = klein_clamp_groups(p, shape.asplit);
+        return e;
+    }
     if (tma && !quad_form(p)) {
         e.stage = (shape.stage == 8 || shape.stage == 32) ? shape.stage : kStage;
         while (e.stage > 8 && tma_smem(p, e.stage, esz) > kMaxDirectSmem) e.stage >>= 1;
@@ -372,6 +383,9 @@ bp_status launch_direct_t(bp_plan *p, const Tin *sino, float *img, int batch, in
 
 bp_status launch_direct_shape(bp_plan *p, const void *sino, bp_dtype dt, float *img, int batch, int accumulate,
                               cudaStream_t st, float wuni, DirectShape shape) {
+    if (dt != BP_F32 && dt != BP_BF16 && dt != BP_F16) return fail(BP_ERR_INVALID_ARG, "invalid dtype");
+    if (shape.workspace && p->klein.eligible)
+        return launch_direct_klein(p, sino, dt, img, batch, accumulate, st, wuni, shape.stage, shape.asplit);
     switch (dt) {
         case BP_F32: return launch_direct_t(p, (const float *)sino, img, batch, accumulate, st, wuni, shape);
         case BP_BF16:

@@ -76,7 +76,9 @@ extern "C" bp_status bp_fbp_static(bp_plan *p, const void *sino, bp_dtype dtype,
         const char *sb = (const char *)sino + esz * slice * b;
         st = launch_filter_response(p, sb, dtype, q, H, 1, s);
         if (st != BP_OK) return st;
-        st = launch_direct(p, q, BP_F32, img + (size_t)b * p->N * p->N, 1, 0, s);
+        DirectShape shape = direct_shape(p, BP_F32, 1);
+        shape.workspace = 0;  // the forms that need a plan workspace would allocate it
+        st = launch_direct_shape(p, q, BP_F32, img + (size_t)b * p->N * p->N, 1, 0, s, 0.f, shape);
         if (st != BP_OK) return st;
     }
     return BP_OK;

@@ -143,6 +143,7 @@ static void plan_free_device(bp_plan *p) {
     free_bst(p);
     free_logpolar(p);
     free_logpolar_partial(p);
+    free_klein(p);
     cudaFree(p->d_stage);
     for (int k = 0; k < kHostSlots; ++k) {
         if (p->ev_h2d[k]) cudaEventDestroy(p->ev_h2d[k]);
@@ -212,6 +213,7 @@ extern "C" bp_plan *bp_plan_create(int N, int n_det, int n_theta, const double *
         return nullptr;
     }
     p->P = 1 << ilog2(2 * n_det);
+    klein_plan(p);
 
     cudaError_t e = cudaMalloc(&p->d_err, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(p->d_err, 0, sizeof(int));

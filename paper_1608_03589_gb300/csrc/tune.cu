@@ -71,6 +71,10 @@ int tiles_of(const bp_plan *p) { return (p->N + kTile - 1) / kTile; }
 // waves of three CTAs per SM.
 DirectShape direct_default(const bp_plan *p, int batch) {
     DirectShape s;
+    if (p->klein.eligible) {
+        s.asplit = klein_default_groups(p);
+        return s;
+    }
     const long long ctas = (long long)tiles_of(p) * tiles_of(p) * batch;
     const long long slots = 3LL * std::max(1, p->sm_count);
     if (ctas < 2 * slots) s.asplit = (int)((2 * slots + ctas - 1) / ctas);
@@ -225,7 +229,8 @@ extern "C" bp_status bp_autotune(bp_plan *p, bp_op op, bp_dtype dtype, int batch
         for (int stage : {16, 8, 32}) {
             for (int a : kSplits) {
                 // more groups than about 16 waves only adds atomic traffic; always try the default
-                if (a > 1 && a != def.asplit && ctas * a > 16 * slots) continue;
+                // (the four-image form's groups cut its persistent schedule: up to 64 of them)
+                if (a > 1 && a != def.asplit && (p->klein.eligible ? a > 64 : ctas * a > 16 * slots)) continue;
                 DirectShape cand;
                 cand.stage = stage;
                 cand.asplit = a;

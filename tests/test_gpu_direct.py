@@ -369,3 +369,62 @@ def test_stage_timer_reports_each_kernel():
     assert plan.stage_times() == {}  # records dropped after a read
     ref = oracle.bp_linear(rounded(q), wl.N, wl.theta, wl.det_spacing)
     assert oracle.rel_l2(img.cpu().numpy(), ref) <= TOL_DIRECT
+
+
+# ----------------------------------------------------------------------------------- R*, four-image form
+def _mirror_set(rng, n_half, whole_circle):
+    """A mirror-symmetric angle set: random angles in (0, pi/2), their mirrors pi - theta, and the
+    self-mirrored 0 and pi/2; optionally some angles moved by pi (their rows then pair backwards)."""
+    half = rng.uniform(0.0, np.pi / 2, n_half)
+    th = np.concatenate([[0.0, np.pi / 2], half, np.pi - half])
+    if whole_circle:
+        th = th + np.pi * (rng.uniform(size=th.shape) < 0.5)
+    return rng.permutation(th)
+
+
+def _kernels(plan, call):
+    plan.stage_timing(True)
+    out = call()
+    names = set(plan.stage_times())
+    plan.stage_timing(False)
+    return out, names
+
+
+@pytest.mark.parametrize("N,n_det,n_theta,dt_scale,seed,angles", [
+    (64, 64, 90, 1.0, 30, "uniform"), (66, 41, 7, 1.3, 31, "uniform"),  # N/2 odd: last block column split
+    (100, 128, 16, 1.3, 32, "mirror"), (130, 130, 61, 1.0, 33, "whole-circle"),
+    (256, 300, 180, 1.2, 34, "uniform"), (192, 150, 40, 1.2, 35, "whole-circle")])
+def test_direct_four_image_form(N, n_det, n_theta, dt_scale, seed, angles):
+    # even N and a mirror-symmetric angle set take the four-image kernel (global row tables); the
+    # whole image against the oracle, also with accumulation, a batch of two and BF16 storage
+    rng = np.random.default_rng(seed)
+    theta = synth.uniform_theta(n_theta) if angles == "uniform" else _mirror_set(rng, n_theta, angles == "whole-circle")
+    dt = dt_scale * 2.0 / n_det
+    plan = bp.Plan(N, n_det, theta, dt)
+    g = to_dev(rng.normal(size=(2, len(theta), n_det)))
+    img, names = _kernels(plan, lambda: plan.backproject(g))
+    assert "bp_direct_klein_kernel" in names and "klein_tables_kernel" in names, names
+    for i in range(2):
+        ref = oracle.bp_linear(rounded(g[i]), N, theta, dt)
+        assert oracle.rel_l2(img[i].cpu().numpy(), ref) <= TOL_DIRECT
+    base = to_dev(rng.normal(size=(2, N, N)))
+    acc = base.clone()
+    plan.backproject(g, out=acc, accumulate=True)
+    assert oracle.rel_l2(acc.cpu().numpy(), img.cpu().numpy() + rounded(base)) <= TOL_DIRECT
+    g16 = g[0].to(torch.bfloat16)
+    ref16 = oracle.bp_linear(rounded(g16), N, theta, dt)
+    assert oracle.rel_l2(plan.backproject(g16).cpu().numpy(), ref16) <= TOL_DIRECT
+    for S in (1, 3, 64):  # angle groups of the persistent schedule
+        plan.set_shape((16, S), "direct", torch.float32, 2)
+        assert oracle.rel_l2(plan.backproject(g).cpu().numpy(), img.cpu().numpy()) <= TOL_DIRECT
+
+
+def test_direct_four_image_form_not_taken_without_symmetry():
+    # odd N, or an angle set without mirror partners, keeps the shared-memory kernels
+    rng = np.random.default_rng(36)
+    for N, theta in ((65, synth.uniform_theta(40)), (64, random_theta(rng, 40))):
+        plan = bp.Plan(N, 64, theta)
+        g = to_dev(rng.normal(size=(len(theta), 64)))
+        img, names = _kernels(plan, lambda: plan.backproject(g))
+        assert "bp_direct_klein_kernel" not in names and any(n.startswith("bp_direct") for n in names), names
+        assert oracle.rel_l2(img.cpu().numpy(), oracle.bp_linear(rounded(g), N, theta, plan.det_spacing)) <= TOL_DIRECT
