@@ -16,6 +16,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -31,9 +32,11 @@ sys.path.insert(0, ROOT)
 FLOPS_PER_UPDATE = 7          # coordinate FMA (2) + fraction (1) + lerp sub and FMA (3) + accumulate (1)
 FP32_LANES_PER_SM = 128       # FP32 FMA lanes per SM
 L2_FLUSH_BYTES = 256 << 20    # > 129 MB L2
-# shared-memory wavefront caps (128 B/clk/SM): the pair-table kernel reads 8 B per update,
-# the 2 x 2-block kernel one 16-byte entry per 4 updates
-SMEM_UPDATES_PER_CLK = {"bp_direct_tma_kernel": 16, "bp_direct_quad_sync_kernel": 32}
+# sources whose content the committed DRAM-traffic record of a kernel is tied to
+KERNEL_SOURCES = {
+    "bp_direct_klein_kernel": ("direct_klein.cu", "direct_tile.cuh", "tma.cuh", "f32x2.cuh", "geometry.cuh"),
+    "bp_direct_quad_sync_kernel": ("direct.cu", "direct_tile.cuh", "tma.cuh", "geometry.cuh", "f32x2.cuh"),
+}
 
 
 def _peaks():
@@ -44,22 +47,22 @@ def _peaks():
         return {}
 
 
-def _kernel_hash() -> str:
+def kernel_hash(kernel: str) -> str:
     h = hashlib.sha256()
-    for fn in ("direct.cu", "direct_tile.cuh", "tma.cuh", "geometry.cuh", "f32x2.cuh"):
+    for fn in KERNEL_SOURCES.get(kernel, ()):
         with open(os.path.join(ROOT, "paper_1608_03589_gb300", "csrc", fn), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
-def _traffic_record(shape):
-    """DRAM bytes per launch of the direct kernel from the committed ncu summary, if the
-    kernel source is unchanged since that capture and it used the same launch shape; else None."""
-    path = os.path.join(ROOT, "profiles", "bp_direct_kernel_traffic.json")
+def _traffic_record(kernel, shape):
+    """DRAM bytes per launch of `kernel` from its committed ncu summary, if the kernel's sources are
+    unchanged since that capture and it used the same launch shape; else None."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_traffic.json")
     try:
         with open(path) as f:
             rec = json.load(f)
-        if rec.get("kernel_hash") == _kernel_hash() and list(rec.get("launch_shape", [])) == list(shape):
+        if rec.get("kernel_hash") == kernel_hash(kernel) and list(rec.get("launch_shape", [])) == list(shape):
             return rec
     except Exception:
         pass
@@ -206,23 +209,143 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline():
+def cpu_baseline(img_gpu=None):
     """The oracle as it stands on this host's cores: the whole filtered backprojection of the
-    2048^2 x 1800 workload (oracle Shepp-Logan filter on all rows, oracle R* on all pixels)."""
+    2048^2 x 1800 workload (oracle Shepp-Logan filter on all rows, oracle R* on all pixels); and
+    the step's GPU image against that FP64 result (the same float32 input)."""
     import oracle
     from paper_1608_03589_gb300 import synth
 
     wl = synth.LARGE
-    g = wl.sinogram()
+    g = wl.sinogram().astype(np.float32).astype(np.float64)  # the float32 values the device reads
     t0 = time.perf_counter()
     q = oracle.filter_rows(g, wl.det_spacing, oracle.SHEPP_LOGAN)
     t1 = time.perf_counter()
-    oracle.bp_linear(q, wl.N, wl.theta, wl.det_spacing)
+    b = oracle.bp_linear(q, wl.N, wl.theta, wl.det_spacing)
     t2 = time.perf_counter()
-    return {"value": wl.updates / (t2 - t0) / 1e9, "unit": "Gupdates/s", "cores": oracle.num_threads(),
+    base = {"value": wl.updates / (t2 - t0) / 1e9, "unit": "Gupdates/s", "cores": oracle.num_threads(),
             "kind": "oracle",
             "sample": f"the full workload once: FP64 oracle Shepp-Logan filter on all {wl.n_theta} rows "
                       f"({t1 - t0:.1f} s) + oracle R* on all {wl.N}x{wl.N} pixels ({t2 - t1:.1f} s)"}
+    err = None
+    if img_gpu is not None:
+        err = {"rel_l2": oracle.rel_l2(img_gpu, b),
+               "against": "FP64 oracle filter + R* of the same float32 sinogram, whole image (the step's output: "
+                          "FP32 filter and R* together)"}
+    return base, err
+
+
+# ----------------------------------------------------------------------------------------------- kernel rooflines
+# FP32 peak of the ALU roofline, TFLOP/s at 2070 MHz: the derived 152 SM x 128 lanes x 2 x f_clk
+# figure.  An FFMA-throughput probe on a GB300 of this pool reached FP32_PROBE_TFLOPS (recorded in
+# the design notes); the roofline uses the smaller of the two.
+FP32_PROBE_TFLOPS = 79.48  # paired-FMA (f32x2) issue probe, 152 SMs, clocks at 2070 MHz (scalar FFMA: 76.7)
+
+
+def fp32_peak_tflops(sm_count: int, sm_max_mhz: float):
+    derived = sm_count * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12
+    if FP32_PROBE_TFLOPS and FP32_PROBE_TFLOPS < derived:
+        return FP32_PROBE_TFLOPS, f"measured by an FFMA-throughput probe ({FP32_PROBE_TFLOPS:.1f} TFLOP/s, below " \
+                                  f"the derived {derived:.1f})"
+    return derived, f"{sm_count} SM x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max_mhz:.0f} MHz (max SM clock)"
+
+
+def klein_table_entries(N: int, n_det: int, theta, dt: float) -> int:
+    """Entries per row of the four-image form's row tables (the bins its blocks reach plus 4 on
+    each side), restated for the byte count of klein_tables_kernel."""
+    r = (2.0 / N) / dt
+    nr = (N // 2 + 31) // 32
+    E = 32 * nr - 1
+    c, s = np.cos(theta) * r, np.sin(theta) * r
+    u00 = (c + s) * (0.5 - 0.5 * N) + 0.5 * (n_det - 1)
+    lo = u00 + np.minimum(0, c * E) + np.minimum(0, s * E)
+    hi = u00 + np.maximum(0, c * E) + np.maximum(0, s * E)
+    return int(np.floor(hi.max()) + 4 - (np.floor(lo.min()) - 4) + 1)
+
+
+def kernel_work(name: str, c: dict):
+    """Algorithmic (bytes, flops) of one launch of kernel `name` on workload c (N, n_det, n_theta,
+    esz, P, M, W; an FFT of n points counts 5 n log2 n flops, an FMA 2): the per-unit figures of
+    the measurement plan times the units one slice processes.  None when no model is kept (the
+    kernels of the paper's own BST and of the log-polar methods)."""
+    N, nd, nt, esz = c["N"], c["n_det"], c["n_theta"], c.get("esz", 4)
+    P, M, W = c.get("P", 0), c.get("M", 0), c.get("W", 6)
+    upd = N * N * nt
+    lg = lambda n: math.log2(n) if n else 0.0
+    if name.startswith("bp_direct") or name in ("radon_quad_kernel", "radon_direct_kernel"):
+        return nt * nd * esz + 4 * N * N, 7 * upd
+    if name == "klein_tables_kernel":
+        L = klein_table_entries(N, nd, c["theta"], c["dt"])
+        return nt * nd * esz + 2 * 16 * nt * L, 8 * nt * L
+    if name.startswith("memset"):
+        return c.get("memset_bytes", 4 * N * N), 0
+    if name in ("filter_pt_kernel", "filter_kernel"):
+        return nt * nd * (esz + 4), nt * (5 * P * lg(P) + P)
+    if name in ("fourier_spectra_pt_kernel", "fourier_spectra_kernel"):
+        return nt * nd * esz + nt * (P // 2) * 8, nt * (2.5 * P * lg(P) + 6 * P)
+    if name == "gridding":
+        return nt * (P // 2) * 8 + 8 * M * M, 8 * W * W * nt * (P // 2)
+    if name in ("ifft_pt_kernel (y pass)", "ifft_pass_y_kernel"):
+        return 8 * M * M + 8 * N * M, M * 5 * M * lg(M)
+    if name in ("ifft_pt_kernel (x pass)", "ifft_pass_x_kernel"):
+        return 8 * N * M + 4 * N * N, N * 5 * M * lg(M)
+    if name == "fft_pt_fwd_kernel (x pass)":
+        return 4 * N * N + 8 * N * M, N * 5 * M * lg(M)
+    if name in ("fft_pt_fwd_cols_kernel", "fft_pt_fwd_kernel (y pass)"):
+        return 8 * N * M + 8 * M * M, M * 5 * M * lg(M)
+    if name == "adj_interp_tiled_kernel":
+        return 8 * M * M + nt * (P // 2) * 8, 8 * W * W * nt * (P // 2)
+    if name == "adj_rows_pt_kernel":
+        return nt * (P // 2) * 8 + 4 * nt * nd, nt * (2.5 * P * lg(P) + 6 * P)
+    return None
+
+
+def kernel_rooflines(times: dict, ctx: dict, hbm_gbs: float, fp32_tflops: float) -> dict:
+    """Per kernel of one call: its time (CUDA events on the launching stream, averaged over the
+    profiled calls), launches, algorithmic bytes and flops, and the fraction of the slower of the
+    HBM and FP32 bounds it reaches.  The two gridding kernels are reported together."""
+    times = dict(times)
+    gp = [k for k in ("grid_gather_pair_kernel", "grid_gather_core_kernel") if k in times]
+    if gp:
+        times["gridding"] = {"ms": sum(times[k]["ms"] for k in gp),
+                             "launches_per_call": sum(times[k]["launches_per_call"] for k in gp),
+                             "kernels": gp}
+        for k in gp:
+            times.pop(k)
+    out = {}
+    for name, t in times.items():
+        row = dict(t)
+        w = kernel_work(name, ctx)
+        if w is not None and t["ms"] > 0:
+            b, f = w
+            if not name.startswith("memset"):  # per-slice models; memset_bytes covers the whole call
+                b, f = b * ctx.get("batch", 1), f * ctx.get("batch", 1)
+            t_hbm = b / (hbm_gbs * 1e9)
+            t_alu = f / (fp32_tflops * 1e12)
+            sec = t["ms"] / 1e3
+            bound = "hbm" if t_hbm >= t_alu else "alu"
+            row.update({"bytes": b, "flops": f, "bound": bound,
+                        "achieved": (b / sec / 1e9) if bound == "hbm" else (f / sec / 1e12),
+                        "peak": hbm_gbs if bound == "hbm" else fp32_tflops,
+                        "unit": "GB/s" if bound == "hbm" else "TFLOP/s",
+                        "frac": max(t_hbm, t_alu) / sec})
+        out[name] = row
+    return out
+
+
+def kernel_profile(plan, fn, flush, reps=3):
+    """Per-kernel CUDA-event times of `fn` (calls on `plan`) from the library's stage timer: the
+    average per call over `reps` calls, the L2 flushed before each."""
+    import torch
+    plan.stage_timing(True)
+    plan.stage_times()
+    for _ in range(reps):
+        flush.zero_()
+        fn()
+    torch.cuda.synchronize()
+    t = plan.stage_times()
+    plan.stage_timing(False)
+    return {k: {"ms": ms / reps, "launches_per_call": n / reps} for k, (ms, n) in t.items()}
 
 
 # ----------------------------------------------------------------------------------------------- other paths
@@ -242,8 +365,10 @@ def _timed(fn, stream, flush, reps):
     return tot / reps
 
 
-def other_paths(plan, q, img, flush, stream, dev, only=()):
-    """Every other row of the path on its own workload, each timed with CUDA events."""
+def other_paths(plan, q, img, flush, stream, dev, only=(), peaks=(6778.3, 80.5), checks=None):
+    """Every other row of the path on its own workload, each timed with CUDA events; per kernel its
+    own event time and roofline fraction; for each, a check against the FP64 oracle is queued in
+    `checks` (name -> callable returning (rel_l2, what)), run later in the CPU-baseline leg."""
     import numpy as np
     import torch
 
@@ -251,7 +376,21 @@ def other_paths(plan, q, img, flush, stream, dev, only=()):
     from paper_1608_03589_gb300 import bp, synth
 
     wl = synth.LARGE
+    hbm, fp32 = peaks
     out = {}
+    checks = {} if checks is None else checks
+    ctx = {"N": wl.N, "n_det": wl.n_det, "n_theta": wl.n_theta, "esz": 4, "P": 4096, "M": 4096, "W": 6,
+           "theta": wl.theta, "dt": wl.det_spacing}
+    qh = q.double().cpu().numpy()  # the exact float32 values the kernels read, as FP64
+    rng = np.random.default_rng(11)
+    pix2048 = rng.choice(wl.N * wl.N, 120, replace=False)
+
+    def pick(t, idx):
+        return t.reshape(-1)[torch.from_numpy(np.asarray(idx)).to(t.device)].double().cpu().numpy()
+
+    def rel(a, b):
+        a, b = np.asarray(a, np.float64).ravel(), np.asarray(b, np.float64).ravel()
+        return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
     def guard(name, fn):
         if only and name not in only:
@@ -262,72 +401,166 @@ def other_paths(plan, q, img, flush, stream, dev, only=()):
             out[name] = {"unavailable": f"{type(exc).__name__}: {str(exc)[:160]}"}
         torch.cuda.empty_cache()
 
+    def prof(p, fn, c=ctx, reps=3):
+        return kernel_rooflines(kernel_profile(p, fn, flush, reps), c, hbm, fp32)
+
     # 2048^2 x 1800 slice: Fourier R*, R (direct and Fourier adjoint), BF16 storage
     def fourier():
         ms = _timed(lambda: plan.backproject_fourier(q, out=img), stream, flush, 10)
+        kern = prof(plan, lambda: plan.backproject_fourier(q, out=img))
+        got6 = pick(img, pix2048)
         plan.set_fourier_width(4)
         ms4 = _timed(lambda: plan.backproject_fourier(q, out=img), stream, flush, 10)
+        kern4 = prof(plan, lambda: plan.backproject_fourier(q, out=img), dict(ctx, W=4))
+        got4 = pick(img, pix2048)
         plan.set_fourier_width(6)
-        return {"ms": ms, "equiv_Gupdates_s": wl.updates / ms / 1e6, "kernel_width": 6,
-                "width4_ms": ms4, "width4_equiv_Gupdates_s": wl.updates / ms4 / 1e6}
+
+        def chk():
+            import oracle
+            ref = oracle.bp_trig_points(qh, wl.N, wl.theta, wl.det_spacing, pix2048)
+            return ({"width6": rel(got6, ref), "width4": rel(got4, ref)},
+                    f"band-limited oracle (bp_trig_points) at {len(pix2048)} random pixels")
+        checks["fourier_backprojection_2048"] = chk
+        return {"ms": ms, "equiv_Gupdates_s": wl.updates / ms / 1e6, "kernel_width": 6, "kernels": kern,
+                "width4_ms": ms4, "width4_equiv_Gupdates_s": wl.updates / ms4 / 1e6, "width4_kernels": kern4}
     guard("fourier_backprojection_2048", fourier)
 
     def fbp_fourier():
         tmp = torch.empty_like(q)
         fused = _timed(lambda: plan.fbp_fourier(q, "shepp-logan", out=img), stream, flush, 10)
+        kern = prof(plan, lambda: plan.fbp_fourier(q, "shepp-logan", out=img))
+        got = pick(img, pix2048)
         two = _timed(lambda: (plan.filter(q, "shepp-logan", out=tmp), plan.backproject_fourier(tmp, out=img)),
                      stream, flush, 10)
-        return {"fused_ms": fused, "filter_then_fourier_ms": two, "equiv_Gupdates_s": wl.updates / fused / 1e6}
+
+        def chk():
+            import oracle
+            qf = oracle.filter_rows(qh, wl.det_spacing, oracle.SHEPP_LOGAN)
+            return rel(got, oracle.bp_trig_points(qf, wl.N, wl.theta, wl.det_spacing, pix2048)), \
+                "oracle Shepp-Logan filter + band-limited R* at %d random pixels" % len(pix2048)
+        checks["fbp_fourier_fused_2048"] = chk
+        return {"fused_ms": fused, "filter_then_fourier_ms": two, "equiv_Gupdates_s": wl.updates / fused / 1e6,
+                "kernels": kern}
     guard("fbp_fourier_fused_2048", fbp_fourier)
 
     def bst():
-        res = {}
-        for os in (1, 4):
-            ms = _timed(lambda: plan.backproject_bst(q, os, out=img), stream, flush, 10)
-            res[f"oversampling_{os}"] = {"ms": ms, "equiv_Gupdates_s": wl.updates / ms / 1e6}
+        res, imgs = {}, {}
+        for os_ in (1, 4):
+            ms = _timed(lambda: plan.backproject_bst(q, os_, out=img), stream, flush, 10)
+            kern = prof(plan, lambda: plan.backproject_bst(q, os_, out=img))
+            imgs[os_] = img.double().cpu().numpy()
+            res[f"oversampling_{os_}"] = {"ms": ms, "equiv_Gupdates_s": wl.updates / ms / 1e6, "kernels": kern}
+
+        def chk():
+            import oracle
+            return ({f"oversampling_{o}": rel(imgs[o], oracle.bp_bst_interp(qh, wl.N, wl.theta, wl.det_spacing,
+                                                                             P=oracle.fourier_pad(wl.n_det) * o))
+                     for o in (1, 4)}, "the oracle of the paper's BST algorithm (bp_bst_interp), whole image")
+        checks["bst_interpolation_2048"] = chk
         return res
     guard("bst_interpolation_2048", bst)
 
     def bst_windowed():
-        res = {}
-        for os in (1, 4):
-            ms = _timed(lambda: plan.backproject_bst_windowed(q, 6.0, os, out=img), stream, flush, 10)
-            res[f"oversampling_{os}"] = {"ms": ms, "equiv_Gupdates_s": wl.updates / ms / 1e6, "beta": 6.0}
+        res, imgs = {}, {}
+        for os_ in (1, 4):
+            ms = _timed(lambda: plan.backproject_bst_windowed(q, 6.0, os_, out=img), stream, flush, 10)
+            kern = prof(plan, lambda: plan.backproject_bst_windowed(q, 6.0, os_, out=img))
+            imgs[os_] = img.double().cpu().numpy()
+            res[f"oversampling_{os_}"] = {"ms": ms, "equiv_Gupdates_s": wl.updates / ms / 1e6, "beta": 6.0,
+                                          "kernels": kern}
+
+        def chk():
+            import oracle
+            return ({f"oversampling_{o}": rel(imgs[o], oracle.bp_bst_semipolar(qh, wl.N, wl.theta, wl.det_spacing,
+                                                                                6.0, P=oracle.fourier_pad(wl.n_det) * o))
+                     for o in (1, 4)}, "the oracle of the windowed semi-polar BST (bp_bst_semipolar), whole image")
+        checks["bst_windowed_2048"] = chk
         return res
     guard("bst_windowed_2048", bst_windowed)
 
     def logpolar():
         ms = _timed(lambda: plan.backproject_logpolar(q, out=img), stream, flush, 5)
-        return {"ms": ms, "equiv_Gupdates_s": wl.updates / ms / 1e6}
+        kern = prof(plan, lambda: plan.backproject_logpolar(q, out=img))
+        got = img.double().cpu().numpy()
+
+        def chk():
+            import oracle
+            return rel(got, oracle.bp_logpolar(qh, wl.N, wl.theta, wl.det_spacing)), \
+                "the oracle of Andersson's log-polar method (bp_logpolar), whole image"
+        checks["logpolar_2048"] = chk
+        return {"ms": ms, "equiv_Gupdates_s": wl.updates / ms / 1e6, "kernels": kern}
     guard("logpolar_2048", logpolar)
 
     def logpolar_partial():
         plan.backproject_logpolar_partial(q, 8, 0.25, out=img)  # workspace and pixel tables (untimed)
         ms = _timed(lambda: plan.backproject_logpolar_partial(q, 8, 0.25, out=img), stream, flush, 5)
-        return {"ms": ms, "equiv_Gupdates_s": wl.updates / ms / 1e6, "sectors": 8, "a_r": 0.25}
+        kern = prof(plan, lambda: plan.backproject_logpolar_partial(q, 8, 0.25, out=img))
+        got = img.double().cpu().numpy()
+
+        def chk():
+            import oracle
+            return rel(got, oracle.bp_logpolar_partial(qh, wl.N, wl.theta, wl.det_spacing, Q=8, a_r=0.25)), \
+                "the oracle of the partial (sector) log-polar method, whole image"
+        checks["logpolar_partial_2048"] = chk
+        return {"ms": ms, "equiv_Gupdates_s": wl.updates / ms / 1e6, "sectors": 8, "a_r": 0.25, "kernels": kern}
     guard("logpolar_partial_2048", logpolar_partial)
+
+    # the image R and R_F act on: the direct R* of the workload (as a realistic input)
+    plan.backproject(q, out=img)
+    f_img = img.clone()
+    fh = f_img.double().cpu().numpy()
+    sino = torch.empty_like(q)
 
     def radon():
         shape, _ = plan.autotune("radon", batch=1)
-        ms = _timed(lambda: plan.radon(img, out=q), stream, flush, 5)
+        ms = _timed(lambda: plan.radon(f_img, out=sino), stream, flush, 5)
+        kern = prof(plan, lambda: plan.radon(f_img, out=sino))
+        ks = np.sort(rng.choice(wl.n_theta, 6, replace=False))
+        got = sino[torch.from_numpy(ks).to(dev)].double().cpu().numpy()
+
+        def chk():
+            import oracle
+            return rel(got, oracle.radon(fh, wl.n_det, wl.theta[ks], wl.det_spacing)), \
+                f"oracle R on {len(ks)} random angles (all bins)"
+        checks["radon_direct_2048"] = chk
         return {"ms": ms, "Gupdates_s": wl.updates / ms / 1e6, "launch_shape": {"angles_per_cta": shape[0],
-                                                                               "bands": shape[1]}}
+                                                                               "bands": shape[1]}, "kernels": kern}
     guard("radon_direct_2048", radon)
 
     def radon_f():
-        ms = _timed(lambda: plan.radon(img, out=q, fourier=True), stream, flush, 10)
-        return {"ms": ms, "equiv_Gupdates_s": wl.updates / ms / 1e6}
+        ms = _timed(lambda: plan.radon(f_img, out=sino, fourier=True), stream, flush, 10)
+        kern = prof(plan, lambda: plan.radon(f_img, out=sino, fourier=True))
+        kj = np.array([k * wl.n_det + j for k in rng.choice(wl.n_theta, 4, replace=False)
+                       for j in rng.integers(wl.n_det // 4, 3 * wl.n_det // 4, 4)])
+        got = pick(sino, kj)
+
+        def chk():
+            import oracle
+            return rel(got, oracle.radon_trig_points(fh, wl.n_det, wl.theta, wl.det_spacing, kj)), \
+                f"oracle of the Fourier-path transpose at {len(kj)} sinogram entries"
+        checks["radon_fourier_2048"] = chk
+        return {"ms": ms, "equiv_Gupdates_s": wl.updates / ms / 1e6, "kernels": kern}
     guard("radon_fourier_2048", radon_f)
 
     def bf16():
         q16 = q.to(torch.bfloat16)
         shape, _ = plan.autotune("direct", torch.bfloat16, 1)
         ms = _timed(lambda: plan.backproject(q16, out=img), stream, flush, 10)
+        kern = prof(plan, lambda: plan.backproject(q16, out=img), dict(ctx, esz=2))
+        got = pick(img, pix2048)
+        q16h = q16.double().cpu().numpy()
+
+        def chk():
+            import oracle
+            return rel(got, oracle.bp_linear_points(q16h, wl.N, wl.theta, wl.det_spacing, pix2048)), \
+                f"oracle R* on the BF16-rounded sinogram at {len(pix2048)} random pixels"
+        checks["direct_bf16_storage_2048"] = chk
         return {"ms": ms, "Gupdates_s": wl.updates / ms / 1e6, "launch_shape": {"stage": shape[0],
-                                                                               "angle_groups": shape[1]}}
+                                                                               "angle_groups": shape[1]},
+                "kernels": kern}
     guard("direct_bf16_storage_2048", bf16)
 
-    # 256^2 slice, 256 bins, 180 angles (16 pixel tiles): default launch shape vs autotuned
+    # 256^2 slice, 256 bins, 180 angles: default launch shape vs autotuned
     def small():
         S = synth.SMALL
         ps = bp.Plan(S.N, S.n_det, S.theta, S.det_spacing)
@@ -335,45 +568,71 @@ def other_paths(plan, q, img, flush, stream, dev, only=()):
         qs = ps.filter(gs, "ramlak")
         ims = torch.empty((S.N, S.N), dtype=torch.float32, device=dev)
         res = {}
-        for label, shp in (("one_cta_per_tile", (16, 1)), ("default", None)):
-            if shp:
-                ps.set_shape(shp, "direct", torch.float32, 1)
-            else:
-                ps = bp.Plan(S.N, S.n_det, S.theta, S.det_spacing)
-            used = ps.get_shape("direct", torch.float32, 1)
-            ms = _timed(lambda: ps.backproject(qs, out=ims), stream, flush, 20)
-            res[label] = {"ms": ms, "Gupdates_s": S.updates / ms / 1e6, "launch_shape": list(used)}
+        used = ps.get_shape("direct", torch.float32, 1)
+        ms = _timed(lambda: ps.backproject(qs, out=ims), stream, flush, 20)
+        res["default"] = {"ms": ms, "Gupdates_s": S.updates / ms / 1e6, "launch_shape": list(used)}
         shape, _ = ps.autotune("direct", torch.float32, 1)
         ms = _timed(lambda: ps.backproject(qs, out=ims), stream, flush, 20)
-        res["autotuned"] = {"ms": ms, "Gupdates_s": S.updates / ms / 1e6, "launch_shape": list(shape)}
+        sctx = {"N": S.N, "n_det": S.n_det, "n_theta": S.n_theta, "theta": S.theta, "dt": S.det_spacing}
+        res["autotuned"] = {"ms": ms, "Gupdates_s": S.updates / ms / 1e6, "launch_shape": list(shape),
+                            "kernels": prof(ps, lambda: ps.backproject(qs, out=ims), sctx)}
+        got = ims.double().cpu().numpy()
+        qsh = qs.double().cpu().numpy()
         ps.close()
+
+        def chk():
+            import oracle
+            return rel(got, oracle.bp_linear(qsh, S.N, S.theta, S.det_spacing)), "oracle R*, whole image"
+        checks["slice256_bins256_ang180_shapes"] = chk
         return res
     guard("slice256_bins256_ang180_shapes", small)
 
-    # volume: 256 slices of 2048^2 from BF16 sinograms, one batched launch replayed from a CUDA graph
+    # volume: 256 slices of 2048^2 from BF16 sinograms; filter and R* captured in one CUDA graph,
+    # the R* launch shape tuned at batch 256
     def volume():
         V = synth.VOLUME
         n = synth.VOLUME_SLICES
-        vol = torch.empty((n, V.n_theta, V.n_det), dtype=torch.bfloat16, device=dev)
-        chunk = 32
-        tmp = torch.empty((chunk, V.n_theta, V.n_det), dtype=torch.float32, device=dev)
-        for c0 in range(0, n, chunk):
-            for i in range(chunk):
-                e = synth.random_ellipses(V.n_ellipses, V.seed + c0 + i)
-                tmp[i] = synth.ellipse_sinogram_torch(e, V.theta, V.n_det, V.det_spacing, dev).float()
-            plan.filter(tmp, "shepp-logan", out=tmp)
-            vol[c0:c0 + chunk] = tmp.to(torch.bfloat16)
-        del tmp
+        raw = torch.empty((n, V.n_theta, V.n_det), dtype=torch.bfloat16, device=dev)
+        for i in range(n):
+            e = synth.random_ellipses(V.n_ellipses, V.seed + i)
+            raw[i] = synth.ellipse_sinogram_torch(e, V.theta, V.n_det, V.det_spacing, dev).to(torch.bfloat16)
+        pv = bp.Plan(V.N, V.n_det, V.theta, V.det_spacing)
+        filt = torch.empty((n, V.n_theta, V.n_det), dtype=torch.float32, device=dev)
         imgs = torch.empty((n, V.N, V.N), dtype=torch.float32, device=dev)
-        plan.backproject(vol, out=imgs)
+        shape, _ = pv.autotune("direct", torch.float32, n)
+
+        def step():
+            pv.filter(raw, "shepp-logan", out=filt)
+            pv.backproject(filt, out=imgs)
+        step()
+        kern = kernel_rooflines(kernel_profile(pv, step, flush, 1), dict(ctx, memset_bytes=4 * n * V.N * V.N,
+                                                                           batch=n), hbm, fp32)
         s2 = torch.cuda.Stream(dev)
         s2.wait_stream(torch.cuda.current_stream(dev))
         graph = torch.cuda.CUDAGraph()
         with torch.cuda.graph(graph, stream=s2):
-            plan.backproject(vol, out=imgs)
+            step()
         ms = _timed(graph.replay, stream, flush, 3)
+        sl = [0, n - 1]
+        got = {i: pick(imgs[i], pix2048) for i in sl}
+        fh = {i: filt[i].double().cpu().numpy() for i in sl}
+        rawh = {i: raw[i].double().cpu().numpy() for i in sl}
+        launches = sum(v["launches_per_call"] for v in kern.values())
+        pv.close()
+        del raw, filt, imgs
+
+        def chk():
+            import oracle
+            e_bp = max(rel(got[i], oracle.bp_linear_points(fh[i], V.N, V.theta, V.det_spacing, pix2048)) for i in sl)
+            e_f = max(rel(fh[i], oracle.filter_rows(rawh[i], V.det_spacing, oracle.SHEPP_LOGAN)) for i in sl)
+            return {"direct": e_bp, "filter": e_f}, (f"slices {sl}: oracle R* at {len(pix2048)} random pixels on the "
+                                                     "filtered sinogram the device made; oracle filter on the BF16 "
+                                                     "input, all rows")
+        checks["volume256_bf16_graph"] = chk
         return {"slices": n, "ms": ms, "Gupdates_s": n * V.updates / ms / 1e6, "storage": "bf16",
-                "launch": "one batched launch replayed from a CUDA graph"}
+                "step": "bp_filter (all slices, one launch) + bp_backproject_direct (one call) in one CUDA graph",
+                "launch_shape": {"stage": shape[0], "angle_groups": shape[1], "tuned_at_batch": n},
+                "launches_per_replay": launches, "kernels": kern}
     guard("volume256_bf16_graph", volume)
 
     # differentiable reconstruction: 8 x 1024^2, 1024 bins, 720 angles, 50 GD iterations on ||Rf-g||^2 + 1e-3 TV
@@ -396,7 +655,8 @@ def other_paths(plan, q, img, flush, stream, dev, only=()):
         p2.close()
         return {"batch": B, "iterations": 50, "ms": ms, "ms_per_iteration": ms / 50,
                 "loss_first_last": [st.losses[0], st.losses[-1]],
-                "Gupdates_s": 2 * 50 * B * N * N * nt / ms / 1e6}
+                "Gupdates_s": 2 * 50 * B * N * N * nt / ms / 1e6,
+                "err_vs_fp64": {"not_measured": "iterative; its operators are checked against the oracle by the tests"}}
     guard("tv_reconstruction_8x1024", tv)
 
     # uneven batch: 64 slices, widths in {512..4096}, 360-3000 angles, FP16, one persistent launch
@@ -414,27 +674,55 @@ def other_paths(plan, q, img, flush, stream, dev, only=()):
             imgs2.append(torch.empty((N, N), dtype=torch.float32, device=dev))
             upd += N * N * nt
         ms = _timed(lambda: bp.backproject_batched(plans, sinos, imgs2), stream, flush, 3)
+        sel = [0, int(np.argmax([g[0] for g in geo]))]
+        chk_data = []
+        for i in sel:
+            N, nd, nt = geo[i]
+            px = rng.choice(N * N, 100, replace=False)
+            chk_data.append((N, nd, synth.uniform_theta(nt), sinos[i].double().cpu().numpy(), px, pick(imgs2[i], px)))
         for pi in plans:
             pi.close()
+
+        def chk():
+            import oracle
+            return max(rel(got, oracle.bp_linear_points(sh, N, th, 2.0 / nd, px)) for N, nd, th, sh, px, got in chk_data), \
+                f"slices {sel}: oracle R* on the FP16-rounded sinograms at 100 random pixels each"
+        checks["mixed64_fp16_persistent"] = chk
         return {"slices": len(geo), "updates": upd, "ms": ms, "Gupdates_s": upd / ms / 1e6, "storage": "fp16",
                 "launch": "one persistent launch (dynamic tile queue)"}
     guard("mixed64_fp16_persistent", mixed)
 
     # single 8192^2 slice, 8192 bins, 6000 angles: direct and Fourier
     def big():
-        N, nd, nt = 8192, 8192, 6000
-        th = synth.uniform_theta(nt)
-        pb = bp.Plan(N, nd, th)
-        g = synth.ellipse_sinogram_torch(synth.random_ellipses(30, 5999), th, nd, 2.0 / nd, dev).float()
+        H = synth.HIRES
+        pb = bp.Plan(H.N, H.n_det, H.theta, H.det_spacing)
+        g = synth.ellipse_sinogram_torch(synth.random_ellipses(H.n_ellipses, H.seed), H.theta, H.n_det, H.det_spacing,
+                                         dev).float()
         qb = pb.filter(g, "shepp-logan")
         del g
-        ib = torch.empty((N, N), dtype=torch.float32, device=dev)
+        ib = torch.empty((H.N, H.N), dtype=torch.float32, device=dev)
         pb.autotune("direct", torch.float32, 1)
+        hctx = {"N": H.N, "n_det": H.n_det, "n_theta": H.n_theta, "esz": 4, "P": 16384, "M": 16384, "W": 6,
+                "theta": H.theta, "dt": H.det_spacing}
         msd = _timed(lambda: pb.backproject(qb, out=ib), stream, flush, 2)
+        kd = kernel_rooflines(kernel_profile(pb, lambda: pb.backproject(qb, out=ib), flush, 1), hctx, hbm, fp32)
+        pxd = rng.choice(H.N * H.N, 150, replace=False)
+        gotd = pick(ib, pxd)
         msf = _timed(lambda: pb.backproject_fourier(qb, out=ib), stream, flush, 2)
+        kf = kernel_rooflines(kernel_profile(pb, lambda: pb.backproject_fourier(qb, out=ib), flush, 1), hctx, hbm, fp32)
+        pxf = rng.choice(H.N * H.N, 24, replace=False)
+        gotf = pick(ib, pxf)
+        qbh = qb.double().cpu().numpy()
         pb.close()
-        return {"direct_ms": msd, "direct_Gupdates_s": N * N * nt / msd / 1e6, "fourier_ms": msf,
-                "fourier_equiv_Gupdates_s": N * N * nt / msf / 1e6}
+
+        def chk():
+            import oracle
+            return ({"direct": rel(gotd, oracle.bp_linear_points(qbh, H.N, H.theta, H.det_spacing, pxd)),
+                     "fourier": rel(gotf, oracle.bp_trig_points(qbh, H.N, H.theta, H.det_spacing, pxf))},
+                    f"oracle R* at {len(pxd)} and band-limited oracle at {len(pxf)} random pixels")
+        checks["slice8192_bins8192_ang6000"] = chk
+        return {"direct_ms": msd, "direct_Gupdates_s": H.updates / msd / 1e6, "direct_kernels": kd,
+                "fourier_ms": msf, "fourier_equiv_Gupdates_s": H.updates / msf / 1e6, "fourier_kernels": kf}
     guard("slice8192_bins8192_ang6000", big)
     return out
 
@@ -514,6 +802,7 @@ def run_gpu(args, world, rank, local):
     if dist:
         dist.barrier()
     clocks = sampler.stop()
+    img_step = img.double().cpu().numpy()  # the last timed step's image (checked against the oracle below)
     step_ms = [a.elapsed_time(c) for a, b, c in ev]
     bp_ms = [b.elapsed_time(c) for a, b, c in ev]
     filt_ms = [a.elapsed_time(b) for a, b, c in ev]
@@ -547,27 +836,34 @@ def run_gpu(args, world, rank, local):
     e2e_t = max_over_ranks(e2e_t, dist, dev)
     n_e2e *= e2e_reps
 
+    props = torch.cuda.get_device_properties(dev)
+    peaks = _peaks()
+    sm_max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    hbm_gbs = float(peaks.get("hbm_gbs", 6778.3))
+    peak_tflops, peak_basis = fp32_peak_tflops(props.multi_processor_count, sm_max_mhz)
+    # per-kernel event times of the step (a separate pass after the timed region, from the library's
+    # stage timer on the launching stream)
+    ctx = {"N": wl.N, "n_det": wl.n_det, "n_theta": wl.n_theta, "esz": 4, "P": 4096, "M": 4096, "W": 6,
+           "theta": wl.theta, "dt": wl.det_spacing}
+    step_kernels = kernel_rooflines(kernel_profile(plan, step, flush, max(3, min(args.steps, 10))), ctx, hbm_gbs,
+                                    peak_tflops)
+    launches_per_step = int(round(sum(v["launches_per_call"] for v in step_kernels.values())))
     # other operators and workloads of the path (reported under "paths", not part of the step)
+    checks = {}
     extra = {} if args.no_paths else other_paths(plan, q, img, flush, stream, dev,
-                                                 tuple(x for x in args.only.split(",") if x))
+                                                 tuple(x for x in args.only.split(",") if x),
+                                                 (hbm_gbs, peak_tflops), checks)
     if rank != 0:
         if dist:
             dist.barrier()
             dist.destroy_process_group()
         return
 
-    props = torch.cuda.get_device_properties(dev)
-    peaks = _peaks()
-    sm_max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    peak_tflops = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12
     bp_avg_s = statistics.mean(bp_ms) / 1e3
-    achieved = wl.updates * FLOPS_PER_UPDATE / bp_avg_s / 1e12
-    traffic = _traffic_record(shape)
-    # the library takes the 2 x 2-block kernel when every pixel step |c|, |s| = |cos|, |sin| dx/dt <= 1
-    ratio = (2.0 / wl.N) / wl.det_spacing
-    steps = np.abs(np.stack([np.cos(wl.theta), np.sin(wl.theta)])) * ratio
-    kernel = "bp_direct_quad_sync_kernel" if float(np.max(steps.astype(np.float32))) <= 1.0 else "bp_direct_tma_kernel"
-    smem_cap = SMEM_UPDATES_PER_CLK[kernel] * props.multi_processor_count * sm_max_mhz * 1e6
+    # the dominant kernel of the step: its own event time and algorithmic flops
+    dom = max(step_kernels, key=lambda k: step_kernels[k]["ms"])
+    dk = step_kernels[dom]
+    traffic = _traffic_record(dom, shape)
     line = {
         "metric": "backprojection G pixel·angle updates/s at 2048²×1800; % of roofline",
         "value": throughput(wl.updates, world, args.steps, total_ms),
@@ -581,41 +877,39 @@ def run_gpu(args, world, rank, local):
                    "launch_shape": {"stage": shape[0], "angle_groups": shape[1],
                                     "picked_by": picked},
                    "parallelism": f"independent slice per GPU x{world}"},
-        "roofline": {"bound": "alu", "kernel": kernel, "achieved": achieved,
-                     "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
-                     "flops_per_update": FLOPS_PER_UPDATE,
-                     "peak_basis": f"{props.multi_processor_count} SM x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
-                                   f"{sm_max_mhz:.0f} MHz (max SM clock)",
+        "roofline": {"bound": dk.get("bound", "alu"), "kernel": dom, "achieved": dk.get("achieved"),
+                     "peak": dk.get("peak"), "unit": dk.get("unit"), "frac": dk.get("frac"),
+                     "flops_per_update": FLOPS_PER_UPDATE, "peak_basis": peak_basis, "hbm_peak_gbs": hbm_gbs,
                      "traffic": (traffic["dram_bytes_per_launch"] if traffic else None),
-                     "algorithmic_bytes": wl.n_theta * wl.n_det * 4 + wl.N * wl.N * 4,
-                     "kernel_ms": bp_avg_s * 1e3, "filter_ms": statistics.mean(filt_ms),
-                     "smem_limit": {
-                         "resource": "shared-memory wavefronts, 1/clk/SM (" + (
-                             "one 16-byte table entry per 2 x 2 pixel block" if kernel == "bp_direct_quad_sync_kernel"
-                             else "one 8-byte table pair per update") + ")",
-                         "cap_Gupdates_s": smem_cap / 1e9,
-                         "frac": wl.updates / bp_avg_s / smem_cap},
-                     "issue_limit": ({
-                         "resource": "instruction issue, 1 warp instruction/clk per SM sub-partition",
-                         "warp_inst_per_update_ncu": traffic["warp_inst_per_update"],
-                         "cap_Gupdates_s": 4 * 32 / traffic["warp_inst_per_update"] * props.multi_processor_count *
-                                           sm_max_mhz / 1e3,
-                         "frac": wl.updates / bp_avg_s / (4 * 32 / traffic["warp_inst_per_update"] *
-                                                          props.multi_processor_count * sm_max_mhz * 1e6)}
-                                     if traffic and "warp_inst_per_update" in traffic else None)},
+                     "algorithmic_bytes": dk.get("bytes"), "kernel_ms": dk["ms"],
+                     "kernel_ms_basis": "CUDA events around the kernel on its stream (library stage timer), "
+                                        "average over a pass after the timed region",
+                     "direct_call_ms": bp_avg_s * 1e3, "filter_ms": statistics.mean(filt_ms),
+                     "step_kernels": step_kernels},
         "e2e": {"value": wl.updates * world * n_e2e / e2e_t / 1e9, "unit": "Gupdates/s",
                 "h2d_bytes_per_step": g_host.nbytes, "d2h_bytes_per_step": wl.N * wl.N * 4,
                 "call": "bp_fbp_host over %d pinned host slices per call (copies of neighbouring slices "
                         "overlap the kernels)" % (n_e2e // e2e_reps)},
-        "gpu_launches": 2 * args.steps,
+        "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
         "paths": extra,
     }
     if not args.no_cpu_baseline:
         try:
-            line["cpu_baseline"] = cpu_baseline()
+            line["cpu_baseline"], line["err_vs_fp64"] = cpu_baseline(img_step)
         except Exception as exc:  # pragma: no cover
             line["cpu_baseline"] = {"unavailable": str(exc)[:120]}
+        # every other path against the FP64 oracle, outside every timed region
+        for name, chk in checks.items():
+            try:
+                t0 = time.perf_counter()
+                err, what = chk()
+                extra[name]["err_vs_fp64"] = {"rel_l2": err, "against": what,
+                                              "oracle_s": round(time.perf_counter() - t0, 1)}
+            except Exception as exc:  # pragma: no cover
+                extra[name]["err_vs_fp64"] = {"unavailable": f"{type(exc).__name__}: {str(exc)[:120]}"}
+    else:
+        line["err_vs_fp64"] = {"not_measured": "--no-cpu-baseline (the oracle runs only in that leg)"}
     print(json.dumps(line), flush=True)
     plan.close()
     if dist:
