@@ -129,6 +129,7 @@ struct KleinWork {
     std::vector<unsigned char> host;     // per-angle records (KleinAngle)
     void *d_ang = nullptr;
     float4 *tab = nullptr;
+    unsigned *gbar = nullptr;            // grid-barrier counters of the batched launch
 };
 struct RadonShape {
     int kang = 0;   // 0 = the default rule

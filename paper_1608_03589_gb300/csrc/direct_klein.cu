@@ -237,16 +237,82 @@ struct StageSeq {
     }
 };
 
+// Grid-wide barrier of a cooperative launch (every CTA resident): bar[0] counts arrivals, bar[1]
+// is the generation.  The wait is bounded (about a second); on expiry it sets *err and returns
+// false, and the caller leaves without issuing further work.
+constexpr unsigned kGridSpinLimit = 1u << 24;
+__device__ bool grid_barrier(unsigned *bar, unsigned nblocks, int *err) {
+    __shared__ int ok_s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *gen = bar + 1;
+        const unsigned g = *gen;
+        __threadfence();
+        int ok = 1;
+        if (atomicAdd(bar, 1u) == nblocks - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            for (unsigned it = 0; *gen == g; ++it) {
+                if (it >= kGridSpinLimit) {
+                    ok = 0;
+                    atomicExch(err, 1);
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        ok_s = ok;
+    }
+    __syncthreads();
+    return ok_s != 0;
+}
+
+// The row tables of klein_tables_kernel for rows cta, cta + nctas, ... built inside the
+// persistent kernel; sg: shared staging of n_det + 8 floats.
+template <typename Tin>
+__device__ void klein_build_rows(const Tin *__restrict__ sino, float4 *__restrict__ tab,
+                                 const AngleParam *__restrict__ ap, int n_det, int n_theta, int jlo, int L, int RS,
+                                 float wuni, float *sg, int cta, int nctas) {
+    for (int k = cta; k < n_theta; k += nctas) {
+        __syncthreads();  // the previous row's entries are written
+        const Tin *row = sino + (long long)k * n_det;
+        for (int i = threadIdx.x; i < n_det + 8; i += blockDim.x) {
+            const int j = i - 4;
+            sg[i] = (j >= 0 && j < n_det) ? load_f(row + j) : 0.f;
+        }
+        __syncthreads();
+        const float w = wuni > 0.f ? wuni : ap[k].w;
+        auto g = [&](int j) { return (j >= -4 && j < n_det + 4) ? sg[j + 4] : 0.f; };
+        float4 *p0 = tab + 2 * (long long)k * RS, *p1 = p0 + RS;
+        for (int m = threadIdx.x; m < L; m += blockDim.x) {
+            const int j = jlo + m, jr = n_det - 1 - j;
+            const float a0 = g(j), a1 = g(j + 1), a2 = g(j + 2), a3 = g(j + 3);
+            const float b0 = g(jr), b1 = g(jr - 1), b2 = g(jr - 2), b3 = g(jr - 3);
+            p0[m] = make_float4(w * a0, w * b0, w * (a1 - a0), w * (b1 - b0));
+            p1[m] = make_float4(w * (a2 - a1), w * (b2 - b1), w * (a3 - a2), w * (b3 - b2));
+        }
+    }
+    // the tables are read next by bulk copies (the async proxy), the staging buffer is written by
+    // them next: order the generic writes before both
+    asm volatile("fence.proxy.async;" ::: "memory");
+    __threadfence();
+}
+
 // A persistent grid (the schedule in the header).  The warps take turns as producer: after
 // finishing stage s, warp s mod 8 copies the windows of stage s - 1 + NBUF (cp.async.bulk, 768
 // bytes per image) from the row tables of klein_tables_kernel into the buffer of stage s - 1,
 // once every warp has left it.  img is
 // added to atomically (cleared before unless accumulating).  Every wait is bounded: on expiry
 // the kernel sets *err, waits (bounded) for the copies it issued and returns.
-template <int MINB, int NBUF>
+template <typename Tin, int MINB, int NBUF, bool BUILD>
 __global__ void __launch_bounds__(kKThreads, MINB)
-bp_direct_klein_kernel(float *__restrict__ img, const KleinAngle *__restrict__ ka, const float4 *__restrict__ tab,
-                       int N, int n_theta, int RS, int jlo, int nr, int S, int *__restrict__ err) {
+bp_direct_klein_kernel(float *__restrict__ img, const KleinAngle *__restrict__ ka, float4 *__restrict__ tab,
+                       const Tin *__restrict__ sino, const AngleParam *__restrict__ ap, float wuni, int N, int n_det,
+                       int n_theta, int RS, int L, int jlo, int nr, int S, int batch, long long img_stride,
+                       long long sino_stride, unsigned *__restrict__ gbar, int *__restrict__ err) {
     // [NBUF][row k, row k'][plane 0, 1][kKStage][kKW] entries of 16 bytes
     extern __shared__ __align__(128) ulonglong2 ktab[];
     __shared__ float4 prmA[NBUF][kKStage], prmO[NBUF][kKStage];
@@ -334,18 +400,31 @@ bp_direct_klein_kernel(float *__restrict__ img, const KleinAngle *__restrict__ k
 
     bool ok = true;
     int issued = 0;
-#pragma unroll
-    for (int i = 0; i < NBUF; ++i) issued += produce(warp == 0) ? 1 : 0;
-
     KleinAcc acc;
     auto clear = [&]() {
 #pragma unroll
         for (int i = 0; i < 4; ++i) acc.a[i] = acc.b[i] = 0ull;
         acc.ga = acc.gb = 0ull;
     };
-    clear();
     int role = 0, dir = 0, cstage = 0, b = 0;
     uint32_t ph = 0;
+    for (int sl = 0; sl < batch; ++sl) {
+    float *const im = img + sl * img_stride;
+    if (BUILD) {
+        // slice sl's row tables, by all CTAs; then every CTA waits until all are written
+        klein_build_rows(sino + sl * sino_stride, tab, ap, n_det, n_theta, jlo, L, RS, wuni,
+                         reinterpret_cast<float *>(ktab), cta, nctas);
+        if (!grid_barrier(gbar, (unsigned)nctas, err)) {
+            ok = false;
+            break;
+        }
+    }
+    cons.enter(0, S, n_theta, R, cta, nctas);
+    prod = cons;
+#pragma unroll
+    for (int i = 0; i < NBUF; ++i) issued += produce(warp == 0) ? 1 : 0;
+    clear();
+    int sst = 0;  // stage index within the slice
     int rg, k0, kn;
     bool last;
     while (cons.next(rg, k0, kn, last, S, n_theta, R, cta, nctas)) {
@@ -381,7 +460,7 @@ bp_direct_klein_kernel(float *__restrict__ img, const KleinAngle *__restrict__ k
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(eb + 8 * b);
-        if (cstage >= 1) {
+        if (sst++ >= 1) {
             // refill the buffer of stage cstage - 1 with stage cstage - 1 + NBUF; the warps take
             // turns, and the issuing warp has finished the stage after it, so every warp has
             // almost surely left the buffer
@@ -430,20 +509,27 @@ bp_direct_klein_kernel(float *__restrict__ img, const KleinAngle *__restrict__ k
                         i0[px] += ga0; i3[px] += ga3; i1[px] += gb1; i2[px] += gb2;
                     }
                     const int y = iy + py, ym = N - 1 - (iy + py);
-                    put_pair(img + (long long)y * N + ix, i0[0], i0[1], x1, 1);
-                    put_pair(img + (long long)ym * N + ix, i2[0], i2[1], x1, 1);
+                    put_pair(im + (long long)y * N + ix, i0[0], i0[1], x1, 1);
+                    put_pair(im + (long long)ym * N + ix, i2[0], i2[1], x1, 1);
                     // x-mirrored: base pixels ix, ix + 1 land at N - 1 - ix, N - 2 - ix
                     if (x1) {
-                        put_pair(img + (long long)y * N + (N - 2 - ix), i1[1], i1[0], true, 1);
-                        put_pair(img + (long long)ym * N + (N - 2 - ix), i3[1], i3[0], true, 1);
+                        put_pair(im + (long long)y * N + (N - 2 - ix), i1[1], i1[0], true, 1);
+                        put_pair(im + (long long)ym * N + (N - 2 - ix), i3[1], i3[0], true, 1);
                     } else {
-                        put_pair(img + (long long)y * N + (N - 1 - ix), i1[0], 0.f, false, 1);
-                        put_pair(img + (long long)ym * N + (N - 1 - ix), i3[0], 0.f, false, 1);
+                        put_pair(im + (long long)y * N + (N - 1 - ix), i1[0], 0.f, false, 1);
+                        put_pair(im + (long long)ym * N + (N - 1 - ix), i3[0], 0.f, false, 1);
                     }
                 }
             }
             clear();
         }
+    }
+    if (!ok) break;
+    // every CTA has left slice sl (its copies all consumed) before the next slice's tables are built
+    if (BUILD && sl + 1 < batch && !grid_barrier(gbar, (unsigned)nctas, err)) {
+        ok = false;
+        break;
+    }
     }
     if (!ok) {
         // wait (bounded) for the copies still in flight: stages cstage .. issued - 1
@@ -554,8 +640,10 @@ void klein_plan(bp_plan *p) {
 void free_klein(bp_plan *p) {
     cudaFree(p->klein.d_ang);
     cudaFree(p->klein.tab);
+    cudaFree(p->klein.gbar);
     p->klein.d_ang = nullptr;
     p->klein.tab = nullptr;
+    p->klein.gbar = nullptr;
 }
 
 // Default angle groups: enough that the table rows of one group (1 / S of the workspace) stay
@@ -582,47 +670,83 @@ bp_status klein_tables(bp_plan *p, const Tin *sino, cudaStream_t st, float wuni)
     return BP_OK;
 }
 
-template <int MINB, int NBUF>
-bp_status launch_klein_t(bp_plan *p, const void *sino, bp_dtype dt, float *img, int batch, int accumulate,
-                         cudaStream_t st, float wuni, int S) {
+template <typename Tin, int MINB, int NBUF>
+bp_status launch_klein_t(bp_plan *p, const Tin *sino, float *img, int batch, int accumulate, cudaStream_t st,
+                         float wuni, int S) {
     KleinWork &kw = p->klein;
     if (!kw.d_ang) {
         BP_CUDA_TRY(cudaMalloc(&kw.d_ang, kw.host.size()));
         BP_CUDA_TRY(cudaMemcpy(kw.d_ang, kw.host.data(), kw.host.size(), cudaMemcpyHostToDevice));
+        BP_CUDA_TRY(cudaMalloc(&kw.gbar, 2 * sizeof(unsigned)));
     }
     const int RS = kw.L + kKW;
-    if (!kw.tab) BP_CUDA_TRY(cudaMalloc(&kw.tab, 2 * sizeof(float4) * (size_t)p->n_theta * RS));  // 32 B entries
+    if (!kw.tab) BP_CUDA_TRY(cudaMalloc(&kw.tab, 2 * sizeof(float4) * (size_t)p->n_theta * RS));  // two planes
     S = klein_clamp_groups(p, S);
     constexpr size_t smem = NBUF * (size_t)kKBufBytes;
-    auto kern = bp_direct_klein_kernel<MINB, NBUF>;
-    static int per_sm_cache = 0;
-    if (!per_sm_cache) {
-        BP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        BP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_cache, kern, kKThreads, smem));
-    }
-    const int grid = std::max(1, per_sm_cache) * std::max(1, p->sm_count);
+    if ((size_t)(p->n_det + 8) * sizeof(float) > smem)
+        return fail(BP_ERR_UNSUPPORTED, "direct R*: detector row too long for the four-image form");
     const size_t img_n = (size_t)p->N * p->N, sino_n = (size_t)p->n_theta * p->n_det;
-    const size_t esz = dt == BP_F32 ? 4 : 2;
     stage_begin(p, st);
     if (!accumulate) {
         BP_CUDA_TRY(cudaMemsetAsync(img, 0, sizeof(float) * img_n * batch, st));
         stage_mark(p, st, "memset (direct R* image)");
     }
-    for (int b = 0; b < batch; ++b) {
-        const void *sb = (const char *)sino + esz * sino_n * b;
-        bp_status s = BP_OK;
-        switch (dt) {
-            case BP_F32: s = klein_tables(p, (const float *)sb, st, wuni); break;
-            case BP_BF16: s = klein_tables(p, (const __nv_bfloat16 *)sb, st, wuni); break;
-            case BP_F16: s = klein_tables(p, (const __half *)sb, st, wuni); break;
+    const KleinAngle *ka = (const KleinAngle *)kw.d_ang;
+    if (batch == 1) {
+        // one slice: the tables by their own launch, then the main kernel
+        auto kern = bp_direct_klein_kernel<float, MINB, NBUF, false>;
+        static int per_sm = 0;
+        if (!per_sm) {
+            BP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            BP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kKThreads, smem));
         }
+        bp_status s = klein_tables(p, sino, st, wuni);
         if (s != BP_OK) return s;
-        kern<<<grid, kKThreads, smem, st>>>(img + img_n * b, (const KleinAngle *)kw.d_ang, kw.tab, p->N,
-                                            p->n_theta, RS, kw.jlo, kw.nr, S, p->d_err);
+        const int grid = std::max(1, per_sm) * std::max(1, p->sm_count);
+        kern<<<grid, kKThreads, smem, st>>>(img, ka, kw.tab, nullptr, p->d_ang, wuni, p->N, p->n_det, p->n_theta, RS,
+                                            kw.L, kw.jlo, kw.nr, S, 1, 0, 0, kw.gbar, p->d_err);
         BP_CUDA_TRY(cudaGetLastError());
         stage_mark(p, st, "bp_direct_klein_kernel");
+        return BP_OK;
     }
+    // a batch: one cooperative persistent launch; each slice's tables are built inside it, between
+    // grid-wide barriers
+    auto kern = bp_direct_klein_kernel<Tin, MINB, NBUF, true>;
+    static int per_sm = 0;
+    if (!per_sm) {
+        BP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        BP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kKThreads, smem));
+    }
+    const int grid = std::max(1, per_sm) * std::max(1, p->sm_count);
+    BP_CUDA_TRY(cudaMemsetAsync(kw.gbar, 0, 2 * sizeof(unsigned), st));
+    float *a_img = img;
+    const KleinAngle *a_ka = ka;
+    float4 *a_tab = kw.tab;
+    const Tin *a_sino = sino;
+    const AngleParam *a_ap = p->d_ang;
+    float a_wuni = wuni;
+    int a_N = p->N, a_nd = p->n_det, a_nt = p->n_theta, a_RS = RS, a_L = kw.L, a_jlo = kw.jlo, a_nr = kw.nr,
+        a_S = S, a_batch = batch;
+    long long a_is = (long long)img_n, a_ss = (long long)sino_n;
+    unsigned *a_gbar = kw.gbar;
+    int *a_err = p->d_err;
+    void *args[] = {&a_img, &a_ka, &a_tab, &a_sino, &a_ap, &a_wuni, &a_N, &a_nd, &a_nt, &a_RS, &a_L, &a_jlo,
+                    &a_nr, &a_S, &a_batch, &a_is, &a_ss, &a_gbar, &a_err};
+    BP_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)kern, dim3(grid), dim3(kKThreads), args, smem, st));
+    stage_mark(p, st, "bp_direct_klein_batch_kernel");
     return BP_OK;
+}
+
+template <int MINB>
+bp_status launch_klein_dt(bp_plan *p, const void *sino, bp_dtype dt, float *img, int batch, int accumulate,
+                          cudaStream_t st, float wuni, int S) {
+    switch (dt) {
+        case BP_BF16:
+            return launch_klein_t<__nv_bfloat16, MINB, 3>(p, (const __nv_bfloat16 *)sino, img, batch, accumulate, st,
+                                                         wuni, S);
+        case BP_F16: return launch_klein_t<__half, MINB, 3>(p, (const __half *)sino, img, batch, accumulate, st, wuni, S);
+        default: return launch_klein_t<float, MINB, 3>(p, (const float *)sino, img, batch, accumulate, st, wuni, S);
+    }
 }
 
 }  // namespace
@@ -632,8 +756,8 @@ bp_status launch_klein_t(bp_plan *p, const void *sino, bp_dtype dt, float *img, 
 // windows are in flight either way.
 bp_status launch_direct_klein(bp_plan *p, const void *sino, bp_dtype dt, float *img, int batch, int accumulate,
                               cudaStream_t st, float wuni, int stage, int S) {
-    if (stage == 8) return launch_klein_t<2, 3>(p, sino, dt, img, batch, accumulate, st, wuni, S);
-    return launch_klein_t<3, 3>(p, sino, dt, img, batch, accumulate, st, wuni, S);
+    if (stage == 8) return launch_klein_dt<2>(p, sino, dt, img, batch, accumulate, st, wuni, S);
+    return launch_klein_dt<3>(p, sino, dt, img, batch, accumulate, st, wuni, S);
 }
 
 }  // namespace bp

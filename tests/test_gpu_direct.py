@@ -403,7 +403,9 @@ def test_direct_four_image_form(N, n_det, n_theta, dt_scale, seed, angles):
     plan = bp.Plan(N, n_det, theta, dt)
     g = to_dev(rng.normal(size=(2, len(theta), n_det)))
     img, names = _kernels(plan, lambda: plan.backproject(g))
-    assert "bp_direct_klein_kernel" in names and "klein_tables_kernel" in names, names
+    assert "bp_direct_klein_batch_kernel" in names, names  # a batch: one cooperative launch
+    _, names1 = _kernels(plan, lambda: plan.backproject(g[0]))
+    assert "bp_direct_klein_kernel" in names1 and "klein_tables_kernel" in names1, names1
     for i in range(2):
         ref = oracle.bp_linear(rounded(g[i]), N, theta, dt)
         assert oracle.rel_l2(img[i].cpu().numpy(), ref) <= TOL_DIRECT
@@ -411,9 +413,11 @@ def test_direct_four_image_form(N, n_det, n_theta, dt_scale, seed, angles):
     acc = base.clone()
     plan.backproject(g, out=acc, accumulate=True)
     assert oracle.rel_l2(acc.cpu().numpy(), img.cpu().numpy() + rounded(base)) <= TOL_DIRECT
-    g16 = g[0].to(torch.bfloat16)
-    ref16 = oracle.bp_linear(rounded(g16), N, theta, dt)
-    assert oracle.rel_l2(plan.backproject(g16).cpu().numpy(), ref16) <= TOL_DIRECT
+    g16 = g.to(torch.bfloat16)  # a batch of 16-bit slices: one persistent launch builds each slice's tables
+    img16 = plan.backproject(g16)
+    for i in range(2):
+        ref16 = oracle.bp_linear(rounded(g16[i]), N, theta, dt)
+        assert oracle.rel_l2(img16[i].cpu().numpy(), ref16) <= TOL_DIRECT
     for S in (1, 3, 64):  # angle groups of the persistent schedule
         plan.set_shape((16, S), "direct", torch.float32, 2)
         assert oracle.rel_l2(plan.backproject(g).cpu().numpy(), img.cpu().numpy()) <= TOL_DIRECT
