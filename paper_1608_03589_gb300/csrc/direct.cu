@@ -286,7 +286,7 @@ DirectShape direct_effective(const bp_plan *p, int esz, bool tma, DirectShape sh
     e.stage = kStage;
     e.workspace = shape.workspace;
     if (shape.workspace && p->klein.eligible) {
-        e.stage = shape.stage == 8 ? 8 : kStage;  // the four-image form: 2 or 3 CTAs per SM
+        e.stage = (shape.stage == 8 || shape.stage == 32) ? shape.stage : kStage;  // four-image variants
         e.asplit = klein_clamp_groups(p, shape.asplit);
         return e;
     }

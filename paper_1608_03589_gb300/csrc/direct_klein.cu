@@ -157,28 +157,37 @@ __device__ __forceinline__ void klein_row(const ulonglong2 x0, const ulonglong2 
     else q[3] = ffma2(x1.y, S3b, ffma2(x1.x, S3a, ffma2(x0.y, S3c, q[3])));
 }
 
-// One angle: CHECK = per-angle role and direction test, FAR = 0 per-angle far-corner test,
-// 1 two ramps (|c| + |s| >= 1), 2 three ramps.  A = (q0, c, s, role | dir << 2), O = (|c| - 1,
-// |s| - 1, |c| + |s| - 1, |c| + |s| - 2); tabs[wi]: the first entry of the angle's window in
-// row k's plane 0; row k's plane 1 and row k''s planes 0 and 1 follow kKStage windows apart.
-template <bool CHECK, int FAR>
-__device__ __forceinline__ void klein_angle(const float4 A, const float4 O, const ulonglong2 *__restrict__ tabs, int wi,
-                                            KleinAcc &acc, int &role, int &dir, float fx, float fy) {
-    if (CHECK) {
-        const int w = __float_as_int(A.w);
-        const int rl = w & 3, dr = w >> 2;
-        if (rl != role) {
-            xor_permute2(acc.a, rl ^ role);
-            xor_permute2(acc.b, rl ^ role);
-            role = rl;
-        }
-        if (dr != dir) {
+// Exchange the accumulators of `n` blocks when the corner roles or the row-k' direction of the
+// next angle (w = role | dir << 2) differ from the current ones.
+template <int BPT>
+__device__ __forceinline__ void klein_roles(int w, KleinAcc (&acc)[BPT], int &role, int &dir) {
+    const int rl = w & 3, dr = (w >> 2) & 1;
+    if (rl != role) {
 #pragma unroll
-            for (int i = 0; i < 4; ++i) acc.b[i] = swap2(acc.b[i]);
-            acc.gb = swap2(acc.gb);
-            dir = dr;
+        for (int h = 0; h < BPT; ++h) {
+            xor_permute2(acc[h].a, rl ^ role);
+            xor_permute2(acc[h].b, rl ^ role);
         }
+        role = rl;
     }
+    if (dr != dir) {
+#pragma unroll
+        for (int h = 0; h < BPT; ++h) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) acc[h].b[i] = swap2(acc[h].b[i]);
+            acc[h].gb = swap2(acc[h].gb);
+        }
+        dir = dr;
+    }
+}
+
+// One angle for one block and its three images: FAR = 0 per-angle far-corner test, 1 two ramps
+// (|c| + |s| >= 1), 2 three ramps.  A = (q0, c, s, role | dir << 2), O = (|c| - 1, |s| - 1,
+// |c| + |s| - 1, |c| + |s| - 2); tabs[wi]: the first entry of the angle's window in row k's plane
+// 0; row k's plane 1 and row k''s planes 0 and 1 follow kKStage windows apart.
+template <int FAR>
+__device__ __forceinline__ void klein_angle(const float4 A, const float4 O, const ulonglong2 *__restrict__ tabs, int wi,
+                                            KleinAcc &acc, float fx, float fy) {
     const float qt = fmaf(fy, A.z, fmaf(fx, A.y, A.x));
     const float v = __fadd_rd(qt, kMagic);  // magic + floor(qt)
     const float r = qt - (v - kMagic);       // r = qt - floor(qt)
@@ -307,8 +316,8 @@ __device__ void klein_build_rows(const Tin *__restrict__ sino, float4 *__restric
 // once every warp has left it.  img is
 // added to atomically (cleared before unless accumulating).  Every wait is bounded: on expiry
 // the kernel sets *err, waits (bounded) for the copies it issued and returns.
-template <typename Tin, int MINB, int NBUF, bool BUILD>
-__global__ void __launch_bounds__(kKThreads, MINB)
+template <typename Tin, int MINB, int NBUF, bool BUILD, int BPT>
+__global__ void __launch_bounds__(kKThreads / BPT, MINB)
 bp_direct_klein_kernel(float *__restrict__ img, const KleinAngle *__restrict__ ka, float4 *__restrict__ tab,
                        const Tin *__restrict__ sino, const AngleParam *__restrict__ ap, float wuni, int N, int n_det,
                        int n_theta, int RS, int L, int jlo, int nr, int S, int batch, long long img_stride,
@@ -318,11 +327,12 @@ bp_direct_klein_kernel(float *__restrict__ img, const KleinAngle *__restrict__ k
     __shared__ float4 prmA[NBUF][kKStage], prmO[NBUF][kKStage];
     __shared__ int prmU[NBUF];  // stage uniformity: role | dir << 2 | 8 when all agree, | 16 when all far corners take two ramps
     __shared__ __align__(8) unsigned long long full[NBUF], empty[NBUF];
+    constexpr int NW = kKThreads / BPT / 32;  // warps per CTA
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, qtr = lane >> 3;
-    // warp -> 16 x 8 pixels, quarter warp -> 8 x 4 pixels (its table entries lie within 8
-    // consecutive bins); the block's origin inside its region
-    const int bx = (lane & 3) + 4 * (qtr & 1) + 8 * (warp & 1);
-    const int by = ((lane >> 2) & 1) + 2 * (qtr >> 1) + 4 * (warp >> 1);
+    // a warp's blocks h -> 16 x 8 pixels, a quarter warp's -> 8 x 4 pixels (its table entries lie
+    // within 8 consecutive bins); block h's origin inside the region is (2 bx + 16 h, 2 by)
+    const int bx = (lane & 3) + 4 * (qtr & 1) + (BPT == 1 ? 8 * (warp & 1) : 0);
+    const int by = ((lane >> 2) & 1) + 2 * (qtr >> 1) + 4 * (BPT == 1 ? warp >> 1 : warp);
     const float fx = (float)(2 * bx), fy = (float)(2 * by);
     const int h2 = N / 2;
     const int R = nr * nr, cta = blockIdx.x, nctas = gridDim.x;
@@ -335,7 +345,7 @@ bp_direct_klein_kernel(float *__restrict__ img, const KleinAngle *__restrict__ k
 #pragma unroll
         for (int i = 0; i < NBUF; ++i) {
             mbar_init(fb + 8 * i, 1);
-            mbar_init(eb + 8 * i, kKThreads / 32);
+            mbar_init(eb + 8 * i, NW);
         }
         mbar_fence_init();
     }
@@ -400,11 +410,14 @@ bp_direct_klein_kernel(float *__restrict__ img, const KleinAngle *__restrict__ k
 
     bool ok = true;
     int issued = 0;
-    KleinAcc acc;
+    KleinAcc acc[BPT];
     auto clear = [&]() {
 #pragma unroll
-        for (int i = 0; i < 4; ++i) acc.a[i] = acc.b[i] = 0ull;
-        acc.ga = acc.gb = 0ull;
+        for (int h = 0; h < BPT; ++h) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) acc[h].a[i] = acc[h].b[i] = 0ull;
+            acc[h].ga = acc[h].gb = 0ull;
+        }
     };
     int role = 0, dir = 0, cstage = 0, b = 0;
     uint32_t ph = 0;
@@ -435,28 +448,32 @@ bp_direct_klein_kernel(float *__restrict__ img, const KleinAngle *__restrict__ k
         const int uw = prmU[b];
         const int wb = b * 4 * kKStage * kKW;  // row k's plane-0 windows of this stage (entries)
         if (uw & 8) {
-            const int rl0 = uw & 3, d0 = (uw >> 2) & 1;
-            if (rl0 != role) {
-                xor_permute2(acc.a, rl0 ^ role);
-                xor_permute2(acc.b, rl0 ^ role);
-                role = rl0;
-            }
-            if (d0 != dir) {
-#pragma unroll
-                for (int i = 0; i < 4; ++i) acc.b[i] = swap2(acc.b[i]);
-                acc.gb = swap2(acc.gb);
-                dir = d0;
-            }
+            klein_roles<BPT>(uw & 7, acc, role, dir);
             if (uw & 16) {
-                for (int kk = 0; kk < kn; ++kk)
-                    klein_angle<false, 1>(prmA[b][kk], prmO[b][kk], ktab, wb + kk * kKW, acc, role, dir, fx, fy);
+#pragma unroll 2
+                for (int kk = 0; kk < kn; ++kk) {
+                    const float4 A = prmA[b][kk], O = prmO[b][kk];
+#pragma unroll
+                    for (int h = 0; h < BPT; ++h)
+                        klein_angle<1>(A, O, ktab, wb + kk * kKW, acc[h], fx + (float)(16 * h), fy);
+                }
             } else {
-                for (int kk = 0; kk < kn; ++kk)
-                    klein_angle<false, 2>(prmA[b][kk], prmO[b][kk], ktab, wb + kk * kKW, acc, role, dir, fx, fy);
+#pragma unroll 2
+                for (int kk = 0; kk < kn; ++kk) {
+                    const float4 A = prmA[b][kk], O = prmO[b][kk];
+#pragma unroll
+                    for (int h = 0; h < BPT; ++h)
+                        klein_angle<2>(A, O, ktab, wb + kk * kKW, acc[h], fx + (float)(16 * h), fy);
+                }
             }
         } else {
-            for (int kk = 0; kk < kn; ++kk)
-                klein_angle<true, 0>(prmA[b][kk], prmO[b][kk], ktab, wb + kk * kKW, acc, role, dir, fx, fy);
+            for (int kk = 0; kk < kn; ++kk) {
+                const float4 A = prmA[b][kk], O = prmO[b][kk];
+                klein_roles<BPT>(__float_as_int(A.w), acc, role, dir);
+#pragma unroll
+                for (int h = 0; h < BPT; ++h)
+                    klein_angle<0>(A, O, ktab, wb + kk * kKW, acc[h], fx + (float)(16 * h), fy);
+            }
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(eb + 8 * b);
@@ -464,7 +481,7 @@ bp_direct_klein_kernel(float *__restrict__ img, const KleinAngle *__restrict__ k
             // refill the buffer of stage cstage - 1 with stage cstage - 1 + NBUF; the warps take
             // turns, and the issuing warp has finished the stage after it, so every warp has
             // almost surely left the buffer
-            const bool mine = warp == cstage % (kKThreads / 32);
+            const bool mine = warp == cstage % NW;
             if (mine) {
                 const int bp = b == 0 ? NBUF - 1 : b - 1;
                 const uint32_t pp = b == 0 ? ph ^ 1u : ph;
@@ -481,17 +498,21 @@ bp_direct_klein_kernel(float *__restrict__ img, const KleinAngle *__restrict__ k
             ph ^= 1u;
         }
         if (last) {
-            // flush: pixel px + 2 py of the block has role (px + 2 py) ^ role; pair A holds images
-            // 0 and -P, pair B images M_x and M_y (exchanged while dir = 1)
+            // flush: pixel px + 2 py of a block has role (px + 2 py) ^ role; pair A holds images 0
+            // and -P, pair B images M_x and M_y (exchanged while dir = 1)
             const int rx = rg % nr, ry = rg / nr;
-            const int ix = kKRegion * rx + 2 * bx, iy = kKRegion * ry + 2 * by;
-            const bool x1 = ix + 1 < h2;
-            xor_permute2(acc.a, role);
-            xor_permute2(acc.b, role);
-            if (ix < h2) {
+            const int iy = kKRegion * ry + 2 * by;
+#pragma unroll
+            for (int h = 0; h < BPT; ++h) {
+                KleinAcc &ac = acc[h];
+                const int ix = kKRegion * rx + 2 * bx + 16 * h;
+                const bool x1 = ix + 1 < h2;
+                xor_permute2(ac.a, role);
+                xor_permute2(ac.b, role);
+                if (ix >= h2) continue;
                 float ga0, ga3, gb1, gb2;
-                upk2(acc.ga, ga0, ga3);
-                upk2(acc.gb, gb1, gb2);
+                upk2(ac.ga, ga0, ga3);
+                upk2(ac.gb, gb1, gb2);
                 if (dir) {
                     const float t = gb1; gb1 = gb2; gb2 = t;
                 }
@@ -501,8 +522,8 @@ bp_direct_klein_kernel(float *__restrict__ img, const KleinAngle *__restrict__ k
                     float i0[2], i3[2], i1[2], i2[2];
 #pragma unroll
                     for (int px = 0; px < 2; ++px) {
-                        upk2(acc.a[2 * py + px], i0[px], i3[px]);
-                        upk2(acc.b[2 * py + px], i1[px], i2[px]);
+                        upk2(ac.a[2 * py + px], i0[px], i3[px]);
+                        upk2(ac.b[2 * py + px], i1[px], i2[px]);
                         if (dir) {
                             const float t = i1[px]; i1[px] = i2[px]; i2[px] = t;
                         }
@@ -646,11 +667,11 @@ void free_klein(bp_plan *p) {
     p->klein.gbar = nullptr;
 }
 
-// Default angle groups: enough that the table rows of one group (1 / S of the workspace) stay
-// well inside L2.
+// Default angle groups: about one per 96 MB of row tables, so that one group's rows mostly stay
+// in L2 (measured at 2048^2 x 1800: two groups best; more add partial-sum flushes).
 int klein_default_groups(const bp_plan *p) {
     const double bytes = 2.0 * 16.0 * p->n_theta * (double)(p->klein.L + kKW);
-    const int S = (int)std::ceil(bytes / (24.0 * 1024 * 1024));
+    const int S = (int)std::ceil(bytes / (96.0 * 1024 * 1024));
     return std::max(1, std::min(std::min(S, 64), p->n_theta));
 }
 
@@ -670,9 +691,10 @@ bp_status klein_tables(bp_plan *p, const Tin *sino, cudaStream_t st, float wuni)
     return BP_OK;
 }
 
-template <typename Tin, int MINB, int NBUF>
+template <typename Tin, int MINB, int NBUF, int BPT>
 bp_status launch_klein_t(bp_plan *p, const Tin *sino, float *img, int batch, int accumulate, cudaStream_t st,
                          float wuni, int S) {
+    constexpr int NT = kKThreads / BPT;
     KleinWork &kw = p->klein;
     if (!kw.d_ang) {
         BP_CUDA_TRY(cudaMalloc(&kw.d_ang, kw.host.size()));
@@ -694,16 +716,16 @@ bp_status launch_klein_t(bp_plan *p, const Tin *sino, float *img, int batch, int
     const KleinAngle *ka = (const KleinAngle *)kw.d_ang;
     if (batch == 1) {
         // one slice: the tables by their own launch, then the main kernel
-        auto kern = bp_direct_klein_kernel<float, MINB, NBUF, false>;
+        auto kern = bp_direct_klein_kernel<float, MINB, NBUF, false, BPT>;
         static int per_sm = 0;
         if (!per_sm) {
             BP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            BP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kKThreads, smem));
+            BP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem));
         }
         bp_status s = klein_tables(p, sino, st, wuni);
         if (s != BP_OK) return s;
         const int grid = std::max(1, per_sm) * std::max(1, p->sm_count);
-        kern<<<grid, kKThreads, smem, st>>>(img, ka, kw.tab, nullptr, p->d_ang, wuni, p->N, p->n_det, p->n_theta, RS,
+        kern<<<grid, NT, smem, st>>>(img, ka, kw.tab, nullptr, p->d_ang, wuni, p->N, p->n_det, p->n_theta, RS,
                                             kw.L, kw.jlo, kw.nr, S, 1, 0, 0, kw.gbar, p->d_err);
         BP_CUDA_TRY(cudaGetLastError());
         stage_mark(p, st, "bp_direct_klein_kernel");
@@ -711,11 +733,11 @@ bp_status launch_klein_t(bp_plan *p, const Tin *sino, float *img, int batch, int
     }
     // a batch: one cooperative persistent launch; each slice's tables are built inside it, between
     // grid-wide barriers
-    auto kern = bp_direct_klein_kernel<Tin, MINB, NBUF, true>;
+    auto kern = bp_direct_klein_kernel<Tin, MINB, NBUF, true, BPT>;
     static int per_sm = 0;
     if (!per_sm) {
         BP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        BP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kKThreads, smem));
+        BP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem));
     }
     const int grid = std::max(1, per_sm) * std::max(1, p->sm_count);
     BP_CUDA_TRY(cudaMemsetAsync(kw.gbar, 0, 2 * sizeof(unsigned), st));
@@ -732,32 +754,36 @@ bp_status launch_klein_t(bp_plan *p, const Tin *sino, float *img, int batch, int
     int *a_err = p->d_err;
     void *args[] = {&a_img, &a_ka, &a_tab, &a_sino, &a_ap, &a_wuni, &a_N, &a_nd, &a_nt, &a_RS, &a_L, &a_jlo,
                     &a_nr, &a_S, &a_batch, &a_is, &a_ss, &a_gbar, &a_err};
-    BP_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)kern, dim3(grid), dim3(kKThreads), args, smem, st));
+    BP_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)kern, dim3(grid), dim3(NT), args, smem, st));
     stage_mark(p, st, "bp_direct_klein_batch_kernel");
     return BP_OK;
 }
 
-template <int MINB>
+template <int MINB, int BPT>
 bp_status launch_klein_dt(bp_plan *p, const void *sino, bp_dtype dt, float *img, int batch, int accumulate,
                           cudaStream_t st, float wuni, int S) {
     switch (dt) {
         case BP_BF16:
-            return launch_klein_t<__nv_bfloat16, MINB, 3>(p, (const __nv_bfloat16 *)sino, img, batch, accumulate, st,
-                                                         wuni, S);
-        case BP_F16: return launch_klein_t<__half, MINB, 3>(p, (const __half *)sino, img, batch, accumulate, st, wuni, S);
-        default: return launch_klein_t<float, MINB, 3>(p, (const float *)sino, img, batch, accumulate, st, wuni, S);
+            return launch_klein_t<__nv_bfloat16, MINB, 3, BPT>(p, (const __nv_bfloat16 *)sino, img, batch, accumulate,
+                                                              st, wuni, S);
+        case BP_F16:
+            return launch_klein_t<__half, MINB, 3, BPT>(p, (const __half *)sino, img, batch, accumulate, st, wuni, S);
+        default:
+            return launch_klein_t<float, MINB, 3, BPT>(p, (const float *)sino, img, batch, accumulate, st, wuni, S);
     }
 }
 
 }  // namespace
 
-// The four-image form's launch shape: shape[0] = 8 -> two CTAs per SM (up to 128 registers),
-// else three (up to 80); shape[1] = angle groups S of the persistent schedule.  Three stages of
-// windows are in flight either way.
+// The four-image form's launch shape: shape[0] = 16 -> one block per thread, three 256-thread
+// CTAs per SM (up to 80 registers); 8 -> the same at two CTAs per SM (up to 128 registers);
+// 32 -> two blocks per thread (128-thread CTAs share the per-angle work), three CTAs per SM;
+// shape[1] = angle groups S of the persistent schedule.  Three stages of windows are in flight.
 bp_status launch_direct_klein(bp_plan *p, const void *sino, bp_dtype dt, float *img, int batch, int accumulate,
                               cudaStream_t st, float wuni, int stage, int S) {
-    if (stage == 8) return launch_klein_dt<2>(p, sino, dt, img, batch, accumulate, st, wuni, S);
-    return launch_klein_dt<3>(p, sino, dt, img, batch, accumulate, st, wuni, S);
+    if (stage == 8) return launch_klein_dt<2, 1>(p, sino, dt, img, batch, accumulate, st, wuni, S);
+    if (stage == 32) return launch_klein_dt<3, 2>(p, sino, dt, img, batch, accumulate, st, wuni, S);
+    return launch_klein_dt<3, 1>(p, sino, dt, img, batch, accumulate, st, wuni, S);
 }
 
 }  // namespace bp

@@ -72,6 +72,7 @@ int tiles_of(const bp_plan *p) { return (p->N + kTile - 1) / kTile; }
 DirectShape direct_default(const bp_plan *p, int batch) {
     DirectShape s;
     if (p->klein.eligible) {
+        s.stage = 32;  // the four-image form with two blocks per thread
         s.asplit = klein_default_groups(p);
         return s;
     }

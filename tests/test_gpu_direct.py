@@ -418,9 +418,13 @@ def test_direct_four_image_form(N, n_det, n_theta, dt_scale, seed, angles):
     for i in range(2):
         ref16 = oracle.bp_linear(rounded(g16[i]), N, theta, dt)
         assert oracle.rel_l2(img16[i].cpu().numpy(), ref16) <= TOL_DIRECT
-    for S in (1, 3, 64):  # angle groups of the persistent schedule
-        plan.set_shape((16, S), "direct", torch.float32, 2)
-        assert oracle.rel_l2(plan.backproject(g).cpu().numpy(), img.cpu().numpy()) <= TOL_DIRECT
+    # variants (one block per thread at 3 or 2 CTAs per SM, two blocks per thread) and angle groups
+    for shp in ((16, 1), (16, 3), (16, 64), (8, 2), (32, 1), (32, 5)):
+        plan.set_shape(shp, "direct", torch.float32, 2)
+        assert oracle.rel_l2(plan.backproject(g).cpu().numpy(), img.cpu().numpy()) <= TOL_DIRECT, shp
+        plan.set_shape(shp, "direct", torch.float32, 1)
+        g1 = g[1].clone()  # own (16-byte aligned) allocation
+        assert oracle.rel_l2(plan.backproject(g1).cpu().numpy(), img[1].cpu().numpy()) <= TOL_DIRECT, shp
 
 
 def test_direct_four_image_form_not_taken_without_symmetry():

@@ -59,7 +59,7 @@ def test_autotune_picks_a_candidate_and_keeps_parity():
     wl = synth.SMALL
     plan = bp.Plan(wl.N, wl.n_det, wl.theta, wl.det_spacing)
     default = plan.get_shape("direct", torch.float32, 1)
-    assert default[0] == 16 and default[1] >= 1
+    assert default[0] in (16, 32) and default[1] >= 1
     shape, ms = plan.autotune("direct", torch.float32, 1)
     assert ms > 0 and shape == plan.get_shape("direct", torch.float32, 1)
     q = to_dev(oracle.filter_rows(wl.sinogram(), wl.det_spacing, oracle.RAMLAK))
