@@ -52,10 +52,10 @@ namespace {
 
 constexpr int kKRegion = 32;          // region side (pixels)
 constexpr int kKThreads = 256;        // one 2 x 2 block per thread
-constexpr int kKStage = 8;            // angles per shared-memory stage (two stages in flight)
+constexpr int kKStage = 8;            // angles per shared-memory stage (three stages in flight)
 constexpr int kKW = 48;               // table entries per region window: 31 (|c| + |s|) + 4 <= 48
 constexpr int kKWin = kKW * 16;       // bytes of one window of one plane
-constexpr int kKBufBytes = 4 * kKStage * kKWin;  // one stage: two planes of rows k and k' of kKStage angles
+constexpr int kKBufBytes = 4 * kKStage * kKWin;  // one 8-angle stage: two planes of rows k and k' per angle
 constexpr int kKMargin = 4;           // extra table entries beyond the reachable bins
 
 // Table of one row, forward and backward interleaved, in two planes of 16-byte entries: entry
@@ -185,7 +185,7 @@ __device__ __forceinline__ void klein_roles(int w, KleinAcc (&acc)[BPT], int &ro
 // (|c| + |s| >= 1), 2 three ramps.  A = (q0, c, s, role | dir << 2), O = (|c| - 1, |s| - 1,
 // |c| + |s| - 1, |c| + |s| - 2); tabs[wi]: the first entry of the angle's window in row k's plane
 // 0; row k's plane 1 and row k''s planes 0 and 1 follow kKStage windows apart.
-template <int FAR>
+template <int FAR, int STG>
 __device__ __forceinline__ void klein_angle(const float4 A, const float4 O, const ulonglong2 *__restrict__ tabs, int wi,
                                             KleinAcc &acc, float fx, float fy) {
     const float qt = fmaf(fy, A.z, fmaf(fx, A.y, A.x));
@@ -197,7 +197,7 @@ __device__ __forceinline__ void klein_angle(const float4 A, const float4 O, cons
     const float s2a = sat_add(r, fabsf(A.z)), s2b = sat_add(r, O.y);
     const float s3a = sat_add(r, O.z), s3b = sat_add(r, O.w);
     const float s3c = far2 ? 1.f : sat_add(r, O.z + 1.f);
-    constexpr int P = kKStage * kKW;
+    constexpr int P = STG * kKW;
     const ulonglong2 a0 = tabs[e], a1 = tabs[e + P];
     const ulonglong2 b0 = tabs[e + 2 * P], b1 = tabs[e + 3 * P];
     const unsigned long long R2 = pk2(r, r), S1a = pk2(s1a, s1a), S1b = pk2(s1b, s1b), S2a = pk2(s2a, s2a),
@@ -214,6 +214,7 @@ __device__ __forceinline__ void klein_angle(const float4 A, const float4 O, cons
 // the same order, so only one group's table rows are in use at a time), its share of the
 // group's (region, slot) pairs, region-major, in stages of at most kKStage slots that never
 // cross a region.
+template <int STG>
 struct StageSeq {
     int g, u, u1, Ag, k_a;
     int rg, off;  // region of position u and u - rg Ag (kept without division)
@@ -234,7 +235,7 @@ struct StageSeq {
         }
         r = rg;
         k0 = k_a + off;
-        kn = min(kKStage, min(u1 - u, Ag - off));
+        kn = min(STG, min(u1 - u, Ag - off));
         u += kn;
         off += kn;
         last = u >= u1 || off == Ag;
@@ -316,15 +317,15 @@ __device__ void klein_build_rows(const Tin *__restrict__ sino, float4 *__restric
 // once every warp has left it.  img is
 // added to atomically (cleared before unless accumulating).  Every wait is bounded: on expiry
 // the kernel sets *err, waits (bounded) for the copies it issued and returns.
-template <typename Tin, int MINB, int NBUF, bool BUILD, int BPT>
+template <typename Tin, int MINB, int NBUF, bool BUILD, int BPT, int STG>
 __global__ void __launch_bounds__(kKThreads / BPT, MINB)
 bp_direct_klein_kernel(float *__restrict__ img, const KleinAngle *__restrict__ ka, float4 *__restrict__ tab,
                        const Tin *__restrict__ sino, const AngleParam *__restrict__ ap, float wuni, int N, int n_det,
                        int n_theta, int RS, int L, int jlo, int nr, int S, int batch, long long img_stride,
                        long long sino_stride, unsigned *__restrict__ gbar, int *__restrict__ err) {
-    // [NBUF][row k, row k'][plane 0, 1][kKStage][kKW] entries of 16 bytes
+    // [NBUF][row k, row k'][plane 0, 1][STG][kKW] entries of 16 bytes
     extern __shared__ __align__(128) ulonglong2 ktab[];
-    __shared__ float4 prmA[NBUF][kKStage], prmO[NBUF][kKStage];
+    __shared__ float4 prmA[NBUF][STG], prmO[NBUF][STG];
     __shared__ int prmU[NBUF];  // stage uniformity: role | dir << 2 | 8 when all agree, | 16 when all far corners take two ramps
     __shared__ __align__(8) unsigned long long full[NBUF], empty[NBUF];
     constexpr int NW = kKThreads / BPT / 32;  // warps per CTA
@@ -336,9 +337,9 @@ bp_direct_klein_kernel(float *__restrict__ img, const KleinAngle *__restrict__ k
     const float fx = (float)(2 * bx), fy = (float)(2 * by);
     const int h2 = N / 2;
     const int R = nr * nr, cta = blockIdx.x, nctas = gridDim.x;
-    StageSeq cons;
+    StageSeq<STG> cons;
     cons.enter(0, S, n_theta, R, cta, nctas);
-    StageSeq prod = cons;
+    StageSeq<STG> prod = cons;
     const unsigned tab_u32 = smem_u32(ktab);
     const uint32_t fb = smem_u32(&full[0]), eb = smem_u32(&empty[0]);
     if (tid == 0) {
@@ -398,7 +399,7 @@ bp_direct_klein_kernel(float *__restrict__ img, const KleinAngle *__restrict__ k
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const float4 *src = (q < 2 ? src0 : src1) + (q & 1) * (long long)RS;
-                const unsigned dst = tab_u32 + (unsigned)(((b * 4 + q) * kKStage + lane) * kKWin);
+                const unsigned dst = tab_u32 + (unsigned)(((b * 4 + q) * STG + lane) * kKWin);
                 asm volatile(
                     "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
                     ::"r"(dst), "l"(src), "r"((uint32_t)kKWin), "r"(fb + 8 * b)
@@ -446,7 +447,7 @@ bp_direct_klein_kernel(float *__restrict__ img, const KleinAngle *__restrict__ k
             break;
         }
         const int uw = prmU[b];
-        const int wb = b * 4 * kKStage * kKW;  // row k's plane-0 windows of this stage (entries)
+        const int wb = b * 4 * STG * kKW;  // row k's plane-0 windows of this stage (entries)
         if (uw & 8) {
             klein_roles<BPT>(uw & 7, acc, role, dir);
             if (uw & 16) {
@@ -455,7 +456,7 @@ bp_direct_klein_kernel(float *__restrict__ img, const KleinAngle *__restrict__ k
                     const float4 A = prmA[b][kk], O = prmO[b][kk];
 #pragma unroll
                     for (int h = 0; h < BPT; ++h)
-                        klein_angle<1>(A, O, ktab, wb + kk * kKW, acc[h], fx + (float)(16 * h), fy);
+                        klein_angle<1, STG>(A, O, ktab, wb + kk * kKW, acc[h], fx + (float)(16 * h), fy);
                 }
             } else {
 #pragma unroll 2
@@ -463,7 +464,7 @@ bp_direct_klein_kernel(float *__restrict__ img, const KleinAngle *__restrict__ k
                     const float4 A = prmA[b][kk], O = prmO[b][kk];
 #pragma unroll
                     for (int h = 0; h < BPT; ++h)
-                        klein_angle<2>(A, O, ktab, wb + kk * kKW, acc[h], fx + (float)(16 * h), fy);
+                        klein_angle<2, STG>(A, O, ktab, wb + kk * kKW, acc[h], fx + (float)(16 * h), fy);
                 }
             }
         } else {
@@ -472,7 +473,7 @@ bp_direct_klein_kernel(float *__restrict__ img, const KleinAngle *__restrict__ k
                 klein_roles<BPT>(__float_as_int(A.w), acc, role, dir);
 #pragma unroll
                 for (int h = 0; h < BPT; ++h)
-                    klein_angle<0>(A, O, ktab, wb + kk * kKW, acc[h], fx + (float)(16 * h), fy);
+                    klein_angle<0, STG>(A, O, ktab, wb + kk * kKW, acc[h], fx + (float)(16 * h), fy);
             }
         }
         __syncwarp();
@@ -691,7 +692,7 @@ bp_status klein_tables(bp_plan *p, const Tin *sino, cudaStream_t st, float wuni)
     return BP_OK;
 }
 
-template <typename Tin, int MINB, int NBUF, int BPT>
+template <typename Tin, int MINB, int NBUF, int BPT, int STG>
 bp_status launch_klein_t(bp_plan *p, const Tin *sino, float *img, int batch, int accumulate, cudaStream_t st,
                          float wuni, int S) {
     constexpr int NT = kKThreads / BPT;
@@ -704,7 +705,7 @@ bp_status launch_klein_t(bp_plan *p, const Tin *sino, float *img, int batch, int
     const int RS = kw.L + kKW;
     if (!kw.tab) BP_CUDA_TRY(cudaMalloc(&kw.tab, 2 * sizeof(float4) * (size_t)p->n_theta * RS));  // two planes
     S = klein_clamp_groups(p, S);
-    constexpr size_t smem = NBUF * (size_t)kKBufBytes;
+    constexpr size_t smem = (size_t)NBUF * 4 * STG * kKWin;
     if ((size_t)(p->n_det + 8) * sizeof(float) > smem)
         return fail(BP_ERR_UNSUPPORTED, "direct R*: detector row too long for the four-image form");
     const size_t img_n = (size_t)p->N * p->N, sino_n = (size_t)p->n_theta * p->n_det;
@@ -716,7 +717,7 @@ bp_status launch_klein_t(bp_plan *p, const Tin *sino, float *img, int batch, int
     const KleinAngle *ka = (const KleinAngle *)kw.d_ang;
     if (batch == 1) {
         // one slice: the tables by their own launch, then the main kernel
-        auto kern = bp_direct_klein_kernel<float, MINB, NBUF, false, BPT>;
+        auto kern = bp_direct_klein_kernel<float, MINB, NBUF, false, BPT, STG>;
         static int per_sm = 0;
         if (!per_sm) {
             BP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -733,7 +734,7 @@ bp_status launch_klein_t(bp_plan *p, const Tin *sino, float *img, int batch, int
     }
     // a batch: one cooperative persistent launch; each slice's tables are built inside it, between
     // grid-wide barriers
-    auto kern = bp_direct_klein_kernel<Tin, MINB, NBUF, true, BPT>;
+    auto kern = bp_direct_klein_kernel<Tin, MINB, NBUF, true, BPT, STG>;
     static int per_sm = 0;
     if (!per_sm) {
         BP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -759,31 +760,32 @@ bp_status launch_klein_t(bp_plan *p, const Tin *sino, float *img, int batch, int
     return BP_OK;
 }
 
-template <int MINB, int BPT>
+template <int MINB, int BPT, int STG>
 bp_status launch_klein_dt(bp_plan *p, const void *sino, bp_dtype dt, float *img, int batch, int accumulate,
                           cudaStream_t st, float wuni, int S) {
     switch (dt) {
         case BP_BF16:
-            return launch_klein_t<__nv_bfloat16, MINB, 3, BPT>(p, (const __nv_bfloat16 *)sino, img, batch, accumulate,
+            return launch_klein_t<__nv_bfloat16, MINB, 3, BPT, STG>(p, (const __nv_bfloat16 *)sino, img, batch, accumulate,
                                                               st, wuni, S);
         case BP_F16:
-            return launch_klein_t<__half, MINB, 3, BPT>(p, (const __half *)sino, img, batch, accumulate, st, wuni, S);
+            return launch_klein_t<__half, MINB, 3, BPT, STG>(p, (const __half *)sino, img, batch, accumulate, st, wuni, S);
         default:
-            return launch_klein_t<float, MINB, 3, BPT>(p, (const float *)sino, img, batch, accumulate, st, wuni, S);
+            return launch_klein_t<float, MINB, 3, BPT, STG>(p, (const float *)sino, img, batch, accumulate, st, wuni, S);
     }
 }
 
 }  // namespace
 
 // The four-image form's launch shape: shape[0] = 16 -> one block per thread, three 256-thread
-// CTAs per SM (up to 80 registers); 8 -> the same at two CTAs per SM (up to 128 registers);
-// 32 -> two blocks per thread (128-thread CTAs share the per-angle work), three CTAs per SM;
-// shape[1] = angle groups S of the persistent schedule.  Three stages of windows are in flight.
+// CTAs per SM (up to 80 registers), 8-angle stages; 32 -> two blocks per thread (128-thread CTAs
+// share the per-angle work), three CTAs per SM, 8-angle stages; 8 -> two blocks per thread, four
+// CTAs per SM (up to 128 registers), 6-angle stages; shape[1] = angle groups S of the
+// persistent schedule.  Three stages of windows are in flight.
 bp_status launch_direct_klein(bp_plan *p, const void *sino, bp_dtype dt, float *img, int batch, int accumulate,
                               cudaStream_t st, float wuni, int stage, int S) {
-    if (stage == 8) return launch_klein_dt<2, 1>(p, sino, dt, img, batch, accumulate, st, wuni, S);
-    if (stage == 32) return launch_klein_dt<3, 2>(p, sino, dt, img, batch, accumulate, st, wuni, S);
-    return launch_klein_dt<3, 1>(p, sino, dt, img, batch, accumulate, st, wuni, S);
+    if (stage == 8) return launch_klein_dt<4, 2, 6>(p, sino, dt, img, batch, accumulate, st, wuni, S);
+    if (stage == 32) return launch_klein_dt<3, 2, 8>(p, sino, dt, img, batch, accumulate, st, wuni, S);
+    return launch_klein_dt<3, 1, 8>(p, sino, dt, img, batch, accumulate, st, wuni, S);
 }
 
 }  // namespace bp
