@@ -33,9 +33,15 @@ FLOPS_PER_UPDATE = 7          # coordinate FMA (2) + fraction (1) + lerp sub and
 FP32_LANES_PER_SM = 128       # FP32 FMA lanes per SM
 L2_FLUSH_BYTES = 256 << 20    # > 129 MB L2
 # sources whose content the committed DRAM-traffic record of a kernel is tied to
+_FOURIER_SOURCES = ("fourier.cu", "fft.cuh", "fft_pt.cuh", "tma.cuh", "geometry.cuh")
 KERNEL_SOURCES = {
     "bp_direct_klein_kernel": ("direct_klein.cu", "direct_tile.cuh", "tma.cuh", "f32x2.cuh", "geometry.cuh"),
     "bp_direct_quad_sync_kernel": ("direct.cu", "direct_tile.cuh", "tma.cuh", "geometry.cuh", "f32x2.cuh"),
+    "filter_pt_kernel": ("filter.cu", "fft.cuh", "fft_pt.cuh"),
+    "fourier_spectra_pt_kernel": _FOURIER_SOURCES,
+    "gridding": _FOURIER_SOURCES,
+    "ifft_pt_kernel (y pass)": _FOURIER_SOURCES,
+    "ifft_pt_kernel (x pass)": _FOURIER_SOURCES,
 }
 
 
@@ -55,18 +61,29 @@ def kernel_hash(kernel: str) -> str:
     return h.hexdigest()[:16]
 
 
-def _traffic_record(kernel, shape):
-    """DRAM bytes per launch of `kernel` from its committed ncu summary, if the kernel's sources are
-    unchanged since that capture and it used the same launch shape; else None."""
-    path = os.path.join(ROOT, "profiles", f"{kernel}_traffic.json")
+def traffic_path(kernel: str) -> str:
+    slug = "".join(ch if ch.isalnum() else "_" for ch in kernel).strip("_")
+    while "__" in slug:
+        slug = slug.replace("__", "_")
+    return os.path.join(ROOT, "profiles", f"{slug}_traffic.json")
+
+
+def _traffic_record(kernel, shape=None, workload=None):
+    """The committed ncu DRAM-traffic record of `kernel` (per call of its operator), if the
+    kernel's sources are unchanged since that capture and it ran the same launch shape (direct
+    kernels) on the same workload; else None."""
     try:
-        with open(path) as f:
+        with open(traffic_path(kernel)) as f:
             rec = json.load(f)
-        if rec.get("kernel_hash") == kernel_hash(kernel) and list(rec.get("launch_shape", [])) == list(shape):
-            return rec
+        if rec.get("kernel_hash") != kernel_hash(kernel):
+            return None
+        if shape is not None and list(rec.get("launch_shape", [])) != list(shape):
+            return None
+        if workload is not None and rec.get("workload") != workload:
+            return None
+        return rec
     except Exception:
-        pass
-    return None
+        return None
 
 
 class ClockSampler:
@@ -329,6 +346,11 @@ def kernel_rooflines(times: dict, ctx: dict, hbm_gbs: float, fp32_tflops: float)
                         "peak": hbm_gbs if bound == "hbm" else fp32_tflops,
                         "unit": "GB/s" if bound == "hbm" else "TFLOP/s",
                         "frac": max(t_hbm, t_alu) / sec})
+            rec = None if name.startswith("bp_direct") or ctx.get("batch", 1) != 1 else \
+                _traffic_record(name, None, ctx.get("workload"))
+            if rec and all(ctx.get(k) == v for k, v in rec.get("match", {}).items()):  # ncu dram__bytes_read.sum + dram__bytes_write.sum of the same kernel(s), per call
+                row["traffic"] = rec["dram_bytes_per_call"]
+                row["traffic_over_algorithmic"] = rec["dram_bytes_per_call"] / b
         out[name] = row
     return out
 
@@ -380,7 +402,7 @@ def other_paths(plan, q, img, flush, stream, dev, only=(), peaks=(6778.3, 80.5),
     out = {}
     checks = {} if checks is None else checks
     ctx = {"N": wl.N, "n_det": wl.n_det, "n_theta": wl.n_theta, "esz": 4, "P": 4096, "M": 4096, "W": 6,
-           "theta": wl.theta, "dt": wl.det_spacing}
+           "theta": wl.theta, "dt": wl.det_spacing, "workload": wl.name}
     qh = q.double().cpu().numpy()  # the exact float32 values the kernels read, as FP64
     rng = np.random.default_rng(11)
     pix2048 = rng.choice(wl.N * wl.N, 120, replace=False)
@@ -546,7 +568,7 @@ def other_paths(plan, q, img, flush, stream, dev, only=(), peaks=(6778.3, 80.5),
         q16 = q.to(torch.bfloat16)
         shape, _ = plan.autotune("direct", torch.bfloat16, 1)
         ms = _timed(lambda: plan.backproject(q16, out=img), stream, flush, 10)
-        kern = prof(plan, lambda: plan.backproject(q16, out=img), dict(ctx, esz=2))
+        kern = prof(plan, lambda: plan.backproject(q16, out=img), dict(ctx, esz=2, workload=None))
         got = pick(img, pix2048)
         q16h = q16.double().cpu().numpy()
 
@@ -844,7 +866,7 @@ def run_gpu(args, world, rank, local):
     # per-kernel event times of the step (a separate pass after the timed region, from the library's
     # stage timer on the launching stream)
     ctx = {"N": wl.N, "n_det": wl.n_det, "n_theta": wl.n_theta, "esz": 4, "P": 4096, "M": 4096, "W": 6,
-           "theta": wl.theta, "dt": wl.det_spacing}
+           "theta": wl.theta, "dt": wl.det_spacing, "workload": wl.name}
     step_kernels = kernel_rooflines(kernel_profile(plan, step, flush, max(3, min(args.steps, 10))), ctx, hbm_gbs,
                                     peak_tflops)
     launches_per_step = int(round(sum(v["launches_per_call"] for v in step_kernels.values())))

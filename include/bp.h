@@ -362,9 +362,12 @@ bp_status bp_stage_times(bp_plan *plan, int cap, const char **names, float *ms, 
  *               angle set closed under theta -> pi - theta (every uniform set) take the
  *               four-image form instead (one thread serves a pixel block and its three mirror
  *               images; per-call row tables in a plan workspace allocated on first use):
- *               shape[0] = 8 selects two CTAs per SM, else three; shape[1] = angle groups of
- *               its persistent schedule (<= 64); its partial sums are always added atomically,
- *               so its summation order varies between runs within FP32 rounding.
+ *               shape[0] = 32 gives each thread two pixel blocks at three CTAs per SM (the
+ *               default), 16 one block at three CTAs per SM, 8 two blocks at four CTAs per SM
+ *               with 6-angle stages; shape[1] = angle groups of its persistent schedule
+ *               (<= 64; default: one per ~96 MB of row tables, so that a group's tables stay
+ *               in L2); its partial sums are always added atomically, so its summation order
+ *               varies between runs within FP32 rounding.
  *               bp_fbp_static never takes it (it allocates nothing).
  * BP_OP_RADON   direct R (bp_radon and bp_backproject_transpose with the direct form):
  *               shape[0] = angles per CTA (1, 2 or 4); shape[1] = image bands per angle block
@@ -375,9 +378,10 @@ bp_status bp_stage_times(bp_plan *plan, int cap, const char **names, float *ms, 
  *
  * A call (op, dtype, batch) takes the plan's own shape for (op, dtype, batch), else the
  * process-wide tuning cache entry for the plan's geometry (N, n_det, n_theta, window, SM
- * count), else the default rule: stage 16 and enough angle groups for about two waves of
- * three CTAs per SM; Radon: 4 angles per CTA (2 or 1 when their detector rows exceed
- * 64 KB) and enough bands for four CTAs per SM.  Out-of-range values are clamped at launch
+ * count), else the default rule: the four-image form's default above where it applies, else
+ * stage 16 and enough angle groups for about two waves of three CTAs per SM; Radon: 4
+ * angles per CTA (2 or 1 when their detector rows exceed 64 KB) and enough bands for four
+ * CTAs per SM.  Out-of-range values are clamped at launch
  * (stage lowered when its shared memory does not fit, groups kept <= the number of stages).
  */
 typedef enum { BP_OP_DIRECT = 0, BP_OP_RADON = 1 } bp_op;
@@ -386,7 +390,8 @@ typedef enum { BP_OP_DIRECT = 0, BP_OP_RADON = 1 } bp_op;
  * bp_autotune -- time the candidate shapes of `op` for this plan at (dtype, batch) on
  * `stream` with CUDA events (scratch device buffers are allocated, filled with a fixed
  * pattern and freed inside the call; the stream is synchronised) and keep the fastest for
- * the plan and in the process-wide cache.  dtype is ignored for BP_OP_RADON.  shape
+ * the plan and in the process-wide cache (for BP_OP_DIRECT the default shape is kept unless
+ * another is more than 1 % faster).  dtype is ignored for BP_OP_RADON.  shape
  * (nullable, 2 ints) receives the chosen shape, ms (nullable) the best time of one call in
  * milliseconds.  Not allowed while `stream` is being captured.
  */
