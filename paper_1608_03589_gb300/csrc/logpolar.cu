@@ -35,6 +35,7 @@ namespace bp {
 namespace {
 
 constexpr int kMaxLP = 16384;  // longest transform held in shared memory
+constexpr int kLpBatch = 8;    // column-segment loads in flight per thread
 
 // Row source of the first transform: the log-polar resampled sinogram, or the kernel.
 template <typename Tin>
@@ -114,9 +115,20 @@ lp_cols_kernel(float2 *__restrict__ T, float2 *__restrict__ Khat, const float2 *
     float2 *tws = z + (size_t)C * n_phi;
     stage_twiddles(tws, tw, n_phi / 2);
     const long long k0 = (long long)blockIdx.x * C;
-    for (int e = threadIdx.x; e < C * n_phi; e += blockDim.x) {
-        const int q = e / C, c = e - q * C;
-        z[c * n_phi + q] = T[(long long)q * L + k0 + c];
+    const int nel = C * n_phi, bd = (int)blockDim.x;
+    // column segments of 8 C bytes from n_phi rows: eight loads in flight per thread
+    for (int e0 = threadIdx.x; e0 < nel; e0 += kLpBatch * bd) {
+        float2 v[kLpBatch];
+#pragma unroll
+        for (int u = 0; u < kLpBatch; ++u) {
+            const int e = e0 + u * bd, q = e / C, c = e - q * C;
+            if (e < nel) v[u] = T[(long long)q * L + k0 + c];
+        }
+#pragma unroll
+        for (int u = 0; u < kLpBatch; ++u) {
+            const int e = e0 + u * bd, q = e / C, c = e - q * C;
+            if (e < nel) z[c * n_phi + q] = v[u];
+        }
     }
     __syncthreads();
     const int nthr = fft_threads(n_phi), groups = blockDim.x / nthr;
@@ -130,9 +142,18 @@ lp_cols_kernel(float2 *__restrict__ T, float2 *__restrict__ Khat, const float2 *
         }
         return;
     }
-    for (int e = threadIdx.x; e < C * n_phi; e += blockDim.x) {
-        const int q = e / C, c = e - q * C;
-        z[c * n_phi + q] = cmul(z[c * n_phi + q], __ldg(Khat + (long long)q * L + k0 + c));
+    for (int e0 = threadIdx.x; e0 < nel; e0 += kLpBatch * bd) {
+        float2 kv[kLpBatch];
+#pragma unroll
+        for (int u = 0; u < kLpBatch; ++u) {
+            const int e = e0 + u * bd, q = e / C, c = e - q * C;
+            if (e < nel) kv[u] = __ldg(Khat + (long long)q * L + k0 + c);
+        }
+#pragma unroll
+        for (int u = 0; u < kLpBatch; ++u) {
+            const int e = e0 + u * bd, q = e / C, c = e - q * C;
+            if (e < nel) z[c * n_phi + q] = cmul(z[c * n_phi + q], kv[u]);
+        }
     }
     __syncthreads();
     for (int c0 = 0; c0 < C; c0 += groups) stockham_fft<E>(z + (c0 + g) * n_phi, logPhi, tws, 1, true, tid, nthr);

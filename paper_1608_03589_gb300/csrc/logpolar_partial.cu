@@ -32,6 +32,8 @@ namespace bp {
 
 namespace {
 
+constexpr int kLppBatch = 8;  // column-segment loads in flight per thread
+
 constexpr int kMaxLPP = 16384;  // longest transform held in shared memory
 
 __device__ __forceinline__ void norm_frac(int &k, float &f) {
@@ -136,9 +138,20 @@ lpp_cols_kernel(float2 *__restrict__ T, float2 *__restrict__ Khat, const float2 
     float2 *tws = z + (size_t)C * Lp;
     stage_twiddles(tws, tw, Lp / 2);
     const long long k0 = (long long)blockIdx.x * C;
-    for (int e = threadIdx.x; e < C * Lp; e += blockDim.x) {
-        const int q = e / C, c = e - q * C;
-        z[c * Lp + q] = q < n_in ? T[(long long)q * Lr + k0 + c] : make_float2(0.f, 0.f);
+    const int nel = C * Lp, bd = (int)blockDim.x;
+    // column segments of 8 C bytes from the n_in rows: eight loads in flight per thread
+    for (int e0 = threadIdx.x; e0 < nel; e0 += kLppBatch * bd) {
+        float2 v[kLppBatch];
+#pragma unroll
+        for (int u = 0; u < kLppBatch; ++u) {
+            const int e = e0 + u * bd, q = e / C, c = e - q * C;
+            v[u] = (e < nel && q < n_in) ? T[(long long)q * Lr + k0 + c] : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < kLppBatch; ++u) {
+            const int e = e0 + u * bd, q = e / C, c = e - q * C;
+            if (e < nel) z[c * Lp + q] = v[u];
+        }
     }
     __syncthreads();
     const int nthr = fft_threads(Lp), groups = blockDim.x / nthr;
@@ -152,9 +165,18 @@ lpp_cols_kernel(float2 *__restrict__ T, float2 *__restrict__ Khat, const float2 
         }
         return;
     }
-    for (int e = threadIdx.x; e < C * Lp; e += blockDim.x) {
-        const int q = e / C, c = e - q * C;
-        z[c * Lp + q] = cmul(z[c * Lp + q], __ldg(Khat + (long long)q * Lr + k0 + c));
+    for (int e0 = threadIdx.x; e0 < nel; e0 += kLppBatch * bd) {
+        float2 kv[kLppBatch];
+#pragma unroll
+        for (int u = 0; u < kLppBatch; ++u) {
+            const int e = e0 + u * bd, q = e / C, c = e - q * C;
+            if (e < nel) kv[u] = __ldg(Khat + (long long)q * Lr + k0 + c);
+        }
+#pragma unroll
+        for (int u = 0; u < kLppBatch; ++u) {
+            const int e = e0 + u * bd, q = e / C, c = e - q * C;
+            if (e < nel) z[c * Lp + q] = cmul(z[c * Lp + q], kv[u]);
+        }
     }
     __syncthreads();
     for (int c0 = 0; c0 < C; c0 += groups) stockham_fft<E>(z + (c0 + g) * Lp, logLp, tws, 1, true, tid, nthr);
