@@ -1,6 +1,7 @@
 // Shared declarations of the sm_103a backprojection library (internal, not part of the ABI).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -42,6 +43,8 @@ struct FourierWork {
     float2 *spec = nullptr;     // [n_theta][P/2] sample values c_{k,m}
     float2 *grid = nullptr;     // [M][M] gridded spectrum, G[l_x][l_y]
     float2 *mid = nullptr;      // [N][M] after the first inverse-FFT pass
+    CUtensorMap mid_map;        // mid as FP32 [N][2M], boxes of 16 bytes x 256 rows (TMA stores)
+    bool mid_map_ok = false;
     float *deapod = nullptr;    // [N] 1 / phi_hat(i - floor(N/2))
     float *wk = nullptr;        // [n_theta] quadrature weights (float)
     float2 *twM = nullptr;      // M/2 twiddles exp(-2 pi i r / M)

@@ -589,26 +589,42 @@ ifft_pass_x_kernel(const float2 *__restrict__ inter, float *__restrict__ img, co
 // pos = i of the transform, i.e. image index (i + floor(N/2)) mod M when that is below N.
 //   XPASS false: rows l_x of G in pairs (2p, 2p + 1); the first row's outputs wait in shared
 //                memory and leave with the second's as 16-byte pairs,
-//                inter[i_y][2p .. 2p + 1] = z * deap[i_y];
+//                inter[i_y][2p .. 2p + 1] = z * deap[i_y] (TST: the pairs are staged in shared
+//                memory and written by 2D TMA stores of 256 rows, off the load/store path);
 //   XPASS true:  rows i_y of inter, img[i_y][i_x] = Re z * deap[i_x].
-template <int LOGM, bool XPASS>
+// 128-byte aligned start (in float2) of the y pass's output staging after the work array and
+// twiddles
+template <int LOGM>
+__host__ __device__ constexpr int ifft_pt_stage_off() {
+    return ((1 << LOGM) + pt_offset<LOGM>(PtPlan<LOGM>::npass) + 15) & ~15;
+}
+template <int LOGM, bool XPASS, bool TST = false>
 __host__ __device__ constexpr int ifft_pt_smem_elems() {
-    // work array, per-pass twiddles (even count), held first-row outputs (N <= M/2)
-    return (1 << LOGM) + pt_offset<LOGM>(PtPlan<LOGM>::npass) + (XPASS ? 0 : (1 << LOGM) / 2);
+    // work array, per-pass twiddles (even count); y pass: the held first-row outputs (N <= M/2),
+    // or with TMA stores a staging buffer of M/2 16-byte pairs
+    return XPASS ? (1 << LOGM) + pt_offset<LOGM>(PtPlan<LOGM>::npass)
+                 : ifft_pt_stage_off<LOGM>() + (TST ? (1 << LOGM) : (1 << LOGM) / 2);
+}
+// the TMA-store y pass: 256-row boxes tile M/2, and two CTAs of its shared memory fit an SM
+template <int LOGM>
+constexpr bool ifft_tst_ok() {
+    return (1 << LOGM) >= 512 && sizeof(float2) * ifft_pt_smem_elems<LOGM, false, true>() <= 110u * 1024u;
 }
 
-template <int LOGM, bool XPASS>
+template <int LOGM, bool XPASS, bool TST = false>
 __global__ void __launch_bounds__((1 << LOGM) / kPassE, 1024 / ((1 << LOGM) / kPassE))
 ifft_pt_kernel(const float2 *__restrict__ in, float2 *__restrict__ inter, float *__restrict__ img,
-               const float *__restrict__ deap, const float2 *__restrict__ twp, int rows, int N) {
+               const float *__restrict__ deap, const float2 *__restrict__ twp, int rows, int N,
+               const __grid_constant__ CUtensorMap omap) {
     using PL = PtPlan<LOGM>;
     constexpr int M = 1 << LOGM, NT = M / kPassE, Rl = PL::Rl, Gl = kPassE / Rl;
     constexpr int TWN = pt_offset<LOGM>(PL::npass);
     static_assert(TWN % 2 == 0, "per-pass twiddle count");
-    extern __shared__ __align__(16) float2 pz[];
-    float2 *z = pz;          // [M] work array
-    float2 *T = z + M;       // [TWN] per-pass twiddles
-    float2 *hold = T + TWN;  // [M/2] first row's outputs of a pair, by image index (y pass)
+    extern __shared__ __align__(128) float2 pz[];
+    float2 *z = pz;                                 // [M] work array
+    float2 *T = z + M;                              // [TWN] per-pass twiddles
+    float2 *hold = pz + ifft_pt_stage_off<LOGM>();  // y pass: [M/2] first row's outputs, by image index;
+                                                    // TST: [M/2] 16-byte output pairs
     const int t = threadIdx.x;
     const int h = N / 2;
     float2 nxt[kPassE];  // inputs of the first pass: x[t + r NT]
@@ -645,6 +661,44 @@ ifft_pt_kernel(const float2 *__restrict__ in, float2 *__restrict__ inter, float 
                     if (o >= 0 && o < N) img[(long long)row * N + o] = c[g][q].x * __ldg(deap + o);
                 }
         }
+    } else if constexpr (TST) {
+        // rows 2p, 2p + 1: each output pair (first row .xy, second .zw) is staged in shared
+        // memory and the staged column pair leaves as 2D TMA stores of 256 rows
+        // inter[o0 .. o0 + 255][2p .. 2p + 1] (the tensor map clips rows >= N); the staging
+        // buffer is rewritten once the previous pair's stores have read it
+        float4 *sb = reinterpret_cast<float4 *>(hold);
+        for (; row < rows; row = (row & 1) ? row - 1 + 2 * (int)gridDim.x : row + 1) {
+            float2 a[kPassE];
+#pragma unroll
+            for (int r = 0; r < kPassE; ++r) a[r] = nxt[r];
+            const int nr = (row & 1) ? row - 1 + 2 * (int)gridDim.x : row + 1;
+            if (nr < rows) fetch(nr);
+            // the previous pair's stores have read the buffer (the barriers inside the transform
+            // order this wait before every thread's staging writes)
+            if (!(row & 1) && t == 0) bulk_wait_read<0>();
+            float2 c[Gl][Rl];
+            pt_row<LOGM, true>(a, z, T, t, c);
+#pragma unroll
+            for (int g = 0; g < Gl; ++g)
+#pragma unroll
+                for (int q = 0; q < Rl; ++q) {
+                    const int i = t + (g + q * Gl) * NT;
+                    const int o = i < N - h ? i + h : i - (M - h);
+                    if (o >= 0 && o < N) {
+                        const float d = __ldg(deap + o);
+                        reinterpret_cast<float2 *>(sb + o)[row & 1] = make_float2(c[g][q].x * d, c[g][q].y * d);
+                    }
+                }
+            if (row & 1) {
+                fence_proxy_async_smem();  // this thread's staging writes, before the async-proxy reads
+                __syncthreads();           // the pair is staged
+                if (t == 0) {
+                    for (int o0 = 0; o0 < N; o0 += 256) tma_store_2d(&omap, 2 * (row - 1), o0, smem_u32(sb + o0));
+                    bulk_commit();
+                }
+            }
+        }
+        if (t == 0) bulk_wait_all();
     } else {
         // rows 2p, 2p + 1 (p = b, b + G, ...): the first row's outputs wait in shared memory
         // (read back by the same thread) and leave with the second's as 16-byte pairs
@@ -869,6 +923,91 @@ fft_pt_fwd_cols_kernel(const float2 *__restrict__ Tin, float2 *__restrict__ out,
                 for (int r = 0; r < kPassE; ++r) a[r] = make_float2(0.f, 0.f);
 #pragma unroll
                 for (int j = 0; j < 4; ++j) a[RV[j]] = hold[j * NT + t];
+            }
+            float2 c[Gl][Rl];
+            pt_row<LOGM, false>(a, z, T, t, c);
+            float2 *dst = out + (long long)(2 * pair + half) * M;
+#pragma unroll
+            for (int g = 0; g < Gl; ++g)
+#pragma unroll
+                for (int q = 0; q < Rl; ++q) dst[t + (g + q * Gl) * NT] = c[g][q];
+        }
+    }
+}
+
+// The same column pass with the column pairs brought in by 2D TMA loads (boxes of one column
+// pair x 256 rows of the intermediate, through its tensor map) into a shared staging buffer:
+// the first column's inputs are read as .xy, the second's as .zw, and once the second's are in
+// registers the next pair's loads are issued, in flight during the second transform.  Every
+// wait is bounded: on expiry the kernel sets *err, waits (bounded) for its copy once more and
+// returns.
+template <int LOGM>
+__global__ void __launch_bounds__((1 << LOGM) / kPassE, 1024 / ((1 << LOGM) / kPassE))
+fft_pt_fwd_cols_tma_kernel(const __grid_constant__ CUtensorMap imap, float2 *__restrict__ out,
+                           const float2 *__restrict__ twp, int rows, int *__restrict__ err) {
+    using PL = PtPlan<LOGM>;
+    constexpr int M = 1 << LOGM, NT = M / kPassE, Rl = PL::Rl, Gl = kPassE / Rl;
+    constexpr int TWN = pt_offset<LOGM>(PL::npass);
+    constexpr int N = M / 2, h = N / 2;
+    constexpr int NBOX = (N + 255) / 256;
+    constexpr int RV[4] = {0, 1, kPassE - 2, kPassE - 1};  // the inputs inside the image
+    static_assert(TWN % 2 == 0, "per-pass twiddle count");
+    extern __shared__ __align__(128) float2 pz[];
+    __shared__ __align__(8) unsigned long long bar;
+    float2 *z = pz;  // [M] work array
+    float2 *T = z + M;  // [TWN] per-pass twiddles
+    float4 *stg = reinterpret_cast<float4 *>(pz + ifft_pt_stage_off<LOGM>());  // [NBOX 256] staged pairs
+    const int t = threadIdx.x;
+    const uint32_t b = smem_u32(&bar);
+    const int npairs = rows / 2;
+    auto issue = [&](int pr) {  // thread 0: the column pair's boxes
+        mbar_expect_tx(b, (uint32_t)(NBOX * 256 * sizeof(float4)));
+        for (int k = 0; k < NBOX; ++k) tma_load_2d(smem_u32(stg + 256 * k), &imap, 4 * pr, 256 * k, b);
+    };
+    if (t == 0) {
+        mbar_init(b, 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    int pair = blockIdx.x;
+    if (t == 0 && pair < npairs) issue(pair);
+    {
+        constexpr int n4t = TWN / 2;
+        const float4 *ts = reinterpret_cast<const float4 *>(twp);
+        float4 *td = reinterpret_cast<float4 *>(T);
+#pragma unroll
+        for (int i = 0; i < (n4t + NT - 1) / NT; ++i)
+            if (t + i * NT < n4t) td[t + i * NT] = __ldg(ts + t + i * NT);
+    }
+    int o[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int pos = t + RV[j] * NT;
+        o[j] = pos < N - h ? pos + h : pos - (M - h);
+    }
+    uint32_t parity = 0;
+    for (; pair < npairs; pair += gridDim.x) {
+        if (__syncthreads_or(!mbar_wait(b, parity))) {
+            if (t == 0) atomicExch(err, 1);
+            mbar_wait(b, parity);
+            return;
+        }
+        parity ^= 1u;
+#pragma unroll 1
+        for (int half = 0; half < 2; ++half) {
+            float2 a[kPassE];
+#pragma unroll
+            for (int r = 0; r < kPassE; ++r) a[r] = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float4 v = stg[o[j]];
+                a[RV[j]] = half ? make_float2(v.z, v.w) : make_float2(v.x, v.y);
+            }
+            if (half) {
+                // every thread holds its inputs: the staging buffer takes the next pair
+                fence_proxy_async_smem();
+                __syncthreads();
+                if (t == 0 && pair + (int)gridDim.x < npairs) issue(pair + gridDim.x);
             }
             float2 c[Gl][Rl];
             pt_row<LOGM, false>(a, z, T, t, c);
@@ -1244,6 +1383,18 @@ bp_status ensure_fourier(bp_plan *p) {
         free_fourier(p);
         return cuda_fail(e, "Fourier workspace");
     }
+    // mid as FP32 [N][2M] for the y pass's TMA stores: boxes of 4 floats (one column pair) x
+    // 256 rows
+    f.mid_map_ok = false;
+    if (PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder()) {
+        const cuuint64_t gdim[2] = {(cuuint64_t)2 * M, (cuuint64_t)N};
+        const cuuint64_t gstride[1] = {(cuuint64_t)M * sizeof(float2)};
+        const cuuint32_t box[2] = {4, 256};
+        const cuuint32_t estr[2] = {1, 1};
+        f.mid_map_ok = enc(&f.mid_map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, f.mid, gdim, gstride, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    }
     return BP_OK;
 }
 
@@ -1316,9 +1467,12 @@ template <int LOGM>
 static bp_status launch_ifft_pt(bp_plan *p, const float *deap, float *img, cudaStream_t st) {
     FourierWork &f = p->four;
     constexpr int M = 1 << LOGM, NT = M / kPassE;
-    constexpr size_t smem_y = sizeof(float2) * ifft_pt_smem_elems<LOGM, false>();
+    constexpr bool TST = ifft_tst_ok<LOGM>();
+    const bool tst = TST && f.mid_map_ok;
+    const size_t smem_y =
+        sizeof(float2) * (tst ? ifft_pt_smem_elems<LOGM, false, true>() : ifft_pt_smem_elems<LOGM, false>());
     constexpr size_t smem_x = sizeof(float2) * ifft_pt_smem_elems<LOGM, true>();
-    auto ky = ifft_pt_kernel<LOGM, false>;
+    auto ky = tst ? ifft_pt_kernel<LOGM, false, TST> : ifft_pt_kernel<LOGM, false>;
     auto kx = ifft_pt_kernel<LOGM, true>;
     BP_CUDA_TRY(cudaFuncSetAttribute(ky, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_y));
     BP_CUDA_TRY(cudaFuncSetAttribute(kx, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_x));
@@ -1328,10 +1482,10 @@ static bp_status launch_ifft_pt(bp_plan *p, const float *deap, float *img, cudaS
     const int sms = std::max(1, p->sm_count);
     // the y pass takes rows in pairs (M is even)
     ky<<<std::min(std::max(1, per_sm_y) * sms, M / 2), NT, smem_y, st>>>(f.grid, f.mid, nullptr, deap, f.twpassM, M,
-                                                                        p->N);
+                                                                        p->N, f.mid_map);
     stage_mark(p, st, "ifft_pt_kernel (y pass)");
     kx<<<std::min(std::max(1, per_sm_x) * sms, p->N), NT, smem_x, st>>>(f.mid, nullptr, img, deap, f.twpassM, p->N,
-                                                                       p->N);
+                                                                       p->N, f.mid_map);
     stage_mark(p, st, "ifft_pt_kernel (x pass)");
     BP_CUDA_TRY(cudaGetLastError());
     return BP_OK;
@@ -1488,7 +1642,17 @@ static bp_status launch_fft_pt_fwd(bp_plan *p, const float *img, cudaStream_t st
     const int ctas = std::max(1, per_sm) * std::max(1, p->sm_count);
     kx<<<std::min(ctas, p->N), NT, smem, st>>>(img, nullptr, f.mid, f.deapod, f.twpassM, p->N, p->N);
     stage_mark(p, st, "fft_pt_fwd_kernel (x pass)");
-    if (2 * p->N == M) {
+    if (2 * p->N == M && f.mid_map_ok && ifft_tst_ok<LOGM>()) {
+        // columns in pairs through 2D TMA loads
+        constexpr size_t smem2 = sizeof(float2) * (ifft_pt_stage_off<LOGM>() + M);
+        auto kc = fft_pt_fwd_cols_tma_kernel<LOGM>;
+        BP_CUDA_TRY(cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2));
+        int per_sm2 = 0;
+        BP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, kc, NT, smem2));
+        kc<<<std::min(std::max(1, per_sm2) * std::max(1, p->sm_count), M / 2), NT, smem2, st>>>(
+            f.mid_map, f.grid, f.twpassM, M, p->d_err);
+        stage_mark(p, st, "fft_pt_fwd_cols_kernel");
+    } else if (2 * p->N == M) {
         // columns in pairs, 16-byte loads
         constexpr size_t smem2 = smem + sizeof(float2) * (M / 2);
         auto kc = fft_pt_fwd_cols_kernel<LOGM>;
