@@ -89,9 +89,12 @@ struct LogPolarWork {
     float2 *kfrac = nullptr;   // [n_phi] kernel node and fraction of -ln cos(theta') / drho
     int4 *pix = nullptr;       // [N*N] pixel -> (rho node, fraction, theta node, fraction)
     float2 *twL = nullptr, *twPhi = nullptr;
+    float2 *twPassPhi = nullptr;  // per-pass twiddles of the n_phi-point transform (n_phi = 512 .. 4096)
     float2 *T = nullptr;       // [n_phi][L] complex work array
     float2 *Khat = nullptr;    // [n_phi][L] kernel transform (scaled)
     float *B = nullptr;        // [n_phi][n_out] backprojection on the log-polar mesh
+    CUtensorMap T_map, K_map;  // T and Khat as FP32 [n_phi][2L], boxes of one column pair x min(256, n_phi) rows
+    bool maps_ok = false;
     size_t bytes = 0;
 };
 

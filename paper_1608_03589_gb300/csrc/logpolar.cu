@@ -29,6 +29,8 @@
 
 #include "common.cuh"
 #include "fft.cuh"
+#include "fft_pt.cuh"
+#include "tma.cuh"
 
 namespace bp {
 
@@ -163,6 +165,116 @@ lp_cols_kernel(float2 *__restrict__ T, float2 *__restrict__ Khat, const float2 *
     }
 }
 
+// The same column pass (prep = 0) over column pairs through the TMA, with the persistent
+// transform (first and last passes in registers, per-pass twiddles in shared memory): the pair
+// of T arrives by 2D TMA loads (boxes of 16 bytes x BR rows) in a staging buffer and both
+// columns' inputs go to registers; the pair of Khat then arrives in the same buffer during the
+// forward transforms and is multiplied into their register outputs, which are the inverse
+// transforms' inputs; the next pair of T is requested before the inverse transforms, and the
+// result leaves through a second staging buffer by 2D TMA stores.  Every wait is bounded: on
+// expiry the kernel sets *err, waits (bounded) for its copy once more and returns.
+template <int LOGP>
+__host__ __device__ constexpr int lp_cols_stage_off() {
+    return ((1 << LOGP) + pt_offset<LOGP>(PtPlan<LOGP>::npass) + 15) & ~15;
+}
+template <int LOGP>
+constexpr size_t lp_cols_pt_smem() {
+    return sizeof(float2) * ((size_t)lp_cols_stage_off<LOGP>() + 4 * (size_t)(1 << LOGP));
+}
+
+template <int LOGP>
+__global__ void __launch_bounds__((1 << LOGP) / kPassE, 1)
+lp_cols_pt_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap kmap,
+                  const float2 *__restrict__ twp, int L, int BR, int *__restrict__ err) {
+    using PL = PtPlan<LOGP>;
+    constexpr int NP = 1 << LOGP, NT = NP / kPassE, Rl = PL::Rl, Gl = kPassE / Rl;
+    constexpr int TWN = pt_offset<LOGP>(PL::npass);
+    extern __shared__ __align__(128) float2 z[];  // [NP] work | [TWN] twiddles | [NP] pairs in | [NP] pairs out
+    __shared__ __align__(8) unsigned long long bar;
+    float2 *T = z + NP;
+    float4 *sin = reinterpret_cast<float4 *>(z + lp_cols_stage_off<LOGP>());
+    float4 *sout = sin + NP;
+    const int t = threadIdx.x, nbox = NP / BR;
+    const uint32_t b = smem_u32(&bar);
+    auto issue = [&](const CUtensorMap *map, int pr) {  // thread 0: one column pair of map
+        mbar_expect_tx(b, (uint32_t)(NP * sizeof(float4)));
+        for (int k = 0; k < nbox; ++k) tma_load_2d(smem_u32(sin + k * BR), map, 4 * pr, k * BR, b);
+    };
+    if (t == 0) {
+        mbar_init(b, 1);
+        mbar_fence_init();
+    }
+    {
+        constexpr int n4t = (TWN + 1) / 2;  // float4 loads of the (even-padded) table
+        const float4 *ts = reinterpret_cast<const float4 *>(twp);
+        float4 *td = reinterpret_cast<float4 *>(T);
+        for (int i = t; i < n4t; i += NT) td[i] = __ldg(ts + i);
+    }
+    __syncthreads();
+    const int npairs = L / 2;
+    int pair = blockIdx.x;
+    if (t == 0 && pair < npairs) issue(&tmap, pair);
+    uint32_t parity = 0;
+    auto wait = [&]() -> bool {
+        if (__syncthreads_or(!mbar_wait(b, parity))) {
+            if (t == 0) atomicExch(err, 1);
+            mbar_wait(b, parity);
+            return false;
+        }
+        parity ^= 1u;
+        return true;
+    };
+    for (; pair < npairs; pair += gridDim.x) {
+        if (!wait()) return;  // T's pair
+        float2 a0[kPassE], a1[kPassE];
+#pragma unroll
+        for (int r = 0; r < kPassE; ++r) {
+            const float4 v = sin[t + r * NT];
+            a0[r] = make_float2(v.x, v.y);
+            a1[r] = make_float2(v.z, v.w);
+        }
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (t == 0) issue(&kmap, pair);
+        float2 c0[Gl][Rl], c1[Gl][Rl];
+        pt_row<LOGP, false>(a0, z, T, t, c0);
+        pt_row<LOGP, false>(a1, z, T, t, c1);
+        if (!wait()) return;  // Khat's pair
+#pragma unroll
+        for (int g = 0; g < Gl; ++g)
+#pragma unroll
+            for (int q = 0; q < Rl; ++q) {
+                const float4 k = sin[t + (g + q * Gl) * NT];
+                a0[g + q * Gl] = cmul(c0[g][q], make_float2(k.x, k.y));
+                a1[g + q * Gl] = cmul(c1[g][q], make_float2(k.z, k.w));
+            }
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (t == 0) {
+            if (pair + (int)gridDim.x < npairs) issue(&tmap, pair + gridDim.x);
+            bulk_wait_read<0>();  // the previous pair's stores have read the out buffer
+        }
+        // (the barrier at the start of each transform orders that wait before the writes below)
+        pt_row<LOGP, true>(a0, z, T, t, c0);
+#pragma unroll
+        for (int g = 0; g < Gl; ++g)
+#pragma unroll
+            for (int q = 0; q < Rl; ++q) reinterpret_cast<float2 *>(sout + t + (g + q * Gl) * NT)[0] = c0[g][q];
+        pt_row<LOGP, true>(a1, z, T, t, c1);
+#pragma unroll
+        for (int g = 0; g < Gl; ++g)
+#pragma unroll
+            for (int q = 0; q < Rl; ++q) reinterpret_cast<float2 *>(sout + t + (g + q * Gl) * NT)[1] = c1[g][q];
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (t == 0) {
+            for (int k = 0; k < nbox; ++k) tma_store_2d(&tmap, 4 * pair, k * BR, smem_u32(sout + k * BR));
+            bulk_commit();
+        }
+    }
+    if (t == 0) bulk_wait_all();
+}
+
 // Inverse transform along rho of row pair (2b, 2b+1), both real: packed as T_a + i T_b; the
 // first n_out outputs of each go to B.
 template <int E>
@@ -239,8 +351,30 @@ bp_status rows_fwd(bp_plan *p, const Tin *sino, int kernel_src, cudaStream_t st)
 
 int cols_per_cta(int n_phi) { return std::max(1, std::min(4, (int)(131072 / (sizeof(float2) * n_phi)))); }
 
+template <int LOGP>
+bp_status cols_pt(bp_plan *p, cudaStream_t st) {
+    LogPolarWork &w = p->lp;
+    constexpr size_t smem = lp_cols_pt_smem<LOGP>();
+    auto kern = lp_cols_pt_kernel<LOGP>;
+    BP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int ctas = std::min(w.L / 2, std::max(1, p->sm_count));
+    kern<<<ctas, (1 << LOGP) / kPassE, smem, st>>>(w.T_map, w.K_map, w.twPassPhi, w.L, std::min(256, w.n_phi),
+                                                    p->d_err);
+    BP_CUDA_TRY(cudaGetLastError());
+    return BP_OK;
+}
+
 bp_status cols(bp_plan *p, int prep, float scale, cudaStream_t st) {
     LogPolarWork &w = p->lp;
+    if (!prep && w.maps_ok && w.twPassPhi) {
+        switch (ilog2(w.n_phi)) {
+            case 9: return cols_pt<9>(p, st);
+            case 10: return cols_pt<10>(p, st);
+            case 11: return cols_pt<11>(p, st);
+            case 12: return cols_pt<12>(p, st);
+            default: break;
+        }
+    }
     const int C = cols_per_cta(w.n_phi);
     const size_t smem = sizeof(float2) * ((size_t)C * w.n_phi + w.n_phi / 2);
     auto kern = fft_elems(w.n_phi) == 16 ? lp_cols_kernel<16> : lp_cols_kernel<8>;
@@ -392,6 +526,12 @@ bp_status ensure_logpolar(bp_plan *p, cudaStream_t st) {
     alloc((void **)&w.pix, sizeof(int4) * pix.size());
     alloc((void **)&w.twL, sizeof(float2) * twL.size());
     alloc((void **)&w.twPhi, sizeof(float2) * twP.size());
+    std::vector<float2> twpp;  // per-pass twiddles of the n_phi-point transform (the persistent column pass)
+    if (n_phi >= 512 && n_phi <= 4096) {
+        build_pass_twiddles(ilog2(n_phi), twpp);
+        twpp.resize((twpp.size() + 1) & ~(size_t)1);
+        alloc((void **)&w.twPassPhi, sizeof(float2) * twpp.size());
+    }
     alloc((void **)&w.T, sizeof(float2) * (size_t)n_phi * L);
     alloc((void **)&w.Khat, sizeof(float2) * (size_t)n_phi * L);
     alloc((void **)&w.B, sizeof(float) * (size_t)n_phi * n_out);
@@ -404,9 +544,24 @@ bp_status ensure_logpolar(bp_plan *p, cudaStream_t st) {
     up(w.pix, pix.data(), sizeof(int4) * pix.size());
     up(w.twL, twL.data(), sizeof(float2) * twL.size());
     up(w.twPhi, twP.data(), sizeof(float2) * twP.size());
+    if (!twpp.empty()) up(w.twPassPhi, twpp.data(), sizeof(float2) * twpp.size());
     if (e != cudaSuccess) {
         free_logpolar(p);
         return cuda_fail(e, "log-polar workspace");
+    }
+    // T and Khat as FP32 [n_phi][2L] for the column pass's TMA copies (one column pair per box)
+    w.maps_ok = false;
+    if (PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder()) {
+        const cuuint64_t gdim[2] = {(cuuint64_t)2 * L, (cuuint64_t)n_phi};
+        const cuuint64_t gstride[1] = {(cuuint64_t)L * sizeof(float2)};
+        const cuuint32_t box[2] = {4, (cuuint32_t)std::min(256, n_phi)};
+        const cuuint32_t estr[2] = {1, 1};
+        auto encode = [&](CUtensorMap *m, void *base) {
+            return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, gdim, gstride, box, estr,
+                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+        };
+        w.maps_ok = encode(&w.T_map, w.T) && encode(&w.K_map, w.Khat);
     }
     // kernel transform, scaled by dphi / (N_phi L) (the two inverse transforms are unnormalised)
     bp_status s = rows_fwd<float>(p, nullptr, 1, st);
@@ -428,6 +583,7 @@ void free_logpolar(bp_plan *p) {
     cudaFree(w.pix);
     cudaFree(w.twL);
     cudaFree(w.twPhi);
+    cudaFree(w.twPassPhi);
     cudaFree(w.T);
     cudaFree(w.Khat);
     cudaFree(w.B);
