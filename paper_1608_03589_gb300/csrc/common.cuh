@@ -109,6 +109,9 @@ struct LppWork {
     int4 *atab = nullptr;      // [n_half] bracketing projections, flip bits, weight
     float2 *kfrac = nullptr;   // [Lp] kernel node and fraction per angular-transform row
     float2 *twLr = nullptr, *twLp = nullptr;
+    float2 *twPassLp = nullptr;  // per-pass twiddles of the Lp-point transform (Lp = 512 .. 4096)
+    CUtensorMap Tin_map, Tout_map, K_map;  // T (first K rows, first n_aout rows) and Khat as FP32 [rows][2 Lr]
+    bool maps_ok = false;
     float2 *T = nullptr;       // [Lp][Lr] complex work array
     float2 *Khat = nullptr;    // [Lp][Lr] kernel transform (scaled)
     float *B = nullptr;        // [n_aout + 1][n_out] one sector's output mesh

@@ -27,6 +27,8 @@
 
 #include "common.cuh"
 #include "fft.cuh"
+#include "fft_pt.cuh"
+#include "tma.cuh"
 
 namespace bp {
 
@@ -187,6 +189,125 @@ lpp_cols_kernel(float2 *__restrict__ T, float2 *__restrict__ Khat, const float2 
     }
 }
 
+// The column pass over column pairs through the TMA with the persistent transform (as the full
+// log-polar column pass): the pair's n_in input rows arrive by 2D TMA loads (rows beyond n_in
+// of the last box read as zero; those beyond the boxes are zero in registers), both columns'
+// inputs go to registers, the pair of Khat arrives during the forward transforms and is
+// multiplied into their outputs, the next pair is requested before the inverse transforms, and
+// the n_aout output rows (a_lo + r) mod Lp leave through a staging buffer by 2D TMA stores.
+// Every wait is bounded: on expiry the kernel sets *err, waits (bounded) for its copy once more
+// and returns.
+template <int LOGP>
+__host__ __device__ constexpr int lpp_cols_stage_off() {
+    return ((1 << LOGP) + pt_offset<LOGP>(PtPlan<LOGP>::npass) + 15) & ~15;
+}
+template <int LOGP>
+constexpr size_t lpp_cols_pt_smem() {
+    return sizeof(float2) * ((size_t)lpp_cols_stage_off<LOGP>() + 4 * (size_t)(1 << LOGP));
+}
+
+template <int LOGP>
+__global__ void __launch_bounds__((1 << LOGP) / kPassE)
+lpp_cols_pt_kernel(const __grid_constant__ CUtensorMap imap, const __grid_constant__ CUtensorMap omap,
+                   const __grid_constant__ CUtensorMap kmap, const float2 *__restrict__ twp, int Lr, int n_in,
+                   int a_lo, int n_aout, int BR, int *__restrict__ err) {
+    using PL = PtPlan<LOGP>;
+    constexpr int NP = 1 << LOGP, NT = NP / kPassE, Rl = PL::Rl, Gl = kPassE / Rl;
+    constexpr int TWN = pt_offset<LOGP>(PL::npass);
+    extern __shared__ __align__(128) float2 z[];  // [NP] work | [TWN] twiddles | [NP] pairs in | [NP] pairs out
+    __shared__ __align__(8) unsigned long long bar;
+    float2 *T = z + NP;
+    float4 *sin = reinterpret_cast<float4 *>(z + lpp_cols_stage_off<LOGP>());
+    float4 *sout = sin + NP;
+    const int t = threadIdx.x;
+    const int nb_in = (n_in + BR - 1) / BR, nb_k = NP / BR, nb_out = (n_aout + BR - 1) / BR;
+    const uint32_t b = smem_u32(&bar);
+    auto issue = [&](const CUtensorMap *map, int nb, int pr) {  // thread 0: nb boxes of one column pair
+        mbar_expect_tx(b, (uint32_t)(nb * BR * sizeof(float4)));
+        for (int k = 0; k < nb; ++k) tma_load_2d(smem_u32(sin + k * BR), map, 4 * pr, k * BR, b);
+    };
+    if (t == 0) {
+        mbar_init(b, 1);
+        mbar_fence_init();
+    }
+    {
+        constexpr int n4t = (TWN + 1) / 2;  // float4 loads of the (even-padded) table
+        const float4 *ts = reinterpret_cast<const float4 *>(twp);
+        float4 *td = reinterpret_cast<float4 *>(T);
+        for (int i = t; i < n4t; i += NT) td[i] = __ldg(ts + i);
+    }
+    __syncthreads();
+    const int npairs = Lr / 2;
+    int pair = blockIdx.x;
+    if (t == 0 && pair < npairs) issue(&imap, nb_in, pair);
+    uint32_t parity = 0;
+    auto wait = [&]() -> bool {
+        if (__syncthreads_or(!mbar_wait(b, parity))) {
+            if (t == 0) atomicExch(err, 1);
+            mbar_wait(b, parity);
+            return false;
+        }
+        parity ^= 1u;
+        return true;
+    };
+    for (; pair < npairs; pair += gridDim.x) {
+        if (!wait()) return;  // the input rows of the pair
+        float2 a0[kPassE], a1[kPassE];
+#pragma unroll
+        for (int r = 0; r < kPassE; ++r) {
+            const int q = t + r * NT;
+            const float4 v = q < n_in ? sin[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+            a0[r] = make_float2(v.x, v.y);
+            a1[r] = make_float2(v.z, v.w);
+        }
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (t == 0) issue(&kmap, nb_k, pair);
+        float2 c0[Gl][Rl], c1[Gl][Rl];
+        pt_row<LOGP, false>(a0, z, T, t, c0);
+        pt_row<LOGP, false>(a1, z, T, t, c1);
+        if (!wait()) return;  // Khat's pair
+#pragma unroll
+        for (int g = 0; g < Gl; ++g)
+#pragma unroll
+            for (int q = 0; q < Rl; ++q) {
+                const float4 k = sin[t + (g + q * Gl) * NT];
+                a0[g + q * Gl] = cmul(c0[g][q], make_float2(k.x, k.y));
+                a1[g + q * Gl] = cmul(c1[g][q], make_float2(k.z, k.w));
+            }
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (t == 0) {
+            if (pair + (int)gridDim.x < npairs) issue(&imap, nb_in, pair + gridDim.x);
+            bulk_wait_read<0>();  // the previous pair's stores have read the out buffer
+        }
+        // (the barrier at the start of each transform orders that wait before the writes below)
+        pt_row<LOGP, true>(a0, z, T, t, c0);
+#pragma unroll
+        for (int g = 0; g < Gl; ++g)
+#pragma unroll
+            for (int q = 0; q < Rl; ++q) {
+                const int r = (t + (g + q * Gl) * NT - a_lo) & (NP - 1);
+                if (r < n_aout) reinterpret_cast<float2 *>(sout + r)[0] = c0[g][q];
+            }
+        pt_row<LOGP, true>(a1, z, T, t, c1);
+#pragma unroll
+        for (int g = 0; g < Gl; ++g)
+#pragma unroll
+            for (int q = 0; q < Rl; ++q) {
+                const int r = (t + (g + q * Gl) * NT - a_lo) & (NP - 1);
+                if (r < n_aout) reinterpret_cast<float2 *>(sout + r)[1] = c1[g][q];
+            }
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (t == 0) {
+            for (int k = 0; k < nb_out; ++k) tma_store_2d(&omap, 4 * pair, k * BR, smem_u32(sout + k * BR));
+            bulk_commit();
+        }
+    }
+    if (t == 0) bulk_wait_all();
+}
+
 // Inverse transform along rho of output rows (2b, 2b+1) < n_rows (both real, packed as
 // T_a + i T_b); outputs c_lo .. c_lo + n_out - 1 go to B.
 template <int E>
@@ -304,8 +425,32 @@ bp_status rows_fwd_lpp(bp_plan *p, const Tin *sino, int q, int kernel_src, cudaS
     return BP_OK;
 }
 
+template <int LOGP>
+bp_status cols_lpp_pt(bp_plan *p, cudaStream_t st) {
+    LppWork &w = p->lpp;
+    constexpr size_t smem = lpp_cols_pt_smem<LOGP>();
+    auto kern = lpp_cols_pt_kernel<LOGP>;
+    BP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    BP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, (1 << LOGP) / kPassE, smem));
+    const int ctas = std::min(w.Lr / 2, std::max(1, per_sm) * std::max(1, p->sm_count));
+    kern<<<ctas, (1 << LOGP) / kPassE, smem, st>>>(w.Tin_map, w.Tout_map, w.K_map, w.twPassLp, w.Lr, w.K, w.a_lo,
+                                                    w.n_aout, std::min(256, w.Lp), p->d_err);
+    BP_CUDA_TRY(cudaGetLastError());
+    return BP_OK;
+}
+
 bp_status cols_lpp(bp_plan *p, int prep, float scale, cudaStream_t st) {
     LppWork &w = p->lpp;
+    if (!prep && w.maps_ok && w.twPassLp) {
+        switch (ilog2(w.Lp)) {
+            case 9: return cols_lpp_pt<9>(p, st);
+            case 10: return cols_lpp_pt<10>(p, st);
+            case 11: return cols_lpp_pt<11>(p, st);
+            case 12: return cols_lpp_pt<12>(p, st);
+            default: break;
+        }
+    }
     const int C = cols_per_cta_lpp(w.Lp);
     const size_t smem = sizeof(float2) * ((size_t)C * w.Lp + w.Lp / 2);
     auto kern = fft_elems(w.Lp) == 16 ? lpp_cols_kernel<16> : lpp_cols_kernel<8>;
@@ -428,6 +573,12 @@ bp_status ensure_lpp(bp_plan *p, int Q, float a_r, cudaStream_t st) {
     alloc((void **)&w.kfrac, sizeof(float2) * kfrac.size());
     alloc((void **)&w.twLr, sizeof(float2) * twr.size());
     alloc((void **)&w.twLp, sizeof(float2) * twp.size());
+    std::vector<float2> twpp;  // per-pass twiddles of the Lp-point transform (the persistent column pass)
+    if (w.Lp >= 512 && w.Lp <= 4096) {
+        build_pass_twiddles(ilog2(w.Lp), twpp);
+        twpp.resize((twpp.size() + 1) & ~(size_t)1);
+        alloc((void **)&w.twPassLp, sizeof(float2) * twpp.size());
+    }
     alloc((void **)&w.T, sizeof(float2) * (size_t)w.Lp * w.Lr);
     alloc((void **)&w.Khat, sizeof(float2) * (size_t)w.Lp * w.Lr);
     alloc((void **)&w.B, sizeof(float) * (size_t)(n_aout + 1) * w.n_out);
@@ -441,9 +592,26 @@ bp_status ensure_lpp(bp_plan *p, int Q, float a_r, cudaStream_t st) {
     up(w.kfrac, kfrac.data(), sizeof(float2) * kfrac.size());
     up(w.twLr, twr.data(), sizeof(float2) * twr.size());
     up(w.twLp, twp.data(), sizeof(float2) * twp.size());
+    if (!twpp.empty()) up(w.twPassLp, twpp.data(), sizeof(float2) * twpp.size());
     if (e != cudaSuccess) {
         free_logpolar_partial(p);
         return cuda_fail(e, "partial log-polar workspace");
+    }
+    // T (its first K rows as input, its first n_aout rows as output) and Khat as FP32
+    // [rows][2 Lr] for the column pass's TMA copies (one column pair per box)
+    w.maps_ok = false;
+    if (PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder()) {
+        const cuuint64_t gstride[1] = {(cuuint64_t)w.Lr * sizeof(float2)};
+        const cuuint32_t box[2] = {4, (cuuint32_t)std::min(256, w.Lp)};
+        const cuuint32_t estr[2] = {1, 1};
+        auto encode = [&](CUtensorMap *m, void *base, int rows) {
+            const cuuint64_t gdim[2] = {(cuuint64_t)2 * w.Lr, (cuuint64_t)rows};
+            return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, gdim, gstride, box, estr,
+                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+        };
+        w.maps_ok = n_aout <= w.Lp && K <= w.Lp && encode(&w.Tin_map, w.T, K) && encode(&w.Tout_map, w.T, n_aout) &&
+                    encode(&w.K_map, w.Khat, w.Lp);
     }
     PixGeom G{dx, d, rho0, drho, dphi, N, K, c_lo, a_lo, (int)n_out, n_aout, Q};
     const long long total = (long long)NN * Q;
@@ -469,6 +637,7 @@ void free_logpolar_partial(bp_plan *p) {
     cudaFree(w.kfrac);
     cudaFree(w.twLr);
     cudaFree(w.twLp);
+    cudaFree(w.twPassLp);
     cudaFree(w.T);
     cudaFree(w.Khat);
     cudaFree(w.B);
