@@ -90,6 +90,7 @@ struct LogPolarWork {
     int4 *pix = nullptr;       // [N*N] pixel -> (rho node, fraction, theta node, fraction)
     float2 *twL = nullptr, *twPhi = nullptr;
     float2 *twPassPhi = nullptr;  // per-pass twiddles of the n_phi-point transform (n_phi = 512 .. 4096)
+    float2 *twPassH = nullptr;    // per-pass twiddles of the L/2-point transform (L/2 = 512 .. 8192)
     float2 *T = nullptr;       // [n_phi][L] complex work array
     float2 *Khat = nullptr;    // [n_phi][L] kernel transform (scaled)
     float *B = nullptr;        // [n_phi][n_out] backprojection on the log-polar mesh

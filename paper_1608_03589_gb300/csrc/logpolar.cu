@@ -300,6 +300,156 @@ lp_rows_inv_kernel(const float2 *__restrict__ T, float *__restrict__ B, const fl
     }
 }
 
+// Persistent forms of the two row passes for L = 2^(LOGH + 1), LOGH = 9 .. 13: a length-L
+// transform is two register-first length-H transforms (H = L/2, per-pass twiddles in shared
+// memory, as the Fourier passes) of the even and odd samples, combined by one radix-2 step in
+// registers (decimation in time: X[k] = E[k] + w^k O[k], X[k + H] = E[k] - w^k O[k],
+// w = exp(-+2 pi i / L)); a thread's E outputs wait in shared memory while O is transformed.
+template <int LOGH>
+__host__ __device__ constexpr int lp_rows_pt_tw_off() {
+    return ((1 << LOGH) + 15) & ~15;  // after the work array
+}
+template <int LOGH>
+constexpr size_t lp_rows_pt_smem() {
+    // work array, per-pass twiddles (even-padded), held E outputs
+    return sizeof(float2) * ((size_t)lp_rows_pt_tw_off<LOGH>() + ((pt_offset<LOGH>(PtPlan<LOGH>::npass) + 1) & ~1) +
+                             (size_t)(1 << LOGH));
+}
+
+template <int LOGH>
+__device__ __forceinline__ void lp_stage_pass_twiddles(float2 *Tw, const float2 *__restrict__ twp, int t) {
+    constexpr int NT = (1 << LOGH) / kPassE, n4t = (pt_offset<LOGH>(PtPlan<LOGH>::npass) + 1) / 2;
+    const float4 *ts = reinterpret_cast<const float4 *>(twp);
+    float4 *td = reinterpret_cast<float4 *>(Tw);
+    for (int i = t; i < n4t; i += NT) td[i] = __ldg(ts + i);
+}
+
+// Forward along rho of row pairs (2b, 2b + 1), persistent: the log-polar samples of the two
+// rows (packed as one complex row, zero from n_rho on) go straight to registers, and the
+// two real rows' spectra are separated through the work array in two halves.
+template <typename Tin, int LOGH>
+__global__ void __launch_bounds__((1 << LOGH) / kPassE, 1)
+lp_rows_fwd_pt_kernel(const Tin *__restrict__ sino, int n_det, const int4 *__restrict__ atab,
+                      const int4 *__restrict__ rtab, int n_rho, int n_rows, float2 *__restrict__ Tout,
+                      const float2 *__restrict__ twp, const float2 *__restrict__ twL) {
+    using PL = PtPlan<LOGH>;
+    constexpr int H = 1 << LOGH, L = 2 * H, NT = H / kPassE, Rl = PL::Rl, Gl = kPassE / Rl;
+    extern __shared__ __align__(128) float2 z[];  // [H] work | per-pass twiddles | [H] E outputs
+    float2 *Tw = z + lp_rows_pt_tw_off<LOGH>();
+    float2 *sE = Tw + ((pt_offset<LOGH>(PL::npass) + 1) & ~1);
+    const int t = threadIdx.x;
+    lp_stage_pass_twiddles<LOGH>(Tw, twp, t);
+    for (int pr = blockIdx.x; 2 * pr < n_rows; pr += gridDim.x) {
+        const int q0 = 2 * pr, q1 = q0 + 1;
+        const int4 a0 = __ldg(atab + q0), a1 = __ldg(atab + q1);
+        float2 ae[kPassE], ao[kPassE];
+#pragma unroll
+        for (int r = 0; r < kPassE; ++r) {
+            const int i = 2 * (t + r * NT);  // even sample i, odd sample i + 1
+            ae[r] = i < n_rho ? make_float2(lp_sample(sino, n_det, a0, rtab, i), lp_sample(sino, n_det, a1, rtab, i))
+                              : make_float2(0.f, 0.f);
+            ao[r] = i + 1 < n_rho
+                        ? make_float2(lp_sample(sino, n_det, a0, rtab, i + 1), lp_sample(sino, n_det, a1, rtab, i + 1))
+                        : make_float2(0.f, 0.f);
+        }
+        float2 c[Gl][Rl];
+        pt_row<LOGH, false>(ae, z, Tw, t, c);
+#pragma unroll
+        for (int g = 0; g < Gl; ++g)
+#pragma unroll
+            for (int q = 0; q < Rl; ++q) sE[t + (g + q * Gl) * NT] = c[g][q];
+        pt_row<LOGH, false>(ao, z, Tw, t, c);
+        // X[k] (lower half) and X[k + H] (upper) for this thread's k = t + m NT
+        float2 xl[kPassE], xu[kPassE];
+#pragma unroll
+        for (int g = 0; g < Gl; ++g)
+#pragma unroll
+            for (int q = 0; q < Rl; ++q) {
+                const int m = g + q * Gl, k = t + m * NT;
+                const float2 e = sE[k], o = cmul(c[g][q], __ldg(twL + k));
+                xl[m] = make_float2(e.x + o.x, e.y + o.y);
+                xu[m] = make_float2(e.x - o.x, e.y - o.y);
+            }
+        // separation: A[k] = (X[k] + conj X[L - k]) / 2, B[k] = (X[k] - conj X[L - k]) / (2i)
+        float2 *ta = Tout + (long long)q0 * L, *tb = Tout + (long long)q1 * L;
+        __syncthreads();  // every thread is done with z (the second transform)
+#pragma unroll
+        for (int m = 0; m < kPassE; ++m) z[t + m * NT] = xu[m];
+        __syncthreads();
+#pragma unroll
+        for (int m = 0; m < kPassE; ++m) {  // lower k: X[L - k] = X[H + (H - k)] (k > 0), X[0] for k = 0
+            const int k = t + m * NT;
+            const float2 zm = xl[m], zc = k == 0 ? xl[m] : z[H - k];
+            ta[k] = make_float2(0.5f * (zm.x + zc.x), 0.5f * (zm.y - zc.y));
+            tb[k] = make_float2(0.5f * (zm.y + zc.y), -0.5f * (zm.x - zc.x));
+        }
+        __syncthreads();
+#pragma unroll
+        for (int m = 0; m < kPassE; ++m) z[t + m * NT] = xl[m];
+        __syncthreads();
+#pragma unroll
+        for (int m = 0; m < kPassE; ++m) {  // upper k' = H + k: X[L - k'] = X[H - k] (lower; X[H] itself for k = 0)
+            const int k = t + m * NT;
+            const float2 zm = xu[m], zc = k == 0 ? xu[m] : z[H - k];
+            ta[H + k] = make_float2(0.5f * (zm.x + zc.x), 0.5f * (zm.y - zc.y));
+            tb[H + k] = make_float2(0.5f * (zm.y + zc.y), -0.5f * (zm.x - zc.x));
+        }
+    }
+}
+
+// Inverse along rho of row pairs (2b, 2b + 1), persistent: Z = T_a + i T_b split into even and
+// odd entries at the load (16-byte pairs), the first n_out outputs of each real row to B.
+template <int LOGH>
+__global__ void __launch_bounds__((1 << LOGH) / kPassE, 1)
+lp_rows_inv_pt_kernel(const float2 *__restrict__ Tin, float *__restrict__ B, const float2 *__restrict__ twp,
+                      const float2 *__restrict__ twL, int n_rows, int n_out) {
+    using PL = PtPlan<LOGH>;
+    constexpr int H = 1 << LOGH, L = 2 * H, NT = H / kPassE, Rl = PL::Rl, Gl = kPassE / Rl;
+    extern __shared__ __align__(128) float2 z[];  // [H] work | per-pass twiddles | [H] E outputs
+    float2 *Tw = z + lp_rows_pt_tw_off<LOGH>();
+    float2 *sE = Tw + ((pt_offset<LOGH>(PL::npass) + 1) & ~1);
+    const int t = threadIdx.x;
+    lp_stage_pass_twiddles<LOGH>(Tw, twp, t);
+    for (int pr = blockIdx.x; 2 * pr < n_rows; pr += gridDim.x) {
+        const int q0 = 2 * pr, q1 = q0 + 1;
+        const float4 *ta = reinterpret_cast<const float4 *>(Tin + (long long)q0 * L);
+        const float4 *tb = reinterpret_cast<const float4 *>(Tin + (long long)q1 * L);
+        float2 ae[kPassE], ao[kPassE];
+#pragma unroll
+        for (int r = 0; r < kPassE; ++r) {
+            const int j = t + r * NT;  // entries 2j, 2j + 1 of both rows
+            const float4 va = __ldg(ta + j), vb = __ldg(tb + j);
+            ae[r] = make_float2(va.x - vb.y, va.y + vb.x);
+            ao[r] = make_float2(va.z - vb.w, va.w + vb.z);
+        }
+        float2 c[Gl][Rl];
+        pt_row<LOGH, true>(ae, z, Tw, t, c);
+#pragma unroll
+        for (int g = 0; g < Gl; ++g)
+#pragma unroll
+            for (int q = 0; q < Rl; ++q) sE[t + (g + q * Gl) * NT] = c[g][q];
+        pt_row<LOGH, true>(ao, z, Tw, t, c);
+        float *b0 = B + (long long)q0 * n_out, *b1 = B + (long long)q1 * n_out;
+#pragma unroll
+        for (int g = 0; g < Gl; ++g)
+#pragma unroll
+            for (int q = 0; q < Rl; ++q) {
+                const int n = t + (g + q * Gl) * NT;
+                float2 w = __ldg(twL + n);
+                w.y = -w.y;  // exp(+2 pi i n / L)
+                const float2 e = sE[n], o = cmul(c[g][q], w);
+                if (n < n_out) {
+                    b0[n] = e.x + o.x;
+                    b1[n] = e.y + o.y;
+                }
+                if (n + H < n_out) {
+                    b0[n + H] = e.x - o.x;
+                    b1[n + H] = e.y - o.y;
+                }
+            }
+    }
+}
+
 // Step 4: pixel p takes B at its (rho node + fraction, theta node + fraction).
 __global__ void __launch_bounds__(256)
 lp_cart_kernel(const float *__restrict__ B, const int4 *__restrict__ pix, float *__restrict__ img, int NN, int n_phi,
@@ -337,9 +487,48 @@ int pow2_at_least(long long n) {
     return p;
 }
 
+template <typename Tin, int LOGH>
+bp_status rows_fwd_pt(bp_plan *p, const Tin *sino, cudaStream_t st) {
+    LogPolarWork &w = p->lp;
+    constexpr size_t smem = lp_rows_pt_smem<LOGH>();
+    auto kern = lp_rows_fwd_pt_kernel<Tin, LOGH>;
+    BP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    BP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, (1 << LOGH) / kPassE, smem));
+    const int ctas = std::min(w.n_phi / 2, std::max(1, per_sm) * std::max(1, p->sm_count));
+    kern<<<ctas, (1 << LOGH) / kPassE, smem, st>>>(sino, p->n_det, w.atab, w.rtab, w.n_rho, w.n_phi, w.T, w.twPassH,
+                                                    w.twL);
+    BP_CUDA_TRY(cudaGetLastError());
+    return BP_OK;
+}
+
+template <int LOGH>
+bp_status rows_inv_pt(bp_plan *p, cudaStream_t st) {
+    LogPolarWork &w = p->lp;
+    constexpr size_t smem = lp_rows_pt_smem<LOGH>();
+    auto kern = lp_rows_inv_pt_kernel<LOGH>;
+    BP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    BP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, (1 << LOGH) / kPassE, smem));
+    const int ctas = std::min(w.n_phi / 2, std::max(1, per_sm) * std::max(1, p->sm_count));
+    kern<<<ctas, (1 << LOGH) / kPassE, smem, st>>>(w.T, w.B, w.twPassH, w.twL, w.n_phi, w.n_out);
+    BP_CUDA_TRY(cudaGetLastError());
+    return BP_OK;
+}
+
 template <typename Tin>
 bp_status rows_fwd(bp_plan *p, const Tin *sino, int kernel_src, cudaStream_t st) {
     LogPolarWork &w = p->lp;
+    if (!kernel_src && w.twPassH) {
+        switch (ilog2(w.L) - 1) {
+            case 9: return rows_fwd_pt<Tin, 9>(p, sino, st);
+            case 10: return rows_fwd_pt<Tin, 10>(p, sino, st);
+            case 11: return rows_fwd_pt<Tin, 11>(p, sino, st);
+            case 12: return rows_fwd_pt<Tin, 12>(p, sino, st);
+            case 13: return rows_fwd_pt<Tin, 13>(p, sino, st);
+            default: break;
+        }
+    }
     const size_t smem = sizeof(float2) * ((size_t)w.L + w.L / 2);
     auto kern = fft_elems(w.L) == 16 ? lp_rows_fwd_kernel<Tin, 16> : lp_rows_fwd_kernel<Tin, 8>;
     BP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -526,6 +715,12 @@ bp_status ensure_logpolar(bp_plan *p, cudaStream_t st) {
     alloc((void **)&w.pix, sizeof(int4) * pix.size());
     alloc((void **)&w.twL, sizeof(float2) * twL.size());
     alloc((void **)&w.twPhi, sizeof(float2) * twP.size());
+    std::vector<float2> twph;  // per-pass twiddles of the L/2-point transform (the persistent row passes)
+    if (L / 2 >= 512 && L / 2 <= 8192) {
+        build_pass_twiddles(ilog2(L / 2), twph);
+        twph.resize((twph.size() + 1) & ~(size_t)1);
+        alloc((void **)&w.twPassH, sizeof(float2) * twph.size());
+    }
     std::vector<float2> twpp;  // per-pass twiddles of the n_phi-point transform (the persistent column pass)
     if (n_phi >= 512 && n_phi <= 4096) {
         build_pass_twiddles(ilog2(n_phi), twpp);
@@ -545,6 +740,7 @@ bp_status ensure_logpolar(bp_plan *p, cudaStream_t st) {
     up(w.twL, twL.data(), sizeof(float2) * twL.size());
     up(w.twPhi, twP.data(), sizeof(float2) * twP.size());
     if (!twpp.empty()) up(w.twPassPhi, twpp.data(), sizeof(float2) * twpp.size());
+    if (!twph.empty()) up(w.twPassH, twph.data(), sizeof(float2) * twph.size());
     if (e != cudaSuccess) {
         free_logpolar(p);
         return cuda_fail(e, "log-polar workspace");
@@ -584,6 +780,7 @@ void free_logpolar(bp_plan *p) {
     cudaFree(w.twL);
     cudaFree(w.twPhi);
     cudaFree(w.twPassPhi);
+    cudaFree(w.twPassH);
     cudaFree(w.T);
     cudaFree(w.Khat);
     cudaFree(w.B);
@@ -611,7 +808,15 @@ bp_status launch_logpolar(bp_plan *p, const void *sino, bp_dtype dt, float *img,
         stage_mark(p, st, "lp_rows_fwd_kernel");
         if ((s = cols(p, 0, 1.f, st)) != BP_OK) return s;
         stage_mark(p, st, "lp_cols_kernel");
-        kinv<<<w.n_phi / 2, fft_threads(w.L), smemL, st>>>(w.T, w.B, w.twL, ilog2(w.L), w.n_out);
+        switch (w.twPassH ? ilog2(w.L) - 1 : 0) {
+            case 9: s = rows_inv_pt<9>(p, st); break;
+            case 10: s = rows_inv_pt<10>(p, st); break;
+            case 11: s = rows_inv_pt<11>(p, st); break;
+            case 12: s = rows_inv_pt<12>(p, st); break;
+            case 13: s = rows_inv_pt<13>(p, st); break;
+            default: kinv<<<w.n_phi / 2, fft_threads(w.L), smemL, st>>>(w.T, w.B, w.twL, ilog2(w.L), w.n_out);
+        }
+        if (s != BP_OK) return s;
         stage_mark(p, st, "lp_rows_inv_kernel");
         float *ib = img + (size_t)b * N * N;
         const int NN = N * N;
