@@ -111,6 +111,7 @@ struct LppWork {
     float2 *kfrac = nullptr;   // [Lp] kernel node and fraction per angular-transform row
     float2 *twLr = nullptr, *twLp = nullptr;
     float2 *twPassLp = nullptr;  // per-pass twiddles of the Lp-point transform (Lp = 512 .. 4096)
+    float2 *twPassH = nullptr;   // per-pass twiddles of the Lr/2-point transform (Lr/2 = 512 .. 8192)
     CUtensorMap Tin_map, Tout_map, K_map;  // T (first K rows, first n_aout rows) and Khat as FP32 [rows][2 Lr]
     bool maps_ok = false;
     float2 *T = nullptr;       // [Lp][Lr] complex work array

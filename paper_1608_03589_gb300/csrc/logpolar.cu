@@ -30,6 +30,7 @@
 #include "common.cuh"
 #include "fft.cuh"
 #include "fft_pt.cuh"
+#include "lp_rows.cuh"
 #include "tma.cuh"
 
 namespace bp {
@@ -300,43 +301,18 @@ lp_rows_inv_kernel(const float2 *__restrict__ T, float *__restrict__ B, const fl
     }
 }
 
-// Persistent forms of the two row passes for L = 2^(LOGH + 1), LOGH = 9 .. 13: a length-L
-// transform is two register-first length-H transforms (H = L/2, per-pass twiddles in shared
-// memory, as the Fourier passes) of the even and odd samples, combined by one radix-2 step in
-// registers (decimation in time: X[k] = E[k] + w^k O[k], X[k + H] = E[k] - w^k O[k],
-// w = exp(-+2 pi i / L)); a thread's E outputs wait in shared memory while O is transformed.
-template <int LOGH>
-__host__ __device__ constexpr int lp_rows_pt_tw_off() {
-    return ((1 << LOGH) + 15) & ~15;  // after the work array
-}
-template <int LOGH>
-constexpr size_t lp_rows_pt_smem() {
-    // work array, per-pass twiddles (even-padded), held E outputs
-    return sizeof(float2) * ((size_t)lp_rows_pt_tw_off<LOGH>() + ((pt_offset<LOGH>(PtPlan<LOGH>::npass) + 1) & ~1) +
-                             (size_t)(1 << LOGH));
-}
-
-template <int LOGH>
-__device__ __forceinline__ void lp_stage_pass_twiddles(float2 *Tw, const float2 *__restrict__ twp, int t) {
-    constexpr int NT = (1 << LOGH) / kPassE, n4t = (pt_offset<LOGH>(PtPlan<LOGH>::npass) + 1) / 2;
-    const float4 *ts = reinterpret_cast<const float4 *>(twp);
-    float4 *td = reinterpret_cast<float4 *>(Tw);
-    for (int i = t; i < n4t; i += NT) td[i] = __ldg(ts + i);
-}
-
-// Forward along rho of row pairs (2b, 2b + 1), persistent: the log-polar samples of the two
-// rows (packed as one complex row, zero from n_rho on) go straight to registers, and the
-// two real rows' spectra are separated through the work array in two halves.
+// Persistent forms of the two row passes for L = 2^(LOGH + 1), LOGH = 9 .. 13 (lp_rows.cuh).
+// Forward along rho of row pairs (2b, 2b + 1): the log-polar samples of the two rows (packed as
+// one complex row, zero from n_rho on) go straight to registers.
 template <typename Tin, int LOGH>
 __global__ void __launch_bounds__((1 << LOGH) / kPassE, 1)
 lp_rows_fwd_pt_kernel(const Tin *__restrict__ sino, int n_det, const int4 *__restrict__ atab,
                       const int4 *__restrict__ rtab, int n_rho, int n_rows, float2 *__restrict__ Tout,
                       const float2 *__restrict__ twp, const float2 *__restrict__ twL) {
-    using PL = PtPlan<LOGH>;
-    constexpr int H = 1 << LOGH, L = 2 * H, NT = H / kPassE, Rl = PL::Rl, Gl = kPassE / Rl;
+    constexpr int H = 1 << LOGH, L = 2 * H, NT = H / kPassE;
     extern __shared__ __align__(128) float2 z[];  // [H] work | per-pass twiddles | [H] E outputs
     float2 *Tw = z + lp_rows_pt_tw_off<LOGH>();
-    float2 *sE = Tw + ((pt_offset<LOGH>(PL::npass) + 1) & ~1);
+    float2 *sE = Tw + lp_rows_pt_twn<LOGH>();
     const int t = threadIdx.x;
     lp_stage_pass_twiddles<LOGH>(Tw, twp, t);
     for (int pr = blockIdx.x; 2 * pr < n_rows; pr += gridDim.x) {
@@ -352,62 +328,22 @@ lp_rows_fwd_pt_kernel(const Tin *__restrict__ sino, int n_det, const int4 *__res
                         ? make_float2(lp_sample(sino, n_det, a0, rtab, i + 1), lp_sample(sino, n_det, a1, rtab, i + 1))
                         : make_float2(0.f, 0.f);
         }
-        float2 c[Gl][Rl];
-        pt_row<LOGH, false>(ae, z, Tw, t, c);
-#pragma unroll
-        for (int g = 0; g < Gl; ++g)
-#pragma unroll
-            for (int q = 0; q < Rl; ++q) sE[t + (g + q * Gl) * NT] = c[g][q];
-        pt_row<LOGH, false>(ao, z, Tw, t, c);
-        // X[k] (lower half) and X[k + H] (upper) for this thread's k = t + m NT
         float2 xl[kPassE], xu[kPassE];
-#pragma unroll
-        for (int g = 0; g < Gl; ++g)
-#pragma unroll
-            for (int q = 0; q < Rl; ++q) {
-                const int m = g + q * Gl, k = t + m * NT;
-                const float2 e = sE[k], o = cmul(c[g][q], __ldg(twL + k));
-                xl[m] = make_float2(e.x + o.x, e.y + o.y);
-                xu[m] = make_float2(e.x - o.x, e.y - o.y);
-            }
-        // separation: A[k] = (X[k] + conj X[L - k]) / 2, B[k] = (X[k] - conj X[L - k]) / (2i)
-        float2 *ta = Tout + (long long)q0 * L, *tb = Tout + (long long)q1 * L;
-        __syncthreads();  // every thread is done with z (the second transform)
-#pragma unroll
-        for (int m = 0; m < kPassE; ++m) z[t + m * NT] = xu[m];
-        __syncthreads();
-#pragma unroll
-        for (int m = 0; m < kPassE; ++m) {  // lower k: X[L - k] = X[H + (H - k)] (k > 0), X[0] for k = 0
-            const int k = t + m * NT;
-            const float2 zm = xl[m], zc = k == 0 ? xl[m] : z[H - k];
-            ta[k] = make_float2(0.5f * (zm.x + zc.x), 0.5f * (zm.y - zc.y));
-            tb[k] = make_float2(0.5f * (zm.y + zc.y), -0.5f * (zm.x - zc.x));
-        }
-        __syncthreads();
-#pragma unroll
-        for (int m = 0; m < kPassE; ++m) z[t + m * NT] = xl[m];
-        __syncthreads();
-#pragma unroll
-        for (int m = 0; m < kPassE; ++m) {  // upper k' = H + k: X[L - k'] = X[H - k] (lower; X[H] itself for k = 0)
-            const int k = t + m * NT;
-            const float2 zm = xu[m], zc = k == 0 ? xu[m] : z[H - k];
-            ta[H + k] = make_float2(0.5f * (zm.x + zc.x), 0.5f * (zm.y - zc.y));
-            tb[H + k] = make_float2(0.5f * (zm.y + zc.y), -0.5f * (zm.x - zc.x));
-        }
+        lp_dit_row<LOGH, false>(ae, ao, z, Tw, sE, twL, t, xl, xu);
+        lp_separate_store<LOGH>(xl, xu, z, t, Tout + (long long)q0 * L, Tout + (long long)q1 * L);
     }
 }
 
-// Inverse along rho of row pairs (2b, 2b + 1), persistent: Z = T_a + i T_b split into even and
-// odd entries at the load (16-byte pairs), the first n_out outputs of each real row to B.
+// Inverse along rho of row pairs (2b, 2b + 1): Z = T_a + i T_b split into even and odd entries
+// at the load (16-byte pairs), the first n_out outputs of each real row to B.
 template <int LOGH>
 __global__ void __launch_bounds__((1 << LOGH) / kPassE, 1)
 lp_rows_inv_pt_kernel(const float2 *__restrict__ Tin, float *__restrict__ B, const float2 *__restrict__ twp,
                       const float2 *__restrict__ twL, int n_rows, int n_out) {
-    using PL = PtPlan<LOGH>;
-    constexpr int H = 1 << LOGH, L = 2 * H, NT = H / kPassE, Rl = PL::Rl, Gl = kPassE / Rl;
+    constexpr int H = 1 << LOGH, L = 2 * H, NT = H / kPassE;
     extern __shared__ __align__(128) float2 z[];  // [H] work | per-pass twiddles | [H] E outputs
     float2 *Tw = z + lp_rows_pt_tw_off<LOGH>();
-    float2 *sE = Tw + ((pt_offset<LOGH>(PL::npass) + 1) & ~1);
+    float2 *sE = Tw + lp_rows_pt_twn<LOGH>();
     const int t = threadIdx.x;
     lp_stage_pass_twiddles<LOGH>(Tw, twp, t);
     for (int pr = blockIdx.x; 2 * pr < n_rows; pr += gridDim.x) {
@@ -422,31 +358,21 @@ lp_rows_inv_pt_kernel(const float2 *__restrict__ Tin, float *__restrict__ B, con
             ae[r] = make_float2(va.x - vb.y, va.y + vb.x);
             ao[r] = make_float2(va.z - vb.w, va.w + vb.z);
         }
-        float2 c[Gl][Rl];
-        pt_row<LOGH, true>(ae, z, Tw, t, c);
-#pragma unroll
-        for (int g = 0; g < Gl; ++g)
-#pragma unroll
-            for (int q = 0; q < Rl; ++q) sE[t + (g + q * Gl) * NT] = c[g][q];
-        pt_row<LOGH, true>(ao, z, Tw, t, c);
+        float2 xl[kPassE], xu[kPassE];
+        lp_dit_row<LOGH, true>(ae, ao, z, Tw, sE, twL, t, xl, xu);
         float *b0 = B + (long long)q0 * n_out, *b1 = B + (long long)q1 * n_out;
 #pragma unroll
-        for (int g = 0; g < Gl; ++g)
-#pragma unroll
-            for (int q = 0; q < Rl; ++q) {
-                const int n = t + (g + q * Gl) * NT;
-                float2 w = __ldg(twL + n);
-                w.y = -w.y;  // exp(+2 pi i n / L)
-                const float2 e = sE[n], o = cmul(c[g][q], w);
-                if (n < n_out) {
-                    b0[n] = e.x + o.x;
-                    b1[n] = e.y + o.y;
-                }
-                if (n + H < n_out) {
-                    b0[n + H] = e.x - o.x;
-                    b1[n + H] = e.y - o.y;
-                }
+        for (int m = 0; m < kPassE; ++m) {
+            const int n = t + m * NT;
+            if (n < n_out) {
+                b0[n] = xl[m].x;
+                b1[n] = xl[m].y;
             }
+            if (n + H < n_out) {
+                b0[n + H] = xu[m].x;
+                b1[n + H] = xu[m].y;
+            }
+        }
     }
 }
 

@@ -28,6 +28,7 @@
 #include "common.cuh"
 #include "fft.cuh"
 #include "fft_pt.cuh"
+#include "lp_rows.cuh"
 #include "tma.cuh"
 
 namespace bp {
@@ -308,6 +309,91 @@ lpp_cols_pt_kernel(const __grid_constant__ CUtensorMap imap, const __grid_consta
     if (t == 0) bulk_wait_all();
 }
 
+// Persistent forms of the two row passes for Lr = 2^(LOGH + 1), LOGH = 9 .. 13 (lp_rows.cuh).
+// Forward along rho of rows (2b, 2b + 1) < n_rows: the sector's Step 1 samples go straight to
+// registers (the second row is zero when n_rows is odd).
+template <typename Tin, int LOGH>
+__global__ void __launch_bounds__((1 << LOGH) / kPassE, 1)
+lpp_rows_fwd_pt_kernel(const Tin *__restrict__ sino, int n_det, const int4 *__restrict__ atab,
+                       const int4 *__restrict__ rowtab, const int2 *__restrict__ stab, int n_rho, int n_rows,
+                       float2 *__restrict__ Tout, const float2 *__restrict__ twp, const float2 *__restrict__ twL) {
+    constexpr int H = 1 << LOGH, L = 2 * H, NT = H / kPassE;
+    extern __shared__ __align__(128) float2 z[];  // [H] work | per-pass twiddles | [H] E outputs
+    float2 *Tw = z + lp_rows_pt_tw_off<LOGH>();
+    float2 *sE = Tw + lp_rows_pt_twn<LOGH>();
+    const int t = threadIdx.x;
+    lp_stage_pass_twiddles<LOGH>(Tw, twp, t);
+    for (int pr = blockIdx.x; 2 * pr < n_rows; pr += gridDim.x) {
+        const int q0 = 2 * pr, q1 = q0 + 1;
+        const bool has1 = q1 < n_rows;
+        const int4 a0 = __ldg(atab + q0), r0 = __ldg(rowtab + q0);
+        const int4 a1 = has1 ? __ldg(atab + q1) : a0, r1 = has1 ? __ldg(rowtab + q1) : r0;
+        float2 ae[kPassE], ao[kPassE];
+#pragma unroll
+        for (int r = 0; r < kPassE; ++r) {
+            const int i = 2 * (t + r * NT);  // even sample i, odd sample i + 1
+            float2 ve = make_float2(0.f, 0.f), vo = ve;
+            if (i < n_rho) {
+                const int2 s = __ldg(stab + i);
+                ve.x = lpp_sample(sino, n_det, a0, r0, s);
+                if (has1) ve.y = lpp_sample(sino, n_det, a1, r1, s);
+            }
+            if (i + 1 < n_rho) {
+                const int2 s = __ldg(stab + i + 1);
+                vo.x = lpp_sample(sino, n_det, a0, r0, s);
+                if (has1) vo.y = lpp_sample(sino, n_det, a1, r1, s);
+            }
+            ae[r] = ve;
+            ao[r] = vo;
+        }
+        float2 xl[kPassE], xu[kPassE];
+        lp_dit_row<LOGH, false>(ae, ao, z, Tw, sE, twL, t, xl, xu);
+        lp_separate_store<LOGH>(xl, xu, z, t, Tout + (long long)q0 * L, has1 ? Tout + (long long)q1 * L : nullptr);
+    }
+}
+
+// Inverse along rho of output rows (2b, 2b + 1) < n_rows: outputs c_lo .. c_lo + n_out - 1 to B.
+template <int LOGH>
+__global__ void __launch_bounds__((1 << LOGH) / kPassE, 1)
+lpp_rows_inv_pt_kernel(const float2 *__restrict__ Tin, float *__restrict__ B, const float2 *__restrict__ twp,
+                       const float2 *__restrict__ twL, int n_rows, int c_lo, int n_out) {
+    constexpr int H = 1 << LOGH, L = 2 * H, NT = H / kPassE;
+    extern __shared__ __align__(128) float2 z[];  // [H] work | per-pass twiddles | [H] E outputs
+    float2 *Tw = z + lp_rows_pt_tw_off<LOGH>();
+    float2 *sE = Tw + lp_rows_pt_twn<LOGH>();
+    const int t = threadIdx.x;
+    lp_stage_pass_twiddles<LOGH>(Tw, twp, t);
+    for (int pr = blockIdx.x; 2 * pr < n_rows; pr += gridDim.x) {
+        const int q0 = 2 * pr, q1 = q0 + 1;
+        const bool has1 = q1 < n_rows;
+        const float4 *ta = reinterpret_cast<const float4 *>(Tin + (long long)q0 * L);
+        const float4 *tb = reinterpret_cast<const float4 *>(Tin + (long long)q1 * L);
+        float2 ae[kPassE], ao[kPassE];
+#pragma unroll
+        for (int r = 0; r < kPassE; ++r) {
+            const int j = t + r * NT;  // entries 2j, 2j + 1 of both rows
+            const float4 va = __ldg(ta + j), vb = has1 ? __ldg(tb + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+            ae[r] = make_float2(va.x - vb.y, va.y + vb.x);
+            ao[r] = make_float2(va.z - vb.w, va.w + vb.z);
+        }
+        float2 xl[kPassE], xu[kPassE];
+        lp_dit_row<LOGH, true>(ae, ao, z, Tw, sE, twL, t, xl, xu);
+        float *b0 = B + (long long)q0 * n_out, *b1 = B + (long long)q1 * n_out;
+#pragma unroll
+        for (int m = 0; m < kPassE; ++m) {
+            const int n = t + m * NT - c_lo, nu = n + H;
+            if (n >= 0 && n < n_out) {
+                b0[n] = xl[m].x;
+                if (has1) b1[n] = xl[m].y;
+            }
+            if (nu >= 0 && nu < n_out) {
+                b0[nu] = xu[m].x;
+                if (has1) b1[nu] = xu[m].y;
+            }
+        }
+    }
+}
+
 // Inverse transform along rho of output rows (2b, 2b+1) < n_rows (both real, packed as
 // T_a + i T_b); outputs c_lo .. c_lo + n_out - 1 go to B.
 template <int E>
@@ -411,9 +497,48 @@ void split(double v, int &k, float &f) {
 
 int cols_per_cta_lpp(int Lp) { return std::max(1, std::min(8, (int)(131072 / (sizeof(float2) * Lp)))); }
 
+template <typename Tin, int LOGH>
+bp_status rows_fwd_lpp_pt(bp_plan *p, const Tin *sino, int q, cudaStream_t st) {
+    LppWork &w = p->lpp;
+    constexpr size_t smem = lp_rows_pt_smem<LOGH>();
+    auto kern = lpp_rows_fwd_pt_kernel<Tin, LOGH>;
+    BP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    BP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, (1 << LOGH) / kPassE, smem));
+    const int ctas = std::min((w.K + 1) / 2, std::max(1, per_sm) * std::max(1, p->sm_count));
+    kern<<<ctas, (1 << LOGH) / kPassE, smem, st>>>(sino, p->n_det, w.atab + (size_t)q * w.K, w.rowtab, w.stab,
+                                                    w.n_rho, w.K, w.T, w.twPassH, w.twLr);
+    BP_CUDA_TRY(cudaGetLastError());
+    return BP_OK;
+}
+
+template <int LOGH>
+bp_status rows_inv_lpp_pt(bp_plan *p, cudaStream_t st) {
+    LppWork &w = p->lpp;
+    constexpr size_t smem = lp_rows_pt_smem<LOGH>();
+    auto kern = lpp_rows_inv_pt_kernel<LOGH>;
+    BP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    BP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, (1 << LOGH) / kPassE, smem));
+    const int ctas = std::min((w.n_aout + 1) / 2, std::max(1, per_sm) * std::max(1, p->sm_count));
+    kern<<<ctas, (1 << LOGH) / kPassE, smem, st>>>(w.T, w.B, w.twPassH, w.twLr, w.n_aout, w.c_lo, w.n_out);
+    BP_CUDA_TRY(cudaGetLastError());
+    return BP_OK;
+}
+
 template <typename Tin>
 bp_status rows_fwd_lpp(bp_plan *p, const Tin *sino, int q, int kernel_src, cudaStream_t st) {
     LppWork &w = p->lpp;
+    if (!kernel_src && w.twPassH) {
+        switch (ilog2(w.Lr) - 1) {
+            case 9: return rows_fwd_lpp_pt<Tin, 9>(p, sino, q, st);
+            case 10: return rows_fwd_lpp_pt<Tin, 10>(p, sino, q, st);
+            case 11: return rows_fwd_lpp_pt<Tin, 11>(p, sino, q, st);
+            case 12: return rows_fwd_lpp_pt<Tin, 12>(p, sino, q, st);
+            case 13: return rows_fwd_lpp_pt<Tin, 13>(p, sino, q, st);
+            default: break;
+        }
+    }
     const size_t smem = sizeof(float2) * ((size_t)w.Lr + w.Lr / 2);
     auto kern = fft_elems(w.Lr) == 16 ? lpp_rows_fwd_kernel<Tin, 16> : lpp_rows_fwd_kernel<Tin, 8>;
     BP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -573,6 +698,12 @@ bp_status ensure_lpp(bp_plan *p, int Q, float a_r, cudaStream_t st) {
     alloc((void **)&w.kfrac, sizeof(float2) * kfrac.size());
     alloc((void **)&w.twLr, sizeof(float2) * twr.size());
     alloc((void **)&w.twLp, sizeof(float2) * twp.size());
+    std::vector<float2> twph;  // per-pass twiddles of the Lr/2-point transform (the persistent row passes)
+    if (w.Lr / 2 >= 512 && w.Lr / 2 <= 8192) {
+        build_pass_twiddles(ilog2(w.Lr / 2), twph);
+        twph.resize((twph.size() + 1) & ~(size_t)1);
+        alloc((void **)&w.twPassH, sizeof(float2) * twph.size());
+    }
     std::vector<float2> twpp;  // per-pass twiddles of the Lp-point transform (the persistent column pass)
     if (w.Lp >= 512 && w.Lp <= 4096) {
         build_pass_twiddles(ilog2(w.Lp), twpp);
@@ -593,6 +724,7 @@ bp_status ensure_lpp(bp_plan *p, int Q, float a_r, cudaStream_t st) {
     up(w.twLr, twr.data(), sizeof(float2) * twr.size());
     up(w.twLp, twp.data(), sizeof(float2) * twp.size());
     if (!twpp.empty()) up(w.twPassLp, twpp.data(), sizeof(float2) * twpp.size());
+    if (!twph.empty()) up(w.twPassH, twph.data(), sizeof(float2) * twph.size());
     if (e != cudaSuccess) {
         free_logpolar_partial(p);
         return cuda_fail(e, "partial log-polar workspace");
@@ -638,6 +770,7 @@ void free_logpolar_partial(bp_plan *p) {
     cudaFree(w.twLr);
     cudaFree(w.twLp);
     cudaFree(w.twPassLp);
+    cudaFree(w.twPassH);
     cudaFree(w.T);
     cudaFree(w.Khat);
     cudaFree(w.B);
@@ -669,8 +802,17 @@ bp_status launch_logpolar_partial(bp_plan *p, const void *sino, bp_dtype dt, flo
             stage_mark(p, st, "lpp_rows_fwd_kernel");
             if ((s = cols_lpp(p, 0, 1.f, st)) != BP_OK) return s;
             stage_mark(p, st, "lpp_cols_kernel");
-            kinv<<<(w.n_aout + 1) / 2, fft_threads(w.Lr), smemL, st>>>(w.T, w.B, w.twLr, ilog2(w.Lr), w.n_aout,
-                                                                       w.c_lo, w.n_out);
+            switch (w.twPassH ? ilog2(w.Lr) - 1 : 0) {
+                case 9: s = rows_inv_lpp_pt<9>(p, st); break;
+                case 10: s = rows_inv_lpp_pt<10>(p, st); break;
+                case 11: s = rows_inv_lpp_pt<11>(p, st); break;
+                case 12: s = rows_inv_lpp_pt<12>(p, st); break;
+                case 13: s = rows_inv_lpp_pt<13>(p, st); break;
+                default:
+                    kinv<<<(w.n_aout + 1) / 2, fft_threads(w.Lr), smemL, st>>>(w.T, w.B, w.twLr, ilog2(w.Lr),
+                                                                               w.n_aout, w.c_lo, w.n_out);
+            }
+            if (s != BP_OK) return s;
             stage_mark(p, st, "lpp_rows_inv_kernel");
             lpp_cart_kernel<<<(NN + 255) / 256, 256, 0, st>>>(w.B, w.pix + (size_t)q * NN, ib, NN, w.n_out, q > 0);
             BP_CUDA_TRY(cudaGetLastError());
