@@ -27,6 +27,7 @@
 
 #include "common.cuh"
 #include "fft.cuh"
+#include "lp_rows.cuh"
 
 namespace bp {
 
@@ -83,6 +84,61 @@ bst_polar_kernel(const Tin *__restrict__ sino, float2 *__restrict__ polar, const
 // is shared by the two half-lines.  By linearity the transform of this line is the sum of the
 // two half-lines' one-sided transforms (conjugated for the opposite one), which is what
 // Step 2.2 needs on each ray, so the full-line kernels below do the rest.
+// The same polar values from a persistent kernel for Pb = 2^(LOGH + 1), LOGH = 9 .. 13: each
+// Pb-point transform of a packed projection pair as two register-first Pb/2-point transforms
+// of its even and odd samples combined in registers (lp_rows.cuh); X[Pb - m] for the two
+// rows' separation comes from the upper half through the work array.
+template <typename Tin, int LOGH>
+__global__ void __launch_bounds__((1 << LOGH) / kPassE, 1)
+bst_polar_pt_kernel(const Tin *__restrict__ sino, float2 *__restrict__ polar, const float2 *__restrict__ twp,
+                    const float2 *__restrict__ twPb, int n_theta, int n_det, float scale) {
+    constexpr int H = 1 << LOGH, P = 2 * H, NT = H / kPassE;
+    extern __shared__ __align__(128) float2 z[];  // [H] work | per-pass twiddles | [H] E outputs
+    float2 *Tw = z + lp_rows_pt_tw_off<LOGH>();
+    float2 *sE = Tw + lp_rows_pt_twn<LOGH>();
+    const int t = threadIdx.x;
+    lp_stage_pass_twiddles<LOGH>(Tw, twp, t);
+    const long long twoP = 2LL * P;
+    for (int pr = blockIdx.x; 2 * pr < n_theta; pr += gridDim.x) {
+        const int k0 = 2 * pr, k1 = k0 + 1;
+        const bool has1 = k1 < n_theta;
+        const Tin *a = sino + (long long)k0 * n_det;
+        const Tin *b = sino + (long long)k1 * n_det;
+        float2 ae[kPassE], ao[kPassE];
+#pragma unroll
+        for (int r = 0; r < kPassE; ++r) {
+            const int i = 2 * (t + r * NT);  // even sample i, odd sample i + 1
+            ae[r] = make_float2(i < n_det ? load_f(a + i) : 0.f, (has1 && i < n_det) ? load_f(b + i) : 0.f);
+            ao[r] = make_float2(i + 1 < n_det ? load_f(a + i + 1) : 0.f,
+                                (has1 && i + 1 < n_det) ? load_f(b + i + 1) : 0.f);
+        }
+        float2 xl[kPassE], xu[kPassE];
+        lp_dit_row<LOGH, false>(ae, ao, z, Tw, sE, twPb, t, xl, xu);
+        __syncthreads();  // every thread is done with z (the second transform)
+#pragma unroll
+        for (int m = 0; m < kPassE; ++m) z[t + m * NT] = xu[m];
+        __syncthreads();
+#pragma unroll
+        for (int mi = 0; mi < kPassE; ++mi) {
+            const int m = t + mi * NT;  // Z[Pb - m] = X[H + (H - m)] (m > 0), X[0] for m = 0
+            const float2 zm = xl[mi], zc = m == 0 ? xl[mi] : z[H - m];
+            const float2 A = make_float2(0.5f * (zm.x + zc.x), 0.5f * (zm.y - zc.y));
+            const float2 B = make_float2(0.5f * (zm.y + zc.y), -0.5f * (zm.x - zc.x));
+            const long long r = ((long long)m * (n_det - 1)) % twoP;  // detector-centre phase, reduced mod 2P
+            float sn, cs;
+            sincospif((float)r / (float)P, &sn, &cs);
+            const float2 ph = make_float2(cs, sn);
+            const float f = scale / (float)max(m, 1);  // K^sigma
+            const float2 ca = cmul(A, ph);
+            polar[(long long)k0 * H + m] = make_float2(f * ca.x, f * ca.y);
+            if (has1) {
+                const float2 cb = cmul(B, ph);
+                polar[(long long)k1 * H + m] = make_float2(f * cb.x, f * cb.y);
+            }
+        }
+    }
+}
+
 template <typename Tin>
 __global__ void __launch_bounds__(256)
 bst_window_rows_kernel(const Tin *__restrict__ sino, float *__restrict__ rows, const float *__restrict__ win,
@@ -203,9 +259,35 @@ bst_interp_kernel(const float2 *__restrict__ polar, const float *__restrict__ an
 }
 
 // Rows of n_det samples (n_det <= Pb) centred on t = 0.
+template <typename Tin, int LOGH>
+bp_status polar_pt(bp_plan *p, const Tin *sino, int n_det, float scale, cudaStream_t st) {
+    BstWork &w = p->bst;
+    constexpr size_t smem = lp_rows_pt_smem<LOGH>();
+    auto kern = bst_polar_pt_kernel<Tin, LOGH>;
+    BP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    BP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, (1 << LOGH) / kPassE, smem));
+    const int ctas = std::min((p->n_theta + 1) / 2, std::max(1, per_sm) * std::max(1, p->sm_count));
+    kern<<<ctas, (1 << LOGH) / kPassE, smem, st>>>(sino, w.polar, w.twPassH, w.twPb, p->n_theta, n_det, scale);
+    BP_CUDA_TRY(cudaGetLastError());
+    stage_mark(p, st, "bst_polar_kernel");
+    return BP_OK;
+}
+
 template <typename Tin>
 bp_status polar_t(bp_plan *p, const Tin *sino, int n_det, cudaStream_t st) {
     BstWork &w = p->bst;
+    if (w.twPassH) {
+        const float scale = (float)((double)w.Pb * p->dt * p->dt);
+        switch (ilog2(w.Pb) - 1) {
+            case 9: return polar_pt<Tin, 9>(p, sino, n_det, scale, st);
+            case 10: return polar_pt<Tin, 10>(p, sino, n_det, scale, st);
+            case 11: return polar_pt<Tin, 11>(p, sino, n_det, scale, st);
+            case 12: return polar_pt<Tin, 12>(p, sino, n_det, scale, st);
+            case 13: return polar_pt<Tin, 13>(p, sino, n_det, scale, st);
+            default: break;
+        }
+    }
     const int logP = ilog2(w.Pb);
     const size_t smem = sizeof(float2) * (w.Pb + w.Pb / 2);
     auto kern = fft_elems(w.Pb) == 16 ? bst_polar_kernel<Tin, 16> : bst_polar_kernel<Tin, 8>;
@@ -280,6 +362,12 @@ bp_status ensure_bst(bp_plan *p, int os) {
         if (e == cudaSuccess) e = cudaMalloc(ptr, std::max<size_t>(bytes, 16));
         if (e == cudaSuccess) w.bytes += bytes;
     };
+    std::vector<float2> twph;  // per-pass twiddles of the Pb/2-point transform (the persistent polar kernel)
+    if (H >= 512 && H <= 8192) {
+        build_pass_twiddles(ilog2(H), twph);
+        twph.resize((twph.size() + 1) & ~(size_t)1);
+        alloc((void **)&w.twPassH, sizeof(float2) * twph.size());
+    }
     alloc((void **)&w.polar, sizeof(float2) * (size_t)n * H);
     alloc((void **)&w.twPb, sizeof(float2) * tw.size());
     alloc((void **)&w.ang, sizeof(float) * R);
@@ -293,6 +381,8 @@ bp_status ensure_bst(bp_plan *p, int os) {
     if (e == cudaSuccess) e = cudaMemcpy(w.ang, ang.data(), sizeof(float) * R, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(w.ray, code.data(), sizeof(int) * R, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(w.ones, ones.data(), sizeof(float) * p->N, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !twph.empty())
+        e = cudaMemcpy(w.twPassH, twph.data(), sizeof(float2) * twph.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         free_bst(p);
         return cuda_fail(e, "BST workspace");
@@ -340,6 +430,7 @@ void free_bst(bp_plan *p) {
     cudaFree(w.win);
     cudaFree(w.polar);
     cudaFree(w.twPb);
+    cudaFree(w.twPassH);
     cudaFree(w.ang);
     cudaFree(w.ray);
     cudaFree(w.ones);

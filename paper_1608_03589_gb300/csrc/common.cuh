@@ -68,6 +68,7 @@ struct BstWork {
     int Pb = 0;                 // projection transform length
     float2 *polar = nullptr;    // [n_theta][Pb/2] polar values of the backprojection's transform
     float2 *twPb = nullptr;     // Pb/2 twiddles
+    float2 *twPassH = nullptr;  // per-pass twiddles of the Pb/2-point transform (Pb/2 = 512 .. 8192)
     float *ang = nullptr;       // [2 n_theta] ray angles theta_k, theta_k + pi in [0, 2 pi), sorted
     int *ray = nullptr;         // [2 n_theta] projection index, bit 30 set for the opposite ray
     float *ones = nullptr;      // [N] unit deapodisation
