@@ -34,6 +34,7 @@ FP32_LANES_PER_SM = 128       # FP32 FMA lanes per SM
 L2_FLUSH_BYTES = 256 << 20    # > 129 MB L2
 # sources whose content the committed DRAM-traffic record of a kernel is tied to
 _FOURIER_SOURCES = ("fourier.cu", "fft.cuh", "fft_pt.cuh", "tma.cuh", "geometry.cuh")
+_LP_SOURCES = ("logpolar.cu", "lp_rows.cuh", "fft.cuh", "fft_pt.cuh", "tma.cuh")
 KERNEL_SOURCES = {
     "bp_direct_klein_kernel": ("direct_klein.cu", "direct_tile.cuh", "tma.cuh", "f32x2.cuh", "geometry.cuh"),
     "bp_direct_quad_sync_kernel": ("direct.cu", "direct_tile.cuh", "tma.cuh", "geometry.cuh", "f32x2.cuh"),
@@ -42,6 +43,9 @@ KERNEL_SOURCES = {
     "gridding": _FOURIER_SOURCES,
     "ifft_pt_kernel (y pass)": _FOURIER_SOURCES,
     "ifft_pt_kernel (x pass)": _FOURIER_SOURCES,
+    "lp_rows_fwd_kernel": _LP_SOURCES,
+    "lp_cols_kernel": _LP_SOURCES,
+    "lp_rows_inv_kernel": _LP_SOURCES,
 }
 
 
@@ -280,11 +284,55 @@ def klein_table_entries(N: int, n_det: int, theta, dt: float) -> int:
     return int(np.floor(hi.max()) + 4 - (np.floor(lo.min()) - 4) + 1)
 
 
+def _pow2_at_least(n: int) -> int:
+    p = 1
+    while p < n:
+        p <<= 1
+    return p
+
+
+def lp_meshes(N: int, n_det: int, n_theta: int, dt: float) -> dict:
+    """Mesh sizes of the adaptive-rho_0 log-polar R* (Section 5.1-5.2; the library builds the
+    same from these formulas): rho nodes, output nodes, angle nodes and the rho transform length."""
+    dx = 2.0 / N
+    s_max = 0.5 * (n_det - 1) * dt + dt
+    rho0, top = math.log(0.5 * dx), math.log(s_max)
+    step = -math.log(1.0 - dt / s_max)
+    n_rho = math.ceil((top - rho0) / step) + 1
+    drho = (top - rho0) / (n_rho - 1)
+    r_far = math.sqrt(2.0) * (1.0 - 0.5 * dx)
+    n_out = math.ceil((math.log(max(r_far, 0.5 * dx)) - rho0) / drho) + 2
+    return {"lp_nphi": _pow2_at_least(2 * n_theta), "lp_L": _pow2_at_least(n_rho + n_out), "lp_nout": n_out}
+
+
+def lpp_meshes(N: int, n_det: int, n_theta: int, dt: float, Q: int, a_r: float) -> dict:
+    """Mesh sizes of the partial (sector) log-polar R* with Q sectors and shift ratio a_r."""
+    dx, R = 2.0 / N, math.sqrt(2.0)
+    n_half = _pow2_at_least(max(n_theta, 1))
+    K = n_half // Q
+    dphi, d = math.pi / n_half, R * (1.0 - a_r) / a_r
+    beta, alpha = 0.5 * (K - 1) * dphi, math.asin(R / d)
+    gamma = alpha + beta + 3.0 * dphi
+    step = -math.log(1.0 - dt / (d + R))
+    rho0, top = math.log((d - R) * math.cos(gamma)) - 2.0 * step, math.log(d + R)
+    n_rho = math.ceil((top - rho0) / step) + 1
+    drho = (top - rho0) / (n_rho - 1)
+    c_lo = math.floor((math.log(d - R) - rho0) / drho)
+    n_out = n_rho - c_lo
+    A = alpha / dphi
+    a_lo, a_hi = math.floor(0.5 * (K - 1) - A) - 1, math.ceil(0.5 * (K - 1) + A) + 1
+    n_aout = a_hi - a_lo + 1
+    b_lo, b_hi = a_lo - (K - 1), a_hi
+    kmax = math.floor(-math.log(math.cos(max(-b_lo, b_hi) * dphi)) / drho) + 1
+    return {"lpp_Q": Q, "lpp_K": K, "lpp_nout": n_out, "lpp_naout": n_aout,
+            "lpp_Lr": _pow2_at_least(n_rho + kmax + 1), "lpp_Lp": _pow2_at_least(max(b_hi - b_lo + 1, n_aout, K))}
+
+
 def kernel_work(name: str, c: dict):
     """Algorithmic (bytes, flops) of one launch of kernel `name` on workload c (N, n_det, n_theta,
-    esz, P, M, W; an FFT of n points counts 5 n log2 n flops, an FMA 2): the per-unit figures of
-    the measurement plan times the units one slice processes.  None when no model is kept (the
-    kernels of the paper's own BST and of the log-polar methods)."""
+    esz, P, M, W, and the BST / log-polar mesh sizes; an FFT of n points counts 5 n log2 n flops,
+    an FMA 2): the per-unit figures of the measurement plan times the units one slice (one call)
+    processes.  None when no model is kept."""
     N, nd, nt, esz = c["N"], c["n_det"], c["n_theta"], c.get("esz", 4)
     P, M, W = c.get("P", 0), c.get("M", 0), c.get("W", 6)
     upd = N * N * nt
@@ -314,6 +362,39 @@ def kernel_work(name: str, c: dict):
         return 8 * M * M + nt * (P // 2) * 8, 8 * W * W * nt * (P // 2)
     if name == "adj_rows_pt_kernel":
         return nt * (P // 2) * 8 + 4 * nt * nd, nt * (2.5 * P * lg(P) + 6 * P)
+    # the paper's BST (Pb-point polar transforms of projection pairs, bilinear polar -> Cartesian
+    # interpolation of complex values) and its windowed semi-polar rows
+    Pb = c.get("Pb", 0)
+    if name == "bst_window_rows_kernel":
+        npr = 2 * (nd // 2 + 1) - 1
+        return nt * nd * esz + 4 * nt * npr, 2 * nt * npr
+    if name == "bst_polar_kernel" and Pb:
+        return nt * nd * c.get("bst_in_esz", esz) + nt * (Pb // 2) * 8, (nt / 2) * 5 * Pb * lg(Pb)
+    if name == "bst_interp_kernel" and Pb:
+        return nt * (Pb // 2) * 8 + 8 * M * M, 16 * M * M
+    # log-polar: rho transforms of n_phi rows of length L (two real rows per complex transform),
+    # phi transforms of the L columns (forward, kernel product, inverse), Cartesian interpolation
+    nphi, Llp, nout = c.get("lp_nphi", 0), c.get("lp_L", 0), c.get("lp_nout", 0)
+    if nphi:
+        if name == "lp_rows_fwd_kernel":
+            return nt * nd * esz + 8 * nphi * Llp, (nphi / 2) * 5 * Llp * lg(Llp)
+        if name == "lp_cols_kernel":
+            return 3 * 8 * nphi * Llp, Llp * (10 * nphi * lg(nphi) + 6 * nphi)
+        if name == "lp_rows_inv_kernel":
+            return 8 * nphi * Llp + 4 * nphi * nout, (nphi / 2) * 5 * Llp * lg(Llp)
+        if name == "lp_cart_kernel":
+            return 20 * N * N + 4 * nphi * nout, 10 * N * N
+    Q = c.get("lpp_Q", 0)
+    if Q:
+        K, Lr, Lp, na, no = c["lpp_K"], c["lpp_Lr"], c["lpp_Lp"], c["lpp_naout"], c["lpp_nout"]
+        if name == "lpp_rows_fwd_kernel":
+            return nt * nd * esz + Q * 8 * K * Lr, Q * (K / 2) * 5 * Lr * lg(Lr)
+        if name == "lpp_cols_kernel":
+            return Q * 8 * Lr * (K + Lp + na), Q * Lr * (10 * Lp * lg(Lp) + 6 * Lp)
+        if name == "lpp_rows_inv_kernel":
+            return Q * (8 * na * Lr + 4 * na * no), Q * (na / 2) * 5 * Lr * lg(Lr)
+        if name == "lpp_cart_kernel":
+            return Q * 24 * N * N, Q * 10 * N * N
     return None
 
 
@@ -469,7 +550,7 @@ def other_paths(plan, q, img, flush, stream, dev, only=(), peaks=(6778.3, 80.5),
         res, imgs = {}, {}
         for os_ in (1, 4):
             ms = _timed(lambda: plan.backproject_bst(q, os_, out=img), stream, flush, 10)
-            kern = prof(plan, lambda: plan.backproject_bst(q, os_, out=img))
+            kern = prof(plan, lambda: plan.backproject_bst(q, os_, out=img), dict(ctx, Pb=4096 * os_))
             imgs[os_] = img.double().cpu().numpy()
             res[f"oversampling_{os_}"] = {"ms": ms, "equiv_Gupdates_s": wl.updates / ms / 1e6, "kernels": kern}
 
@@ -486,7 +567,8 @@ def other_paths(plan, q, img, flush, stream, dev, only=(), peaks=(6778.3, 80.5),
         res, imgs = {}, {}
         for os_ in (1, 4):
             ms = _timed(lambda: plan.backproject_bst_windowed(q, 6.0, os_, out=img), stream, flush, 10)
-            kern = prof(plan, lambda: plan.backproject_bst_windowed(q, 6.0, os_, out=img))
+            kern = prof(plan, lambda: plan.backproject_bst_windowed(q, 6.0, os_, out=img),
+                        dict(ctx, Pb=4096 * os_, bst_in_esz=4))
             imgs[os_] = img.double().cpu().numpy()
             res[f"oversampling_{os_}"] = {"ms": ms, "equiv_Gupdates_s": wl.updates / ms / 1e6, "beta": 6.0,
                                           "kernels": kern}
@@ -502,7 +584,8 @@ def other_paths(plan, q, img, flush, stream, dev, only=(), peaks=(6778.3, 80.5),
 
     def logpolar():
         ms = _timed(lambda: plan.backproject_logpolar(q, out=img), stream, flush, 5)
-        kern = prof(plan, lambda: plan.backproject_logpolar(q, out=img))
+        kern = prof(plan, lambda: plan.backproject_logpolar(q, out=img),
+                    dict(ctx, **lp_meshes(wl.N, wl.n_det, wl.n_theta, wl.det_spacing)))
         got = img.double().cpu().numpy()
 
         def chk():
@@ -516,7 +599,8 @@ def other_paths(plan, q, img, flush, stream, dev, only=(), peaks=(6778.3, 80.5),
     def logpolar_partial():
         plan.backproject_logpolar_partial(q, 8, 0.25, out=img)  # workspace and pixel tables (untimed)
         ms = _timed(lambda: plan.backproject_logpolar_partial(q, 8, 0.25, out=img), stream, flush, 5)
-        kern = prof(plan, lambda: plan.backproject_logpolar_partial(q, 8, 0.25, out=img))
+        kern = prof(plan, lambda: plan.backproject_logpolar_partial(q, 8, 0.25, out=img),
+                    dict(ctx, **lpp_meshes(wl.N, wl.n_det, wl.n_theta, wl.det_spacing, 8, 0.25)))
         got = img.double().cpu().numpy()
 
         def chk():
