@@ -210,21 +210,8 @@ bst_interp_kernel(const float2 *__restrict__ polar, const float *__restrict__ an
     if (lx >= M || ly >= M) return;
     const int cx = lx < M / 2 ? lx : lx - M, cy = ly < M / 2 ? ly : ly - M;
     const float fx = (float)cx, fy = (float)cy;
-    const float twopi = 6.2831853071795865f;
-    float phi = atan2f(fy, fx);
-    if (phi < 0.f) phi += twopi;
-    // bracketing rays a, b (cyclic in angle); t = angle from ray a / angular gap a -> b
-    const int n = ri.n;
-    int a = last_at_most(ang, ri, phi);
-    if (a < 0) a = n - 1;
-    const int b = (a + 1 == n) ? 0 : a + 1;
-    const float4 d = __ldg(dir + a);  // (cos, sin) of ray a: high parts, low parts
-    const float p1 = d.x * fy, p2 = d.y * fx;
-    const float e1 = fmaf(d.x, fy, -p1), e2 = fmaf(d.y, fx, -p2);
-    const float cr = (p1 - p2) + ((e1 - e2) + fmaf(d.z, fy, -d.w * fx));  // xi_a x l
-    const float dt = fmaf(d.x, fx, d.y * fy);                              // xi_a . l
-    const float t = (n > 1) ? atan2f(cr, dt) * __ldg(inv_gap + a) : 0.f;
-    // fractional radial sample index m' = |l| / rho: |l| = s + slo (two floats), u = |l|^2 exact
+    // fractional radial sample index m' = |l| / rho: |l| = s + slo (two floats), u = |l|^2 exact;
+    // nodes beyond the last radial sample are zero (no angle needed)
     const int u = cx * cx + cy * cy;
     const float uh = (float)(u & ~0xff), ul = (float)(u & 0xff);
     const float sq = sqrtf(uh + ul);
@@ -240,8 +227,26 @@ bst_interp_kernel(const float2 *__restrict__ polar, const float *__restrict__ an
         m0 += 1;
         tm -= 1.f;
     }
+    if (m0 >= H) {
+        grid[(long long)lx * M + ly] = make_float2(0.f, 0.f);
+        return;
+    }
+    const float twopi = 6.2831853071795865f;
+    float phi = atan2f(fy, fx);
+    if (phi < 0.f) phi += twopi;
+    // bracketing rays a, b (cyclic in angle); t = angle from ray a / angular gap a -> b
+    const int n = ri.n;
+    int a = last_at_most(ang, ri, phi);
+    if (a < 0) a = n - 1;
+    const int b = (a + 1 == n) ? 0 : a + 1;
+    const float4 d = __ldg(dir + a);  // (cos, sin) of ray a: high parts, low parts
+    const float p1 = d.x * fy, p2 = d.y * fx;
+    const float e1 = fmaf(d.x, fy, -p1), e2 = fmaf(d.y, fx, -p2);
+    const float cr = (p1 - p2) + ((e1 - e2) + fmaf(d.z, fy, -d.w * fx));  // xi_a x l
+    const float dt = fmaf(d.x, fx, d.y * fy);                              // xi_a . l
+    const float t = (n > 1) ? atan2f(cr, dt) * __ldg(inv_gap + a) : 0.f;
     float2 v = make_float2(0.f, 0.f);
-    if (m0 < H) {
+    {
         const int ca = __ldg(ray + a), cb = __ldg(ray + b);
         const float2 a0 = ray_sample(polar, ca, m0, H), a1 = ray_sample(polar, ca, m0 + 1, H);
         const float2 b0 = ray_sample(polar, cb, m0, H), b1 = ray_sample(polar, cb, m0 + 1, H);
