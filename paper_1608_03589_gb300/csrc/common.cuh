@@ -49,6 +49,7 @@ struct FourierWork {
     float *wk = nullptr;        // [n_theta] quadrature weights (float)
     float2 *twM = nullptr;      // M/2 twiddles exp(-2 pi i r / M)
     float2 *twpassM = nullptr;  // per-pass twiddles of the M-point transform (build_pass_twiddles)
+    float2 *twpassH = nullptr;  // per-pass twiddles of the M/2-point transform (M = 16384: split transforms)
     long long *ray = nullptr;   // [n_theta][2] rho cos, rho sin in 32.32 fixed point
     void *sray = nullptr;       // rays sorted by angle (gather gridding)
     float *sphi = nullptr;      // sorted ray angles in [0, 2 pi)

@@ -37,6 +37,7 @@
 #include "common.cuh"
 #include "fft.cuh"
 #include "fft_pt.cuh"
+#include "lp_rows.cuh"
 #include "tma.cuh"
 
 namespace bp {
@@ -579,6 +580,50 @@ ifft_pass_x_kernel(const float2 *__restrict__ inter, float *__restrict__ img, co
         const int r = i / N, ix = i - r * N;
         const int pos = (ix - h) & (M - 1);
         img[(long long)(iy0 + r) * N + ix] = z[r * M + pos].x * __ldg(deap + ix);
+    }
+}
+
+// Persistent form of the two passes for M = 2^14: each M-point transform as two register-first
+// M/2-point transforms of its even and odd entries combined in registers (lp_rows.cuh); rows
+// arrive as 16-byte (even, odd) pairs.  XPASS false: rows l_x of G, outputs
+// inter[i_y][l_x] = z * deap[i_y] (8-byte stores); true: rows i_y of inter,
+// img[i_y][i_x] = Re z * deap[i_x].  Output position pos is image index
+// (pos + floor(N/2)) mod M when that is below N.
+template <bool XPASS>
+__global__ void __launch_bounds__(1024, 1)
+ifft_split_kernel(const float2 *__restrict__ in, float2 *__restrict__ inter, float *__restrict__ img,
+                  const float *__restrict__ deap, const float2 *__restrict__ twp, const float2 *__restrict__ twM,
+                  int rows, int N) {
+    constexpr int LOGH = 13, H = 1 << LOGH, M = 2 * H, NT = H / kPassE;
+    extern __shared__ __align__(128) float2 z[];  // [H] work | per-pass twiddles | [H] E outputs
+    float2 *Tw = z + lp_rows_pt_tw_off<LOGH>();
+    float2 *sE = Tw + lp_rows_pt_twn<LOGH>();
+    const int t = threadIdx.x, h = N / 2;
+    lp_stage_pass_twiddles<LOGH>(Tw, twp, t);
+    for (int row = blockIdx.x; row < rows; row += gridDim.x) {
+        const float4 *src = reinterpret_cast<const float4 *>(in + (long long)row * M);
+        float2 ae[kPassE], ao[kPassE];
+#pragma unroll
+        for (int r = 0; r < kPassE; ++r) {
+            const float4 v = __ldg(src + t + r * NT);
+            ae[r] = make_float2(v.x, v.y);
+            ao[r] = make_float2(v.z, v.w);
+        }
+        float2 xl[kPassE], xu[kPassE];
+        lp_dit_row<LOGH, true>(ae, ao, z, Tw, sE, twM, t, xl, xu);
+#pragma unroll
+        for (int m = 0; m < kPassE; ++m) {
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                const int pos = t + m * NT + half * H;
+                const int o = pos < N - h ? pos + h : pos - (M - h);
+                if (o < 0 || o >= N) continue;
+                const float2 v = half ? xu[m] : xl[m];
+                const float d = __ldg(deap + o);
+                if (XPASS) img[(long long)row * N + o] = v.x * d;
+                else inter[(long long)o * M + row] = make_float2(v.x * d, v.y * d);
+            }
+        }
     }
 }
 
@@ -1247,6 +1292,7 @@ void free_fourier(bp_plan *p) {
     cudaFree(f.wk);
     cudaFree(f.twM);
     cudaFree(f.twpassM);
+    cudaFree(f.twpassH);
     cudaFree(f.ray);
     cudaFree(f.sray);
     cudaFree(f.sphi);
@@ -1343,9 +1389,13 @@ bp_status ensure_fourier(bp_plan *p) {
         tw[i] = make_float2((float)std::cos(an), (float)std::sin(an));
     }
 
-    std::vector<float2> twp;
+    std::vector<float2> twp, twh;
     build_pass_twiddles(ilog2(M), twp);
     twp.resize((twp.size() + 1) & ~(size_t)1);  // a whole number of float4 loads
+    if (M == 16384) {  // the split M-point transforms (two M/2-point ones)
+        build_pass_twiddles(ilog2(M) - 1, twh);
+        twh.resize((twh.size() + 1) & ~(size_t)1);
+    }
 
     f.M = M;
     f.W = kW;
@@ -1365,6 +1415,7 @@ bp_status ensure_fourier(bp_plan *p) {
     alloc((void **)&f.wk, sizeof(float) * n_theta);
     alloc((void **)&f.twM, sizeof(float2) * tw.size());
     alloc((void **)&f.twpassM, sizeof(float2) * twp.size());
+    if (!twh.empty()) alloc((void **)&f.twpassH, sizeof(float2) * twh.size());
     alloc((void **)&f.ray, sizeof(long long) * ray.size());
     alloc(&f.sray, sizeof(SortedRay) * sray.size());
     alloc((void **)&f.sphi, sizeof(float) * sphi.size());
@@ -1374,6 +1425,8 @@ bp_status ensure_fourier(bp_plan *p) {
     if (e == cudaSuccess) e = cudaMemcpy(f.twM, tw.data(), sizeof(float2) * tw.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(f.twpassM, twp.data(), sizeof(float2) * twp.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !twh.empty())
+        e = cudaMemcpy(f.twpassH, twh.data(), sizeof(float2) * twh.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(f.ray, ray.data(), sizeof(long long) * ray.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(f.sray, sray.data(), sizeof(SortedRay) * sray.size(), cudaMemcpyHostToDevice);
@@ -1446,6 +1499,20 @@ static int rows_per_cta(int M) { return M <= 8192 ? 2 : 1; }
 static bp_status launch_grid_to_image_rows(bp_plan *p, const float *deap, float *img, cudaStream_t st) {
     FourierWork &f = p->four;
     const int N = p->N, M = f.M;
+    if (M == 16384 && f.twpassH) {
+        constexpr size_t smem = lp_rows_pt_smem<13>();
+        auto ky = ifft_split_kernel<false>;
+        auto kx = ifft_split_kernel<true>;
+        BP_CUDA_TRY(cudaFuncSetAttribute(ky, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        BP_CUDA_TRY(cudaFuncSetAttribute(kx, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        const int sms = std::max(1, p->sm_count);
+        ky<<<std::min(sms, M), 1024, smem, st>>>(f.grid, f.mid, nullptr, deap, f.twpassH, f.twM, M, N);
+        stage_mark(p, st, "ifft_pass_y_kernel");
+        kx<<<std::min(sms, N), 1024, smem, st>>>(f.mid, nullptr, img, deap, f.twpassH, f.twM, N, N);
+        stage_mark(p, st, "ifft_pass_x_kernel");
+        BP_CUDA_TRY(cudaGetLastError());
+        return BP_OK;
+    }
     const int R = rows_per_cta(M);
     const size_t smemR = sizeof(float2) * ((size_t)R * M + M / 2);
     auto pass_y = fft_elems(M) == 16 ? ifft_pass_y_kernel<16> : ifft_pass_y_kernel<8>;
