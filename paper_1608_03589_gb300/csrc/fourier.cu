@@ -583,6 +583,65 @@ ifft_pass_x_kernel(const float2 *__restrict__ inter, float *__restrict__ img, co
     }
 }
 
+// The spectra for P = 2^14 (no fused filter) from a persistent kernel: each P-point transform of
+// a packed projection pair as two register-first P/2-point transforms combined in registers
+// (lp_rows.cuh); Z[P - m] for the two rows' separation comes from the upper half through the
+// work array; then the detector-centre and half-pixel phases and the weights as above.
+template <typename Tin>
+__global__ void __launch_bounds__(1024, 1)
+fourier_spectra_split_kernel(const Tin *__restrict__ sino, float2 *__restrict__ spec, const float *__restrict__ wk,
+                             const float2 *__restrict__ twp, const float2 *__restrict__ twP, int n_theta, int n_det,
+                             float wuni, const long long *__restrict__ ray, float delta2_over_M) {
+    constexpr int LOGH = 13, H = 1 << LOGH, P = 2 * H, NT = H / kPassE;
+    extern __shared__ __align__(128) float2 z[];  // [H] work | per-pass twiddles | [H] E outputs
+    float2 *Tw = z + lp_rows_pt_tw_off<LOGH>();
+    float2 *sE = Tw + lp_rows_pt_twn<LOGH>();
+    const int t = threadIdx.x;
+    lp_stage_pass_twiddles<LOGH>(Tw, twp, t);
+    const long long twoP = 2LL * P;
+    for (int pr = blockIdx.x; 2 * pr < n_theta; pr += gridDim.x) {
+        const int k0 = 2 * pr, k1 = k0 + 1;
+        const bool has1 = k1 < n_theta;
+        const Tin *a = sino + (long long)k0 * n_det;
+        const Tin *b = sino + (long long)k1 * n_det;
+        float2 ae[kPassE], ao[kPassE];
+#pragma unroll
+        for (int r = 0; r < kPassE; ++r) {
+            const int i = 2 * (t + r * NT);  // even sample i, odd sample i + 1
+            ae[r] = make_float2(i < n_det ? load_f(a + i) : 0.f, (has1 && i < n_det) ? load_f(b + i) : 0.f);
+            ao[r] = make_float2(i + 1 < n_det ? load_f(a + i + 1) : 0.f,
+                                (has1 && i + 1 < n_det) ? load_f(b + i + 1) : 0.f);
+        }
+        float2 xl[kPassE], xu[kPassE];
+        lp_dit_row<LOGH, false>(ae, ao, z, Tw, sE, twP, t, xl, xu);
+        __syncthreads();  // every thread is done with z (the second transform)
+#pragma unroll
+        for (int m = 0; m < kPassE; ++m) z[t + m * NT] = xu[m];
+        __syncthreads();
+        const float wa = (wuni > 0.f ? wuni : __ldg(wk + k0)) / (float)P;
+        const float wb = has1 ? (wuni > 0.f ? wuni : __ldg(wk + k1)) / (float)P : 0.f;
+#pragma unroll
+        for (int mi = 0; mi < kPassE; ++mi) {
+            const int m = t + mi * NT;  // Z[P - m] = X[H + (H - m)] (m > 0), X[0] for m = 0
+            const float2 zm = xl[mi], zc = m == 0 ? xl[mi] : z[H - m];
+            const float2 A = make_float2(0.5f * (zm.x + zc.x), 0.5f * (zm.y - zc.y));
+            const float2 B = make_float2(0.5f * (zm.y + zc.y), -0.5f * (zm.x - zc.x));
+            const long long r = ((long long)m * (n_det - 1)) % twoP;
+            float sn, cs;
+            sincospif((float)r / (float)P, &sn, &cs);
+            float2 pa = make_float2(cs, sn), pb = pa;
+            if (delta2_over_M != 0.f) {
+                pa = cmul(pa, half_pixel_phase(ray + 2 * k0, m, delta2_over_M));
+                if (has1) pb = cmul(pb, half_pixel_phase(ray + 2 * k1, m, delta2_over_M));
+            }
+            const float f = (m == 0) ? 1.f : 2.f;
+            const float2 ca = cmul(A, pa), cb = cmul(B, pb);
+            spec[(long long)k0 * H + m] = make_float2(f * wa * ca.x, f * wa * ca.y);
+            if (has1) spec[(long long)k1 * H + m] = make_float2(f * wb * cb.x, f * wb * cb.y);
+        }
+    }
+}
+
 // Persistent form of the two passes for M = 2^14: each M-point transform as two register-first
 // M/2-point transforms of its even and odd entries combined in registers (lp_rows.cuh); rows
 // arrive as 16-byte (even, odd) pairs.  XPASS false: rows l_x of G, outputs
@@ -1478,6 +1537,16 @@ static bp_status spectra_t(bp_plan *p, const Tin *sino, cudaStream_t st, float w
             case 12: return spectra_pt<Tin, 12>(p, sino, st, wuni, delta2, Hf);
             default: break;
         }
+    }
+    const FourierWork &f = p->four;
+    if (!Hf && p->P == 16384 && f.M == 16384 && f.twpassH) {  // the split transforms (twiddles of M = P)
+        constexpr size_t smem = lp_rows_pt_smem<13>();
+        auto kern = fourier_spectra_split_kernel<Tin>;
+        BP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        const int ctas = std::min((p->n_theta + 1) / 2, std::max(1, p->sm_count));
+        kern<<<ctas, 1024, smem, st>>>(sino, f.spec, f.wk, f.twpassH, f.twM, p->n_theta, p->n_det, wuni, f.ray, delta2);
+        stage_mark(p, st, "fourier_spectra_kernel");
+        return BP_OK;
     }
     const size_t smem = sizeof(float2) * (p->P + p->P / 2);
     const int threads = fft_threads(p->P);
