@@ -451,7 +451,7 @@ bp_direct_klein_kernel(float *__restrict__ img, const KleinAngle *__restrict__ k
         if (uw & 8) {
             klein_roles<BPT>(uw & 7, acc, role, dir);
             if (uw & 16) {
-#pragma unroll 2
+#pragma unroll(2 * BPT)
                 for (int kk = 0; kk < kn; ++kk) {
                     const float4 A = prmA[b][kk], O = prmO[b][kk];
 #pragma unroll
@@ -459,7 +459,7 @@ bp_direct_klein_kernel(float *__restrict__ img, const KleinAngle *__restrict__ k
                         klein_angle<1, STG>(A, O, ktab, wb + kk * kKW, acc[h], fx + (float)(16 * h), fy);
                 }
             } else {
-#pragma unroll 2
+#pragma unroll(2 * BPT)
                 for (int kk = 0; kk < kn; ++kk) {
                     const float4 A = prmA[b][kk], O = prmO[b][kk];
 #pragma unroll
