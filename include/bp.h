@@ -240,6 +240,24 @@ bp_status bp_fbp_fourier(bp_plan *plan, const void *sino, bp_dtype dtype, float 
                          float param, int batch, void *stream);
 
 /*
+ * bp_fbp_direct -- filtered backprojection in the direct form: bp_filter (kind, param =
+ * Tikhonov lambda, else ignored; Section 3 Remark 1 (ii) eq "fbp") followed by
+ * bp_backproject_direct (Section 2 eq "bp_app"), with the BP_F32 launch shape.  Where
+ * bp_backproject_direct takes the four-image form and n_det <= 2048, the filter's last
+ * transform writes each filtered row pair straight into that form's per-call row tables (one
+ * launch instead of two, and no filtered sinogram in memory); otherwise the filtered slices go
+ * to a plan-owned float32 array (batch x n_theta x n_det, allocated or grown on demand after a
+ * synchronisation of `stream`, released by bp_destroy) and are backprojected from it.  The
+ * filtered values are those of bp_filter (bit for bit when batch is 1 or n_theta is even), so
+ * the image equals bp_filter followed by bp_backproject_direct up to the order of the direct
+ * form's atomic partial sums.
+ *   sino  device [batch][n_theta][n_det] of dtype (not modified);  img  device [batch][N][N]
+ *   float32, overwritten.  Limits and errors as bp_filter and bp_backproject_direct.
+ */
+bp_status bp_fbp_direct(bp_plan *plan, const void *sino, bp_dtype dtype, float *img, bp_filter_kind kind,
+                        float param, int batch, void *stream);
+
+/*
  * bp_radon -- R, the forward Radon transform (Section 1 eq "P_theta"), as the scaled
  * exact transpose of a discrete R*:  R = (dx^2/dt) diag(1/w_k) A^T  where A is the
  * matrix of R*.  With fourier_adjoint = 0, A is the direct (linear-interpolation) R*;
@@ -273,7 +291,7 @@ bp_status bp_backproject_transpose(bp_plan *plan, const float *img, float *sino,
 /*
  * bp_fbp_host -- filtered backprojection from HOST memory to HOST memory:
  * for each slice of sino (host, batch x n_theta x n_det float32): copy it to the device,
- * bp_filter(kind, param), bp_backproject_direct, copy the image back into img (host,
+ * bp_fbp_direct(kind, param), copy the image back into img (host,
  * batch x N x N float32); synchronise before returning.  The slices go through three device
  * slots: slice i + 1 is copied in and slice i - 1 copied out (on two internal streams of the
  * plan) while slice i is filtered and backprojected on `stream`, so with pinned host memory

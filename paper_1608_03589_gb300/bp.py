@@ -25,8 +25,8 @@ _DTYPES = {torch.float32: BP_F32, torch.bfloat16: BP_BF16, torch.float16: BP_F16
 
 # Every symbol the header declares (checked by the ABI test).
 SYMBOLS = ("bp_plan_create", "bp_destroy", "bp_filter", "bp_backproject_direct", "bp_backproject_fourier",
-           "bp_radon", "bp_fbp_host", "bp_fbp_fourier", "bp_backproject_bst", "bp_backproject_bst_windowed",
-           "bp_backproject_logpolar", "bp_backproject_logpolar_partial", "bp_set_fourier_width", "bp_backproject_batched", "bp_fbp_static", "bp_check", "bp_radon_transpose",
+           "bp_radon", "bp_fbp_host", "bp_fbp_fourier", "bp_fbp_direct", "bp_backproject_bst",
+           "bp_backproject_bst_windowed", "bp_backproject_logpolar", "bp_backproject_logpolar_partial", "bp_set_fourier_width", "bp_backproject_batched", "bp_fbp_static", "bp_check", "bp_radon_transpose",
            "bp_backproject_transpose", "bp_autotune", "bp_get_shape", "bp_set_shape", "bp_tune_cache_save",
            "bp_tune_cache_load", "bp_stage_timing", "bp_stage_times", "bp_last_error", "bp_version")
 OPS = {"direct": 0, "radon": 1}
@@ -60,6 +60,7 @@ def lib() -> ctypes.CDLL:
             L.bp_fbp_host.argtypes = [vp, vp, vp, i, f, i, vp]
             L.bp_fbp_static.argtypes = [vp, vp, i, vp, i, i, vp]
             L.bp_fbp_fourier.argtypes = [vp, vp, i, vp, i, f, i, vp]
+            L.bp_fbp_direct.argtypes = [vp, vp, i, vp, i, f, i, vp]
             L.bp_backproject_bst.argtypes = [vp, vp, i, vp, i, i, vp]
             L.bp_backproject_bst_windowed.argtypes = [vp, vp, i, vp, i, f, i, vp]
             L.bp_backproject_logpolar.argtypes = [vp, vp, i, vp, i, vp]
@@ -79,7 +80,7 @@ def lib() -> ctypes.CDLL:
             L.bp_stage_timing.argtypes = [vp, i]
             L.bp_stage_times.argtypes = [vp, i, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(f), ip, ip]
             for name in ("bp_filter", "bp_backproject_direct", "bp_backproject_fourier", "bp_radon",
-                         "bp_fbp_host", "bp_fbp_fourier", "bp_backproject_bst", "bp_backproject_bst_windowed",
+                         "bp_fbp_host", "bp_fbp_fourier", "bp_fbp_direct", "bp_backproject_bst", "bp_backproject_bst_windowed",
                          "bp_backproject_logpolar", "bp_backproject_logpolar_partial",
                          "bp_set_fourier_width",
                          "bp_backproject_batched", "bp_fbp_static",
@@ -292,6 +293,26 @@ class Plan:
         with torch.cuda.device(self.device):
             _check(lib().bp_fbp_fourier(self.handle, sino.data_ptr(), _DTYPES[sino.dtype], out.data_ptr(), k,
                                         float(param), b, _stream(sino)), "bp_fbp_fourier")
+        return out
+
+    def fbp_direct(self, sino: torch.Tensor, kind: str | int = "ramlak", param: float = 0.0,
+                   out: torch.Tensor | None = None) -> torch.Tensor:
+        """Filtered backprojection in the direct form (bp_fbp_direct): filter() then backproject()
+        of the float32 filtered rows, the filter writing the four-image form's row tables
+        directly where that form runs."""
+        _cuda(sino, "sino")
+        b = self._batch(sino, (self.n_theta, self.n_det), "sino")
+        if sino.dtype not in _DTYPES:
+            raise BPError(f"unsupported sinogram dtype {sino.dtype}")
+        k = FILTERS[kind] if isinstance(kind, str) else int(kind)
+        if out is None:
+            out = torch.empty((*sino.shape[:-2], self.N, self.N), dtype=torch.float32, device=sino.device)
+        _cuda(out, "out")
+        if out.dtype != torch.float32 or out.numel() != b * self.N * self.N:
+            raise BPError("out must be float32 with batch x N x N elements")
+        with torch.cuda.device(self.device):
+            _check(lib().bp_fbp_direct(self.handle, sino.data_ptr(), _DTYPES[sino.dtype], out.data_ptr(), k,
+                                       float(param), b, _stream(sino)), "bp_fbp_direct")
         return out
 
     def radon(self, img: torch.Tensor, out: torch.Tensor | None = None, fourier: bool = False) -> torch.Tensor:

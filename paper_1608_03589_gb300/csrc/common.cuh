@@ -187,6 +187,9 @@ struct bp_plan {
     float2 *d_twpass = nullptr;  // per-pass twiddles of the persistent filter kernel (512 <= P <= 4096)
     float *d_H[3] = {nullptr, nullptr, nullptr};   // scaled responses (dt/P) DFT_P(h) per kind, natural order
     float H_param[3] = {0.f, 0.f, 0.f};
+    // bp_fbp_direct on a geometry without the fused form: the filtered sinograms
+    float *d_fbp = nullptr;
+    size_t fbp_n = 0;                       // floats allocated
     // Fourier path
     int fourier_W = 6;          // Kaiser-Bessel width of the gridding (bp_set_fourier_width)
     bp::FourierWork four;
@@ -259,7 +262,9 @@ void free_klein(bp_plan *p);
 int klein_default_groups(const bp_plan *p);
 int klein_clamp_groups(const bp_plan *p, int S);
 bp_status launch_direct_klein(bp_plan *p, const void *sino, bp_dtype dt, float *img, int batch, int accumulate,
-                              cudaStream_t st, float wuni, int stage, int S);
+                              cudaStream_t st, float wuni, int stage, int S, const float *H = nullptr);
+bp_status launch_fbp_direct(bp_plan *p, const void *sino, bp_dtype dt, float *img, int kind, float param, int batch,
+                            cudaStream_t st);
 void free_fourier(bp_plan *p);
 void free_bst(bp_plan *p);
 void free_logpolar(bp_plan *p);

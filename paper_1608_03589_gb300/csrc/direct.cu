@@ -386,6 +386,32 @@ bp_status launch_direct(bp_plan *p, const void *sino, bp_dtype dt, float *img, i
     return launch_direct_shape(p, sino, dt, img, batch, accumulate, st, wuni, direct_shape(p, dt, batch));
 }
 
+// Filter + direct R* (bp_fbp_direct).  With the four-image form and the persistent filter
+// transform, each slice's filtered rows go straight into the row tables (one launch, the
+// filtered sinogram never leaves the chip); otherwise the slices are filtered into a plan-owned
+// array and backprojected from it.  The launch shape is the one of BP_F32 sinograms (what the
+// tables and the array hold).
+bp_status launch_fbp_direct(bp_plan *p, const void *sino, bp_dtype dt, float *img, int kind, float param, int batch,
+                            cudaStream_t st) {
+    bp_status s = ensure_filter(p, kind, param);
+    if (s != BP_OK) return s;
+    const DirectShape shape = direct_shape(p, BP_F32, batch);
+    if (shape.workspace && p->klein.eligible && p->d_twpass)
+        return launch_direct_klein(p, sino, dt, img, batch, 0, st, 0.f, shape.stage, shape.asplit, p->d_H[kind]);
+    const size_t n = (size_t)batch * p->n_theta * p->n_det;
+    if (n > p->fbp_n) {
+        BP_CUDA_TRY(cudaStreamSynchronize(st));  // no queued call may still read the old array
+        cudaFree(p->d_fbp);
+        p->d_fbp = nullptr;
+        p->fbp_n = 0;
+        BP_CUDA_TRY(cudaMalloc(&p->d_fbp, sizeof(float) * n));
+        p->fbp_n = n;
+    }
+    s = launch_filter(p, sino, dt, p->d_fbp, kind, param, batch, st);
+    if (s != BP_OK) return s;
+    return launch_direct_shape(p, p->d_fbp, BP_F32, img, batch, 0, st, 0.f, shape);
+}
+
 DirectShape direct_clamp(const bp_plan *p, bp_dtype dt, DirectShape shape) {
     const int esz = dt == BP_F32 ? 4 : 2;
     return direct_effective(p, esz, tensor_map_encoder() != nullptr && tma_eligible(p, esz), shape);

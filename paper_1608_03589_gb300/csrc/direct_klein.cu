@@ -45,6 +45,7 @@
 #include "direct_tile.cuh"
 #include "tma.cuh"
 #include "f32x2.cuh"
+#include "filter_pt.cuh"
 
 namespace bp {
 
@@ -89,6 +90,48 @@ klein_tables_kernel(const Tin *__restrict__ sino, float4 *__restrict__ tab, cons
         p0[m] = make_float4(w * a0, w * b0, w * (a1 - a0), w * (b1 - b0));
         p1[m] = make_float4(w * (a2 - a1), w * (b2 - b1), w * (a3 - a2), w * (b3 - b2));
     }
+}
+
+// The fused FBP form of the tables: the persistent row filter of filter_pt.cuh turns each row
+// pair into its filtered values in shared memory, and the pair's table entries (the layout of
+// klein_tables_kernel, the same arithmetic on the same values) are written from there, so the
+// filtered sinogram never goes through global memory.  rows = n_theta (one slice).
+struct KleinTabOut {
+    static constexpr bool kStaged = true;
+    float4 *tab;
+    const AngleParam *ap;
+    int jlo, L, RS;
+    float wuni;
+    __device__ __forceinline__ void rows(const float *sg, long long r0, bool has1, int n_det) const {
+        for (int h = 0; h < 2; ++h) {
+            if (h == 1 && !has1) break;
+            const long long k = r0 + h;
+            const float *sr = sg + h * (n_det + 8);
+            const float w = wuni > 0.f ? wuni : ap[k].w;
+            auto g = [&](int j) { return (j >= -4 && j < n_det + 4) ? sr[j + 4] : 0.f; };
+            float4 *p0 = tab + 2 * k * RS, *p1 = p0 + RS;
+            for (int m = threadIdx.x; m < L; m += blockDim.x) {
+                const int j = jlo + m, jr = n_det - 1 - j;
+                const float a0 = g(j), a1 = g(j + 1), a2 = g(j + 2), a3 = g(j + 3);
+                const float b0 = g(jr), b1 = g(jr - 1), b2 = g(jr - 2), b3 = g(jr - 3);
+                p0[m] = make_float4(w * a0, w * b0, w * (a1 - a0), w * (b1 - b0));
+                p1[m] = make_float4(w * (a2 - a1), w * (b2 - b1), w * (a3 - a2), w * (b3 - b2));
+            }
+        }
+    }
+};
+
+// zero: the slice's image (n4 float4), cleared here for the main kernel's atomic adds (null when
+// it accumulates), in place of a memset launch.
+template <typename Tin, int LOGP>
+__global__ void __launch_bounds__((1 << LOGP) / kPassE, 1024 / ((1 << LOGP) / kPassE))
+klein_filter_tables_kernel(const Tin *__restrict__ sino, KleinTabOut out, const float *__restrict__ H,
+                           const float2 *__restrict__ twp, int n_theta, int n_det, float4 *__restrict__ zero,
+                           long long n4) {
+    if (zero)
+        for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n4; i += (long long)gridDim.x * blockDim.x)
+            zero[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    filter_pt_body<Tin, LOGP>(sino, out, H, twp, (long long)n_theta, n_det);
 }
 
 // Add (or store) two horizontally adjacent pixels; x even, so the pair is 8-byte aligned.
@@ -692,9 +735,42 @@ bp_status klein_tables(bp_plan *p, const Tin *sino, cudaStream_t st, float wuni)
     return BP_OK;
 }
 
+template <typename Tin, int LOGP>
+bp_status klein_filter_tables_p(bp_plan *p, const Tin *sino, const float *H, cudaStream_t st, float wuni,
+                                float *zero) {
+    constexpr int NT = (1 << LOGP) / kPassE;
+    constexpr size_t smem = filter_pt_smem<LOGP>();
+    auto kern = klein_filter_tables_kernel<Tin, LOGP>;
+    static int per_sm = 0;
+    if (!per_sm) {
+        BP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        BP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem));
+    }
+    const int npairs = (p->n_theta + 1) / 2;
+    const int grid = std::max(1, std::min(npairs, std::max(1, per_sm) * std::max(1, p->sm_count)));
+    const KleinWork &kw = p->klein;
+    kern<<<grid, NT, smem, st>>>(sino, KleinTabOut{kw.tab, p->d_ang, kw.jlo, kw.L, kw.L + kKW, wuni}, H,
+                                 p->d_twpass, p->n_theta, p->n_det, (float4 *)zero,
+                                 zero ? (long long)p->N * p->N / 4 : 0LL);
+    BP_CUDA_TRY(cudaGetLastError());
+    stage_mark(p, st, "klein_filter_tables_kernel");
+    return BP_OK;
+}
+
+template <typename Tin>
+bp_status klein_filter_tables(bp_plan *p, const Tin *sino, const float *H, cudaStream_t st, float wuni,
+                              float *zero) {
+    switch (ilog2(p->P)) {
+        case 9: return klein_filter_tables_p<Tin, 9>(p, sino, H, st, wuni, zero);
+        case 10: return klein_filter_tables_p<Tin, 10>(p, sino, H, st, wuni, zero);
+        case 11: return klein_filter_tables_p<Tin, 11>(p, sino, H, st, wuni, zero);
+        default: return klein_filter_tables_p<Tin, 12>(p, sino, H, st, wuni, zero);
+    }
+}
+
 template <typename Tin, int MINB, int NBUF, int BPT, int STG>
 bp_status launch_klein_t(bp_plan *p, const Tin *sino, float *img, int batch, int accumulate, cudaStream_t st,
-                         float wuni, int S) {
+                         float wuni, int S, const float *H) {
     constexpr int NT = kKThreads / BPT;
     KleinWork &kw = p->klein;
     if (!kw.d_ang) {
@@ -710,26 +786,33 @@ bp_status launch_klein_t(bp_plan *p, const Tin *sino, float *img, int batch, int
         return fail(BP_ERR_UNSUPPORTED, "direct R*: detector row too long for the four-image form");
     const size_t img_n = (size_t)p->N * p->N, sino_n = (size_t)p->n_theta * p->n_det;
     stage_begin(p, st);
-    if (!accumulate) {
+    // the fused FBP form clears each slice's image inside its table launch (N even: N^2 / 4 float4)
+    const bool clear_in_tables = H && !accumulate && aligned16(img) && img_n % 4 == 0;
+    if (!accumulate && !clear_in_tables) {
         BP_CUDA_TRY(cudaMemsetAsync(img, 0, sizeof(float) * img_n * batch, st));
         stage_mark(p, st, "memset (direct R* image)");
     }
     const KleinAngle *ka = (const KleinAngle *)kw.d_ang;
-    if (batch == 1) {
-        // one slice: the tables by their own launch, then the main kernel
+    if (batch == 1 || H) {
+        // slice by slice: the tables by their own launch (filtered on the way when H is given),
+        // then the main kernel
         auto kern = bp_direct_klein_kernel<float, MINB, NBUF, false, BPT, STG>;
         static int per_sm = 0;
         if (!per_sm) {
             BP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             BP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem));
         }
-        bp_status s = klein_tables(p, sino, st, wuni);
-        if (s != BP_OK) return s;
         const int grid = std::max(1, per_sm) * std::max(1, p->sm_count);
-        kern<<<grid, NT, smem, st>>>(img, ka, kw.tab, nullptr, p->d_ang, wuni, p->N, p->n_det, p->n_theta, RS,
-                                            kw.L, kw.jlo, kw.nr, S, 1, 0, 0, kw.gbar, p->d_err);
-        BP_CUDA_TRY(cudaGetLastError());
-        stage_mark(p, st, "bp_direct_klein_kernel");
+        for (int b = 0; b < batch; ++b) {
+            const Tin *sb = sino + sino_n * b;
+            bp_status s = H ? klein_filter_tables(p, sb, H, st, wuni, clear_in_tables ? img + img_n * b : nullptr)
+                            : klein_tables(p, sb, st, wuni);
+            if (s != BP_OK) return s;
+            kern<<<grid, NT, smem, st>>>(img + img_n * b, ka, kw.tab, nullptr, p->d_ang, wuni, p->N, p->n_det,
+                                         p->n_theta, RS, kw.L, kw.jlo, kw.nr, S, 1, 0, 0, kw.gbar, p->d_err);
+            BP_CUDA_TRY(cudaGetLastError());
+            stage_mark(p, st, "bp_direct_klein_kernel");
+        }
         return BP_OK;
     }
     // a batch: one cooperative persistent launch; each slice's tables are built inside it, between
@@ -762,15 +845,17 @@ bp_status launch_klein_t(bp_plan *p, const Tin *sino, float *img, int batch, int
 
 template <int MINB, int BPT, int STG>
 bp_status launch_klein_dt(bp_plan *p, const void *sino, bp_dtype dt, float *img, int batch, int accumulate,
-                          cudaStream_t st, float wuni, int S) {
+                          cudaStream_t st, float wuni, int S, const float *H) {
     switch (dt) {
         case BP_BF16:
-            return launch_klein_t<__nv_bfloat16, MINB, 3, BPT, STG>(p, (const __nv_bfloat16 *)sino, img, batch, accumulate,
-                                                              st, wuni, S);
+            return launch_klein_t<__nv_bfloat16, MINB, 3, BPT, STG>(p, (const __nv_bfloat16 *)sino, img, batch,
+                                                                    accumulate, st, wuni, S, H);
         case BP_F16:
-            return launch_klein_t<__half, MINB, 3, BPT, STG>(p, (const __half *)sino, img, batch, accumulate, st, wuni, S);
+            return launch_klein_t<__half, MINB, 3, BPT, STG>(p, (const __half *)sino, img, batch, accumulate, st, wuni,
+                                                             S, H);
         default:
-            return launch_klein_t<float, MINB, 3, BPT, STG>(p, (const float *)sino, img, batch, accumulate, st, wuni, S);
+            return launch_klein_t<float, MINB, 3, BPT, STG>(p, (const float *)sino, img, batch, accumulate, st, wuni,
+                                                            S, H);
     }
 }
 
@@ -782,10 +867,12 @@ bp_status launch_klein_dt(bp_plan *p, const void *sino, bp_dtype dt, float *img,
 // CTAs per SM (up to 128 registers), 6-angle stages; shape[1] = angle groups S of the
 // persistent schedule.  Three stages of windows are in flight.
 bp_status launch_direct_klein(bp_plan *p, const void *sino, bp_dtype dt, float *img, int batch, int accumulate,
-                              cudaStream_t st, float wuni, int stage, int S) {
-    if (stage == 8) return launch_klein_dt<4, 2, 6>(p, sino, dt, img, batch, accumulate, st, wuni, S);
-    if (stage == 32) return launch_klein_dt<3, 2, 8>(p, sino, dt, img, batch, accumulate, st, wuni, S);
-    return launch_klein_dt<3, 1, 8>(p, sino, dt, img, batch, accumulate, st, wuni, S);
+                              cudaStream_t st, float wuni, int stage, int S, const float *H) {
+    if (H && !(p->d_twpass && aligned16(H) && aligned16(p->d_twpass)))
+        return fail(BP_ERR_UNSUPPORTED, "fused FBP: no persistent filter transform for this detector length");
+    if (stage == 8) return launch_klein_dt<4, 2, 6>(p, sino, dt, img, batch, accumulate, st, wuni, S, H);
+    if (stage == 32) return launch_klein_dt<3, 2, 8>(p, sino, dt, img, batch, accumulate, st, wuni, S, H);
+    return launch_klein_dt<3, 1, 8>(p, sino, dt, img, batch, accumulate, st, wuni, S, H);
 }
 
 }  // namespace bp

@@ -13,6 +13,7 @@
 #include "common.cuh"
 #include "fft.cuh"
 #include "fft_pt.cuh"
+#include "filter_pt.cuh"
 
 namespace bp {
 
@@ -56,145 +57,23 @@ filter_kernel(const Tin *__restrict__ in, float *__restrict__ out, const float *
     }
 }
 
-// ------------------------------------------------------------------ per-pass-twiddle kernel
-// Transform lengths P = 2^9 .. 2^12 (n_det <= 2048) take a persistent kernel instead: each CTA
-// stages H and a per-pass twiddle table in shared memory once and then walks row pairs.  The
-// passes are the Stockham radix-8 passes of fft.cuh (a radix-4 or radix-2 pass last when
-// log2 P is not a multiple of 3) with P / 8 threads, but
-//  * pass twiddles come from a table laid out per pass as T[(r - 1) L + k] = W_{LR}^{rk}, so
-//    the lanes of a warp (consecutive k) read consecutive entries, free of bank conflicts;
-//  * the first forward pass reads the two rows straight from global memory (the upper half
-//    of the zero-padded row is known to be zero) and the next pair's loads are in flight
-//    while the current pair is transformed;
-//  * the outputs of the last forward pass that a thread holds are exactly the inputs of its
-//    first inverse pass, so H is applied and that pass computed in registers;
-//  * the last inverse pass writes the first n_det outputs straight to global memory.
+// Transform lengths P = 2^9 .. 2^12 (n_det <= 2048) take the persistent kernel of filter_pt.cuh
+// instead, its filtered rows written straight from registers.
+struct RowsOut {
+    static constexpr bool kStaged = false;
+    float *out;
+    __device__ __forceinline__ void put(long long r0, bool has1, int n_det, int i, float2 v) const {
+        float *oa = out + r0 * n_det;
+        oa[i] = v.x;
+        if (has1) oa[n_det + i] = v.y;
+    }
+};
+
 template <typename Tin, int LOGP>
 __global__ void __launch_bounds__((1 << LOGP) / kPassE, 1024 / ((1 << LOGP) / kPassE))
 filter_pt_kernel(const Tin *__restrict__ in, float *__restrict__ out, const float *__restrict__ H,
                  const float2 *__restrict__ twp, long long rows, int n_det) {
-    using PL = PtPlan<LOGP>;
-    constexpr int P = 1 << LOGP, NT = P / kPassE, Rl = PL::Rl, Gl = kPassE / Rl;
-    constexpr int TWN = pt_offset<LOGP>(PL::npass);
-    static_assert(TWN % 2 == 0, "per-pass twiddle count");
-    extern __shared__ __align__(16) float2 pz[];
-    float2 *z = pz;                                           // [P] work array
-    float2 *T = z + P;                                        // [TWN] per-pass twiddles
-    float *Hs = reinterpret_cast<float *>(T + ((TWN + 1) & ~1));  // [P] response
-    const int t = threadIdx.x;
-    const long long npairs = (rows + 1) / 2;
-    // inputs of the first forward pass: x[t + r NT], r < 4 (r >= 4 lies in the zero padding)
-    float2 nxt[4];
-    auto fetch = [&](long long pair) {
-        const long long r0 = 2 * pair;
-        const bool has1 = r0 + 1 < rows;
-        const Tin *a = in + r0 * n_det, *b = a + n_det;
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const int i = t + r * NT;
-            float va = 0.f, vb = 0.f;
-            if (i < n_det) {
-                va = load_f(a + i);
-                if (has1) vb = load_f(b + i);
-            }
-            nxt[r] = make_float2(va, vb);
-        }
-    };
-    long long pair = blockIdx.x;
-    if (pair < npairs) fetch(pair);
-    // stage the twiddles and H (16-byte loads, all in flight together; T and Hs start
-    // 16-byte aligned, TWN is even and P a multiple of 4)
-    {
-        constexpr int n4t = TWN / 2, n4h = P / 4;
-        const float4 *ts = reinterpret_cast<const float4 *>(twp);
-        const float4 *hs = reinterpret_cast<const float4 *>(H);
-        float4 *td = reinterpret_cast<float4 *>(T);
-        float4 *hd = reinterpret_cast<float4 *>(Hs);
-#pragma unroll
-        for (int i = 0; i < (n4t + NT - 1) / NT; ++i)
-            if (t + i * NT < n4t) td[t + i * NT] = __ldg(ts + t + i * NT);
-#pragma unroll
-        for (int i = 0; i < (n4h + NT - 1) / NT; ++i)
-            if (t + i * NT < n4h) hd[t + i * NT] = __ldg(hs + t + i * NT);
-    }
-    for (; pair < npairs; pair += gridDim.x) {
-        float2 a[8];
-#pragma unroll
-        for (int r = 0; r < 4; ++r) a[r] = nxt[r];
-#pragma unroll
-        for (int r = 4; r < 8; ++r) a[r] = make_float2(0.f, 0.f);
-        if (pair + gridDim.x < npairs) fetch(pair + gridDim.x);
-        __syncthreads();  // previous pair's last reads of z (and the staged tables) are done
-        // forward pass 0 (L = 1, radix 8) from registers
-        dft_reg<8>(a, false);
-#pragma unroll
-        for (int q = 0; q < 8; ++q) z[fft_swz<kPassE>(t * 8 + q)] = a[q];
-        __syncthreads();
-        int L = 8;
-#pragma unroll
-        for (int p = 1; p < PL::n8; ++p) {
-            if (p == PL::npass - 1) break;
-            pt_pass<8, LOGP>(z, T + pt_offset<LOGP>(p), L, t, false);
-            L *= 8;
-        }
-        // last forward pass into registers, times H, first inverse pass (L = 1, radix 8)
-        float2 b[8];
-        {
-            constexpr int lp = PL::npass - 1, m = P / Rl;
-            float2 c[Gl][Rl];
-#pragma unroll
-            for (int g = 0; g < Gl; ++g)
-#pragma unroll
-                for (int r = 0; r < Rl; ++r) c[g][r] = z[fft_swz<kPassE>(t + g * NT + r * m)];
-#pragma unroll
-            for (int g = 0; g < Gl; ++g) {
-                // here L * Rl = P: k = t + g NT, j = 0, outputs at k + q L = t + (g + q Gl) NT
-                pt_twiddle_dft<Rl>(c[g], T + pt_offset<LOGP>(lp), L, t + g * NT, false);
-#pragma unroll
-                for (int q = 0; q < Rl; ++q) {
-                    const int r = g + q * Gl;
-                    const float h = Hs[t + r * NT];
-                    b[r] = make_float2(c[g][q].x * h, c[g][q].y * h);
-                }
-            }
-        }
-        dft_reg<8>(b, true);
-        __syncthreads();  // all reads of the last forward pass done before z is overwritten
-#pragma unroll
-        for (int q = 0; q < 8; ++q) z[fft_swz<kPassE>(t * 8 + q)] = b[q];
-        __syncthreads();
-        L = 8;
-#pragma unroll
-        for (int p = 1; p < PL::n8; ++p) {
-            if (p == PL::npass - 1) break;
-            pt_pass<8, LOGP>(z, T + pt_offset<LOGP>(p), L, t, true);
-            L *= 8;
-        }
-        // last inverse pass: outputs t + (g + q Gl) NT straight to global memory
-        {
-            constexpr int lp = PL::npass - 1, m = P / Rl;
-            float2 c[Gl][Rl];
-#pragma unroll
-            for (int g = 0; g < Gl; ++g)
-#pragma unroll
-                for (int r = 0; r < Rl; ++r) c[g][r] = z[fft_swz<kPassE>(t + g * NT + r * m)];
-            const long long r0 = 2 * pair;
-            const bool has1 = r0 + 1 < rows;
-            float *oa = out + r0 * n_det, *ob = oa + n_det;
-#pragma unroll
-            for (int g = 0; g < Gl; ++g) {
-                pt_twiddle_dft<Rl>(c[g], T + pt_offset<LOGP>(lp), L, t + g * NT, true);
-#pragma unroll
-                for (int q = 0; q < Rl; ++q) {
-                    const int i = t + (g + q * Gl) * NT;
-                    if (i < n_det) {
-                        oa[i] = c[g][q].x;
-                        if (has1) ob[i] = c[g][q].y;
-                    }
-                }
-            }
-        }
-    }
+    filter_pt_body<Tin, LOGP>(in, RowsOut{out}, H, twp, rows, n_det);
 }
 
 // Spatial taps h(n), |n| < n_det, of the three filters (host, FP64).
@@ -280,8 +159,7 @@ namespace {
 template <typename Tin, int LOGP>
 bp_status launch_pt(bp_plan *p, const Tin *in, float *out, const float *H, long long rows, cudaStream_t st) {
     constexpr int P = 1 << LOGP, NT = P / kPassE;
-    constexpr int TWN = pt_offset<LOGP>(PtPlan<LOGP>::npass);
-    const size_t smem = sizeof(float2) * (P + ((TWN + 1) & ~1)) + sizeof(float) * P;
+    constexpr size_t smem = filter_pt_smem<LOGP>();
     auto kern = filter_pt_kernel<Tin, LOGP>;
     BP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;

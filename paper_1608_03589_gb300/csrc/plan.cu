@@ -145,6 +145,7 @@ static void plan_free_device(bp_plan *p) {
     free_logpolar_partial(p);
     free_klein(p);
     cudaFree(p->d_stage);
+    cudaFree(p->d_fbp);
     for (int k = 0; k < kHostSlots; ++k) {
         if (p->ev_h2d[k]) cudaEventDestroy(p->ev_h2d[k]);
         if (p->ev_comp[k]) cudaEventDestroy(p->ev_comp[k]);
@@ -321,6 +322,19 @@ extern "C" bp_status bp_fbp_fourier(bp_plan *p, const void *sino, bp_dtype dtype
     return launch_fourier(p, sino, dtype, img, batch, (cudaStream_t)stream, 0.f, (int)kind, param);
 }
 
+extern "C" bp_status bp_fbp_direct(bp_plan *p, const void *sino, bp_dtype dtype, float *img, bp_filter_kind kind,
+                                   float param, int batch, void *stream) {
+    set_error("");
+    bp_status st = check_common(p, sino, img, batch);
+    if (st != BP_OK) return st;
+    if (!valid_dtype(dtype)) return fail(BP_ERR_INVALID_ARG, "invalid dtype");
+    if (kind != BP_RAMLAK && kind != BP_SHEPP_LOGAN && kind != BP_TIKHONOV)
+        return fail(BP_ERR_INVALID_ARG, "invalid filter kind");
+    if (kind == BP_TIKHONOV && !(param >= 0.f && std::isfinite(param)))
+        return fail(BP_ERR_INVALID_ARG, "Tikhonov lambda must be finite and >= 0");
+    return launch_fbp_direct(p, sino, dtype, img, (int)kind, param, batch, (cudaStream_t)stream);
+}
+
 extern "C" bp_status bp_backproject_bst(bp_plan *p, const void *sino, bp_dtype dtype, float *img,
                                         int radial_oversampling, int batch, void *stream) {
     set_error("");
@@ -449,9 +463,7 @@ extern "C" bp_status bp_fbp_host(bp_plan *p, const float *sino, float *img, bp_f
         BP_HOST_TRY(cudaEventRecord(p->ev_h2d[k], p->s_h2d));
         BP_HOST_TRY(cudaStreamWaitEvent(s, p->ev_h2d[k], 0));
         if (i >= S) BP_HOST_TRY(cudaStreamWaitEvent(s, p->ev_d2h[k], 0));
-        st = bp_filter(p, d_sino, BP_F32, d_sino, kind, param, 1, stream);
-        if (st != BP_OK) return drain(st);
-        st = bp_backproject_direct(p, d_sino, BP_F32, d_img, 1, 0, stream);
+        st = bp_fbp_direct(p, d_sino, BP_F32, d_img, kind, param, 1, stream);
         if (st != BP_OK) return drain(st);
         BP_HOST_TRY(cudaEventRecord(p->ev_comp[k], s));
         BP_HOST_TRY(cudaStreamWaitEvent(p->s_d2h, p->ev_comp[k], 0));

@@ -65,6 +65,8 @@ def test_calls_reject_null_plan(lib):
     assert lib.bp_backproject_fourier(None, None, 0, None, 1, None) == 1
     assert lib.bp_radon(None, None, None, 1, 0, None) == 1
     assert lib.bp_fbp_host(None, None, None, 0, 0.0, 1, None) == 1
+    assert lib.bp_fbp_direct(None, None, 0, None, 0, 0.0, 1, None) == 1
+    assert lib.bp_fbp_fourier(None, None, 0, None, 0, 0.0, 1, None) == 1
     assert lib.bp_backproject_batched(None, None, None, None, 0, None) == 1
     assert "NULL" in lib.bp_last_error().decode()
     lib.bp_destroy(None)  # no-op

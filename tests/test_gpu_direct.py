@@ -436,3 +436,70 @@ def test_direct_four_image_form_not_taken_without_symmetry():
         img, names = _kernels(plan, lambda: plan.backproject(g))
         assert "bp_direct_klein_kernel" not in names and any(n.startswith("bp_direct") for n in names), names
         assert oracle.rel_l2(img.cpu().numpy(), oracle.bp_linear(rounded(g), N, theta, plan.det_spacing)) <= TOL_DIRECT
+
+
+# ----------------------------------------------------------------------------------- fused FBP, direct form
+@pytest.mark.parametrize("N,n_det,n_theta,angles,kind,param,seed", [
+    (256, 256, 180, "uniform", "shepp-logan", 0.0, 40),      # P = 512
+    (300, 300, 61, "uniform", "ramlak", 0.0, 41),             # odd n_theta: the last pair holds one row
+    (1024, 1100, 40, "whole-circle", "tikhonov", 0.05, 42),   # P = 4096, rows read backwards
+    (100, 128, 16, "mirror", "shepp-logan", 0.0, 43),         # P = 256: filtered array path
+    (64, 64, 40, "random", "shepp-logan", 0.0, 44),           # no mirror partners: filtered array path
+    (130, 300, 61, "uniform", "ramlak", 0.0, 45),             # pixels larger than bins: filtered array path
+    (64, 2100, 20, "uniform", "ramlak", 0.0, 46)])            # P = 8192: filtered array path
+def test_fbp_direct_matches_filter_then_backproject(N, n_det, n_theta, angles, kind, param, seed):
+    # the fused form (the filter writes the four-image tables and clears the image) where the
+    # four-image form runs (N even, mirror-symmetric angles, pixels no larger than bins) and
+    # 512 <= P <= 4096, else filter into the plan's array and backproject; either way the image
+    # of filter() then backproject(), and the oracle's
+    rng = np.random.default_rng(seed)
+    if angles == "uniform":
+        theta = synth.uniform_theta(n_theta)
+    elif angles == "random":
+        theta = random_theta(rng, n_theta)
+    else:
+        theta = _mirror_set(rng, n_theta, angles == "whole-circle")
+    plan = bp.Plan(N, n_det, theta, 1.1 * 2.0 / n_det)
+    g = to_dev(rng.normal(size=(3, len(theta), n_det)))
+    P = 1 << int(np.ceil(np.log2(2 * n_det)))
+    fused = 512 <= P <= 4096 and angles != "random" and 2.0 / N <= plan.det_spacing
+    img, names = _kernels(plan, lambda: plan.fbp_direct(g[0], kind, param))
+    if fused:
+        assert "klein_filter_tables_kernel" in names and "bp_direct_klein_kernel" in names, names
+        assert not any(n.startswith(("filter", "memset", "klein_tables")) for n in names), names
+    else:
+        assert "klein_filter_tables_kernel" not in names and any(n.startswith("filter") for n in names), names
+    q = plan.filter(g[0], kind, param)
+    two = plan.backproject(q)
+    assert oracle.rel_l2(img.cpu().numpy(), two.cpu().numpy()) <= 1e-6  # atomic summation order
+    # R* of the same filtered rows (the fused filter's values are bp_filter's) against the oracle,
+    # and the whole FBP against the oracle's filter and R*: within the sum of the filter's and
+    # R*'s float32 tolerances
+    assert oracle.rel_l2(img.cpu().numpy(), oracle.bp_linear(rounded(q), N, theta, plan.det_spacing)) <= TOL_DIRECT
+    fk = {"ramlak": oracle.RAMLAK, "shepp-logan": oracle.SHEPP_LOGAN, "tikhonov": oracle.TIKHONOV}[kind]
+    ref = oracle.bp_linear(oracle.filter_rows(rounded(g[0]), plan.det_spacing, fk, param), N, theta,
+                           plan.det_spacing)
+    assert oracle.rel_l2(img.cpu().numpy(), ref) <= 2 * TOL_DIRECT
+    # into a buffer holding garbage (the clear inside the table launch), a batch (slice by slice
+    # through the tables) and 16-bit storage
+    dirty = torch.full_like(img, 7.0)
+    plan.fbp_direct(g[0], kind, param, out=dirty)
+    assert oracle.rel_l2(dirty.cpu().numpy(), img.cpu().numpy()) <= 1e-6
+    imgs = plan.fbp_direct(g, kind, param)
+    for i in range(3):
+        ri = plan.backproject(plan.filter(g[i].clone(), kind, param))
+        assert oracle.rel_l2(imgs[i].cpu().numpy(), ri.cpu().numpy()) <= 1e-6, i
+    g16 = g[:2].to(torch.float16)
+    i16 = plan.fbp_direct(g16, kind, param)
+    r16 = plan.backproject(plan.filter(g16, kind, param))
+    assert oracle.rel_l2(i16.cpu().numpy(), r16.cpu().numpy()) <= 1e-6
+
+
+def test_fbp_direct_rejects_bad_arguments():
+    plan = bp.Plan(64, 64, synth.uniform_theta(16))
+    g = torch.zeros((16, 64), device=dev())
+    with pytest.raises(bp.BPError, match="lambda"):
+        plan.fbp_direct(g, "tikhonov", -1.0)
+    with pytest.raises(bp.BPError):
+        plan.fbp_direct(g, 7)
+    assert plan.fbp_direct(g, "ramlak").abs().max().item() == 0.0
