@@ -698,8 +698,9 @@ def other_paths(plan, q, img, flush, stream, dev, only=(), peaks=(6778.3, 80.5),
         return res
     guard("slice256_bins256_ang180_shapes", small)
 
-    # volume: 256 slices of 2048^2 from BF16 sinograms; filter and R* captured in one CUDA graph,
-    # the R* launch shape tuned at batch 256
+    # volume: 256 slices of 2048^2 from BF16 sinograms; the fused filtered backprojection (one
+    # launch filters all slices into their row tables, one persistent launch backprojects them)
+    # captured in a CUDA graph, the R* launch shape tuned at batch 256
     def volume():
         V = synth.VOLUME
         n = synth.VOLUME_SLICES
@@ -713,10 +714,9 @@ def other_paths(plan, q, img, flush, stream, dev, only=(), peaks=(6778.3, 80.5),
         shape, _ = pv.autotune("direct", torch.float32, n)
 
         def step():
-            pv.filter(raw, "shepp-logan", out=filt)
-            pv.backproject(filt, out=imgs)
+            pv.fbp_direct(raw, "shepp-logan", out=imgs)
         step()
-        kern = kernel_rooflines(kernel_profile(pv, step, flush, 1), dict(ctx, memset_bytes=4 * n * V.N * V.N,
+        kern = kernel_rooflines(kernel_profile(pv, step, flush, 1), dict(ctx, esz=2, memset_bytes=4 * n * V.N * V.N,
                                                                            batch=n), hbm, fp32)
         s2 = torch.cuda.Stream(dev)
         s2.wait_stream(torch.cuda.current_stream(dev))
@@ -726,6 +726,7 @@ def other_paths(plan, q, img, flush, stream, dev, only=(), peaks=(6778.3, 80.5),
         ms = _timed(graph.replay, stream, flush, 3)
         sl = [0, n - 1]
         got = {i: pick(imgs[i], pix2048) for i in sl}
+        pv.filter(raw, "shepp-logan", out=filt)  # the fused call's filtered values (n_theta even), for the check
         fh = {i: filt[i].double().cpu().numpy() for i in sl}
         rawh = {i: raw[i].double().cpu().numpy() for i in sl}
         launches = sum(v["launches_per_call"] for v in kern.values())
@@ -741,7 +742,8 @@ def other_paths(plan, q, img, flush, stream, dev, only=(), peaks=(6778.3, 80.5),
                                                      "input, all rows")
         checks["volume256_bf16_graph"] = chk
         return {"slices": n, "ms": ms, "Gupdates_s": n * V.updates / ms / 1e6, "storage": "bf16",
-                "step": "bp_filter (all slices, one launch) + bp_backproject_direct (one call) in one CUDA graph",
+                "step": "bp_fbp_direct in one CUDA graph: one launch filters all slices into the four-image "
+                        "form's row tables (and clears the images), one persistent launch backprojects all slices",
                 "launch_shape": {"stage": shape[0], "angle_groups": shape[1], "tuned_at_batch": n},
                 "launches_per_replay": launches, "kernels": kern}
     guard("volume256_bf16_graph", volume)

@@ -141,8 +141,8 @@ struct KleinWork {
     int jlo = 0, L = 0, nr = 0;          // table extent (bins jlo .. jlo + L - 1), regions per side
     std::vector<unsigned char> host;     // per-angle records (KleinAngle)
     void *d_ang = nullptr;
-    float4 *tab = nullptr;
-    unsigned *gbar = nullptr;            // grid-barrier counters of the batched launch
+    float4 *tab = nullptr;               // row tables of tab_slices slices
+    int tab_slices = 0;
 };
 struct RadonShape {
     int kang = 0;   // 0 = the default rule

@@ -24,18 +24,19 @@
 // M_y P); a row's table interleaves the forward and backward entries, so each pair is updated
 // with paired f32x2 instructions whose operands arrive in adjacent registers.
 //
-// Tables.  One launch (klein_tables_kernel) writes each row's entries once per call to a global
-// workspace, over the bins any block can reach.  The main kernel copies 48-entry windows of them
-// (one per plane, row and angle: 768 bytes) into shared memory with cp.async.bulk, three stages
-// of 8 angles in flight, so its block barriers and table builds disappear; the warps take turns
-// issuing the copies of the stage two ahead.
+// Tables.  One launch (klein_tables_kernel, or the row filter of the fused FBP) writes each row's
+// entries once per call to a global workspace, over the bins any block can reach, for a chunk of
+// slices at once (as many as a quarter of the free device memory holds).  The main kernel copies
+// 48-entry windows of them (one per plane, row and angle: 768 bytes) into shared memory with
+// cp.async.bulk, three stages of 8 angles in flight, so its block barriers and table builds
+// disappear; the warps take turns issuing the copies of the stage two ahead.
 //
 // Schedule.  The quadrant is cut into 32 x 32-pixel regions (one 2 x 2 block per thread, 256
 // threads), and the angles (in runs of 32 followed by their 32 partners) into S groups.  A
-// persistent grid sweeps the groups in order; each group's (region, angle) pairs, region-major,
-// are split evenly over all CTAs, so every CTA does the same amount of work and only one group's
-// table rows are in use at a time (they stay in L2).  A CTA adds its partial sums with vector
-// atomic adds whenever it leaves a region.
+// persistent grid sweeps the chunk's slices and, within each, the groups in order; each group's
+// (region, angle) pairs, region-major, are split evenly over all CTAs, so every CTA does the same
+// amount of work and only one group's table rows are in use at a time (they stay in L2).  A CTA
+// adds its partial sums with vector atomic adds whenever it leaves a region.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -53,10 +54,8 @@ namespace {
 
 constexpr int kKRegion = 32;          // region side (pixels)
 constexpr int kKThreads = 256;        // one 2 x 2 block per thread
-constexpr int kKStage = 8;            // angles per shared-memory stage (three stages in flight)
 constexpr int kKW = 48;               // table entries per region window: 31 (|c| + |s|) + 4 <= 48
 constexpr int kKWin = kKW * 16;       // bytes of one window of one plane
-constexpr int kKBufBytes = 4 * kKStage * kKWin;  // one 8-angle stage: two planes of rows k and k' per angle
 constexpr int kKMargin = 4;           // extra table entries beyond the reachable bins
 
 // Table of one row, forward and backward interleaved, in two planes of 16-byte entries: entry
@@ -64,17 +63,18 @@ constexpr int kKMargin = 4;           // extra table entries beyond the reachabl
 // w dg'_{j+1}, w dg_{j+2}, w dg'_{j+2}) in plane 1, g'_j = g_{n_det - 1 - j} the reversed row,
 // dg_j = g_{j+1} - g_j, zero outside the detector: the two images that read a row (forwards and
 // backwards) find their operands in adjacent registers of two 16-byte loads, and the loads of a
-// quarter warp (8 consecutive entries of a plane) are free of bank conflicts.  One CTA per row;
-// the row is staged in shared memory with four zeros on each side.  A plane holds RS >= L + kKW
-// entries, so a window copied from any reachable bin stays inside it; row k's planes start at
-// entry 2 k RS.
+// quarter warp (8 consecutive entries of a plane) are free of bank conflicts.  One CTA per row r
+// of a chunk of slices (angle k = r mod n_theta); the row is staged in shared memory with four
+// zeros on each side.  A plane holds RS >= L + kKW entries, so a window copied from any reachable
+// bin stays inside it; row r's planes start at entry 2 r RS.
 template <typename Tin>
 __global__ void __launch_bounds__(256)
 klein_tables_kernel(const Tin *__restrict__ sino, float4 *__restrict__ tab, const AngleParam *__restrict__ ap,
-                    int n_det, int jlo, int L, int RS, float wuni) {
+                    int n_theta, int n_det, int jlo, int L, int RS, float wuni) {
     extern __shared__ float sg[];  // [n_det + 8]
-    const int k = blockIdx.x;
-    const Tin *row = sino + (long long)k * n_det;
+    const long long r = blockIdx.x;
+    const int k = (int)(r % n_theta);
+    const Tin *row = sino + r * n_det;
     for (int i = threadIdx.x; i < n_det + 8; i += blockDim.x) {
         const int j = i - 4;
         sg[i] = (j >= 0 && j < n_det) ? load_f(row + j) : 0.f;
@@ -82,7 +82,7 @@ klein_tables_kernel(const Tin *__restrict__ sino, float4 *__restrict__ tab, cons
     __syncthreads();
     const float w = wuni > 0.f ? wuni : ap[k].w;
     auto g = [&](int j) { return (j >= -4 && j < n_det + 4) ? sg[j + 4] : 0.f; };
-    float4 *p0 = tab + 2 * (long long)k * RS, *p1 = p0 + RS;
+    float4 *p0 = tab + 2 * r * RS, *p1 = p0 + RS;
     for (int m = threadIdx.x; m < L; m += blockDim.x) {
         const int j = jlo + m, jr = n_det - 1 - j;
         const float a0 = g(j), a1 = g(j + 1), a2 = g(j + 2), a3 = g(j + 3);
@@ -95,21 +95,22 @@ klein_tables_kernel(const Tin *__restrict__ sino, float4 *__restrict__ tab, cons
 // The fused FBP form of the tables: the persistent row filter of filter_pt.cuh turns each row
 // pair into its filtered values in shared memory, and the pair's table entries (the layout of
 // klein_tables_kernel, the same arithmetic on the same values) are written from there, so the
-// filtered sinogram never goes through global memory.  rows = n_theta (one slice).
+// filtered sinogram never goes through global memory.  Rows r of a chunk of slices, angle
+// k = r mod n_theta.
 struct KleinTabOut {
     static constexpr bool kStaged = true;
     float4 *tab;
     const AngleParam *ap;
-    int jlo, L, RS;
+    int n_theta, jlo, L, RS;
     float wuni;
     __device__ __forceinline__ void rows(const float *sg, long long r0, bool has1, int n_det) const {
         for (int h = 0; h < 2; ++h) {
             if (h == 1 && !has1) break;
-            const long long k = r0 + h;
+            const long long r = r0 + h;
             const float *sr = sg + h * (n_det + 8);
-            const float w = wuni > 0.f ? wuni : ap[k].w;
+            const float w = wuni > 0.f ? wuni : ap[r % n_theta].w;
             auto g = [&](int j) { return (j >= -4 && j < n_det + 4) ? sr[j + 4] : 0.f; };
-            float4 *p0 = tab + 2 * k * RS, *p1 = p0 + RS;
+            float4 *p0 = tab + 2 * r * RS, *p1 = p0 + RS;
             for (int m = threadIdx.x; m < L; m += blockDim.x) {
                 const int j = jlo + m, jr = n_det - 1 - j;
                 const float a0 = g(j), a1 = g(j + 1), a2 = g(j + 2), a3 = g(j + 3);
@@ -121,17 +122,17 @@ struct KleinTabOut {
     }
 };
 
-// zero: the slice's image (n4 float4), cleared here for the main kernel's atomic adds (null when
-// it accumulates), in place of a memset launch.
+// rows: the chunk's rows; zero: the chunk's images (n4 float4), cleared here for the main
+// kernel's atomic adds (null when it accumulates), in place of a memset launch.
 template <typename Tin, int LOGP>
 __global__ void __launch_bounds__((1 << LOGP) / kPassE, 1024 / ((1 << LOGP) / kPassE))
 klein_filter_tables_kernel(const Tin *__restrict__ sino, KleinTabOut out, const float *__restrict__ H,
-                           const float2 *__restrict__ twp, int n_theta, int n_det, float4 *__restrict__ zero,
+                           const float2 *__restrict__ twp, long long rows, int n_det, float4 *__restrict__ zero,
                            long long n4) {
     if (zero)
         for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n4; i += (long long)gridDim.x * blockDim.x)
             zero[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-    filter_pt_body<Tin, LOGP>(sino, out, H, twp, (long long)n_theta, n_det);
+    filter_pt_body<Tin, LOGP>(sino, out, H, twp, rows, n_det);
 }
 
 // Add (or store) two horizontally adjacent pixels; x even, so the pair is 8-byte aligned.
@@ -227,7 +228,7 @@ __device__ __forceinline__ void klein_roles(int w, KleinAcc (&acc)[BPT], int &ro
 // One angle for one block and its three images: FAR = 0 per-angle far-corner test, 1 two ramps
 // (|c| + |s| >= 1), 2 three ramps.  A = (q0, c, s, role | dir << 2), O = (|c| - 1, |s| - 1,
 // |c| + |s| - 1, |c| + |s| - 2); tabs[wi]: the first entry of the angle's window in row k's plane
-// 0; row k's plane 1 and row k''s planes 0 and 1 follow kKStage windows apart.
+// 0; row k's plane 1 and row k''s planes 0 and 1 follow STG windows apart.
 template <int FAR, int STG>
 __device__ __forceinline__ void klein_angle(const float4 A, const float4 O, const ulonglong2 *__restrict__ tabs, int wi,
                                             KleinAcc &acc, float fx, float fy) {
@@ -251,11 +252,9 @@ __device__ __forceinline__ void klein_angle(const float4 A, const float4 O, cons
     klein_row<FAR == 1>(b0, b1, acc.b, acc.gb, R2, S1a, S1b, S2a, S2b, S3a, S3b, S3c);
 }
 
-// The CTA's sequence of stages: its share [u0, u1) of the group's (region, angle) pairs,
-// region-major, in stages of at most kKStage angles that never cross a region.
-// The CTA's sequence of stages: for each angle group g in turn (all CTAs sweep the groups in
-// the same order, so only one group's table rows are in use at a time), its share of the
-// group's (region, slot) pairs, region-major, in stages of at most kKStage slots that never
+// The CTA's sequence of stages (of one slice): for each angle group g in turn (all CTAs sweep the
+// groups in the same order, so only one group's table rows are in use at a time), its share of
+// the group's (region, slot) pairs, region-major, in stages of at most STG slots that never
 // cross a region.
 template <int STG>
 struct StageSeq {
@@ -290,82 +289,18 @@ struct StageSeq {
     }
 };
 
-// Grid-wide barrier of a cooperative launch (every CTA resident): bar[0] counts arrivals, bar[1]
-// is the generation.  The wait is bounded (about a second); on expiry it sets *err and returns
-// false, and the caller leaves without issuing further work.
-constexpr unsigned kGridSpinLimit = 1u << 24;
-__device__ bool grid_barrier(unsigned *bar, unsigned nblocks, int *err) {
-    __shared__ int ok_s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        volatile unsigned *gen = bar + 1;
-        const unsigned g = *gen;
-        __threadfence();
-        int ok = 1;
-        if (atomicAdd(bar, 1u) == nblocks - 1) {
-            atomicExch(bar, 0u);
-            __threadfence();
-            atomicAdd(bar + 1, 1u);
-        } else {
-            for (unsigned it = 0; *gen == g; ++it) {
-                if (it >= kGridSpinLimit) {
-                    ok = 0;
-                    atomicExch(err, 1);
-                    break;
-                }
-                __nanosleep(64);
-            }
-        }
-        __threadfence();
-        ok_s = ok;
-    }
-    __syncthreads();
-    return ok_s != 0;
-}
-
-// The row tables of klein_tables_kernel for rows cta, cta + nctas, ... built inside the
-// persistent kernel; sg: shared staging of n_det + 8 floats.
-template <typename Tin>
-__device__ void klein_build_rows(const Tin *__restrict__ sino, float4 *__restrict__ tab,
-                                 const AngleParam *__restrict__ ap, int n_det, int n_theta, int jlo, int L, int RS,
-                                 float wuni, float *sg, int cta, int nctas) {
-    for (int k = cta; k < n_theta; k += nctas) {
-        __syncthreads();  // the previous row's entries are written
-        const Tin *row = sino + (long long)k * n_det;
-        for (int i = threadIdx.x; i < n_det + 8; i += blockDim.x) {
-            const int j = i - 4;
-            sg[i] = (j >= 0 && j < n_det) ? load_f(row + j) : 0.f;
-        }
-        __syncthreads();
-        const float w = wuni > 0.f ? wuni : ap[k].w;
-        auto g = [&](int j) { return (j >= -4 && j < n_det + 4) ? sg[j + 4] : 0.f; };
-        float4 *p0 = tab + 2 * (long long)k * RS, *p1 = p0 + RS;
-        for (int m = threadIdx.x; m < L; m += blockDim.x) {
-            const int j = jlo + m, jr = n_det - 1 - j;
-            const float a0 = g(j), a1 = g(j + 1), a2 = g(j + 2), a3 = g(j + 3);
-            const float b0 = g(jr), b1 = g(jr - 1), b2 = g(jr - 2), b3 = g(jr - 3);
-            p0[m] = make_float4(w * a0, w * b0, w * (a1 - a0), w * (b1 - b0));
-            p1[m] = make_float4(w * (a2 - a1), w * (b2 - b1), w * (a3 - a2), w * (b3 - b2));
-        }
-    }
-    // the tables are read next by bulk copies (the async proxy), the staging buffer is written by
-    // them next: order the generic writes before both
-    asm volatile("fence.proxy.async;" ::: "memory");
-    __threadfence();
-}
-
-// A persistent grid (the schedule in the header).  The warps take turns as producer: after
-// finishing stage s, warp s mod 8 copies the windows of stage s - 1 + NBUF (cp.async.bulk, 768
-// bytes per image) from the row tables of klein_tables_kernel into the buffer of stage s - 1,
-// once every warp has left it.  img is
-// added to atomically (cleared before unless accumulating).  Every wait is bounded: on expiry
-// the kernel sets *err, waits (bounded) for the copies it issued and returns.
-template <typename Tin, int MINB, int NBUF, bool BUILD, int BPT, int STG>
+// A persistent grid (the schedule in the header) over `batch` slices, slice sl's tables at
+// tab + sl tab_stride and its image at img + sl img_stride.  The warps take turns as producer:
+// after finishing stage s, warp s mod 8 copies the windows of stage s - 1 + NBUF (cp.async.bulk,
+// 768 bytes per image) from the row tables into the buffer of stage s - 1, once every warp has
+// left it.  img is added to atomically (cleared before unless accumulating).  Every wait is
+// bounded: on expiry the kernel sets *err, waits (bounded) for the copies it issued and returns.
+// MULTI false: one slice (batch 1), without the slice bookkeeping.
+template <int MINB, int NBUF, int BPT, int STG, bool MULTI>
 __global__ void __launch_bounds__(kKThreads / BPT, MINB)
-bp_direct_klein_kernel(float *__restrict__ img, const KleinAngle *__restrict__ ka, float4 *__restrict__ tab,
-                       const Tin *__restrict__ sino, const AngleParam *__restrict__ ap, float wuni, int N, int n_det,
-                       int n_theta, int RS, int L, int jlo, int nr, int S, int batch, long long img_stride,
-                       long long sino_stride, unsigned *__restrict__ gbar, int *__restrict__ err) {
+bp_direct_klein_kernel(float *__restrict__ img, const KleinAngle *__restrict__ ka, const float4 *__restrict__ tab,
+                       int N, int n_theta, int RS, int jlo, int nr, int S, int batch, long long img_stride,
+                       long long tab_stride, int *__restrict__ err) {
     // [NBUF][row k, row k'][plane 0, 1][STG][kKW] entries of 16 bytes
     extern __shared__ __align__(128) ulonglong2 ktab[];
     __shared__ float4 prmA[NBUF][STG], prmO[NBUF][STG];
@@ -395,13 +330,18 @@ bp_direct_klein_kernel(float *__restrict__ img, const KleinAngle *__restrict__ k
     }
     __syncthreads();
 
-    // the producer's next stage: every warp advances the producer's position; the warp that
-    // issues (`issue`) writes the stage's parameters and copies its windows into buffer b
-    int pstage = 0;
+    // the producer's next stage (of slice psl; the sequence runs on into the next slice without
+    // a break): every warp advances the producer's position; the warp that issues (`issue`)
+    // writes the stage's parameters and copies its windows into buffer b
+    int pstage = 0, psl = 0;
     auto produce = [&](bool issue) -> bool {
         int rg, k0, kn;
         bool last;
-        if (!prod.next(rg, k0, kn, last, S, n_theta, R, cta, nctas)) return false;
+        while (!prod.next(rg, k0, kn, last, S, n_theta, R, cta, nctas)) {
+            if (!MULTI || psl + 1 >= batch) return false;
+            ++psl;
+            prod.enter(0, S, n_theta, R, cta, nctas);
+        }
         const int b = pstage % NBUF;
         ++pstage;
         if (!issue) return true;
@@ -423,8 +363,9 @@ bp_direct_klein_kernel(float *__restrict__ img, const KleinAngle *__restrict__ k
             f2 = af - 1.f >= 0.f;
             prmA[b][kk] = make_float4((float)(Ji - J0) + frac + lo, a.c, a.s, __int_as_float(w));
             prmO[b][kk] = make_float4(ac - 1.f, as - 1.f, af - 1.f, af - 2.f);
-            src0 = tab + 2 * (long long)a.row * RS + (J0 - jlo);
-            src1 = tab + 2 * (long long)kp * RS + (J0 - jlo);
+            const float4 *ts = MULTI ? tab + psl * tab_stride : tab;
+            src0 = ts + 2 * (long long)a.row * RS + (J0 - jlo);
+            src1 = ts + 2 * (long long)kp * RS + (J0 - jlo);
         }
         const bool act = lane < kn;
         const int w0 = __shfl_sync(0xffffffffu, w, 0);
@@ -465,26 +406,23 @@ bp_direct_klein_kernel(float *__restrict__ img, const KleinAngle *__restrict__ k
     };
     int role = 0, dir = 0, cstage = 0, b = 0;
     uint32_t ph = 0;
-    for (int sl = 0; sl < batch; ++sl) {
-    float *const im = img + sl * img_stride;
-    if (BUILD) {
-        // slice sl's row tables, by all CTAs; then every CTA waits until all are written
-        klein_build_rows(sino + sl * sino_stride, tab, ap, n_det, n_theta, jlo, L, RS, wuni,
-                         reinterpret_cast<float *>(ktab), cta, nctas);
-        if (!grid_barrier(gbar, (unsigned)nctas, err)) {
-            ok = false;
-            break;
-        }
-    }
-    cons.enter(0, S, n_theta, R, cta, nctas);
     prod = cons;
 #pragma unroll
     for (int i = 0; i < NBUF; ++i) issued += produce(warp == 0) ? 1 : 0;
     clear();
-    int sst = 0;  // stage index within the slice
+    int sst = 0;  // stages consumed
+    int csl = 0;  // the consumer's slice
+    float *im = img;
     int rg, k0, kn;
     bool last;
-    while (cons.next(rg, k0, kn, last, S, n_theta, R, cta, nctas)) {
+    for (;;) {
+        if (!cons.next(rg, k0, kn, last, S, n_theta, R, cta, nctas)) {
+            if (!MULTI || csl + 1 >= batch) break;
+            ++csl;
+            im = img + csl * img_stride;
+            cons.enter(0, S, n_theta, R, cta, nctas);
+            continue;
+        }
         if (!mbar_wait(fb + 8 * b, ph)) {
             ok = false;
             break;
@@ -588,13 +526,6 @@ bp_direct_klein_kernel(float *__restrict__ img, const KleinAngle *__restrict__ k
             }
             clear();
         }
-    }
-    if (!ok) break;
-    // every CTA has left slice sl (its copies all consumed) before the next slice's tables are built
-    if (BUILD && sl + 1 < batch && !grid_barrier(gbar, (unsigned)nctas, err)) {
-        ok = false;
-        break;
-    }
     }
     if (!ok) {
         // wait (bounded) for the copies still in flight: stages cstage .. issued - 1
@@ -705,10 +636,9 @@ void klein_plan(bp_plan *p) {
 void free_klein(bp_plan *p) {
     cudaFree(p->klein.d_ang);
     cudaFree(p->klein.tab);
-    cudaFree(p->klein.gbar);
     p->klein.d_ang = nullptr;
     p->klein.tab = nullptr;
-    p->klein.gbar = nullptr;
+    p->klein.tab_slices = 0;
 }
 
 // Default angle groups: about one per 96 MB of row tables, so that one group's rows mostly stay
@@ -723,20 +653,23 @@ int klein_clamp_groups(const bp_plan *p, int S) { return std::max(1, std::min(st
 
 namespace {
 
+// Row tables of `n` slices (rows r = 0 .. n n_theta - 1) into the workspace.
 template <typename Tin>
-bp_status klein_tables(bp_plan *p, const Tin *sino, cudaStream_t st, float wuni) {
+bp_status klein_tables(bp_plan *p, const Tin *sino, int n, cudaStream_t st, float wuni) {
     const size_t smem = sizeof(float) * ((size_t)p->n_det + 8);
     auto kern = klein_tables_kernel<Tin>;
     if (smem > 48 * 1024) BP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<p->n_theta, 256, smem, st>>>(sino, p->klein.tab, p->d_ang, p->n_det, p->klein.jlo, p->klein.L,
-                                        p->klein.L + kKW, wuni);
+    kern<<<(unsigned)(n * p->n_theta), 256, smem, st>>>(sino, p->klein.tab, p->d_ang, p->n_theta, p->n_det,
+                                                        p->klein.jlo, p->klein.L, p->klein.L + kKW, wuni);
     BP_CUDA_TRY(cudaGetLastError());
     stage_mark(p, st, "klein_tables_kernel");
     return BP_OK;
 }
 
+// The fused form: the rows of `n` slices filtered (response H) into their tables; their images
+// cleared on the way when `zero` is given.
 template <typename Tin, int LOGP>
-bp_status klein_filter_tables_p(bp_plan *p, const Tin *sino, const float *H, cudaStream_t st, float wuni,
+bp_status klein_filter_tables_p(bp_plan *p, const Tin *sino, int n, const float *H, cudaStream_t st, float wuni,
                                 float *zero) {
     constexpr int NT = (1 << LOGP) / kPassE;
     constexpr size_t smem = filter_pt_smem<LOGP>();
@@ -746,26 +679,59 @@ bp_status klein_filter_tables_p(bp_plan *p, const Tin *sino, const float *H, cud
         BP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         BP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem));
     }
-    const int npairs = (p->n_theta + 1) / 2;
-    const int grid = std::max(1, std::min(npairs, std::max(1, per_sm) * std::max(1, p->sm_count)));
+    const long long rows = (long long)n * p->n_theta, npairs = (rows + 1) / 2;
+    const long long grid = std::max(1LL, std::min(npairs, (long long)std::max(1, per_sm) * std::max(1, p->sm_count)));
     const KleinWork &kw = p->klein;
-    kern<<<grid, NT, smem, st>>>(sino, KleinTabOut{kw.tab, p->d_ang, kw.jlo, kw.L, kw.L + kKW, wuni}, H,
-                                 p->d_twpass, p->n_theta, p->n_det, (float4 *)zero,
-                                 zero ? (long long)p->N * p->N / 4 : 0LL);
+    kern<<<(unsigned)grid, NT, smem, st>>>(sino, KleinTabOut{kw.tab, p->d_ang, p->n_theta, kw.jlo, kw.L, kw.L + kKW,
+                                                             wuni},
+                                           H, p->d_twpass, rows, p->n_det, (float4 *)zero,
+                                           zero ? (long long)n * p->N * p->N / 4 : 0LL);
     BP_CUDA_TRY(cudaGetLastError());
     stage_mark(p, st, "klein_filter_tables_kernel");
     return BP_OK;
 }
 
 template <typename Tin>
-bp_status klein_filter_tables(bp_plan *p, const Tin *sino, const float *H, cudaStream_t st, float wuni,
+bp_status klein_filter_tables(bp_plan *p, const Tin *sino, int n, const float *H, cudaStream_t st, float wuni,
                               float *zero) {
     switch (ilog2(p->P)) {
-        case 9: return klein_filter_tables_p<Tin, 9>(p, sino, H, st, wuni, zero);
-        case 10: return klein_filter_tables_p<Tin, 10>(p, sino, H, st, wuni, zero);
-        case 11: return klein_filter_tables_p<Tin, 11>(p, sino, H, st, wuni, zero);
-        default: return klein_filter_tables_p<Tin, 12>(p, sino, H, st, wuni, zero);
+        case 9: return klein_filter_tables_p<Tin, 9>(p, sino, n, H, st, wuni, zero);
+        case 10: return klein_filter_tables_p<Tin, 10>(p, sino, n, H, st, wuni, zero);
+        case 11: return klein_filter_tables_p<Tin, 11>(p, sino, n, H, st, wuni, zero);
+        default: return klein_filter_tables_p<Tin, 12>(p, sino, n, H, st, wuni, zero);
     }
+}
+
+// Slices whose tables the workspace holds at once for a call of `batch` slices: all of them
+// while they take at most a quarter of the device memory free when the workspace grows, else
+// as many as that quarter holds (at least one).  The workspace grows (after a synchronisation
+// of the stream) when a call needs more slices than it holds and the budget allows.
+bp_status klein_reserve(bp_plan *p, int batch, cudaStream_t st, int *chunk) {
+    KleinWork &kw = p->klein;
+    const size_t per = 2 * sizeof(float4) * (size_t)p->n_theta * (size_t)(kw.L + kKW);
+    if (kw.tab && batch <= kw.tab_slices) {
+        *chunk = batch;
+        return BP_OK;
+    }
+    size_t free_b = 0, total_b = 0;
+    BP_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+    const size_t have = kw.tab ? per * (size_t)kw.tab_slices : 0;
+    const size_t budget = (free_b + have) / 4;
+    const int fit = (int)std::min<size_t>((size_t)batch, std::max<size_t>(1, budget / per));
+    if (kw.tab && fit <= kw.tab_slices) {
+        *chunk = kw.tab_slices;
+        return BP_OK;
+    }
+    if (kw.tab) {
+        BP_CUDA_TRY(cudaStreamSynchronize(st));  // no queued launch may still read the old tables
+        cudaFree(kw.tab);
+        kw.tab = nullptr;
+        kw.tab_slices = 0;
+    }
+    BP_CUDA_TRY(cudaMalloc(&kw.tab, per * (size_t)fit));
+    kw.tab_slices = fit;
+    *chunk = fit;
+    return BP_OK;
 }
 
 template <typename Tin, int MINB, int NBUF, int BPT, int STG>
@@ -776,70 +742,51 @@ bp_status launch_klein_t(bp_plan *p, const Tin *sino, float *img, int batch, int
     if (!kw.d_ang) {
         BP_CUDA_TRY(cudaMalloc(&kw.d_ang, kw.host.size()));
         BP_CUDA_TRY(cudaMemcpy(kw.d_ang, kw.host.data(), kw.host.size(), cudaMemcpyHostToDevice));
-        BP_CUDA_TRY(cudaMalloc(&kw.gbar, 2 * sizeof(unsigned)));
     }
     const int RS = kw.L + kKW;
-    if (!kw.tab) BP_CUDA_TRY(cudaMalloc(&kw.tab, 2 * sizeof(float4) * (size_t)p->n_theta * RS));  // two planes
     S = klein_clamp_groups(p, S);
     constexpr size_t smem = (size_t)NBUF * 4 * STG * kKWin;
-    if ((size_t)(p->n_det + 8) * sizeof(float) > smem)
-        return fail(BP_ERR_UNSUPPORTED, "direct R*: detector row too long for the four-image form");
+    if ((size_t)(p->n_det + 8) * sizeof(float) > 200u * 1024u)
+        return fail(BP_ERR_UNSUPPORTED, "direct R*: detector row too long for the four-image form's tables");
+    int chunk = 1;
+    bp_status s = klein_reserve(p, batch, st, &chunk);
+    if (s != BP_OK) return s;
     const size_t img_n = (size_t)p->N * p->N, sino_n = (size_t)p->n_theta * p->n_det;
+    const long long tab_stride = 2LL * p->n_theta * RS;
     stage_begin(p, st);
-    // the fused FBP form clears each slice's image inside its table launch (N even: N^2 / 4 float4)
+    // the fused FBP form clears the images inside its table launch (N even: N^2 / 4 float4)
     const bool clear_in_tables = H && !accumulate && aligned16(img) && img_n % 4 == 0;
     if (!accumulate && !clear_in_tables) {
         BP_CUDA_TRY(cudaMemsetAsync(img, 0, sizeof(float) * img_n * batch, st));
         stage_mark(p, st, "memset (direct R* image)");
     }
-    const KleinAngle *ka = (const KleinAngle *)kw.d_ang;
-    if (batch == 1 || H) {
-        // slice by slice: the tables by their own launch (filtered on the way when H is given),
-        // then the main kernel
-        auto kern = bp_direct_klein_kernel<float, MINB, NBUF, false, BPT, STG>;
-        static int per_sm = 0;
-        if (!per_sm) {
-            BP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            BP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem));
-        }
-        const int grid = std::max(1, per_sm) * std::max(1, p->sm_count);
-        for (int b = 0; b < batch; ++b) {
-            const Tin *sb = sino + sino_n * b;
-            bp_status s = H ? klein_filter_tables(p, sb, H, st, wuni, clear_in_tables ? img + img_n * b : nullptr)
-                            : klein_tables(p, sb, st, wuni);
-            if (s != BP_OK) return s;
-            kern<<<grid, NT, smem, st>>>(img + img_n * b, ka, kw.tab, nullptr, p->d_ang, wuni, p->N, p->n_det,
-                                         p->n_theta, RS, kw.L, kw.jlo, kw.nr, S, 1, 0, 0, kw.gbar, p->d_err);
-            BP_CUDA_TRY(cudaGetLastError());
-            stage_mark(p, st, "bp_direct_klein_kernel");
-        }
-        return BP_OK;
-    }
-    // a batch: one cooperative persistent launch; each slice's tables are built inside it, between
-    // grid-wide barriers
-    auto kern = bp_direct_klein_kernel<Tin, MINB, NBUF, true, BPT, STG>;
+    auto kern1 = bp_direct_klein_kernel<MINB, NBUF, BPT, STG, false>;
+    auto kernm = bp_direct_klein_kernel<MINB, NBUF, BPT, STG, true>;
     static int per_sm = 0;
     if (!per_sm) {
-        BP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        BP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem));
+        BP_CUDA_TRY(cudaFuncSetAttribute(kern1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        BP_CUDA_TRY(cudaFuncSetAttribute(kernm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int pm = 0;
+        BP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern1, NT, smem));
+        BP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pm, kernm, NT, smem));
+        per_sm = std::max(1, std::min(per_sm, pm));
     }
-    const int grid = std::max(1, per_sm) * std::max(1, p->sm_count);
-    BP_CUDA_TRY(cudaMemsetAsync(kw.gbar, 0, 2 * sizeof(unsigned), st));
-    float *a_img = img;
-    const KleinAngle *a_ka = ka;
-    float4 *a_tab = kw.tab;
-    const Tin *a_sino = sino;
-    const AngleParam *a_ap = p->d_ang;
-    float a_wuni = wuni;
-    int a_N = p->N, a_nd = p->n_det, a_nt = p->n_theta, a_RS = RS, a_L = kw.L, a_jlo = kw.jlo, a_nr = kw.nr,
-        a_S = S, a_batch = batch;
-    long long a_is = (long long)img_n, a_ss = (long long)sino_n;
-    unsigned *a_gbar = kw.gbar;
-    int *a_err = p->d_err;
-    void *args[] = {&a_img, &a_ka, &a_tab, &a_sino, &a_ap, &a_wuni, &a_N, &a_nd, &a_nt, &a_RS, &a_L, &a_jlo,
-                    &a_nr, &a_S, &a_batch, &a_is, &a_ss, &a_gbar, &a_err};
-    BP_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)kern, dim3(grid), dim3(NT), args, smem, st));
-    stage_mark(p, st, "bp_direct_klein_batch_kernel");
+    const int grid = per_sm * std::max(1, p->sm_count);
+    const KleinAngle *ka = (const KleinAngle *)kw.d_ang;
+    // chunk by chunk: the chunk's tables by one launch (filtered on the way when H is given),
+    // then one persistent launch over the chunk's slices
+    for (int c0 = 0; c0 < batch; c0 += chunk) {
+        const int cn = std::min(chunk, batch - c0);
+        const Tin *sc = sino + sino_n * c0;
+        float *ic = img + img_n * c0;
+        s = H ? klein_filter_tables(p, sc, cn, H, st, wuni, clear_in_tables ? ic : nullptr)
+              : klein_tables(p, sc, cn, st, wuni);
+        if (s != BP_OK) return s;
+        (cn > 1 ? kernm : kern1)<<<grid, NT, smem, st>>>(ic, ka, kw.tab, p->N, p->n_theta, RS, kw.jlo, kw.nr, S, cn,
+                                                         (long long)img_n, tab_stride, p->d_err);
+        BP_CUDA_TRY(cudaGetLastError());
+        stage_mark(p, st, cn > 1 ? "bp_direct_klein_batch_kernel" : "bp_direct_klein_kernel");
+    }
     return BP_OK;
 }
 

@@ -446,7 +446,7 @@ def test_direct_four_image_form_not_taken_without_symmetry():
     (100, 128, 16, "mirror", "shepp-logan", 0.0, 43),         # P = 256: filtered array path
     (64, 64, 40, "random", "shepp-logan", 0.0, 44),           # no mirror partners: filtered array path
     (130, 300, 61, "uniform", "ramlak", 0.0, 45),             # pixels larger than bins: filtered array path
-    (64, 2100, 20, "uniform", "ramlak", 0.0, 46)])            # P = 8192: filtered array path
+    (2048, 2100, 20, "uniform", "ramlak", 0.0, 46)])          # P = 8192: filtered array path
 def test_fbp_direct_matches_filter_then_backproject(N, n_det, n_theta, angles, kind, param, seed):
     # the fused form (the filter writes the four-image tables and clears the image) where the
     # four-image form runs (N even, mirror-symmetric angles, pixels no larger than bins) and
@@ -460,7 +460,10 @@ def test_fbp_direct_matches_filter_then_backproject(N, n_det, n_theta, angles, k
     else:
         theta = _mirror_set(rng, n_theta, angles == "whole-circle")
     plan = bp.Plan(N, n_det, theta, 1.1 * 2.0 / n_det)
-    g = to_dev(rng.normal(size=(3, len(theta), n_det)))
+    # sinograms shaped like the workloads: seeded ellipse phantoms plus 1 % Gaussian noise
+    g = to_dev(np.stack([synth.add_gaussian_noise(synth.ellipse_sinogram(synth.random_ellipses(10, seed + i), theta,
+                                                                         n_det, plan.det_spacing), 0.01, seed + i)
+                         for i in range(3)]))
     P = 1 << int(np.ceil(np.log2(2 * n_det)))
     fused = 512 <= P <= 4096 and angles != "random" and 2.0 / N <= plan.det_spacing
     img, names = _kernels(plan, lambda: plan.fbp_direct(g[0], kind, param))
@@ -480,15 +483,18 @@ def test_fbp_direct_matches_filter_then_backproject(N, n_det, n_theta, angles, k
     ref = oracle.bp_linear(oracle.filter_rows(rounded(g[0]), plan.det_spacing, fk, param), N, theta,
                            plan.det_spacing)
     assert oracle.rel_l2(img.cpu().numpy(), ref) <= 2 * TOL_DIRECT
-    # into a buffer holding garbage (the clear inside the table launch), a batch (slice by slice
-    # through the tables) and 16-bit storage
+    # into a buffer holding garbage (the clear inside the table launch), a batch (one table launch
+    # and one persistent launch for all slices; rows are filtered in pairs across the batch, as
+    # bp_filter pairs them) and 16-bit storage
     dirty = torch.full_like(img, 7.0)
     plan.fbp_direct(g[0], kind, param, out=dirty)
     assert oracle.rel_l2(dirty.cpu().numpy(), img.cpu().numpy()) <= 1e-6
-    imgs = plan.fbp_direct(g, kind, param)
+    imgs, bnames = _kernels(plan, lambda: plan.fbp_direct(g, kind, param))
+    if fused:
+        assert "bp_direct_klein_batch_kernel" in bnames and "klein_filter_tables_kernel" in bnames, bnames
+    refs = plan.backproject(plan.filter(g, kind, param))
     for i in range(3):
-        ri = plan.backproject(plan.filter(g[i].clone(), kind, param))
-        assert oracle.rel_l2(imgs[i].cpu().numpy(), ri.cpu().numpy()) <= 1e-6, i
+        assert oracle.rel_l2(imgs[i].cpu().numpy(), refs[i].cpu().numpy()) <= 1e-6, i
     g16 = g[:2].to(torch.float16)
     i16 = plan.fbp_direct(g16, kind, param)
     r16 = plan.backproject(plan.filter(g16, kind, param))
