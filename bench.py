@@ -1,7 +1,8 @@
 """Benchmark: filtered backprojection of one 2048^2 slice (2048 bins, 1800 angles) on GB300.
 
-One step = the hot path over one synthetic slice: Shepp-Logan row filter (bp_filter)
-followed by the direct pixel-driven R* (bp_backproject_direct), both through the C ABI.
+One step = the hot path over one synthetic slice through the C ABI: bp_fbp_direct, the
+Shepp-Logan row filter (its filtered rows written straight into the row tables of the
+four-image direct R*) followed by the direct pixel-driven R*.
 Metric: backprojection pixel-angle updates per second (N^2 * n_theta per step), in G/s.
 
 Prints ONE JSON line on rank 0.  `e2e` is the same metric through bp_fbp_host from pinned
