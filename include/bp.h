@@ -223,6 +223,19 @@ bp_status bp_backproject_logpolar_partial(bp_plan *plan, const void *sino, bp_dt
 bp_status bp_set_fourier_width(bp_plan *plan, int width);
 
 /*
+ * bp_set_direct_workspace -- upper bound (bytes) on the four-image direct R*'s row-table
+ * workspace (Section 2 eq "bp_app"; the tables hold each row's weighted samples and their
+ * differences, 32 bytes per reachable bin and angle, about 146 MB per 2048^2 x 1800 slice).
+ * A batch of one geometry writes the tables of as many slices as the workspace holds with one
+ * launch and backprojects them with one persistent launch, chunk after chunk; one slice's
+ * tables are always allocated, whatever the bound.  0 (the default) = a quarter of the device
+ * memory free when the workspace grows.  Takes effect at the next call that grows or shrinks
+ * the workspace: the plan's current tables are released here (after a device
+ * synchronisation) when they exceed the new bound.  BP_ERR_INVALID_ARG for a NULL plan.
+ */
+bp_status bp_set_direct_workspace(bp_plan *plan, unsigned long long bytes);
+
+/*
  * bp_fbp_fourier -- filtered backprojection in the Fourier form: the filter `kind` (param =
  * Tikhonov lambda, else ignored) applied inside the projection transforms of
  * bp_backproject_fourier (Section 3 Remark 1 (ii) eq "fbp" with Section 5.3 Step 2.2: one

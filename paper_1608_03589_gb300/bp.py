@@ -26,7 +26,7 @@ _DTYPES = {torch.float32: BP_F32, torch.bfloat16: BP_BF16, torch.float16: BP_F16
 # Every symbol the header declares (checked by the ABI test).
 SYMBOLS = ("bp_plan_create", "bp_destroy", "bp_filter", "bp_backproject_direct", "bp_backproject_fourier",
            "bp_radon", "bp_fbp_host", "bp_fbp_fourier", "bp_fbp_direct", "bp_backproject_bst",
-           "bp_backproject_bst_windowed", "bp_backproject_logpolar", "bp_backproject_logpolar_partial", "bp_set_fourier_width", "bp_backproject_batched", "bp_fbp_static", "bp_check", "bp_radon_transpose",
+           "bp_backproject_bst_windowed", "bp_backproject_logpolar", "bp_backproject_logpolar_partial", "bp_set_fourier_width", "bp_set_direct_workspace", "bp_backproject_batched", "bp_fbp_static", "bp_check", "bp_radon_transpose",
            "bp_backproject_transpose", "bp_autotune", "bp_get_shape", "bp_set_shape", "bp_tune_cache_save",
            "bp_tune_cache_load", "bp_stage_timing", "bp_stage_times", "bp_last_error", "bp_version")
 OPS = {"direct": 0, "radon": 1}
@@ -66,6 +66,7 @@ def lib() -> ctypes.CDLL:
             L.bp_backproject_logpolar.argtypes = [vp, vp, i, vp, i, vp]
             L.bp_backproject_logpolar_partial.argtypes = [vp, vp, i, vp, i, f, i, vp]
             L.bp_set_fourier_width.argtypes = [vp, i]
+            L.bp_set_direct_workspace.argtypes = [vp, ctypes.c_ulonglong]
             L.bp_check.argtypes = [vp, vp]
             L.bp_radon_transpose.argtypes = [vp, vp, vp, i, i, vp]
             L.bp_backproject_transpose.argtypes = [vp, vp, vp, i, i, vp]
@@ -82,7 +83,7 @@ def lib() -> ctypes.CDLL:
             for name in ("bp_filter", "bp_backproject_direct", "bp_backproject_fourier", "bp_radon",
                          "bp_fbp_host", "bp_fbp_fourier", "bp_fbp_direct", "bp_backproject_bst", "bp_backproject_bst_windowed",
                          "bp_backproject_logpolar", "bp_backproject_logpolar_partial",
-                         "bp_set_fourier_width",
+                         "bp_set_fourier_width", "bp_set_direct_workspace",
                          "bp_backproject_batched", "bp_fbp_static",
                          "bp_check",
                          "bp_radon_transpose", "bp_backproject_transpose", "bp_autotune", "bp_get_shape",
@@ -275,6 +276,12 @@ class Plan:
         """Kaiser-Bessel width (6 or 4 grid cells) of the Fourier path's gridding."""
         with torch.cuda.device(self.device):
             _check(lib().bp_set_fourier_width(self.handle, int(width)), "bp_set_fourier_width")
+
+    def set_direct_workspace(self, nbytes: int) -> None:
+        """Upper bound in bytes on the four-image direct R*'s row-table workspace (0: a quarter
+        of the free device memory); batches beyond it run in chunks."""
+        with torch.cuda.device(self.device):
+            _check(lib().bp_set_direct_workspace(self.handle, int(nbytes)), "bp_set_direct_workspace")
 
     def fbp_fourier(self, sino: torch.Tensor, kind: str | int = "ramlak", param: float = 0.0,
                     out: torch.Tensor | None = None) -> torch.Tensor:

@@ -143,6 +143,7 @@ struct KleinWork {
     void *d_ang = nullptr;
     float4 *tab = nullptr;               // row tables of tab_slices slices
     int tab_slices = 0;
+    size_t tab_limit = 0;                // bp_set_direct_workspace (0: a quarter of the free memory)
 };
 struct RadonShape {
     int kang = 0;   // 0 = the default rule
@@ -263,6 +264,7 @@ int klein_default_groups(const bp_plan *p);
 int klein_clamp_groups(const bp_plan *p, int S);
 bp_status launch_direct_klein(bp_plan *p, const void *sino, bp_dtype dt, float *img, int batch, int accumulate,
                               cudaStream_t st, float wuni, int stage, int S, const float *H = nullptr);
+bp_status klein_set_workspace(bp_plan *p, size_t bytes);
 bp_status launch_fbp_direct(bp_plan *p, const void *sino, bp_dtype dt, float *img, int kind, float param, int batch,
                             cudaStream_t st);
 void free_fourier(bp_plan *p);

@@ -702,21 +702,46 @@ bp_status klein_filter_tables(bp_plan *p, const Tin *sino, int n, const float *H
     }
 }
 
+size_t klein_slice_bytes(const bp_plan *p) {
+    return 2 * sizeof(float4) * (size_t)p->n_theta * (size_t)(p->klein.L + kKW);
+}
+
+}  // namespace
+
+// bp_set_direct_workspace: the new bound; tables above it are released now.
+bp_status klein_set_workspace(bp_plan *p, size_t bytes) {
+    KleinWork &kw = p->klein;
+    kw.tab_limit = bytes;
+    if (kw.tab && bytes && klein_slice_bytes(p) * (size_t)kw.tab_slices > bytes) {
+        BP_CUDA_TRY(cudaDeviceSynchronize());  // no call of this plan may still read the tables
+        cudaFree(kw.tab);
+        kw.tab = nullptr;
+        kw.tab_slices = 0;
+    }
+    return BP_OK;
+}
+
+namespace {
+
 // Slices whose tables the workspace holds at once for a call of `batch` slices: all of them
-// while they take at most a quarter of the device memory free when the workspace grows, else
-// as many as that quarter holds (at least one).  The workspace grows (after a synchronisation
-// of the stream) when a call needs more slices than it holds and the budget allows.
+// while they fit the budget (the bp_set_direct_workspace bound, else a quarter of the device
+// memory free when the workspace grows), else as many as the budget holds (at least one).  The
+// workspace grows (after a synchronisation of the stream) when a call needs more slices than
+// it holds and the budget allows.
 bp_status klein_reserve(bp_plan *p, int batch, cudaStream_t st, int *chunk) {
     KleinWork &kw = p->klein;
-    const size_t per = 2 * sizeof(float4) * (size_t)p->n_theta * (size_t)(kw.L + kKW);
+    const size_t per = klein_slice_bytes(p);
     if (kw.tab && batch <= kw.tab_slices) {
         *chunk = batch;
         return BP_OK;
     }
-    size_t free_b = 0, total_b = 0;
-    BP_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
     const size_t have = kw.tab ? per * (size_t)kw.tab_slices : 0;
-    const size_t budget = (free_b + have) / 4;
+    size_t budget = kw.tab_limit;
+    if (!budget) {
+        size_t free_b = 0, total_b = 0;
+        BP_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+        budget = (free_b + have) / 4;
+    }
     const int fit = (int)std::min<size_t>((size_t)batch, std::max<size_t>(1, budget / per));
     if (kw.tab && fit <= kw.tab_slices) {
         *chunk = kw.tab_slices;

@@ -380,6 +380,13 @@ extern "C" bp_status bp_backproject_logpolar_partial(bp_plan *p, const void *sin
     return launch_logpolar_partial(p, sino, dtype, img, batch, sectors, a_r, (cudaStream_t)stream);
 }
 
+extern "C" bp_status bp_set_direct_workspace(bp_plan *p, unsigned long long bytes) {
+    set_error("");
+    bp_status st = check_plan(p);
+    if (st != BP_OK) return st;
+    return klein_set_workspace(p, (size_t)bytes);
+}
+
 extern "C" bp_status bp_set_fourier_width(bp_plan *p, int width) {
     set_error("");
     bp_status st = check_plan(p);

@@ -509,3 +509,48 @@ def test_fbp_direct_rejects_bad_arguments():
     with pytest.raises(bp.BPError):
         plan.fbp_direct(g, 7)
     assert plan.fbp_direct(g, "ramlak").abs().max().item() == 0.0
+
+
+def _table_bytes_per_slice(N, n_det, theta, dt):
+    """About the four-image form's row-table bytes per slice: 2 planes x 16 B x (reachable bins + 4
+    on each side + 48) per angle (restated from the layout; only used to pick workspace bounds)."""
+    r = (2.0 / N) / dt
+    E = 32 * ((N // 2 + 31) // 32) - 1
+    c, s = np.cos(theta) * r, np.sin(theta) * r
+    u00 = (c + s) * (0.5 - 0.5 * N) + 0.5 * (n_det - 1)
+    lo = u00 + np.minimum(0, c * E) + np.minimum(0, s * E)
+    hi = u00 + np.maximum(0, c * E) + np.maximum(0, s * E)
+    L = int(np.floor(hi.max()) + 4 - (np.floor(lo.min()) - 4) + 1)
+    return 32 * len(theta) * (L + 48)
+
+
+def test_direct_batch_in_chunks():
+    # a workspace bound smaller than the batch: the slices go through in chunks (one table launch
+    # and one persistent launch each), with the result of the single-chunk call
+    N, n_det = 256, 256
+    theta = synth.uniform_theta(90)
+    plan = bp.Plan(N, n_det, theta)
+    rng = np.random.default_rng(50)
+    g = to_dev(np.stack([synth.add_gaussian_noise(synth.ellipse_sinogram(synth.random_ellipses(10, 50 + i), theta,
+                                                                         n_det, plan.det_spacing), 0.01, 50 + i)
+                         for i in range(5)]))
+    whole, names = _kernels(plan, lambda: plan.backproject(g))
+    assert "bp_direct_klein_batch_kernel" in names and "bp_direct_klein_kernel" not in names, names
+    fbp_whole = plan.fbp_direct(g, "shepp-logan")
+    per = _table_bytes_per_slice(N, n_det, theta, plan.det_spacing)
+    for bound, want in ((1, {"bp_direct_klein_kernel"}), (int(2.5 * per), {"bp_direct_klein_batch_kernel",
+                                                                         "bp_direct_klein_kernel"})):
+        plan.set_direct_workspace(bound)  # chunks of 1, then of 2, 2, 1
+        img, names = _kernels(plan, lambda: plan.backproject(g))
+        assert want == {n for n in names if n.startswith("bp_direct")}, (bound, names)
+        for i in range(5):
+            assert oracle.rel_l2(img[i].cpu().numpy(), whole[i].cpu().numpy()) <= 1e-6, (bound, i)
+        acc = whole.clone()
+        plan.backproject(g, out=acc, accumulate=True)
+        assert oracle.rel_l2(acc.cpu().numpy(), 2 * whole.cpu().numpy()) <= 1e-6, bound
+        fimg = plan.fbp_direct(g, "shepp-logan")
+        for i in range(5):
+            assert oracle.rel_l2(fimg[i].cpu().numpy(), fbp_whole[i].cpu().numpy()) <= 1e-6, (bound, i)
+    plan.set_direct_workspace(0)
+    ref = oracle.bp_linear(rounded(g[4]), N, theta, plan.det_spacing)
+    assert oracle.rel_l2(plan.backproject(g)[4].cpu().numpy(), ref) <= TOL_DIRECT
