@@ -773,7 +773,8 @@ def other_paths(plan, q, img, flush, stream, dev, only=(), peaks=(6778.3, 80.5),
                 "err_vs_fp64": {"not_measured": "iterative; its operators are checked against the oracle by the tests"}}
     guard("tv_reconstruction_8x1024", tv)
 
-    # uneven batch: 64 slices, widths in {512..4096}, 360-3000 angles, FP16, one persistent launch
+    # uneven batch: 64 slices, widths in {512..4096}, 360-3000 angles, FP16: one launch writes every
+    # slice's row tables, one persistent four-image launch backprojects all slices
     def mixed():
         geo = synth.mixed_batch_geometries()
         plans, sinos, imgs2 = [], [], []
@@ -788,6 +789,11 @@ def other_paths(plan, q, img, flush, stream, dev, only=(), peaks=(6778.3, 80.5),
             imgs2.append(torch.empty((N, N), dtype=torch.float32, device=dev))
             upd += N * N * nt
         ms = _timed(lambda: bp.backproject_batched(plans, sinos, imgs2), stream, flush, 3)
+        kern = kernel_profile(plans[0], lambda: bp.backproject_batched(plans, sinos, imgs2), flush, 1)
+        for name, t in kern.items():  # the whole batch's algorithmic work (7 flops per update)
+            if name.startswith("bp_direct") and t["ms"] > 0:
+                t.update({"flops": 7 * upd, "bound": "alu", "achieved": 7 * upd / (t["ms"] / 1e3) / 1e12,
+                          "peak": fp32, "unit": "TFLOP/s", "frac": 7 * upd / (fp32 * 1e12) / (t["ms"] / 1e3)})
         sel = [0, int(np.argmax([g[0] for g in geo]))]
         chk_data = []
         for i in sel:
@@ -803,7 +809,8 @@ def other_paths(plan, q, img, flush, stream, dev, only=(), peaks=(6778.3, 80.5),
                 f"slices {sel}: oracle R* on the FP16-rounded sinograms at 100 random pixels each"
         checks["mixed64_fp16_persistent"] = chk
         return {"slices": len(geo), "updates": upd, "ms": ms, "Gupdates_s": upd / ms / 1e6, "storage": "fp16",
-                "launch": "one persistent launch (dynamic tile queue)"}
+                "launch": "bp_backproject_batched: one launch writes every slice's four-image row tables (and clears "
+                          "the images), one persistent launch backprojects all slices", "kernels": kern}
     guard("mixed64_fp16_persistent", mixed)
 
     # single 8192^2 slice, 8192 bins, 6000 angles: direct and Fourier

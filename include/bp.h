@@ -317,12 +317,18 @@ bp_status bp_fbp_host(bp_plan *plan, const float *sino, float *img, bp_filter_ki
                       float param, int batch, void *stream);
 
 /*
- * bp_backproject_batched -- R* (direct) of n independent slices with possibly different
- * geometries in ONE persistent kernel launch: CTAs pull (slice, tile) work items from a
- * device counter.  plans[i] gives slice i's geometry (all on the same device);
- * sinos[i] / imgs[i] are device pointers, dtypes[i] the sinogram element type.
- * The descriptor upload uses the first plan's stream-ordered workspace, so the call is
- * graph-capturable after one warm-up call with the same n.
+ * bp_backproject_batched -- R* (direct, Section 2 eq "bp_app") of n independent slices with
+ * possibly different geometries.  plans[i] gives slice i's geometry (all on the same device);
+ * sinos[i] / imgs[i] are device pointers (imgs overwritten), dtypes[i] the sinogram element
+ * type.  When every slice takes the four-image form (N even, mirror-symmetric angles, pixels
+ * no larger than bins; images 16-byte aligned): one launch writes every slice's row tables and
+ * clears the images, then ONE persistent launch backprojects all slices, each in its own
+ * geometry (at most 256 slices per launch pair, and as many as the first plan's table budget
+ * holds: its bp_set_direct_workspace bound, else a quarter of the free device memory; the
+ * tables live in a workspace of the first plan, grown on demand after a synchronisation of
+ * `stream`).  Otherwise ONE persistent kernel launch in which CTAs pull (slice, tile) work
+ * items from a device counter.  The descriptors travel in the kernel parameters; after one
+ * warm-up call with the same slices the call allocates nothing and can be graph-captured.
  */
 bp_status bp_backproject_batched(bp_plan *const *plans, const void *const *sinos,
                                  const bp_dtype *dtypes, float *const *imgs, int n, void *stream);

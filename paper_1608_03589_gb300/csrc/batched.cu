@@ -94,6 +94,7 @@ bp_batched_kernel(const __grid_constant__ BatchParams bpm, int *__restrict__ cou
 
 bp_status launch_batched(bp_plan *const *plans, const void *const *sinos, const bp_dtype *dtypes, float *const *imgs,
                          int n, cudaStream_t st) {
+    if (klein_mixed_eligible(plans, imgs, n)) return launch_klein_mixed(plans, sinos, dtypes, imgs, n, st);
     bp_plan *p0 = plans[0];
     if (!p0->d_counter) BP_CUDA_TRY(cudaMalloc(&p0->d_counter, sizeof(int)));
     static int sms = 0, dev_of_sms = -1;

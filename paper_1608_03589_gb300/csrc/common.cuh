@@ -144,6 +144,8 @@ struct KleinWork {
     float4 *tab = nullptr;               // row tables of tab_slices slices
     int tab_slices = 0;
     size_t tab_limit = 0;                // bp_set_direct_workspace (0: a quarter of the free memory)
+    float4 *mix_tab = nullptr;           // row tables of a mixed batch led by this plan
+    size_t mix_bytes = 0;
 };
 struct RadonShape {
     int kang = 0;   // 0 = the default rule
@@ -265,6 +267,9 @@ int klein_clamp_groups(const bp_plan *p, int S);
 bp_status launch_direct_klein(bp_plan *p, const void *sino, bp_dtype dt, float *img, int batch, int accumulate,
                               cudaStream_t st, float wuni, int stage, int S, const float *H = nullptr);
 bp_status klein_set_workspace(bp_plan *p, size_t bytes);
+bool klein_mixed_eligible(bp_plan *const *plans, float *const *imgs, int n);
+bp_status launch_klein_mixed(bp_plan *const *plans, const void *const *sinos, const bp_dtype *dtypes,
+                             float *const *imgs, int n, cudaStream_t st);
 bp_status launch_fbp_direct(bp_plan *p, const void *sino, bp_dtype dt, float *img, int kind, float param, int batch,
                             cudaStream_t st);
 void free_fourier(bp_plan *p);

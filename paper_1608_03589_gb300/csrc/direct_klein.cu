@@ -67,6 +67,21 @@ constexpr int kKMargin = 4;           // extra table entries beyond the reachabl
 // of a chunk of slices (angle k = r mod n_theta); the row is staged in shared memory with four
 // zeros on each side.  A plane holds RS >= L + kKW entries, so a window copied from any reachable
 // bin stays inside it; row r's planes start at entry 2 r RS.
+// The table entries m < L of one row (planes p0 and p0 + RS) from its values staged in shared
+// memory at sr[4 + j] with four zeros on each side, weight w; by the CTA's threads.
+__device__ __forceinline__ void klein_write_row(float4 *__restrict__ p0, const float *sr, int n_det, int jlo, int L,
+                                                int RS, float w) {
+    auto g = [&](int j) { return (j >= -4 && j < n_det + 4) ? sr[j + 4] : 0.f; };
+    float4 *p1 = p0 + RS;
+    for (int m = threadIdx.x; m < L; m += blockDim.x) {
+        const int j = jlo + m, jr = n_det - 1 - j;
+        const float a0 = g(j), a1 = g(j + 1), a2 = g(j + 2), a3 = g(j + 3);
+        const float b0 = g(jr), b1 = g(jr - 1), b2 = g(jr - 2), b3 = g(jr - 3);
+        p0[m] = make_float4(w * a0, w * b0, w * (a1 - a0), w * (b1 - b0));
+        p1[m] = make_float4(w * (a2 - a1), w * (b2 - b1), w * (a3 - a2), w * (b3 - b2));
+    }
+}
+
 template <typename Tin>
 __global__ void __launch_bounds__(256)
 klein_tables_kernel(const Tin *__restrict__ sino, float4 *__restrict__ tab, const AngleParam *__restrict__ ap,
@@ -80,16 +95,52 @@ klein_tables_kernel(const Tin *__restrict__ sino, float4 *__restrict__ tab, cons
         sg[i] = (j >= 0 && j < n_det) ? load_f(row + j) : 0.f;
     }
     __syncthreads();
-    const float w = wuni > 0.f ? wuni : ap[k].w;
-    auto g = [&](int j) { return (j >= -4 && j < n_det + 4) ? sg[j + 4] : 0.f; };
-    float4 *p0 = tab + 2 * r * RS, *p1 = p0 + RS;
-    for (int m = threadIdx.x; m < L; m += blockDim.x) {
-        const int j = jlo + m, jr = n_det - 1 - j;
-        const float a0 = g(j), a1 = g(j + 1), a2 = g(j + 2), a3 = g(j + 3);
-        const float b0 = g(jr), b1 = g(jr - 1), b2 = g(jr - 2), b3 = g(jr - 3);
-        p0[m] = make_float4(w * a0, w * b0, w * (a1 - a0), w * (b1 - b0));
-        p1[m] = make_float4(w * (a2 - a1), w * (b2 - b1), w * (a3 - a2), w * (b3 - b2));
+    klein_write_row(tab + 2 * r * RS, sg, n_det, jlo, L, RS, wuni > 0.f ? wuni : ap[k].w);
+}
+
+// Mixed batches (bp_backproject_batched): one CTA per row of every slice (rows d.row0 ..
+// d.row0 + n_theta - 1 of slice d), each slice's own geometry, element type and table block; a
+// row's CTA also clears its share of the slice's image (the main kernel adds into it).
+struct KleinTabSlice {
+    const void *sino;
+    float4 *tab;
+    const AngleParam *ap;
+    float4 *img;
+    int N, n_det, n_theta, jlo, L, RS, dtype, row0;
+};
+struct KleinTabBatch {
+    KleinTabSlice d[256];
+    int n;
+};
+static_assert(sizeof(KleinTabBatch) <= 31 * 1024, "kernel parameter block too large");
+
+__device__ __forceinline__ float load_any(const void *p, int dtype, long long i) {
+    if (dtype == BP_BF16) return load_f((const __nv_bfloat16 *)p + i);
+    if (dtype == BP_F16) return load_f((const __half *)p + i);
+    return load_f((const float *)p + i);
+}
+
+__global__ void __launch_bounds__(256) klein_tables_mixed_kernel(const __grid_constant__ KleinTabBatch tb) {
+    extern __shared__ float sg[];  // [max n_det + 8]
+    const int r = blockIdx.x;
+    int lo = 0, hi = tb.n - 1;  // the last slice with row0 <= r
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (tb.d[mid].row0 <= r) lo = mid;
+        else hi = mid - 1;
     }
+    const KleinTabSlice &d = tb.d[lo];
+    const int k = r - d.row0, n_det = d.n_det;
+    const long long base = (long long)k * n_det;
+    for (int i = threadIdx.x; i < n_det + 8; i += blockDim.x) {
+        const int j = i - 4;
+        sg[i] = (j >= 0 && j < n_det) ? load_any(d.sino, d.dtype, base + j) : 0.f;
+    }
+    const long long n4 = (long long)d.N * d.N / 4, per = (n4 + d.n_theta - 1) / d.n_theta;
+    const long long z1 = min(n4, (k + 1) * per);
+    for (long long i = k * per + threadIdx.x; i < z1; i += blockDim.x) d.img[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncthreads();
+    klein_write_row(d.tab + 2LL * k * d.RS, sg, n_det, d.jlo, d.L, d.RS, __ldg(&d.ap[k].w));
 }
 
 // The fused FBP form of the tables: the persistent row filter of filter_pt.cuh turns each row
@@ -107,17 +158,8 @@ struct KleinTabOut {
         for (int h = 0; h < 2; ++h) {
             if (h == 1 && !has1) break;
             const long long r = r0 + h;
-            const float *sr = sg + h * (n_det + 8);
-            const float w = wuni > 0.f ? wuni : ap[r % n_theta].w;
-            auto g = [&](int j) { return (j >= -4 && j < n_det + 4) ? sr[j + 4] : 0.f; };
-            float4 *p0 = tab + 2 * r * RS, *p1 = p0 + RS;
-            for (int m = threadIdx.x; m < L; m += blockDim.x) {
-                const int j = jlo + m, jr = n_det - 1 - j;
-                const float a0 = g(j), a1 = g(j + 1), a2 = g(j + 2), a3 = g(j + 3);
-                const float b0 = g(jr), b1 = g(jr - 1), b2 = g(jr - 2), b3 = g(jr - 3);
-                p0[m] = make_float4(w * a0, w * b0, w * (a1 - a0), w * (b1 - b0));
-                p1[m] = make_float4(w * (a2 - a1), w * (b2 - b1), w * (a3 - a2), w * (b3 - b2));
-            }
+            klein_write_row(tab + 2 * r * RS, sg + h * (n_det + 8), n_det, jlo, L, RS,
+                            wuni > 0.f ? wuni : ap[r % n_theta].w);
         }
     }
 };
@@ -289,18 +331,58 @@ struct StageSeq {
     }
 };
 
-// A persistent grid (the schedule in the header) over `batch` slices, slice sl's tables at
-// tab + sl tab_stride and its image at img + sl img_stride.  The warps take turns as producer:
+// Per-slice geometry of the persistent kernel, by slice index: the slices of one plan (tables and
+// images at fixed strides) or of several plans (one descriptor each, bp_backproject_batched).
+struct KleinGeoSame {
+    const KleinAngle *ka_;
+    const float4 *tab_;
+    float *img_;
+    int N_, n_theta_, RS_, jlo_, nr_, S_, batch_;
+    long long img_stride_, tab_stride_;
+    __device__ __forceinline__ const KleinAngle *ka(int) const { return ka_; }
+    __device__ __forceinline__ const float4 *tab(int sl) const { return tab_ + sl * tab_stride_; }
+    __device__ __forceinline__ float *img(int sl) const { return img_ + sl * img_stride_; }
+    __device__ __forceinline__ int N(int) const { return N_; }
+    __device__ __forceinline__ int n_theta(int) const { return n_theta_; }
+    __device__ __forceinline__ int RS(int) const { return RS_; }
+    __device__ __forceinline__ int jlo(int) const { return jlo_; }
+    __device__ __forceinline__ int nr(int) const { return nr_; }
+    __device__ __forceinline__ int S(int) const { return S_; }
+    __device__ __forceinline__ int batch() const { return batch_; }
+};
+struct KleinSlice {
+    const KleinAngle *ka;
+    const float4 *tab;
+    float *img;
+    int N, n_theta, RS, jlo, nr, S;
+};
+constexpr int kKMaxSlices = 256;  // descriptors per launch (larger batches take several)
+struct KleinGeoMixed {
+    KleinSlice d[kKMaxSlices];
+    int n;
+    __device__ __forceinline__ const KleinAngle *ka(int sl) const { return d[sl].ka; }
+    __device__ __forceinline__ const float4 *tab(int sl) const { return d[sl].tab; }
+    __device__ __forceinline__ float *img(int sl) const { return d[sl].img; }
+    __device__ __forceinline__ int N(int sl) const { return d[sl].N; }
+    __device__ __forceinline__ int n_theta(int sl) const { return d[sl].n_theta; }
+    __device__ __forceinline__ int RS(int sl) const { return d[sl].RS; }
+    __device__ __forceinline__ int jlo(int sl) const { return d[sl].jlo; }
+    __device__ __forceinline__ int nr(int sl) const { return d[sl].nr; }
+    __device__ __forceinline__ int S(int sl) const { return d[sl].S; }
+    __device__ __forceinline__ int batch() const { return n; }
+};
+static_assert(sizeof(KleinGeoMixed) <= 31 * 1024, "kernel parameter block too large");
+
+// A persistent grid (the schedule in the header) over geo.batch() slices, slice sl's tables at
+// geo.tab(sl) and its image at geo.img(sl).  The warps take turns as producer:
 // after finishing stage s, warp s mod 8 copies the windows of stage s - 1 + NBUF (cp.async.bulk,
 // 768 bytes per image) from the row tables into the buffer of stage s - 1, once every warp has
 // left it.  img is added to atomically (cleared before unless accumulating).  Every wait is
 // bounded: on expiry the kernel sets *err, waits (bounded) for the copies it issued and returns.
 // MULTI false: one slice (batch 1), without the slice bookkeeping.
-template <int MINB, int NBUF, int BPT, int STG, bool MULTI>
+template <int MINB, int NBUF, int BPT, int STG, bool MULTI, typename Geo>
 __global__ void __launch_bounds__(kKThreads / BPT, MINB)
-bp_direct_klein_kernel(float *__restrict__ img, const KleinAngle *__restrict__ ka, const float4 *__restrict__ tab,
-                       int N, int n_theta, int RS, int jlo, int nr, int S, int batch, long long img_stride,
-                       long long tab_stride, int *__restrict__ err) {
+bp_direct_klein_kernel(const __grid_constant__ Geo geo, int *__restrict__ err) {
     // [NBUF][row k, row k'][plane 0, 1][STG][kKW] entries of 16 bytes
     extern __shared__ __align__(128) ulonglong2 ktab[];
     __shared__ float4 prmA[NBUF][STG], prmO[NBUF][STG];
@@ -313,10 +395,10 @@ bp_direct_klein_kernel(float *__restrict__ img, const KleinAngle *__restrict__ k
     const int bx = (lane & 3) + 4 * (qtr & 1) + (BPT == 1 ? 8 * (warp & 1) : 0);
     const int by = ((lane >> 2) & 1) + 2 * (qtr >> 1) + 4 * (BPT == 1 ? warp >> 1 : warp);
     const float fx = (float)(2 * bx), fy = (float)(2 * by);
-    const int h2 = N / 2;
-    const int R = nr * nr, cta = blockIdx.x, nctas = gridDim.x;
+    const int cta = blockIdx.x, nctas = gridDim.x;
+    auto regions = [&](int sl) { return geo.nr(sl) * geo.nr(sl); };
     StageSeq<STG> cons;
-    cons.enter(0, S, n_theta, R, cta, nctas);
+    cons.enter(0, geo.S(0), geo.n_theta(0), regions(0), cta, nctas);
     StageSeq<STG> prod = cons;
     const unsigned tab_u32 = smem_u32(ktab);
     const uint32_t fb = smem_u32(&full[0]), eb = smem_u32(&empty[0]);
@@ -337,21 +419,21 @@ bp_direct_klein_kernel(float *__restrict__ img, const KleinAngle *__restrict__ k
     auto produce = [&](bool issue) -> bool {
         int rg, k0, kn;
         bool last;
-        while (!prod.next(rg, k0, kn, last, S, n_theta, R, cta, nctas)) {
-            if (!MULTI || psl + 1 >= batch) return false;
+        while (!prod.next(rg, k0, kn, last, geo.S(psl), geo.n_theta(psl), regions(psl), cta, nctas)) {
+            if (!MULTI || psl + 1 >= geo.batch()) return false;
             ++psl;
-            prod.enter(0, S, n_theta, R, cta, nctas);
+            prod.enter(0, geo.S(psl), geo.n_theta(psl), regions(psl), cta, nctas);
         }
         const int b = pstage % NBUF;
         ++pstage;
         if (!issue) return true;
-        const int rx = rg % nr, ry = rg / nr;
+        const int nr = geo.nr(psl), rx = rg % nr, ry = rg / nr;
         const float4 *src0 = nullptr, *src1 = nullptr;
         int w = 0;
         bool f2 = true;
         if (lane < kn) {
             const int kk = lane;
-            const KleinAngle a = ka[k0 + kk];
+            const KleinAngle a = geo.ka(psl)[k0 + kk];
             const long long U = a.U00 + (long long)(kKRegion * rx) * a.CP + (long long)(kKRegion * ry) * a.SP;
             const int Ji = (int)(U >> 32);
             const float frac = (float)(unsigned)(U & 0xffffffffLL) * 2.3283064365386963e-10f;
@@ -363,7 +445,8 @@ bp_direct_klein_kernel(float *__restrict__ img, const KleinAngle *__restrict__ k
             f2 = af - 1.f >= 0.f;
             prmA[b][kk] = make_float4((float)(Ji - J0) + frac + lo, a.c, a.s, __int_as_float(w));
             prmO[b][kk] = make_float4(ac - 1.f, as - 1.f, af - 1.f, af - 2.f);
-            const float4 *ts = MULTI ? tab + psl * tab_stride : tab;
+            const float4 *ts = geo.tab(psl);
+            const int RS = geo.RS(psl), jlo = geo.jlo(psl);
             src0 = ts + 2 * (long long)a.row * RS + (J0 - jlo);
             src1 = ts + 2 * (long long)kp * RS + (J0 - jlo);
         }
@@ -382,7 +465,7 @@ bp_direct_klein_kernel(float *__restrict__ img, const KleinAngle *__restrict__ k
             // the angle's four 768-byte windows: rows k and k', planes 0 and 1
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const float4 *src = (q < 2 ? src0 : src1) + (q & 1) * (long long)RS;
+                const float4 *src = (q < 2 ? src0 : src1) + (q & 1) * (long long)geo.RS(psl);
                 const unsigned dst = tab_u32 + (unsigned)(((b * 4 + q) * STG + lane) * kKWin);
                 asm volatile(
                     "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
@@ -412,15 +495,15 @@ bp_direct_klein_kernel(float *__restrict__ img, const KleinAngle *__restrict__ k
     clear();
     int sst = 0;  // stages consumed
     int csl = 0;  // the consumer's slice
-    float *im = img;
+    float *im = geo.img(0);
     int rg, k0, kn;
     bool last;
     for (;;) {
-        if (!cons.next(rg, k0, kn, last, S, n_theta, R, cta, nctas)) {
-            if (!MULTI || csl + 1 >= batch) break;
+        if (!cons.next(rg, k0, kn, last, geo.S(csl), geo.n_theta(csl), regions(csl), cta, nctas)) {
+            if (!MULTI || csl + 1 >= geo.batch()) break;
             ++csl;
-            im = img + csl * img_stride;
-            cons.enter(0, S, n_theta, R, cta, nctas);
+            im = geo.img(csl);
+            cons.enter(0, geo.S(csl), geo.n_theta(csl), regions(csl), cta, nctas);
             continue;
         }
         if (!mbar_wait(fb + 8 * b, ph)) {
@@ -482,7 +565,8 @@ bp_direct_klein_kernel(float *__restrict__ img, const KleinAngle *__restrict__ k
         if (last) {
             // flush: pixel px + 2 py of a block has role (px + 2 py) ^ role; pair A holds images 0
             // and -P, pair B images M_x and M_y (exchanged while dir = 1)
-            const int rx = rg % nr, ry = rg / nr;
+            const int nr = geo.nr(csl), rx = rg % nr, ry = rg / nr;
+            const int N = geo.N(csl), h2 = N / 2;
             const int iy = kKRegion * ry + 2 * by;
 #pragma unroll
             for (int h = 0; h < BPT; ++h) {
@@ -636,9 +720,12 @@ void klein_plan(bp_plan *p) {
 void free_klein(bp_plan *p) {
     cudaFree(p->klein.d_ang);
     cudaFree(p->klein.tab);
+    cudaFree(p->klein.mix_tab);
     p->klein.d_ang = nullptr;
     p->klein.tab = nullptr;
     p->klein.tab_slices = 0;
+    p->klein.mix_tab = nullptr;
+    p->klein.mix_bytes = 0;
 }
 
 // Default angle groups: about one per 96 MB of row tables, so that one group's rows mostly stay
@@ -723,6 +810,16 @@ bp_status klein_set_workspace(bp_plan *p, size_t bytes) {
 
 namespace {
 
+// The per-slot angle records, uploaded on first use.
+bp_status klein_upload(bp_plan *p) {
+    KleinWork &kw = p->klein;
+    if (!kw.d_ang) {
+        BP_CUDA_TRY(cudaMalloc(&kw.d_ang, kw.host.size()));
+        BP_CUDA_TRY(cudaMemcpy(kw.d_ang, kw.host.data(), kw.host.size(), cudaMemcpyHostToDevice));
+    }
+    return BP_OK;
+}
+
 // Slices whose tables the workspace holds at once for a call of `batch` slices: all of them
 // while they fit the budget (the bp_set_direct_workspace bound, else a quarter of the device
 // memory free when the workspace grows), else as many as the budget holds (at least one).  The
@@ -764,17 +861,15 @@ bp_status launch_klein_t(bp_plan *p, const Tin *sino, float *img, int batch, int
                          float wuni, int S, const float *H) {
     constexpr int NT = kKThreads / BPT;
     KleinWork &kw = p->klein;
-    if (!kw.d_ang) {
-        BP_CUDA_TRY(cudaMalloc(&kw.d_ang, kw.host.size()));
-        BP_CUDA_TRY(cudaMemcpy(kw.d_ang, kw.host.data(), kw.host.size(), cudaMemcpyHostToDevice));
-    }
+    bp_status s = klein_upload(p);
+    if (s != BP_OK) return s;
     const int RS = kw.L + kKW;
     S = klein_clamp_groups(p, S);
     constexpr size_t smem = (size_t)NBUF * 4 * STG * kKWin;
     if ((size_t)(p->n_det + 8) * sizeof(float) > 200u * 1024u)
         return fail(BP_ERR_UNSUPPORTED, "direct R*: detector row too long for the four-image form's tables");
     int chunk = 1;
-    bp_status s = klein_reserve(p, batch, st, &chunk);
+    s = klein_reserve(p, batch, st, &chunk);
     if (s != BP_OK) return s;
     const size_t img_n = (size_t)p->N * p->N, sino_n = (size_t)p->n_theta * p->n_det;
     const long long tab_stride = 2LL * p->n_theta * RS;
@@ -785,8 +880,8 @@ bp_status launch_klein_t(bp_plan *p, const Tin *sino, float *img, int batch, int
         BP_CUDA_TRY(cudaMemsetAsync(img, 0, sizeof(float) * img_n * batch, st));
         stage_mark(p, st, "memset (direct R* image)");
     }
-    auto kern1 = bp_direct_klein_kernel<MINB, NBUF, BPT, STG, false>;
-    auto kernm = bp_direct_klein_kernel<MINB, NBUF, BPT, STG, true>;
+    auto kern1 = bp_direct_klein_kernel<MINB, NBUF, BPT, STG, false, KleinGeoSame>;
+    auto kernm = bp_direct_klein_kernel<MINB, NBUF, BPT, STG, true, KleinGeoSame>;
     static int per_sm = 0;
     if (!per_sm) {
         BP_CUDA_TRY(cudaFuncSetAttribute(kern1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -807,8 +902,8 @@ bp_status launch_klein_t(bp_plan *p, const Tin *sino, float *img, int batch, int
         s = H ? klein_filter_tables(p, sc, cn, H, st, wuni, clear_in_tables ? ic : nullptr)
               : klein_tables(p, sc, cn, st, wuni);
         if (s != BP_OK) return s;
-        (cn > 1 ? kernm : kern1)<<<grid, NT, smem, st>>>(ic, ka, kw.tab, p->N, p->n_theta, RS, kw.jlo, kw.nr, S, cn,
-                                                         (long long)img_n, tab_stride, p->d_err);
+        const KleinGeoSame geo{ka, kw.tab, ic, p->N, p->n_theta, RS, kw.jlo, kw.nr, S, cn, (long long)img_n, tab_stride};
+        (cn > 1 ? kernm : kern1)<<<grid, NT, smem, st>>>(geo, p->d_err);
         BP_CUDA_TRY(cudaGetLastError());
         stage_mark(p, st, cn > 1 ? "bp_direct_klein_batch_kernel" : "bp_direct_klein_kernel");
     }
@@ -845,6 +940,105 @@ bp_status launch_direct_klein(bp_plan *p, const void *sino, bp_dtype dt, float *
     if (stage == 8) return launch_klein_dt<4, 2, 6>(p, sino, dt, img, batch, accumulate, st, wuni, S, H);
     if (stage == 32) return launch_klein_dt<3, 2, 8>(p, sino, dt, img, batch, accumulate, st, wuni, S, H);
     return launch_klein_dt<3, 1, 8>(p, sino, dt, img, batch, accumulate, st, wuni, S, H);
+}
+
+
+// ---------------------------------------------------------------------------------- mixed batches
+// bp_backproject_batched when every slice takes the four-image form: slices in chunks whose
+// tables fit the budget of plans[0] (its bp_set_direct_workspace bound, else a quarter of the free
+// device memory; at least one slice), per chunk one launch that writes every slice's tables and
+// clears its image, and one persistent launch of the two-blocks-per-thread kernel over the
+// chunk's slices, each with its own geometry and the angle groups of its default launch shape.
+bool klein_mixed_eligible(bp_plan *const *plans, float *const *imgs, int n) {
+    for (int i = 0; i < n; ++i) {
+        const bp_plan *p = plans[i];
+        if (!p->klein.eligible || (size_t)(p->n_det + 8) * sizeof(float) > 200u * 1024u || !aligned16(imgs[i]))
+            return false;
+    }
+    return true;
+}
+
+bp_status launch_klein_mixed(bp_plan *const *plans, const void *const *sinos, const bp_dtype *dtypes,
+                             float *const *imgs, int n, cudaStream_t st) {
+    constexpr int MINB = 3, NBUF = 3, BPT = 2, STG = 8, NT = kKThreads / BPT;
+    constexpr size_t smem = (size_t)NBUF * 4 * STG * kKWin;
+    bp_plan *p0 = plans[0];
+    KleinWork &w0 = p0->klein;
+    size_t most = 0, nd_max = 0;
+    for (int i = 0; i < n; ++i) {
+        bp_status s = klein_upload(plans[i]);
+        if (s != BP_OK) return s;
+        most = std::max(most, klein_slice_bytes(plans[i]));
+        nd_max = std::max(nd_max, (size_t)plans[i]->n_det);
+    }
+    size_t budget = w0.tab_limit;
+    if (!budget) {
+        size_t free_b = 0, total_b = 0;
+        BP_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+        budget = (free_b + w0.mix_bytes) / 4;
+    }
+    // the workspace: the largest chunk the budget allows (at least the largest slice)
+    size_t need = 0;
+    for (int c0 = 0; c0 < n;) {
+        size_t bytes = 0;
+        int c1 = c0;
+        while (c1 < n && c1 - c0 < kKMaxSlices &&
+               (c1 == c0 || bytes + klein_slice_bytes(plans[c1]) <= std::max(budget, most)))
+            bytes += klein_slice_bytes(plans[c1++]);
+        need = std::max(need, bytes);
+        c0 = c1;
+    }
+    if (need > w0.mix_bytes) {
+        if (w0.mix_tab) {
+            BP_CUDA_TRY(cudaStreamSynchronize(st));  // no queued launch may still read the old tables
+            cudaFree(w0.mix_tab);
+            w0.mix_tab = nullptr;
+            w0.mix_bytes = 0;
+        }
+        BP_CUDA_TRY(cudaMalloc(&w0.mix_tab, need));
+        w0.mix_bytes = need;
+    }
+    auto kern = bp_direct_klein_kernel<MINB, NBUF, BPT, STG, true, KleinGeoMixed>;
+    static int per_sm = 0;
+    if (!per_sm) {
+        BP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        BP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem));
+        per_sm = std::max(1, per_sm);
+    }
+    const size_t tsmem = sizeof(float) * (nd_max + 8);
+    if (tsmem > 48 * 1024)
+        BP_CUDA_TRY(cudaFuncSetAttribute(klein_tables_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)tsmem));
+    stage_begin(p0, st);
+    for (int c0 = 0; c0 < n;) {
+        KleinTabBatch tb;
+        KleinGeoMixed geo;
+        size_t off = 0;  // float4 entries
+        int rows = 0, c1 = c0;
+        while (c1 < n && c1 - c0 < kKMaxSlices &&
+               (c1 == c0 || (off * sizeof(float4) + klein_slice_bytes(plans[c1])) <= std::max(budget, most))) {
+            const bp_plan *p = plans[c1];
+            const KleinWork &kw = p->klein;
+            const int i = c1 - c0, RS = kw.L + kKW;
+            float4 *tab = w0.mix_tab + off;
+            tb.d[i] = KleinTabSlice{sinos[c1], tab, p->d_ang, (float4 *)imgs[c1], p->N, p->n_det, p->n_theta, kw.jlo,
+                                    kw.L, RS, (int)dtypes[c1], rows};
+            geo.d[i] = KleinSlice{(const KleinAngle *)kw.d_ang, tab, imgs[c1], p->N, p->n_theta, RS, kw.jlo, kw.nr,
+                                  klein_clamp_groups(p, direct_shape(p, BP_F32, 1).asplit)};
+            off += klein_slice_bytes(p) / sizeof(float4);
+            rows += p->n_theta;
+            ++c1;
+        }
+        tb.n = geo.n = c1 - c0;
+        klein_tables_mixed_kernel<<<rows, 256, tsmem, st>>>(tb);
+        BP_CUDA_TRY(cudaGetLastError());
+        stage_mark(p0, st, "klein_tables_mixed_kernel");
+        kern<<<per_sm * std::max(1, p0->sm_count), NT, smem, st>>>(geo, p0->d_err);
+        BP_CUDA_TRY(cudaGetLastError());
+        stage_mark(p0, st, "bp_direct_klein_mixed_kernel");
+        c0 = c1;
+    }
+    return BP_OK;
 }
 
 }  // namespace bp
