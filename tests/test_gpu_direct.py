@@ -110,12 +110,18 @@ def test_direct_full_size_sampled(shape):
     plan = bp.Plan(wl.N, wl.n_det, wl.theta, wl.det_spacing)
     if shape == "autotuned":
         plan.autotune("direct", torch.float32, 1)
-    q = plan.filter(to_dev(wl.sinogram()), "shepp-logan")
+    g = to_dev(wl.sinogram())
+    q = plan.filter(g, "shepp-logan")
     img = plan.backproject(q)
     pix = sample_pixels(wl.N, 400, seed=1)
     ref = oracle.bp_linear_points(rounded(q), wl.N, wl.theta, wl.det_spacing, pix)
     got = img.reshape(-1)[torch.from_numpy(pix).to(dev())].cpu().numpy()
     assert oracle.rel_l2(got, ref) <= TOL_DIRECT
+    # the benchmark's step: the filter writing the row tables (its filtered values are bp_filter's)
+    fused = plan.fbp_direct(g, "shepp-logan")
+    got = fused.reshape(-1)[torch.from_numpy(pix).to(dev())].cpu().numpy()
+    assert oracle.rel_l2(got, ref) <= TOL_DIRECT
+    assert oracle.rel_l2(fused.cpu().numpy(), img.cpu().numpy()) <= 1e-6
 
 
 def test_direct_full_size_shuffled_angles():
