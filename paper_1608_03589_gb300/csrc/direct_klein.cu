@@ -66,7 +66,9 @@ constexpr int kKMargin = 4;           // extra table entries beyond the reachabl
 // quarter warp (8 consecutive entries of a plane) are free of bank conflicts.  One CTA per row r
 // of a chunk of slices (angle k = r mod n_theta); the row is staged in shared memory with four
 // zeros on each side.  A plane holds RS >= L + kKW entries, so a window copied from any reachable
-// bin stays inside it; row r's planes start at entry 2 r RS.
+// bin stays inside it; row r's planes start at entry 2 r RS.  zero (unless null): the chunk's
+// images, N^2 / 4 float4 each, cleared for the main kernel's atomic adds, each row's CTA its
+// share of its slice's image.
 // The table entries m < L of one row (planes p0 and p0 + RS) from its values staged in shared
 // memory at sr[4 + j] with four zeros on each side, weight w; by the CTA's threads.
 __device__ __forceinline__ void klein_write_row(float4 *__restrict__ p0, const float *sr, int n_det, int jlo, int L,
@@ -85,7 +87,7 @@ __device__ __forceinline__ void klein_write_row(float4 *__restrict__ p0, const f
 template <typename Tin>
 __global__ void __launch_bounds__(256)
 klein_tables_kernel(const Tin *__restrict__ sino, float4 *__restrict__ tab, const AngleParam *__restrict__ ap,
-                    int n_theta, int n_det, int jlo, int L, int RS, float wuni) {
+                    int n_theta, int n_det, int jlo, int L, int RS, float wuni, float4 *__restrict__ zero, long long n4) {
     extern __shared__ float sg[];  // [n_det + 8]
     const long long r = blockIdx.x;
     const int k = (int)(r % n_theta);
@@ -93,6 +95,11 @@ klein_tables_kernel(const Tin *__restrict__ sino, float4 *__restrict__ tab, cons
     for (int i = threadIdx.x; i < n_det + 8; i += blockDim.x) {
         const int j = i - 4;
         sg[i] = (j >= 0 && j < n_det) ? load_f(row + j) : 0.f;
+    }
+    if (zero) {
+        float4 *im = zero + (r / n_theta) * n4;
+        const long long per = (n4 + n_theta - 1) / n_theta, z1 = min(n4, (k + 1) * per);
+        for (long long i = k * per + threadIdx.x; i < z1; i += blockDim.x) im[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     __syncthreads();
     klein_write_row(tab + 2 * r * RS, sg, n_det, jlo, L, RS, wuni > 0.f ? wuni : ap[k].w);
@@ -740,14 +747,16 @@ int klein_clamp_groups(const bp_plan *p, int S) { return std::max(1, std::min(st
 
 namespace {
 
-// Row tables of `n` slices (rows r = 0 .. n n_theta - 1) into the workspace.
+// Row tables of `n` slices (rows r = 0 .. n n_theta - 1) into the workspace; their images cleared
+// on the way when `zero` is given.
 template <typename Tin>
-bp_status klein_tables(bp_plan *p, const Tin *sino, int n, cudaStream_t st, float wuni) {
+bp_status klein_tables(bp_plan *p, const Tin *sino, int n, cudaStream_t st, float wuni, float *zero) {
     const size_t smem = sizeof(float) * ((size_t)p->n_det + 8);
     auto kern = klein_tables_kernel<Tin>;
     if (smem > 48 * 1024) BP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     kern<<<(unsigned)(n * p->n_theta), 256, smem, st>>>(sino, p->klein.tab, p->d_ang, p->n_theta, p->n_det,
-                                                        p->klein.jlo, p->klein.L, p->klein.L + kKW, wuni);
+                                                        p->klein.jlo, p->klein.L, p->klein.L + kKW, wuni,
+                                                        (float4 *)zero, (long long)p->N * p->N / 4);
     BP_CUDA_TRY(cudaGetLastError());
     stage_mark(p, st, "klein_tables_kernel");
     return BP_OK;
@@ -874,8 +883,8 @@ bp_status launch_klein_t(bp_plan *p, const Tin *sino, float *img, int batch, int
     const size_t img_n = (size_t)p->N * p->N, sino_n = (size_t)p->n_theta * p->n_det;
     const long long tab_stride = 2LL * p->n_theta * RS;
     stage_begin(p, st);
-    // the fused FBP form clears the images inside its table launch (N even: N^2 / 4 float4)
-    const bool clear_in_tables = H && !accumulate && aligned16(img) && img_n % 4 == 0;
+    // the table launch clears the images (N even: N^2 / 4 float4)
+    const bool clear_in_tables = !accumulate && aligned16(img) && img_n % 4 == 0;
     if (!accumulate && !clear_in_tables) {
         BP_CUDA_TRY(cudaMemsetAsync(img, 0, sizeof(float) * img_n * batch, st));
         stage_mark(p, st, "memset (direct R* image)");
@@ -900,7 +909,7 @@ bp_status launch_klein_t(bp_plan *p, const Tin *sino, float *img, int batch, int
         const Tin *sc = sino + sino_n * c0;
         float *ic = img + img_n * c0;
         s = H ? klein_filter_tables(p, sc, cn, H, st, wuni, clear_in_tables ? ic : nullptr)
-              : klein_tables(p, sc, cn, st, wuni);
+              : klein_tables(p, sc, cn, st, wuni, clear_in_tables ? ic : nullptr);
         if (s != BP_OK) return s;
         const KleinGeoSame geo{ka, kw.tab, ic, p->N, p->n_theta, RS, kw.jlo, kw.nr, S, cn, (long long)img_n, tab_stride};
         (cn > 1 ? kernm : kern1)<<<grid, NT, smem, st>>>(geo, p->d_err);

@@ -463,6 +463,9 @@ def test_direct_four_image_form(N, n_det, n_theta, dt_scale, seed, angles):
     acc = base.clone()
     plan.backproject(g, out=acc, accumulate=True)
     assert oracle.rel_l2(acc.cpu().numpy(), img.cpu().numpy() + rounded(base)) <= TOL_DIRECT
+    dirty = torch.full_like(img, 7.0)  # cleared inside the table launch
+    plan.backproject(g, out=dirty)
+    assert oracle.rel_l2(dirty.cpu().numpy(), img.cpu().numpy()) <= 1e-6
     g16 = g.to(torch.bfloat16)  # a batch of 16-bit slices: one persistent launch builds each slice's tables
     img16 = plan.backproject(g16)
     for i in range(2):
