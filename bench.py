@@ -989,8 +989,8 @@ def run_gpu(args, world, rank, local):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": wl.name, "N": wl.N, "n_det": wl.n_det, "n_theta": wl.n_theta,
                    "phantom": "50 seeded random ellipses + 1% Gaussian noise", "filter": "shepp-logan",
-                   "step": "bp_fbp_direct (the filter writes the four-image form's row tables, then the "
-                           "image memset and the direct R* kernel)",
+                   "step": "bp_fbp_direct: one launch filters the rows into the four-image form's row tables "
+                           "and clears the image, one launch runs the direct R* kernel",
                    "l2": "flushed (256 MiB write) between steps",
                    "launch_shape": {"stage": shape[0], "angle_groups": shape[1],
                                     "picked_by": picked},
