@@ -907,7 +907,7 @@ fft_pt_fwd_kernel(const float *__restrict__ img, const float2 *__restrict__ Tin,
     constexpr int M = 1 << LOGM, NT = M / kPassE, Rl = PL::Rl, Gl = kPassE / Rl;
     constexpr int TWN = pt_offset<LOGM>(PL::npass);
     static_assert(TWN % 2 == 0, "per-pass twiddle count");
-    extern __shared__ __align__(16) float2 pz[];
+    extern __shared__ __align__(128) float2 pz[];
     float2 *z = pz;      // [M] work array
     float2 *T = z + M;   // [TWN] per-pass twiddles
     const int t = threadIdx.x;
@@ -985,7 +985,7 @@ fft_pt_fwd_cols_kernel(const float2 *__restrict__ Tin, float2 *__restrict__ out,
     constexpr int N = M / 2, h = N / 2;
     constexpr int RV[4] = {0, 1, kPassE - 2, kPassE - 1};  // the inputs inside the image
     static_assert(TWN % 2 == 0, "per-pass twiddle count");
-    extern __shared__ __align__(16) float2 pz[];
+    extern __shared__ __align__(128) float2 pz[];
     float2 *z = pz;          // [M] work array
     float2 *T = z + M;       // [TWN] per-pass twiddles
     float2 *hold = T + TWN;  // [4 NT] second column's inputs
